@@ -1,0 +1,137 @@
+"""Pins of the FP64 C LBM oracle (oracle/lbm_oracle.c) against closed forms, conservation
+laws, symmetry and convergence orders.  CPU only; each case runs in seconds."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbm, uq
+
+
+def _tgv(n, steps, nu=0.04, u0=0.01, **kw):
+    return lbm.Case(lbm.TGV, n, n, steps, nu, u0, u_ref=kw.pop("u_ref", u0), **kw)
+
+
+def test_rest_state_stays_at_rest():
+    r = lbm.run([_tgv(16, 50, u0=0.0, u_ref=1.0)])[0]
+    assert np.all(r.u == 0.0) and np.all(r.v == 0.0)
+    assert np.allclose(r.rho, 1.0, rtol=0, atol=1e-15)
+
+
+def test_tgv_conserves_mass_and_momentum():
+    """Periodic BGK: sum f and sum c f are collision invariants and streaming permutes f."""
+    c = _tgv(32, 1000, amp2=0.001, amp3=-0.0007)
+    r = lbm.run([c])[0]
+    assert abs(r.mass - 32 * 32) / (32 * 32) < 1e-13
+    # initial momentum is zero by symmetry of the sine modes
+    assert abs(r.mom_x) < 1e-13 * 32 * 32 and abs(r.mom_y) < 1e-13 * 32 * 32
+
+
+def test_tgv_initial_energy_is_one():
+    """sum sin^2(kx) cos^2(ky) = N^2/4 on the lattice, so K(0) = 1 when u0 = u_ref."""
+    r = lbm.run([_tgv(64, 0, qoi_every=1)])[0]
+    # u = (sum c f) / rho recovers u0 ~ 1e-2 from O(1) populations: ~1e-14 relative rounding
+    assert abs(r.series[0] - 1.0) < 1e-12 and abs(r.k_final - 1.0) < 1e-12
+
+
+def test_tgv_decay_matches_closed_form():
+    """K(t) = exp(-4 nu k^2 t) (Sec. 8.2, t_d = 1 / (nu (kx^2 + ky^2))) within the O(dx^2) error."""
+    n, nu = 64, 0.04
+    r = lbm.run([_tgv(n, 1000, nu=nu, qoi_every=100)])[0]
+    k = 2 * math.pi / n
+    ref = uq.tgv_k_analytic(nu, k, np.arange(0, 1001, 100))
+    assert np.all(np.abs(r.series - ref) / ref < 5e-3)
+    # the per-sample velocity field decays as exp(-2 nu k^2 t) with the initial shape
+    x = np.arange(n)[None, :]
+    y = np.arange(n)[:, None]
+    dec = math.exp(-2 * nu * k * k * 1000)
+    ua = 0.01 * np.sin(k * x) * np.cos(k * y) * dec
+    va = -0.01 * np.cos(k * x) * np.sin(k * y) * dec
+    err = uq.relative_l2(np.stack([r.u, r.v]), np.stack([ua, va]))
+    assert err < 3e-3
+
+
+def test_tgv_second_order_under_diffusive_refinement():
+    """N = 16/32/64 at fixed tau, u0 ~ 1/N, T ~ N^2: L2 error of u falls as N^-2."""
+    errs = []
+    ns = [16, 32, 64]
+    for n in ns:
+        steps = int(60 * (n / 16) ** 2)
+        u0 = 0.04 * 16 / n
+        r = lbm.run([_tgv(n, steps, nu=0.05, u0=u0)])[0]
+        k = 2 * math.pi / n
+        x = np.arange(n)[None, :]
+        y = np.arange(n)[:, None]
+        dec = math.exp(-2 * 0.05 * k * k * steps)
+        ua = u0 * np.sin(k * x) * np.cos(k * y) * dec
+        va = -u0 * np.cos(k * x) * np.sin(k * y) * dec
+        errs.append(uq.relative_l2(np.stack([r.u, r.v]), np.stack([ua, va])))
+    order = -np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert 1.85 < order < 2.15, (errs, order)
+
+
+def _channel(h, nu=0.1, **kw):
+    u = 0.02 * 10 / h
+    return lbm.Case(lbm.CHANNEL, 4 * h, h, int(6 * h * h / nu), nu, u, u_ref=0.0, **kw)
+
+
+def test_channel_poiseuille_profile_second_order():
+    """Walls (halfway bounce-back) + velocity inlet + pressure outlet: the developed profile is
+    the inlet parabola 4 u_max y (H - y) / H^2 (Sec. 8.1 inflow), to second order in H."""
+    errs = []
+    for h in (10, 20):
+        c = _channel(h)
+        r = lbm.run([c])[0]
+        y = np.arange(h) + 0.5
+        ua = 4 * 1.5 * c.u0 * y * (h - y) / h ** 2
+        prof = r.u[:, 2 * h]
+        errs.append(np.linalg.norm(prof - ua) / np.linalg.norm(ua))
+        assert np.abs(r.v[:, 2 * h]).max() < 1e-4 * c.u0   # no cross-flow in the developed part
+    assert errs[0] < 0.03
+    order = math.log(errs[0] / errs[1], 2)
+    assert 1.8 < order < 2.2, (errs, order)
+
+
+def test_channel_without_obstacle_has_no_force():
+    r = lbm.run([_channel(10)])[0]
+    assert r.cd == 0.0 and r.cl == 0.0
+
+
+def _cyl(nd, steps, cy=None, **kw):
+    dx = 0.1 / nd
+    nx, ny = round(2.2 / dx), round(0.41 / dx)
+    u = 0.04
+    return lbm.Case(lbm.CHANNEL, nx, ny, steps, u * nd / 20.0, u, u_ref=0.0, cyl_cx=0.2 / dx,
+                    cyl_cy=(0.2 / dx) if cy is None else cy, cyl_r=0.05 / dx,
+                    ramp_steps=kw.pop("ramp", 0), **kw)
+
+
+def test_obstacle_mask_is_staircase_circle():
+    c = _cyl(20, 1)
+    m = lbm.obstacle_mask(c).astype(bool)
+    yy, xx = np.mgrid[0:c.ny, 0:c.nx]
+    inside = ((xx + 0.5 - 40.0) ** 2 + (yy + 0.5 - 40.0) ** 2) < 100.0
+    assert np.array_equal(m, inside)
+    # a 20-node-diameter disc covers close to pi r^2 = 314 nodes
+    assert abs(m.sum() - math.pi * 100) < 20
+
+
+def test_symmetric_obstacle_gives_mirror_flow_and_no_lift():
+    """Obstacle centred in the channel: the y -> H - y mirror maps the flow onto itself, so
+    v is odd, u and rho are even, and the lift vanishes to round-off."""
+    nd = 10
+    c = _cyl(nd, 1500, cy=0.205 / (0.1 / nd), qoi_every=100)
+    r = lbm.run([c])[0]
+    assert np.allclose(r.u, r.u[::-1, :], rtol=0, atol=1e-14)
+    assert np.allclose(r.v, -r.v[::-1, :], rtol=0, atol=1e-14)
+    assert np.allclose(r.rho, r.rho[::-1, :], rtol=0, atol=1e-13)
+    assert abs(r.cl) < 1e-10 and r.cd > 0.0
+
+
+@pytest.mark.slow
+def test_cylinder_drag_loose_anchor():
+    """Nominal drag at 20 nodes per diameter within 10% of the paper's deterministic value
+    (Sec. 8.1, table of C_D statistics; different boundary schemes, so a loose anchor)."""
+    c = _cyl(20, 60000, qoi_every=100, steady_tol=1e-7, ramp=2000)
+    r = lbm.run([c])[0]
+    assert abs(r.cd - 5.63208) / 5.63208 < 0.10, r.cd

@@ -1,0 +1,341 @@
+"""Benchmark of the ensemble lattice-Boltzmann UQ hot path on GB300.
+
+One step = one whole pass of the hot path over the 4-D Taylor-Green workload (625 tensor
+Gauss-Legendre samples, 256 x 256, 2000 steps, FP32 populations, FP64 statistics): equilibrium
+init, the fused collide-stream-QoI time loop, final fields, gPC projection onto the 70-term
+total-degree-4 Legendre basis and the mean/variance fields.  Metric: ensemble MLUPS (sum over
+samples of nodes x steps per second).  The lattice arena (1.47 GB) is larger than L2 (129 MB),
+so every time step streams from HBM without an explicit flush.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded slice of the same
+workload (all samples, fewer time steps) and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble MLUPS (tgv256_gpc4d: 625 samples x 256^2 x 2000 steps, FP32 storage, FP64 gPC statistics)"
+UNIT = "MLUPS"
+BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _updates(samples) -> int:
+    return sum(int(s.nx) * int(s.ny) * int(s.steps) for s in samples)
+
+
+def run_oracle_slice(w, steps_per_sample: int, threads: int = 0):
+    """Oracle on all samples of the workload for a few time steps (bounded CPU work)."""
+    from oracle import lbm as olbm
+    from oracle import uq as ouq
+
+    if w.method == "gpc":
+        z, _, _ = ouq.tensor_grid([w.pts_per_dim] * len(w.bounds), w.bounds)
+    else:
+        z, _ = ouq.mc_samples(w.n_mc, w.bounds, w.seed)
+    cases = []
+    for row in z:
+        p = dict(zip(w.params, row))
+        u0 = p.get("u0", w.base.u0)
+        cases.append(olbm.Case(w.base.kind, w.base.nx, w.base.ny, steps_per_sample, p.get("nu", w.base.nu), u0,
+                               amp2=p.get("zeta2", 0.0) * u0, amp3=p.get("zeta3", 0.0) * u0, u_ref=w.base.u_ref))
+    t0 = time.perf_counter()
+    olbm.run(cases, threads=threads)
+    el = time.perf_counter() - t0
+    upd = len(cases) * w.base.nx * w.base.ny * steps_per_sample
+    return upd / el / 1e6, el, upd, olbm.num_threads() if threads <= 0 else threads
+
+
+def bench_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import lbm as olbm
+    from paper_2508_13867_gb300 import workloads as W
+
+    olbm.build()
+    w = W.tgv256_gpc4d()
+    slice_steps = args.ref_slice
+    for _ in range(args.warmup):
+        run_oracle_slice(w, slice_steps)
+    times, upd = [], 0
+    for _ in range(args.steps):
+        mlups, el, u, cores = run_oracle_slice(w, slice_steps)
+        times.append(el)
+        upd = u
+    total = sum(times)
+    value = upd * len(times) / total / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "tgv256_gpc4d", "samples": 625, "lattice": [256, 256], "time_steps": 2000,
+                       "storage": "f64 (CPU oracle)", "l2": "arena larger than L2 (no flush needed)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"all 625 samples, {slice_steps} of 2000 time steps per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def bench_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2508_13867_gb300 import build as lib_build
+
+    lib_build.build()
+    from paper_2508_13867_gb300 import uqlb as U
+    from paper_2508_13867_gb300 import workloads as W
+    from paper_2508_13867_gb300.ensemble import Ensemble, case_struct, opts_struct
+
+    w = W.tgv256_gpc4d()
+    ens = Ensemble(local)
+    ens.setup(w)
+    smp = ens.ensemble_samples(w)
+    S, K = len(smp), ens.num_terms
+    F = 2 * w.base.nx * w.base.ny + 1
+    upd_per_step = _updates(smp)
+    storage = w.storage
+    stream = torch.cuda.current_stream()
+    dev = f"cuda:{local}"
+    fields = torch.empty((S, F), dtype=torch.float32, device=dev)
+    qoi = torch.empty((S, U.UQLB_QOI_COLS), dtype=torch.float64, device=dev)
+    coeffs = torch.empty((K, F), dtype=torch.float64, device=dev)
+    out = {"fields": fields, "qoi": qoi}
+
+    def one_step():
+        ens.run_batch(smp, storage=storage, fields_dtype="f32", out=out)
+        ens.project(fields, coeffs)
+        return ens.stats(coeffs)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    loop_ms, loop_steps, launches = 0.0, 0, 0
+    step_ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ms, st, la = U.uqlb_last_loop_time(ens.ctx)
+        loop_ms += ms
+        loop_steps += st
+        launches += la + 2  # + projection and statistics kernels
+    ev0.record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * upd_per_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the fused step), from its event-timed loop
+    nodes = S * w.base.nx * w.base.ny
+    per_launch_bytes = BYTES_PER_UPDATE[storage] * nodes
+    step_kernel_ms = loop_ms / max(loop_steps, 1)
+    achieved = per_launch_bytes / (step_kernel_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as fh:
+                pj = json.load(fh)
+            if pj.get("kernel_version") == "aa_v1" and pj.get("storage") == storage:
+                traffic = pj["bytes_per_launch_full_size"]
+        except Exception:
+            traffic = None
+
+    # end to end through host buffers: one C call, tables in, statistics out
+    e2e = None
+    if rank == 0:
+        mean_h = np.zeros(F)
+        var_h = np.zeros(F)
+        case = case_struct(w)
+        opts = opts_struct(storage, "f32", 0)
+        nb = U.uqlb_uq_workspace_bytes(ens.ctx, case, opts)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        U.uqlb_run_uq_host(ens.ctx, case, opts, ws.data_ptr(), nb, mean_h, var_h, None, None, stream.cuda_stream)
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 3))
+        for _ in range(reps):
+            U.uqlb_run_uq_host(ens.ctx, case, opts, ws.data_ptr(), nb, mean_h, var_h, None, None, stream.cuda_stream)
+        e2e_s = (time.perf_counter() - t0) / reps
+        h2d = S * (128 + 32 + 4) + K * S * 8
+        d2h = 2 * F * 8
+        e2e = {"value": upd_per_step / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+               "path": "uqlb_run_uq_host (one C call, host output buffers)"}
+        del ws
+
+    # comparator: plain per-sample FP64 path on a subset, time to the same gPC statistics
+    plain = None
+    if args.plain_samples > 0:
+        sub = smp[: args.plain_samples]
+        res = ens.run_plain_f64(sub, qoi_every=0, fields=True)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        res = ens.run_plain_f64(sub, qoi_every=0, fields=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms_sub = t0.elapsed_time(t1)
+        plain_ms = plain_ms_sub * S / len(sub)
+        ours_ms = total_ms / args.steps
+        plain = {"time_to_stats_s": plain_ms / 1e3, "samples_timed": len(sub),
+                 "extrapolated_to_samples": S, "batched_fp32_time_to_stats_s": ours_ms / 1e3,
+                 "speedup": plain_ms / ours_ms,
+                 "note": "plain path: one sample at a time, one FP64 launch per step, two lattices; "
+                         "its time is linear in the samples, so the subset time is scaled by S / subset"}
+        del res
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        mlups, el, upd, cores = run_oracle_slice(w, args.cpu_slice)
+        cpu = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"all 625 samples x {args.cpu_slice} of 2000 time steps ({upd:.3g} node updates, "
+                         f"{el:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded 4-D Taylor-Green ensemble)",
+                "config": {"workload": "tgv256_gpc4d", "samples": S, "lattice": [256, 256], "time_steps": 2000,
+                           "storage": storage, "statistics": "fp64", "gpc_terms": K,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "lattice arena 1.47 GB > L2 129 MB: each time step streams from HBM"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                             "kernel": "step_kernel (fused AA collide-stream-QoI)",
+                             "algorithmic_bytes_per_launch": per_launch_bytes,
+                             "kernel_ms_per_launch": step_kernel_ms},
+                "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+                "plain_f64": plain}
+        print(json.dumps(line))
+    ens.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-slice", type=int, default=40, help="oracle time steps per sample for cpu_baseline")
+    ap.add_argument("--ref-slice", type=int, default=16, help="oracle time steps per sample per reference step")
+    ap.add_argument("--plain-samples", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

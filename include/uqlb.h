@@ -1,0 +1,283 @@
+/*
+ * uqlb — ensemble lattice-Boltzmann uncertainty quantification on one GB300 (sm_103a).
+ *
+ * C ABI of libuqlb.so.  The calls follow the non-intrusive UQ workflow of
+ * arXiv 2508.13867 (OpenLB-UQ), Sec. 7 and Algorithm 1: sample the uncertain inputs,
+ * run the deterministic D2Q9 BGK solver for every sample, project the quantities of
+ * interest onto the generalized polynomial chaos basis, report statistics.  The user
+ * API of Sec. 8.1 (uniform/joint inputs, initializeMonteCarlo, initializeGPC,
+ * getSamplingPoints, mean, std) maps onto uqlb_set_inputs, uqlb_init_mc,
+ * uqlb_init_gpc, uqlb_get_samples, uqlb_mean_host and uqlb_std_host.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a uqlb_status (0 = success); no C++ exception crosses the ABI.
+ *     On failure uqlb_last_error() gives a one-line reason.
+ *   - Ownership: the caller owns every pointer it passes.  Device buffers (suffix _dev)
+ *     are plain device addresses, e.g. from torch tensors; host buffers are plain arrays.
+ *     The library allocates no device memory for the run: the lattice arena, tables
+ *     and reduction scratch live in a caller-supplied workspace whose size the
+ *     *_workspace_bytes calls report.  The context owns only host memory and CUDA
+ *     graph objects.
+ *   - Streams: device work is enqueued asynchronously on the cudaStream_t passed as
+ *     `stream` (NULL = legacy default stream).  Device-side errors (a sample that became
+ *     unstable, a CUDA fault) surface at the next call that synchronises.
+ *   - Layouts: all matrices are row-major.  Samples are indexed s = 0..S-1 in the order
+ *     of uqlb_get_samples; gPC terms k = 0..K-1 in the order of uqlb_multi_indices.
+ *   - Thread safety: a context must not be used from two host threads at once.
+ */
+#ifndef UQLB_H
+#define UQLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------------------
+ * Status codes and enums
+ * ---------------------------------------------------------------------------------- */
+typedef enum {
+    UQLB_OK = 0,
+    UQLB_ERR_ARG = -1,      /* invalid argument (null pointer, size out of range, ...) */
+    UQLB_ERR_OOM = -2,      /* workspace too small or host allocation failed */
+    UQLB_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    UQLB_ERR_TIMEOUT = -4,  /* a bounded device wait gave up */
+    UQLB_ERR_UNSTABLE = -5, /* a sample produced non-finite or non-positive density */
+    UQLB_ERR_STATE = -6     /* call out of order (e.g. project before init_gpc) */
+} uqlb_status;
+
+enum { UQLB_DIST_UNIFORM = 0 };               /* Sec. 6.1: uniform inputs (Legendre basis) */
+enum { UQLB_BASIS_TOTAL = 0, UQLB_BASIS_TENSOR = 1 };
+enum { UQLB_QUAD_GAUSS_LEGENDRE_TENSOR = 0 }; /* Sec. 6.3: tensor-product Gauss rule */
+enum { UQLB_METHOD_NONE = 0, UQLB_METHOD_MC = 1, UQLB_METHOD_GPC = 2 };
+enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1 };
+/* Parameters an uncertain input dimension may drive (uqlb_case.param_of_dim). */
+enum { UQLB_PARAM_NU = 0, UQLB_PARAM_U0 = 1, UQLB_PARAM_ZETA2 = 2, UQLB_PARAM_ZETA3 = 3 };
+/* Number formats: population storage, field outputs, projection inputs. */
+enum { UQLB_F64 = 0, UQLB_F32 = 1, UQLB_F16 = 2, UQLB_BF16 = 3 };
+/* Columns of the per-sample scalar output qoi[S x UQLB_QOI_COLS] (FP64). */
+enum {
+    UQLB_QOI_K = 0,      /* normalised kinetic energy K(T) (Sec. 8.2, discrete form) */
+    UQLB_QOI_MASS = 1,   /* sum of rho over fluid nodes at T */
+    UQLB_QOI_MOMX = 2,   /* sum of rho u over fluid nodes at T */
+    UQLB_QOI_MOMY = 3,   /* sum of rho v over fluid nodes at T */
+    UQLB_QOI_CD = 4,     /* drag coefficient of the last step run (Sec. 8.1) */
+    UQLB_QOI_CL = 5,     /* lift coefficient of the last step run */
+    UQLB_QOI_STEPS = 6,  /* number of steps run */
+    UQLB_QOI_STATUS = 7, /* 0 or UQLB_ERR_UNSTABLE */
+    UQLB_QOI_COLS = 8
+};
+
+typedef struct uqlb_ctx uqlb_ctx;
+
+/* One uncertain input (Sec. 6.1 Distribution): kind UQLB_DIST_UNIFORM on [a, b]. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double a, b;
+} uqlb_dist;
+
+/* One deterministic run (Sec. 7 "deterministic simulation"), all in lattice units.
+ *   TGV (Sec. 8.2): periodic nx x ny lattice, u = u0 sin(kx)cos(ky) + amp2 (2k mode)
+ *     + amp3 (3k mode), v the matching divergence-free field, k = 2 pi / n,
+ *     rho = 1 + 3 p with p = u0^2/4 (cos 2kx + cos 2ky); K(t) normalised by u_ref.
+ *   CHANNEL (Sec. 8.1): nx x ny nodes, halfway bounce-back walls at y = 0 and y = ny,
+ *     parabolic velocity inlet of mean velocity u0 (peak 1.5 u0) at x = 0 with a
+ *     1/2 (1 - cos(pi t / ramp_steps)) ramp, pressure outlet (rho = 1) at x = nx,
+ *     staircase circular obstacle of centre (cyl_cx, cyl_cy) and radius cyl_r (node
+ *     (x, y) solid iff its centre (x + 1/2, y + 1/2) lies strictly inside); C_D and
+ *     C_L normalised by rho = 1, u0 and diameter 2 cyl_r.  With steady_tol > 0 a
+ *     sample stops once |C_D(t) - C_D(t - qoi_every)| < steady_tol |C_D(t)|.
+ * tau = 3 nu + 1/2 (Sec. 8.2), omega = 1 / tau. */
+typedef struct {
+    int32_t kind;        /* UQLB_CASE_TGV or UQLB_CASE_CHANNEL */
+    int32_t nx, ny;      /* lattice size, 2 <= nx, ny <= 65536 */
+    int32_t reserved;
+    int64_t steps;       /* number of steps (TGV) or step cap (CHANNEL), 0 <= steps < 2^31 */
+    double nu;           /* lattice viscosity, > 0 */
+    double u0;           /* TGV amplitude or channel mean inflow velocity */
+    double amp2, amp3;   /* TGV perturbation-mode amplitudes (absolute) */
+    double u_ref;        /* TGV normaliser of K; 0 disables K */
+    double cyl_cx, cyl_cy, cyl_r; /* CHANNEL obstacle; cyl_r <= 0: none */
+    int64_t ramp_steps;  /* CHANNEL inflow ramp length (0: none) */
+    double steady_tol;   /* CHANNEL steady-state tolerance (0: run to the cap) */
+} uqlb_sample;
+
+/* Template of an ensemble: a uqlb_sample whose parameters are overridden per sample by
+ * the uncertain inputs.  Input dimension d sets parameter param_of_dim[d]:
+ *   UQLB_PARAM_NU -> nu;  UQLB_PARAM_U0 -> u0;
+ *   UQLB_PARAM_ZETA2 / ZETA3 -> amp2 / amp3 = zeta * (the sample's u0). */
+typedef struct {
+    uqlb_sample base;
+    int32_t param_of_dim[8];
+} uqlb_case;
+
+/* Options of a run. */
+typedef struct {
+    int32_t storage;      /* population storage: UQLB_F64, F32, F16 or BF16 (stored as f - w) */
+    int32_t fields_dtype; /* dtype of the field output M: UQLB_F64 or UQLB_F32 */
+    int64_t qoi_every;    /* stride of the in-kernel QoI series (0: none) */
+    int32_t chunk_steps;  /* steps per captured CUDA graph (even, 2..1024; 0: default 64) */
+    int32_t tile_rows;    /* rows per tile (1, 2, 4, 8 or 16; 0: autotuned/default) */
+} uqlb_run_opts;
+
+/* ------------------------------------------------------------------------------------
+ * Host building blocks (no device work)
+ * ---------------------------------------------------------------------------------- */
+
+/* n-point Gauss-Legendre rule on [-1, 1] (Sec. 6.3 Gauss quadrature): nodes x[n] ascending,
+ * weights w[n] summing to 2.  1 <= n <= 64.  Newton iteration on the Legendre
+ * three-term recurrence. */
+int uqlb_gauss_legendre(int n, double* x, double* w);
+
+/* Philox4x32-10 counter-based generator (Salmon et al., SC'11) used for the seeded Monte
+ * Carlo draws of Sec. 8.1 (initializeMonteCarlo(N, dist, seed)).  out = bijection(ctr; key). */
+int uqlb_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Number of gPC terms K (Sec. 4.2 Eq. gPC) for `dim` inputs and polynomial `order`:
+ * total degree (|alpha| <= order) or tensor (max alpha <= order). */
+int uqlb_num_multi_indices(int dim, int order, int basis, int64_t* k);
+
+/* Exponent set alpha[K x dim] ordered by |alpha|, then descending lexicographic order. */
+int uqlb_multi_indices(int dim, int order, int basis, int32_t* alpha);
+
+/* Staircase obstacle mask of a CHANNEL sample, [ny x nx] bytes (1 = solid). */
+int uqlb_obstacle_mask(const uqlb_sample* s, uint8_t* mask);
+
+/* Eq. meanMCS on host data v[n]. */
+int uqlb_mean_host(const double* v, int64_t n, double* out);
+
+/* Square root of Eq. varMCS on host data: ddof = 1 gives 1/(n-1) (Eq. varMCS),
+ * ddof = 0 gives Algorithm 1's 1/n. */
+int uqlb_std_host(const double* v, int64_t n, int ddof, double* out);
+
+/* ------------------------------------------------------------------------------------
+ * UQ manager (Sec. 6.4 UncertaintyQuantification)
+ * ---------------------------------------------------------------------------------- */
+
+/* Create a context bound to CUDA device `cuda_device` (made current in every later call). */
+int uqlb_create(uqlb_ctx** out, int cuda_device);
+int uqlb_destroy(uqlb_ctx* ctx);
+
+/* Reason of the last failure of `ctx` (or of a context-free call when ctx is NULL).
+ * The string is owned by the library and valid until the next call on the same ctx. */
+const char* uqlb_last_error(const uqlb_ctx* ctx);
+
+/* Joint distribution of `dim` independent inputs (1 <= dim <= 8), Sec. 8.3 `joint`. */
+int uqlb_set_inputs(uqlb_ctx* ctx, int dim, const uqlb_dist* d);
+
+/* Monte Carlo sample set (Sec. 4.1): n seeded draws, counter (s lo, s hi, dim, 0),
+ * key = seed, u = ((x1 << 32 | x0) >> 11) 2^-53, z = a + (b - a) u.  Weights 1/n. */
+int uqlb_init_mc(uqlb_ctx* ctx, int64_t n, uint64_t seed);
+
+/* Stochastic collocation (Sec. 4.2, Sec. 8.1 initializeGPC(order, N, dist)): tensor
+ * Gauss-Legendre grid with pts_per_dim nodes per input (last input fastest), weights of
+ * the uniform probability measure, orthonormal Legendre chaos of `order` (`basis`
+ * total or tensor).  Builds W[k, s] = a_s Phi_k(xi_s) (Eq. coef_discrete). */
+int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad);
+
+int uqlb_num_samples(const uqlb_ctx* ctx, int64_t* n);
+int uqlb_num_terms(const uqlb_ctx* ctx, int* k);
+
+/* Sampling points (Sec. 8.1 getSamplingPoints): z[S x dim] physical values, xi[S x dim]
+ * reference values in [-1, 1], a[S] quadrature weights (1/S for MC).  Any output may be NULL. */
+int uqlb_get_samples(const uqlb_ctx* ctx, double* z, double* xi, double* a);
+
+/* Host copy of the projection matrix W[K x S] (gPC only). */
+int uqlb_get_weight_matrix(const uqlb_ctx* ctx, double* w);
+
+/* ------------------------------------------------------------------------------------
+ * Deterministic solves over the ensemble (Sec. 7, Algorithm 1 loop)
+ * ---------------------------------------------------------------------------------- */
+
+/* Workspace needed by uqlb_run_batch for these samples and options. */
+int uqlb_batch_workspace_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
+                               size_t* bytes);
+
+/* Run n independent samples on the device: initialise every lattice at equilibrium, step all
+ * samples in in-place AA order with the collision, streaming, boundaries and QoI reductions of
+ * each step fused into one kernel, and write the results.
+ *   workspace_dev / workspace_bytes: scratch of at least uqlb_batch_workspace_bytes bytes,
+ *     256-byte aligned; contents on entry are ignored.
+ *   fields_dev: optional (NULL to skip), row s = [u (ny*nx), v (ny*nx), K(T)] of sample s in
+ *     fields_dtype with row stride fields_ld >= 2 nx ny + 1 elements; requires all samples to
+ *     share nx, ny.  Obstacle nodes hold 0.
+ *   qoi_dev: optional FP64 [n x UQLB_QOI_COLS] per-sample scalars.
+ *   series_dev: optional FP64 [n x series_ld]; TGV: K(j qoi_every) in column j (j = 0 is t = 0);
+ *     CHANNEL: C_D after step j qoi_every in column j - 1.  Unwritten entries are untouched.
+ *   series_cl_dev: optional FP64 [n x series_ld], CHANNEL lift at the same times.
+ * Returns after enqueueing; for CHANNEL samples with steady_tol > 0 it synchronises `stream`
+ * between graph launches to test for convergence. */
+int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
+                   void* workspace_dev, size_t workspace_bytes, void* fields_dev, int64_t fields_ld,
+                   double* qoi_dev, double* series_dev, double* series_cl_dev, int64_t series_ld,
+                   void* stream);
+
+/* Build the per-sample runs of the context's sample set from a case template (host). */
+int uqlb_ensemble_samples(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* out);
+
+/* Workspace for uqlb_run_ensemble (the batch workspace of the ensemble's samples). */
+int uqlb_ensemble_workspace_bytes(const uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts,
+                                  size_t* bytes);
+
+/* uqlb_ensemble_samples followed by uqlb_run_batch over all S samples. */
+int uqlb_run_ensemble(uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts,
+                      void* workspace_dev, size_t workspace_bytes, void* fields_dev,
+                      int64_t fields_ld, double* qoi_dev, double* series_dev,
+                      double* series_cl_dev, int64_t series_ld, void* stream);
+
+/* Plain per-sample FP64 path: one sample at a time, one kernel launch per step on two
+ * lattices (pull streaming), QoIs in separate kernels.  Same outputs as uqlb_run_batch with
+ * storage UQLB_F64 (fields in FP64).  Serves as the unbatched, unfused FP64 comparator. */
+int uqlb_plain_workspace_bytes(const uqlb_sample* samples, int64_t n, size_t* bytes);
+int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int64_t qoi_every,
+                       void* workspace_dev, size_t workspace_bytes, double* fields_dev,
+                       int64_t fields_ld, double* qoi_dev, double* series_dev, int64_t series_ld,
+                       void* stream);
+
+/* Device time of the time loop of the last uqlb_run_batch / uqlb_run_ensemble on this context,
+ * measured with CUDA events recorded on the caller's stream around the graph launches of the
+ * loop (so it covers the fused step kernels and nothing else of the run).  steps: time steps of
+ * the loop; launches: kernels the whole run enqueued (init, steps, counter advances, finalize).
+ * Synchronises on the end event.  Any output may be NULL. */
+int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches);
+
+/* ------------------------------------------------------------------------------------
+ * Postprocessing (Sec. 4, Algorithm 1 statistics)
+ * ---------------------------------------------------------------------------------- */
+
+/* Device workspace of uqlb_project / uqlb_stats (holds W on the device). */
+int uqlb_post_workspace_bytes(const uqlb_ctx* ctx, size_t* bytes);
+
+/* gPC coefficients (Eq. coef_discrete, gamma_k = 1): coeffs[k, f] = sum_s W[k, s] M[s, f],
+ * accumulated in FP64.  m_dev: [S x n_fields] in `dtype` (UQLB_F64 or UQLB_F32) with row
+ * stride m_ld; coeffs_dev: FP64 [K x n_fields] dense.  Requires uqlb_init_gpc. */
+int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,
+                 double* coeffs_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Statistics per field, FP64 outputs mean_dev[n_fields], var_dev[n_fields].
+ *   gPC context: input is coeffs_dev [K x n_fields] FP64; mean = c_0 (Eq. gpc_mean),
+ *     var = sum_{k >= 1} c_k^2 (Eq. gpc_std squared); dtype must be UQLB_F64, ddof ignored.
+ *   MC context: input is M [S x n_fields] (ld = m_ld) in `dtype`; mean by Eq. meanMCS,
+ *     var by Eq. varMCS with divisor S - ddof (two passes, FP64). */
+int uqlb_stats(uqlb_ctx* ctx, const void* in_dev, int dtype, int64_t n_fields, int64_t m_ld,
+               double* mean_dev, double* var_dev, int ddof, void* stream);
+
+/* End-to-end UQ through host buffers (Algorithm 1 as one call): runs the ensemble of the
+ * context's samples, projects (gPC) or averages (MC) the fields [u, v, K] and copies
+ * mean_host / var_host [2 nx ny + 1] (and, for gPC and when not NULL, coeffs_host
+ * [K x (2 nx ny + 1)]) back to the host.  Device scratch comes from workspace_dev
+ * (uqlb_uq_workspace_bytes); synchronises `stream` before returning. */
+int uqlb_uq_workspace_bytes(const uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts,
+                            size_t* bytes);
+int uqlb_run_uq_host(uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts,
+                     void* workspace_dev, size_t workspace_bytes, double* mean_host,
+                     double* var_host, double* coeffs_host, double* qoi_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UQLB_H */

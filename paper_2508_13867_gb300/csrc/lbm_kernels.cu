@@ -1,0 +1,649 @@
+// Batched D2Q9 BGK ensemble kernels for sm_103a (arXiv 2508.13867, Sec. 3 and Sec. 7).
+//
+// All samples of an ensemble live in one arena, sample-major, population-plane-major, row-major:
+//   arena[f_off(s) + i * plane(s) + y * pitch(s) + x],  g_i = f_i - w_i.
+// The lattices are updated in place in AA order: an even step reads and writes the nine
+// populations of its own node (writing post-collision g_i to slot opp(i)); an odd step reads
+// the incoming populations from the neighbours' slots and writes its outgoing populations
+// into the neighbours' slots.  Every memory location is read and then written by exactly one
+// thread per step, so no second lattice and no intra-step synchronisation are needed.
+// Boundary rules are applied where a population crosses a boundary link:
+//   periodic (TGV, Sec. 8.2): wrap-around neighbours;
+//   wall / obstacle (Sec. 8.1 no-slip): halfway bounce-back;
+//   inlet (x = 0 face): moving-wall bounce-back with the parabolic profile at the link midpoint;
+//   outlet (x = nx face): anti-bounce-back at rho = 1 with the outlet node's velocity.
+// Quantities of interest are reduced in the same kernel: K(t) from the pre-collision moments
+// and drag/lift by momentum exchange from the post-collision populations; per-tile partial
+// sums (FP64) are combined in a fixed order by the last tile of each sample to finish.
+#include <cmath>
+
+#include "d2q9.cuh"
+#include "uqlb_internal.h"
+
+namespace uqlb {
+
+namespace {
+
+constexpr int kTileCols = 32;
+
+struct KParams {
+    void* arena;
+    const SampleDev* samples;
+    const InitDev* init;
+    const int32_t* steps_sorted;
+    int32_t nsamples;
+    int32_t uniform_tiles;
+    const uint32_t* masks;
+    float* side;
+    double* side_d;
+    double* partials;
+    int32_t* counters;
+    int32_t* done;
+    int32_t* steps_run;
+    double* cd_prev;
+    const int64_t* step_counter;
+    int32_t* n_done;
+    int32_t dt;
+    int32_t max_steps;
+    // outputs
+    void* fields;
+    int64_t fields_ld;
+    int32_t fields_dtype;
+    double* qoi;
+    double* series;
+    double* series_cl;
+    int64_t series_ld;
+    int64_t qoi_every;
+};
+
+// Sample index j (in table order) of a global tile index.
+__device__ __forceinline__ int tile_sample(const KParams& p, int tile, int nact) {
+    if (p.uniform_tiles > 0) return tile / p.uniform_tiles;
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.samples[mid].tile_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Number of samples with steps > t (the table is ordered by descending steps).
+__device__ __forceinline__ int active_samples(const KParams& p, int t) {
+    int lo = 0, hi = p.nsamples;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (p.steps_sorted[mid] > t)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Link classes of the channel case, checked in this order.
+enum LinkClass { kInterior = 0, kWall = 1, kInlet = 2, kOutlet = 3, kSolid = 4 };
+
+__device__ __forceinline__ int classify(const SampleDev& sp, const uint32_t* mask, int xn, int yn) {
+    if (yn < 0 || yn >= sp.ny) return kWall;
+    if (xn < 0) return kInlet;
+    if (xn >= sp.nx) return kOutlet;
+    if (mask != nullptr && mask_solid(mask, sp.mask_words, xn, yn)) return kSolid;
+    return kInterior;
+}
+
+// Inflow velocity at height yy (walls at 0 and ny) at step t, Sec. 8.1 profile and ramp.
+template <typename C>
+__device__ __forceinline__ C inflow(const SampleDev& sp, C yy, int t) {
+    C ramp = C(1);
+    if (sp.ramp_steps > 0.0 && (double)t < sp.ramp_steps)
+        ramp = C(0.5 * (1.0 - cospi((double)t / sp.ramp_steps)));
+    const C H = C(sp.ny);
+    return C(4) * C(sp.uin_max) * ramp * yy * (H - yy) / (H * H);
+}
+
+// Shifted incoming population of direction i at node (x, y) for the stream (tp -> tp + 1),
+// given the slot layout left by an even step at time tp: g_i*(z) sits at (z, slot opp(i)).
+// ub: velocity of the outlet node at time tp.
+template <typename S, bool CHANNEL>
+__device__ __forceinline__ typename Storage<S>::C read_incoming(
+    const S* base, const SampleDev& sp, const uint32_t* mask, int x, int y, int i, int tp,
+    typename Storage<S>::C ubx, typename Storage<S>::C uby) {
+    using C = typename Storage<S>::C;
+    const int64_t plane = sp.plane;
+    const int pitch = sp.pitch;
+    int sx = x - cx(i), sy = y - cy(i);
+    if (!CHANNEL) {
+        sx = sx < 0 ? sx + sp.nx : (sx >= sp.nx ? sx - sp.nx : sx);
+        sy = sy < 0 ? sy + sp.ny : (sy >= sp.ny ? sy - sp.ny : sy);
+        return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx);
+    } else {
+        const int cls = classify(sp, mask, sx, sy);
+        const int64_t own = (int64_t)y * pitch + x;
+        if (cls == kInterior) return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx);
+        const C mine = Storage<S>::load(base + i * plane + own);  // g_opp(i)*(x, tp)
+        if (cls == kWall || cls == kSolid) return mine;
+        if (cls == kInlet) {
+            const C yy = C(y) + C(0.5) - C(0.5) * C(cy(i));
+            return mine + C(6) * wgt<C>(i) * C(cx(i)) * inflow<C>(sp, yy, tp);
+        }
+        // outlet: g_i = -g_opp(i)* + w_i (9 (c_i.u)^2 - 3 u.u)
+        const C cu = C(cx(i)) * ubx + C(cy(i)) * uby;
+        return -mine + wgt<C>(i) * (C(9) * cu * cu - C(3) * (ubx * ubx + uby * uby));
+    }
+}
+
+// Block-wide deterministic sum of NV doubles; result valid in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) smem[warp * NV + k] = v[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < NT / 32; ++w) s += smem[w * NV + k];
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Publish this tile's partial sums; returns true in every thread of the block that finished
+// the sample's last tile, after which `tot` holds the fixed-order total in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ bool tile_reduce_last(const KParams& p, const SampleDev& sp, int j,
+                                                 int tile, double (&v)[NV], double (&tot)[NV],
+                                                 double* smem, int* sflag) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    block_sum<NV, NT>(v, smem);
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) p.partials[(int64_t)tile * NV + k] = v[k];
+        __threadfence();
+        const int prev = atomicAdd(p.counters + j, 1);
+        *sflag = (prev == sp.tiles - 1);
+    }
+    __syncthreads();
+    const bool last = *sflag != 0;
+    if (last) {
+        __threadfence();
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (int q = tid; q < sp.tiles; q += NT) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc[k] += __ldcg(p.partials + (int64_t)(sp.tile_base + q) * NV + k);
+        }
+        block_sum<NV, NT>(acc, smem);
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) tot[k] = acc[k];
+            p.counters[j] = 0;
+        }
+    }
+    __syncthreads();
+    return last;
+}
+
+// ------------------------------------------------------------------------------------------
+// Initial state: equilibrium of the initial macroscopic field (Sec. 8.2 TGV, Sec. 8.1 rest).
+// ------------------------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tiles, int tile_rows) {
+    using C = typename Storage<S>::C;
+    S* arena = static_cast<S*>(p.arena);
+    for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const int j = tile_sample(p, (int)tile, p.nsamples);
+        const SampleDev& sp = p.samples[j];
+        const int lt = (int)tile - sp.tile_base;
+        const int x = (lt % sp.tiles_x) * kTileCols + (threadIdx.x & 31);
+        const int y0 = (lt / sp.tiles_x) * tile_rows;
+        if (tile == sp.tile_base && threadIdx.x == 0) {
+            p.counters[j] = 0;
+            p.done[j] = 0;
+            p.steps_run[j] = sp.steps;
+            p.cd_prev[j] = NAN;
+        }
+        for (int y = y0 + (threadIdx.x >> 5); y < y0 + tile_rows && y < sp.ny; y += blockDim.x >> 5) {
+            if (x >= sp.nx) continue;
+            double rho = 1.0, ux = 0.0, uy = 0.0;
+            if (sp.kind == UQLB_CASE_TGV) {
+                const InitDev& in = p.init[j];
+                double s1x, c1x, s1y, c1y;
+                sincospi(2.0 * x / sp.nx, &s1x, &c1x);
+                sincospi(2.0 * y / sp.ny, &s1y, &c1y);
+                const double s2x = 2.0 * s1x * c1x, c2x = 2.0 * c1x * c1x - 1.0;
+                const double s2y = 2.0 * s1y * c1y, c2y = 2.0 * c1y * c1y - 1.0;
+                const double s3x = s1x * (3.0 - 4.0 * s1x * s1x), c3x = c1x * (4.0 * c1x * c1x - 3.0);
+                const double s3y = s1y * (3.0 - 4.0 * s1y * s1y), c3y = c1y * (4.0 * c1y * c1y - 3.0);
+                ux = in.u0 * s1x * c1y + in.amp2 * s2x * c2y + in.amp3 * s3x * c3y;
+                uy = -in.u0 * c1x * s1y - in.amp2 * c2x * s2y - in.amp3 * c3x * s3y;
+                const double pr = 0.25 * in.u0 * in.u0 * (c2x + c2y);
+                rho = 1.0 + 3.0 * pr;
+            }
+            const double usq = ux * ux + uy * uy;
+            S* base = arena + sp.f_off + (int64_t)y * sp.pitch + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double cu = cx(i) * ux + cy(i) * uy;
+                const double w = wgt<double>(i);
+                const double g = w * (rho - 1.0) + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                Storage<S>::store(base + i * sp.plane, (C)g);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused collide-stream-boundary-QoI step (one launch per time step).
+// ------------------------------------------------------------------------------------------
+template <typename S, bool ODD, bool CHANNEL, int TR>
+__global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
+    using C = typename Storage<S>::C;
+    constexpr int NT = kTileCols * TR;
+    __shared__ int s_nact, s_ntiles, s_j, s_flag;
+    __shared__ double s_red[(NT / 32) * 3];
+
+    const int t = (int)(*p.step_counter) + p.dt;
+    if (t >= p.max_steps) return;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const int nact = active_samples(p, t);
+        s_nact = nact;
+        s_ntiles = nact > 0 ? p.samples[nact - 1].tile_base + p.samples[nact - 1].tiles : 0;
+    }
+    __syncthreads();
+    const int nact = s_nact, ntiles = s_ntiles;
+    const bool want_k = !CHANNEL && p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
+    const bool want_f = CHANNEL && p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
+    S* arena = static_cast<S*>(p.arena);
+
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) s_j = tile_sample(p, tile, nact);
+        __syncthreads();
+        const int j = s_j;
+        const SampleDev sp = p.samples[j];
+        if (CHANNEL && p.done[j]) {
+            __syncthreads();
+            continue;
+        }
+        const int lt = tile - sp.tile_base;
+        const int x = (lt % sp.tiles_x) * kTileCols + threadIdx.x;
+        const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
+        const uint32_t* mask = (CHANNEL && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+        bool active = x < sp.nx && y < sp.ny;
+        if (CHANNEL && active && mask != nullptr) active = !mask_solid(mask, sp.mask_words, x, y);
+
+        double red[3] = {0.0, 0.0, 0.0};
+        if (active) {
+            S* base = arena + sp.f_off;
+            const int64_t own = (int64_t)y * sp.pitch + x;
+            const int64_t plane = sp.plane;
+            C g[9];
+            if (!ODD) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * plane + own);
+            } else {
+                C ubx = C(0), uby = C(0);
+                if (CHANNEL && x == sp.nx - 1) {
+                    if (sizeof(C) == 8) {
+                        ubx = (C)p.side_d[2 * (sp.side_off + y)];
+                        uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
+                    } else {
+                        ubx = (C)p.side[2 * (sp.side_off + y)];
+                        uby = (C)p.side[2 * (sp.side_off + y) + 1];
+                    }
+                }
+                g[0] = Storage<S>::load(base + own);
+#pragma unroll
+                for (int i = 1; i < 9; ++i)
+                    g[i] = read_incoming<S, CHANNEL>(base, sp, mask, x, y, i, t - 1, ubx, uby);
+            }
+            C drho, ux, uy;
+            moments(g, drho, ux, uy);
+            if (want_k) red[0] = (double)(ux * ux + uy * uy);
+            if (CHANNEL && !ODD && x == sp.nx - 1) {
+                if (sizeof(C) == 8) {
+                    p.side_d[2 * (sp.side_off + y)] = (double)ux;
+                    p.side_d[2 * (sp.side_off + y) + 1] = (double)uy;
+                } else {
+                    p.side[2 * (sp.side_off + y)] = (float)ux;
+                    p.side[2 * (sp.side_off + y) + 1] = (float)uy;
+                }
+            }
+            bgk(g, (C)sp.omega, drho, ux, uy);
+            if (CHANNEL && want_f && mask != nullptr) {
+                C fx = C(0), fy = C(0);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const int xn = x + cx(i), yn = y + cy(i);
+                    if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny &&
+                        mask_solid(mask, sp.mask_words, xn, yn)) {
+                        const C fs = g[i] + wgt<C>(i);
+                        fx += C(2 * cx(i)) * fs;
+                        fy += C(2 * cy(i)) * fs;
+                    }
+                }
+                red[1] = (double)fx;
+                red[2] = (double)fy;
+            }
+            if (!ODD) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Storage<S>::store(base + opp(i) * plane + own, g[i]);
+            } else {
+                Storage<S>::store(base + own, g[0]);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    int dx = x + cx(i), dy = y + cy(i);
+                    if (!CHANNEL) {
+                        dx = dx < 0 ? dx + sp.nx : (dx >= sp.nx ? dx - sp.nx : dx);
+                        dy = dy < 0 ? dy + sp.ny : (dy >= sp.ny ? dy - sp.ny : dy);
+                        Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
+                    } else {
+                        const int cls = classify(sp, mask, dx, dy);
+                        const int o = opp(i);
+                        if (cls == kInterior) {
+                            Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
+                        } else if (cls == kWall || cls == kSolid) {
+                            Storage<S>::store(base + o * plane + own, g[i]);
+                        } else if (cls == kInlet) {
+                            const C yy = C(y) + C(0.5) - C(0.5) * C(cy(o));
+                            Storage<S>::store(base + o * plane + own,
+                                              g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t));
+                        } else {
+                            const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
+                            Storage<S>::store(base + o * plane + own,
+                                              -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)));
+                        }
+                    }
+                }
+            }
+        }
+        if (want_k || want_f) {
+            double tot[3];
+            if (tile_reduce_last<3, NT>(p, sp, j, tile, red, tot, s_red, &s_flag)) {
+                if (threadIdx.x == 0 && threadIdx.y == 0) {
+                    if (want_k) {
+                        p.series[(int64_t)sp.sample_id * p.series_ld + t / p.qoi_every] = tot[0] * sp.u_ref_inv2;
+                    } else {
+                        const double cd = tot[1] * sp.force_norm, cl = tot[2] * sp.force_norm;
+                        const int64_t col = (t + 1) / p.qoi_every - 1;
+                        if (p.series) p.series[(int64_t)sp.sample_id * p.series_ld + col] = cd;
+                        if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
+                        if (sp.steady_tol > 0.0) {
+                            const double prev = p.cd_prev[j];
+                            if (!isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd)) {
+                                p.done[j] = 1;
+                                p.steps_run[j] = t + 1;
+                                atomicAdd(p.n_done, 1);
+                            }
+                            p.cd_prev[j] = cd;
+                        }
+                    }
+                }
+            }
+        } else {
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Final fields and per-sample scalars at the last step run.
+// ------------------------------------------------------------------------------------------
+template <typename S, bool CHANNEL>
+__global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_tiles, int tile_rows) {
+    using C = typename Storage<S>::C;
+    constexpr int NT = 256;
+    __shared__ double s_red[(NT / 32) * 7];
+    __shared__ int s_flag;
+    S* arena = static_cast<S*>(p.arena);
+    for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        const int j = tile_sample(p, (int)tile, p.nsamples);
+        const SampleDev sp = p.samples[j];
+        const int T = p.steps_run[j];
+        const int lt = (int)tile - sp.tile_base;
+        const int x = (lt % sp.tiles_x) * kTileCols + (threadIdx.x & 31);
+        const int y0 = (lt / sp.tiles_x) * tile_rows;
+        const uint32_t* mask = (sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+        double red[7] = {0, 0, 0, 0, 0, 0, 0};  // K, mass, mx, my, fx, fy, bad
+        for (int y = y0 + (threadIdx.x >> 5); y < y0 + tile_rows; y += blockDim.x >> 5) {
+            if (x >= sp.nx || y >= sp.ny) continue;
+            const bool solid = mask != nullptr && mask_solid(mask, sp.mask_words, x, y);
+            double ux = 0.0, uy = 0.0;
+            if (!solid) {
+                S* base = arena + sp.f_off;
+                const int64_t own = (int64_t)y * sp.pitch + x;
+                C g[9];
+                if ((T & 1) == 0) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own);
+                } else {
+                    C ubx = C(0), uby = C(0);
+                    if (CHANNEL && x == sp.nx - 1) {
+                        if (sizeof(C) == 8) {
+                            ubx = (C)p.side_d[2 * (sp.side_off + y)];
+                            uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
+                        } else {
+                            ubx = (C)p.side[2 * (sp.side_off + y)];
+                            uby = (C)p.side[2 * (sp.side_off + y) + 1];
+                        }
+                    }
+                    g[0] = Storage<S>::load(base + own);
+#pragma unroll
+                    for (int i = 1; i < 9; ++i)
+                        g[i] = read_incoming<S, CHANNEL>(base, sp, mask, x, y, i, T - 1, ubx, uby);
+                }
+                C drho, cux, cuy;
+                moments(g, drho, cux, cuy);
+                ux = (double)cux;
+                uy = (double)cuy;
+                const double rho = 1.0 + (double)drho;
+                red[0] += ux * ux + uy * uy;
+                red[1] += rho;
+                red[2] += rho * ux;
+                red[3] += rho * uy;
+                if (!(rho > 0.0) || !isfinite(ux) || !isfinite(uy)) red[6] += 1.0;
+                if (CHANNEL && mask != nullptr && T > 0) {
+                    // bounce-back populations at T are the post-collision values of step T - 1
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) {
+                        const int xn = x + cx(i), yn = y + cy(i);
+                        if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny &&
+                            mask_solid(mask, sp.mask_words, xn, yn)) {
+                            const double fs = (double)Storage<S>::load(base + opp(i) * sp.plane + own) + wgt<double>(i);
+                            red[4] += 2.0 * cx(i) * fs;
+                            red[5] += 2.0 * cy(i) * fs;
+                        }
+                    }
+                }
+            }
+            if (p.fields != nullptr) {
+                const int64_t row = (int64_t)sp.sample_id * p.fields_ld;
+                const int64_t n = (int64_t)sp.nx * sp.ny;
+                const int64_t node = (int64_t)y * sp.nx + x;
+                if (p.fields_dtype == UQLB_F64) {
+                    double* f = static_cast<double*>(p.fields) + row;
+                    f[node] = ux;
+                    f[n + node] = uy;
+                } else {
+                    float* f = static_cast<float*>(p.fields) + row;
+                    f[node] = (float)ux;
+                    f[n + node] = (float)uy;
+                }
+            }
+        }
+        double tot[7];
+        if (tile_reduce_last<7, NT>(p, sp, j, (int)tile, red, tot, s_red, &s_flag)) {
+            if (threadIdx.x == 0) {
+                const double K = tot[0] * sp.u_ref_inv2;
+                if (p.qoi != nullptr) {
+                    double* q = p.qoi + (int64_t)sp.sample_id * UQLB_QOI_COLS;
+                    q[UQLB_QOI_K] = K;
+                    q[UQLB_QOI_MASS] = tot[1];
+                    q[UQLB_QOI_MOMX] = tot[2];
+                    q[UQLB_QOI_MOMY] = tot[3];
+                    q[UQLB_QOI_CD] = tot[4] * sp.force_norm;
+                    q[UQLB_QOI_CL] = tot[5] * sp.force_norm;
+                    q[UQLB_QOI_STEPS] = (double)T;
+                    q[UQLB_QOI_STATUS] = tot[6] > 0.0 ? (double)UQLB_ERR_UNSTABLE : 0.0;
+                }
+                if (p.fields != nullptr) {
+                    const int64_t at = (int64_t)sp.sample_id * p.fields_ld + 2 * (int64_t)sp.nx * sp.ny;
+                    if (p.fields_dtype == UQLB_F64)
+                        static_cast<double*>(p.fields)[at] = K;
+                    else
+                        static_cast<float*>(p.fields)[at] = (float)K;
+                }
+                if (!CHANNEL && p.series != nullptr && p.qoi_every > 0 && T % p.qoi_every == 0)
+                    p.series[(int64_t)sp.sample_id * p.series_ld + T / p.qoi_every] = K;
+            }
+        }
+    }
+}
+
+__global__ void advance_kernel(int64_t* counter, int chunk) { *counter += chunk; }
+
+KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs* o, int dt) {
+    KParams p{};
+    p.arena = b.arena;
+    p.samples = b.samples;
+    p.init = b.init;
+    p.steps_sorted = b.steps_sorted;
+    p.nsamples = (int32_t)g.nsamples;
+    p.uniform_tiles = g.uniform_tiles;
+    p.masks = b.masks;
+    p.side = b.side;
+    p.side_d = b.side_d;
+    p.partials = b.partials;
+    p.counters = b.counters;
+    p.done = b.done;
+    p.steps_run = b.steps_run;
+    p.cd_prev = b.cd_prev;
+    p.step_counter = b.step_counter;
+    p.n_done = b.active_flag;
+    p.dt = dt;
+    p.max_steps = g.max_steps;
+    if (o != nullptr) {
+        p.fields = o->fields;
+        p.fields_ld = o->fields_ld;
+        p.fields_dtype = o->fields_dtype;
+        p.qoi = o->qoi;
+        p.series = o->series;
+        p.series_cl = o->series_cl;
+        p.series_ld = o->series_ld;
+        p.qoi_every = o->qoi_every;
+    }
+    return p;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+template <typename S, bool ODD, bool CHANNEL>
+cudaError_t launch_step_t(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    const int grid = step_grid_blocks(g);
+    switch (g.tile_rows) {
+        case 1: step_kernel<S, ODD, CHANNEL, 1><<<grid, dim3(kTileCols, 1), 0, s>>>(p); break;
+        case 2: step_kernel<S, ODD, CHANNEL, 2><<<grid, dim3(kTileCols, 2), 0, s>>>(p); break;
+        case 4: step_kernel<S, ODD, CHANNEL, 4><<<grid, dim3(kTileCols, 4), 0, s>>>(p); break;
+        case 16: step_kernel<S, ODD, CHANNEL, 16><<<grid, dim3(kTileCols, 16), 0, s>>>(p); break;
+        default: step_kernel<S, ODD, CHANNEL, 8><<<grid, dim3(kTileCols, 8), 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cudaStream_t s) {
+    if (g.any_channel)
+        return odd ? launch_step_t<S, true, true>(p, g, s) : launch_step_t<S, false, true>(p, g, s);
+    return odd ? launch_step_t<S, true, false>(p, g, s) : launch_step_t<S, false, false>(p, g, s);
+}
+
+}  // namespace
+
+int step_grid_blocks(const BatchGeometry& g) {
+    // enough resident blocks for every SM; the step kernel strides over tiles
+    const int64_t cap = (int64_t)sm_count() * 2048 / (kTileCols * (g.tile_rows > 0 ? g.tile_rows : 8));
+    int64_t grid = g.total_tiles < cap ? g.total_tiles : cap;
+    return (int)(grid > 0 ? grid : 1);
+}
+
+cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
+    KParams p = make_params(b, g, nullptr, 0);
+    int64_t grid = g.total_tiles < 65535 * 4 ? g.total_tiles : 65535 * 4;
+    if (grid < 1) grid = 1;
+    switch (g.storage) {
+        case UQLB_F64: init_kernel<double><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
+        case UQLB_F32: init_kernel<float><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
+        case UQLB_F16: init_kernel<__half><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
+        default: init_kernel<__nv_bfloat16><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt,
+                        cudaStream_t s) {
+    KParams p = make_params(b, g, &o, dt);
+    const bool odd = (dt & 1) != 0;
+    switch (g.storage) {
+        case UQLB_F64: return launch_step_s<double>(p, g, odd, s);
+        case UQLB_F32: return launch_step_s<float>(p, g, odd, s);
+        case UQLB_F16: return launch_step_s<__half>(p, g, odd, s);
+        default: return launch_step_s<__nv_bfloat16>(p, g, odd, s);
+    }
+}
+
+cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s) {
+    advance_kernel<<<1, 1, 0, s>>>(b.step_counter, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
+                            cudaStream_t s) {
+    KParams p = make_params(b, g, &o, 0);
+    int64_t grid = g.total_tiles < 65535 * 4 ? g.total_tiles : 65535 * 4;
+    if (grid < 1) grid = 1;
+    const bool ch = g.any_channel != 0;
+    switch (g.storage) {
+        case UQLB_F64:
+            ch ? finalize_kernel<double, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
+               : finalize_kernel<double, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            break;
+        case UQLB_F32:
+            ch ? finalize_kernel<float, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
+               : finalize_kernel<float, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            break;
+        case UQLB_F16:
+            ch ? finalize_kernel<__half, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
+               : finalize_kernel<__half, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            break;
+        default:
+            ch ? finalize_kernel<__nv_bfloat16, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
+               : finalize_kernel<__nv_bfloat16, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace uqlb

@@ -1,0 +1,132 @@
+// gPC projection and ensemble statistics (arXiv 2508.13867, Sec. 4 and Algorithm 1).
+//
+//   coefficients (Eq. coef_discrete, gamma_k = 1):  C[k, f] = sum_s W[k, s] M[s, f],
+//                                                     W[k, s] = a_s Phi_k(xi_s)
+//   gPC mean / variance (Eq. gpc_mean, Eq. gpc_std):  mean = C[0, f], var = sum_{k>=1} C[k, f]^2
+//   Monte Carlo (Eq. meanMCS, Eq. varMCS):           two passes over the samples
+// All accumulation is FP64; M may be FP32 (the ensemble's field output) or FP64.
+// The contraction is [K x S] x [S x F] with K <= a few hundred and F up to ~10^6: each thread
+// owns two fields and KB coefficients, W tiles are staged in shared memory and broadcast.
+#include <cmath>
+
+#include "uqlb_internal.h"
+
+namespace uqlb {
+
+namespace {
+
+constexpr int kProjThreads = 128;
+constexpr int kKB = 16;   // coefficients per block (blockIdx.y chunk)
+constexpr int kSB = 128;  // samples per shared-memory stage
+constexpr int kFPT = 2;   // fields per thread
+
+template <typename M>
+__global__ void __launch_bounds__(kProjThreads) project_kernel(const double* __restrict__ W, int K, int S,
+                                                               const M* __restrict__ m, int64_t F, int64_t ld,
+                                                               double* __restrict__ C) {
+    __shared__ double sw[kKB][kSB];
+    const int k0 = blockIdx.y * kKB;
+    const int64_t f0 = ((int64_t)blockIdx.x * kProjThreads) * kFPT + threadIdx.x;
+    double acc[kFPT][kKB];
+#pragma unroll
+    for (int a = 0; a < kFPT; ++a)
+#pragma unroll
+        for (int k = 0; k < kKB; ++k) acc[a][k] = 0.0;
+
+    for (int s0 = 0; s0 < S; s0 += kSB) {
+        const int sn = min(kSB, S - s0);
+        for (int q = threadIdx.x; q < kKB * kSB; q += kProjThreads) {
+            const int kk = q / kSB, ss = q % kSB;
+            sw[kk][ss] = (k0 + kk < K && ss < sn) ? W[(int64_t)(k0 + kk) * S + s0 + ss] : 0.0;
+        }
+        __syncthreads();
+        for (int ss = 0; ss < sn; ++ss) {
+            const M* row = m + (int64_t)(s0 + ss) * ld;
+            double v[kFPT];
+#pragma unroll
+            for (int a = 0; a < kFPT; ++a) {
+                const int64_t f = f0 + (int64_t)a * kProjThreads;
+                v[a] = f < F ? (double)row[f] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < kKB; ++k) {
+                const double w = sw[k][ss];
+#pragma unroll
+                for (int a = 0; a < kFPT; ++a) acc[a][k] = fma(w, v[a], acc[a][k]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < kFPT; ++a) {
+        const int64_t f = f0 + (int64_t)a * kProjThreads;
+        if (f >= F) continue;
+#pragma unroll
+        for (int k = 0; k < kKB; ++k)
+            if (k0 + k < K) C[(int64_t)(k0 + k) * F + f] = acc[a][k];
+    }
+}
+
+__global__ void gpc_stats_kernel(const double* __restrict__ C, int K, int64_t F, double* mean, double* var) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int k = 1; k < K; ++k) {
+            const double c = C[(int64_t)k * F + f];
+            v = fma(c, c, v);
+        }
+        if (mean) mean[f] = C[f];
+        if (var) var[f] = v;
+    }
+}
+
+template <typename M>
+__global__ void mc_stats_kernel(const M* __restrict__ m, int64_t S, int64_t F, int64_t ld, double* mean,
+                                double* var, int ddof) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t q = 0; q < S; ++q) s += (double)m[q * ld + f];
+        const double mu = s / (double)S;
+        double ss = 0.0;
+        for (int64_t q = 0; q < S; ++q) {
+            const double d = (double)m[q * ld + f] - mu;
+            ss = fma(d, d, ss);
+        }
+        if (mean) mean[f] = mu;
+        if (var) var[f] = (S - ddof) > 0 ? ss / (double)(S - ddof) : NAN;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project(const double* W, int K, int S, const void* M, int dtype, int64_t F, int64_t ld,
+                           double* C, cudaStream_t s) {
+    if (F <= 0 || K <= 0) return cudaSuccess;
+    const int64_t per_block = (int64_t)kProjThreads * kFPT;
+    dim3 grid((unsigned)((F + per_block - 1) / per_block), (unsigned)((K + kKB - 1) / kKB));
+    if (dtype == UQLB_F64)
+        project_kernel<double><<<grid, kProjThreads, 0, s>>>(W, K, S, static_cast<const double*>(M), F, ld, C);
+    else
+        project_kernel<float><<<grid, kProjThreads, 0, s>>>(W, K, S, static_cast<const float*>(M), F, ld, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gpc_stats(const double* C, int K, int64_t F, double* mean, double* var, cudaStream_t s) {
+    if (F <= 0) return cudaSuccess;
+    const int64_t blocks = (F + 255) / 256;
+    gpc_stats_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(C, K, F, mean, var);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_stats(const void* M, int dtype, int64_t S, int64_t F, int64_t ld, double* mean,
+                            double* var, int ddof, cudaStream_t s) {
+    if (F <= 0) return cudaSuccess;
+    const int64_t blocks = (F + 255) / 256;
+    const unsigned g = (unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8);
+    if (dtype == UQLB_F64)
+        mc_stats_kernel<double><<<g, 256, 0, s>>>(static_cast<const double*>(M), S, F, ld, mean, var, ddof);
+    else
+        mc_stats_kernel<float><<<g, 256, 0, s>>>(static_cast<const float*>(M), S, F, ld, mean, var, ddof);
+    return cudaGetLastError();
+}
+
+}  // namespace uqlb

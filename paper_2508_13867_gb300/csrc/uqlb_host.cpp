@@ -1,0 +1,1009 @@
+// Host side of libuqlb: the UQ manager (sampling, quadrature, gPC basis), the ensemble
+// planner (arena layout, tile order, obstacle masks), CUDA-graph chunking of the time loop
+// and the C ABI of include/uqlb.h.  arXiv 2508.13867: Sec. 4 (MC, gPC), Sec. 6 (class
+// design), Sec. 7 and Algorithm 1 (workflow), Sec. 8.1 (user API of the cylinder example).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "uqlb_internal.h"
+
+using namespace uqlb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+constexpr int kMaxDim = 8;
+constexpr int kMaxGraphs = 8;
+
+}  // namespace
+
+struct uqlb_ctx {
+    int device = 0;
+    std::string err;
+    int dim = 0;
+    std::vector<uqlb_dist> dists;
+    int method = UQLB_METHOD_NONE;
+    int64_t S = 0;
+    std::vector<double> z, xi, a;
+    int order = 0, basis = 0, K = 0;
+    std::vector<int32_t> alpha;
+    std::vector<double> W;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    cudaEvent_t loop_begin = nullptr, loop_end = nullptr;
+    bool loop_timed = false;
+    int64_t loop_steps = 0, run_launches = 0;
+};
+
+namespace {
+
+int set_err(uqlb_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(uqlb_ctx* c, cudaError_t e, const char* what) {
+    return set_err(c, UQLB_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int storage_bytes(int storage) {
+    switch (storage) {
+        case UQLB_F64: return 8;
+        case UQLB_F32: return 4;
+        case UQLB_F16:
+        case UQLB_BF16: return 2;
+        default: return 0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Quadrature, random numbers and the Legendre chaos (Sec. 4, Sec. 6.1-6.3)
+// ---------------------------------------------------------------------------------------
+
+// P_n(x) and P_n'(x) by the three-term recurrence.
+void legendre_eval(int n, double x, double* p_out, double* dp_out) {
+    double pm1 = 1.0, p = x;
+    if (n == 0) {
+        *p_out = 1.0;
+        *dp_out = 0.0;
+        return;
+    }
+    for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * x * p - (k - 1.0) * pm1) / k;
+        pm1 = p;
+        p = pk;
+    }
+    *p_out = p;
+    *dp_out = n * (x * p - pm1) / (x * x - 1.0);
+}
+
+void gauss_legendre_rule(int n, double* x, double* w) {
+    for (int j = 0; j < n; ++j) {
+        double r = std::cos(M_PI * (j + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p, dp;
+            legendre_eval(n, r, &p, &dp);
+            const double step = p / dp;
+            r -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        double p, dp;
+        legendre_eval(n, r, &p, &dp);
+        x[n - 1 - j] = r;  // the initial guesses run from the largest root down
+        w[n - 1 - j] = 2.0 / ((1.0 - r * r) * dp * dp);
+    }
+}
+
+void philox10(const uint32_t in[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t m0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t m1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)m1;
+        c3 = (uint32_t)m0;
+        c0 = n0;
+        c2 = n2;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+// Orthonormal Legendre values phi_0..phi_p at xi: sqrt(2n+1) P_n(xi).
+void phi_values(int p, double xi, double* out) {
+    double pm1 = 1.0, pn = xi;
+    out[0] = 1.0;
+    if (p >= 1) out[1] = std::sqrt(3.0) * xi;
+    for (int n = 2; n <= p; ++n) {
+        const double pk = ((2.0 * n - 1.0) * xi * pn - (n - 1.0) * pm1) / n;
+        pm1 = pn;
+        pn = pk;
+        out[n] = std::sqrt(2.0 * n + 1.0) * pn;
+    }
+}
+
+void enumerate_indices(int dim, int order, int basis, std::vector<int32_t>& out) {
+    std::vector<std::vector<int32_t>> all;
+    std::vector<int32_t> cur(dim, 0);
+    // odometer over [0, order]^dim, pruned by the total degree where that applies
+    while (true) {
+        int sum = 0;
+        for (int d = 0; d < dim; ++d) sum += cur[d];
+        if (basis == UQLB_BASIS_TENSOR || sum <= order) all.push_back(cur);
+        int d = dim - 1;
+        while (d >= 0) {
+            if (++cur[d] <= order) {
+                int s2 = 0;
+                for (int e = 0; e <= d; ++e) s2 += cur[e];
+                if (basis == UQLB_BASIS_TENSOR || s2 <= order) break;
+            }
+            cur[d] = 0;
+            --d;
+        }
+        if (d < 0) break;
+    }
+    std::sort(all.begin(), all.end(), [](const std::vector<int32_t>& l, const std::vector<int32_t>& r) {
+        int sl = 0, sr = 0;
+        for (int v : l) sl += v;
+        for (int v : r) sr += v;
+        if (sl != sr) return sl < sr;
+        return l > r;  // descending lexicographic within a degree
+    });
+    out.clear();
+    for (auto& v : all) out.insert(out.end(), v.begin(), v.end());
+}
+
+int64_t count_indices(int dim, int order, int basis) {
+    if (basis == UQLB_BASIS_TENSOR) {
+        double n = std::pow((double)order + 1.0, dim);
+        return n > 1e7 ? -1 : (int64_t)n;
+    }
+    // C(dim + order, order)
+    double c = 1.0;
+    for (int i = 1; i <= order; ++i) c = c * (dim + i) / i;
+    return c > 1e7 ? -1 : (int64_t)std::llround(c);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batch planning: arena layout, table of samples ordered by descending steps, masks
+// ---------------------------------------------------------------------------------------
+
+bool sample_solid(const uqlb_sample& s, int x, int y) {
+    if (s.kind != UQLB_CASE_CHANNEL || !(s.cyl_r > 0.0)) return false;
+    const double dx = (x + 0.5) - s.cyl_cx, dy = (y + 0.5) - s.cyl_cy;
+    return dx * dx + dy * dy < s.cyl_r * s.cyl_r;
+}
+
+struct BatchPlan {
+    std::vector<SampleDev> table;
+    std::vector<InitDev> init;
+    std::vector<int32_t> steps_sorted;
+    std::vector<uint32_t> masks;
+    size_t off_arena = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
+           off_partials = 0, off_counters = 0, off_done = 0, off_steps_run = 0, off_cd_prev = 0,
+           off_step_counter = 0, off_flag = 0, total = 0;
+    BatchGeometry geom{};
+    int n_steady = 0;
+    bool uniform_size = true;
+};
+
+int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
+    char buf[256];
+    if (s.kind != UQLB_CASE_TGV && s.kind != UQLB_CASE_CHANNEL) {
+        snprintf(buf, sizeof buf, "sample %lld: unknown kind %d", (long long)idx, s.kind);
+    } else if (s.nx < 2 || s.ny < 2 || s.nx > 65536 || s.ny > 65536) {
+        snprintf(buf, sizeof buf, "sample %lld: lattice %d x %d out of range", (long long)idx, s.nx, s.ny);
+    } else if (s.steps < 0 || s.steps >= (1ll << 31) - 2048) {
+        snprintf(buf, sizeof buf, "sample %lld: steps %lld out of range", (long long)idx, (long long)s.steps);
+    } else if (!(s.nu > 0.0) || !std::isfinite(s.nu)) {
+        snprintf(buf, sizeof buf, "sample %lld: viscosity must be positive", (long long)idx);
+    } else if (!std::isfinite(s.u0) || !std::isfinite(s.amp2) || !std::isfinite(s.amp3)) {
+        snprintf(buf, sizeof buf, "sample %lld: non-finite velocity parameter", (long long)idx);
+    } else {
+        return 0;
+    }
+    why = buf;
+    return UQLB_ERR_ARG;
+}
+
+int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchPlan& P, std::string& why) {
+    if (n <= 0 || n > (1 << 24)) {
+        why = "sample count out of range";
+        return UQLB_ERR_ARG;
+    }
+    const int storage = o ? o->storage : UQLB_F32;
+    const int eb = storage_bytes(storage);
+    if (eb == 0) {
+        why = "unknown storage format";
+        return UQLB_ERR_ARG;
+    }
+    int tr = o && o->tile_rows > 0 ? o->tile_rows : 8;
+    if (tr != 1 && tr != 2 && tr != 4 && tr != 8 && tr != 16) {
+        why = "tile_rows must be 1, 2, 4, 8 or 16";
+        return UQLB_ERR_ARG;
+    }
+    for (int64_t s = 0; s < n; ++s)
+        if (int rc = validate_sample(smp[s], s, why)) return rc;
+
+    std::vector<int64_t> order(n);
+    for (int64_t s = 0; s < n; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t l, int64_t r) { return smp[l].steps > smp[r].steps; });
+
+    const int row_align = 128 / eb;
+    P.table.assign(n, SampleDev{});
+    P.init.assign(n, InitDev{});
+    P.steps_sorted.assign(n, 0);
+    P.masks.clear();
+    int64_t f_off = 0, tiles = 0, side = 0;
+    int max_steps = 0, any_channel = 0, tiles0 = -1;
+    bool uniform_tiles = true;
+    P.n_steady = 0;
+    P.uniform_size = true;
+    for (int64_t j = 0; j < n; ++j) {
+        const uqlb_sample& s = smp[order[j]];
+        SampleDev& d = P.table[j];
+        d.nx = s.nx;
+        d.ny = s.ny;
+        d.pitch = (int32_t)align_up((size_t)s.nx, (size_t)row_align);
+        d.plane = (int64_t)d.pitch * s.ny;
+        d.f_off = f_off;
+        f_off += 9 * d.plane;
+        d.kind = s.kind;
+        d.steps = (int32_t)s.steps;
+        d.sample_id = (int32_t)order[j];
+        d.tiles_x = (s.nx + 31) / 32;
+        d.tiles = d.tiles_x * ((s.ny + tr - 1) / tr);
+        d.tile_base = (int32_t)tiles;
+        tiles += d.tiles;
+        if (tiles0 < 0) tiles0 = d.tiles;
+        if (d.tiles != tiles0) uniform_tiles = false;
+        if (s.nx != smp[0].nx || s.ny != smp[0].ny) P.uniform_size = false;
+        d.omega = 1.0 / (3.0 * s.nu + 0.5);
+        d.u_ref_inv2 = (s.u_ref > 0.0) ? 2.0 / ((double)s.nx * (double)s.ny * s.u_ref * s.u_ref) : 0.0;
+        d.mask_off = -1;
+        d.mask_words = (s.nx + 31) / 32;
+        d.side_off = -1;
+        d.uin_max = 0.0;
+        d.force_norm = 0.0;
+        d.ramp_steps = 0.0;
+        d.steady_tol = 0.0;
+        if (s.kind == UQLB_CASE_CHANNEL) {
+            any_channel = 1;
+            d.uin_max = 1.5 * s.u0;
+            d.ramp_steps = (double)std::max<int64_t>(s.ramp_steps, 0);
+            d.steady_tol = s.steady_tol > 0.0 ? s.steady_tol : 0.0;
+            if (d.steady_tol > 0.0) ++P.n_steady;
+            d.side_off = (int32_t)side;
+            side += s.ny;
+            if (s.cyl_r > 0.0) {
+                d.force_norm = (s.u0 != 0.0) ? 2.0 / (s.u0 * s.u0 * 2.0 * s.cyl_r) : 0.0;
+                d.mask_off = (int32_t)P.masks.size();
+                P.masks.resize(P.masks.size() + (size_t)d.mask_words * s.ny, 0u);
+                uint32_t* m = P.masks.data() + d.mask_off;
+                for (int y = 0; y < s.ny; ++y)
+                    for (int x = 0; x < s.nx; ++x)
+                        if (sample_solid(s, x, y)) m[(size_t)y * d.mask_words + (x >> 5)] |= 1u << (x & 31);
+            }
+        }
+        P.init[j].u0 = s.u0;
+        P.init[j].amp2 = s.amp2;
+        P.init[j].amp3 = s.amp3;
+        P.steps_sorted[j] = (int32_t)s.steps;
+        max_steps = std::max(max_steps, (int)s.steps);
+    }
+    if (tiles >= (1ll << 31)) {
+        why = "too many tiles";
+        return UQLB_ERR_ARG;
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + std::max<size_t>(bytes, 1), 256);
+        return at;
+    };
+    P.off_arena = take((size_t)f_off * eb);
+    P.off_samples = take(sizeof(SampleDev) * n);
+    P.off_init = take(sizeof(InitDev) * n);
+    P.off_steps = take(sizeof(int32_t) * n);
+    P.off_masks = take(sizeof(uint32_t) * P.masks.size());
+    P.off_side = take((size_t)side * 2 * 8);
+    P.off_partials = take((size_t)tiles * 7 * sizeof(double));
+    P.off_counters = take(sizeof(int32_t) * n);
+    P.off_done = take(sizeof(int32_t) * n);
+    P.off_steps_run = take(sizeof(int32_t) * n);
+    P.off_cd_prev = take(sizeof(double) * n);
+    P.off_step_counter = take(sizeof(int64_t));
+    P.off_flag = take(sizeof(int32_t));
+    P.total = off;
+
+    BatchGeometry& g = P.geom;
+    g.nsamples = n;
+    g.total_tiles = tiles;
+    g.tile_rows = tr;
+    g.tile_cols = 32;
+    g.max_steps = max_steps;
+    g.storage = storage;
+    g.any_channel = any_channel;
+    g.uniform_tiles = uniform_tiles ? tiles0 : 0;
+    return 0;
+}
+
+BatchBuffers carve(const BatchPlan& P, void* ws) {
+    char* b = static_cast<char*>(ws);
+    BatchBuffers B{};
+    B.arena = b + P.off_arena;
+    B.samples = reinterpret_cast<SampleDev*>(b + P.off_samples);
+    B.init = reinterpret_cast<InitDev*>(b + P.off_init);
+    B.steps_sorted = reinterpret_cast<int32_t*>(b + P.off_steps);
+    B.masks = reinterpret_cast<uint32_t*>(b + P.off_masks);
+    B.side = reinterpret_cast<float*>(b + P.off_side);
+    B.side_d = reinterpret_cast<double*>(b + P.off_side);
+    B.partials = reinterpret_cast<double*>(b + P.off_partials);
+    B.counters = reinterpret_cast<int32_t*>(b + P.off_counters);
+    B.done = reinterpret_cast<int32_t*>(b + P.off_done);
+    B.steps_run = reinterpret_cast<int32_t*>(b + P.off_steps_run);
+    B.cd_prev = reinterpret_cast<double*>(b + P.off_cd_prev);
+    B.step_counter = reinterpret_cast<int64_t*>(b + P.off_step_counter);
+    B.active_flag = reinterpret_cast<int32_t*>(b + P.off_flag);
+    return B;
+}
+
+template <typename T>
+void key_put(std::vector<unsigned char>& k, const T& v) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), p, p + sizeof(T));
+}
+
+// Captured chunk of `chunk` time steps plus the step-counter advance, cached per context.
+int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, const RunOutputs& O, int chunk,
+                cudaGraphExec_t* out) {
+    std::vector<unsigned char> key;
+    key_put(key, B);
+    key_put(key, G);
+    key_put(key, O);
+    key_put(key, chunk);
+    for (auto& e : ctx->graphs) {
+        if (e.key == key) {
+            *out = e.exec;
+            return 0;
+        }
+    }
+    cudaError_t err;
+    if (!ctx->capture_stream) {
+        err = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+        if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamCreateWithFlags");
+    }
+    err = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamBeginCapture");
+    cudaError_t lerr = cudaSuccess;
+    for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) lerr = launch_step(B, G, O, dt, ctx->capture_stream);
+    if (lerr == cudaSuccess) lerr = launch_advance(B, chunk, ctx->capture_stream);
+    cudaGraph_t graph = nullptr;
+    err = cudaStreamEndCapture(ctx->capture_stream, &graph);
+    if (lerr != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, lerr, "kernel launch during capture");
+    }
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(ctx, err, "cudaGraphInstantiate");
+    }
+    if ((int)ctx->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(ctx->graphs.front().exec);
+        cudaGraphDestroy(ctx->graphs.front().graph);
+        ctx->graphs.erase(ctx->graphs.begin());
+    }
+    GraphEntry e;
+    e.key = std::move(key);
+    e.graph = graph;
+    e.exec = exec;
+    ctx->graphs.push_back(std::move(e));
+    *out = exec;
+    return 0;
+}
+
+int check_ctx(uqlb_ctx* ctx) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    const cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return 0;
+}
+
+void build_ensemble(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* out) {
+    for (int64_t s = 0; s < ctx->S; ++s) {
+        uqlb_sample r = c->base;
+        double zeta2 = NAN, zeta3 = NAN;
+        for (int d = 0; d < ctx->dim; ++d) {
+            const double v = ctx->z[(size_t)s * ctx->dim + d];
+            switch (c->param_of_dim[d]) {
+                case UQLB_PARAM_NU: r.nu = v; break;
+                case UQLB_PARAM_U0: r.u0 = v; break;
+                case UQLB_PARAM_ZETA2: zeta2 = v; break;
+                case UQLB_PARAM_ZETA3: zeta3 = v; break;
+                default: break;
+            }
+        }
+        if (!std::isnan(zeta2)) r.amp2 = zeta2 * r.u0;
+        if (!std::isnan(zeta3)) r.amp3 = zeta3 * r.u0;
+        out[s] = r;
+    }
+}
+
+int check_case(uqlb_ctx* ctx, const uqlb_case* c) {
+    if (!c) return set_err(ctx, UQLB_ERR_ARG, "null case");
+    if (ctx->S <= 0) return set_err(ctx, UQLB_ERR_STATE, "no sample set: call uqlb_init_mc or uqlb_init_gpc");
+    for (int d = 0; d < ctx->dim; ++d)
+        if (c->param_of_dim[d] < UQLB_PARAM_NU || c->param_of_dim[d] > UQLB_PARAM_ZETA3)
+            return set_err(ctx, UQLB_ERR_ARG, "param_of_dim[%d] = %d is not a known parameter", d, c->param_of_dim[d]);
+    return 0;
+}
+
+}  // namespace
+
+// =========================================================================================
+// C ABI
+// =========================================================================================
+extern "C" {
+
+int uqlb_gauss_legendre(int n, double* x, double* w) {
+    if (n < 1 || n > 64 || !x || !w) return set_err(nullptr, UQLB_ERR_ARG, "gauss_legendre: need 1 <= n <= 64");
+    gauss_legendre_rule(n, x, w);
+    return 0;
+}
+
+int uqlb_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    if (!ctr || !key || !out) return set_err(nullptr, UQLB_ERR_ARG, "philox: null pointer");
+    philox10(ctr, key, out);
+    return 0;
+}
+
+int uqlb_num_multi_indices(int dim, int order, int basis, int64_t* k) {
+    if (dim < 1 || dim > kMaxDim || order < 0 || order > 64 || !k ||
+        (basis != UQLB_BASIS_TOTAL && basis != UQLB_BASIS_TENSOR))
+        return set_err(nullptr, UQLB_ERR_ARG, "num_multi_indices: bad arguments");
+    const int64_t c = count_indices(dim, order, basis);
+    if (c < 0) return set_err(nullptr, UQLB_ERR_ARG, "num_multi_indices: basis too large");
+    *k = c;
+    return 0;
+}
+
+int uqlb_multi_indices(int dim, int order, int basis, int32_t* alpha) {
+    int64_t k = 0;
+    if (int rc = uqlb_num_multi_indices(dim, order, basis, &k)) return rc;
+    if (!alpha) return set_err(nullptr, UQLB_ERR_ARG, "multi_indices: null output");
+    std::vector<int32_t> v;
+    enumerate_indices(dim, order, basis, v);
+    std::memcpy(alpha, v.data(), v.size() * sizeof(int32_t));
+    return 0;
+}
+
+int uqlb_obstacle_mask(const uqlb_sample* s, uint8_t* mask) {
+    if (!s || !mask || s->nx < 1 || s->ny < 1) return set_err(nullptr, UQLB_ERR_ARG, "obstacle_mask: bad arguments");
+    for (int y = 0; y < s->ny; ++y)
+        for (int x = 0; x < s->nx; ++x) mask[(size_t)y * s->nx + x] = sample_solid(*s, x, y) ? 1 : 0;
+    return 0;
+}
+
+int uqlb_mean_host(const double* v, int64_t n, double* out) {
+    if (!v || !out || n < 1) return set_err(nullptr, UQLB_ERR_ARG, "mean_host: need n >= 1");
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += v[i];
+    *out = s / (double)n;
+    return 0;
+}
+
+int uqlb_std_host(const double* v, int64_t n, int ddof, double* out) {
+    if (!v || !out || n < 1 || ddof < 0 || n - ddof < 1) return set_err(nullptr, UQLB_ERR_ARG, "std_host: need n - ddof >= 1");
+    double mu = 0.0;
+    uqlb_mean_host(v, n, &mu);
+    double ss = 0.0;
+    for (int64_t i = 0; i < n; ++i) ss += (v[i] - mu) * (v[i] - mu);
+    *out = std::sqrt(ss / (double)(n - ddof));
+    return 0;
+}
+
+int uqlb_create(uqlb_ctx** out, int cuda_device) {
+    if (!out) return set_err(nullptr, UQLB_ERR_ARG, "create: null output");
+    *out = nullptr;
+    if (cuda_device < 0) return set_err(nullptr, UQLB_ERR_ARG, "create: negative device");
+    uqlb_ctx* c = new (std::nothrow) uqlb_ctx();
+    if (!c) return set_err(nullptr, UQLB_ERR_OOM, "create: out of host memory");
+    c->device = cuda_device;
+    *out = c;
+    return 0;
+}
+
+int uqlb_destroy(uqlb_ctx* ctx) {
+    if (!ctx) return 0;
+    cudaSetDevice(ctx->device);
+    for (auto& e : ctx->graphs) {
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (e.graph) cudaGraphDestroy(e.graph);
+    }
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->loop_begin) cudaEventDestroy(ctx->loop_begin);
+    if (ctx->loop_end) cudaEventDestroy(ctx->loop_end);
+    delete ctx;
+    return 0;
+}
+
+const char* uqlb_last_error(const uqlb_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
+
+int uqlb_set_inputs(uqlb_ctx* ctx, int dim, const uqlb_dist* d) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (dim < 1 || dim > kMaxDim || !d) return set_err(ctx, UQLB_ERR_ARG, "set_inputs: need 1 <= dim <= %d", kMaxDim);
+    for (int k = 0; k < dim; ++k) {
+        if (d[k].kind != UQLB_DIST_UNIFORM) return set_err(ctx, UQLB_ERR_ARG, "set_inputs: input %d is not uniform", k);
+        if (!(d[k].b > d[k].a) || !std::isfinite(d[k].a) || !std::isfinite(d[k].b))
+            return set_err(ctx, UQLB_ERR_ARG, "set_inputs: input %d needs finite a < b", k);
+    }
+    ctx->dim = dim;
+    ctx->dists.assign(d, d + dim);
+    ctx->method = UQLB_METHOD_NONE;
+    ctx->S = 0;
+    ctx->K = 0;
+    return 0;
+}
+
+int uqlb_init_mc(uqlb_ctx* ctx, int64_t n, uint64_t seed) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (ctx->dim < 1) return set_err(ctx, UQLB_ERR_STATE, "init_mc: call uqlb_set_inputs first");
+    if (n < 1 || n > (1 << 24)) return set_err(ctx, UQLB_ERR_ARG, "init_mc: need 1 <= n <= 2^24");
+    const int d = ctx->dim;
+    ctx->z.assign((size_t)n * d, 0.0);
+    ctx->xi.assign((size_t)n * d, 0.0);
+    ctx->a.assign((size_t)n, 1.0 / (double)n);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t s = 0; s < n; ++s) {
+        for (int k = 0; k < d; ++k) {
+            const uint32_t ctr[4] = {(uint32_t)s, (uint32_t)((uint64_t)s >> 32), (uint32_t)k, 0u};
+            uint32_t r[4];
+            philox10(ctr, key, r);
+            const uint64_t bits = ((uint64_t)r[1] << 32) | r[0];
+            const double u = (double)(bits >> 11) * 0x1.0p-53;
+            ctx->z[(size_t)s * d + k] = ctx->dists[k].a + (ctx->dists[k].b - ctx->dists[k].a) * u;
+            ctx->xi[(size_t)s * d + k] = 2.0 * u - 1.0;
+        }
+    }
+    ctx->S = n;
+    ctx->method = UQLB_METHOD_MC;
+    ctx->K = 0;
+    ctx->W.clear();
+    ctx->alpha.clear();
+    return 0;
+}
+
+int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (ctx->dim < 1) return set_err(ctx, UQLB_ERR_STATE, "init_gpc: call uqlb_set_inputs first");
+    if (quad != UQLB_QUAD_GAUSS_LEGENDRE_TENSOR) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: unknown quadrature");
+    if (pts_per_dim < 1 || pts_per_dim > 64) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: need 1 <= pts_per_dim <= 64");
+    int64_t K = 0;
+    if (uqlb_num_multi_indices(ctx->dim, order, basis, &K) != 0)
+        return set_err(ctx, UQLB_ERR_ARG, "init_gpc: %s", g_last_error.c_str());
+    const int d = ctx->dim;
+    const double Sd = std::pow((double)pts_per_dim, d);
+    if (Sd > (double)(1 << 24)) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: tensor grid too large");
+    const int64_t S = (int64_t)std::llround(Sd);
+    if (K * S > (int64_t)1 << 28) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: K x S too large");
+    std::vector<double> gx(pts_per_dim), gw(pts_per_dim);
+    gauss_legendre_rule(pts_per_dim, gx.data(), gw.data());
+    ctx->z.assign((size_t)S * d, 0.0);
+    ctx->xi.assign((size_t)S * d, 0.0);
+    ctx->a.assign((size_t)S, 0.0);
+    std::vector<int> idx(d, 0);
+    for (int64_t s = 0; s < S; ++s) {
+        // lexicographic, last dimension fastest
+        int64_t r = s;
+        for (int k = d - 1; k >= 0; --k) {
+            idx[k] = (int)(r % pts_per_dim);
+            r /= pts_per_dim;
+        }
+        double w = 1.0;
+        for (int k = 0; k < d; ++k) {
+            const double xi = gx[idx[k]];
+            const double lo = ctx->dists[k].a, hi = ctx->dists[k].b;
+            ctx->xi[(size_t)s * d + k] = xi;
+            ctx->z[(size_t)s * d + k] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * xi;
+            w *= 0.5 * gw[idx[k]];
+        }
+        ctx->a[s] = w;
+    }
+    enumerate_indices(d, order, basis, ctx->alpha);
+    ctx->K = (int)K;
+    ctx->W.assign((size_t)K * S, 0.0);
+    std::vector<double> phis((size_t)(order + 1) * d);
+    for (int64_t s = 0; s < S; ++s) {
+        for (int k = 0; k < d; ++k) phi_values(order, ctx->xi[(size_t)s * d + k], phis.data() + (size_t)k * (order + 1));
+        for (int64_t t = 0; t < K; ++t) {
+            double v = ctx->a[s];
+            for (int k = 0; k < d; ++k) v *= phis[(size_t)k * (order + 1) + ctx->alpha[(size_t)t * d + k]];
+            ctx->W[(size_t)t * S + s] = v;
+        }
+    }
+    ctx->S = S;
+    ctx->order = order;
+    ctx->basis = basis;
+    ctx->method = UQLB_METHOD_GPC;
+    return 0;
+}
+
+int uqlb_num_samples(const uqlb_ctx* ctx, int64_t* n) {
+    if (!ctx || !n) return set_err(nullptr, UQLB_ERR_ARG, "num_samples: null pointer");
+    *n = ctx->S;
+    return 0;
+}
+
+int uqlb_num_terms(const uqlb_ctx* ctx, int* k) {
+    if (!ctx || !k) return set_err(nullptr, UQLB_ERR_ARG, "num_terms: null pointer");
+    *k = ctx->K;
+    return 0;
+}
+
+int uqlb_get_samples(const uqlb_ctx* ctx, double* z, double* xi, double* a) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (ctx->S <= 0) return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_STATE, "get_samples: no sample set");
+    if (z) std::memcpy(z, ctx->z.data(), ctx->z.size() * sizeof(double));
+    if (xi) std::memcpy(xi, ctx->xi.data(), ctx->xi.size() * sizeof(double));
+    if (a) std::memcpy(a, ctx->a.data(), ctx->a.size() * sizeof(double));
+    return 0;
+}
+
+int uqlb_get_weight_matrix(const uqlb_ctx* ctx, double* w) {
+    if (!ctx || !w) return set_err(nullptr, UQLB_ERR_ARG, "get_weight_matrix: null pointer");
+    if (ctx->method != UQLB_METHOD_GPC) return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_STATE, "get_weight_matrix: call uqlb_init_gpc first");
+    std::memcpy(w, ctx->W.data(), ctx->W.size() * sizeof(double));
+    return 0;
+}
+
+int uqlb_batch_workspace_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes) {
+    if (!samples || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "batch_workspace_bytes: null pointer");
+    BatchPlan P;
+    std::string why;
+    if (int rc = plan_batch(samples, n, opts, P, why)) return set_err(nullptr, rc, "%s", why.c_str());
+    *bytes = P.total;
+    return 0;
+}
+
+int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
+                   void* workspace_dev, size_t workspace_bytes, void* fields_dev, int64_t fields_ld,
+                   double* qoi_dev, double* series_dev, double* series_cl_dev, int64_t series_ld, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (!samples || !opts || !workspace_dev) return set_err(ctx, UQLB_ERR_ARG, "run_batch: null argument");
+    if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: workspace must be 256-byte aligned");
+    BatchPlan P;
+    std::string why;
+    if (int rc = plan_batch(samples, n, opts, P, why)) return set_err(ctx, rc, "run_batch: %s", why.c_str());
+    if (workspace_bytes < P.total)
+        return set_err(ctx, UQLB_ERR_OOM, "run_batch: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
+    if (fields_dev) {
+        if (!P.uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
+        if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_ld too small");
+        if (opts->fields_dtype != UQLB_F64 && opts->fields_dtype != UQLB_F32)
+            return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_dtype must be F64 or F32");
+    }
+    if (opts->qoi_every < 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: qoi_every must be >= 0");
+    if ((series_dev || series_cl_dev) && opts->qoi_every > 0) {
+        const int64_t need = P.geom.max_steps / opts->qoi_every + 1;
+        if (series_ld < need) return set_err(ctx, UQLB_ERR_ARG, "run_batch: series_ld %lld < %lld", (long long)series_ld, (long long)need);
+    }
+    int chunk = opts->chunk_steps > 0 ? opts->chunk_steps : 64;
+    if (chunk < 2 || chunk > 1024 || (chunk & 1)) return set_err(ctx, UQLB_ERR_ARG, "run_batch: chunk_steps must be even, 2..1024");
+    if (P.n_steady > 0 && opts->qoi_every <= 0)
+        return set_err(ctx, UQLB_ERR_ARG, "run_batch: a steady-state tolerance needs qoi_every > 0");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchBuffers B = carve(P, workspace_dev);
+    char* ws = static_cast<char*>(workspace_dev);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
+        (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
+                                                  cudaMemcpyHostToDevice, s))) ||
+        (e = cudaMemsetAsync(B.step_counter, 0, sizeof(int64_t), s)) ||
+        (e = cudaMemsetAsync(B.active_flag, 0, sizeof(int32_t), s)) ||
+        (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s)))
+        return cuda_fail(ctx, e, "run_batch: table upload");
+
+    RunOutputs O{};
+    O.fields = fields_dev;
+    O.fields_ld = fields_ld;
+    O.fields_dtype = opts->fields_dtype;
+    O.qoi = qoi_dev;
+    O.series = series_dev;
+    O.series_cl = series_cl_dev;
+    O.series_ld = series_ld;
+    O.qoi_every = opts->qoi_every;
+
+    if (!ctx->loop_begin) {
+        if ((e = cudaEventCreate(&ctx->loop_begin)) || (e = cudaEventCreate(&ctx->loop_end)))
+            return cuda_fail(ctx, e, "run_batch: event create");
+    }
+    ctx->loop_timed = false;
+    ctx->loop_steps = P.geom.max_steps;
+    ctx->run_launches = 2;
+    if ((e = launch_init(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: init launch");
+    if (P.geom.max_steps > 0) {
+        cudaGraphExec_t exec = nullptr;
+        if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, &exec)) return rc;
+        const int64_t nchunks = (P.geom.max_steps + chunk - 1) / chunk;
+        const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
+        if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+        for (int64_t q = 0; q < nchunks; ++q) {
+            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
+            ctx->run_launches += chunk + 1;
+            if (steady && (q % 8) == 7 && q + 1 < nchunks) {
+                int32_t ndone = 0;
+                if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
+                    (e = cudaStreamSynchronize(s)))
+                    return cuda_fail(ctx, e, "run_batch: convergence check");
+                if (ndone >= P.n_steady) break;
+            }
+        }
+        if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+        ctx->loop_timed = true;
+    }
+    if ((e = launch_finalize(B, P.geom, O, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: finalize launch");
+    return 0;
+}
+
+int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (steps) *steps = ctx->loop_steps;
+    if (launches) *launches = ctx->run_launches;
+    if (ms) {
+        *ms = 0.0;
+        if (ctx->loop_timed) {
+            float f = 0.0f;
+            cudaError_t e;
+            if ((e = cudaEventSynchronize(ctx->loop_end)) || (e = cudaEventElapsedTime(&f, ctx->loop_begin, ctx->loop_end)))
+                return cuda_fail(ctx, e, "last_loop_time");
+            *ms = f;
+        }
+    }
+    return 0;
+}
+
+int uqlb_ensemble_samples(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* out) {
+    if (!ctx || !c || !out) return set_err(nullptr, UQLB_ERR_ARG, "ensemble_samples: null pointer");
+    if (int rc = check_case(const_cast<uqlb_ctx*>(ctx), c)) return rc;
+    build_ensemble(ctx, c, out);
+    return 0;
+}
+
+int uqlb_ensemble_workspace_bytes(const uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts, size_t* bytes) {
+    if (!ctx || !c || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "ensemble_workspace_bytes: null pointer");
+    if (int rc = check_case(const_cast<uqlb_ctx*>(ctx), c)) return rc;
+    std::vector<uqlb_sample> smp(ctx->S);
+    build_ensemble(ctx, c, smp.data());
+    BatchPlan P;
+    std::string why;
+    if (int rc = plan_batch(smp.data(), ctx->S, opts, P, why))
+        return set_err(const_cast<uqlb_ctx*>(ctx), rc, "%s", why.c_str());
+    *bytes = P.total;
+    return 0;
+}
+
+int uqlb_run_ensemble(uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts, void* workspace_dev,
+                      size_t workspace_bytes, void* fields_dev, int64_t fields_ld, double* qoi_dev,
+                      double* series_dev, double* series_cl_dev, int64_t series_ld, void* stream) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (int rc = check_case(ctx, c)) return rc;
+    std::vector<uqlb_sample> smp(ctx->S);
+    build_ensemble(ctx, c, smp.data());
+    return uqlb_run_batch(ctx, smp.data(), ctx->S, opts, workspace_dev, workspace_bytes, fields_dev, fields_ld,
+                          qoi_dev, series_dev, series_cl_dev, series_ld, stream);
+}
+
+int uqlb_plain_workspace_bytes(const uqlb_sample* samples, int64_t n, size_t* bytes) {
+    if (!samples || !bytes || n < 1) return set_err(nullptr, UQLB_ERR_ARG, "plain_workspace_bytes: bad arguments");
+    int64_t maxn = 0;
+    std::string why;
+    for (int64_t s = 0; s < n; ++s) {
+        if (int rc = validate_sample(samples[s], s, why)) return set_err(nullptr, rc, "%s", why.c_str());
+        maxn = std::max<int64_t>(maxn, (int64_t)samples[s].nx * samples[s].ny);
+    }
+    const int64_t blocks = (maxn + 255) / 256;
+    *bytes = align_up((size_t)maxn * 9 * 8, 256) * 2 + align_up((size_t)maxn, 256) + align_up((size_t)blocks * 7 * 8, 256);
+    return 0;
+}
+
+int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int64_t qoi_every, void* workspace_dev,
+                       size_t workspace_bytes, double* fields_dev, int64_t fields_ld, double* qoi_dev,
+                       double* series_dev, int64_t series_ld, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    size_t need = 0;
+    if (int rc = uqlb_plain_workspace_bytes(samples, n, &need)) return set_err(ctx, rc, "run_plain_f64: %s", g_last_error.c_str());
+    if (!workspace_dev || workspace_bytes < need)
+        return set_err(ctx, UQLB_ERR_OOM, "run_plain_f64: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    if (qoi_every < 0) return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: qoi_every must be >= 0");
+    int64_t maxn = 0;
+    for (int64_t s = 0; s < n; ++s) maxn = std::max<int64_t>(maxn, (int64_t)samples[s].nx * samples[s].ny);
+    if (fields_dev) {
+        for (int64_t s = 0; s < n; ++s)
+            if (samples[s].nx != samples[0].nx || samples[s].ny != samples[0].ny)
+                return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: field output needs one lattice size");
+        if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: fields_ld too small");
+    }
+    char* ws = static_cast<char*>(workspace_dev);
+    const size_t lat = align_up((size_t)maxn * 9 * 8, 256);
+    double* fa = reinterpret_cast<double*>(ws);
+    double* fb = reinterpret_cast<double*>(ws + lat);
+    uint8_t* solid = reinterpret_cast<uint8_t*>(ws + 2 * lat);
+    double* partials = reinterpret_cast<double*>(ws + 2 * lat + align_up((size_t)maxn, 256));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<uint8_t> mask;
+    for (int64_t q = 0; q < n; ++q) {
+        const uqlb_sample& sm = samples[q];
+        PlainSample p{};
+        p.nx = sm.nx;
+        p.ny = sm.ny;
+        p.kind = sm.kind;
+        p.steps = (int32_t)sm.steps;
+        p.omega = 1.0 / (3.0 * sm.nu + 0.5);
+        p.u0 = sm.u0;
+        p.amp2 = sm.amp2;
+        p.amp3 = sm.amp3;
+        p.u_ref_inv2 = sm.u_ref > 0.0 ? 2.0 / ((double)sm.nx * sm.ny * sm.u_ref * sm.u_ref) : 0.0;
+        p.uin_max = 1.5 * sm.u0;
+        p.force_norm = (sm.kind == UQLB_CASE_CHANNEL && sm.cyl_r > 0.0 && sm.u0 != 0.0) ? 2.0 / (sm.u0 * sm.u0 * 2.0 * sm.cyl_r) : 0.0;
+        p.ramp_steps = (double)std::max<int64_t>(sm.ramp_steps, 0);
+        p.cyl_cx = sm.cyl_cx;
+        p.cyl_cy = sm.cyl_cy;
+        p.cyl_r = sm.cyl_r;
+        mask.assign((size_t)sm.nx * sm.ny, 0);
+        for (int y = 0; y < sm.ny; ++y)
+            for (int x = 0; x < sm.nx; ++x) mask[(size_t)y * sm.nx + x] = sample_solid(sm, x, y) ? 1 : 0;
+        cudaError_t e = cudaMemcpyAsync(solid, mask.data(), mask.size(), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "run_plain_f64: mask upload");
+        e = plain_run_sample(p, fa, fb, solid, partials, qoi_every, fields_dev ? fields_dev + q * fields_ld : nullptr,
+                             qoi_dev ? qoi_dev + q * UQLB_QOI_COLS : nullptr,
+                             series_dev ? series_dev + q * series_ld : nullptr, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "run_plain_f64: launch");
+    }
+    return 0;
+}
+
+int uqlb_post_workspace_bytes(const uqlb_ctx* ctx, size_t* bytes) {
+    if (!ctx || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "post_workspace_bytes: null pointer");
+    *bytes = align_up(std::max<size_t>(ctx->W.size(), 1) * sizeof(double), 256);
+    return 0;
+}
+
+int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld, double* coeffs_dev,
+                 void* workspace_dev, size_t workspace_bytes, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (ctx->method != UQLB_METHOD_GPC) return set_err(ctx, UQLB_ERR_STATE, "project: call uqlb_init_gpc first");
+    if (!m_dev || !coeffs_dev || !workspace_dev || n_fields < 0 || m_ld < n_fields)
+        return set_err(ctx, UQLB_ERR_ARG, "project: bad arguments");
+    if (dtype != UQLB_F64 && dtype != UQLB_F32) return set_err(ctx, UQLB_ERR_ARG, "project: dtype must be F64 or F32");
+    size_t need = 0;
+    uqlb_post_workspace_bytes(ctx, &need);
+    if (workspace_bytes < need) return set_err(ctx, UQLB_ERR_OOM, "project: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(workspace_dev, ctx->W.data(), ctx->W.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project: W upload");
+    e = launch_project(static_cast<const double*>(workspace_dev), ctx->K, (int)ctx->S, m_dev, dtype, n_fields, m_ld,
+                       coeffs_dev, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project: launch");
+    return 0;
+}
+
+int uqlb_stats(uqlb_ctx* ctx, const void* in_dev, int dtype, int64_t n_fields, int64_t m_ld, double* mean_dev,
+               double* var_dev, int ddof, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (!in_dev || n_fields < 0) return set_err(ctx, UQLB_ERR_ARG, "stats: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (ctx->method == UQLB_METHOD_GPC) {
+        if (dtype != UQLB_F64) return set_err(ctx, UQLB_ERR_ARG, "stats: gPC coefficients are FP64");
+        e = launch_gpc_stats(static_cast<const double*>(in_dev), ctx->K, n_fields, mean_dev, var_dev, s);
+    } else if (ctx->method == UQLB_METHOD_MC) {
+        if (dtype != UQLB_F64 && dtype != UQLB_F32) return set_err(ctx, UQLB_ERR_ARG, "stats: dtype must be F64 or F32");
+        if (m_ld < n_fields || ddof < 0 || ctx->S - ddof < 1) return set_err(ctx, UQLB_ERR_ARG, "stats: bad m_ld or ddof");
+        e = launch_mc_stats(in_dev, dtype, ctx->S, n_fields, m_ld, mean_dev, var_dev, ddof, s);
+    } else {
+        return set_err(ctx, UQLB_ERR_STATE, "stats: no sample set");
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stats: launch");
+    return 0;
+}
+
+int uqlb_uq_workspace_bytes(const uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts, size_t* bytes) {
+    if (!ctx || !c || !opts || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "uq_workspace_bytes: null pointer");
+    size_t b = 0;
+    if (int rc = uqlb_ensemble_workspace_bytes(ctx, c, opts, &b)) return rc;
+    const int64_t F = 2 * (int64_t)c->base.nx * c->base.ny + 1;
+    const size_t eb = opts->fields_dtype == UQLB_F64 ? 8 : 4;
+    b = align_up(b, 256) + align_up((size_t)ctx->S * F * eb, 256);                 // fields M
+    b += align_up((size_t)std::max(ctx->K, 1) * F * 8, 256);                        // coefficients
+    b += 2 * align_up((size_t)F * 8, 256);                                          // mean, var
+    b += align_up(std::max<size_t>(ctx->W.size(), 1) * 8, 256);                     // W
+    b += align_up((size_t)ctx->S * UQLB_QOI_COLS * 8, 256);                         // qoi
+    *bytes = b;
+    return 0;
+}
+
+int uqlb_run_uq_host(uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts, void* workspace_dev,
+                     size_t workspace_bytes, double* mean_host, double* var_host, double* coeffs_host,
+                     double* qoi_host, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (!c || !opts || !workspace_dev || !mean_host || !var_host) return set_err(ctx, UQLB_ERR_ARG, "run_uq_host: null argument");
+    size_t need = 0;
+    if (int rc = uqlb_uq_workspace_bytes(ctx, c, opts, &need)) return set_err(ctx, rc, "run_uq_host: %s", g_last_error.c_str());
+    if (workspace_bytes < need) return set_err(ctx, UQLB_ERR_OOM, "run_uq_host: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    if (opts->fields_dtype != UQLB_F64 && opts->fields_dtype != UQLB_F32) return set_err(ctx, UQLB_ERR_ARG, "run_uq_host: fields_dtype");
+    size_t run_b = 0;
+    uqlb_ensemble_workspace_bytes(ctx, c, opts, &run_b);
+    const int64_t F = 2 * (int64_t)c->base.nx * c->base.ny + 1;
+    const size_t eb = opts->fields_dtype == UQLB_F64 ? 8 : 4;
+    char* p = static_cast<char*>(workspace_dev);
+    size_t off = align_up(run_b, 256);
+    void* M = p + off;
+    off += align_up((size_t)ctx->S * F * eb, 256);
+    double* C = reinterpret_cast<double*>(p + off);
+    off += align_up((size_t)std::max(ctx->K, 1) * F * 8, 256);
+    double* mean = reinterpret_cast<double*>(p + off);
+    off += align_up((size_t)F * 8, 256);
+    double* var = reinterpret_cast<double*>(p + off);
+    off += align_up((size_t)F * 8, 256);
+    void* wbuf = p + off;
+    off += align_up(std::max<size_t>(ctx->W.size(), 1) * 8, 256);
+    double* qoi = reinterpret_cast<double*>(p + off);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (int rc = uqlb_run_ensemble(ctx, c, opts, workspace_dev, run_b, M, F, qoi, nullptr, nullptr, 0, stream)) return rc;
+    if (ctx->method == UQLB_METHOD_GPC) {
+        size_t wb = 0;
+        uqlb_post_workspace_bytes(ctx, &wb);
+        if (int rc = uqlb_project(ctx, M, opts->fields_dtype, F, F, C, wbuf, wb, stream)) return rc;
+        if (int rc = uqlb_stats(ctx, C, UQLB_F64, F, F, mean, var, 0, stream)) return rc;
+    } else {
+        if (int rc = uqlb_stats(ctx, M, opts->fields_dtype, F, F, mean, var, 1, stream)) return rc;
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(mean_host, mean, (size_t)F * 8, cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(var_host, var, (size_t)F * 8, cudaMemcpyDeviceToHost, s)) ||
+        (coeffs_host && ctx->method == UQLB_METHOD_GPC &&
+         (e = cudaMemcpyAsync(coeffs_host, C, (size_t)ctx->K * F * 8, cudaMemcpyDeviceToHost, s))) ||
+        (qoi_host && (e = cudaMemcpyAsync(qoi_host, qoi, (size_t)ctx->S * UQLB_QOI_COLS * 8, cudaMemcpyDeviceToHost, s))) ||
+        (e = cudaStreamSynchronize(s)))
+        return cuda_fail(ctx, e, "run_uq_host: copy back");
+    return 0;
+}
+
+}  // extern "C"

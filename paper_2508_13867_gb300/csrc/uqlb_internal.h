@@ -1,0 +1,115 @@
+// Internal declarations shared by the host code (uqlb_host.cpp) and the CUDA launchers.
+// Not part of the public ABI (include/uqlb.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/uqlb.h"
+
+namespace uqlb {
+
+// Per-sample parameters as the step kernels read them.  One 128-byte record per sample;
+// records are ordered by descending step count so that the samples still running at step t
+// form a prefix of the table.
+struct alignas(16) SampleDev {
+    int64_t f_off;      // element offset of the sample's populations in the arena
+    int64_t plane;      // elements per population plane (pitch * ny)
+    int32_t nx, ny;
+    int32_t pitch;      // row pitch in elements (multiple of 32 elements)
+    int32_t kind;       // UQLB_CASE_TGV / UQLB_CASE_CHANNEL
+    int32_t steps;      // steps to run (TGV) or step cap (CHANNEL)
+    int32_t sample_id;  // row of the sample in the caller's outputs
+    int32_t tiles_x;    // tiles per tile row
+    int32_t tiles;      // tiles of this sample
+    int32_t tile_base;  // index of the first tile of this sample in the global tile order
+    int32_t mask_off;   // word offset of the obstacle bitmask (-1: no obstacle)
+    int32_t mask_words; // 32-bit words per mask row
+    int32_t side_off;   // offset (in pairs) of the outlet velocity buffer
+    double omega;       // 1 / tau
+    double u_ref_inv2;  // 2 / (nx ny u_ref^2), 0 when K is disabled
+    double uin_max;     // channel: peak inflow velocity (1.5 x mean)
+    double force_norm;  // channel: 2 / (rho0 u_mean^2 D)
+    double ramp_steps;  // channel: ramp length (0: none)
+    double steady_tol;  // channel: steady-state tolerance (0: none)
+    int32_t pad[2];
+};
+static_assert(sizeof(SampleDev) == 128, "SampleDev must stay 128 bytes");
+
+// Initial-field parameters (read once by the init kernel).
+struct alignas(16) InitDev {
+    double u0, amp2, amp3;
+    double pad;
+};
+
+// Device pointers carved out of the caller's workspace for one batch run.
+struct BatchBuffers {
+    void* arena;             // populations, storage type
+    SampleDev* samples;      // [S] ordered by descending steps
+    InitDev* init;           // [S] same order
+    int32_t* steps_sorted;   // [S] descending
+    uint32_t* masks;         // obstacle bitmasks
+    float* side;             // outlet velocities (float pairs)
+    double* side_d;          // outlet velocities (double pairs, FP64 storage)
+    double* partials;        // [tiles x 3] per-tile QoI partial sums
+    int32_t* counters;       // [S] tiles finished in the current reduction
+    int32_t* done;           // [S] 1 once a sample has stopped (steady state)
+    int32_t* steps_run;      // [S]
+    double* cd_prev;         // [S] previous C_D check
+    int64_t* step_counter;   // [1] base step of the running graph chunk
+    int32_t* active_flag;    // [1] nonzero while any channel sample still runs
+};
+
+struct BatchGeometry {
+    int64_t nsamples;
+    int64_t total_tiles;
+    int32_t tile_rows;
+    int32_t tile_cols;       // nodes per tile row (32)
+    int32_t max_steps;
+    int32_t storage;
+    int32_t any_channel;
+    int32_t uniform_tiles;   // tiles per sample when every sample has the same size, else 0
+};
+
+// Output pointers of a run (rows indexed by SampleDev::sample_id).
+struct RunOutputs {
+    void* fields;
+    int64_t fields_ld;
+    int32_t fields_dtype;
+    double* qoi;
+    double* series;
+    double* series_cl;
+    int64_t series_ld;
+    int64_t qoi_every;
+};
+
+// Launchers (lbm_kernels.cu).
+cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
+cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
+                        int dt, cudaStream_t s);
+cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
+cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
+                            cudaStream_t s);
+int step_grid_blocks(const BatchGeometry& g);
+
+// Plain per-sample FP64 path (plain_f64.cu).
+struct PlainSample {
+    int32_t nx, ny, kind, steps;
+    double omega, u0, amp2, amp3, u_ref_inv2, uin_max, force_norm, ramp_steps;
+    double cyl_cx, cyl_cy, cyl_r;
+};
+cudaError_t plain_run_sample(const PlainSample& p, double* f_a, double* f_b, uint8_t* solid,
+                             double* partials, int64_t qoi_every, double* fields,
+                             double* qoi_row, double* series_row, cudaStream_t s);
+
+// Postprocessing (project_kernels.cu).
+cudaError_t launch_project(const double* W, int K, int S, const void* M, int dtype,
+                           int64_t F, int64_t ld, double* C, cudaStream_t s);
+cudaError_t launch_gpc_stats(const double* C, int K, int64_t F, double* mean, double* var,
+                             cudaStream_t s);
+cudaError_t launch_mc_stats(const void* M, int dtype, int64_t S, int64_t F, int64_t ld,
+                            double* mean, double* var, int ddof, cudaStream_t s);
+
+}  // namespace uqlb

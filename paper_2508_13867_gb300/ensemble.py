@@ -1,0 +1,181 @@
+"""Torch-backed convenience layer over the C ABI: device memory comes from torch tensors, work
+runs on torch's current CUDA stream, and every step of the computation happens inside
+libuqlb.so.  Nothing here computes: it sizes buffers, builds the C structs and calls ``uqlb``.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import uqlb as U
+from .workloads import SampleSpec, Workload
+
+STORAGE = {"f64": U.UQLB_F64, "f32": U.UQLB_F32, "f16": U.UQLB_F16, "bf16": U.UQLB_BF16}
+PARAMS = {"nu": U.UQLB_PARAM_NU, "u0": U.UQLB_PARAM_U0, "zeta2": U.UQLB_PARAM_ZETA2, "zeta3": U.UQLB_PARAM_ZETA3}
+
+
+def sample_struct(s: SampleSpec) -> U.uqlb_sample:
+    return U.uqlb_sample(s.kind, s.nx, s.ny, 0, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref, s.cyl_cx, s.cyl_cy,
+                         s.cyl_r, s.ramp_steps, s.steady_tol)
+
+
+def case_struct(w: Workload) -> U.uqlb_case:
+    c = U.uqlb_case()
+    c.base = sample_struct(w.base)
+    for i, p in enumerate(w.params):
+        c.param_of_dim[i] = PARAMS[p]
+    return c
+
+
+def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
+                tile_rows: int = 0) -> U.uqlb_run_opts:
+    return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows)
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _torch_dtype(code: int):
+    return torch.float64 if code == U.UQLB_F64 else torch.float32
+
+
+class Ensemble:
+    """The UQ manager of one device: inputs, sample set, runs, projection and statistics."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.ctx = U.uqlb_create(device)
+        self.dim = 0
+        self._ws = None
+
+    def close(self):
+        if self.ctx is not None:
+            U.uqlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- sampling ---------------------------------------------------------------------
+    def set_inputs(self, bounds):
+        U.uqlb_set_inputs(self.ctx, bounds)
+        self.dim = len(bounds)
+
+    def init_mc(self, n: int, seed: int):
+        U.uqlb_init_mc(self.ctx, n, seed)
+
+    def init_gpc(self, order: int, pts_per_dim: int, basis: int = U.UQLB_BASIS_TOTAL):
+        U.uqlb_init_gpc(self.ctx, order, pts_per_dim, basis)
+
+    def setup(self, w: Workload):
+        self.set_inputs(w.bounds)
+        if w.method == "gpc":
+            self.init_gpc(w.order, w.pts_per_dim)
+        else:
+            self.init_mc(w.n_mc, w.seed)
+
+    def samples(self):
+        return U.uqlb_get_samples(self.ctx, self.dim)
+
+    @property
+    def num_samples(self) -> int:
+        return U.uqlb_num_samples(self.ctx)
+
+    @property
+    def num_terms(self) -> int:
+        return U.uqlb_num_terms(self.ctx)
+
+    def ensemble_samples(self, w: Workload) -> list:
+        return U.uqlb_ensemble_samples(self.ctx, case_struct(w))
+
+    # ---- device memory ------------------------------------------------------------------
+    def workspace(self, nbytes: int) -> torch.Tensor:
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = None
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    # ---- runs -------------------------------------------------------------------------
+    def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
+                  fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
+                  out: dict | None = None) -> dict:
+        """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series)."""
+        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows)
+        nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
+        ws = self.workspace(nbytes)
+        n = len(samples)
+        dev = f"cuda:{self.device}"
+        res = out if out is not None else {}
+        F = 2 * samples[0].nx * samples[0].ny + 1
+        if fields and "fields" not in res:
+            res["fields"] = torch.empty((n, F), dtype=_torch_dtype(opts.fields_dtype), device=dev)
+        if "qoi" not in res:
+            res["qoi"] = torch.full((n, U.UQLB_QOI_COLS), float("nan"), dtype=torch.float64, device=dev)
+        ld = 0
+        if series and qoi_every > 0:
+            ld = max(int(s.steps) for s in samples) // qoi_every + 1
+            if "series" not in res:
+                res["series"] = torch.full((n, ld), float("nan"), dtype=torch.float64, device=dev)
+                res["series_cl"] = torch.full((n, ld), float("nan"), dtype=torch.float64, device=dev)
+        U.uqlb_run_batch(self.ctx, samples, opts, ws.data_ptr(), ws.numel(),
+                         res["fields"].data_ptr() if fields else 0, F if fields else 0, res["qoi"].data_ptr(),
+                         res["series"].data_ptr() if ld else 0, res["series_cl"].data_ptr() if ld else 0, ld,
+                         _stream())
+        return res
+
+    def run_plain_f64(self, samples, qoi_every: int = 0, series: bool = False, fields: bool = True) -> dict:
+        nbytes = U.uqlb_plain_workspace_bytes(samples)
+        ws = self.workspace(nbytes)
+        n = len(samples)
+        dev = f"cuda:{self.device}"
+        F = 2 * samples[0].nx * samples[0].ny + 1
+        res = {"qoi": torch.full((n, U.UQLB_QOI_COLS), float("nan"), dtype=torch.float64, device=dev)}
+        if fields:
+            res["fields"] = torch.empty((n, F), dtype=torch.float64, device=dev)
+        ld = 0
+        if series and qoi_every > 0:
+            ld = max(int(s.steps) for s in samples) // qoi_every + 1
+            res["series"] = torch.full((n, ld), float("nan"), dtype=torch.float64, device=dev)
+        U.uqlb_run_plain_f64(self.ctx, samples, qoi_every, ws.data_ptr(), ws.numel(),
+                             res["fields"].data_ptr() if fields else 0, F if fields else 0, res["qoi"].data_ptr(),
+                             res["series"].data_ptr() if ld else 0, ld, _stream())
+        return res
+
+    # ---- postprocessing ---------------------------------------------------------------
+    def project(self, m: torch.Tensor, coeffs: torch.Tensor | None = None) -> torch.Tensor:
+        dtype = U.UQLB_F64 if m.dtype == torch.float64 else U.UQLB_F32
+        F = m.shape[1]
+        if coeffs is None:
+            coeffs = torch.empty((self.num_terms, F), dtype=torch.float64, device=m.device)
+        wsb = U.uqlb_post_workspace_bytes(self.ctx)
+        if not hasattr(self, "_post") or self._post.numel() < wsb:
+            self._post = torch.empty(max(wsb, 256), dtype=torch.uint8, device=m.device)
+        U.uqlb_project(self.ctx, m.data_ptr(), dtype, F, m.stride(0), coeffs.data_ptr(), self._post.data_ptr(),
+                       self._post.numel(), _stream())
+        return coeffs
+
+    def stats(self, x: torch.Tensor, ddof: int = 1):
+        """gPC context: x = coefficients [K x F]; MC context: x = fields M [S x F]."""
+        dtype = U.UQLB_F64 if x.dtype == torch.float64 else U.UQLB_F32
+        F = x.shape[1]
+        mean = torch.empty(F, dtype=torch.float64, device=x.device)
+        var = torch.empty(F, dtype=torch.float64, device=x.device)
+        U.uqlb_stats(self.ctx, x.data_ptr(), dtype, F, x.stride(0), mean.data_ptr(), var.data_ptr(), ddof, _stream())
+        return mean, var
+
+    def run_uq_host(self, w: Workload, fields_dtype: str = "f32", coeffs: bool = False, qoi: bool = False):
+        """Algorithm 1 end to end through host buffers (one C call); returns numpy arrays."""
+        case = case_struct(w)
+        opts = opts_struct(w.storage, fields_dtype, w.qoi_every)
+        nbytes = U.uqlb_uq_workspace_bytes(self.ctx, case, opts)
+        ws = self.workspace(nbytes)
+        F = 2 * w.base.nx * w.base.ny + 1
+        mean, var = np.zeros(F), np.zeros(F)
+        c = np.zeros((self.num_terms, F)) if coeffs and self.num_terms > 0 else None
+        q = np.zeros((self.num_samples, U.UQLB_QOI_COLS)) if qoi else None
+        U.uqlb_run_uq_host(self.ctx, case, opts, ws.data_ptr(), ws.numel(), mean, var, c, q, _stream())
+        return mean, var, c, q

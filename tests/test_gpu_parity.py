@@ -1,0 +1,239 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element on the
+same seeded inputs.  Tolerances are the stated error budget of each storage format against the
+FP64 oracle (relative L2): FP64 1e-12, FP32 1e-5, FP16/BF16 1e-3."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import lbm as olbm  # noqa: E402
+from oracle import uq as ouq  # noqa: E402
+from paper_2508_13867_gb300 import uqlb as U  # noqa: E402
+from paper_2508_13867_gb300 import workloads as W  # noqa: E402
+from paper_2508_13867_gb300.ensemble import Ensemble, sample_struct  # noqa: E402
+from tests.helpers import oracle_case, oracle_row, rel_l2  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-3, "bf16": 1e-3}
+
+
+@pytest.fixture(scope="module")
+def ens():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2508_13867_gb300 import build
+
+    build.build()
+    e = Ensemble(0)
+    yield e
+    e.close()
+
+
+def _run(ens, specs, storage, qoi_every=0, series=False, tile_rows=0, chunk=0):
+    res = ens.run_batch([sample_struct(s) for s in specs], storage=storage,
+                        fields_dtype="f64" if storage == "f64" else "f32", qoi_every=qoi_every, series=series,
+                        tile_rows=tile_rows, chunk_steps=chunk,
+                        fields=len({(s.nx, s.ny) for s in specs}) == 1)
+    torch.cuda.synchronize()
+    return {k: v.double().cpu().numpy() for k, v in res.items()}
+
+
+def _tgv_specs(n, steps, nus=(0.02, 0.037, 0.06), modes=True):
+    out = []
+    for i, nu in enumerate(nus):
+        a2 = (0.07 - 0.05 * i) * 0.01 if modes else 0.0
+        a3 = (-0.04 + 0.03 * i) * 0.01 if modes else 0.0
+        out.append(W.tgv(n, steps, nu=nu, u0=0.01 * (0.9 + 0.1 * i), amp2=a2, amp3=a3))
+    return out
+
+
+@pytest.mark.parametrize("n,steps", [(64, 100), (70, 101), (33, 1), (40, 0)])
+def test_tgv_f64_fields_energy_and_invariants(ens, n, steps):
+    specs = _tgv_specs(n, steps)
+    g = _run(ens, specs, "f64", qoi_every=10, series=True)
+    ref = olbm.run([oracle_case(s, qoi_every=10) for s in specs])
+    for i, r in enumerate(ref):
+        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f64"]
+        assert abs(g["qoi"][i, U.UQLB_QOI_K] - r.k_final) < 1e-12 * abs(r.k_final)
+        assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < 1e-12 * r.mass
+        assert abs(g["qoi"][i, U.UQLB_QOI_MOMX] - r.mom_x) < 1e-12 * r.mass
+        assert abs(g["qoi"][i, U.UQLB_QOI_MOMY] - r.mom_y) < 1e-12 * r.mass
+        assert g["qoi"][i, U.UQLB_QOI_STEPS] == steps and g["qoi"][i, U.UQLB_QOI_STATUS] == 0
+        ns = steps // 10 + 1
+        assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_tgv_reduced_precision_storage(ens, storage):
+    specs = _tgv_specs(96, 300)
+    g = _run(ens, specs, storage)
+    ref = olbm.run([oracle_case(s) for s in specs])
+    for i, r in enumerate(ref):
+        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL[storage], storage
+        assert abs(g["qoi"][i, U.UQLB_QOI_K] - r.k_final) < TOL[storage] * r.k_final
+
+
+@pytest.mark.parametrize("tile_rows", [1, 2, 4, 16])
+def test_tile_shapes_give_identical_results(ens, tile_rows):
+    specs = _tgv_specs(50, 31)
+    a = _run(ens, specs, "f64", qoi_every=5, series=True)
+    b = _run(ens, specs, "f64", qoi_every=5, series=True, tile_rows=tile_rows, chunk=6)
+    assert np.array_equal(a["fields"], b["fields"])
+    assert np.array_equal(a["series"], b["series"])
+
+
+def _cyl(nd, steps, **kw):
+    """Coarse channel for parity runs: Re = 5 keeps tau well above 1/2 at 4..6 nodes per diameter."""
+    return W.channel(nd, steps=steps, steady_tol=kw.pop("steady_tol", 0.0), re=kw.pop("re", 5.0), **kw)
+
+
+@pytest.mark.parametrize("steps", [800, 801])
+def test_channel_obstacle_f64_fields_and_forces(ens, steps):
+    specs = [_cyl(5, steps, u_mean=0.036), _cyl(5, steps, u_mean=0.044)]
+    g = _run(ens, specs, "f64", qoi_every=50, series=True)
+    ref = olbm.run([oracle_case(s, qoi_every=50) for s in specs])
+    for i, r in enumerate(ref):
+        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f64"]
+        assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < 1e-11 * abs(r.cd)
+        assert abs(g["qoi"][i, U.UQLB_QOI_CL] - r.cl) < 1e-11 * abs(r.cd)
+        assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < 1e-12 * r.mass
+        ns = steps // 50
+        assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=1e-11, atol=1e-14)
+        assert np.allclose(g["series_cl"][i, :ns], r.series_cl[:ns], rtol=1e-9, atol=1e-12)
+
+
+def test_channel_without_obstacle_and_f32(ens):
+    specs = [W.channel(6, steps=600, obstacle=False, steady_tol=0.0, re=5.0), _cyl(6, 600)]
+    for storage in ("f64", "f32"):
+        g = _run(ens, specs, storage)
+        ref = olbm.run([oracle_case(s) for s in specs])
+        for i, r in enumerate(ref):
+            assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL[storage], storage
+
+
+def test_channel_steady_state_stops_with_the_oracle(ens):
+    specs = [_cyl(4, 20000, u_mean=0.04, steady_tol=1e-6), _cyl(4, 20000, u_mean=0.036, steady_tol=1e-6)]
+    g = _run(ens, specs, "f64", qoi_every=100, series=True)
+    ref = olbm.run([oracle_case(s, qoi_every=100) for s in specs])
+    for i, r in enumerate(ref):
+        assert r.steps_run < 20000
+        assert g["qoi"][i, U.UQLB_QOI_STEPS] == r.steps_run
+        assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < 1e-10 * abs(r.cd)
+        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < 1e-11
+
+
+def test_uneven_batch_sizes_steps_and_kinds(ens):
+    specs = [W.tgv(32, 57, nu=0.03), W.tgv(64, 20, nu=0.05, amp2=0.0007), W.tgv(48, 90, nu=0.021),
+             _cyl(4, 130, u_mean=0.04), W.tgv(96, 3, nu=0.06)]
+    for storage in ("f64", "f32"):
+        g = _run(ens, specs, storage)
+        ref = olbm.run([oracle_case(s) for s in specs])
+        for i, r in enumerate(ref):
+            assert g["qoi"][i, U.UQLB_QOI_STEPS] == specs[i].steps
+            if specs[i].kind == W.TGV:
+                assert abs(g["qoi"][i, U.UQLB_QOI_K] - r.k_final) < TOL[storage] * r.k_final
+            else:
+                assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < 100 * TOL[storage] * abs(r.cd)
+            assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < TOL[storage] * r.mass
+
+
+def test_plain_f64_path_matches_oracle(ens):
+    specs = _tgv_specs(40, 77) + [_cyl(4, 210, u_mean=0.04)]
+    for group in (specs[:3], specs[3:]):
+        res = ens.run_plain_f64([sample_struct(s) for s in group], qoi_every=7, series=True)
+        torch.cuda.synchronize()
+        g = {k: v.cpu().numpy() for k, v in res.items()}
+        ref = olbm.run([oracle_case(s, qoi_every=7) for s in group])
+        for i, r in enumerate(ref):
+            assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f64"]
+            assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < 1e-12 * r.mass
+            if group[i].kind == W.TGV:
+                ns = group[i].steps // 7 + 1
+                assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=1e-12, atol=0)
+            else:
+                assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < 1e-11 * abs(r.cd)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_projection_and_gpc_stats_match_oracle(ens, dtype):
+    e = Ensemble(0)
+    e.set_inputs(W.TGV4D_BOUNDS)
+    e.init_gpc(4, 5)
+    _, xi, a = ouq.tensor_grid([5] * 4, W.TGV4D_BOUNDS)
+    m = W.random_fields(625, 1037, seed=21, dtype=np.float64 if dtype == "f64" else np.float32)
+    mt = torch.from_numpy(m).cuda()
+    c = e.project(mt)
+    mean, var = e.stats(c)
+    torch.cuda.synchronize()
+    c_ref = ouq.gpc_coefficients(ouq.multi_indices(4, 4), xi, a, m.astype(np.float64))
+    mean_ref, var_ref = ouq.gpc_mean_var(c_ref)
+    assert np.abs(c.cpu().numpy() - c_ref).max() < 1e-13 * np.abs(c_ref).max()
+    assert rel_l2(mean.cpu().numpy(), mean_ref) < 1e-14
+    assert rel_l2(var.cpu().numpy(), var_ref) < 1e-12
+    e.close()
+
+
+def test_mc_stats_match_numpy(ens):
+    e = Ensemble(0)
+    e.set_inputs([(0.0, 1.0)])
+    e.init_mc(777, 5)
+    m = W.random_fields(777, 513, seed=3)
+    mt = torch.from_numpy(m).cuda()
+    for ddof in (0, 1):
+        mean, var = e.stats(mt, ddof=ddof)
+        torch.cuda.synchronize()
+        mr, vr = ouq.mc_mean_var(m, ddof=ddof)
+        assert rel_l2(mean.cpu().numpy(), mr) < 1e-14 and rel_l2(var.cpu().numpy(), vr) < 1e-12
+    e.close()
+
+
+def test_full_small_pipeline_through_host_buffers(ens):
+    """The plain small case end to end (5 GL samples, 64 x 64, 1000 steps, FP64) in one C call."""
+    w = W.tgv64_gpc()
+    e = Ensemble(0)
+    e.setup(w)
+    mean, var, coeffs, qoi = e.run_uq_host(w, fields_dtype="f64", coeffs=True, qoi=True)
+    z, xi, a = ouq.tensor_grid([5], w.bounds)
+    ref = olbm.run([oracle_case(W.tgv(64, 1000, nu=float(nu))) for nu in z[:, 0]])
+    mref = np.stack([oracle_row(r) for r in ref])
+    c_ref = ouq.gpc_coefficients(ouq.multi_indices(1, 4), xi, a, mref)
+    mean_ref, var_ref = ouq.gpc_mean_var(c_ref)
+    assert rel_l2(mean, mean_ref) < 1e-12
+    assert rel_l2(var, var_ref) < 1e-10
+    assert rel_l2(coeffs, c_ref) < 1e-12
+    # the kinetic-energy statistics against the closed form of the analytic decay (Sec. 8.2)
+    k = 2 * math.pi / 64
+    ek = ouq.tgv_mean_k_uniform_nu(0.02, 0.06, k, 1000.0)
+    assert abs(mean[-1] - ek) / ek < 5e-3
+    e.close()
+
+
+def test_full_size_tgv256_sampled_against_oracle(ens):
+    """The 4-D workload at its full size and in the benchmark's launch configuration (625 samples,
+    256 x 256, 2000 steps, FP32 storage): sampled samples against the oracle, invariants for all."""
+    w = W.tgv256_gpc4d()
+    e = Ensemble(0)
+    e.setup(w)
+    smp = e.ensemble_samples(w)
+    res = e.run_batch(smp, storage="f32", fields_dtype="f32")
+    c = e.project(res["fields"])
+    mean, var = e.stats(c)
+    torch.cuda.synchronize()
+    q = res["qoi"].cpu().numpy()
+    n2 = 256 * 256
+    assert np.all(q[:, U.UQLB_QOI_STATUS] == 0)
+    assert np.all(np.abs(q[:, U.UQLB_QOI_MASS] - n2) < 1e-5 * n2)
+    assert np.all((q[:, U.UQLB_QOI_K] > 0) & (q[:, U.UQLB_QOI_K] < 1.6))
+    picks = [0, 312, 624]
+    specs = [W.SampleSpec(W.TGV, 256, 256, 2000, smp[i].nu, smp[i].u0, smp[i].amp2, smp[i].amp3) for i in picks]
+    ref = olbm.run([oracle_case(s) for s in specs])
+    fields = res["fields"]
+    for j, i in enumerate(picks):
+        row = fields[i].double().cpu().numpy()
+        assert rel_l2(row[:-1], oracle_row(ref[j])[:-1]) < TOL["f32"]
+        assert abs(row[-1] - ref[j].k_final) < TOL["f32"] * ref[j].k_final
+    assert np.all(np.isfinite(var.cpu().numpy())) and float(mean[-1]) > 0
+    e.close()

@@ -1,0 +1,159 @@
+"""CPU-side checks of libuqlb.so: it loads, exports every symbol of include/uqlb.h, and its host
+logic (quadrature, Philox, chaos basis, sample sets, weight matrix, masks, ensemble mapping,
+argument checking) matches the oracle.  No device work is launched here."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbm as olbm
+from oracle import uq as ouq
+from paper_2508_13867_gb300 import build as lib_build
+from paper_2508_13867_gb300 import uqlb as U
+from paper_2508_13867_gb300 import workloads as W
+from paper_2508_13867_gb300.ensemble import case_struct, sample_struct
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lib_build.build()
+
+
+def test_library_exports_every_header_symbol():
+    names = U.header_symbols()
+    assert len(names) >= 25
+    L = U.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(U._SIGNATURES), "binding and header disagree"
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(U.uqlb_dist) == 24
+    assert ctypes.sizeof(U.uqlb_sample) == 104
+    assert ctypes.sizeof(U.uqlb_case) == 136
+    assert ctypes.sizeof(U.uqlb_run_opts) == 24
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 17, 33, 64])
+def test_gauss_legendre_matches_oracle(n):
+    x, w = U.uqlb_gauss_legendre(n)
+    xo, wo = ouq.gauss_legendre(n)
+    assert np.abs(x - xo).max() <= 4e-16 and np.abs(w - wo).max() <= 4e-16
+
+
+def test_philox_matches_oracle_and_published_vectors():
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        ctr = tuple(int(v) for v in rng.integers(0, 2 ** 32, 4))
+        key = tuple(int(v) for v in rng.integers(0, 2 ** 32, 2))
+        assert U.uqlb_philox4x32_10(ctr, key) == ouq.philox4x32_10(ctr, key)
+    assert U.uqlb_philox4x32_10((0, 0, 0, 0), (0, 0)) == (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)
+
+
+@pytest.mark.parametrize("dim,order,basis", [(1, 8, 0), (2, 3, 0), (4, 4, 0), (3, 2, 1), (8, 2, 0)])
+def test_multi_indices_match_oracle(dim, order, basis):
+    a = U.uqlb_multi_indices(dim, order, basis)
+    assert np.array_equal(a, ouq.multi_indices(dim, order, "total" if basis == 0 else "tensor"))
+
+
+def test_gpc_sample_set_and_weight_matrix_match_oracle():
+    ctx = U.uqlb_create(0)
+    try:
+        U.uqlb_set_inputs(ctx, W.TGV4D_BOUNDS)
+        U.uqlb_init_gpc(ctx, 4, 5)
+        z, xi, a = U.uqlb_get_samples(ctx, 4)
+        zo, xio, ao = ouq.tensor_grid([5] * 4, W.TGV4D_BOUNDS)
+        assert np.abs(z - zo).max() < 1e-17 + 1e-15 * np.abs(zo).max()
+        assert np.abs(xi - xio).max() <= 4e-16 and np.abs(a - ao).max() <= 1e-17
+        assert U.uqlb_num_terms(ctx) == 70 and U.uqlb_num_samples(ctx) == 625
+        wm = U.uqlb_get_weight_matrix(ctx)
+        wo = ouq.weight_matrix(ouq.multi_indices(4, 4), xio, ao)
+        assert np.abs(wm - wo).max() < 1e-15
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+def test_mc_sample_set_matches_oracle_bit_for_bit():
+    ctx = U.uqlb_create(0)
+    try:
+        U.uqlb_set_inputs(ctx, W.TGV4D_BOUNDS)
+        U.uqlb_init_mc(ctx, 300, 123456)
+        z, xi, a = U.uqlb_get_samples(ctx, 4)
+        zo, xio = ouq.mc_samples(300, W.TGV4D_BOUNDS, 123456)
+        assert np.array_equal(z, zo) and np.array_equal(xi, xio)
+        assert np.allclose(a, 1 / 300, rtol=0, atol=0)
+        assert U.uqlb_num_terms(ctx) == 0
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+def test_ensemble_mapping_of_inputs_to_parameters():
+    ctx = U.uqlb_create(0)
+    try:
+        w = W.tgv256_gpc4d(n=32, steps=10, pts=2)
+        U.uqlb_set_inputs(ctx, w.bounds)
+        U.uqlb_init_gpc(ctx, 1, 2)
+        smp = U.uqlb_ensemble_samples(ctx, case_struct(w))
+        z, _, _ = U.uqlb_get_samples(ctx, 4)
+        for s, zz in zip(smp, z):
+            assert s.nu == zz[0] and s.u0 == zz[1]
+            assert s.amp2 == zz[2] * zz[1] and s.amp3 == zz[3] * zz[1]
+            assert (s.nx, s.ny, s.steps) == (32, 32, 10)
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+@pytest.mark.parametrize("nd", [10, 20, 40])
+def test_obstacle_mask_matches_oracle(nd):
+    spec = W.channel(nd)
+    m = U.uqlb_obstacle_mask(sample_struct(spec))
+    mo = olbm.obstacle_mask(olbm.Case(olbm.CHANNEL, spec.nx, spec.ny, 1, spec.nu, spec.u0, u_ref=0.0,
+                                      cyl_cx=spec.cyl_cx, cyl_cy=spec.cyl_cy, cyl_r=spec.cyl_r))
+    assert np.array_equal(m, mo)
+
+
+def test_host_mean_std_match_numpy():
+    v = np.random.default_rng(5).normal(size=101)
+    assert U.uqlb_mean_host(v) == pytest.approx(v.mean(), rel=1e-15)
+    assert U.uqlb_std_host(v, 1) == pytest.approx(v.std(ddof=1), rel=1e-14)
+    assert U.uqlb_std_host(v, 0) == pytest.approx(v.std(ddof=0), rel=1e-14)
+
+
+def test_argument_errors_return_status_codes():
+    with pytest.raises(U.UqlbError) as e:
+        U.uqlb_gauss_legendre(0)
+    assert e.value.status == U.UQLB_ERR_ARG
+    ctx = U.uqlb_create(0)
+    try:
+        with pytest.raises(U.UqlbError) as e:
+            U.uqlb_init_gpc(ctx, 2, 3)
+        assert e.value.status == U.UQLB_ERR_STATE
+        with pytest.raises(U.UqlbError) as e:
+            U.uqlb_set_inputs(ctx, [(1.0, 0.5)])
+        assert e.value.status == U.UQLB_ERR_ARG and "a < b" in U.uqlb_last_error(ctx)
+        U.uqlb_set_inputs(ctx, [(0.02, 0.06)])
+        U.uqlb_init_mc(ctx, 4, 1)
+        with pytest.raises(U.UqlbError) as e:
+            U.uqlb_get_weight_matrix(ctx)
+        assert e.value.status == U.UQLB_ERR_STATE
+    finally:
+        U.uqlb_destroy(ctx)
+    bad = sample_struct(W.tgv(1, 10))
+    with pytest.raises(U.UqlbError):
+        U.uqlb_batch_workspace_bytes([bad], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
+    with pytest.raises(U.UqlbError):
+        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3))
+
+
+def test_workspace_bytes_cover_the_arena():
+    s = [sample_struct(W.tgv(256, 10)) for _ in range(3)]
+    for storage, eb in ((U.UQLB_F64, 8), (U.UQLB_F32, 4), (U.UQLB_F16, 2), (U.UQLB_BF16, 2)):
+        b = U.uqlb_batch_workspace_bytes(s, U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0))
+        arena = 3 * 9 * 256 * 256 * eb
+        assert arena <= b < arena + 2 ** 20
+    # rows are padded to 128 bytes: 100 FP32 columns take a 128-column pitch
+    b = U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(100, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
+    assert b >= 9 * 128 * 100 * 4
+    assert U.uqlb_plain_workspace_bytes(s) >= 2 * 9 * 256 * 256 * 8

@@ -130,8 +130,14 @@ def test_symmetric_obstacle_gives_mirror_flow_and_no_lift():
 
 @pytest.mark.slow
 def test_cylinder_drag_loose_anchor():
-    """Nominal drag at 20 nodes per diameter within 10% of the paper's deterministic value
-    (Sec. 8.1, table of C_D statistics; different boundary schemes, so a loose anchor)."""
-    c = _cyl(20, 60000, qoi_every=100, steady_tol=1e-7, ramp=2000)
+    """Steady nominal drag at 10 nodes per diameter within 10% of the paper's deterministic
+    value at n_x = 20 (Sec. 8.1, table of C_D statistics).  The paper uses Bouzidi and
+    interpolated inlet/outlet conditions, so this is a loose anchor, not a pin."""
+    rows = [r.split("|") for r in open(__file__.replace("test_oracle_lbm.py", "golden/cylinder_table1.txt"))
+            if r.strip() and not r.startswith("#")]
+    cd_paper = float([r for r in rows if r[0].strip() == "deterministic"][0][1])
+    c = _cyl(10, 40000, qoi_every=100, steady_tol=1e-7, ramp=1000)
     r = lbm.run([c])[0]
-    assert abs(r.cd - 5.63208) / 5.63208 < 0.10, r.cd
+    assert r.steps_run < 40000                       # reached the steady-state criterion
+    assert abs(r.cd - cd_paper) / cd_paper < 0.10, r.cd
+    assert abs(r.cl) < 0.05 * r.cd                   # small lift from the 0.2 vs 0.205 offset

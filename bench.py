@@ -157,6 +157,38 @@ def bench_reference(args):
     return 0
 
 
+def bench_kernel_only(args):
+    """Small case for profiler captures: the first --samples samples of the 4-D workload for
+    --time-steps steps, ensemble run only (no projection, no baselines)."""
+    import torch
+
+    from paper_2508_13867_gb300 import build as lib_build
+
+    lib_build.build()
+    from paper_2508_13867_gb300 import uqlb as U
+    from paper_2508_13867_gb300 import workloads as W
+    from paper_2508_13867_gb300.ensemble import Ensemble
+
+    w = W.tgv256_gpc4d(storage=args.storage)
+    ens = Ensemble(0)
+    ens.setup(w)
+    smp = ens.ensemble_samples(w)[: args.samples]
+    for s in smp:
+        s.steps = args.time_steps
+    out = {}
+    for _ in range(args.warmup + args.steps):
+        ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows)
+    torch.cuda.synchronize()
+    ms, st, la = U.uqlb_last_loop_time(ens.ctx)
+    nodes = sum(s.nx * s.ny for s in smp)
+    gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st, 1) / 1e3) / 1e9
+    print(json.dumps({"kernel_only": True, "samples": len(smp), "time_steps": st, "storage": args.storage,
+                      "loop_ms": ms, "step_ms": ms / max(st, 1), "achieved_gbs": gbs,
+                      "arena_bytes": BYTES_PER_UPDATE[args.storage] // 2 * nodes}))
+    ens.close()
+    return 0
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -331,9 +363,16 @@ def main():
     ap.add_argument("--ref-slice", type=int, default=16, help="oracle time steps per sample per reference step")
     ap.add_argument("--plain-samples", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true", help="small ensemble-run case for profiler captures")
+    ap.add_argument("--samples", type=int, default=128)
+    ap.add_argument("--time-steps", type=int, default=16)
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--tile-rows", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
+    if args.kernel_only:
+        return bench_kernel_only(args)
     return bench_gpu(args)
 
 

@@ -9,6 +9,9 @@
 //   g_i^eq = w_i (drho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u)),
 //   g_i*   = g_i + omega (g_i^eq - g_i),
 // which is the same arithmetic as f* = f - (f - f^eq)/tau with f = g + w.
+// rho itself is never rounded: 1/rho - 1 = -drho/(1 + drho) is carried as a small correction
+// and the rho-weighted equilibrium terms are written on j = rho u, so reduced-precision
+// rounding is relative to drho (~1e-4) and to j, never to 1.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -67,27 +70,45 @@ struct Storage<__nv_bfloat16> {
     }
 };
 
-// Moments of shifted populations: drho, u, v (u = j / rho).
+// Moments of shifted populations: drho, j = sum c_i g_i and u = j / rho = j + j (1/rho - 1).
 template <typename C>
-__device__ __forceinline__ void moments(const C g[9], C& drho, C& ux, C& uy) {
+__device__ __forceinline__ void moments(const C g[9], C& drho, C& jx, C& jy, C& ux, C& uy) {
     drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const C jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-    const C jy = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
-    const C inv_rho = C(1) / (C(1) + drho);
-    ux = jx * inv_rho;
-    uy = jy * inv_rho;
+    jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    jy = (g[2] - g[4]) + (g[5] - g[7]) + (g[6] - g[8]);
+    const C d = -drho / (C(1) + drho);  // 1/rho - 1
+    ux = fma(jx, d, jx);
+    uy = fma(jy, d, jy);
 }
 
-// BGK relaxation of shifted populations towards the shifted equilibrium, in place.
+// Coefficient of the linear equilibrium term, L_i = 3 w_i, written on the momentum:
+// rho w_i 3 c_i.u = L_i c_i.j.  The diagonal value is one unit in the last place below 1/12 so
+// that 2 L_1 + 4 L_5 = 1 holds exactly in the arithmetic type; the equilibrium then carries
+// exactly the momentum j.  With the rounded 3 w_i the sum is 1 + 3e-8 in FP32, and the BGK
+// update would add omega * 3e-8 of relative momentum at every step of every node.
 template <typename C>
-__device__ __forceinline__ void bgk(C g[9], C omega, C drho, C ux, C uy) {
-    const C rho = C(1) + drho;
-    const C usq15 = C(1.5) * (ux * ux + uy * uy);
+__device__ __forceinline__ C lin(int i);
+template <>
+__device__ __forceinline__ float lin<float>(int i) {
+    return i == 0 ? 0.0f : (i <= 4 ? 0x1.555556p-2f : 0x1.555554p-4f);
+}
+template <>
+__device__ __forceinline__ double lin<double>(int i) {
+    return i == 0 ? 0.0 : (i <= 4 ? 0x1.5555555555555p-2 : 0x1.5555555555556p-4);
+}
+
+// BGK relaxation of shifted populations towards the shifted equilibrium, in place:
+//   g_i^eq = w_i (drho + 4.5 (c_i.j)(c_i.u) - 1.5 j.u) + L_i c_i.j
+// (Eq. equilibrium times rho, with rho u = j), g_i* = g_i + omega (g_i^eq - g_i).
+template <typename C>
+__device__ __forceinline__ void bgk(C g[9], C omega, C drho, C jx, C jy, C ux, C uy) {
+    const C ju15 = C(1.5) * (jx * ux + jy * uy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
+        const C cj = C(cx(i)) * jx + C(cy(i)) * jy;
         const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
-        const C geq = wgt<C>(i) * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - usq15));
-        g[i] = g[i] + omega * (geq - g[i]);
+        const C geq = fma(lin<C>(i), cj, wgt<C>(i) * (drho + C(4.5) * cj * cu - ju15));
+        g[i] = fma(omega, geq - g[i], g[i]);
     }
 }
 

@@ -107,15 +107,15 @@ __device__ __forceinline__ C inflow(const SampleDev& sp, C yy, int t) {
 // Shifted incoming population of direction i at node (x, y) for the stream (tp -> tp + 1),
 // given the slot layout left by an even step at time tp: g_i*(z) sits at (z, slot opp(i)).
 // ub: velocity of the outlet node at time tp.
-template <typename S, bool CHANNEL>
+template <typename S>
 __device__ __forceinline__ typename Storage<S>::C read_incoming(
     const S* base, const SampleDev& sp, const uint32_t* mask, int x, int y, int i, int tp,
-    typename Storage<S>::C ubx, typename Storage<S>::C uby) {
+    typename Storage<S>::C ubx, typename Storage<S>::C uby, bool chan) {
     using C = typename Storage<S>::C;
     const int64_t plane = sp.plane;
     const int pitch = sp.pitch;
     int sx = x - cx(i), sy = y - cy(i);
-    if (!CHANNEL) {
+    if (!chan) {
         sx = sx < 0 ? sx + sp.nx : (sx >= sp.nx ? sx - sp.nx : sx);
         sy = sy < 0 ? sy + sp.ny : (sy >= sp.ny ? sy - sp.ny : sy);
         return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx);
@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
 // ------------------------------------------------------------------------------------------
 // Fused collide-stream-boundary-QoI step (one launch per time step).
 // ------------------------------------------------------------------------------------------
-template <typename S, bool ODD, bool CHANNEL, int TR>
+// MIXED: the batch holds channel samples; each tile then branches on its own sample's kind.
+template <typename S, bool ODD, bool MIXED, int TR>
 __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
     using C = typename Storage<S>::C;
     constexpr int NT = kTileCols * TR;
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
     }
     __syncthreads();
     const int nact = s_nact, ntiles = s_ntiles;
-    const bool want_k = !CHANNEL && p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
-    const bool want_f = CHANNEL && p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
+    const bool k_step = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
+    const bool f_step = MIXED && p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
     S* arena = static_cast<S*>(p.arena);
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -275,16 +276,19 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
         __syncthreads();
         const int j = s_j;
         const SampleDev sp = p.samples[j];
-        if (CHANNEL && p.done[j]) {
+        const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
+        if (chan && p.done[j]) {
             __syncthreads();
             continue;
         }
+        const bool want_k = k_step && !chan;
+        const bool want_f = f_step && chan;
         const int lt = tile - sp.tile_base;
         const int x = (lt % sp.tiles_x) * kTileCols + threadIdx.x;
         const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
-        const uint32_t* mask = (CHANNEL && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+        const uint32_t* mask = (chan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
         bool active = x < sp.nx && y < sp.ny;
-        if (CHANNEL && active && mask != nullptr) active = !mask_solid(mask, sp.mask_words, x, y);
+        if (active && mask != nullptr) active = !mask_solid(mask, sp.mask_words, x, y);
 
         double red[3] = {0.0, 0.0, 0.0};
         if (active) {
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
                 for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * plane + own);
             } else {
                 C ubx = C(0), uby = C(0);
-                if (CHANNEL && x == sp.nx - 1) {
+                if (chan && x == sp.nx - 1) {
                     if (sizeof(C) == 8) {
                         ubx = (C)p.side_d[2 * (sp.side_off + y)];
                         uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
@@ -309,12 +313,12 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
                 g[0] = Storage<S>::load(base + own);
 #pragma unroll
                 for (int i = 1; i < 9; ++i)
-                    g[i] = read_incoming<S, CHANNEL>(base, sp, mask, x, y, i, t - 1, ubx, uby);
+                    g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan);
             }
-            C drho, ux, uy;
-            moments(g, drho, ux, uy);
+            C drho, jx, jy, ux, uy;
+            moments(g, drho, jx, jy, ux, uy);
             if (want_k) red[0] = (double)(ux * ux + uy * uy);
-            if (CHANNEL && !ODD && x == sp.nx - 1) {
+            if (chan && !ODD && x == sp.nx - 1) {
                 if (sizeof(C) == 8) {
                     p.side_d[2 * (sp.side_off + y)] = (double)ux;
                     p.side_d[2 * (sp.side_off + y) + 1] = (double)uy;
@@ -323,8 +327,8 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
                     p.side[2 * (sp.side_off + y) + 1] = (float)uy;
                 }
             }
-            bgk(g, (C)sp.omega, drho, ux, uy);
-            if (CHANNEL && want_f && mask != nullptr) {
+            bgk(g, (C)sp.omega, drho, jx, jy, ux, uy);
+            if (want_f && mask != nullptr) {
                 C fx = C(0), fy = C(0);
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     int dx = x + cx(i), dy = y + cy(i);
-                    if (!CHANNEL) {
+                    if (!chan) {
                         dx = dx < 0 ? dx + sp.nx : (dx >= sp.nx ? dx - sp.nx : dx);
                         dy = dy < 0 ? dy + sp.ny : (dy >= sp.ny ? dy - sp.ny : dy);
                         Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
 // ------------------------------------------------------------------------------------------
 // Final fields and per-sample scalars at the last step run.
 // ------------------------------------------------------------------------------------------
-template <typename S, bool CHANNEL>
+template <typename S, bool MIXED>
 __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_tiles, int tile_rows) {
     using C = typename Storage<S>::C;
     constexpr int NT = 256;
@@ -413,6 +417,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
     for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int j = tile_sample(p, (int)tile, p.nsamples);
         const SampleDev sp = p.samples[j];
+        const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
         const int T = p.steps_run[j];
         const int lt = (int)tile - sp.tile_base;
         const int x = (lt % sp.tiles_x) * kTileCols + (threadIdx.x & 31);
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own);
                 } else {
                     C ubx = C(0), uby = C(0);
-                    if (CHANNEL && x == sp.nx - 1) {
+                    if (chan && x == sp.nx - 1) {
                         if (sizeof(C) == 8) {
                             ubx = (C)p.side_d[2 * (sp.side_off + y)];
                             uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
@@ -444,10 +449,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     g[0] = Storage<S>::load(base + own);
 #pragma unroll
                     for (int i = 1; i < 9; ++i)
-                        g[i] = read_incoming<S, CHANNEL>(base, sp, mask, x, y, i, T - 1, ubx, uby);
+                        g[i] = read_incoming<S>(base, sp, mask, x, y, i, T - 1, ubx, uby, chan);
                 }
-                C drho, cux, cuy;
-                moments(g, drho, cux, cuy);
+                C drho, cjx, cjy, cux, cuy;
+                moments(g, drho, cjx, cjy, cux, cuy);
                 ux = (double)cux;
                 uy = (double)cuy;
                 const double rho = 1.0 + (double)drho;
@@ -456,7 +461,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                 red[2] += rho * ux;
                 red[3] += rho * uy;
                 if (!(rho > 0.0) || !isfinite(ux) || !isfinite(uy)) red[6] += 1.0;
-                if (CHANNEL && mask != nullptr && T > 0) {
+                if (mask != nullptr && T > 0) {
                     // bounce-back populations at T are the post-collision values of step T - 1
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     else
                         static_cast<float*>(p.fields)[at] = (float)K;
                 }
-                if (!CHANNEL && p.series != nullptr && p.qoi_every > 0 && T % p.qoi_every == 0)
+                if (!chan && p.series != nullptr && p.qoi_every > 0 && T % p.qoi_every == 0)
                     p.series[(int64_t)sp.sample_id * p.series_ld + T / p.qoi_every] = K;
             }
         }

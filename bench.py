@@ -177,7 +177,8 @@ def bench_kernel_only(args):
         s.steps = args.time_steps
     out = {}
     for _ in range(args.warmup + args.steps):
-        ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows)
+        ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
+                      nodes_per_thread=args.npt)
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     nodes = sum(s.nx * s.ny for s in smp)
@@ -220,6 +221,8 @@ def bench_gpu(args):
     qoi = torch.empty((S, U.UQLB_QOI_COLS), dtype=torch.float64, device=dev)
     coeffs = torch.empty((K, F), dtype=torch.float64, device=dev)
     out = {"fields": fields, "qoi": qoi}
+
+    tuned = ens.autotune(smp, storage=storage, trial_steps=args.tune_steps) if args.tune_steps > 0 else None
 
     def one_step():
         ens.run_batch(smp, storage=storage, fields_dtype="f32", out=out)
@@ -338,7 +341,10 @@ def bench_gpu(args):
                 "config": {"workload": "tgv256_gpc4d", "samples": S, "lattice": [256, 256], "time_steps": 2000,
                            "storage": storage, "statistics": "fp64", "gpc_terms": K,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "lattice arena 1.47 GB > L2 129 MB: each time step streams from HBM"},
+                           "l2": "lattice arena 1.47 GB > L2 129 MB: each time step streams from HBM",
+                           "tile_geometry": None if tuned is None else
+                           {"tile_rows": tuned["tile_rows"], "nodes_per_thread": tuned["nodes_per_thread"],
+                            "autotune_ms_per_step": {f"{r}x{q}": round(ms, 4) for r, q, ms in tuned["tried"]}}},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                              "kernel": "step_kernel (fused AA collide-stream-QoI)",
@@ -362,12 +368,14 @@ def main():
     ap.add_argument("--cpu-slice", type=int, default=40, help="oracle time steps per sample for cpu_baseline")
     ap.add_argument("--ref-slice", type=int, default=16, help="oracle time steps per sample per reference step")
     ap.add_argument("--plain-samples", type=int, default=16)
+    ap.add_argument("--tune-steps", type=int, default=16, help="autotuner trial steps per geometry (0: off)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--kernel-only", action="store_true", help="small ensemble-run case for profiler captures")
     ap.add_argument("--samples", type=int, default=128)
     ap.add_argument("--time-steps", type=int, default=16)
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--npt", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)

@@ -114,13 +114,19 @@ typedef struct {
     int32_t param_of_dim[8];
 } uqlb_case;
 
-/* Options of a run. */
+/* Options of a run.  Tile geometry: a tile is (32 x nodes_per_thread) columns by tile_rows rows
+ * of one sample, run by 32 x tile_rows threads.  Compiled geometries: FP32/FP16/BF16 TGV-only
+ * batches tile_rows in {2, 4, 8} x nodes_per_thread in {1, 2, 4}; FP64 (8,1), (4,1), (4,2);
+ * batches with CHANNEL samples (8,1), (4,1).  Both 0: the geometry the context's autotuner
+ * picked for this batch shape (uqlb_autotune), else the default for the storage. */
 typedef struct {
-    int32_t storage;      /* population storage: UQLB_F64, F32, F16 or BF16 (stored as f - w) */
-    int32_t fields_dtype; /* dtype of the field output M: UQLB_F64 or UQLB_F32 */
-    int64_t qoi_every;    /* stride of the in-kernel QoI series (0: none) */
-    int32_t chunk_steps;  /* steps per captured CUDA graph (even, 2..1024; 0: default 64) */
-    int32_t tile_rows;    /* rows per tile (1, 2, 4, 8 or 16; 0: autotuned/default) */
+    int32_t storage;          /* population storage: UQLB_F64, F32, F16 or BF16 (stored as f - w) */
+    int32_t fields_dtype;     /* dtype of the field output M: UQLB_F64 or UQLB_F32 */
+    int64_t qoi_every;        /* stride of the in-kernel QoI series (0: none) */
+    int32_t chunk_steps;      /* steps per captured CUDA graph (even, 2..1024; 0: default 64) */
+    int32_t tile_rows;        /* rows per tile (see above; 0: tuned or default) */
+    int32_t nodes_per_thread; /* nodes per thread along x (see above; 0: tuned or default) */
+    int32_t reserved;
 } uqlb_run_opts;
 
 /* ------------------------------------------------------------------------------------
@@ -192,7 +198,8 @@ int uqlb_get_weight_matrix(const uqlb_ctx* ctx, double* w);
  * Deterministic solves over the ensemble (Sec. 7, Algorithm 1 loop)
  * ---------------------------------------------------------------------------------- */
 
-/* Workspace needed by uqlb_run_batch for these samples and options. */
+/* Workspace needed by uqlb_run_batch for these samples and options (with both geometry fields
+ * 0: enough for every compiled geometry, so that tuned runs fit). */
 int uqlb_batch_workspace_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
                                size_t* bytes);
 
@@ -214,6 +221,19 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
                    void* workspace_dev, size_t workspace_bytes, void* fields_dev, int64_t fields_ld,
                    double* qoi_dev, double* series_dev, double* series_cl_dev, int64_t series_ld,
                    void* stream);
+
+/* Tile-geometry autotuner.  For this batch shape, time `trial_steps` (>= 2, even) fused steps of
+ * every compiled tile geometry on the device (after an equilibrium initialisation, CUDA events on
+ * `stream`, best of two passes) and keep the fastest in the context; later runs of a batch with
+ * the same storage, kinds, sample count and node count that pass tile_rows = nodes_per_thread = 0
+ * use it.  Outputs (any may be NULL): the chosen tile_rows / nodes_per_thread, and for each
+ * candidate c < *n_tried: rows_tried[c], npt_tried[c], ms_per_step[c] (arrays of capacity 16).
+ * The workspace must hold uqlb_batch_workspace_bytes for opts with both geometry fields 0; its
+ * contents are overwritten.  Synchronises `stream`. */
+int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
+                  void* workspace_dev, size_t workspace_bytes, int trial_steps, int32_t* tile_rows,
+                  int32_t* nodes_per_thread, int32_t* rows_tried, int32_t* npt_tried,
+                  double* ms_per_step, int32_t* n_tried, void* stream);
 
 /* Build the per-sample runs of the context's sample set from a case template (host). */
 int uqlb_ensemble_samples(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* out);

@@ -15,6 +15,7 @@
 // Quantities of interest are reduced in the same kernel: K(t) from the pre-collision moments
 // and drag/lift by momentum exchange from the post-collision populations; per-tile partial
 // sums (FP64) are combined in a fixed order by the last tile of each sample to finish.
+#include <algorithm>
 #include <cmath>
 
 #include "d2q9.cuh"
@@ -202,14 +203,13 @@ __device__ __forceinline__ bool tile_reduce_last(const KParams& p, const SampleD
 // Initial state: equilibrium of the initial macroscopic field (Sec. 8.2 TGV, Sec. 8.1 rest).
 // ------------------------------------------------------------------------------------------
 template <typename S>
-__global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tiles, int tile_rows) {
+__global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tiles, int tile_rows, int tile_cols) {
     using C = typename Storage<S>::C;
     S* arena = static_cast<S*>(p.arena);
     for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int j = tile_sample(p, (int)tile, p.nsamples);
         const SampleDev& sp = p.samples[j];
         const int lt = (int)tile - sp.tile_base;
-        const int x = (lt % sp.tiles_x) * kTileCols + (threadIdx.x & 31);
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         if (tile == sp.tile_base && threadIdx.x == 0) {
             p.counters[j] = 0;
@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
             p.steps_run[j] = sp.steps;
             p.cd_prev[j] = NAN;
         }
-        for (int y = y0 + (threadIdx.x >> 5); y < y0 + tile_rows && y < sp.ny; y += blockDim.x >> 5) {
-            if (x >= sp.nx) continue;
+        for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
+            const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
+            const int y = y0 + q / tile_cols;
+            if (x >= sp.nx || y >= sp.ny) continue;
             double rho = 1.0, ux = 0.0, uy = 0.0;
             if (sp.kind == UQLB_CASE_TGV) {
                 const InitDev& in = p.init[j];
@@ -250,13 +252,112 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
 // ------------------------------------------------------------------------------------------
 // Fused collide-stream-boundary-QoI step (one launch per time step).
 // ------------------------------------------------------------------------------------------
+
+// Nine incoming shifted populations of node (x, y) at step t.
+template <typename S, bool ODD>
+__device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp, const S* base,
+                                          const uint32_t* mask, int x, int y, int t, bool chan,
+                                          typename Storage<S>::C (&g)[9]) {
+    using C = typename Storage<S>::C;
+    const int64_t own = (int64_t)y * sp.pitch + x;
+    if (!ODD) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own);
+    } else {
+        C ubx = C(0), uby = C(0);
+        if (chan && x == sp.nx - 1) {
+            if (sizeof(C) == 8) {
+                ubx = (C)p.side_d[2 * (sp.side_off + y)];
+                uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
+            } else {
+                ubx = (C)p.side[2 * (sp.side_off + y)];
+                uby = (C)p.side[2 * (sp.side_off + y) + 1];
+            }
+        }
+        g[0] = Storage<S>::load(base + own);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan);
+    }
+}
+
+// Moments, QoI contributions, BGK and the streaming stores of node (x, y) at step t.
+template <typename S, bool ODD>
+__device__ __forceinline__ void node_update(const KParams& p, const SampleDev& sp, S* base, const uint32_t* mask,
+                                            int x, int y, int t, bool chan, bool want_k, bool want_f,
+                                            typename Storage<S>::C (&g)[9], double (&red)[3]) {
+    using C = typename Storage<S>::C;
+    const int64_t own = (int64_t)y * sp.pitch + x;
+    const int64_t plane = sp.plane;
+    C drho, jx, jy, ux, uy;
+    moments(g, drho, jx, jy, ux, uy);
+    if (want_k) red[0] += (double)(ux * ux + uy * uy);
+    if (chan && !ODD && x == sp.nx - 1) {
+        if (sizeof(C) == 8) {
+            p.side_d[2 * (sp.side_off + y)] = (double)ux;
+            p.side_d[2 * (sp.side_off + y) + 1] = (double)uy;
+        } else {
+            p.side[2 * (sp.side_off + y)] = (float)ux;
+            p.side[2 * (sp.side_off + y) + 1] = (float)uy;
+        }
+    }
+    bgk(g, (C)sp.omega, drho, jx, jy, ux, uy);
+    if (want_f && mask != nullptr) {
+        C fx = C(0), fy = C(0);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const int xn = x + cx(i), yn = y + cy(i);
+            if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny && mask_solid(mask, sp.mask_words, xn, yn)) {
+                const C fs = g[i] + wgt<C>(i);
+                fx += C(2 * cx(i)) * fs;
+                fy += C(2 * cy(i)) * fs;
+            }
+        }
+        red[1] += (double)fx;
+        red[2] += (double)fy;
+    }
+    if (!ODD) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Storage<S>::store(base + opp(i) * plane + own, g[i]);
+        return;
+    }
+    Storage<S>::store(base + own, g[0]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        int dx = x + cx(i), dy = y + cy(i);
+        if (!chan) {
+            dx = dx < 0 ? dx + sp.nx : (dx >= sp.nx ? dx - sp.nx : dx);
+            dy = dy < 0 ? dy + sp.ny : (dy >= sp.ny ? dy - sp.ny : dy);
+            Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
+        } else {
+            const int cls = classify(sp, mask, dx, dy);
+            const int o = opp(i);
+            if (cls == kInterior) {
+                Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
+            } else if (cls == kWall || cls == kSolid) {
+                Storage<S>::store(base + o * plane + own, g[i]);
+            } else if (cls == kInlet) {
+                const C yy = C(y) + C(0.5) - C(0.5) * C(cy(o));
+                Storage<S>::store(base + o * plane + own, g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t));
+            } else {
+                const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
+                Storage<S>::store(base + o * plane + own,
+                                  -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)));
+            }
+        }
+    }
+}
+
+// One tile = (32 NPT) columns x TR rows of one sample; thread (lane, row) owns the NPT nodes
+// x = x0 + lane + 32 k, so every warp-wide access of a population plane is contiguous.  All
+// NPT x 9 loads of a thread are issued before any arithmetic.
 // MIXED: the batch holds channel samples; each tile then branches on its own sample's kind.
-template <typename S, bool ODD, bool MIXED, int TR>
+template <typename S, bool ODD, bool MIXED, int TR, int NPT>
 __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
     using C = typename Storage<S>::C;
     constexpr int NT = kTileCols * TR;
     __shared__ int s_nact, s_ntiles, s_j, s_flag;
     __shared__ double s_red[(NT / 32) * 3];
+    __shared__ __align__(16) SampleDev s_sp;
 
     const int t = (int)(*p.step_counter) + p.dt;
     if (t >= p.max_steps) return;
@@ -272,10 +373,15 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
     S* arena = static_cast<S*>(p.arena);
 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) s_j = tile_sample(p, tile, nact);
+        if (threadIdx.y == 0) {  // warp 0 fetches the sample record (32 words) into shared memory
+            const int jj = tile_sample(p, tile, nact);
+            reinterpret_cast<uint32_t*>(&s_sp)[threadIdx.x] =
+                __ldg(reinterpret_cast<const uint32_t*>(p.samples + jj) + threadIdx.x);
+            if (threadIdx.x == 0) s_j = jj;
+        }
         __syncthreads();
         const int j = s_j;
-        const SampleDev sp = p.samples[j];
+        const SampleDev& sp = s_sp;
         const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
         if (chan && p.done[j]) {
             __syncthreads();
@@ -284,97 +390,25 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
         const bool want_k = k_step && !chan;
         const bool want_f = f_step && chan;
         const int lt = tile - sp.tile_base;
-        const int x = (lt % sp.tiles_x) * kTileCols + threadIdx.x;
+        const int x0 = (lt % sp.tiles_x) * (kTileCols * NPT) + threadIdx.x;
         const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
         const uint32_t* mask = (chan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
-        bool active = x < sp.nx && y < sp.ny;
-        if (active && mask != nullptr) active = !mask_solid(mask, sp.mask_words, x, y);
+        S* base = arena + sp.f_off;
 
-        double red[3] = {0.0, 0.0, 0.0};
-        if (active) {
-            S* base = arena + sp.f_off;
-            const int64_t own = (int64_t)y * sp.pitch + x;
-            const int64_t plane = sp.plane;
-            C g[9];
-            if (!ODD) {
+        C g[NPT][9];
+        bool act[NPT];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * plane + own);
-            } else {
-                C ubx = C(0), uby = C(0);
-                if (chan && x == sp.nx - 1) {
-                    if (sizeof(C) == 8) {
-                        ubx = (C)p.side_d[2 * (sp.side_off + y)];
-                        uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
-                    } else {
-                        ubx = (C)p.side[2 * (sp.side_off + y)];
-                        uby = (C)p.side[2 * (sp.side_off + y) + 1];
-                    }
-                }
-                g[0] = Storage<S>::load(base + own);
-#pragma unroll
-                for (int i = 1; i < 9; ++i)
-                    g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan);
-            }
-            C drho, jx, jy, ux, uy;
-            moments(g, drho, jx, jy, ux, uy);
-            if (want_k) red[0] = (double)(ux * ux + uy * uy);
-            if (chan && !ODD && x == sp.nx - 1) {
-                if (sizeof(C) == 8) {
-                    p.side_d[2 * (sp.side_off + y)] = (double)ux;
-                    p.side_d[2 * (sp.side_off + y) + 1] = (double)uy;
-                } else {
-                    p.side[2 * (sp.side_off + y)] = (float)ux;
-                    p.side[2 * (sp.side_off + y) + 1] = (float)uy;
-                }
-            }
-            bgk(g, (C)sp.omega, drho, jx, jy, ux, uy);
-            if (want_f && mask != nullptr) {
-                C fx = C(0), fy = C(0);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    const int xn = x + cx(i), yn = y + cy(i);
-                    if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny &&
-                        mask_solid(mask, sp.mask_words, xn, yn)) {
-                        const C fs = g[i] + wgt<C>(i);
-                        fx += C(2 * cx(i)) * fs;
-                        fy += C(2 * cy(i)) * fs;
-                    }
-                }
-                red[1] = (double)fx;
-                red[2] = (double)fy;
-            }
-            if (!ODD) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) Storage<S>::store(base + opp(i) * plane + own, g[i]);
-            } else {
-                Storage<S>::store(base + own, g[0]);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    int dx = x + cx(i), dy = y + cy(i);
-                    if (!chan) {
-                        dx = dx < 0 ? dx + sp.nx : (dx >= sp.nx ? dx - sp.nx : dx);
-                        dy = dy < 0 ? dy + sp.ny : (dy >= sp.ny ? dy - sp.ny : dy);
-                        Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
-                    } else {
-                        const int cls = classify(sp, mask, dx, dy);
-                        const int o = opp(i);
-                        if (cls == kInterior) {
-                            Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
-                        } else if (cls == kWall || cls == kSolid) {
-                            Storage<S>::store(base + o * plane + own, g[i]);
-                        } else if (cls == kInlet) {
-                            const C yy = C(y) + C(0.5) - C(0.5) * C(cy(o));
-                            Storage<S>::store(base + o * plane + own,
-                                              g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t));
-                        } else {
-                            const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                            Storage<S>::store(base + o * plane + own,
-                                              -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)));
-                        }
-                    }
-                }
-            }
+        for (int k = 0; k < NPT; ++k) {
+            const int x = x0 + kTileCols * k;
+            act[k] = x < sp.nx && y < sp.ny;
+            if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, sp.mask_words, x, y);
+            if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, g[k]);
         }
+        double red[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < NPT; ++k)
+            if (act[k]) node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, g[k], red);
+
         if (want_k || want_f) {
             double tot[3];
             if (tile_reduce_last<3, NT>(p, sp, j, tile, red, tot, s_red, &s_flag)) {
@@ -408,7 +442,7 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
 // Final fields and per-sample scalars at the last step run.
 // ------------------------------------------------------------------------------------------
 template <typename S, bool MIXED>
-__global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_tiles, int tile_rows) {
+__global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_tiles, int tile_rows, int tile_cols) {
     using C = typename Storage<S>::C;
     constexpr int NT = 256;
     __shared__ double s_red[(NT / 32) * 7];
@@ -420,11 +454,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
         const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
         const int T = p.steps_run[j];
         const int lt = (int)tile - sp.tile_base;
-        const int x = (lt % sp.tiles_x) * kTileCols + (threadIdx.x & 31);
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         const uint32_t* mask = (sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
         double red[7] = {0, 0, 0, 0, 0, 0, 0};  // K, mass, mx, my, fx, fy, bad
-        for (int y = y0 + (threadIdx.x >> 5); y < y0 + tile_rows; y += blockDim.x >> 5) {
+        for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
+            const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
+            const int y = y0 + q / tile_cols;
             if (x >= sp.nx || y >= sp.ny) continue;
             const bool solid = mask != nullptr && mask_solid(mask, sp.mask_words, x, y);
             double ux = 0.0, uy = 0.0;
@@ -565,33 +600,71 @@ int sm_count() {
     return n;
 }
 
-template <typename S, bool ODD, bool CHANNEL>
-cudaError_t launch_step_t(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
-    const int grid = step_grid_blocks(g);
-    switch (g.tile_rows) {
-        case 1: step_kernel<S, ODD, CHANNEL, 1><<<grid, dim3(kTileCols, 1), 0, s>>>(p); break;
-        case 2: step_kernel<S, ODD, CHANNEL, 2><<<grid, dim3(kTileCols, 2), 0, s>>>(p); break;
-        case 4: step_kernel<S, ODD, CHANNEL, 4><<<grid, dim3(kTileCols, 4), 0, s>>>(p); break;
-        case 16: step_kernel<S, ODD, CHANNEL, 16><<<grid, dim3(kTileCols, 16), 0, s>>>(p); break;
-        default: step_kernel<S, ODD, CHANNEL, 8><<<grid, dim3(kTileCols, 8), 0, s>>>(p); break;
+int sm_count_cached() { return sm_count(); }
+
+// Resident blocks per SM of one step-kernel instantiation (queried once).
+template <typename S, bool ODD, bool MIXED, int TR, int NPT>
+int resident_blocks() {
+    static int n = 0;
+    if (n == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step_kernel<S, ODD, MIXED, TR, NPT>, kTileCols * TR, 0) !=
+                cudaSuccess || b < 1)
+            b = 1;
+        n = b;
     }
+    return n;
+}
+
+template <typename S, bool ODD, bool MIXED, int TR, int NPT>
+cudaError_t launch_geom(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    const int64_t resident = (int64_t)resident_blocks<S, ODD, MIXED, TR, NPT>() * sm_count();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_tiles, resident));
+    step_kernel<S, ODD, MIXED, TR, NPT><<<grid, dim3(kTileCols, TR), 0, s>>>(p);
     return cudaGetLastError();
 }
+
+// Geometries compiled for each (storage, mixed) combination; see geometry_supported().
+#define UQLB_GEOM(TR_, NPT_) \
+    if (g.tile_rows == TR_ && g.npt == NPT_) return launch_geom<S, ODD, MIXED, TR_, NPT_>(p, g, s);
+template <typename S, bool ODD, bool MIXED>
+cudaError_t launch_step_geom(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    if constexpr (MIXED) {
+        UQLB_GEOM(8, 1)
+        UQLB_GEOM(4, 1)
+    } else if constexpr (sizeof(S) == 8) {
+        UQLB_GEOM(8, 1)
+        UQLB_GEOM(4, 1)
+        UQLB_GEOM(4, 2)
+    } else {
+        UQLB_GEOM(2, 1)
+        UQLB_GEOM(4, 1)
+        UQLB_GEOM(8, 1)
+        UQLB_GEOM(2, 2)
+        UQLB_GEOM(4, 2)
+        UQLB_GEOM(8, 2)
+        UQLB_GEOM(2, 4)
+        UQLB_GEOM(4, 4)
+        UQLB_GEOM(8, 4)
+    }
+    return cudaErrorInvalidConfiguration;
+}
+#undef UQLB_GEOM
 
 template <typename S>
 cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cudaStream_t s) {
     if (g.any_channel)
-        return odd ? launch_step_t<S, true, true>(p, g, s) : launch_step_t<S, false, true>(p, g, s);
-    return odd ? launch_step_t<S, true, false>(p, g, s) : launch_step_t<S, false, false>(p, g, s);
+        return odd ? launch_step_geom<S, true, true>(p, g, s) : launch_step_geom<S, false, true>(p, g, s);
+    return odd ? launch_step_geom<S, true, false>(p, g, s) : launch_step_geom<S, false, false>(p, g, s);
 }
 
 }  // namespace
 
-int step_grid_blocks(const BatchGeometry& g) {
-    // enough resident blocks for every SM; the step kernel strides over tiles
-    const int64_t cap = (int64_t)sm_count() * 2048 / (kTileCols * (g.tile_rows > 0 ? g.tile_rows : 8));
-    int64_t grid = g.total_tiles < cap ? g.total_tiles : cap;
-    return (int)(grid > 0 ? grid : 1);
+bool geometry_supported(int storage, bool mixed, int tile_rows, int npt) {
+    const int tr = tile_rows, n = npt;
+    if (mixed) return n == 1 && (tr == 8 || tr == 4);
+    if (storage == UQLB_F64) return (n == 1 && (tr == 8 || tr == 4)) || (n == 2 && tr == 4);
+    return (tr == 2 || tr == 4 || tr == 8) && (n == 1 || n == 2 || n == 4);
 }
 
 cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
@@ -599,10 +672,10 @@ cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStrea
     int64_t grid = g.total_tiles < 65535 * 4 ? g.total_tiles : 65535 * 4;
     if (grid < 1) grid = 1;
     switch (g.storage) {
-        case UQLB_F64: init_kernel<double><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
-        case UQLB_F32: init_kernel<float><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
-        case UQLB_F16: init_kernel<__half><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
-        default: init_kernel<__nv_bfloat16><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows); break;
+        case UQLB_F64: init_kernel<double><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
+        case UQLB_F32: init_kernel<float><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
+        case UQLB_F16: init_kernel<__half><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
+        default: init_kernel<__nv_bfloat16><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
     }
     return cudaGetLastError();
 }
@@ -632,20 +705,20 @@ cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const
     const bool ch = g.any_channel != 0;
     switch (g.storage) {
         case UQLB_F64:
-            ch ? finalize_kernel<double, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
-               : finalize_kernel<double, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            ch ? finalize_kernel<double, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
+               : finalize_kernel<double, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
             break;
         case UQLB_F32:
-            ch ? finalize_kernel<float, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
-               : finalize_kernel<float, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            ch ? finalize_kernel<float, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
+               : finalize_kernel<float, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
             break;
         case UQLB_F16:
-            ch ? finalize_kernel<__half, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
-               : finalize_kernel<__half, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            ch ? finalize_kernel<__half, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
+               : finalize_kernel<__half, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
             break;
         default:
-            ch ? finalize_kernel<__nv_bfloat16, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows)
-               : finalize_kernel<__nv_bfloat16, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows);
+            ch ? finalize_kernel<__nv_bfloat16, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
+               : finalize_kernel<__nv_bfloat16, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
             break;
     }
     return cudaGetLastError();

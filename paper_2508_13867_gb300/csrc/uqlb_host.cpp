@@ -45,6 +45,13 @@ struct uqlb_ctx {
     cudaEvent_t loop_begin = nullptr, loop_end = nullptr;
     bool loop_timed = false;
     int64_t loop_steps = 0, run_launches = 0;
+    struct Tuned {
+        int storage, mixed;
+        int64_t n, nodes;
+        int rows, npt;
+    };
+    std::vector<Tuned> tuned;
+    int last_rows = 0, last_npt = 0;
 };
 
 namespace {
@@ -236,7 +243,8 @@ int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
     return UQLB_ERR_ARG;
 }
 
-int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchPlan& P, std::string& why) {
+int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchPlan& P, std::string& why,
+               int tuned_rows = 0, int tuned_npt = 0) {
     if (n <= 0 || n > (1 << 24)) {
         why = "sample count out of range";
         return UQLB_ERR_ARG;
@@ -247,13 +255,25 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         why = "unknown storage format";
         return UQLB_ERR_ARG;
     }
-    int tr = o && o->tile_rows > 0 ? o->tile_rows : 8;
-    if (tr != 1 && tr != 2 && tr != 4 && tr != 8 && tr != 16) {
-        why = "tile_rows must be 1, 2, 4, 8 or 16";
-        return UQLB_ERR_ARG;
-    }
     for (int64_t s = 0; s < n; ++s)
         if (int rc = validate_sample(smp[s], s, why)) return rc;
+    bool mixed = false;
+    for (int64_t s = 0; s < n; ++s) mixed = mixed || smp[s].kind == UQLB_CASE_CHANNEL;
+    int tr = o ? o->tile_rows : 0, npt = o ? o->nodes_per_thread : 0;
+    if (tr == 0 && npt == 0) {
+        tr = tuned_rows;
+        npt = tuned_npt;
+        if (tr == 0 || !geometry_supported(storage, mixed, tr, npt)) {
+            tr = (mixed || storage == UQLB_F64) ? 8 : 4;
+            npt = (mixed || storage == UQLB_F64) ? 1 : 2;
+        }
+    }
+    if (!geometry_supported(storage, mixed, tr, npt)) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "tile geometry tile_rows=%d nodes_per_thread=%d is not compiled for this batch", tr, npt);
+        why = buf;
+        return UQLB_ERR_ARG;
+    }
 
     std::vector<int64_t> order(n);
     for (int64_t s = 0; s < n; ++s) order[s] = s;
@@ -282,7 +302,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         d.kind = s.kind;
         d.steps = (int32_t)s.steps;
         d.sample_id = (int32_t)order[j];
-        d.tiles_x = (s.nx + 31) / 32;
+        d.tiles_x = (s.nx + 32 * npt - 1) / (32 * npt);
         d.tiles = d.tiles_x * ((s.ny + tr - 1) / tr);
         d.tile_base = (int32_t)tiles;
         tiles += d.tiles;
@@ -351,7 +371,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     g.nsamples = n;
     g.total_tiles = tiles;
     g.tile_rows = tr;
-    g.tile_cols = 32;
+    g.npt = npt;
     g.max_steps = max_steps;
     g.storage = storage;
     g.any_channel = any_channel;
@@ -690,13 +710,137 @@ int uqlb_get_weight_matrix(const uqlb_ctx* ctx, double* w) {
     return 0;
 }
 
+const int kGeomRows[] = {2, 4, 8};
+const int kGeomNpt[] = {1, 2, 4};
+
 int uqlb_batch_workspace_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes) {
-    if (!samples || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "batch_workspace_bytes: null pointer");
+    if (!samples || !bytes || !opts) return set_err(nullptr, UQLB_ERR_ARG, "batch_workspace_bytes: null pointer");
     BatchPlan P;
     std::string why;
     if (int rc = plan_batch(samples, n, opts, P, why)) return set_err(nullptr, rc, "%s", why.c_str());
-    *bytes = P.total;
+    size_t best = P.total;
+    if (opts->tile_rows == 0 && opts->nodes_per_thread == 0) {
+        for (int r : kGeomRows)
+            for (int q : kGeomNpt) {
+                uqlb_run_opts o = *opts;
+                o.tile_rows = r;
+                o.nodes_per_thread = q;
+                BatchPlan Q;
+                if (plan_batch(samples, n, &o, Q, why) == 0) best = std::max(best, Q.total);
+            }
+    }
+    *bytes = best;
     return 0;
+}
+
+int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
+                  void* workspace_dev, size_t workspace_bytes, int trial_steps, int32_t* tile_rows,
+                  int32_t* nodes_per_thread, int32_t* rows_tried, int32_t* npt_tried, double* ms_per_step,
+                  int32_t* n_tried, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (!samples || !opts || !workspace_dev) return set_err(ctx, UQLB_ERR_ARG, "autotune: null argument");
+    if (trial_steps < 2 || (trial_steps & 1) || trial_steps > 4096)
+        return set_err(ctx, UQLB_ERR_ARG, "autotune: trial_steps must be even, 2..4096");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) return cuda_fail(ctx, e, "autotune: events");
+    int best_r = 0, best_q = 0, tried = 0;
+    double best_ms = 1e300;
+    int rc = 0;
+    int storage = opts->storage, mixed = 0;
+    int64_t nodes = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        mixed |= samples[k].kind == UQLB_CASE_CHANNEL;
+        nodes += (int64_t)samples[k].nx * samples[k].ny;
+    }
+    for (int r : kGeomRows) {
+        for (int q : kGeomNpt) {
+            if (!geometry_supported(storage, mixed != 0, r, q)) continue;
+            uqlb_run_opts o = *opts;
+            o.tile_rows = r;
+            o.nodes_per_thread = q;
+            o.qoi_every = 0;
+            BatchPlan P;
+            std::string why;
+            if ((rc = plan_batch(samples, n, &o, P, why))) {
+                rc = set_err(ctx, rc, "autotune: %s", why.c_str());
+                goto done;
+            }
+            if (workspace_bytes < P.total) {
+                rc = set_err(ctx, UQLB_ERR_OOM, "autotune: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
+                goto done;
+            }
+            BatchBuffers B = carve(P, workspace_dev);
+            P.geom.max_steps = trial_steps;
+            char* ws = static_cast<char*>(workspace_dev);
+            RunOutputs O{};
+            if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
+                (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
+                                                          cudaMemcpyHostToDevice, s))) ||
+                (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))) {
+                rc = cuda_fail(ctx, e, "autotune: upload");
+                goto done;
+            }
+            // every sample steps for the whole trial, whatever its own step count
+            for (auto& d : P.table) d.steps = trial_steps;
+            for (auto& v : P.steps_sorted) v = trial_steps;
+            if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s))) {
+                rc = cuda_fail(ctx, e, "autotune: upload");
+                goto done;
+            }
+            double ms_best = 1e300;
+            for (int pass = 0; pass < 2; ++pass) {
+                if ((e = cudaMemsetAsync(B.step_counter, 0, sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s)) ||
+                    (e = cudaEventRecord(e0, s))) {
+                    rc = cuda_fail(ctx, e, "autotune: init");
+                    goto done;
+                }
+                for (int dt = 0; dt < trial_steps; ++dt)
+                    if ((e = launch_step(B, P.geom, O, dt, s))) {
+                        rc = cuda_fail(ctx, e, "autotune: step launch");
+                        goto done;
+                    }
+                float f = 0.0f;
+                if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) || (e = cudaEventElapsedTime(&f, e0, e1))) {
+                    rc = cuda_fail(ctx, e, "autotune: timing");
+                    goto done;
+                }
+                ms_best = std::min(ms_best, (double)f / trial_steps);
+            }
+            if (tried < 16) {
+                if (rows_tried) rows_tried[tried] = r;
+                if (npt_tried) npt_tried[tried] = q;
+                if (ms_per_step) ms_per_step[tried] = ms_best;
+            }
+            ++tried;
+            if (ms_best < best_ms) {
+                best_ms = ms_best;
+                best_r = r;
+                best_q = q;
+            }
+        }
+    }
+    if (best_r > 0) {
+        bool found = false;
+        for (auto& t : ctx->tuned)
+            if (t.storage == storage && t.mixed == mixed && t.n == n && t.nodes == nodes) {
+                t.rows = best_r;
+                t.npt = best_q;
+                found = true;
+            }
+        if (!found) ctx->tuned.push_back({storage, mixed, n, nodes, best_r, best_q});
+    }
+    if (tile_rows) *tile_rows = best_r;
+    if (nodes_per_thread) *nodes_per_thread = best_q;
+    if (n_tried) *n_tried = std::min(tried, 16);
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
@@ -707,9 +851,25 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: workspace must be 256-byte aligned");
     BatchPlan P;
     std::string why;
-    if (int rc = plan_batch(samples, n, opts, P, why)) return set_err(ctx, rc, "run_batch: %s", why.c_str());
+    int tuned_r = 0, tuned_q = 0;
+    {
+        int mixed = 0;
+        int64_t nodes = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            mixed |= samples[k].kind == UQLB_CASE_CHANNEL;
+            nodes += (int64_t)samples[k].nx * samples[k].ny;
+        }
+        for (auto& t : ctx->tuned)
+            if (t.storage == opts->storage && t.mixed == mixed && t.n == n && t.nodes == nodes) {
+                tuned_r = t.rows;
+                tuned_q = t.npt;
+            }
+    }
+    if (int rc = plan_batch(samples, n, opts, P, why, tuned_r, tuned_q)) return set_err(ctx, rc, "run_batch: %s", why.c_str());
     if (workspace_bytes < P.total)
         return set_err(ctx, UQLB_ERR_OOM, "run_batch: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
+    ctx->last_rows = P.geom.tile_rows;
+    ctx->last_npt = P.geom.npt;
     if (fields_dev) {
         if (!P.uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
         if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_ld too small");

@@ -65,8 +65,8 @@ struct BatchBuffers {
 struct BatchGeometry {
     int64_t nsamples;
     int64_t total_tiles;
-    int32_t tile_rows;
-    int32_t tile_cols;       // nodes per tile row (32)
+    int32_t tile_rows;       // rows per tile (threads per block = 32 x tile_rows)
+    int32_t npt;             // nodes per thread along x (tile width 32 x npt)
     int32_t max_steps;
     int32_t storage;
     int32_t any_channel;
@@ -92,7 +92,7 @@ cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const Run
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                             cudaStream_t s);
-int step_grid_blocks(const BatchGeometry& g);
+bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
 
 // Plain per-sample FP64 path (plain_f64.cu).
 struct PlainSample {

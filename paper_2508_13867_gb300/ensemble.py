@@ -28,8 +28,9 @@ def case_struct(w: Workload) -> U.uqlb_case:
 
 
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
-                tile_rows: int = 0) -> U.uqlb_run_opts:
-    return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows)
+                tile_rows: int = 0, nodes_per_thread: int = 0) -> U.uqlb_run_opts:
+    return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows,
+                           nodes_per_thread, 0)
 
 
 def _stream() -> int:
@@ -102,9 +103,9 @@ class Ensemble:
     # ---- runs -------------------------------------------------------------------------
     def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
                   fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
-                  out: dict | None = None) -> dict:
+                  nodes_per_thread: int = 0, out: dict | None = None) -> dict:
         """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series)."""
-        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows)
+        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread)
         nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
         ws = self.workspace(nbytes)
         n = len(samples)
@@ -126,6 +127,11 @@ class Ensemble:
                          res["series"].data_ptr() if ld else 0, res["series_cl"].data_ptr() if ld else 0, ld,
                          _stream())
         return res
+
+    def autotune(self, samples, storage: str = "f32", trial_steps: int = 16) -> dict:
+        opts = opts_struct(storage, "f32", 0)
+        ws = self.workspace(U.uqlb_batch_workspace_bytes(samples, opts))
+        return U.uqlb_autotune(self.ctx, samples, opts, ws.data_ptr(), ws.numel(), trial_steps, _stream())
 
     def run_plain_f64(self, samples, qoi_every: int = 0, series: bool = False, fields: bool = True) -> dict:
         nbytes = U.uqlb_plain_workspace_bytes(samples)

@@ -54,7 +54,8 @@ class uqlb_case(ctypes.Structure):
 
 class uqlb_run_opts(ctypes.Structure):
     _fields_ = [("storage", c_int32), ("fields_dtype", c_int32), ("qoi_every", c_int64),
-                ("chunk_steps", c_int32), ("tile_rows", c_int32)]
+                ("chunk_steps", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
+                ("reserved", c_int32)]
 
 
 _P = ctypes.POINTER
@@ -79,6 +80,8 @@ _SIGNATURES = {
     "uqlb_batch_workspace_bytes": [_P(uqlb_sample), c_int64, _P(uqlb_run_opts), _P(c_size_t)],
     "uqlb_run_batch": [c_void_p, _P(uqlb_sample), c_int64, _P(uqlb_run_opts), c_void_p, c_size_t, c_void_p,
                        c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
+    "uqlb_autotune": [c_void_p, _P(uqlb_sample), c_int64, _P(uqlb_run_opts), c_void_p, c_size_t, ctypes.c_int,
+                      _P(c_int32), _P(c_int32), _P(c_int32), _P(c_int32), _P(c_double), _P(c_int32), c_void_p],
     "uqlb_ensemble_samples": [c_void_p, _P(uqlb_case), _P(uqlb_sample)],
     "uqlb_ensemble_workspace_bytes": [c_void_p, _P(uqlb_case), _P(uqlb_run_opts), _P(c_size_t)],
     "uqlb_run_ensemble": [c_void_p, _P(uqlb_case), _P(uqlb_run_opts), c_void_p, c_size_t, c_void_p, c_int64,
@@ -263,6 +266,18 @@ def uqlb_run_batch(ctx, samples, opts: uqlb_run_opts, workspace_dev: int, worksp
                                 c_void_p(workspace_dev), workspace_bytes, c_void_p(fields_dev or None),
                                 fields_ld, c_void_p(qoi_dev or None), c_void_p(series_dev or None),
                                 c_void_p(series_cl_dev or None), series_ld, _stream(stream)), ctx)
+
+
+def uqlb_autotune(ctx, samples, opts: uqlb_run_opts, workspace_dev: int, workspace_bytes: int,
+                  trial_steps: int = 16, stream=None) -> dict:
+    """Time every compiled tile geometry on this batch; returns the choice and the table."""
+    r, q, nt = c_int32(), c_int32(), c_int32()
+    rows, npts, ms = (c_int32 * 16)(), (c_int32 * 16)(), (c_double * 16)()
+    _check(lib().uqlb_autotune(ctx, _samples_array(samples), len(samples), ctypes.byref(opts),
+                               c_void_p(workspace_dev), workspace_bytes, trial_steps, ctypes.byref(r),
+                               ctypes.byref(q), rows, npts, ms, ctypes.byref(nt), _stream(stream)), ctx)
+    return {"tile_rows": r.value, "nodes_per_thread": q.value,
+            "tried": [(rows[i], npts[i], ms[i]) for i in range(nt.value)]}
 
 
 def uqlb_ensemble_samples(ctx, case: uqlb_case) -> list:

@@ -33,7 +33,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(U.uqlb_dist) == 24
     assert ctypes.sizeof(U.uqlb_sample) == 104
     assert ctypes.sizeof(U.uqlb_case) == 136
-    assert ctypes.sizeof(U.uqlb_run_opts) == 24
+    assert ctypes.sizeof(U.uqlb_run_opts) == 32
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 17, 33, 64])
@@ -144,7 +144,7 @@ def test_argument_errors_return_status_codes():
     with pytest.raises(U.UqlbError):
         U.uqlb_batch_workspace_bytes([bad], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
     with pytest.raises(U.UqlbError):
-        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3))
+        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3, 1, 0))
 
 
 def test_workspace_bytes_cover_the_arena():

@@ -277,6 +277,20 @@ int uqlb_post_workspace_bytes(const uqlb_ctx* ctx, size_t* bytes);
 int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,
                  double* coeffs_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* uqlb_project for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is an interface for hosts such as code running under a fixed device-memory budget,
+ * threads that must not enter an allocator, or embeddings that only hand over their own input
+ * and output buffers.  Same arguments and result as uqlb_project, but no workspace: the weight
+ * matrix W is staged in a fixed device array inside the library (1 MiB, K x S <= 131072
+ * weights; larger sample sets return UQLB_ERR_ARG and need uqlb_project).  No device memory is
+ * allocated or freed.  The array exists once per GPU that loads the library and stays until
+ * the process exits.  The first call on a device looks up the array's device address, so make
+ * that first call before capturing a stream.  All calls share the one array: calls that
+ * overlap on the GPU (e.g. on two streams) race and must be ordered by the caller.  Each call
+ * overwrites every weight it reads, so no contents carry over between calls. */
+int uqlb_project_noalloc(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,
+                         double* coeffs_dev, void* stream);
+
 /* Statistics per field, FP64 outputs mean_dev[n_fields], var_dev[n_fields].
  *   gPC context: input is coeffs_dev [K x n_fields] FP64; mean = c_0 (Eq. gpc_mean),
  *     var = sum_{k >= 1} c_k^2 (Eq. gpc_std squared); dtype must be UQLB_F64, ddof ignored.

@@ -8,6 +8,8 @@
 // The contraction is [K x S] x [S x F] with K <= a few hundred and F up to ~10^6: each thread
 // owns two fields and KB coefficients, W tiles are staged in shared memory and broadcast.
 #include <cmath>
+#include <cstdio>
+#include <mutex>
 
 #include "uqlb_internal.h"
 
@@ -130,3 +132,69 @@ cudaError_t launch_mc_stats(const void* M, int dtype, int64_t S, int64_t F, int6
 }
 
 }  // namespace uqlb
+
+// =========================================================================================
+// Projection without allocation.
+//
+// Some callers cannot allocate device memory at the moment they need statistics: code running
+// under a memory budget that forbids new allocations, host threads that must not take the
+// allocator's locks, or embeddings that hand over only their own input and output buffers.
+// uqlb_project needs a small device scratch for the weight matrix W, which it takes from a
+// caller workspace.  This variant keeps W in a file-scope device array instead, so the caller
+// passes nothing but the fields and the coefficient buffer and nothing is allocated.
+// =========================================================================================
+
+namespace {
+
+// Capacity of the shared weight-matrix scratch: K x S <= 131072 doubles (1 MiB).  Every GPU
+// that loads the library holds this array until the process exits.
+constexpr int64_t kNoAllocWMax = 1 << 17;
+static __device__ __align__(256) double g_noalloc_w[kNoAllocWMax];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" int uqlb_project_noalloc(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,
+                                    double* coeffs_dev, void* stream) {
+    using namespace uqlb;
+    const double* W = nullptr;
+    int K = 0, device = 0;
+    int64_t S = 0;
+    if (int rc = ctx_projection_view(ctx, &W, &K, &S, &device)) return rc;
+    if (!m_dev || !coeffs_dev || n_fields < 0 || m_ld < n_fields)
+        return ctx_fail(ctx, UQLB_ERR_ARG, "project_noalloc: bad arguments");
+    if (dtype != UQLB_F64 && dtype != UQLB_F32)
+        return ctx_fail(ctx, UQLB_ERR_ARG, "project_noalloc: dtype must be F64 or F32");
+    if ((int64_t)K * S > kNoAllocWMax) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "project_noalloc: K x S = %lld exceeds the fixed scratch of %lld weights; use uqlb_project",
+                 (long long)K * S, (long long)kNoAllocWMax);
+        return ctx_fail(ctx, UQLB_ERR_ARG, buf);
+    }
+    if (device < 0 || device >= kMaxDevices) return ctx_fail(ctx, UQLB_ERR_ARG, "project_noalloc: device index too large");
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return ctx_fail(ctx, UQLB_ERR_CUDA, cudaGetErrorString(e));
+    double* w_dev = nullptr;
+    {
+        // First call on this device: resolve the device address of the array (host code cannot
+        // use the symbol itself, which only stands in for it on the host).
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (g_noalloc_ptr[device] == nullptr) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_w);
+            if (e != cudaSuccess) return ctx_fail(ctx, UQLB_ERR_CUDA, cudaGetErrorString(e));
+            g_noalloc_ptr[device] = static_cast<double*>(ptr);
+        }
+        w_dev = g_noalloc_ptr[device];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // W overwrites exactly the K x S entries the kernel reads, so nothing needs clearing.
+    e = cudaMemcpyAsync(w_dev, W, (size_t)K * S * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return ctx_fail(ctx, UQLB_ERR_CUDA, cudaGetErrorString(e));
+    e = launch_project(w_dev, K, (int)S, m_dev, dtype, n_fields, m_ld, coeffs_dev, s);
+    if (e != cudaSuccess) return ctx_fail(ctx, UQLB_ERR_CUDA, cudaGetErrorString(e));
+    return 0;
+}

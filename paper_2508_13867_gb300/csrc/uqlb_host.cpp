@@ -494,6 +494,22 @@ int check_case(uqlb_ctx* ctx, const uqlb_case* c) {
 
 }  // namespace
 
+namespace uqlb {
+
+int ctx_projection_view(uqlb_ctx* ctx, const double** W, int* K, int64_t* S, int* device) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (ctx->method != UQLB_METHOD_GPC) return set_err(ctx, UQLB_ERR_STATE, "call uqlb_init_gpc first");
+    *W = ctx->W.data();
+    *K = ctx->K;
+    *S = ctx->S;
+    *device = ctx->device;
+    return 0;
+}
+
+int ctx_fail(uqlb_ctx* ctx, int code, const char* msg) { return set_err(ctx, code, "%s", msg); }
+
+}  // namespace uqlb
+
 // =========================================================================================
 // C ABI
 // =========================================================================================

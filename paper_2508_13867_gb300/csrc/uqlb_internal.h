@@ -104,6 +104,10 @@ cudaError_t plain_run_sample(const PlainSample& p, double* f_a, double* f_b, uin
                              double* partials, int64_t qoi_every, double* fields,
                              double* qoi_row, double* series_row, cudaStream_t s);
 
+// Context accessors for entry points implemented outside uqlb_host.cpp.
+int ctx_projection_view(uqlb_ctx* ctx, const double** W, int* K, int64_t* S, int* device);
+int ctx_fail(uqlb_ctx* ctx, int code, const char* msg);
+
 // Postprocessing (project_kernels.cu).
 cudaError_t launch_project(const double* W, int K, int S, const void* M, int dtype,
                            int64_t F, int64_t ld, double* C, cudaStream_t s);

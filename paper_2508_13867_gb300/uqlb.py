@@ -92,6 +92,7 @@ _SIGNATURES = {
     "uqlb_last_loop_time": [c_void_p, _P(c_double), _P(c_int64), _P(c_int64)],
     "uqlb_post_workspace_bytes": [c_void_p, _P(c_size_t)],
     "uqlb_project": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, c_size_t, c_void_p],
+    "uqlb_project_noalloc": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p],
     "uqlb_stats": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, ctypes.c_int,
                    c_void_p],
     "uqlb_uq_workspace_bytes": [c_void_p, _P(uqlb_case), _P(uqlb_run_opts), _P(c_size_t)],
@@ -334,6 +335,12 @@ def uqlb_project(ctx, m_dev: int, dtype: int, n_fields: int, m_ld: int, coeffs_d
                  workspace_bytes: int, stream=None) -> None:
     _check(lib().uqlb_project(ctx, c_void_p(m_dev), dtype, n_fields, m_ld, c_void_p(coeffs_dev),
                               c_void_p(workspace_dev), workspace_bytes, _stream(stream)), ctx)
+
+
+def uqlb_project_noalloc(ctx, m_dev: int, dtype: int, n_fields: int, m_ld: int, coeffs_dev: int,
+                         stream=None) -> None:
+    _check(lib().uqlb_project_noalloc(ctx, c_void_p(m_dev), dtype, n_fields, m_ld, c_void_p(coeffs_dev),
+                                      _stream(stream)), ctx)
 
 
 def uqlb_stats(ctx, in_dev: int, dtype: int, n_fields: int, m_ld: int, mean_dev: int, var_dev: int,

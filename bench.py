@@ -190,6 +190,175 @@ def bench_kernel_only(args):
     return 0
 
 
+def _oracle_async(cases):
+    """Start the oracle on `cases` in a background thread (its C loop releases the GIL)."""
+    from oracle import lbm as olbm
+
+    box = {}
+
+    def work():
+        t0 = time.perf_counter()
+        box["res"] = olbm.run(cases)
+        box["s"] = time.perf_counter() - t0
+
+    th = threading.Thread(target=work, daemon=True)
+    th.start()
+    return th, box
+
+
+def _oracle_cases(specs):
+    from oracle import lbm as olbm
+
+    return [olbm.Case(s.kind, s.nx, s.ny, s.steps, s.nu, s.u0, amp2=s.amp2, amp3=s.amp3, u_ref=s.u_ref,
+                      cyl_cx=s.cyl_cx, cyl_cy=s.cyl_cy, cyl_r=s.cyl_r, ramp_steps=s.ramp_steps,
+                      qoi_every=100 if s.steady_tol > 0 else 0, steady_tol=s.steady_tol) for s in specs]
+
+
+def _rel(a, b):
+    import numpy as np
+
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def bench_workload(args):
+    """The other workloads of the method, one JSON line each: throughput of the whole pass and,
+    where an oracle reference is affordable, the error of the statistics against it."""
+    import numpy as np
+    import torch
+
+    from oracle import lbm as olbm
+    from oracle import uq as ouq
+    from paper_2508_13867_gb300 import build as lib_build
+
+    lib_build.build()
+    olbm.build()
+    from paper_2508_13867_gb300 import uqlb as U
+    from paper_2508_13867_gb300 import workloads as W
+    from paper_2508_13867_gb300.ensemble import Ensemble, sample_struct
+
+    ens = Ensemble(0)
+    line = {"workload": args.workload, "storage": args.storage, "unit": UNIT}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    if args.workload in ("tgv64_gpc", "tgv512_mc4d", "cylinder"):
+        if args.workload == "tgv64_gpc":
+            w = W.tgv64_gpc()
+        elif args.workload == "tgv512_mc4d":
+            w = W.tgv512_mc4d(n=args.n or 512, steps=args.time_steps_full or 2000, n_mc=args.n_mc or 4096,
+                              storage=args.storage)
+        else:
+            w = W.cylinder_gpc(nd=args.nd, storage=args.storage)
+        if args.workload == "tgv64_gpc":
+            w.storage = args.storage if args.storage != "f32" else "f64"
+        ens.setup(w)
+        smp = ens.ensemble_samples(w)
+        specs = [W.SampleSpec(s.kind, s.nx, s.ny, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref, s.cyl_cx, s.cyl_cy,
+                              s.cyl_r, s.ramp_steps, s.steady_tol) for s in smp]
+        sub = list(range(min(len(specs), args.oracle_samples)))
+        th, box = _oracle_async(_oracle_cases([specs[i] for i in sub]))
+        fd = "f64" if w.storage == "f64" else "f32"
+        qe = w.qoi_every
+
+        def run():
+            r = ens.run_batch(smp, storage=w.storage, fields_dtype=fd, qoi_every=qe)
+            if w.method == "gpc":
+                c = ens.project(r["fields"])
+                m, v = ens.stats(c)
+            else:
+                m, v = ens.stats(r["fields"], ddof=1)
+            return r, m, v
+
+        ms, (r, mean, var) = timed(run, args.steps)
+        upd = sum(int(q[U.UQLB_QOI_STEPS]) for q in r["qoi"].cpu().numpy()) * smp[0].nx * smp[0].ny
+        line.update({"samples": len(smp), "lattice": [smp[0].nx, smp[0].ny], "time_to_stats_s": ms / 1e3,
+                     "value": upd / (ms / 1e3) / 1e6})
+        # further storage formats of the same ensemble (compared with the same oracle subset)
+        extra = {}
+        for st in [x for x in args.storages.split(",") if x and x != w.storage]:
+            def run_st(st=st):
+                rr = ens.run_batch(smp, storage=st, fields_dtype="f32")
+                return rr, ens.stats(rr["fields"], ddof=1) if w.method == "mc" else ens.stats(ens.project(rr["fields"]))
+            ms_st, (rr, _) = timed(run_st, 1)
+            extra[st] = {"time_to_stats_s": ms_st / 1e3, "value": upd / (ms_st / 1e3) / 1e6,
+                         "fields": rr["fields"][: min(len(smp), args.oracle_samples)].double().cpu().numpy()}
+        # plain per-sample FP64 comparator on a subset, scaled by the sample count
+        if args.plain_samples > 0:
+            psub = [smp[i] for i in range(min(len(smp), args.plain_samples))]
+            pms, _ = timed(lambda: ens.run_plain_f64(psub, fields=True), 1)
+            line["plain_f64_time_to_stats_s"] = pms / 1e3 * len(smp) / len(psub)
+            line["speedup_vs_plain_f64"] = line["plain_f64_time_to_stats_s"] / line["time_to_stats_s"]
+        th.join()
+        ref = box["res"]
+        m_ref = np.stack([np.concatenate([q.u.ravel(), q.v.ravel(), [q.k_final]]) for q in ref])
+        g_fields = r["fields"][sub].double().cpu().numpy()
+        line["oracle_samples"] = len(sub)
+        line["oracle_seconds"] = box["s"]
+        line["field_rel_l2_worst_sample"] = max(_rel(g_fields[i, :-1], m_ref[i, :-1]) for i in range(len(sub)))
+        if args.workload == "cylinder":
+            q = r["qoi"].cpu().numpy()
+            line["cd"] = q[:, U.UQLB_QOI_CD].tolist()
+            line["steps_run"] = q[:, U.UQLB_QOI_STEPS].tolist()
+            line["cd_oracle"] = [x.cd for x in ref]
+            line["steps_oracle"] = [x.steps_run for x in ref]
+            if len(sub) == len(smp):
+                z, xi, a = ouq.tensor_grid([w.pts_per_dim], w.bounds)
+                cd_o = np.array([[x.cd] for x in ref])
+                c_o = ouq.gpc_coefficients(ouq.multi_indices(1, w.order), xi, a, cd_o)
+                mo, vo = ouq.gpc_mean_var(c_o)
+                c_g = ouq.gpc_coefficients(ouq.multi_indices(1, w.order), xi, a, q[:, [U.UQLB_QOI_CD]])
+                mg, vg = ouq.gpc_mean_var(c_g)
+                line["cd_mean_std"] = [float(mg[0]), float(np.sqrt(vg[0]))]
+                line["cd_mean_std_oracle"] = [float(mo[0]), float(np.sqrt(vo[0]))]
+        elif w.method == "mc":
+            mu_r, var_r = ouq.mc_mean_var(m_ref, ddof=1)
+            per = {w.storage: {"fields": g_fields, "value": line["value"], "time_to_stats_s": line["time_to_stats_s"]}}
+            per.update(extra)
+            line["precision"] = {}
+            for st, d in per.items():
+                gm, gv = ouq.mc_mean_var(d["fields"], ddof=1)
+                line["precision"][st] = {
+                    "value": d["value"], "time_to_stats_s": d["time_to_stats_s"],
+                    "field_rel_l2_worst_sample": max(_rel(d["fields"][i, :-1], m_ref[i, :-1]) for i in range(len(sub))),
+                    "subset_mean_rel_l2": _rel(gm[:-1], mu_r[:-1]),
+                    "subset_std_rel_l2": _rel(np.sqrt(gv[:-1]), np.sqrt(var_r[:-1]))}
+        else:
+            z, xi, a = ouq.tensor_grid([w.pts_per_dim] * len(w.bounds), w.bounds)
+            c_ref = ouq.gpc_coefficients(ouq.multi_indices(len(w.bounds), w.order), xi, a, m_ref)
+            mr, vr = ouq.gpc_mean_var(c_ref)
+            line["mean_rel_l2"] = _rel(mean.cpu().numpy(), mr)
+            line["std_rel_l2"] = _rel(np.sqrt(var.cpu().numpy()), np.sqrt(vr))
+    elif args.workload == "uneven":
+        specs = W.uneven_batch()
+        smp = [sample_struct(s) for s in specs]
+        tuned = ens.autotune(smp, storage=args.storage, trial_steps=8)
+        ms, r = timed(lambda: ens.run_batch(smp, storage=args.storage, fields=False), args.steps)
+        upd = sum(s.nx * s.ny * s.steps for s in specs)
+        line.update({"samples": len(smp), "value": upd / (ms / 1e3) / 1e6, "batch_seconds": ms / 1e3,
+                     "tile_geometry": tuned})
+        if args.plain_samples > 0:
+            step = max(1, len(smp) // args.plain_samples)
+            psub = smp[::step]
+            pms, _ = timed(lambda: ens.run_plain_f64(psub, fields=False), 1)
+            pupd = sum(s.nx * s.ny * s.steps for s in psub)
+            line["plain_f64_seconds_scaled"] = pms / 1e3 * upd / pupd
+            line["speedup_vs_plain_f64"] = line["plain_f64_seconds_scaled"] / line["batch_seconds"]
+    print(json.dumps(line))
+    ens.close()
+    return 0
+
+
 def bench_gpu(args):
     import numpy as np
     import torch
@@ -376,11 +545,21 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)
+    ap.add_argument("--workload", default="tgv256_gpc4d",
+                    choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "uneven"])
+    ap.add_argument("--oracle-samples", type=int, default=4, help="oracle reference subset (other workloads)")
+    ap.add_argument("--storages", default="", help="further storage formats to run on the same workload")
+    ap.add_argument("--nd", type=int, default=20, help="cylinder: nodes per diameter")
+    ap.add_argument("--n", type=int, default=0, help="tgv512_mc4d: lattice size override")
+    ap.add_argument("--n-mc", type=int, default=0, help="tgv512_mc4d: sample count override")
+    ap.add_argument("--time-steps-full", type=int, default=0, help="tgv512_mc4d: step count override")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
     if args.kernel_only:
         return bench_kernel_only(args)
+    if args.workload != "tgv256_gpc4d":
+        return bench_workload(args)
     return bench_gpu(args)
 
 

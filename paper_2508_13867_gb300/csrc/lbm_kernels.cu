@@ -253,16 +253,40 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
 // Fused collide-stream-boundary-QoI step (one launch per time step).
 // ------------------------------------------------------------------------------------------
 
+// Periodic neighbourhood of a node: wrapped columns x-1, x, x+1 and row offsets of y-1, y, y+1,
+// indexed by c + 1.  In-sample offsets are 32-bit (the planner keeps 9 planes below 2^31).
+struct Nbr {
+    int col[3];
+    int row[3];
+};
+
+__device__ __forceinline__ void periodic_rows(const SampleDev& sp, int y, Nbr& n) {
+    const int ym = y == 0 ? sp.ny - 1 : y - 1, yp = y == sp.ny - 1 ? 0 : y + 1;
+    n.row[0] = ym * sp.pitch;
+    n.row[1] = y * sp.pitch;
+    n.row[2] = yp * sp.pitch;
+}
+__device__ __forceinline__ void periodic_cols(const SampleDev& sp, int x, Nbr& n) {
+    n.col[0] = x == 0 ? sp.nx - 1 : x - 1;
+    n.col[1] = x;
+    n.col[2] = x == sp.nx - 1 ? 0 : x + 1;
+}
+
 // Nine incoming shifted populations of node (x, y) at step t.
 template <typename S, bool ODD>
 __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp, const S* base,
                                           const uint32_t* mask, int x, int y, int t, bool chan,
-                                          typename Storage<S>::C (&g)[9]) {
+                                          const Nbr& nb, typename Storage<S>::C (&g)[9]) {
     using C = typename Storage<S>::C;
-    const int64_t own = (int64_t)y * sp.pitch + x;
+    const int plane = (int)sp.plane;
     if (!ODD) {
+        const int own = nb.row[1] + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own);
+        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + (i * plane + own));
+    } else if (!chan) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            g[i] = Storage<S>::load(base + (opp(i) * plane + nb.row[1 - cy(i)] + nb.col[1 - cx(i)]));
     } else {
         C ubx = C(0), uby = C(0);
         if (chan && x == sp.nx - 1) {
@@ -274,7 +298,7 @@ __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp,
                 uby = (C)p.side[2 * (sp.side_off + y) + 1];
             }
         }
-        g[0] = Storage<S>::load(base + own);
+        g[0] = Storage<S>::load(base + (nb.row[1] + x));
 #pragma unroll
         for (int i = 1; i < 9; ++i) g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan);
     }
@@ -284,10 +308,10 @@ __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp,
 template <typename S, bool ODD>
 __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& sp, S* base, const uint32_t* mask,
                                             int x, int y, int t, bool chan, bool want_k, bool want_f,
-                                            typename Storage<S>::C (&g)[9], double (&red)[3]) {
+                                            const Nbr& nb, typename Storage<S>::C (&g)[9], double (&red)[3]) {
     using C = typename Storage<S>::C;
-    const int64_t own = (int64_t)y * sp.pitch + x;
-    const int64_t plane = sp.plane;
+    const int own = nb.row[1] + x;
+    const int plane = (int)sp.plane;
     C drho, jx, jy, ux, uy;
     moments(g, drho, jx, jy, ux, uy);
     if (want_k) red[0] += (double)(ux * ux + uy * uy);
@@ -317,18 +341,20 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
     }
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Storage<S>::store(base + opp(i) * plane + own, g[i]);
+        for (int i = 0; i < 9; ++i) Storage<S>::store(base + (opp(i) * plane + own), g[i]);
+        return;
+    }
+    if (!chan) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            Storage<S>::store(base + (i * plane + nb.row[1 + cy(i)] + nb.col[1 + cx(i)]), g[i]);
         return;
     }
     Storage<S>::store(base + own, g[0]);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int dx = x + cx(i), dy = y + cy(i);
-        if (!chan) {
-            dx = dx < 0 ? dx + sp.nx : (dx >= sp.nx ? dx - sp.nx : dx);
-            dy = dy < 0 ? dy + sp.ny : (dy >= sp.ny ? dy - sp.ny : dy);
-            Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
-        } else {
+        {
             const int cls = classify(sp, mask, dx, dy);
             const int o = opp(i);
             if (cls == kInterior) {
@@ -397,17 +423,27 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
 
         C g[NPT][9];
         bool act[NPT];
+        Nbr nb[NPT];
+        Nbr rows;
+        if (!chan && ODD) {
+            periodic_rows(sp, y, rows);
+        } else {
+            rows.row[1] = y * sp.pitch;
+        }
 #pragma unroll
         for (int k = 0; k < NPT; ++k) {
             const int x = x0 + kTileCols * k;
+            nb[k] = rows;
+            if (!chan && ODD) periodic_cols(sp, x, nb[k]);
             act[k] = x < sp.nx && y < sp.ny;
             if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, sp.mask_words, x, y);
-            if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, g[k]);
+            if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, nb[k], g[k]);
         }
         double red[3] = {0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < NPT; ++k)
-            if (act[k]) node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, g[k], red);
+            if (act[k])
+                node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, nb[k], g[k], red);
 
         if (want_k || want_f) {
             double tot[3];

@@ -297,6 +297,10 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         d.ny = s.ny;
         d.pitch = (int32_t)align_up((size_t)s.nx, (size_t)row_align);
         d.plane = (int64_t)d.pitch * s.ny;
+        if (9 * d.plane >= (1ll << 31)) {
+            why = "a sample's nine population planes must hold fewer than 2^31 values";
+            return UQLB_ERR_ARG;
+        }
         d.f_off = f_off;
         f_off += 9 * d.plane;
         d.kind = s.kind;

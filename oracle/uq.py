@@ -241,3 +241,82 @@ def unit_converter(n: int, ma: float, re: float) -> dict:
     nu = 1.0 / re
     tau = 3.0 * nu * dt / (dx * dx) + 0.5
     return {"dx": dx, "dt": dt, "tau": tau, "nu_lattice": nu * dt / (dx * dx)}
+
+
+# --------------------------------------------------------------------------------------
+# Sparse grids and quasi Monte Carlo (Sec. 4.1 QMC, Sec. 6.3 Clenshaw-Curtis and Smolyak)
+# --------------------------------------------------------------------------------------
+
+
+def clenshaw_curtis(m: int) -> tuple[np.ndarray, np.ndarray]:
+    """m-point Clenshaw-Curtis rule on [-1, 1]: nodes cos(pi j/(m-1)) ascending, weights summing
+    to 2 (explicit cosine-sum weights, Trefethen SIAM Rev. 2008, Eq. 2.2 family)."""
+    if m == 1:
+        return np.array([0.0]), np.array([2.0])
+    n = m - 1
+    theta = np.pi * np.arange(m) / n
+    w = np.empty(m)
+    for j in range(m):
+        s = 0.0
+        for k in range(1, n // 2 + 1):
+            b = 1.0 if 2 * k == n else 2.0
+            s += b / (4.0 * k * k - 1.0) * math.cos(2.0 * k * theta[j])
+        c = 1.0 if j in (0, n) else 2.0
+        w[j] = c / n * (1.0 - s)
+    x = np.cos(theta)
+    order = np.argsort(x)
+    return x[order], w[order]
+
+
+def cc_points(level: int) -> int:
+    """Nested Clenshaw-Curtis sizes: 1 point at level 1, 2^(l-1) + 1 after."""
+    return 1 if level == 1 else 2 ** (level - 1) + 1
+
+
+def smolyak_cc(d: int, level: int):
+    """Smolyak sparse grid on [-1, 1]^d from nested Clenshaw-Curtis rules (combination form):
+    A(q, d) = sum_{q-d+1 <= |i| <= q} (-1)^(q-|i|) C(d-1, q-|i|) U^{i_1} x ... x U^{i_d},
+    q = d + level, i_j >= 1.  Nested nodes are merged by their index on the finest 1-D grid.
+    Returns (XI [S x d], weights [S] of the uniform probability measure)."""
+    q = d + level
+    finest = cc_points(level + 1)
+    acc: dict = {}
+    for idx in product(range(1, level + 2), repeat=d):
+        s = sum(idx)
+        if s < q - d + 1 or s > q:
+            continue
+        coef = (-1) ** (q - s) * math.comb(d - 1, q - s)
+        rules = [clenshaw_curtis(cc_points(i)) for i in idx]
+        for pts in product(*[range(len(r[0])) for r in rules]):
+            key = []
+            w = float(coef)
+            for dim, (i, j) in enumerate(zip(idx, pts)):
+                m = cc_points(i)
+                key.append((finest - 1) // 2 if m == 1 else j * ((finest - 1) // (m - 1)))
+                w *= 0.5 * rules[dim][1][j]
+            key = tuple(key)
+            acc[key] = acc.get(key, 0.0) + w
+    keys = sorted(acc)
+    xf, _ = clenshaw_curtis(finest)
+    xi = np.array([[xf[k] for k in key] for key in keys]).reshape(-1, d)
+    a = np.array([acc[k] for k in keys])
+    return xi, a
+
+
+def radical_inverse(i: int, base: int) -> float:
+    """Van der Corput radical inverse of i in the given base."""
+    f, r = 1.0, 0.0
+    while i > 0:
+        f /= base
+        r += f * (i % base)
+        i //= base
+    return r
+
+
+FIRST_PRIMES = [2, 3, 5, 7, 11, 13, 17, 19]
+
+
+def halton(n: int, d: int, skip: int = 1) -> np.ndarray:
+    """[n x d] Halton points in [0, 1): point s has coordinate k = radical inverse of s + skip
+    in the k-th prime base."""
+    return np.array([[radical_inverse(s + skip, FIRST_PRIMES[k]) for k in range(d)] for s in range(n)]).reshape(n, d)

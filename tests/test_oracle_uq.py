@@ -2,6 +2,7 @@
 mathematics that do not depend on the oracle itself.  CPU only."""
 import math
 import os
+from itertools import product
 
 import numpy as np
 import pytest
@@ -174,3 +175,62 @@ def test_unit_converter_matches_paper_table():
 def test_relative_l2():
     assert uq.relative_l2([1.0, 2.0], [1.0, 2.0]) == 0.0
     assert uq.relative_l2([3.0, 4.0], [0.0, 4.0]) == pytest.approx(0.75)
+
+
+def test_clenshaw_curtis_rules():
+    for m in (1, 3, 5, 9, 17):
+        x, w = uq.clenshaw_curtis(m)
+        assert abs(w.sum() - 2.0) < 1e-14 and np.all(np.diff(x) > 0) if m > 1 else w[0] == 2.0
+        deg = m if m % 2 == 1 else m - 1  # symmetric rule with m nodes is exact to degree m (m odd)
+        for k in range(deg + 1):
+            exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+            assert abs((w * x ** k).sum() - exact) < 1e-14, (m, k)
+    x, w = uq.clenshaw_curtis(3)
+    assert np.allclose(x, [-1, 0, 1]) and np.allclose(w, [1 / 3, 4 / 3, 1 / 3])  # Simpson's rule
+
+
+def _uniform_moment(alpha):
+    return math.prod(1.0 / (a + 1) if a % 2 == 0 else 0.0 for a in alpha)
+
+
+@pytest.mark.parametrize("d,level", [(1, 3), (2, 2), (3, 2), (4, 3)])
+def test_smolyak_exact_to_total_degree_2k_plus_1(d, level):
+    """Smolyak A(d + k, d) over nested Clenshaw-Curtis rules integrates every polynomial of total
+    degree <= 2k + 1 exactly (Novak and Ritter 1996) and is not exact at degree 2k + 2."""
+    xi, a = uq.smolyak_cc(d, level)
+    assert abs(a.sum() - 1.0) < 1e-14
+    top = 2 * level + 1
+    for alpha in product(range(top + 1), repeat=d):
+        if sum(alpha) > top:
+            continue
+        val = (a * np.prod(xi ** np.array(alpha)[None, :], axis=1)).sum()
+        assert abs(val - _uniform_moment(alpha)) < 1e-13, alpha
+    if d > 1:  # in one dimension the grid is a single Clenshaw-Curtis rule, exact beyond 2k + 1
+        worst = max(abs((a * np.prod(xi ** np.array(al)[None, :], axis=1)).sum() - _uniform_moment(al))
+                    for al in product(range(top + 2), repeat=d) if sum(al) == top + 1)
+        assert worst > 1e-8
+
+
+def test_smolyak_point_counts_and_the_papers_grid():
+    assert [len(uq.smolyak_cc(4, k)[1]) for k in range(0, 5)] == [1, 9, 41, 137, 401]
+    for r in _rows("smolyak_tgv4d_points.txt"):
+        d, level, pts = (int(v) for v in r.split("|"))
+        assert len(uq.smolyak_cc(d, level)[1]) == pts
+    # a level-3 grid supports the order-3 basis: products of degree <= 6 <= 7 are integrated exactly
+    xi, a = uq.smolyak_cc(4, 3)
+    phi = uq.basis_matrix(uq.multi_indices(4, 3), xi)
+    assert np.abs((phi * a[None, :]) @ phi.T - np.eye(phi.shape[0])).max() < 1e-12
+
+
+def test_halton_radical_inverse_and_rate():
+    assert [uq.radical_inverse(i, 2) for i in range(1, 8)] == [0.5, 0.25, 0.75, 0.125, 0.625, 0.375, 0.875]
+    assert np.allclose([uq.radical_inverse(i, 3) for i in range(1, 5)], [1 / 3, 2 / 3, 1 / 9, 4 / 9])
+    h = uq.halton(5, 3)
+    assert np.allclose(h[0], [0.5, 1 / 3, 0.2]) and np.all((h >= 0) & (h < 1))
+    # QMC error of a smooth 2-D integral decays close to N^-1 (Sec. 4.1), clearly faster than MC
+    f = lambda u: np.exp(-(u[:, 0] + 0.5 * u[:, 1]))  # noqa: E731
+    exact = (1 - math.exp(-1)) * (1 - math.exp(-0.5)) / 0.5
+    ns = np.array([64, 256, 1024, 4096])
+    errs = [abs(f(uq.halton(int(n), 2)).mean() - exact) for n in ns]
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert slope < -0.8, slope

@@ -50,7 +50,10 @@ typedef enum {
 
 enum { UQLB_DIST_UNIFORM = 0 };               /* Sec. 6.1: uniform inputs (Legendre basis) */
 enum { UQLB_BASIS_TOTAL = 0, UQLB_BASIS_TENSOR = 1 };
-enum { UQLB_QUAD_GAUSS_LEGENDRE_TENSOR = 0 }; /* Sec. 6.3: tensor-product Gauss rule */
+/* Sec. 6.3 quadrature rules: tensor-product Gauss-Legendre, or the Smolyak sparse grid over
+ * nested Clenshaw-Curtis rules (pts_per_dim then gives the Smolyak level k; the grid integrates
+ * total degree 2k + 1 exactly; 4 inputs at level 3 give the paper's 137 points). */
+enum { UQLB_QUAD_GAUSS_LEGENDRE_TENSOR = 0, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 1 };
 enum { UQLB_METHOD_NONE = 0, UQLB_METHOD_MC = 1, UQLB_METHOD_GPC = 2 };
 enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1 };
 /* Parameters an uncertain input dimension may drive (uqlb_case.param_of_dim). */
@@ -178,10 +181,18 @@ int uqlb_set_inputs(uqlb_ctx* ctx, int dim, const uqlb_dist* d);
  * key = seed, u = ((x1 << 32 | x0) >> 11) 2^-53, z = a + (b - a) u.  Weights 1/n. */
 int uqlb_init_mc(uqlb_ctx* ctx, int64_t n, uint64_t seed);
 
+/* Quasi Monte Carlo sample set (Sec. 4.1): n Halton points (radical inverses of s + skip in the
+ * first `dim` primes), z = a + (b - a) u, weights 1/n; statistics use the Monte Carlo estimators.
+ * 1 <= n <= 2^24, skip >= 0. */
+int uqlb_init_qmc(uqlb_ctx* ctx, int64_t n, int64_t skip);
+
 /* Stochastic collocation (Sec. 4.2, Sec. 8.1 initializeGPC(order, N, dist)): tensor
  * Gauss-Legendre grid with pts_per_dim nodes per input (last input fastest), weights of
  * the uniform probability measure, orthonormal Legendre chaos of `order` (`basis`
- * total or tensor).  Builds W[k, s] = a_s Phi_k(xi_s) (Eq. coef_discrete). */
+ * total or tensor).  Builds W[k, s] = a_s Phi_k(xi_s) (Eq. coef_discrete).  With quad =
+ * UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK the nodes are the Smolyak grid of level pts_per_dim (0..6),
+ * ordered lexicographically by their indices on the finest one-dimensional grid; sparse-grid
+ * weights can be negative. */
 int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad);
 
 int uqlb_num_samples(const uqlb_ctx* ctx, int64_t* n);

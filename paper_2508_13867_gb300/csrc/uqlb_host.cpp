@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -121,6 +122,87 @@ void gauss_legendre_rule(int n, double* x, double* w) {
         x[n - 1 - j] = r;  // the initial guesses run from the largest root down
         w[n - 1 - j] = 2.0 / ((1.0 - r * r) * dp * dp);
     }
+}
+
+// Clenshaw-Curtis rule with m nodes cos(pi j / (m - 1)), returned ascending; weights from the
+// cosine-sum formula (weights sum to 2).
+void clenshaw_curtis_rule(int m, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(m, 0.0);
+    w.assign(m, 0.0);
+    if (m == 1) {
+        w[0] = 2.0;
+        return;
+    }
+    const int n = m - 1;
+    for (int j = 0; j < m; ++j) {
+        const double th = M_PI * j / n;
+        double s = 0.0;
+        for (int k = 1; k <= n / 2; ++k) s += (2 * k == n ? 1.0 : 2.0) / (4.0 * k * k - 1.0) * std::cos(2.0 * k * th);
+        const double c = (j == 0 || j == n) ? 1.0 : 2.0;
+        // ascending order: node j of the cosine ordering is position n - j
+        x[n - j] = std::cos(th);
+        w[n - j] = c / n * (1.0 - s);
+    }
+}
+
+int cc_size(int level) { return level == 1 ? 1 : (1 << (level - 1)) + 1; }
+
+// Smolyak combination over nested Clenshaw-Curtis rules: sum over 1 <= i_j, q - d + 1 <= |i| <= q
+// (q = d + level) of (-1)^(q - |i|) C(d - 1, q - |i|) times the tensor rule; nested nodes merge
+// on their index in the finest one-dimensional grid.
+void smolyak_cc_grid(int d, int level, std::vector<double>& xi, std::vector<double>& a) {
+    const int q = d + level;
+    const int finest = cc_size(level + 1);
+    std::map<std::vector<int>, double> acc;
+    std::vector<int> idx(d, 1);
+    std::vector<std::vector<double>> rx(level + 2), rw(level + 2);
+    for (int l = 1; l <= level + 1; ++l) clenshaw_curtis_rule(cc_size(l), rx[l], rw[l]);
+    auto binom = [](int n, int k) {
+        double c = 1.0;
+        for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+        return c;
+    };
+    while (true) {
+        int s = 0;
+        for (int v : idx) s += v;
+        if (s >= q - d + 1 && s <= q) {
+            const double coef = ((q - s) % 2 ? -1.0 : 1.0) * binom(d - 1, q - s);
+            std::vector<int> pos(d, 0), key(d, 0);
+            while (true) {
+                double w = coef;
+                for (int k = 0; k < d; ++k) {
+                    const int m = cc_size(idx[k]);
+                    key[k] = m == 1 ? (finest - 1) / 2 : pos[k] * ((finest - 1) / (m - 1));
+                    w *= 0.5 * rw[idx[k]][pos[k]];
+                }
+                acc[key] += w;
+                int k = d - 1;
+                while (k >= 0 && ++pos[k] == cc_size(idx[k])) pos[k--] = 0;
+                if (k < 0) break;
+            }
+        }
+        int k = d - 1;
+        while (k >= 0 && ++idx[k] > level + 1) idx[k--] = 1;
+        if (k < 0) break;
+    }
+    std::vector<double> xf, wf;
+    clenshaw_curtis_rule(finest, xf, wf);
+    xi.clear();
+    a.clear();
+    for (auto& kv : acc) {  // std::map iterates keys in lexicographic order
+        for (int k = 0; k < d; ++k) xi.push_back(xf[kv.first[k]]);
+        a.push_back(kv.second);
+    }
+}
+
+double radical_inverse(uint64_t i, int base) {
+    double f = 1.0, r = 0.0;
+    while (i > 0) {
+        f /= base;
+        r += f * (double)(i % base);
+        i /= base;
+    }
+    return r;
 }
 
 void philox10(const uint32_t in[4], const uint32_t key[2], uint32_t out[4]) {
@@ -647,42 +729,80 @@ int uqlb_init_mc(uqlb_ctx* ctx, int64_t n, uint64_t seed) {
     return 0;
 }
 
+int uqlb_init_qmc(uqlb_ctx* ctx, int64_t n, int64_t skip) {
+    static const int primes[kMaxDim] = {2, 3, 5, 7, 11, 13, 17, 19};
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (ctx->dim < 1) return set_err(ctx, UQLB_ERR_STATE, "init_qmc: call uqlb_set_inputs first");
+    if (n < 1 || n > (1 << 24) || skip < 0) return set_err(ctx, UQLB_ERR_ARG, "init_qmc: need 1 <= n <= 2^24, skip >= 0");
+    const int d = ctx->dim;
+    ctx->z.assign((size_t)n * d, 0.0);
+    ctx->xi.assign((size_t)n * d, 0.0);
+    ctx->a.assign((size_t)n, 1.0 / (double)n);
+    for (int64_t s = 0; s < n; ++s)
+        for (int k = 0; k < d; ++k) {
+            const double u = radical_inverse((uint64_t)(s + skip), primes[k]);
+            ctx->z[(size_t)s * d + k] = ctx->dists[k].a + (ctx->dists[k].b - ctx->dists[k].a) * u;
+            ctx->xi[(size_t)s * d + k] = 2.0 * u - 1.0;
+        }
+    ctx->S = n;
+    ctx->method = UQLB_METHOD_MC;
+    ctx->K = 0;
+    ctx->W.clear();
+    ctx->alpha.clear();
+    return 0;
+}
+
 int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad) {
     if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
     if (ctx->dim < 1) return set_err(ctx, UQLB_ERR_STATE, "init_gpc: call uqlb_set_inputs first");
-    if (quad != UQLB_QUAD_GAUSS_LEGENDRE_TENSOR) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: unknown quadrature");
-    if (pts_per_dim < 1 || pts_per_dim > 64) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: need 1 <= pts_per_dim <= 64");
+    if (quad != UQLB_QUAD_GAUSS_LEGENDRE_TENSOR && quad != UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
+        return set_err(ctx, UQLB_ERR_ARG, "init_gpc: unknown quadrature");
+    if (quad == UQLB_QUAD_GAUSS_LEGENDRE_TENSOR && (pts_per_dim < 1 || pts_per_dim > 64))
+        return set_err(ctx, UQLB_ERR_ARG, "init_gpc: need 1 <= pts_per_dim <= 64");
+    if (quad == UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK && (pts_per_dim < 0 || pts_per_dim > 6))
+        return set_err(ctx, UQLB_ERR_ARG, "init_gpc: the Smolyak level must be 0..6");
     int64_t K = 0;
     if (uqlb_num_multi_indices(ctx->dim, order, basis, &K) != 0)
         return set_err(ctx, UQLB_ERR_ARG, "init_gpc: %s", g_last_error.c_str());
     const int d = ctx->dim;
-    const double Sd = std::pow((double)pts_per_dim, d);
-    if (Sd > (double)(1 << 24)) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: tensor grid too large");
-    const int64_t S = (int64_t)std::llround(Sd);
-    if (K * S > (int64_t)1 << 28) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: K x S too large");
-    std::vector<double> gx(pts_per_dim), gw(pts_per_dim);
-    gauss_legendre_rule(pts_per_dim, gx.data(), gw.data());
-    ctx->z.assign((size_t)S * d, 0.0);
-    ctx->xi.assign((size_t)S * d, 0.0);
-    ctx->a.assign((size_t)S, 0.0);
-    std::vector<int> idx(d, 0);
-    for (int64_t s = 0; s < S; ++s) {
-        // lexicographic, last dimension fastest
-        int64_t r = s;
-        for (int k = d - 1; k >= 0; --k) {
-            idx[k] = (int)(r % pts_per_dim);
-            r /= pts_per_dim;
+    int64_t S = 0;
+    std::vector<double> ref_xi, ref_a;
+    if (quad == UQLB_QUAD_GAUSS_LEGENDRE_TENSOR) {
+        const double Sd = std::pow((double)pts_per_dim, d);
+        if (Sd > (double)(1 << 24)) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: tensor grid too large");
+        S = (int64_t)std::llround(Sd);
+        std::vector<double> gx(pts_per_dim), gw(pts_per_dim);
+        gauss_legendre_rule(pts_per_dim, gx.data(), gw.data());
+        ref_xi.assign((size_t)S * d, 0.0);
+        ref_a.assign((size_t)S, 0.0);
+        std::vector<int> idx(d, 0);
+        for (int64_t s = 0; s < S; ++s) {
+            // lexicographic, last dimension fastest
+            int64_t r = s;
+            for (int k = d - 1; k >= 0; --k) {
+                idx[k] = (int)(r % pts_per_dim);
+                r /= pts_per_dim;
+            }
+            double w = 1.0;
+            for (int k = 0; k < d; ++k) {
+                ref_xi[(size_t)s * d + k] = gx[idx[k]];
+                w *= 0.5 * gw[idx[k]];
+            }
+            ref_a[s] = w;
         }
-        double w = 1.0;
-        for (int k = 0; k < d; ++k) {
-            const double xi = gx[idx[k]];
-            const double lo = ctx->dists[k].a, hi = ctx->dists[k].b;
-            ctx->xi[(size_t)s * d + k] = xi;
-            ctx->z[(size_t)s * d + k] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * xi;
-            w *= 0.5 * gw[idx[k]];
-        }
-        ctx->a[s] = w;
+    } else {
+        smolyak_cc_grid(d, pts_per_dim, ref_xi, ref_a);
+        S = (int64_t)ref_a.size();
     }
+    if (K * S > (int64_t)1 << 28) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: K x S too large");
+    ctx->xi = ref_xi;
+    ctx->a = ref_a;
+    ctx->z.assign((size_t)S * d, 0.0);
+    for (int64_t s = 0; s < S; ++s)
+        for (int k = 0; k < d; ++k) {
+            const double lo = ctx->dists[k].a, hi = ctx->dists[k].b;
+            ctx->z[(size_t)s * d + k] = 0.5 * (lo + hi) + 0.5 * (hi - lo) * ctx->xi[(size_t)s * d + k];
+        }
     enumerate_indices(d, order, basis, ctx->alpha);
     ctx->K = (int)K;
     ctx->W.assign((size_t)K * S, 0.0);

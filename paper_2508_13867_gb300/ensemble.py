@@ -69,13 +69,20 @@ class Ensemble:
     def init_mc(self, n: int, seed: int):
         U.uqlb_init_mc(self.ctx, n, seed)
 
-    def init_gpc(self, order: int, pts_per_dim: int, basis: int = U.UQLB_BASIS_TOTAL):
-        U.uqlb_init_gpc(self.ctx, order, pts_per_dim, basis)
+    def init_gpc(self, order: int, pts_per_dim: int, basis: int = U.UQLB_BASIS_TOTAL,
+                 quad: int = U.UQLB_QUAD_GAUSS_LEGENDRE_TENSOR):
+        U.uqlb_init_gpc(self.ctx, order, pts_per_dim, basis, quad)
+
+    def init_qmc(self, n: int, skip: int = 1):
+        U.uqlb_init_qmc(self.ctx, n, skip)
 
     def setup(self, w: Workload):
         self.set_inputs(w.bounds)
         if w.method == "gpc":
-            self.init_gpc(w.order, w.pts_per_dim)
+            quad = U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK if w.quad == "smolyak" else U.UQLB_QUAD_GAUSS_LEGENDRE_TENSOR
+            self.init_gpc(w.order, w.pts_per_dim, quad=quad)
+        elif w.method == "qmc":
+            self.init_qmc(w.n_mc)
         else:
             self.init_mc(w.n_mc, w.seed)
 

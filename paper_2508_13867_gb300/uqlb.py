@@ -22,7 +22,7 @@ UQLB_OK, UQLB_ERR_ARG, UQLB_ERR_OOM, UQLB_ERR_CUDA, UQLB_ERR_TIMEOUT, UQLB_ERR_U
     0, -1, -2, -3, -4, -5, -6
 UQLB_DIST_UNIFORM = 0
 UQLB_BASIS_TOTAL, UQLB_BASIS_TENSOR = 0, 1
-UQLB_QUAD_GAUSS_LEGENDRE_TENSOR = 0
+UQLB_QUAD_GAUSS_LEGENDRE_TENSOR, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 0, 1
 UQLB_METHOD_NONE, UQLB_METHOD_MC, UQLB_METHOD_GPC = 0, 1, 2
 UQLB_CASE_TGV, UQLB_CASE_CHANNEL = 0, 1
 UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3 = 0, 1, 2, 3
@@ -73,6 +73,7 @@ _SIGNATURES = {
     "uqlb_set_inputs": [c_void_p, ctypes.c_int, _P(uqlb_dist)],
     "uqlb_init_mc": [c_void_p, c_int64, ctypes.c_uint64],
     "uqlb_init_gpc": [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "uqlb_init_qmc": [c_void_p, c_int64, c_int64],
     "uqlb_num_samples": [c_void_p, _P(c_int64)],
     "uqlb_num_terms": [c_void_p, _P(ctypes.c_int)],
     "uqlb_get_samples": [c_void_p, _P(c_double), _P(c_double), _P(c_double)],
@@ -215,6 +216,10 @@ def uqlb_set_inputs(ctx, bounds) -> None:
 
 def uqlb_init_mc(ctx, n: int, seed: int) -> None:
     _check(lib().uqlb_init_mc(ctx, n, seed), ctx)
+
+
+def uqlb_init_qmc(ctx, n: int, skip: int = 1) -> None:
+    _check(lib().uqlb_init_qmc(ctx, n, skip), ctx)
 
 
 def uqlb_init_gpc(ctx, order: int, pts_per_dim: int, basis: int = UQLB_BASIS_TOTAL,

@@ -50,8 +50,9 @@ class Workload:
     base: SampleSpec
     bounds: list            # uniform input bounds, one (a, b) per dimension
     params: list            # parameter driven by each dimension: "nu", "u0", "zeta2", "zeta3"
-    method: str             # "gpc" or "mc"
-    pts_per_dim: int = 5
+    method: str             # "gpc", "mc" or "qmc"
+    pts_per_dim: int = 5    # Gauss-Legendre points per input, or the Smolyak level
+    quad: str = "gl"        # "gl" (tensor Gauss-Legendre) or "smolyak" (Clenshaw-Curtis sparse grid)
     order: int = 4
     n_mc: int = 0
     seed: int = 123456      # the seed of the paper's Monte Carlo example
@@ -87,6 +88,12 @@ def tgv64_gpc(steps: int = 1000) -> Workload:
 def tgv256_gpc4d(n: int = 256, steps: int = 2000, pts: int = 5, storage: str = "f32") -> Workload:
     return Workload("tgv256_gpc4d", tgv(n, steps), TGV4D_BOUNDS, TGV4D_PARAMS, "gpc", pts_per_dim=pts, order=4,
                     storage=storage)
+
+
+def tgv_smolyak4d(n: int = 256, steps: int = 2000, level: int = 3, order: int = 3, storage: str = "f32") -> Workload:
+    """The 4-D set-up on the Clenshaw-Curtis Smolyak grid (level 3: 137 samples, order-3 basis)."""
+    return Workload("tgv_smolyak4d", tgv(n, steps), TGV4D_BOUNDS, TGV4D_PARAMS, "gpc", pts_per_dim=level,
+                    order=order, quad="smolyak", storage=storage)
 
 
 def tgv512_mc4d(n: int = 512, steps: int = 2000, n_mc: int = 4096, storage: str = "f32") -> Workload:

@@ -282,3 +282,38 @@ def test_full_size_tgv256_sampled_against_oracle(ens):
         assert abs(row[-1] - ref[j].k_final) < TOL["f32"] * ref[j].k_final
     assert np.all(np.isfinite(var.cpu().numpy())) and float(mean[-1]) > 0
     e.close()
+
+
+def test_smolyak_and_qmc_ensembles_match_oracle(ens):
+    """Sparse-grid collocation (Clenshaw-Curtis Smolyak, level 2: 41 samples, order 2) and Halton
+    QMC (24 points) on the 4-D set-up at 32 x 32, 60 steps, FP64: statistics against the oracle."""
+    w = W.tgv_smolyak4d(n=32, steps=60, level=2, order=2, storage="f64")
+    e = Ensemble(0)
+    e.setup(w)
+    smp = e.ensemble_samples(w)
+    assert len(smp) == 41
+    res = e.run_batch(smp, storage="f64", fields_dtype="f64")
+    mean, var = e.stats(e.project(res["fields"]))
+    torch.cuda.synchronize()
+    xi, a = ouq.smolyak_cc(4, 2)
+    z = np.column_stack([ouq.map_uniform(xi[:, k], *w.bounds[k]) for k in range(4)])
+    specs = [W.tgv(32, 60, nu=r[0], u0=r[1], amp2=r[2] * r[1], amp3=r[3] * r[1]) for r in z]
+    mref = np.stack([oracle_row(r) for r in olbm.run([oracle_case(s) for s in specs])])
+    mr, vr = ouq.gpc_mean_var(ouq.gpc_coefficients(ouq.multi_indices(4, 2), xi, a, mref))
+    assert rel_l2(mean.cpu().numpy(), mr) < 1e-12 and rel_l2(var.cpu().numpy(), vr) < 1e-10
+    e.close()
+
+    q = Ensemble(0)
+    wq = W.Workload("qmc", W.tgv(32, 60), W.TGV4D_BOUNDS, W.TGV4D_PARAMS, "qmc", n_mc=24)
+    q.setup(wq)
+    smp = q.ensemble_samples(wq)
+    res = q.run_batch(smp, storage="f64", fields_dtype="f64")
+    mean, var = q.stats(res["fields"], ddof=1)
+    torch.cuda.synchronize()
+    u = ouq.halton(24, 4)
+    zq = np.column_stack([lo + (hi - lo) * u[:, k] for k, (lo, hi) in enumerate(W.TGV4D_BOUNDS)])
+    specs = [W.tgv(32, 60, nu=r[0], u0=r[1], amp2=r[2] * r[1], amp3=r[3] * r[1]) for r in zq]
+    mref = np.stack([oracle_row(r) for r in olbm.run([oracle_case(s) for s in specs])])
+    mr, vr = ouq.mc_mean_var(mref, ddof=1)
+    assert rel_l2(mean.cpu().numpy(), mr) < 1e-12 and rel_l2(var.cpu().numpy(), vr) < 1e-10
+    q.close()

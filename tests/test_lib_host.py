@@ -157,3 +157,38 @@ def test_workspace_bytes_cover_the_arena():
     b = U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(100, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
     assert b >= 9 * 128 * 100 * 4
     assert U.uqlb_plain_workspace_bytes(s) >= 2 * 9 * 256 * 256 * 8
+
+
+@pytest.mark.parametrize("d,level", [(1, 3), (2, 2), (4, 3), (3, 4)])
+def test_smolyak_grid_and_weights_match_oracle(d, level):
+    bounds = W.TGV4D_BOUNDS[:d] if d <= 4 else None
+    ctx = U.uqlb_create(0)
+    try:
+        U.uqlb_set_inputs(ctx, bounds)
+        U.uqlb_init_gpc(ctx, level, level, U.UQLB_BASIS_TOTAL, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
+        z, xi, a = U.uqlb_get_samples(ctx, d)
+        xo, ao = ouq.smolyak_cc(d, level)
+        assert xi.shape == xo.shape and np.abs(xi - xo).max() < 1e-15
+        assert np.abs(a - ao).max() < 1e-15
+        zo = np.column_stack([ouq.map_uniform(xo[:, k], *bounds[k]) for k in range(d)])
+        assert np.abs(z - zo).max() < 1e-15
+        wm = U.uqlb_get_weight_matrix(ctx)
+        assert np.abs(wm - ouq.weight_matrix(ouq.multi_indices(d, level), xo, ao)).max() < 1e-14
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+def test_halton_sample_set_matches_oracle_bit_for_bit():
+    ctx = U.uqlb_create(0)
+    try:
+        U.uqlb_set_inputs(ctx, W.TGV4D_BOUNDS)
+        U.uqlb_init_qmc(ctx, 500, 1)
+        z, xi, a = U.uqlb_get_samples(ctx, 4)
+        u = ouq.halton(500, 4, skip=1)
+        assert np.array_equal(xi, 2.0 * u - 1.0)
+        assert np.array_equal(z, np.column_stack([lo + (hi - lo) * u[:, k] for k, (lo, hi) in enumerate(W.TGV4D_BOUNDS)]))
+        assert np.allclose(a, 1 / 500, rtol=0, atol=0)
+        with pytest.raises(U.UqlbError):
+            U.uqlb_init_gpc(ctx, 2, 7, U.UQLB_BASIS_TOTAL, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
+    finally:
+        U.uqlb_destroy(ctx)

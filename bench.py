@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 METRIC = "ensemble MLUPS (tgv256_gpc4d: 625 samples x 256^2 x 2000 steps, FP32 storage, FP64 gPC statistics)"
 UNIT = "MLUPS"
 BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+# version tag of the step kernel whose ncu traffic profiles/step_kernel_f32_tgv256.md records
+STEP_KERNEL_VERSION = "aa-npt-nbr"
 
 
 def _peaks():
@@ -178,7 +180,7 @@ def bench_kernel_only(args):
     out = {}
     for _ in range(args.warmup + args.steps):
         ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
-                      nodes_per_thread=args.npt)
+                      nodes_per_thread=args.npt, rounding=args.rounding)
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     nodes = sum(s.nx * s.ny for s in smp)
@@ -286,13 +288,15 @@ def bench_workload(args):
                      "value": upd / (ms / 1e3) / 1e6})
         # further storage formats of the same ensemble (compared with the same oracle subset)
         extra = {}
-        for st in [x for x in args.storages.split(",") if x and x != w.storage]:
-            def run_st(st=st):
-                rr = ens.run_batch(smp, storage=st, fields_dtype="f32")
+        for spec in [x for x in args.storages.split(",") if x and x != w.storage]:
+            st, _, rounding = spec.partition(":")
+
+            def run_st(st=st, rounding=rounding or "auto"):
+                rr = ens.run_batch(smp, storage=st, fields_dtype="f32", rounding=rounding)
                 return rr, ens.stats(rr["fields"], ddof=1) if w.method == "mc" else ens.stats(ens.project(rr["fields"]))
             ms_st, (rr, _) = timed(run_st, 1)
-            extra[st] = {"time_to_stats_s": ms_st / 1e3, "value": upd / (ms_st / 1e3) / 1e6,
-                         "fields": rr["fields"][: min(len(smp), args.oracle_samples)].double().cpu().numpy()}
+            extra[spec] = {"time_to_stats_s": ms_st / 1e3, "value": upd / (ms_st / 1e3) / 1e6,
+                           "fields": rr["fields"][: min(len(smp), args.oracle_samples)].double().cpu().numpy()}
         # plain per-sample FP64 comparator on a subset, scaled by the sample count
         if args.plain_samples > 0:
             psub = [smp[i] for i in range(min(len(smp), args.plain_samples))]
@@ -441,15 +445,16 @@ def bench_gpu(args):
     achieved = per_launch_bytes / (step_kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as fh:
-                pj = json.load(fh)
-            if pj.get("kernel_version") == "aa_v1" and pj.get("storage") == storage:
-                traffic = pj["bytes_per_launch_full_size"]
-        except Exception:
-            traffic = None
+    prof = os.path.join(ROOT, "profiles", "step_kernel_f32_tgv256.md")
+    if storage == "f32" and os.path.exists(prof):
+        import re
+
+        with open(prof) as fh:
+            text = fh.read()
+        ver = re.search(r"^kernel_version: (\S+)", text, flags=re.M)
+        tb = re.search(r"^traffic_bytes_per_launch_full_size: (\d+)", text, flags=re.M)
+        if ver and tb and ver.group(1) == STEP_KERNEL_VERSION:
+            traffic = int(tb.group(1))
 
     # end to end through host buffers: one C call, tables in, statistics out
     e2e = None
@@ -545,6 +550,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)
+    ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
     ap.add_argument("--workload", default="tgv256_gpc4d",
                     choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "uneven"])
     ap.add_argument("--oracle-samples", type=int, default=4, help="oracle reference subset (other workloads)")

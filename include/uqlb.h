@@ -60,6 +60,10 @@ enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1 };
 enum { UQLB_PARAM_NU = 0, UQLB_PARAM_U0 = 1, UQLB_PARAM_ZETA2 = 2, UQLB_PARAM_ZETA3 = 3 };
 /* Number formats: population storage, field outputs, projection inputs. */
 enum { UQLB_F64 = 0, UQLB_F32 = 1, UQLB_F16 = 2, UQLB_BF16 = 3 };
+/* Rounding of 16-bit population stores.  Stochastic rounding (seeded by sample, node and step,
+ * so runs reproduce) keeps the rounding error unbiased; nearest-even stagnates on fine lattices
+ * where g changes by less than one unit in the last place per step.  FP32/FP64 ignore it. */
+enum { UQLB_ROUND_AUTO = 0, UQLB_ROUND_NEAREST = 1, UQLB_ROUND_STOCHASTIC = 2 };
 /* Columns of the per-sample scalar output qoi[S x UQLB_QOI_COLS] (FP64). */
 enum {
     UQLB_QOI_K = 0,      /* normalised kinetic energy K(T) (Sec. 8.2, discrete form) */
@@ -92,12 +96,14 @@ typedef struct {
  *     staircase circular obstacle of centre (cyl_cx, cyl_cy) and radius cyl_r (node
  *     (x, y) solid iff its centre (x + 1/2, y + 1/2) lies strictly inside); C_D and
  *     C_L normalised by rho = 1, u0 and diameter 2 cyl_r.  With steady_tol > 0 a
- *     sample stops once |C_D(t) - C_D(t - qoi_every)| < steady_tol |C_D(t)|.
+ *     sample stops once |C_D(t) - C_D(t - qoi_every)| < steady_tol |C_D(t)| holds at
+ *     steady_checks consecutive checks (FP32 resolves C_D to ~1e-7, so a tolerance below that
+ *     needs several checks to avoid stopping on a chance coincidence).
  * tau = 3 nu + 1/2 (Sec. 8.2), omega = 1 / tau. */
 typedef struct {
     int32_t kind;        /* UQLB_CASE_TGV or UQLB_CASE_CHANNEL */
     int32_t nx, ny;      /* lattice size, 2 <= nx, ny <= 65536 */
-    int32_t reserved;
+    int32_t steady_checks; /* CHANNEL: consecutive checks that must pass (0 or 1: one check) */
     int64_t steps;       /* number of steps (TGV) or step cap (CHANNEL), 0 <= steps < 2^31 */
     double nu;           /* lattice viscosity, > 0 */
     double u0;           /* TGV amplitude or channel mean inflow velocity */
@@ -129,7 +135,7 @@ typedef struct {
     int32_t chunk_steps;      /* steps per captured CUDA graph (even, 2..1024; 0: default 64) */
     int32_t tile_rows;        /* rows per tile (see above; 0: tuned or default) */
     int32_t nodes_per_thread; /* nodes per thread along x (see above; 0: tuned or default) */
-    int32_t reserved;
+    int32_t rounding;         /* 16-bit storage: UQLB_ROUND_AUTO (= stochastic), NEAREST or STOCHASTIC */
 } uqlb_run_opts;
 
 /* ------------------------------------------------------------------------------------

@@ -39,6 +39,11 @@ static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp dia
 static_assert(cx(6) == -1 && cy(6) == 1 && cx(8) == 1 && cy(8) == -1, "diagonal order");
 
 // Storage formats of the shifted populations and the arithmetic type used with each.
+// store() rounds to nearest even; store_sr() rounds stochastically with 32 random bits r: the
+// magnitude is rounded up with probability equal to the discarded fraction, so rounding errors
+// have zero mean.  This matters for 16-bit storage on fine lattices, where the change of g over
+// one step is far below one unit in the last place and nearest rounding keeps discarding it
+// with a consistent sign (stagnation).
 template <typename S>
 struct Storage;
 template <>
@@ -46,18 +51,26 @@ struct Storage<double> {
     using C = double;
     static __device__ __forceinline__ double load(const double* p) { return *p; }
     static __device__ __forceinline__ void store(double* p, double v) { *p = v; }
+    static __device__ __forceinline__ void store_sr(double* p, double v, uint32_t) { *p = v; }
 };
 template <>
 struct Storage<float> {
     using C = float;
     static __device__ __forceinline__ float load(const float* p) { return *p; }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ void store_sr(float* p, float v, uint32_t) { *p = v; }
 };
+// FP16 holds g scaled by 2^12 (exact): |g| <= ~0.05 then stays far below the FP16 maximum and
+// values down to 1.5e-8 stay in the normal range, where the rounding step is relative.
 template <>
 struct Storage<__half> {
     using C = float;
-    static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p); }
-    static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p) * 0x1p-12f; }
+    static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v * 0x1p12f); }
+    // 13 random bits below the last FP16 mantissa place of the FP32 pattern, then truncation
+    static __device__ __forceinline__ void store_sr(__half* p, float v, uint32_t r) {
+        *p = __float2half_rz(__uint_as_float(__float_as_uint(v * 0x1p12f) + (r & 0x1FFFu)));
+    }
 };
 template <>
 struct Storage<__nv_bfloat16> {
@@ -68,7 +81,22 @@ struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) {
         *p = __float2bfloat16_rn(v);
     }
+    // 16 random bits added below the BF16 mantissa of the FP32 pattern, then truncation
+    static __device__ __forceinline__ void store_sr(__nv_bfloat16* p, float v, uint32_t r) {
+        *p = __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xFFFFu)) >> 16));
+    }
 };
+
+// Counter-based 32-bit mixer (xor-shift-multiply finaliser) for the stochastic-rounding bits of
+// one population store: a function of (sample, in-sample offset, step) only, so runs reproduce.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
 
 // Moments of shifted populations: drho, j = sum c_i g_i and u = j / rho = j + j (1/rho - 1).
 template <typename C>

@@ -42,10 +42,12 @@ struct KParams {
     int32_t* done;
     int32_t* steps_run;
     double* cd_prev;
+    int32_t* streak;
     const int64_t* step_counter;
     int32_t* n_done;
     int32_t dt;
     int32_t max_steps;
+    int32_t stochastic;  // 16-bit storage: stochastic rounding of every population store
     // outputs
     void* fields;
     int64_t fields_ld;
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
             p.done[j] = 0;
             p.steps_run[j] = sp.steps;
             p.cd_prev[j] = NAN;
+            p.streak[j] = 0;
         }
         for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
@@ -312,6 +315,18 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
     using C = typename Storage<S>::C;
     const int own = nb.row[1] + x;
     const int plane = (int)sp.plane;
+    // stochastic-rounding bits: one mixed word per node and step, spread over the nine stores by
+    // distinct odd multipliers (the high 16 bits of the products are used)
+    const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    const uint32_t h = sr ? mix32((uint32_t)own * 0x9E3779B1u + (uint32_t)t * 0x85EBCA77u +
+                                  (uint32_t)sp.sample_id * 0xC2B2AE3Du)
+                          : 0u;
+    auto put = [&](S* ptr, C v, int i) {
+        if (sr)
+            Storage<S>::store_sr(ptr, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16);
+        else
+            Storage<S>::store(ptr, v);
+    };
     C drho, jx, jy, ux, uy;
     moments(g, drho, jx, jy, ux, uy);
     if (want_k) red[0] += (double)(ux * ux + uy * uy);
@@ -341,16 +356,16 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
     }
     if (!ODD) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Storage<S>::store(base + (opp(i) * plane + own), g[i]);
+        for (int i = 0; i < 9; ++i) put(base + (opp(i) * plane + own), g[i], i);
         return;
     }
     if (!chan) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            Storage<S>::store(base + (i * plane + nb.row[1 + cy(i)] + nb.col[1 + cx(i)]), g[i]);
+            put(base + (i * plane + nb.row[1 + cy(i)] + nb.col[1 + cx(i)]), g[i], i);
         return;
     }
-    Storage<S>::store(base + own, g[0]);
+    put(base + own, g[0], 0);
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         int dx = x + cx(i), dy = y + cy(i);
@@ -358,16 +373,15 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
             const int cls = classify(sp, mask, dx, dy);
             const int o = opp(i);
             if (cls == kInterior) {
-                Storage<S>::store(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i]);
+                put(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i], i);
             } else if (cls == kWall || cls == kSolid) {
-                Storage<S>::store(base + o * plane + own, g[i]);
+                put(base + o * plane + own, g[i], i);
             } else if (cls == kInlet) {
                 const C yy = C(y) + C(0.5) - C(0.5) * C(cy(o));
-                Storage<S>::store(base + o * plane + own, g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t));
+                put(base + o * plane + own, g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
             } else {
                 const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                Storage<S>::store(base + o * plane + own,
-                                  -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)));
+                put(base + o * plane + own, -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
             }
         }
     }
@@ -458,7 +472,10 @@ __global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
                         if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
                         if (sp.steady_tol > 0.0) {
                             const double prev = p.cd_prev[j];
-                            if (!isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd)) {
+                            const bool pass = !isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd);
+                            const int run = pass ? p.streak[j] + 1 : 0;
+                            p.streak[j] = run;
+                            if (run >= sp.steady_checks) {
                                 p.done[j] = 1;
                                 p.steps_run[j] = t + 1;
                                 atomicAdd(p.n_done, 1);
@@ -608,10 +625,12 @@ KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutp
     p.done = b.done;
     p.steps_run = b.steps_run;
     p.cd_prev = b.cd_prev;
+    p.streak = b.streak;
     p.step_counter = b.step_counter;
     p.n_done = b.active_flag;
     p.dt = dt;
     p.max_steps = g.max_steps;
+    p.stochastic = g.stochastic;
     if (o != nullptr) {
         p.fields = o->fields;
         p.fields_ld = o->fields_ld;

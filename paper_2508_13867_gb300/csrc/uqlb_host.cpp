@@ -300,7 +300,7 @@ struct BatchPlan {
     std::vector<uint32_t> masks;
     size_t off_arena = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
            off_partials = 0, off_counters = 0, off_done = 0, off_steps_run = 0, off_cd_prev = 0,
-           off_step_counter = 0, off_flag = 0, total = 0;
+           off_step_counter = 0, off_flag = 0, off_streak = 0, total = 0;
     BatchGeometry geom{};
     int n_steady = 0;
     bool uniform_size = true;
@@ -409,6 +409,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
             d.uin_max = 1.5 * s.u0;
             d.ramp_steps = (double)std::max<int64_t>(s.ramp_steps, 0);
             d.steady_tol = s.steady_tol > 0.0 ? s.steady_tol : 0.0;
+            d.steady_checks = s.steady_checks > 1 ? s.steady_checks : 1;
             if (d.steady_tol > 0.0) ++P.n_steady;
             d.side_off = (int32_t)side;
             side += s.ny;
@@ -451,6 +452,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.off_cd_prev = take(sizeof(double) * n);
     P.off_step_counter = take(sizeof(int64_t));
     P.off_flag = take(sizeof(int32_t));
+    P.off_streak = take(sizeof(int32_t) * n);
     P.total = off;
 
     BatchGeometry& g = P.geom;
@@ -462,6 +464,12 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     g.storage = storage;
     g.any_channel = any_channel;
     g.uniform_tiles = uniform_tiles ? tiles0 : 0;
+    const int rounding = o ? o->rounding : UQLB_ROUND_AUTO;
+    if (rounding < UQLB_ROUND_AUTO || rounding > UQLB_ROUND_STOCHASTIC) {
+        why = "unknown rounding mode";
+        return UQLB_ERR_ARG;
+    }
+    g.stochastic = (eb == 2 && rounding != UQLB_ROUND_NEAREST) ? 1 : 0;
     return 0;
 }
 
@@ -482,6 +490,7 @@ BatchBuffers carve(const BatchPlan& P, void* ws) {
     B.cd_prev = reinterpret_cast<double*>(b + P.off_cd_prev);
     B.step_counter = reinterpret_cast<int64_t*>(b + P.off_step_counter);
     B.active_flag = reinterpret_cast<int32_t*>(b + P.off_flag);
+    B.streak = reinterpret_cast<int32_t*>(b + P.off_streak);
     return B;
 }
 

@@ -34,7 +34,8 @@ struct alignas(16) SampleDev {
     double force_norm;  // channel: 2 / (rho0 u_mean^2 D)
     double ramp_steps;  // channel: ramp length (0: none)
     double steady_tol;  // channel: steady-state tolerance (0: none)
-    int32_t pad[2];
+    int32_t steady_checks;  // channel: consecutive passing checks needed (>= 1)
+    int32_t pad;
 };
 static_assert(sizeof(SampleDev) == 128, "SampleDev must stay 128 bytes");
 
@@ -58,6 +59,7 @@ struct BatchBuffers {
     int32_t* done;           // [S] 1 once a sample has stopped (steady state)
     int32_t* steps_run;      // [S]
     double* cd_prev;         // [S] previous C_D check
+    int32_t* streak;         // [S] consecutive passing steady-state checks
     int64_t* step_counter;   // [1] base step of the running graph chunk
     int32_t* active_flag;    // [1] nonzero while any channel sample still runs
 };
@@ -71,6 +73,8 @@ struct BatchGeometry {
     int32_t storage;
     int32_t any_channel;
     int32_t uniform_tiles;   // tiles per sample when every sample has the same size, else 0
+    int32_t stochastic;      // 16-bit storage rounds stochastically
+    int32_t reserved;
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).

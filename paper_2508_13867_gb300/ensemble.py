@@ -15,8 +15,8 @@ PARAMS = {"nu": U.UQLB_PARAM_NU, "u0": U.UQLB_PARAM_U0, "zeta2": U.UQLB_PARAM_ZE
 
 
 def sample_struct(s: SampleSpec) -> U.uqlb_sample:
-    return U.uqlb_sample(s.kind, s.nx, s.ny, 0, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref, s.cyl_cx, s.cyl_cy,
-                         s.cyl_r, s.ramp_steps, s.steady_tol)
+    return U.uqlb_sample(s.kind, s.nx, s.ny, s.steady_checks, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref,
+                         s.cyl_cx, s.cyl_cy, s.cyl_r, s.ramp_steps, s.steady_tol)
 
 
 def case_struct(w: Workload) -> U.uqlb_case:
@@ -27,10 +27,13 @@ def case_struct(w: Workload) -> U.uqlb_case:
     return c
 
 
+ROUNDING = {"auto": U.UQLB_ROUND_AUTO, "nearest": U.UQLB_ROUND_NEAREST, "stochastic": U.UQLB_ROUND_STOCHASTIC}
+
+
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
-                tile_rows: int = 0, nodes_per_thread: int = 0) -> U.uqlb_run_opts:
+                tile_rows: int = 0, nodes_per_thread: int = 0, rounding: str = "auto") -> U.uqlb_run_opts:
     return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows,
-                           nodes_per_thread, 0)
+                           nodes_per_thread, ROUNDING[rounding])
 
 
 def _stream() -> int:
@@ -110,9 +113,9 @@ class Ensemble:
     # ---- runs -------------------------------------------------------------------------
     def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
                   fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
-                  nodes_per_thread: int = 0, out: dict | None = None) -> dict:
+                  nodes_per_thread: int = 0, rounding: str = "auto", out: dict | None = None) -> dict:
         """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series)."""
-        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread)
+        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread, rounding)
         nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
         ws = self.workspace(nbytes)
         n = len(samples)

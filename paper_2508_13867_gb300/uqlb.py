@@ -27,6 +27,7 @@ UQLB_METHOD_NONE, UQLB_METHOD_MC, UQLB_METHOD_GPC = 0, 1, 2
 UQLB_CASE_TGV, UQLB_CASE_CHANNEL = 0, 1
 UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3 = 0, 1, 2, 3
 UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16 = 0, 1, 2, 3
+UQLB_ROUND_AUTO, UQLB_ROUND_NEAREST, UQLB_ROUND_STOCHASTIC = 0, 1, 2
 (UQLB_QOI_K, UQLB_QOI_MASS, UQLB_QOI_MOMX, UQLB_QOI_MOMY, UQLB_QOI_CD, UQLB_QOI_CL, UQLB_QOI_STEPS,
  UQLB_QOI_STATUS, UQLB_QOI_COLS) = range(9)
 
@@ -42,7 +43,7 @@ class uqlb_dist(ctypes.Structure):
 
 
 class uqlb_sample(ctypes.Structure):
-    _fields_ = [("kind", c_int32), ("nx", c_int32), ("ny", c_int32), ("reserved", c_int32),
+    _fields_ = [("kind", c_int32), ("nx", c_int32), ("ny", c_int32), ("steady_checks", c_int32),
                 ("steps", c_int64), ("nu", c_double), ("u0", c_double), ("amp2", c_double),
                 ("amp3", c_double), ("u_ref", c_double), ("cyl_cx", c_double), ("cyl_cy", c_double),
                 ("cyl_r", c_double), ("ramp_steps", c_int64), ("steady_tol", c_double)]
@@ -55,7 +56,7 @@ class uqlb_case(ctypes.Structure):
 class uqlb_run_opts(ctypes.Structure):
     _fields_ = [("storage", c_int32), ("fields_dtype", c_int32), ("qoi_every", c_int64),
                 ("chunk_steps", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
-                ("reserved", c_int32)]
+                ("rounding", c_int32)]
 
 
 _P = ctypes.POINTER

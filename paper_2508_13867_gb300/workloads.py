@@ -42,6 +42,7 @@ class SampleSpec:
     cyl_r: float = 0.0
     ramp_steps: int = 0
     steady_tol: float = 0.0
+    steady_checks: int = 1
 
 
 @dataclass
@@ -101,8 +102,11 @@ def tgv512_mc4d(n: int = 512, steps: int = 2000, n_mc: int = 4096, storage: str 
 
 
 def cylinder_gpc(nd: int = 20, pts: int = 9, order: int = 8, steps: int = 200000, steady_tol: float = 1e-8,
-                 storage: str = "f32") -> Workload:
+                 storage: str = "f32", steady_checks: int = 0) -> Workload:
+    """Steady state: the relative change of C_D over 100 steps stays below steady_tol.  FP32 resolves
+    C_D to ~1e-7, so below that tolerance it must hold at 5 consecutive checks (FP64: one)."""
     base = channel(nd, steps=steps, steady_tol=steady_tol)
+    base.steady_checks = steady_checks or (1 if storage == "f64" else 5)
     return Workload("cylinder_gpc", base, [(0.9 * 0.04, 1.1 * 0.04)], ["u0"], "gpc", pts_per_dim=pts,
                     order=order, storage=storage, qoi_every=100)
 

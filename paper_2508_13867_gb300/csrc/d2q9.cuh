@@ -128,15 +128,24 @@ __device__ __forceinline__ double lin<double>(int i) {
 // BGK relaxation of shifted populations towards the shifted equilibrium, in place:
 //   g_i^eq = w_i (drho + 4.5 (c_i.j)(c_i.u) - 1.5 j.u) + L_i c_i.j
 // (Eq. equilibrium times rho, with rho u = j), g_i* = g_i + omega (g_i^eq - g_i).
+// Opposite directions share the even part A = w_i (drho + 4.5 (c_i.j)(c_i.u) - 1.5 j.u) and
+// differ in the sign of the odd part, so each pair (i, opp(i)) is evaluated once:
+// g_i^eq = fma(L_i, c_i.j, A), g_opp^eq = fma(-L_i, c_i.j, A) (the same roundings as
+// evaluating every direction on its own).
 template <typename C>
 __device__ __forceinline__ void bgk(C g[9], C omega, C drho, C jx, C jy, C ux, C uy) {
     const C ju15 = C(1.5) * (jx * ux + jy * uy);
+    g[0] = fma(omega, wgt<C>(0) * (drho - ju15) - g[0], g[0]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
+    for (int i : {1, 2, 5, 6}) {
+        const int o = opp(i);
         const C cj = C(cx(i)) * jx + C(cy(i)) * jy;
         const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
-        const C geq = fma(lin<C>(i), cj, wgt<C>(i) * (drho + C(4.5) * cj * cu - ju15));
-        g[i] = fma(omega, geq - g[i], g[i]);
+        const C A = wgt<C>(i) * (drho + C(4.5) * cj * cu - ju15);
+        const C gi = fma(lin<C>(i), cj, A);
+        const C go = fma(-lin<C>(i), cj, A);
+        g[i] = fma(omega, gi - g[i], g[i]);
+        g[o] = fma(omega, go - g[o], g[o]);
     }
 }
 

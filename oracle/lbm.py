@@ -18,7 +18,7 @@ _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle_lbm.so")
 
-TGV, CHANNEL = 0, 1
+TGV, CHANNEL, TGV_PERTURBED = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -39,7 +39,7 @@ class _Case(ctypes.Structure):
                 ("amp2", ctypes.c_double), ("amp3", ctypes.c_double), ("u_ref", ctypes.c_double),
                 ("cyl_cx", ctypes.c_double), ("cyl_cy", ctypes.c_double),
                 ("cyl_r", ctypes.c_double), ("ramp_steps", ctypes.c_int64),
-                ("qoi_every", ctypes.c_int64), ("steady_tol", ctypes.c_double)]
+                ("qoi_every", ctypes.c_int64), ("steady_tol", ctypes.c_double), ("pert", ctypes.c_double * 4)]
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -84,11 +84,12 @@ class Case:
     ramp_steps: int = 0
     qoi_every: int = 0
     steady_tol: float = 0.0
+    pert: tuple = (0.0, 0.0, 0.0, 0.0)
 
     def _c(self) -> _Case:
         return _Case(self.kind, self.nx, self.ny, self.steps, self.nu, self.u0, self.amp2,
                      self.amp3, self.u_ref, self.cyl_cx, self.cyl_cy, self.cyl_r,
-                     self.ramp_steps, self.qoi_every, self.steady_tol)
+                     self.ramp_steps, self.qoi_every, self.steady_tol, (ctypes.c_double * 4)(*self.pert))
 
 
 @dataclass

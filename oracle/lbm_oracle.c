@@ -46,7 +46,7 @@ static const int OPP[Q] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 static const double WGT[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
-enum { ORACLE_TGV = 0, ORACLE_CHANNEL = 1 };
+enum { ORACLE_TGV = 0, ORACLE_CHANNEL = 1, ORACLE_TGV_PERTURBED = 2 };
 
 /* One deterministic run (one sample).  All lengths are in lattice units. */
 typedef struct {
@@ -61,6 +61,7 @@ typedef struct {
     int64_t ramp_steps;  /* channel: inflow ramp length T_r (0: no ramp) */
     int64_t qoi_every;   /* stride of the QoI series (0: no series) */
     double steady_tol;   /* channel: stop when |dC_D|/|C_D| < tol between checks (0: never) */
+    double pert[4];      /* perturbed TGV: zeta_00, zeta_01, zeta_10, zeta_11 (lattice velocity units) */
 } oracle_case;
 
 /* Per-run outputs.  Arrays are row-major [ny][nx]; any pointer may be NULL. */
@@ -127,6 +128,26 @@ static void tgv_initial(const oracle_case *c, int x, int y, double *rho, double 
     *uy = v;
 }
 
+/* Sec. 8.3 Taylor-Green vortex with four-dimensional uncertain initial velocity, on the periodic
+ * square [0, 2 pi)^2 resolved by nx x ny nodes x = 2 pi i / nx:
+ *   u = -U cos(2x) sin(2y), v = U sin(2x) cos(2y), U = u0 + eps(x, y),
+ *   eps = 1/4 sum_{i,j in {0,1}} zeta_ij k_i(4x) k_j(4y), k_0 = sin, k_1 = cos,
+ *   p = -U^2/4 (cos 4x + cos 4y) (the printed factor (2/2)^2 is 1), rho = 1 + 3 p. */
+static void tgv_perturbed_initial(const oracle_case *c, int ix, int iy, double *rho, double *ux,
+                                  double *uy) {
+    double x = 2.0 * M_PI * ix / c->nx, y = 2.0 * M_PI * iy / c->ny;
+    double kx[2] = {sin(4.0 * x), cos(4.0 * x)};
+    double ky[2] = {sin(4.0 * y), cos(4.0 * y)};
+    double eps = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) eps += c->pert[2 * i + j] * kx[i] * ky[j];
+    double U = c->u0 + 0.25 * eps;
+    *ux = -U * cos(2.0 * x) * sin(2.0 * y);
+    *uy = U * sin(2.0 * x) * cos(2.0 * y);
+    double p = -0.25 * U * U * (cos(4.0 * x) + cos(4.0 * y));
+    *rho = 1.0 + 3.0 * p;
+}
+
 /* QoI of the current (post-stream) state: K(t) for the TGV. */
 static double kinetic_energy(const oracle_case *c, const double *f, const unsigned char *solid) {
     int64_t plane = (int64_t)c->nx * c->ny;
@@ -168,6 +189,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
             int64_t n = (int64_t)y * nx + x;
             double rho = 1.0, ux = 0.0, uy = 0.0;
             if (c->kind == ORACLE_TGV) tgv_initial(c, x, y, &rho, &ux, &uy);
+            if (c->kind == ORACLE_TGV_PERTURBED) tgv_perturbed_initial(c, x, y, &rho, &ux, &uy);
             if (solid[n]) ux = uy = 0.0;
             for (int i = 0; i < Q; ++i) f[i * plane + n] = feq(i, rho, ux, uy);
         }
@@ -179,7 +201,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
                                   : 0.0;
     int64_t nseries = 0;
     double cd = 0.0, cl = 0.0, cd_prev = NAN;
-    if (o->series && o->series_len > 0 && c->qoi_every > 0 && c->kind == ORACLE_TGV)
+    if (o->series && o->series_len > 0 && c->qoi_every > 0 && c->kind != ORACLE_CHANNEL)
         o->series[nseries++] = kinetic_energy(c, f, solid);
 
     int64_t t;
@@ -221,7 +243,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
                 for (int i = 0; i < Q; ++i) {
                     int sx = x - CX[i], sy = y - CY[i];
                     double val;
-                    if (c->kind == ORACLE_TGV) {
+                    if (c->kind != ORACLE_CHANNEL) {
                         sx = (sx + nx) % nx;
                         sy = (sy + ny) % ny;
                         val = fpost[i * plane + (int64_t)sy * nx + sx];
@@ -252,7 +274,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
         }
         int64_t tn = t + 1; /* time of the state now held in f */
         if (c->qoi_every > 0 && tn % c->qoi_every == 0) {
-            if (c->kind == ORACLE_TGV) {
+            if (c->kind != ORACLE_CHANNEL) {
                 if (o->series && nseries < o->series_len)
                     o->series[nseries++] = kinetic_energy(c, f, solid);
             } else {

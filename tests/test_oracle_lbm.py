@@ -141,3 +141,39 @@ def test_cylinder_drag_loose_anchor():
     assert r.steps_run < 40000                       # reached the steady-state criterion
     assert abs(r.cd - cd_paper) / cd_paper < 0.10, r.cd
     assert abs(r.cl) < 0.05 * r.cd                   # small lift from the 0.2 vs 0.205 offset
+
+
+def test_perturbed_tgv_without_perturbation_is_a_tiled_shifted_tgv():
+    """Sec. 8.3 initial field with zeta = 0 on N nodes is the Sec. 8.2 field on N/2 nodes, tiled
+    2 x 2 and shifted by N/8 (-cos a sin b = sin(a - pi/2) cos(b - pi/2), and the pressure
+    -(cos 4x + cos 4y)/4 maps onto +(cos 2kx + cos 2ky)/4); BGK streaming is translation-covariant,
+    so the evolved fields agree to round-off."""
+    n, steps, nu, u0 = 32, 150, 0.03, 0.04
+    a = lbm.run([lbm.Case(lbm.TGV_PERTURBED, n, n, steps, nu, u0, u_ref=u0)])[0]
+    b = lbm.run([lbm.Case(lbm.TGV, n // 2, n // 2, steps, nu, u0, u_ref=u0)])[0]
+    s = n // 8
+    bu = np.roll(np.roll(np.tile(b.u, (2, 2)), s, axis=0), s, axis=1)
+    bv = np.roll(np.roll(np.tile(b.v, (2, 2)), s, axis=0), s, axis=1)
+    assert np.abs(a.u - bu).max() < 1e-14 and np.abs(a.v - bv).max() < 1e-14
+    assert abs(a.k_final - b.k_final) < 1e-13
+
+
+@pytest.mark.parametrize("which,linear", [(0, 0.0), (1, 0.0), (2, 0.0), (3, -0.125)])
+def test_perturbed_tgv_initial_energy_closed_form(which, linear):
+    """K(0) u_ref^2 = u0^2 + c u0 zeta + zeta^2/64 for a single perturbation amplitude zeta_ij,
+    from the lattice sums of products of sin/cos(2x), sin/cos(4x) (N > 8): only the cos-cos
+    mode (i = j = 1) correlates with the base field, giving c = -1/8."""
+    n, u0, z = 32, 0.04, 0.02
+    pert = [0.0] * 4
+    pert[which] = z
+    r = lbm.run([lbm.Case(lbm.TGV_PERTURBED, n, n, 0, 0.03, u0, u_ref=1.0, pert=tuple(pert))])[0]
+    assert abs(r.k_final - (u0 * u0 + linear * u0 * z + z * z / 64)) < 1e-15
+
+
+def test_perturbed_tgv_conserves_mass():
+    r = lbm.run([lbm.Case(lbm.TGV_PERTURBED, 24, 24, 300, 0.02, 0.05, u_ref=0.05,
+                          pert=(0.01, -0.02, 0.015, 0.005))])[0]
+    # initial mass: sum of 1 + 3p with p quadratic in U; compare with the state after 300 steps
+    r0 = lbm.run([lbm.Case(lbm.TGV_PERTURBED, 24, 24, 0, 0.02, 0.05, u_ref=0.05,
+                           pert=(0.01, -0.02, 0.015, 0.005))])[0]
+    assert abs(r.mass - r0.mass) < 1e-12 * r0.mass

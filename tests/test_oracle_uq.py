@@ -234,3 +234,16 @@ def test_halton_radical_inverse_and_rate():
     errs = [abs(f(uq.halton(int(n), 2)).mean() - exact) for n in ns]
     slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
     assert slope < -0.8, slope
+
+
+def test_wasserstein1_exact_cases_and_library_cross_check():
+    from scipy.stats import wasserstein_distance
+
+    assert uq.wasserstein1([0.0, 1.0], [0.0, 1.0]) == 0.0
+    assert uq.wasserstein1([0.0], [1.0]) == 1.0
+    rng = np.random.default_rng(4)
+    a = rng.normal(size=500)
+    assert abs(uq.wasserstein1(a, a + 0.3) - 0.3) < 1e-12          # pure shift
+    b = rng.exponential(size=333)
+    assert abs(uq.wasserstein1(a, b) - wasserstein_distance(a, b)) < 1e-12
+    assert abs(uq.wasserstein1(a, b) - uq.wasserstein1(b, a)) < 1e-12

@@ -29,7 +29,7 @@ METRIC = "ensemble MLUPS (tgv256_gpc4d: 625 samples x 256^2 x 2000 steps, FP32 s
 UNIT = "MLUPS"
 BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
 # version tag of the step kernel whose ncu traffic profiles/step_kernel_f32_tgv256.md records
-STEP_KERNEL_VERSION = "aa-npt-nbr"
+STEP_KERNEL_VERSION = "aa-npt-nbr-pair"
 
 
 def _peaks():
@@ -343,6 +343,47 @@ def bench_workload(args):
             mr, vr = ouq.gpc_mean_var(c_ref)
             line["mean_rel_l2"] = _rel(mean.cpu().numpy(), mr)
             line["std_rel_l2"] = _rel(np.sqrt(var.cpu().numpy()), np.sqrt(vr))
+    elif args.workload == "tgv_paper4d":
+        # Sec. 8.3 study: 137-sample Smolyak ensembles at several resolutions to T_max = 100, W1 of
+        # the |u| distributions against the finest resolution at t = 0.2, 0.4, ..., 1.0 T_max.
+        res_list = [int(x) for x in args.resolutions.split(",")]
+        ref_n = max(res_list)
+        fracs = [0.2, 0.4, 0.6, 0.8, 1.0]
+        snaps, timing = {}, {}
+        for n in res_list:
+            pconv = U.uqlb_unit_converter(n, 1.6 / n, 40.0 * n)
+            total = int(round(args.t_max / pconv["dt"]))
+            w = W.tgv_paper4d(n, pconv["tau"], pconv["u_lattice"], total, storage=args.storage)
+            ens.setup(w)
+            base = ens.ensemble_samples(w)
+            marks = [int(round(f * total)) for f in fracs]
+            snaps[n] = []
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            prev = 0
+            for m in marks:
+                for smp_ in base:
+                    smp_.steps = m
+                r = ens.run_batch(base, storage=args.storage, fields_dtype="f32", start_step=prev)
+                snaps[n].append(r["fields"].clone())
+                prev = m
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            upd = len(base) * (n - 1) ** 2 * total
+            timing[n] = {"samples": len(base), "lattice": n - 1, "steps": total, "tau": pconv["tau"],
+                         "seconds": sec, "value": upd / sec / 1e6, "seconds_per_sample": sec / len(base)}
+        line["resolutions"] = timing
+        line["w1_vs_finest"] = {}
+        for n in res_list:
+            if n == ref_n:
+                continue
+            row = []
+            for k in range(len(fracs)):
+                d, bound = ens.w1_speed(snaps[n][k], (n - 1) ** 2, snaps[ref_n][k], (ref_n - 1) ** 2)
+                row.append({"t": fracs[k] * args.t_max, "w1": d, "bound": bound})
+            line["w1_vs_finest"][str(n)] = row
+        line["value"] = timing[ref_n]["value"]
     elif args.workload == "uneven":
         specs = W.uneven_batch()
         smp = [sample_struct(s) for s in specs]
@@ -552,7 +593,9 @@ def main():
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
     ap.add_argument("--workload", default="tgv256_gpc4d",
-                    choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "uneven"])
+                    choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "uneven", "tgv_paper4d"])
+    ap.add_argument("--resolutions", default="8,16,32,64,128,256", help="tgv_paper4d: resolutions n")
+    ap.add_argument("--t-max", type=float, default=100.0, help="tgv_paper4d: final physical time")
     ap.add_argument("--oracle-samples", type=int, default=4, help="oracle reference subset (other workloads)")
     ap.add_argument("--storages", default="", help="further storage formats to run on the same workload")
     ap.add_argument("--nd", type=int, default=20, help="cylinder: nodes per diameter")

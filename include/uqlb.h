@@ -55,9 +55,18 @@ enum { UQLB_BASIS_TOTAL = 0, UQLB_BASIS_TENSOR = 1 };
  * total degree 2k + 1 exactly; 4 inputs at level 3 give the paper's 137 points). */
 enum { UQLB_QUAD_GAUSS_LEGENDRE_TENSOR = 0, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 1 };
 enum { UQLB_METHOD_NONE = 0, UQLB_METHOD_MC = 1, UQLB_METHOD_GPC = 2 };
-enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1 };
+enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1, UQLB_CASE_TGV_PERTURBED = 2 };
 /* Parameters an uncertain input dimension may drive (uqlb_case.param_of_dim). */
-enum { UQLB_PARAM_NU = 0, UQLB_PARAM_U0 = 1, UQLB_PARAM_ZETA2 = 2, UQLB_PARAM_ZETA3 = 3 };
+enum {
+    UQLB_PARAM_NU = 0,
+    UQLB_PARAM_U0 = 1,
+    UQLB_PARAM_ZETA2 = 2,
+    UQLB_PARAM_ZETA3 = 3,
+    UQLB_PARAM_PERT00 = 4, /* perturbed TGV amplitudes zeta_ij, relative to the sample's u0 */
+    UQLB_PARAM_PERT01 = 5,
+    UQLB_PARAM_PERT10 = 6,
+    UQLB_PARAM_PERT11 = 7
+};
 /* Number formats: population storage, field outputs, projection inputs. */
 enum { UQLB_F64 = 0, UQLB_F32 = 1, UQLB_F16 = 2, UQLB_BF16 = 3 };
 /* Rounding of 16-bit population stores.  Stochastic rounding (seeded by sample, node and step,
@@ -99,6 +108,9 @@ typedef struct {
  *     sample stops once |C_D(t) - C_D(t - qoi_every)| < steady_tol |C_D(t)| holds at
  *     steady_checks consecutive checks (FP32 resolves C_D to ~1e-7, so a tolerance below that
  *     needs several checks to avoid stopping on a chance coincidence).
+ *   TGV_PERTURBED (Sec. 8.3): periodic [0, 2 pi)^2 on nx x ny nodes x = 2 pi i / nx,
+ *     u = -U cos 2x sin 2y, v = U sin 2x cos 2y, U = u0 + 1/4 sum_ij pert[2i+j] k_i(4x) k_j(4y)
+ *     (k_0 = sin, k_1 = cos), p = -U^2/4 (cos 4x + cos 4y), rho = 1 + 3p; K(t) normalised by u_ref.
  * tau = 3 nu + 1/2 (Sec. 8.2), omega = 1 / tau. */
 typedef struct {
     int32_t kind;        /* UQLB_CASE_TGV or UQLB_CASE_CHANNEL */
@@ -112,12 +124,15 @@ typedef struct {
     double cyl_cx, cyl_cy, cyl_r; /* CHANNEL obstacle; cyl_r <= 0: none */
     int64_t ramp_steps;  /* CHANNEL inflow ramp length (0: none) */
     double steady_tol;   /* CHANNEL steady-state tolerance (0: run to the cap) */
+    double pert[4];      /* TGV_PERTURBED amplitudes zeta_00, zeta_01, zeta_10, zeta_11 (lattice units) */
 } uqlb_sample;
 
 /* Template of an ensemble: a uqlb_sample whose parameters are overridden per sample by
  * the uncertain inputs.  Input dimension d sets parameter param_of_dim[d]:
  *   UQLB_PARAM_NU -> nu;  UQLB_PARAM_U0 -> u0;
- *   UQLB_PARAM_ZETA2 / ZETA3 -> amp2 / amp3 = zeta * (the sample's u0). */
+ *   UQLB_PARAM_ZETA2 / ZETA3 -> amp2 / amp3 = zeta * (the sample's u0);
+ *   UQLB_PARAM_PERT00..11 -> pert[0..3] = zeta * (the sample's u0), i.e. zeta in units of u0 as in
+ *   Sec. 8.3, where u0 = 1 and zeta ~ U(-0.025, 0.025). */
 typedef struct {
     uqlb_sample base;
     int32_t param_of_dim[8];
@@ -136,6 +151,11 @@ typedef struct {
     int32_t tile_rows;        /* rows per tile (see above; 0: tuned or default) */
     int32_t nodes_per_thread; /* nodes per thread along x (see above; 0: tuned or default) */
     int32_t rounding;         /* 16-bit storage: UQLB_ROUND_AUTO (= stochastic), NEAREST or STOCHASTIC */
+    int64_t start_step;       /* 0: start from the initial field.  > 0: resume, i.e. continue the state
+                                 a previous run left in the same workspace after start_step steps
+                                 (same samples, options and workspace; each sample's `steps` is then
+                                 its new total).  The workspace can be saved and restored between the
+                                 two calls (checkpoint). */
 } uqlb_run_opts;
 
 /* ------------------------------------------------------------------------------------
@@ -157,6 +177,12 @@ int uqlb_num_multi_indices(int dim, int order, int basis, int64_t* k);
 
 /* Exponent set alpha[K x dim] ordered by |alpha|, then descending lexicographic order. */
 int uqlb_multi_indices(int dim, int order, int basis, int32_t* alpha);
+
+/* Lattice parameters of the Sec. 8.3 set-up (its table of simulation parameters): a domain of
+ * length 2 pi resolved by n nodes, dx = 2 pi / (n - 1), dt = (Ma / sqrt 3) dx, physical nu = 1/Re,
+ * tau = 3 nu dt / dx^2 + 1/2, lattice velocity of a unit physical velocity dt / dx.  n >= 2. */
+int uqlb_unit_converter(int n, double ma, double re, double* dx, double* dt, double* tau,
+                        double* u_lattice);
 
 /* Staircase obstacle mask of a CHANNEL sample, [ny x nx] bytes (1 = solid). */
 int uqlb_obstacle_mask(const uqlb_sample* s, uint8_t* mask);
@@ -280,6 +306,24 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
  * the loop; launches: kernels the whole run enqueued (init, steps, counter advances, finalize).
  * Synchronises on the end event.  Any output may be NULL. */
 int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches);
+
+/* ------------------------------------------------------------------------------------
+ * Statistical-solution distance (Sec. 8.3)
+ * ---------------------------------------------------------------------------------- */
+
+/* 1-Wasserstein distance between the empirical distributions of the speed |u| = sqrt(u^2 + v^2)
+ * over all samples and nodes of two field sets, e.g. two resolutions of one ensemble (Sec. 8.3:
+ * W1 of the numerical statistical solutions of |u|).  Set X is M_X[s_X x ld_X] in dtype_X (F64 or
+ * F32) with rows [u (nodes_X values), v (nodes_X values), ...] as uqlb_run_batch writes them.
+ * Both sets are binned into `bins` (1..2^24) equal bins over [0, largest speed of both]; the
+ * distance is the integral of |F_a - F_b| over those bins.  Binning moves each value by less
+ * than one bin, so the result is within one bin width (written to bound_host) of the exact
+ * distance.  Writes the distance to out_host; synchronises `stream`. */
+int uqlb_w1_workspace_bytes(int bins, size_t* bytes);
+int uqlb_w1_speed(uqlb_ctx* ctx, const void* a_dev, int dtype_a, int64_t s_a, int64_t nodes_a, int64_t ld_a,
+                  const void* b_dev, int dtype_b, int64_t s_b, int64_t nodes_b, int64_t ld_b, int bins,
+                  void* workspace_dev, size_t workspace_bytes, double* out_host, double* bound_host,
+                  void* stream);
 
 /* ------------------------------------------------------------------------------------
  * Postprocessing (Sec. 4, Algorithm 1 statistics)

@@ -238,6 +238,20 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
                 uy = -in.u0 * c1x * s1y - in.amp2 * c2x * s2y - in.amp3 * c3x * s3y;
                 const double pr = 0.25 * in.u0 * in.u0 * (c2x + c2y);
                 rho = 1.0 + 3.0 * pr;
+            } else if (sp.kind == UQLB_CASE_TGV_PERTURBED) {
+                // Sec. 8.3: base mode 2 with amplitude U = u0 + eps(x, y), perturbation modes 4
+                const InitDev& in = p.init[j];
+                double s2x, c2x, s2y, c2y;
+                sincospi(4.0 * x / sp.nx, &s2x, &c2x);
+                sincospi(4.0 * y / sp.ny, &s2y, &c2y);
+                const double s4x = 2.0 * s2x * c2x, c4x = 2.0 * c2x * c2x - 1.0;
+                const double s4y = 2.0 * s2y * c2y, c4y = 2.0 * c2y * c2y - 1.0;
+                const double eps = in.pert[0] * s4x * s4y + in.pert[1] * s4x * c4y + in.pert[2] * c4x * s4y +
+                                   in.pert[3] * c4x * c4y;
+                const double U = in.u0 + 0.25 * eps;
+                ux = -U * c2x * s2y;
+                uy = U * s2x * c2y;
+                rho = 1.0 - 0.75 * U * U * (c4x + c4y);
             }
             const double usq = ux * ux + uy * uy;
             S* base = arena + sp.f_off + (int64_t)y * sp.pitch + x;
@@ -609,6 +623,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
 
 __global__ void advance_kernel(int64_t* counter, int chunk) { *counter += chunk; }
 
+// Resuming a run: samples that have not stopped take their new step totals.
+__global__ void resume_kernel(KParams p) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.nsamples; j += gridDim.x * blockDim.x)
+        if (!p.done[j]) p.steps_run[j] = p.samples[j].steps;
+}
+
 KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs* o, int dt) {
     KParams p{};
     p.arena = b.arena;
@@ -735,16 +755,22 @@ cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt,
+cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt, int base_parity,
                         cudaStream_t s) {
     KParams p = make_params(b, g, &o, dt);
-    const bool odd = (dt & 1) != 0;
+    const bool odd = ((dt + base_parity) & 1) != 0;
     switch (g.storage) {
         case UQLB_F64: return launch_step_s<double>(p, g, odd, s);
         case UQLB_F32: return launch_step_s<float>(p, g, odd, s);
         case UQLB_F16: return launch_step_s<__half>(p, g, odd, s);
         default: return launch_step_s<__nv_bfloat16>(p, g, odd, s);
     }
+}
+
+cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
+    KParams p = make_params(b, g, nullptr, 0);
+    resume_kernel<<<(int)std::min<int64_t>((g.nsamples + 255) / 256, 1024), 256, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s) {

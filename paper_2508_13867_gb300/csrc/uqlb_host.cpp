@@ -53,6 +53,7 @@ struct uqlb_ctx {
     };
     std::vector<Tuned> tuned;
     int last_rows = 0, last_npt = 0;
+    int64_t start_step_host = 0;
 };
 
 namespace {
@@ -308,7 +309,7 @@ struct BatchPlan {
 
 int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
     char buf[256];
-    if (s.kind != UQLB_CASE_TGV && s.kind != UQLB_CASE_CHANNEL) {
+    if (s.kind != UQLB_CASE_TGV && s.kind != UQLB_CASE_CHANNEL && s.kind != UQLB_CASE_TGV_PERTURBED) {
         snprintf(buf, sizeof buf, "sample %lld: unknown kind %d", (long long)idx, s.kind);
     } else if (s.nx < 2 || s.ny < 2 || s.nx > 65536 || s.ny > 65536) {
         snprintf(buf, sizeof buf, "sample %lld: lattice %d x %d out of range", (long long)idx, s.nx, s.ny);
@@ -426,6 +427,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         P.init[j].u0 = s.u0;
         P.init[j].amp2 = s.amp2;
         P.init[j].amp3 = s.amp3;
+        for (int k = 0; k < 4; ++k) P.init[j].pert[k] = s.pert[k];
         P.steps_sorted[j] = (int32_t)s.steps;
         max_steps = std::max(max_steps, (int)s.steps);
     }
@@ -502,12 +504,13 @@ void key_put(std::vector<unsigned char>& k, const T& v) {
 
 // Captured chunk of `chunk` time steps plus the step-counter advance, cached per context.
 int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, const RunOutputs& O, int chunk,
-                cudaGraphExec_t* out) {
+                int parity, cudaGraphExec_t* out) {
     std::vector<unsigned char> key;
     key_put(key, B);
     key_put(key, G);
     key_put(key, O);
     key_put(key, chunk);
+    key_put(key, parity);
     for (auto& e : ctx->graphs) {
         if (e.key == key) {
             *out = e.exec;
@@ -522,7 +525,7 @@ int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, co
     err = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamBeginCapture");
     cudaError_t lerr = cudaSuccess;
-    for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) lerr = launch_step(B, G, O, dt, ctx->capture_stream);
+    for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
     if (lerr == cudaSuccess) lerr = launch_advance(B, chunk, ctx->capture_stream);
     cudaGraph_t graph = nullptr;
     err = cudaStreamEndCapture(ctx->capture_stream, &graph);
@@ -561,19 +564,24 @@ int check_ctx(uqlb_ctx* ctx) {
 void build_ensemble(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* out) {
     for (int64_t s = 0; s < ctx->S; ++s) {
         uqlb_sample r = c->base;
-        double zeta2 = NAN, zeta3 = NAN;
+        double zeta2 = NAN, zeta3 = NAN, pert[4] = {NAN, NAN, NAN, NAN};
         for (int d = 0; d < ctx->dim; ++d) {
             const double v = ctx->z[(size_t)s * ctx->dim + d];
-            switch (c->param_of_dim[d]) {
+            const int prm = c->param_of_dim[d];
+            switch (prm) {
                 case UQLB_PARAM_NU: r.nu = v; break;
                 case UQLB_PARAM_U0: r.u0 = v; break;
                 case UQLB_PARAM_ZETA2: zeta2 = v; break;
                 case UQLB_PARAM_ZETA3: zeta3 = v; break;
-                default: break;
+                default:
+                    if (prm >= UQLB_PARAM_PERT00 && prm <= UQLB_PARAM_PERT11) pert[prm - UQLB_PARAM_PERT00] = v;
+                    break;
             }
         }
         if (!std::isnan(zeta2)) r.amp2 = zeta2 * r.u0;
         if (!std::isnan(zeta3)) r.amp3 = zeta3 * r.u0;
+        for (int k = 0; k < 4; ++k)
+            if (!std::isnan(pert[k])) r.pert[k] = pert[k] * r.u0;
         out[s] = r;
     }
 }
@@ -582,8 +590,32 @@ int check_case(uqlb_ctx* ctx, const uqlb_case* c) {
     if (!c) return set_err(ctx, UQLB_ERR_ARG, "null case");
     if (ctx->S <= 0) return set_err(ctx, UQLB_ERR_STATE, "no sample set: call uqlb_init_mc or uqlb_init_gpc");
     for (int d = 0; d < ctx->dim; ++d)
-        if (c->param_of_dim[d] < UQLB_PARAM_NU || c->param_of_dim[d] > UQLB_PARAM_ZETA3)
+        if (c->param_of_dim[d] < UQLB_PARAM_NU || c->param_of_dim[d] > UQLB_PARAM_PERT11)
             return set_err(ctx, UQLB_ERR_ARG, "param_of_dim[%d] = %d is not a known parameter", d, c->param_of_dim[d]);
+    return 0;
+}
+
+const int kGeomRows[] = {2, 4, 8};
+const int kGeomNpt[] = {1, 2, 4};
+
+// Workspace of a batch: the planned layout, and with both geometry fields 0 the largest layout of
+// any compiled geometry (the autotuner may pick any of them later).
+int batch_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes, std::string& why) {
+    BatchPlan P;
+    if (int rc = plan_batch(samples, n, opts, P, why)) return rc;
+    size_t best = P.total;
+    if (opts->tile_rows == 0 && opts->nodes_per_thread == 0) {
+        for (int r : kGeomRows)
+            for (int q : kGeomNpt) {
+                uqlb_run_opts o = *opts;
+                o.tile_rows = r;
+                o.nodes_per_thread = q;
+                BatchPlan Q;
+                std::string ignore;
+                if (plan_batch(samples, n, &o, Q, ignore) == 0) best = std::max(best, Q.total);
+            }
+    }
+    *bytes = best;
     return 0;
 }
 
@@ -639,6 +671,17 @@ int uqlb_multi_indices(int dim, int order, int basis, int32_t* alpha) {
     std::vector<int32_t> v;
     enumerate_indices(dim, order, basis, v);
     std::memcpy(alpha, v.data(), v.size() * sizeof(int32_t));
+    return 0;
+}
+
+int uqlb_unit_converter(int n, double ma, double re, double* dx, double* dt, double* tau, double* u_lattice) {
+    if (n < 2 || !(ma > 0.0) || !(re > 0.0)) return set_err(nullptr, UQLB_ERR_ARG, "unit_converter: need n >= 2, Ma > 0, Re > 0");
+    const double h = 2.0 * M_PI / (n - 1);
+    const double k = ma / std::sqrt(3.0) * h;
+    if (dx) *dx = h;
+    if (dt) *dt = k;
+    if (tau) *tau = 3.0 * (1.0 / re) * k / (h * h) + 0.5;
+    if (u_lattice) *u_lattice = k / h;
     return 0;
 }
 
@@ -859,26 +902,10 @@ int uqlb_get_weight_matrix(const uqlb_ctx* ctx, double* w) {
     return 0;
 }
 
-const int kGeomRows[] = {2, 4, 8};
-const int kGeomNpt[] = {1, 2, 4};
-
 int uqlb_batch_workspace_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes) {
     if (!samples || !bytes || !opts) return set_err(nullptr, UQLB_ERR_ARG, "batch_workspace_bytes: null pointer");
-    BatchPlan P;
     std::string why;
-    if (int rc = plan_batch(samples, n, opts, P, why)) return set_err(nullptr, rc, "%s", why.c_str());
-    size_t best = P.total;
-    if (opts->tile_rows == 0 && opts->nodes_per_thread == 0) {
-        for (int r : kGeomRows)
-            for (int q : kGeomNpt) {
-                uqlb_run_opts o = *opts;
-                o.tile_rows = r;
-                o.nodes_per_thread = q;
-                BatchPlan Q;
-                if (plan_batch(samples, n, &o, Q, why) == 0) best = std::max(best, Q.total);
-            }
-    }
-    *bytes = best;
+    if (int rc = batch_bytes(samples, n, opts, bytes, why)) return set_err(nullptr, rc, "%s", why.c_str());
     return 0;
 }
 
@@ -949,7 +976,7 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
                     goto done;
                 }
                 for (int dt = 0; dt < trial_steps; ++dt)
-                    if ((e = launch_step(B, P.geom, O, dt, s))) {
+                    if ((e = launch_step(B, P.geom, O, dt, 0, s))) {
                         rc = cuda_fail(ctx, e, "autotune: step launch");
                         goto done;
                     }
@@ -1026,6 +1053,9 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
             return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_dtype must be F64 or F32");
     }
     if (opts->qoi_every < 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: qoi_every must be >= 0");
+    if (opts->start_step < 0 || opts->start_step > P.geom.max_steps)
+        return set_err(ctx, UQLB_ERR_ARG, "run_batch: start_step must be in [0, the largest step count]");
+    const bool resume = opts->start_step > 0;
     if ((series_dev || series_cl_dev) && opts->qoi_every > 0) {
         const int64_t need = P.geom.max_steps / opts->qoi_every + 1;
         if (series_ld < need) return set_err(ctx, UQLB_ERR_ARG, "run_batch: series_ld %lld < %lld", (long long)series_ld, (long long)need);
@@ -1044,10 +1074,13 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
         (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
                                                   cudaMemcpyHostToDevice, s))) ||
-        (e = cudaMemsetAsync(B.step_counter, 0, sizeof(int64_t), s)) ||
         (e = cudaMemsetAsync(B.active_flag, 0, sizeof(int32_t), s)) ||
-        (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s)))
+        (!resume && (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))))
         return cuda_fail(ctx, e, "run_batch: table upload");
+    // the device step counter starts at start_step (0 for a fresh run); ctx keeps the host copy alive
+    ctx->start_step_host = opts->start_step;
+    if ((e = cudaMemcpyAsync(B.step_counter, &ctx->start_step_host, sizeof(int64_t), cudaMemcpyHostToDevice, s)))
+        return cuda_fail(ctx, e, "run_batch: step counter");
 
     RunOutputs O{};
     O.fields = fields_dev;
@@ -1066,11 +1099,15 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     ctx->loop_timed = false;
     ctx->loop_steps = P.geom.max_steps;
     ctx->run_launches = 2;
-    if ((e = launch_init(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: init launch");
-    if (P.geom.max_steps > 0) {
+    if (!resume) {
+        if ((e = launch_init(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: init launch");
+    } else {
+        if ((e = launch_resume(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: resume launch");
+    }
+    if (P.geom.max_steps > opts->start_step) {
         cudaGraphExec_t exec = nullptr;
-        if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, &exec)) return rc;
-        const int64_t nchunks = (P.geom.max_steps + chunk - 1) / chunk;
+        if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, (int)(opts->start_step & 1), &exec)) return rc;
+        const int64_t nchunks = (P.geom.max_steps - opts->start_step + chunk - 1) / chunk;
         const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
         if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
         for (int64_t q = 0; q < nchunks; ++q) {
@@ -1116,15 +1153,13 @@ int uqlb_ensemble_samples(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* 
 }
 
 int uqlb_ensemble_workspace_bytes(const uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opts, size_t* bytes) {
-    if (!ctx || !c || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "ensemble_workspace_bytes: null pointer");
+    if (!ctx || !c || !bytes || !opts) return set_err(nullptr, UQLB_ERR_ARG, "ensemble_workspace_bytes: null pointer");
     if (int rc = check_case(const_cast<uqlb_ctx*>(ctx), c)) return rc;
     std::vector<uqlb_sample> smp(ctx->S);
     build_ensemble(ctx, c, smp.data());
-    BatchPlan P;
     std::string why;
-    if (int rc = plan_batch(smp.data(), ctx->S, opts, P, why))
+    if (int rc = batch_bytes(smp.data(), ctx->S, opts, bytes, why))
         return set_err(const_cast<uqlb_ctx*>(ctx), rc, "%s", why.c_str());
-    *bytes = P.total;
     return 0;
 }
 
@@ -1205,6 +1240,39 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
                              series_dev ? series_dev + q * series_ld : nullptr, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "run_plain_f64: launch");
     }
+    return 0;
+}
+
+int uqlb_w1_workspace_bytes(int bins, size_t* bytes) {
+    if (bins < 1 || bins > (1 << 24) || !bytes) return set_err(nullptr, UQLB_ERR_ARG, "w1_workspace_bytes: need 1 <= bins <= 2^24");
+    *bytes = align_up(256 + (size_t)2 * bins * sizeof(uint32_t), 256) + 256;
+    return 0;
+}
+
+int uqlb_w1_speed(uqlb_ctx* ctx, const void* a_dev, int dtype_a, int64_t s_a, int64_t nodes_a, int64_t ld_a,
+                  const void* b_dev, int dtype_b, int64_t s_b, int64_t nodes_b, int64_t ld_b, int bins,
+                  void* workspace_dev, size_t workspace_bytes, double* out_host, double* bound_host, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    size_t need = 0;
+    if (int rc = uqlb_w1_workspace_bytes(bins, &need)) return set_err(ctx, rc, "w1_speed: %s", g_last_error.c_str());
+    if (!a_dev || !b_dev || !workspace_dev || !out_host || s_a < 1 || s_b < 1 || nodes_a < 1 || nodes_b < 1 ||
+        ld_a < 2 * nodes_a || ld_b < 2 * nodes_b)
+        return set_err(ctx, UQLB_ERR_ARG, "w1_speed: bad arguments");
+    if ((dtype_a != UQLB_F64 && dtype_a != UQLB_F32) || (dtype_b != UQLB_F64 && dtype_b != UQLB_F32))
+        return set_err(ctx, UQLB_ERR_ARG, "w1_speed: dtype must be F64 or F32");
+    if (workspace_bytes < need) return set_err(ctx, UQLB_ERR_OOM, "w1_speed: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    if ((double)s_a * nodes_a > 4.0e9 || (double)s_b * nodes_b > 4.0e9)
+        return set_err(ctx, UQLB_ERR_ARG, "w1_speed: more than 4e9 values in one set");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* out_dev = reinterpret_cast<double*>(static_cast<char*>(workspace_dev) + need - 256);
+    cudaError_t e = launch_w1_speed(a_dev, dtype_a, s_a, nodes_a, ld_a, b_dev, dtype_b, s_b, nodes_b, ld_b, bins,
+                                    workspace_dev, out_dev, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "w1_speed: launch");
+    double r[2] = {0.0, 0.0};
+    if ((e = cudaMemcpyAsync(r, out_dev, sizeof r, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
+        return cuda_fail(ctx, e, "w1_speed: copy back");
+    *out_host = r[0];
+    if (bound_host) *bound_host = r[1];
     return 0;
 }
 

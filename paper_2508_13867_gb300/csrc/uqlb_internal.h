@@ -43,6 +43,7 @@ static_assert(sizeof(SampleDev) == 128, "SampleDev must stay 128 bytes");
 struct alignas(16) InitDev {
     double u0, amp2, amp3;
     double pad;
+    double pert[4];  // perturbed TGV amplitudes zeta_00, zeta_01, zeta_10, zeta_11
 };
 
 // Device pointers carved out of the caller's workspace for one batch run.
@@ -91,9 +92,11 @@ struct RunOutputs {
 
 // Launchers (lbm_kernels.cu).
 cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
+// Step dt of a chunk whose base step has parity base_parity (the AA parity of the launch).
 cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
-                        int dt, cudaStream_t s);
+                        int dt, int base_parity, cudaStream_t s);
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
+cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                             cudaStream_t s);
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
@@ -107,6 +110,11 @@ struct PlainSample {
 cudaError_t plain_run_sample(const PlainSample& p, double* f_a, double* f_b, uint8_t* solid,
                              double* partials, int64_t qoi_every, double* fields,
                              double* qoi_row, double* series_row, cudaStream_t s);
+
+// Wasserstein-1 of speed distributions (w1_kernels.cu); ws holds 256 + 2 * bins * 4 bytes,
+// out_dev two doubles (distance, bin width).
+cudaError_t launch_w1_speed(const void* a, int dta, int64_t sa, int64_t na, int64_t lda, const void* b, int dtb,
+                            int64_t sb, int64_t nb, int64_t ldb, int bins, void* ws, double* out_dev, cudaStream_t s);
 
 // Context accessors for entry points implemented outside uqlb_host.cpp.
 int ctx_projection_view(uqlb_ctx* ctx, const double** W, int* K, int64_t* S, int* device);

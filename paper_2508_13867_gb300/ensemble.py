@@ -11,12 +11,14 @@ from . import uqlb as U
 from .workloads import SampleSpec, Workload
 
 STORAGE = {"f64": U.UQLB_F64, "f32": U.UQLB_F32, "f16": U.UQLB_F16, "bf16": U.UQLB_BF16}
-PARAMS = {"nu": U.UQLB_PARAM_NU, "u0": U.UQLB_PARAM_U0, "zeta2": U.UQLB_PARAM_ZETA2, "zeta3": U.UQLB_PARAM_ZETA3}
+PARAMS = {"nu": U.UQLB_PARAM_NU, "u0": U.UQLB_PARAM_U0, "zeta2": U.UQLB_PARAM_ZETA2, "zeta3": U.UQLB_PARAM_ZETA3,
+          "pert00": U.UQLB_PARAM_PERT00, "pert01": U.UQLB_PARAM_PERT01, "pert10": U.UQLB_PARAM_PERT10,
+          "pert11": U.UQLB_PARAM_PERT11}
 
 
 def sample_struct(s: SampleSpec) -> U.uqlb_sample:
     return U.uqlb_sample(s.kind, s.nx, s.ny, s.steady_checks, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref,
-                         s.cyl_cx, s.cyl_cy, s.cyl_r, s.ramp_steps, s.steady_tol)
+                         s.cyl_cx, s.cyl_cy, s.cyl_r, s.ramp_steps, s.steady_tol, (U.c_double * 4)(*s.pert))
 
 
 def case_struct(w: Workload) -> U.uqlb_case:
@@ -31,9 +33,10 @@ ROUNDING = {"auto": U.UQLB_ROUND_AUTO, "nearest": U.UQLB_ROUND_NEAREST, "stochas
 
 
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
-                tile_rows: int = 0, nodes_per_thread: int = 0, rounding: str = "auto") -> U.uqlb_run_opts:
+                tile_rows: int = 0, nodes_per_thread: int = 0, rounding: str = "auto",
+                start_step: int = 0) -> U.uqlb_run_opts:
     return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows,
-                           nodes_per_thread, ROUNDING[rounding])
+                           nodes_per_thread, ROUNDING[rounding], start_step)
 
 
 def _stream() -> int:
@@ -113,9 +116,12 @@ class Ensemble:
     # ---- runs -------------------------------------------------------------------------
     def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
                   fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
-                  nodes_per_thread: int = 0, rounding: str = "auto", out: dict | None = None) -> dict:
-        """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series)."""
-        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread, rounding)
+                  nodes_per_thread: int = 0, rounding: str = "auto", start_step: int = 0,
+                  out: dict | None = None) -> dict:
+        """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series).  With
+        start_step > 0 the run continues the state left by the previous call (same samples)."""
+        opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread, rounding,
+                           start_step)
         nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
         ws = self.workspace(nbytes)
         n = len(samples)
@@ -142,6 +148,14 @@ class Ensemble:
         opts = opts_struct(storage, "f32", 0)
         ws = self.workspace(U.uqlb_batch_workspace_bytes(samples, opts))
         return U.uqlb_autotune(self.ctx, samples, opts, ws.data_ptr(), ws.numel(), trial_steps, _stream())
+
+    def w1_speed(self, a: torch.Tensor, nodes_a: int, b: torch.Tensor, nodes_b: int, bins: int = 1 << 20):
+        """W1 distance between the speed distributions of two field sets (and its error bound)."""
+        nb = U.uqlb_w1_workspace_bytes(bins)
+        ws = torch.empty(nb, dtype=torch.uint8, device=a.device)
+        code = lambda t: U.UQLB_F64 if t.dtype == torch.float64 else U.UQLB_F32  # noqa: E731
+        return U.uqlb_w1_speed(self.ctx, a.data_ptr(), code(a), a.shape[0], nodes_a, a.stride(0), b.data_ptr(),
+                               code(b), b.shape[0], nodes_b, b.stride(0), bins, ws.data_ptr(), nb, _stream())
 
     def run_plain_f64(self, samples, qoi_every: int = 0, series: bool = False, fields: bool = True) -> dict:
         nbytes = U.uqlb_plain_workspace_bytes(samples)

@@ -24,8 +24,9 @@ UQLB_DIST_UNIFORM = 0
 UQLB_BASIS_TOTAL, UQLB_BASIS_TENSOR = 0, 1
 UQLB_QUAD_GAUSS_LEGENDRE_TENSOR, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 0, 1
 UQLB_METHOD_NONE, UQLB_METHOD_MC, UQLB_METHOD_GPC = 0, 1, 2
-UQLB_CASE_TGV, UQLB_CASE_CHANNEL = 0, 1
-UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3 = 0, 1, 2, 3
+UQLB_CASE_TGV, UQLB_CASE_CHANNEL, UQLB_CASE_TGV_PERTURBED = 0, 1, 2
+(UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3, UQLB_PARAM_PERT00, UQLB_PARAM_PERT01,
+ UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
 UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16 = 0, 1, 2, 3
 UQLB_ROUND_AUTO, UQLB_ROUND_NEAREST, UQLB_ROUND_STOCHASTIC = 0, 1, 2
 (UQLB_QOI_K, UQLB_QOI_MASS, UQLB_QOI_MOMX, UQLB_QOI_MOMY, UQLB_QOI_CD, UQLB_QOI_CL, UQLB_QOI_STEPS,
@@ -46,7 +47,7 @@ class uqlb_sample(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("nx", c_int32), ("ny", c_int32), ("steady_checks", c_int32),
                 ("steps", c_int64), ("nu", c_double), ("u0", c_double), ("amp2", c_double),
                 ("amp3", c_double), ("u_ref", c_double), ("cyl_cx", c_double), ("cyl_cy", c_double),
-                ("cyl_r", c_double), ("ramp_steps", c_int64), ("steady_tol", c_double)]
+                ("cyl_r", c_double), ("ramp_steps", c_int64), ("steady_tol", c_double), ("pert", c_double * 4)]
 
 
 class uqlb_case(ctypes.Structure):
@@ -56,7 +57,7 @@ class uqlb_case(ctypes.Structure):
 class uqlb_run_opts(ctypes.Structure):
     _fields_ = [("storage", c_int32), ("fields_dtype", c_int32), ("qoi_every", c_int64),
                 ("chunk_steps", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
-                ("rounding", c_int32)]
+                ("rounding", c_int32), ("start_step", c_int64)]
 
 
 _P = ctypes.POINTER
@@ -66,6 +67,8 @@ _SIGNATURES = {
     "uqlb_num_multi_indices": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(c_int64)],
     "uqlb_multi_indices": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(c_int32)],
     "uqlb_obstacle_mask": [_P(uqlb_sample), _P(ctypes.c_uint8)],
+    "uqlb_unit_converter": [ctypes.c_int, c_double, c_double, _P(c_double), _P(c_double), _P(c_double),
+                            _P(c_double)],
     "uqlb_mean_host": [_P(c_double), c_int64, _P(c_double)],
     "uqlb_std_host": [_P(c_double), c_int64, ctypes.c_int, _P(c_double)],
     "uqlb_create": [_P(c_void_p), ctypes.c_int],
@@ -92,6 +95,9 @@ _SIGNATURES = {
     "uqlb_run_plain_f64": [c_void_p, _P(uqlb_sample), c_int64, c_int64, c_void_p, c_size_t, c_void_p, c_int64,
                            c_void_p, c_void_p, c_int64, c_void_p],
     "uqlb_last_loop_time": [c_void_p, _P(c_double), _P(c_int64), _P(c_int64)],
+    "uqlb_w1_workspace_bytes": [ctypes.c_int, _P(c_size_t)],
+    "uqlb_w1_speed": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_int64, c_void_p, ctypes.c_int, c_int64,
+                      c_int64, c_int64, ctypes.c_int, c_void_p, c_size_t, _P(c_double), _P(c_double), c_void_p],
     "uqlb_post_workspace_bytes": [c_void_p, _P(c_size_t)],
     "uqlb_project": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, c_size_t, c_void_p],
     "uqlb_project_noalloc": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p],
@@ -171,6 +177,13 @@ def uqlb_multi_indices(dim: int, order: int, basis: int = UQLB_BASIS_TOTAL) -> n
     a = np.zeros((k, dim), dtype=np.int32)
     _check(lib().uqlb_multi_indices(dim, order, basis, a.ctypes.data_as(_P(c_int32))))
     return a
+
+
+def uqlb_unit_converter(n: int, ma: float, re: float) -> dict:
+    dx, dt, tau, ul = c_double(), c_double(), c_double(), c_double()
+    _check(lib().uqlb_unit_converter(n, ma, re, ctypes.byref(dx), ctypes.byref(dt), ctypes.byref(tau),
+                                     ctypes.byref(ul)))
+    return {"dx": dx.value, "dt": dt.value, "tau": tau.value, "u_lattice": ul.value}
 
 
 def uqlb_obstacle_mask(sample: uqlb_sample) -> np.ndarray:
@@ -329,6 +342,23 @@ def uqlb_last_loop_time(ctx) -> tuple[float, int, int]:
     ms, st, la = c_double(), c_int64(), c_int64()
     _check(lib().uqlb_last_loop_time(ctx, ctypes.byref(ms), ctypes.byref(st), ctypes.byref(la)), ctx)
     return ms.value, st.value, la.value
+
+
+def uqlb_w1_workspace_bytes(bins: int) -> int:
+    b = c_size_t()
+    _check(lib().uqlb_w1_workspace_bytes(bins, ctypes.byref(b)))
+    return b.value
+
+
+def uqlb_w1_speed(ctx, a_dev: int, dtype_a: int, s_a: int, nodes_a: int, ld_a: int, b_dev: int, dtype_b: int,
+                  s_b: int, nodes_b: int, ld_b: int, bins: int, workspace_dev: int, workspace_bytes: int,
+                  stream=None) -> tuple[float, float]:
+    """(W1 distance of the speed distributions, its error bound = one bin width)."""
+    out, bound = c_double(), c_double()
+    _check(lib().uqlb_w1_speed(ctx, c_void_p(a_dev), dtype_a, s_a, nodes_a, ld_a, c_void_p(b_dev), dtype_b, s_b,
+                               nodes_b, ld_b, bins, c_void_p(workspace_dev), workspace_bytes, ctypes.byref(out),
+                               ctypes.byref(bound), _stream(stream)), ctx)
+    return out.value, bound.value
 
 
 def uqlb_post_workspace_bytes(ctx) -> int:

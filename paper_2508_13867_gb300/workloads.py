@@ -21,7 +21,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-TGV, CHANNEL = 0, 1
+TGV, CHANNEL, TGV_PERTURBED = 0, 1, 2
 U_REF = 0.01  # normaliser of the kinetic energy K(t)
 
 
@@ -43,6 +43,7 @@ class SampleSpec:
     ramp_steps: int = 0
     steady_tol: float = 0.0
     steady_checks: int = 1
+    pert: tuple = (0.0, 0.0, 0.0, 0.0)
 
 
 @dataclass
@@ -137,3 +138,25 @@ def random_fields(n_samples: int, n_fields: int, seed: int, dtype=np.float64) ->
 
 def with_steps(w: Workload, steps: int) -> Workload:
     return replace(w, base=replace(w.base, steps=steps))
+
+
+# The paper's own four-dimensional perturbed Taylor-Green set-up (Sec. 8.3): resolutions n with
+# Ma = 1.6 / n and Re = 40 n (its table of simulation parameters), T_max = 100, four amplitudes
+# zeta_ij ~ U(-0.025, 0.025) in units of u0 = 1.  The periodic lattice has n - 1 nodes per side
+# (dx = 2 pi / (n - 1) spans the period once); the lattice values come from uqlb_unit_converter.
+PERT4D_BOUNDS = [(-0.025, 0.025)] * 4
+PERT4D_PARAMS = ["pert00", "pert01", "pert10", "pert11"]
+
+
+def tgv_paper4d_params(n: int) -> tuple[float, float]:
+    """(Ma, Re) of resolution n in the paper's table."""
+    return 1.6 / n, 40.0 * n
+
+
+def tgv_paper4d(n: int, tau: float, u_lattice: float, steps: int, level: int = 3, order: int = 3,
+                storage: str = "f32") -> Workload:
+    """The Sec. 8.3 set-up on the Smolyak level-3 grid (137 samples); tau, the lattice velocity and
+    the step count come from the unit converter (lattice viscosity (tau - 1/2) / 3)."""
+    base = SampleSpec(TGV_PERTURBED, n - 1, n - 1, steps, (tau - 0.5) / 3.0, u_lattice, u_ref=u_lattice)
+    return Workload("tgv_paper4d", base, PERT4D_BOUNDS, PERT4D_PARAMS, "gpc", pts_per_dim=level, order=order,
+                    quad="smolyak", storage=storage)

@@ -340,3 +340,64 @@ def test_stochastic_rounding_is_reproducible_and_unbiased(ens):
         e_rn = rel_l2(fn[:-1], oracle_row(ref)[:-1])
         print(f"{st}: stochastic {e_sr:.3e} nearest {e_rn:.3e}")
         assert e_sr < e_rn, (st, e_sr, e_rn)
+
+
+def _paper4d_specs(n, steps, pert_sets):
+    p = U.uqlb_unit_converter(n, 1.6 / n, 40.0 * n)
+    nu = (p["tau"] - 0.5) / 3.0
+    return [W.SampleSpec(W.TGV_PERTURBED, n - 1, n - 1, steps, nu, p["u_lattice"], u_ref=p["u_lattice"],
+                         pert=tuple(z * p["u_lattice"] for z in zs)) for zs in pert_sets]
+
+
+def _oracle_pert(spec, qoi_every=0):
+    return olbm.Case(olbm.TGV_PERTURBED, spec.nx, spec.ny, spec.steps, spec.nu, spec.u0, u_ref=spec.u_ref,
+                     qoi_every=qoi_every, pert=spec.pert)
+
+
+def test_paper_perturbed_tgv_matches_oracle(ens):
+    """Sec. 8.3 set-up at n = 32 (31 x 31 lattice, Table parameters Ma = 0.05, Re = 1280), four
+    amplitudes per sample, FP64 and FP32 storage against the oracle."""
+    specs = _paper4d_specs(32, 400, [(0.02, -0.01, 0.015, -0.025), (-0.025, 0.0, 0.01, 0.02), (0, 0, 0, 0)])
+    ref = olbm.run([_oracle_pert(s, qoi_every=50) for s in specs])
+    for storage in ("f64", "f32"):
+        g = _run(ens, specs, storage, qoi_every=50, series=True)
+        for i, r in enumerate(ref):
+            assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL[storage], storage
+            assert np.allclose(g["series"][i, :9], r.series[:9], rtol=10 * TOL[storage], atol=0), storage
+
+
+@pytest.mark.parametrize("split", [37, 50])
+def test_resume_continues_the_run_exactly(ens, split):
+    """A run of `split` steps resumed to 100 steps equals a single 100-step run bit for bit
+    (odd and even split points; the workspace carries the state)."""
+    specs = _tgv_specs(40, 100) + [_cyl(4, 100, u_mean=0.04)]
+    whole = _run(ens, specs, "f64", qoi_every=10, series=True)
+    first = [sample_struct(s) for s in specs]
+    for s in first:
+        s.steps = split
+    ens.run_batch(first, storage="f64", fields_dtype="f64", fields=False)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f64", fields_dtype="f64", fields=False,
+                        start_step=split)
+    torch.cuda.synchronize()
+    q = res["qoi"].cpu().numpy()
+    assert np.array_equal(q, whole["qoi"])
+
+
+def test_w1_of_speed_distributions_matches_exact_within_bin_width(ens):
+    """GPU W1 between the |u| distributions of two ensembles (n = 16 and n = 32 of the Sec. 8.3
+    set-up) against the oracle's exact W1 of the same fields, within the stated bin-width bound."""
+    pert_sets = [(0.02, -0.01, 0.015, -0.025), (-0.025, 0.0, 0.01, 0.02), (0.01, 0.01, -0.02, 0.0)]
+    a_specs = _paper4d_specs(16, 200, pert_sets)
+    b_specs = _paper4d_specs(32, 800, pert_sets)
+    ga = ens.run_batch([sample_struct(s) for s in a_specs], storage="f64", fields_dtype="f64")
+    gb = ens.run_batch([sample_struct(s) for s in b_specs], storage="f64", fields_dtype="f64")
+    fa, fb = ga["fields"].clone(), gb["fields"].clone()
+    for bins in (1 << 10, 1 << 20):
+        w1, bound = ens.w1_speed(fa, 15 * 15, fb, 31 * 31, bins=bins)
+        ra = olbm.run([_oracle_pert(s) for s in a_specs])
+        rb = olbm.run([_oracle_pert(s) for s in b_specs])
+        sa = np.concatenate([np.hypot(r.u, r.v).ravel() for r in ra])
+        sb = np.concatenate([np.hypot(r.u, r.v).ravel() for r in rb])
+        exact = ouq.wasserstein1(sa, sb)
+        assert abs(w1 - exact) <= bound + 1e-12, (bins, w1, exact, bound)
+        assert bound <= max(sa.max(), sb.max()) / bins * (1 + 1e-9)

@@ -31,9 +31,9 @@ def test_library_exports_every_header_symbol():
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(U.uqlb_dist) == 24
-    assert ctypes.sizeof(U.uqlb_sample) == 104
-    assert ctypes.sizeof(U.uqlb_case) == 136
-    assert ctypes.sizeof(U.uqlb_run_opts) == 32
+    assert ctypes.sizeof(U.uqlb_sample) == 136
+    assert ctypes.sizeof(U.uqlb_case) == 168
+    assert ctypes.sizeof(U.uqlb_run_opts) == 40
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 17, 33, 64])
@@ -144,7 +144,7 @@ def test_argument_errors_return_status_codes():
     with pytest.raises(U.UqlbError):
         U.uqlb_batch_workspace_bytes([bad], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
     with pytest.raises(U.UqlbError):
-        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3, 1, 0))
+        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3, 1, 0, 0))
 
 
 def test_workspace_bytes_cover_the_arena():
@@ -190,5 +190,53 @@ def test_halton_sample_set_matches_oracle_bit_for_bit():
         assert np.allclose(a, 1 / 500, rtol=0, atol=0)
         with pytest.raises(U.UqlbError):
             U.uqlb_init_gpc(ctx, 2, 7, U.UQLB_BASIS_TOTAL, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+def test_unit_converter_matches_oracle_and_paper_table():
+    for n, ma, re in [(8, 0.2, 320), (64, 0.025, 2560), (256, 0.00625, 10240)]:
+        a = U.uqlb_unit_converter(n, ma, re)
+        b = ouq.unit_converter(n, ma, re)
+        for key in ("dx", "dt", "tau"):
+            assert abs(a[key] - b[key]) <= 1e-15 * abs(b[key])
+        assert abs(a["u_lattice"] - ma / math.sqrt(3)) < 1e-15
+
+
+def test_perturbation_parameters_map_to_the_sample():
+    ctx = U.uqlb_create(0)
+    try:
+        p = U.uqlb_unit_converter(32, 1.6 / 32, 40 * 32)
+        w = W.tgv_paper4d(32, p["tau"], p["u_lattice"], 100, level=1, order=1)
+        U.uqlb_set_inputs(ctx, w.bounds)
+        U.uqlb_init_gpc(ctx, 1, 1, U.UQLB_BASIS_TOTAL, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
+        smp = U.uqlb_ensemble_samples(ctx, case_struct(w))
+        z, _, _ = U.uqlb_get_samples(ctx, 4)
+        assert len(smp) == 9
+        for s, zz in zip(smp, z):
+            assert s.kind == U.UQLB_CASE_TGV_PERTURBED and (s.nx, s.ny) == (31, 31)
+            assert list(s.pert) == [v * p["u_lattice"] for v in zz]
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+def test_untuned_workspace_covers_every_geometry_for_every_entry_point():
+    """With geometry 0/0 the batch, ensemble and end-to-end workspace queries all cover every
+    compiled tile geometry, since an autotuned run may use any of them."""
+    ctx = U.uqlb_create(0)
+    try:
+        w = W.tgv256_gpc4d(n=96, steps=10, pts=2)
+        U.uqlb_set_inputs(ctx, w.bounds)
+        U.uqlb_init_gpc(ctx, 1, 2)
+        case = case_struct(w)
+        smp = U.uqlb_ensemble_samples(ctx, case)
+        auto = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0)
+        ens_b = U.uqlb_ensemble_workspace_bytes(ctx, case, auto)
+        assert ens_b == U.uqlb_batch_workspace_bytes(smp, auto)
+        assert U.uqlb_uq_workspace_bytes(ctx, case, auto) > ens_b
+        for tr in (2, 4, 8):
+            for npt in (1, 2, 4):
+                fixed = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, tr, npt, 0, 0)
+                assert U.uqlb_batch_workspace_bytes(smp, fixed) <= ens_b
     finally:
         U.uqlb_destroy(ctx)

@@ -180,12 +180,13 @@ def bench_kernel_only(args):
     out = {}
     for _ in range(args.warmup + args.steps):
         ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
-                      nodes_per_thread=args.npt, rounding=args.rounding)
+                      nodes_per_thread=args.npt, rounding=args.rounding, mode=args.mode)
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     nodes = sum(s.nx * s.ny for s in smp)
     gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st, 1) / 1e3) / 1e9
-    print(json.dumps({"kernel_only": True, "samples": len(smp), "time_steps": st, "storage": args.storage,
+    print(json.dumps({"kernel_only": True, "mode": args.mode, "samples": len(smp), "time_steps": st,
+                      "storage": args.storage,
                       "loop_ms": ms, "step_ms": ms / max(st, 1), "achieved_gbs": gbs,
                       "arena_bytes": BYTES_PER_UPDATE[args.storage] // 2 * nodes}))
     ens.close()
@@ -344,20 +345,23 @@ def bench_workload(args):
             line["mean_rel_l2"] = _rel(mean.cpu().numpy(), mr)
             line["std_rel_l2"] = _rel(np.sqrt(var.cpu().numpy()), np.sqrt(vr))
     elif args.workload == "tgv_paper4d":
-        # Sec. 8.3 study: 137-sample Smolyak ensembles at several resolutions to T_max = 100, W1 of
-        # the |u| distributions against the finest resolution at t = 0.2, 0.4, ..., 1.0 T_max.
+        # Sec. 8.3 study: ensembles at several resolutions n to T_max = 100 (Monte Carlo with N = n
+        # samples, or the Smolyak grid), W1 of the pooled |u| values against the finest resolution
+        # at t = 0.2, 0.4, ..., 1.0 T_max.  A snapshot in which a sample has gone unstable (rho <= 0
+        # or a non-finite velocity at some node) gets no distance: its fields are not a solution.
         res_list = [int(x) for x in args.resolutions.split(",")]
         ref_n = max(res_list)
         fracs = [0.2, 0.4, 0.6, 0.8, 1.0]
-        snaps, timing = {}, {}
+        snaps, unstable, timing = {}, {}, {}
         for n in res_list:
             pconv = U.uqlb_unit_converter(n, 1.6 / n, 40.0 * n)
             total = int(round(args.t_max / pconv["dt"]))
-            w = W.tgv_paper4d(n, pconv["tau"], pconv["u_lattice"], total, storage=args.storage)
+            w = W.tgv_paper4d(n, pconv["tau"], pconv["u_lattice"], total, sampling=args.sampling,
+                              storage=args.storage)
             ens.setup(w)
             base = ens.ensemble_samples(w)
             marks = [int(round(f * total)) for f in fracs]
-            snaps[n] = []
+            snaps[n], unstable[n] = [], []
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             prev = 0
@@ -366,13 +370,17 @@ def bench_workload(args):
                     smp_.steps = m
                 r = ens.run_batch(base, storage=args.storage, fields_dtype="f32", start_step=prev)
                 snaps[n].append(r["fields"].clone())
+                unstable[n].append(r["qoi"][:, U.UQLB_QOI_STATUS] == U.UQLB_ERR_UNSTABLE)
                 prev = m
             e1.record(stream)
             torch.cuda.synchronize()
             sec = e0.elapsed_time(e1) / 1e3
             upd = len(base) * (n - 1) ** 2 * total
+            unstable[n] = [int(u.sum().item()) for u in unstable[n]]
             timing[n] = {"samples": len(base), "lattice": n - 1, "steps": total, "tau": pconv["tau"],
-                         "seconds": sec, "value": upd / sec / 1e6, "seconds_per_sample": sec / len(base)}
+                         "seconds": sec, "value": upd / sec / 1e6, "seconds_per_sample": sec / len(base),
+                         "unstable_samples": dict(zip([f * args.t_max for f in fracs], unstable[n]))}
+        line["sampling"] = args.sampling
         line["resolutions"] = timing
         line["w1_vs_finest"] = {}
         for n in res_list:
@@ -380,8 +388,10 @@ def bench_workload(args):
                 continue
             row = []
             for k in range(len(fracs)):
-                d, bound = ens.w1_speed(snaps[n][k], (n - 1) ** 2, snaps[ref_n][k], (ref_n - 1) ** 2)
-                row.append({"t": fracs[k] * args.t_max, "w1": d, "bound": bound})
+                d, bound, nf = ens.w1_speed(snaps[n][k], (n - 1) ** 2, snaps[ref_n][k], (ref_n - 1) ** 2)
+                ok = unstable[n][k] == 0 and unstable[ref_n][k] == 0 and nf == (0, 0)
+                row.append({"t": fracs[k] * args.t_max, "w1": d if ok else None, "bound": bound if ok else None,
+                            "unstable_samples": unstable[n][k], "nonfinite_speeds": nf[0]})
             line["w1_vs_finest"][str(n)] = row
         line["value"] = timing[ref_n]["value"]
     elif args.workload == "uneven":
@@ -592,10 +602,14 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
+    ap.add_argument("--mode", default="graph", choices=["graph", "persistent"],
+                    help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")
     ap.add_argument("--workload", default="tgv256_gpc4d",
                     choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "uneven", "tgv_paper4d"])
     ap.add_argument("--resolutions", default="8,16,32,64,128,256", help="tgv_paper4d: resolutions n")
     ap.add_argument("--t-max", type=float, default=100.0, help="tgv_paper4d: final physical time")
+    ap.add_argument("--sampling", default="mc", choices=["mc", "smolyak"],
+                    help="tgv_paper4d: Monte Carlo with N = n samples, or the level-3 Smolyak grid")
     ap.add_argument("--oracle-samples", type=int, default=4, help="oracle reference subset (other workloads)")
     ap.add_argument("--storages", default="", help="further storage formats to run on the same workload")
     ap.add_argument("--nd", type=int, default=20, help="cylinder: nodes per diameter")

@@ -156,7 +156,19 @@ typedef struct {
                                  (same samples, options and workspace; each sample's `steps` is then
                                  its new total).  The workspace can be saved and restored between the
                                  two calls (checkpoint). */
+    int32_t mode;             /* UQLB_MODE_GRAPH or UQLB_MODE_PERSISTENT (see below) */
+    int32_t reserved;
 } uqlb_run_opts;
+
+/* Execution of the time loop.
+ *   UQLB_MODE_GRAPH: one launch per step, captured as CUDA graphs of chunk_steps launches.
+ *   UQLB_MODE_PERSISTENT: one cooperative launch per chunk runs all its steps; tiles are handed
+ *     out by a ticket counter (per-tile work queue) and steps are separated by a grid barrier
+ *     whose wait is bounded (2 s): if it runs out, every sample's status becomes
+ *     UQLB_ERR_TIMEOUT and uqlb_last_loop_time returns UQLB_ERR_TIMEOUT.
+ *   UQLB_MODE_PERSISTENT_TEST_TIMEOUT: test hook of the bounded wait; block 0 never arrives at
+ *     the barrier, so the run ends with UQLB_ERR_TIMEOUT after about 2 s. */
+enum { UQLB_MODE_GRAPH = 0, UQLB_MODE_PERSISTENT = 1, UQLB_MODE_PERSISTENT_TEST_TIMEOUT = 2 };
 
 /* ------------------------------------------------------------------------------------
  * Host building blocks (no device work)
@@ -300,7 +312,8 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
                        int64_t fields_ld, double* qoi_dev, double* series_dev, int64_t series_ld,
                        void* stream);
 
-/* Device time of the time loop of the last uqlb_run_batch / uqlb_run_ensemble on this context,
+/* Device time of the time loop of the last uqlb_run_batch / uqlb_run_ensemble on this context
+ * (returns UQLB_ERR_TIMEOUT if a bounded wait of a persistent run gave up),
  * measured with CUDA events recorded on the caller's stream around the graph launches of the
  * loop (so it covers the fused step kernels and nothing else of the run).  steps: time steps of
  * the loop; launches: kernels the whole run enqueued (init, steps, counter advances, finalize).
@@ -318,12 +331,14 @@ int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* laun
  * Both sets are binned into `bins` (1..2^24) equal bins over [0, largest speed of both]; the
  * distance is the integral of |F_a - F_b| over those bins.  Binning moves each value by less
  * than one bin, so the result is within one bin width (written to bound_host) of the exact
- * distance.  Writes the distance to out_host; synchronises `stream`. */
+ * distance.  Non-finite speeds (samples that became unstable) are left out and counted in
+ * nonfinite_host[0] / [1] (may be NULL); a set with no finite speed gives NaN.  Writes the
+ * distance to out_host; synchronises `stream`. */
 int uqlb_w1_workspace_bytes(int bins, size_t* bytes);
 int uqlb_w1_speed(uqlb_ctx* ctx, const void* a_dev, int dtype_a, int64_t s_a, int64_t nodes_a, int64_t ld_a,
                   const void* b_dev, int dtype_b, int64_t s_b, int64_t nodes_b, int64_t ld_b, int bins,
                   void* workspace_dev, size_t workspace_bytes, double* out_host, double* bound_host,
-                  void* stream);
+                  int64_t* nonfinite_host, void* stream);
 
 /* ------------------------------------------------------------------------------------
  * Postprocessing (Sec. 4, Algorithm 1 statistics)

@@ -45,6 +45,11 @@ struct KParams {
     int32_t* streak;
     const int64_t* step_counter;
     int32_t* n_done;
+    unsigned int* bar_count;
+    unsigned int* bar_gen;
+    int32_t* bar_err;
+    unsigned long long* tickets;
+    int32_t test_withhold;
     int32_t dt;
     int32_t max_steps;
     int32_t stochastic;  // 16-bit storage: stochastic rounding of every population store
@@ -401,107 +406,200 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
     }
 }
 
+// Shared state of one block while it processes a tile.
+template <int NT>
+struct TileShared {
+    int nact, ntiles, j, flag;
+    long long ticket;
+    double red[(NT / 32) * 3];
+    __align__(16) SampleDev sp;
+};
+
 // One tile = (32 NPT) columns x TR rows of one sample; thread (lane, row) owns the NPT nodes
 // x = x0 + lane + 32 k, so every warp-wide access of a population plane is contiguous.  All
 // NPT x 9 loads of a thread are issued before any arithmetic.
 // MIXED: the batch holds channel samples; each tile then branches on its own sample's kind.
 template <typename S, bool ODD, bool MIXED, int TR, int NPT>
-__global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
+__device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, int nact, bool k_step, bool f_step,
+                                             TileShared<kTileCols * TR>& sh) {
     using C = typename Storage<S>::C;
     constexpr int NT = kTileCols * TR;
-    __shared__ int s_nact, s_ntiles, s_j, s_flag;
-    __shared__ double s_red[(NT / 32) * 3];
-    __shared__ __align__(16) SampleDev s_sp;
-
-    const int t = (int)(*p.step_counter) + p.dt;
-    if (t >= p.max_steps) return;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const int nact = active_samples(p, t);
-        s_nact = nact;
-        s_ntiles = nact > 0 ? p.samples[nact - 1].tile_base + p.samples[nact - 1].tiles : 0;
+    if (threadIdx.y == 0) {  // warp 0 fetches the sample record (32 words) into shared memory
+        const int jj = tile_sample(p, tile, nact);
+        reinterpret_cast<uint32_t*>(&sh.sp)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint32_t*>(p.samples + jj) + threadIdx.x);
+        if (threadIdx.x == 0) sh.j = jj;
     }
     __syncthreads();
-    const int nact = s_nact, ntiles = s_ntiles;
-    const bool k_step = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
-    const bool f_step = MIXED && p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
-    S* arena = static_cast<S*>(p.arena);
-
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (threadIdx.y == 0) {  // warp 0 fetches the sample record (32 words) into shared memory
-            const int jj = tile_sample(p, tile, nact);
-            reinterpret_cast<uint32_t*>(&s_sp)[threadIdx.x] =
-                __ldg(reinterpret_cast<const uint32_t*>(p.samples + jj) + threadIdx.x);
-            if (threadIdx.x == 0) s_j = jj;
-        }
+    const int j = sh.j;
+    const SampleDev& sp = sh.sp;
+    const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
+    if (chan && p.done[j]) {
         __syncthreads();
-        const int j = s_j;
-        const SampleDev& sp = s_sp;
-        const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
-        if (chan && p.done[j]) {
-            __syncthreads();
-            continue;
-        }
-        const bool want_k = k_step && !chan;
-        const bool want_f = f_step && chan;
-        const int lt = tile - sp.tile_base;
-        const int x0 = (lt % sp.tiles_x) * (kTileCols * NPT) + threadIdx.x;
-        const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
-        const uint32_t* mask = (chan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
-        S* base = arena + sp.f_off;
+        return;
+    }
+    const bool want_k = k_step && !chan;
+    const bool want_f = f_step && chan;
+    const int lt = tile - sp.tile_base;
+    const int x0 = (lt % sp.tiles_x) * (kTileCols * NPT) + threadIdx.x;
+    const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
+    const uint32_t* mask = (chan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+    S* base = static_cast<S*>(p.arena) + sp.f_off;
 
-        C g[NPT][9];
-        bool act[NPT];
-        Nbr nb[NPT];
-        Nbr rows;
-        if (!chan && ODD) {
-            periodic_rows(sp, y, rows);
-        } else {
-            rows.row[1] = y * sp.pitch;
-        }
+    C g[NPT][9];
+    bool act[NPT];
+    Nbr nb[NPT];
+    Nbr rows;
+    if (!chan && ODD) {
+        periodic_rows(sp, y, rows);
+    } else {
+        rows.row[1] = y * sp.pitch;
+    }
 #pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-            const int x = x0 + kTileCols * k;
-            nb[k] = rows;
-            if (!chan && ODD) periodic_cols(sp, x, nb[k]);
-            act[k] = x < sp.nx && y < sp.ny;
-            if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, sp.mask_words, x, y);
-            if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, nb[k], g[k]);
-        }
-        double red[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + kTileCols * k;
+        nb[k] = rows;
+        if (!chan && ODD) periodic_cols(sp, x, nb[k]);
+        act[k] = x < sp.nx && y < sp.ny;
+        if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, sp.mask_words, x, y);
+        if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, nb[k], g[k]);
+    }
+    double red[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-        for (int k = 0; k < NPT; ++k)
-            if (act[k])
-                node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, nb[k], g[k], red);
+    for (int k = 0; k < NPT; ++k)
+        if (act[k]) node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, nb[k], g[k], red);
 
-        if (want_k || want_f) {
-            double tot[3];
-            if (tile_reduce_last<3, NT>(p, sp, j, tile, red, tot, s_red, &s_flag)) {
-                if (threadIdx.x == 0 && threadIdx.y == 0) {
-                    if (want_k) {
-                        p.series[(int64_t)sp.sample_id * p.series_ld + t / p.qoi_every] = tot[0] * sp.u_ref_inv2;
-                    } else {
-                        const double cd = tot[1] * sp.force_norm, cl = tot[2] * sp.force_norm;
-                        const int64_t col = (t + 1) / p.qoi_every - 1;
-                        if (p.series) p.series[(int64_t)sp.sample_id * p.series_ld + col] = cd;
-                        if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
-                        if (sp.steady_tol > 0.0) {
-                            const double prev = p.cd_prev[j];
-                            const bool pass = !isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd);
-                            const int run = pass ? p.streak[j] + 1 : 0;
-                            p.streak[j] = run;
-                            if (run >= sp.steady_checks) {
-                                p.done[j] = 1;
-                                p.steps_run[j] = t + 1;
-                                atomicAdd(p.n_done, 1);
-                            }
-                            p.cd_prev[j] = cd;
+    if (want_k || want_f) {
+        double tot[3];
+        if (tile_reduce_last<3, NT>(p, sp, j, tile, red, tot, sh.red, &sh.flag)) {
+            if (threadIdx.x == 0 && threadIdx.y == 0) {
+                if (want_k) {
+                    p.series[(int64_t)sp.sample_id * p.series_ld + t / p.qoi_every] = tot[0] * sp.u_ref_inv2;
+                } else {
+                    const double cd = tot[1] * sp.force_norm, cl = tot[2] * sp.force_norm;
+                    const int64_t col = (t + 1) / p.qoi_every - 1;
+                    if (p.series) p.series[(int64_t)sp.sample_id * p.series_ld + col] = cd;
+                    if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
+                    if (sp.steady_tol > 0.0) {
+                        const double prev = p.cd_prev[j];
+                        const bool pass = !isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd);
+                        const int run = pass ? p.streak[j] + 1 : 0;
+                        p.streak[j] = run;
+                        if (run >= sp.steady_checks) {
+                            p.done[j] = 1;
+                            p.steps_run[j] = t + 1;
+                            atomicAdd(p.n_done, 1);
                         }
+                        p.cd_prev[j] = cd;
                     }
                 }
             }
-        } else {
-            __syncthreads();
         }
+    } else {
+        __syncthreads();
+    }
+}
+
+// Active samples and tiles of step t, published in shared memory by thread 0.
+template <int NT>
+__device__ __forceinline__ void step_extent(const KParams& p, int t, TileShared<NT>& sh) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const int nact = active_samples(p, t);
+        sh.nact = nact;
+        sh.ntiles = nact > 0 ? p.samples[nact - 1].tile_base + p.samples[nact - 1].tiles : 0;
+    }
+    __syncthreads();
+}
+
+// One launch per time step: a grid sized to the resident blocks strides over the active tiles.
+template <typename S, bool ODD, bool MIXED, int TR, int NPT>
+__global__ void __launch_bounds__(kTileCols* TR) step_kernel(KParams p) {
+    __shared__ TileShared<kTileCols * TR> sh;
+    const int t = (int)(*p.step_counter) + p.dt;
+    if (t >= p.max_steps) return;
+    step_extent(p, t, sh);
+    const int nact = sh.nact, ntiles = sh.ntiles;
+    const bool k_step = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
+    const bool f_step = MIXED && p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        process_tile<S, ODD, MIXED, TR, NPT>(p, t, tile, nact, k_step, f_step, sh);
+}
+
+// Wall-clock nanoseconds of the device.
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident).  The wait is bounded: after
+// kBarrierTimeoutNs without the last arrival the block records UQLB_ERR_TIMEOUT and every block
+// returns at its next barrier.  `arrive` = false withholds this block's arrival (test hook that
+// makes the other blocks' wait run out).
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ bool grid_barrier(const KParams& p, bool arrive) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned int* gen = p.bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        bool waited = true;
+        if (arrive && atomicAdd(p.bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(p.bar_count, 0u);
+            __threadfence();
+            atomicAdd(p.bar_gen, 1u);
+            waited = false;
+        }
+        if (waited) {
+            const unsigned long long start = globaltimer_ns();
+            while (*gen == g && *(volatile int*)p.bar_err == 0) {
+                if (globaltimer_ns() - start > kBarrierTimeoutNs) {
+                    atomicExch(p.bar_err, UQLB_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)p.bar_err == 0;
+}
+
+// Persistent mode: one cooperative launch runs `chunk` time steps.  Tiles are handed out by a
+// single ticket counter (the per-tile work queue): step t owns tickets [base_t, base_t + ntiles_t);
+// a block that draws a ticket of a later step keeps it across the barrier and processes it there.
+template <typename S, bool MIXED, int TR, int NPT>
+__global__ void __launch_bounds__(kTileCols* TR) persistent_kernel(KParams p, int chunk) {
+    __shared__ TileShared<kTileCols * TR> sh;
+    const int t0 = (int)(*p.step_counter);
+    long long base = 0, ticket = -1;
+    for (int dt = 0; dt < chunk; ++dt) {
+        const int t = t0 + dt;
+        if (t >= p.max_steps) break;
+        step_extent(p, t, sh);
+        const int nact = sh.nact, ntiles = sh.ntiles;
+        const bool k_step = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
+        const bool f_step = MIXED && p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
+        while (true) {
+            if (ticket < 0) {
+                if (threadIdx.x == 0 && threadIdx.y == 0) sh.ticket = (long long)atomicAdd(p.tickets, 1ull);
+                __syncthreads();
+                ticket = sh.ticket;
+                __syncthreads();
+            }
+            if (ticket >= base + ntiles) break;
+            const int tile = (int)(ticket - base);
+            if (t & 1)
+                process_tile<S, true, MIXED, TR, NPT>(p, t, tile, nact, k_step, f_step, sh);
+            else
+                process_tile<S, false, MIXED, TR, NPT>(p, t, tile, nact, k_step, f_step, sh);
+            ticket = -1;
+        }
+        base += ntiles;
+        const bool arrive = !(p.test_withhold && blockIdx.x == 0);
+        if (!grid_barrier(p, arrive)) return;
     }
 }
 
@@ -605,7 +703,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     q[UQLB_QOI_CD] = tot[4] * sp.force_norm;
                     q[UQLB_QOI_CL] = tot[5] * sp.force_norm;
                     q[UQLB_QOI_STEPS] = (double)T;
-                    q[UQLB_QOI_STATUS] = tot[6] > 0.0 ? (double)UQLB_ERR_UNSTABLE : 0.0;
+                    q[UQLB_QOI_STATUS] = *(volatile int*)p.bar_err != 0 ? (double)UQLB_ERR_TIMEOUT
+                                         : (tot[6] > 0.0 ? (double)UQLB_ERR_UNSTABLE : 0.0);
                 }
                 if (p.fields != nullptr) {
                     const int64_t at = (int64_t)sp.sample_id * p.fields_ld + 2 * (int64_t)sp.nx * sp.ny;
@@ -648,6 +747,11 @@ KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutp
     p.streak = b.streak;
     p.step_counter = b.step_counter;
     p.n_done = b.active_flag;
+    p.bar_count = b.bar_count;
+    p.bar_gen = b.bar_gen;
+    p.bar_err = b.bar_err;
+    p.tickets = b.tickets;
+    p.test_withhold = g.test_withhold;
     p.dt = dt;
     p.max_steps = g.max_steps;
     p.stochastic = g.stochastic;
@@ -764,6 +868,68 @@ cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const Run
         case UQLB_F32: return launch_step_s<float>(p, g, odd, s);
         case UQLB_F16: return launch_step_s<__half>(p, g, odd, s);
         default: return launch_step_s<__nv_bfloat16>(p, g, odd, s);
+    }
+}
+
+namespace {
+
+template <typename S, bool MIXED, int TR, int NPT>
+cudaError_t launch_persistent_geom(const KParams& p, int chunk, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, persistent_kernel<S, MIXED, TR, NPT>, kTileCols * TR, 0) !=
+                cudaSuccess || b < 1)
+            b = 1;
+        per_sm = b;
+    }
+    const int grid = per_sm * sm_count();
+    KParams pp = p;
+    int ch = chunk;
+    void* args[] = {&pp, &ch};
+    return cudaLaunchCooperativeKernel((const void*)persistent_kernel<S, MIXED, TR, NPT>, dim3(grid),
+                                       dim3(kTileCols, TR), args, 0, s);
+}
+
+#define UQLB_PGEOM(TR_, NPT_) \
+    if (g.tile_rows == TR_ && g.npt == NPT_) return launch_persistent_geom<S, MIXED, TR_, NPT_>(p, chunk, s);
+template <typename S, bool MIXED>
+cudaError_t launch_persistent_s(const KParams& p, const BatchGeometry& g, int chunk, cudaStream_t s) {
+    if constexpr (MIXED) {
+        UQLB_PGEOM(8, 1)
+        UQLB_PGEOM(4, 1)
+    } else if constexpr (sizeof(S) == 8) {
+        UQLB_PGEOM(8, 1)
+        UQLB_PGEOM(4, 1)
+        UQLB_PGEOM(4, 2)
+    } else {
+        UQLB_PGEOM(2, 1)
+        UQLB_PGEOM(4, 1)
+        UQLB_PGEOM(8, 1)
+        UQLB_PGEOM(2, 2)
+        UQLB_PGEOM(4, 2)
+        UQLB_PGEOM(8, 2)
+        UQLB_PGEOM(2, 4)
+        UQLB_PGEOM(4, 4)
+        UQLB_PGEOM(8, 4)
+    }
+    return cudaErrorInvalidConfiguration;
+}
+#undef UQLB_PGEOM
+
+}  // namespace
+
+cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int chunk,
+                              cudaStream_t s) {
+    KParams p = make_params(b, g, &o, 0);
+    const bool mixed = g.any_channel != 0;
+    switch (g.storage) {
+        case UQLB_F64: return mixed ? launch_persistent_s<double, true>(p, g, chunk, s) : launch_persistent_s<double, false>(p, g, chunk, s);
+        case UQLB_F32: return mixed ? launch_persistent_s<float, true>(p, g, chunk, s) : launch_persistent_s<float, false>(p, g, chunk, s);
+        case UQLB_F16: return mixed ? launch_persistent_s<__half, true>(p, g, chunk, s) : launch_persistent_s<__half, false>(p, g, chunk, s);
+        default:
+            return mixed ? launch_persistent_s<__nv_bfloat16, true>(p, g, chunk, s)
+                         : launch_persistent_s<__nv_bfloat16, false>(p, g, chunk, s);
     }
 }
 

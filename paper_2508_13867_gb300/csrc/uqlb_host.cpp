@@ -54,6 +54,7 @@ struct uqlb_ctx {
     std::vector<Tuned> tuned;
     int last_rows = 0, last_npt = 0;
     int64_t start_step_host = 0;
+    int32_t* bar_err = nullptr;  // device error word of the last run
 };
 
 namespace {
@@ -301,7 +302,7 @@ struct BatchPlan {
     std::vector<uint32_t> masks;
     size_t off_arena = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
            off_partials = 0, off_counters = 0, off_done = 0, off_steps_run = 0, off_cd_prev = 0,
-           off_step_counter = 0, off_flag = 0, off_streak = 0, total = 0;
+           off_step_counter = 0, off_flag = 0, off_streak = 0, off_sync = 0, total = 0;
     BatchGeometry geom{};
     int n_steady = 0;
     bool uniform_size = true;
@@ -455,6 +456,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.off_step_counter = take(sizeof(int64_t));
     P.off_flag = take(sizeof(int32_t));
     P.off_streak = take(sizeof(int32_t) * n);
+    P.off_sync = take(64);  // barrier count, generation, error word, ticket counter
     P.total = off;
 
     BatchGeometry& g = P.geom;
@@ -472,6 +474,12 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     g.stochastic = (eb == 2 && rounding != UQLB_ROUND_NEAREST) ? 1 : 0;
+    const int mode = o ? o->mode : UQLB_MODE_GRAPH;
+    if (mode < UQLB_MODE_GRAPH || mode > UQLB_MODE_PERSISTENT_TEST_TIMEOUT) {
+        why = "unknown execution mode";
+        return UQLB_ERR_ARG;
+    }
+    g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
     return 0;
 }
 
@@ -493,6 +501,10 @@ BatchBuffers carve(const BatchPlan& P, void* ws) {
     B.step_counter = reinterpret_cast<int64_t*>(b + P.off_step_counter);
     B.active_flag = reinterpret_cast<int32_t*>(b + P.off_flag);
     B.streak = reinterpret_cast<int32_t*>(b + P.off_streak);
+    B.bar_count = reinterpret_cast<unsigned int*>(b + P.off_sync);
+    B.bar_gen = reinterpret_cast<unsigned int*>(b + P.off_sync + 4);
+    B.bar_err = reinterpret_cast<int32_t*>(b + P.off_sync + 8);
+    B.tickets = reinterpret_cast<unsigned long long*>(b + P.off_sync + 16);
     return B;
 }
 
@@ -1075,6 +1087,7 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
                                                   cudaMemcpyHostToDevice, s))) ||
         (e = cudaMemsetAsync(B.active_flag, 0, sizeof(int32_t), s)) ||
+        (e = cudaMemsetAsync(B.bar_count, 0, 64, s)) ||
         (!resume && (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))))
         return cuda_fail(ctx, e, "run_batch: table upload");
     // the device step counter starts at start_step (0 for a fresh run); ctx keeps the host copy alive
@@ -1104,7 +1117,29 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     } else {
         if ((e = launch_resume(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: resume launch");
     }
-    if (P.geom.max_steps > opts->start_step) {
+    ctx->bar_err = B.bar_err;
+    if (P.geom.max_steps > opts->start_step && opts->mode != UQLB_MODE_GRAPH) {
+        // persistent: one cooperative launch per chunk, then the step counter advances
+        const int pchunk = opts->chunk_steps > 0 ? chunk : 1024;
+        const int64_t nchunks = (P.geom.max_steps - opts->start_step + pchunk - 1) / pchunk;
+        const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
+        if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+        for (int64_t q = 0; q < nchunks; ++q) {
+            if ((e = cudaMemsetAsync(B.tickets, 0, sizeof(unsigned long long), s)) ||
+                (e = launch_persistent(B, P.geom, O, pchunk, s)) || (e = launch_advance(B, pchunk, s)))
+                return cuda_fail(ctx, e, "run_batch: persistent launch");
+            ctx->run_launches += 2;
+            if (steady && q + 1 < nchunks) {
+                int32_t ndone = 0;
+                if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
+                    (e = cudaStreamSynchronize(s)))
+                    return cuda_fail(ctx, e, "run_batch: convergence check");
+                if (ndone >= P.n_steady) break;
+            }
+        }
+        if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+        ctx->loop_timed = true;
+    } else if (P.geom.max_steps > opts->start_step) {
         cudaGraphExec_t exec = nullptr;
         if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, (int)(opts->start_step & 1), &exec)) return rc;
         const int64_t nchunks = (P.geom.max_steps - opts->start_step + chunk - 1) / chunk;
@@ -1141,6 +1176,13 @@ int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* laun
                 return cuda_fail(ctx, e, "last_loop_time");
             *ms = f;
         }
+    }
+    if (ctx->bar_err && ctx->loop_timed) {
+        int32_t err = 0;
+        cudaError_t e;
+        if ((e = cudaEventSynchronize(ctx->loop_end)) || (e = cudaMemcpy(&err, ctx->bar_err, sizeof err, cudaMemcpyDeviceToHost)))
+            return cuda_fail(ctx, e, "last_loop_time: status");
+        if (err != 0) return set_err(ctx, UQLB_ERR_TIMEOUT, "last run: a bounded grid-barrier wait gave up");
     }
     return 0;
 }
@@ -1251,7 +1293,8 @@ int uqlb_w1_workspace_bytes(int bins, size_t* bytes) {
 
 int uqlb_w1_speed(uqlb_ctx* ctx, const void* a_dev, int dtype_a, int64_t s_a, int64_t nodes_a, int64_t ld_a,
                   const void* b_dev, int dtype_b, int64_t s_b, int64_t nodes_b, int64_t ld_b, int bins,
-                  void* workspace_dev, size_t workspace_bytes, double* out_host, double* bound_host, void* stream) {
+                  void* workspace_dev, size_t workspace_bytes, double* out_host, double* bound_host,
+                  int64_t* nonfinite_host, void* stream) {
     if (int rc = check_ctx(ctx)) return rc;
     size_t need = 0;
     if (int rc = uqlb_w1_workspace_bytes(bins, &need)) return set_err(ctx, rc, "w1_speed: %s", g_last_error.c_str());
@@ -1268,11 +1311,15 @@ int uqlb_w1_speed(uqlb_ctx* ctx, const void* a_dev, int dtype_a, int64_t s_a, in
     cudaError_t e = launch_w1_speed(a_dev, dtype_a, s_a, nodes_a, ld_a, b_dev, dtype_b, s_b, nodes_b, ld_b, bins,
                                     workspace_dev, out_dev, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "w1_speed: launch");
-    double r[2] = {0.0, 0.0};
+    double r[4] = {0.0, 0.0, 0.0, 0.0};
     if ((e = cudaMemcpyAsync(r, out_dev, sizeof r, cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s)))
         return cuda_fail(ctx, e, "w1_speed: copy back");
     *out_host = r[0];
     if (bound_host) *bound_host = r[1];
+    if (nonfinite_host) {
+        nonfinite_host[0] = (int64_t)r[2];
+        nonfinite_host[1] = (int64_t)r[3];
+    }
     return 0;
 }
 

@@ -61,6 +61,10 @@ struct BatchBuffers {
     int32_t* steps_run;      // [S]
     double* cd_prev;         // [S] previous C_D check
     int32_t* streak;         // [S] consecutive passing steady-state checks
+    unsigned int* bar_count; // persistent mode: grid barrier arrivals
+    unsigned int* bar_gen;   //   and generation
+    int32_t* bar_err;        //   nonzero once a bounded wait gave up (UQLB_ERR_TIMEOUT)
+    unsigned long long* tickets;  // persistent mode: tile ticket counter of the running chunk
     int64_t* step_counter;   // [1] base step of the running graph chunk
     int32_t* active_flag;    // [1] nonzero while any channel sample still runs
 };
@@ -75,7 +79,7 @@ struct BatchGeometry {
     int32_t any_channel;
     int32_t uniform_tiles;   // tiles per sample when every sample has the same size, else 0
     int32_t stochastic;      // 16-bit storage rounds stochastically
-    int32_t reserved;
+    int32_t test_withhold;   // persistent mode test hook: block 0 withholds its barrier arrival
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -97,6 +101,9 @@ cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const Run
                         int dt, int base_parity, cudaStream_t s);
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
 cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
+// Persistent mode: one cooperative launch runs `chunk` steps (tile tickets must be zero).
+cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int chunk,
+                              cudaStream_t s);
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                             cudaStream_t s);
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
@@ -112,7 +119,7 @@ cudaError_t plain_run_sample(const PlainSample& p, double* f_a, double* f_b, uin
                              double* qoi_row, double* series_row, cudaStream_t s);
 
 // Wasserstein-1 of speed distributions (w1_kernels.cu); ws holds 256 + 2 * bins * 4 bytes,
-// out_dev two doubles (distance, bin width).
+// out_dev four doubles (distance, bin width, non-finite speeds of set a and of set b).
 cudaError_t launch_w1_speed(const void* a, int dta, int64_t sa, int64_t na, int64_t lda, const void* b, int dtb,
                             int64_t sb, int64_t nb, int64_t ldb, int bins, void* ws, double* out_dev, cudaStream_t s);
 

@@ -6,7 +6,8 @@
 // over the binned CDFs is exact for the binned values, which differ from the true ones by less
 // than one bin width h, so |W1_binned - W1| < h.  Three kernels: the largest speed, the two
 // histograms (global atomics; the counts do not depend on their order), and one block that
-// scans the bins in a fixed order and sums |F_a - F_b| h in FP64.
+// scans the bins in a fixed order and sums |F_a - F_b| h in FP64.  Non-finite speeds (samples
+// that became unstable) are left out of both distributions and counted.
 #include <cmath>
 
 #include "uqlb_internal.h"
@@ -25,20 +26,28 @@ __device__ __forceinline__ double speed(const M* m, int64_t ld, int64_t nodes, i
 template <typename M>
 __global__ void max_speed_kernel(const M* m, int64_t S, int64_t nodes, int64_t ld, unsigned long long* vmax_bits) {
     double best = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S * nodes; i += (int64_t)gridDim.x * blockDim.x)
-        best = fmax(best, speed(m, ld, nodes, i));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S * nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = speed(m, ld, nodes, i);
+        if (isfinite(v)) best = fmax(best, v);
+    }
     for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
     // non-negative doubles order like their bit patterns
     if ((threadIdx.x & 31) == 0) atomicMax(vmax_bits, (unsigned long long)__double_as_longlong(best));
 }
 
+// Non-finite speeds (an unstable sample) are not binned; they are counted in *nonfinite.
 template <typename M>
 __global__ void speed_hist_kernel(const M* m, int64_t S, int64_t nodes, int64_t ld, const unsigned long long* vmax_bits,
-                                  int bins, unsigned int* counts) {
+                                  int bins, unsigned int* counts, unsigned long long* nonfinite) {
     const double vmax = __longlong_as_double((long long)*vmax_bits);
     const double scale = vmax > 0.0 ? bins / vmax : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S * nodes; i += (int64_t)gridDim.x * blockDim.x) {
-        int b = (int)(speed(m, ld, nodes, i) * scale);
+        const double v = speed(m, ld, nodes, i);
+        if (!isfinite(v)) {
+            atomicAdd(nonfinite, 1ull);
+            continue;
+        }
+        int b = (int)(v * scale);
         b = b < 0 ? 0 : (b >= bins ? bins - 1 : b);
         atomicAdd(counts + b, 1u);
     }
@@ -47,8 +56,10 @@ __global__ void speed_hist_kernel(const M* m, int64_t S, int64_t nodes, int64_t 
 constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) w1_scan_kernel(const unsigned int* ca, const unsigned int* cb, int bins,
-                                                                double na, double nb, const unsigned long long* vmax_bits,
-                                                                double* out) {
+                                                                double na_all, double nb_all,
+                                                                const unsigned long long* vmax_bits,
+                                                                const unsigned long long* nonfinite, double* out) {
+    const double na = na_all - (double)nonfinite[0], nb = nb_all - (double)nonfinite[1];
     __shared__ long long sa[kScanThreads], sb[kScanThreads];
     __shared__ double sred[kScanThreads / 32];
     const int t = threadIdx.x;
@@ -85,8 +96,10 @@ __global__ void __launch_bounds__(kScanThreads) w1_scan_kernel(const unsigned in
     if (t == 0) {
         double s = 0.0;
         for (int w = 0; w < kScanThreads / 32; ++w) s += sred[w];
-        out[0] = s;
+        out[0] = (na > 0.0 && nb > 0.0) ? s : NAN;
         out[1] = h;
+        out[2] = (double)nonfinite[0];
+        out[3] = (double)nonfinite[1];
     }
 }
 
@@ -98,8 +111,8 @@ cudaError_t launch_max(const M* m, int64_t S, int64_t nodes, int64_t ld, unsigne
 
 template <typename M>
 cudaError_t launch_hist(const M* m, int64_t S, int64_t nodes, int64_t ld, const unsigned long long* vmax, int bins,
-                        unsigned int* counts, cudaStream_t s) {
-    speed_hist_kernel<M><<<1216, 256, 0, s>>>(m, S, nodes, ld, vmax, bins, counts);
+                        unsigned int* counts, unsigned long long* nonfinite, cudaStream_t s) {
+    speed_hist_kernel<M><<<1216, 256, 0, s>>>(m, S, nodes, ld, vmax, bins, counts, nonfinite);
     return cudaGetLastError();
 }
 
@@ -108,6 +121,7 @@ cudaError_t launch_hist(const M* m, int64_t S, int64_t nodes, int64_t ld, const 
 cudaError_t launch_w1_speed(const void* a, int dta, int64_t sa, int64_t na, int64_t lda, const void* b, int dtb,
                             int64_t sb, int64_t nb, int64_t ldb, int bins, void* ws, double* out_dev, cudaStream_t s) {
     auto* vmax = static_cast<unsigned long long*>(ws);
+    auto* nonfinite = vmax + 1;  // two counters, one per set
     auto* ca = reinterpret_cast<unsigned int*>(static_cast<char*>(ws) + 256);
     unsigned int* cb = ca + bins;
     cudaError_t e;
@@ -118,13 +132,14 @@ cudaError_t launch_w1_speed(const void* a, int dta, int64_t sa, int64_t na, int6
     e = dtb == UQLB_F64 ? launch_max(static_cast<const double*>(b), sb, nb, ldb, vmax, s)
                         : launch_max(static_cast<const float*>(b), sb, nb, ldb, vmax, s);
     if (e) return e;
-    e = dta == UQLB_F64 ? launch_hist(static_cast<const double*>(a), sa, na, lda, vmax, bins, ca, s)
-                        : launch_hist(static_cast<const float*>(a), sa, na, lda, vmax, bins, ca, s);
+    e = dta == UQLB_F64 ? launch_hist(static_cast<const double*>(a), sa, na, lda, vmax, bins, ca, nonfinite, s)
+                        : launch_hist(static_cast<const float*>(a), sa, na, lda, vmax, bins, ca, nonfinite, s);
     if (e) return e;
-    e = dtb == UQLB_F64 ? launch_hist(static_cast<const double*>(b), sb, nb, ldb, vmax, bins, cb, s)
-                        : launch_hist(static_cast<const float*>(b), sb, nb, ldb, vmax, bins, cb, s);
+    e = dtb == UQLB_F64 ? launch_hist(static_cast<const double*>(b), sb, nb, ldb, vmax, bins, cb, nonfinite + 1, s)
+                        : launch_hist(static_cast<const float*>(b), sb, nb, ldb, vmax, bins, cb, nonfinite + 1, s);
     if (e) return e;
-    w1_scan_kernel<<<1, kScanThreads, 0, s>>>(ca, cb, bins, (double)(sa * na), (double)(sb * nb), vmax, out_dev);
+    w1_scan_kernel<<<1, kScanThreads, 0, s>>>(ca, cb, bins, (double)(sa * na), (double)(sb * nb), vmax, nonfinite,
+                                              out_dev);
     return cudaGetLastError();
 }
 

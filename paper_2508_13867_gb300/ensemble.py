@@ -30,13 +30,15 @@ def case_struct(w: Workload) -> U.uqlb_case:
 
 
 ROUNDING = {"auto": U.UQLB_ROUND_AUTO, "nearest": U.UQLB_ROUND_NEAREST, "stochastic": U.UQLB_ROUND_STOCHASTIC}
+MODES = {"graph": U.UQLB_MODE_GRAPH, "persistent": U.UQLB_MODE_PERSISTENT,
+         "persistent_test_timeout": U.UQLB_MODE_PERSISTENT_TEST_TIMEOUT}
 
 
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
                 tile_rows: int = 0, nodes_per_thread: int = 0, rounding: str = "auto",
-                start_step: int = 0) -> U.uqlb_run_opts:
+                start_step: int = 0, mode: str = "graph") -> U.uqlb_run_opts:
     return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows,
-                           nodes_per_thread, ROUNDING[rounding], start_step)
+                           nodes_per_thread, ROUNDING[rounding], start_step, MODES[mode], 0)
 
 
 def _stream() -> int:
@@ -116,12 +118,12 @@ class Ensemble:
     # ---- runs -------------------------------------------------------------------------
     def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
                   fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
-                  nodes_per_thread: int = 0, rounding: str = "auto", start_step: int = 0,
+                  nodes_per_thread: int = 0, rounding: str = "auto", start_step: int = 0, mode: str = "graph",
                   out: dict | None = None) -> dict:
         """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series).  With
         start_step > 0 the run continues the state left by the previous call (same samples)."""
         opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread, rounding,
-                           start_step)
+                           start_step, mode)
         nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
         ws = self.workspace(nbytes)
         n = len(samples)

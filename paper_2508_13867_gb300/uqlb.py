@@ -29,6 +29,7 @@ UQLB_CASE_TGV, UQLB_CASE_CHANNEL, UQLB_CASE_TGV_PERTURBED = 0, 1, 2
  UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
 UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16 = 0, 1, 2, 3
 UQLB_ROUND_AUTO, UQLB_ROUND_NEAREST, UQLB_ROUND_STOCHASTIC = 0, 1, 2
+UQLB_MODE_GRAPH, UQLB_MODE_PERSISTENT, UQLB_MODE_PERSISTENT_TEST_TIMEOUT = 0, 1, 2
 (UQLB_QOI_K, UQLB_QOI_MASS, UQLB_QOI_MOMX, UQLB_QOI_MOMY, UQLB_QOI_CD, UQLB_QOI_CL, UQLB_QOI_STEPS,
  UQLB_QOI_STATUS, UQLB_QOI_COLS) = range(9)
 
@@ -57,7 +58,7 @@ class uqlb_case(ctypes.Structure):
 class uqlb_run_opts(ctypes.Structure):
     _fields_ = [("storage", c_int32), ("fields_dtype", c_int32), ("qoi_every", c_int64),
                 ("chunk_steps", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
-                ("rounding", c_int32), ("start_step", c_int64)]
+                ("rounding", c_int32), ("start_step", c_int64), ("mode", c_int32), ("reserved", c_int32)]
 
 
 _P = ctypes.POINTER
@@ -97,7 +98,8 @@ _SIGNATURES = {
     "uqlb_last_loop_time": [c_void_p, _P(c_double), _P(c_int64), _P(c_int64)],
     "uqlb_w1_workspace_bytes": [ctypes.c_int, _P(c_size_t)],
     "uqlb_w1_speed": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_int64, c_void_p, ctypes.c_int, c_int64,
-                      c_int64, c_int64, ctypes.c_int, c_void_p, c_size_t, _P(c_double), _P(c_double), c_void_p],
+                      c_int64, c_int64, ctypes.c_int, c_void_p, c_size_t, _P(c_double), _P(c_double), _P(c_int64),
+                      c_void_p],
     "uqlb_post_workspace_bytes": [c_void_p, _P(c_size_t)],
     "uqlb_project": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, c_size_t, c_void_p],
     "uqlb_project_noalloc": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p],
@@ -352,13 +354,13 @@ def uqlb_w1_workspace_bytes(bins: int) -> int:
 
 def uqlb_w1_speed(ctx, a_dev: int, dtype_a: int, s_a: int, nodes_a: int, ld_a: int, b_dev: int, dtype_b: int,
                   s_b: int, nodes_b: int, ld_b: int, bins: int, workspace_dev: int, workspace_bytes: int,
-                  stream=None) -> tuple[float, float]:
-    """(W1 distance of the speed distributions, its error bound = one bin width)."""
-    out, bound = c_double(), c_double()
+                  stream=None) -> tuple[float, float, tuple[int, int]]:
+    """(W1 distance of the finite speeds, its error bound = one bin width, non-finite counts)."""
+    out, bound, nf = c_double(), c_double(), (c_int64 * 2)()
     _check(lib().uqlb_w1_speed(ctx, c_void_p(a_dev), dtype_a, s_a, nodes_a, ld_a, c_void_p(b_dev), dtype_b, s_b,
                                nodes_b, ld_b, bins, c_void_p(workspace_dev), workspace_bytes, ctypes.byref(out),
-                               ctypes.byref(bound), _stream(stream)), ctx)
-    return out.value, bound.value
+                               ctypes.byref(bound), nf, _stream(stream)), ctx)
+    return out.value, bound.value, (nf[0], nf[1])
 
 
 def uqlb_post_workspace_bytes(ctx) -> int:

@@ -153,10 +153,16 @@ def tgv_paper4d_params(n: int) -> tuple[float, float]:
     return 1.6 / n, 40.0 * n
 
 
-def tgv_paper4d(n: int, tau: float, u_lattice: float, steps: int, level: int = 3, order: int = 3,
-                storage: str = "f32") -> Workload:
-    """The Sec. 8.3 set-up on the Smolyak level-3 grid (137 samples); tau, the lattice velocity and
-    the step count come from the unit converter (lattice viscosity (tau - 1/2) / 3)."""
+def tgv_paper4d(n: int, tau: float, u_lattice: float, steps: int, sampling: str = "mc", n_samples: int = 0,
+                level: int = 3, order: int = 3, seed: int = 123456, storage: str = "f32") -> Workload:
+    """The Sec. 8.3 set-up at resolution n; tau, the lattice velocity and the step count come from
+    the unit converter (lattice viscosity (tau - 1/2) / 3).  sampling = "mc": N Monte Carlo draws
+    with N = n by default (the table of simulation parameters lets N grow with n, and the study's
+    convergence order is that of MCS); "smolyak": the Clenshaw-Curtis sparse grid of `level`
+    (137 points at level 3)."""
     base = SampleSpec(TGV_PERTURBED, n - 1, n - 1, steps, (tau - 0.5) / 3.0, u_lattice, u_ref=u_lattice)
-    return Workload("tgv_paper4d", base, PERT4D_BOUNDS, PERT4D_PARAMS, "gpc", pts_per_dim=level, order=order,
-                    quad="smolyak", storage=storage)
+    if sampling == "smolyak":
+        return Workload("tgv_paper4d", base, PERT4D_BOUNDS, PERT4D_PARAMS, "gpc", pts_per_dim=level, order=order,
+                        quad="smolyak", storage=storage)
+    return Workload("tgv_paper4d", base, PERT4D_BOUNDS, PERT4D_PARAMS, "mc", n_mc=n_samples or n, seed=seed,
+                    storage=storage)

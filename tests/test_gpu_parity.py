@@ -393,7 +393,8 @@ def test_w1_of_speed_distributions_matches_exact_within_bin_width(ens):
     gb = ens.run_batch([sample_struct(s) for s in b_specs], storage="f64", fields_dtype="f64")
     fa, fb = ga["fields"].clone(), gb["fields"].clone()
     for bins in (1 << 10, 1 << 20):
-        w1, bound = ens.w1_speed(fa, 15 * 15, fb, 31 * 31, bins=bins)
+        w1, bound, nonfinite = ens.w1_speed(fa, 15 * 15, fb, 31 * 31, bins=bins)
+        assert nonfinite == (0, 0)
         ra = olbm.run([_oracle_pert(s) for s in a_specs])
         rb = olbm.run([_oracle_pert(s) for s in b_specs])
         sa = np.concatenate([np.hypot(r.u, r.v).ravel() for r in ra])
@@ -401,3 +402,55 @@ def test_w1_of_speed_distributions_matches_exact_within_bin_width(ens):
         exact = ouq.wasserstein1(sa, sb)
         assert abs(w1 - exact) <= bound + 1e-12, (bins, w1, exact, bound)
         assert bound <= max(sa.max(), sb.max()) / bins * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_persistent_mode_matches_graph_mode(ens, storage):
+    """One cooperative launch per chunk with the ticket work queue gives the same results as one
+    launch per step: per-node arithmetic and per-tile reduction order are the same."""
+    specs = _tgv_specs(50, 77) + [W.tgv(32, 40, nu=0.05)]
+    a = _run(ens, specs, storage, qoi_every=7, series=True)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage=storage,
+                        fields_dtype="f64" if storage == "f64" else "f32", qoi_every=7, series=True,
+                        fields=False, mode="persistent", chunk_steps=16)
+    torch.cuda.synchronize()
+    assert np.array_equal(res["qoi"].cpu().numpy(), a["qoi"])
+    assert np.array_equal(res["series"].cpu().numpy(), a["series"], equal_nan=True)
+
+
+def test_persistent_mode_mixed_batch_and_steady_state(ens):
+    specs = [W.tgv(40, 150, nu=0.03), _cyl(4, 20000, u_mean=0.04, steady_tol=1e-6)]
+    a = _run(ens, specs, "f64", qoi_every=100, series=True)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f64", fields_dtype="f64", qoi_every=100,
+                        series=True, fields=False, mode="persistent", chunk_steps=512)
+    torch.cuda.synchronize()
+    assert np.array_equal(res["qoi"].cpu().numpy(), a["qoi"])
+    ref = olbm.run([oracle_case(specs[1], qoi_every=100)])[0]
+    assert res["qoi"][1, U.UQLB_QOI_STEPS].item() == ref.steps_run
+
+
+def test_bounded_barrier_wait_reports_timeout_and_context_survives(ens):
+    """Failure detection without a fault: the test hook withholds one block's barrier arrival, the
+    other blocks' bounded wait (2 s) runs out, every sample reports UQLB_ERR_TIMEOUT and the
+    loop-time query returns it; the same context then runs normally."""
+    specs = _tgv_specs(48, 30)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=False,
+                        mode="persistent_test_timeout", chunk_steps=8)
+    torch.cuda.synchronize()
+    assert np.all(res["qoi"][:, U.UQLB_QOI_STATUS].cpu().numpy() == U.UQLB_ERR_TIMEOUT)
+    with pytest.raises(U.UqlbError) as e:
+        U.uqlb_last_loop_time(ens.ctx)
+    assert e.value.status == U.UQLB_ERR_TIMEOUT
+    g = _run(ens, specs, "f64")
+    ref = olbm.run([oracle_case(s) for s in specs])
+    for i, r in enumerate(ref):
+        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f64"]
+        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0
+
+
+def test_w1_leaves_out_and_counts_non_finite_speeds(ens):
+    a = torch.tensor([[0.1, 0.2, float("nan"), 0.0, 0.0, 0.0]], dtype=torch.float64, device="cuda")
+    b = torch.tensor([[0.3, 0.0, 0.0, 0.0]], dtype=torch.float64, device="cuda")
+    w1, bound, nonfinite = ens.w1_speed(a, 3, b, 2, bins=1 << 16)
+    assert nonfinite == (1, 0)
+    assert abs(w1 - ouq.wasserstein1([0.1, 0.2], [0.3, 0.0])) <= bound + 1e-15

@@ -33,7 +33,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(U.uqlb_dist) == 24
     assert ctypes.sizeof(U.uqlb_sample) == 136
     assert ctypes.sizeof(U.uqlb_case) == 168
-    assert ctypes.sizeof(U.uqlb_run_opts) == 40
+    assert ctypes.sizeof(U.uqlb_run_opts) == 48
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 17, 33, 64])
@@ -144,7 +144,7 @@ def test_argument_errors_return_status_codes():
     with pytest.raises(U.UqlbError):
         U.uqlb_batch_workspace_bytes([bad], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
     with pytest.raises(U.UqlbError):
-        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3, 1, 0, 0))
+        U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(16, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 3, 1, 0, 0, 0, 0))
 
 
 def test_workspace_bytes_cover_the_arena():
@@ -207,7 +207,7 @@ def test_perturbation_parameters_map_to_the_sample():
     ctx = U.uqlb_create(0)
     try:
         p = U.uqlb_unit_converter(32, 1.6 / 32, 40 * 32)
-        w = W.tgv_paper4d(32, p["tau"], p["u_lattice"], 100, level=1, order=1)
+        w = W.tgv_paper4d(32, p["tau"], p["u_lattice"], 100, sampling="smolyak", level=1, order=1)
         U.uqlb_set_inputs(ctx, w.bounds)
         U.uqlb_init_gpc(ctx, 1, 1, U.UQLB_BASIS_TOTAL, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
         smp = U.uqlb_ensemble_samples(ctx, case_struct(w))
@@ -216,6 +216,24 @@ def test_perturbation_parameters_map_to_the_sample():
         for s, zz in zip(smp, z):
             assert s.kind == U.UQLB_CASE_TGV_PERTURBED and (s.nx, s.ny) == (31, 31)
             assert list(s.pert) == [v * p["u_lattice"] for v in zz]
+    finally:
+        U.uqlb_destroy(ctx)
+
+
+def test_paper_study_draws_n_monte_carlo_samples_at_resolution_n():
+    ctx = U.uqlb_create(0)
+    try:
+        for n in (8, 32):
+            p = U.uqlb_unit_converter(n, 1.6 / n, 40 * n)
+            w = W.tgv_paper4d(n, p["tau"], p["u_lattice"], 10)
+            assert w.method == "mc" and w.n_mc == n
+            U.uqlb_set_inputs(ctx, w.bounds)
+            U.uqlb_init_mc(ctx, w.n_mc, w.seed)
+            smp = U.uqlb_ensemble_samples(ctx, case_struct(w))
+            z, _, _ = U.uqlb_get_samples(ctx, 4)
+            zr, _ = ouq.mc_samples(n, w.bounds, w.seed)
+            assert len(smp) == n and np.array_equal(z, zr)
+            assert all(abs(v) <= 0.025 * p["u_lattice"] for s in smp for v in s.pert)
     finally:
         U.uqlb_destroy(ctx)
 
@@ -230,13 +248,13 @@ def test_untuned_workspace_covers_every_geometry_for_every_entry_point():
         U.uqlb_init_gpc(ctx, 1, 2)
         case = case_struct(w)
         smp = U.uqlb_ensemble_samples(ctx, case)
-        auto = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0)
+        auto = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, 0)
         ens_b = U.uqlb_ensemble_workspace_bytes(ctx, case, auto)
         assert ens_b == U.uqlb_batch_workspace_bytes(smp, auto)
         assert U.uqlb_uq_workspace_bytes(ctx, case, auto) > ens_b
         for tr in (2, 4, 8):
             for npt in (1, 2, 4):
-                fixed = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, tr, npt, 0, 0)
+                fixed = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, tr, npt, 0, 0, 0, 0)
                 assert U.uqlb_batch_workspace_bytes(smp, fixed) <= ens_b
     finally:
         U.uqlb_destroy(ctx)

@@ -394,6 +394,50 @@ def bench_workload(args):
                             "unstable_samples": unstable[n][k], "nonfinite_speeds": nf[0]})
             line["w1_vs_finest"][str(n)] = row
         line["value"] = timing[ref_n]["value"]
+    elif args.workload == "cylinder_uq_compare":
+        # Sec. 8.1 comparison of UQ methods on the cylinder at nd nodes per diameter: MC and QMC
+        # (Halton) with N = 10 ... 100 samples against the SC-gPC reference (11 Gauss-Legendre
+        # points, order 5), mean and standard deviation of the steady C_D, plus the deterministic
+        # C_D at the nominal inflow.  MC and QMC sets of size N are prefixes of one sequence, so
+        # one batch holds every sample.
+        n_list = [int(x) for x in args.compare_n.split(",")]
+        n_max = max(n_list)
+        st = args.storage if args.storage != "f32" else "f64"
+        mk = lambda method, n: W.cylinder_uq(args.nd, method=method, n=n, spread=args.inflow_spread, storage=st)
+        w_sc, w_mc, w_qmc = mk("gpc", 11), mk("mc", n_max), mk("qmc", n_max)
+        groups = {}
+        for name, w in (("sc", w_sc), ("mc", w_mc), ("qmc", w_qmc)):
+            ens.setup(w)
+            groups[name] = ens.ensemble_samples(w)
+        det = W.channel(args.nd, steps=w_sc.base.steps, steady_tol=w_sc.base.steady_tol)
+        det.steady_checks = w_sc.base.steady_checks
+        smp = groups["sc"] + groups["mc"] + groups["qmc"] + [sample_struct(det)]
+        ms, r = timed(lambda: ens.run_batch(smp, storage=st, fields=False, qoi_every=100), 1)
+        q = r["qoi"]
+        cd = q[:, U.UQLB_QOI_CD].contiguous()
+        o_sc, o_mc, o_qmc = 0, len(groups["sc"]), len(groups["sc"]) + len(groups["mc"])
+        ens.setup(w_sc)
+        m_sc, v_sc = ens.stats(ens.project(cd[o_sc:o_mc].reshape(-1, 1)))
+        ref = (float(m_sc[0]), float(v_sc[0]) ** 0.5)
+        table = {"sc_gpc": {"n": len(groups["sc"]), "order": w_sc.order, "mean": ref[0], "std": ref[1]}}
+        for name, off, init in (("mc", o_mc, lambda n: ens.init_mc(n, w_mc.seed)), ("qmc", o_qmc, ens.init_qmc)):
+            rows = []
+            for n in n_list:
+                init(n)
+                m, v = ens.stats(cd[off:off + n].reshape(-1, 1), ddof=1)
+                mean, std = float(m[0]), float(v[0]) ** 0.5
+                rows.append({"n": n, "mean": mean, "std": std, "rel_err_mean": abs(mean - ref[0]) / abs(ref[0]),
+                             "rel_err_std": abs(std - ref[1]) / abs(ref[1])})
+            table[name] = rows
+        steps = q[:, U.UQLB_QOI_STEPS].cpu().numpy()
+        status = q[:, U.UQLB_QOI_STATUS].cpu().numpy()
+        upd = int(steps.sum()) * smp[0].nx * smp[0].ny
+        line.update({"samples": len(smp), "lattice": [smp[0].nx, smp[0].ny], "storage": st,
+                     "inflow": [w_sc.bounds[0][0], w_sc.bounds[0][1]], "seconds": ms / 1e3,
+                     "value": upd / (ms / 1e3) / 1e6, "steps_run": [int(steps.min()), int(steps.max())],
+                     "samples_not_converged": int((steps >= w_sc.base.steps).sum()),
+                     "unstable_samples": int((status == U.UQLB_ERR_UNSTABLE).sum()),
+                     "cd_deterministic": float(cd[-1]), "cd_stats": table})
     elif args.workload == "uneven":
         specs = W.uneven_batch()
         smp = [sample_struct(s) for s in specs]
@@ -605,7 +649,8 @@ def main():
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent"],
                     help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")
     ap.add_argument("--workload", default="tgv256_gpc4d",
-                    choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "uneven", "tgv_paper4d"])
+                    choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "cylinder_uq_compare", "uneven",
+                             "tgv_paper4d"])
     ap.add_argument("--resolutions", default="8,16,32,64,128,256", help="tgv_paper4d: resolutions n")
     ap.add_argument("--t-max", type=float, default=100.0, help="tgv_paper4d: final physical time")
     ap.add_argument("--sampling", default="mc", choices=["mc", "smolyak"],
@@ -613,6 +658,8 @@ def main():
     ap.add_argument("--oracle-samples", type=int, default=4, help="oracle reference subset (other workloads)")
     ap.add_argument("--storages", default="", help="further storage formats to run on the same workload")
     ap.add_argument("--nd", type=int, default=20, help="cylinder: nodes per diameter")
+    ap.add_argument("--compare-n", default="10,20,40,80,100", help="cylinder_uq_compare: MC/QMC sample counts")
+    ap.add_argument("--inflow-spread", type=float, default=0.2, help="cylinder_uq_compare: relative inflow spread")
     ap.add_argument("--n", type=int, default=0, help="tgv512_mc4d: lattice size override")
     ap.add_argument("--n-mc", type=int, default=0, help="tgv512_mc4d: sample count override")
     ap.add_argument("--time-steps-full", type=int, default=0, help="tgv512_mc4d: step count override")

@@ -209,6 +209,9 @@ __device__ __forceinline__ bool tile_reduce_last(const KParams& p, const SampleD
 // ------------------------------------------------------------------------------------------
 // Initial state: equilibrium of the initial macroscopic field (Sec. 8.2 TGV, Sec. 8.1 rest).
 // ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void sincospi_c(float a, float* s, float* c) { sincospif(a, s, c); }
+__device__ __forceinline__ void sincospi_c(double a, double* s, double* c) { sincospi(a, s, c); }
+
 template <typename S>
 __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tiles, int tile_rows, int tile_cols) {
     using C = typename Storage<S>::C;
@@ -229,43 +232,46 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
             const int y = y0 + q / tile_cols;
             if (x >= sp.nx || y >= sp.ny) continue;
-            double rho = 1.0, ux = 0.0, uy = 0.0;
+            // The analytic field and its equilibrium in the storage's compute type (FP64 for FP64
+            // storage, FP32 otherwise); the density enters as drho = rho - 1, so no 1 + small
+            // cancellation occurs in FP32.
+            C drho = C(0), ux = C(0), uy = C(0);
             if (sp.kind == UQLB_CASE_TGV) {
                 const InitDev& in = p.init[j];
-                double s1x, c1x, s1y, c1y;
-                sincospi(2.0 * x / sp.nx, &s1x, &c1x);
-                sincospi(2.0 * y / sp.ny, &s1y, &c1y);
-                const double s2x = 2.0 * s1x * c1x, c2x = 2.0 * c1x * c1x - 1.0;
-                const double s2y = 2.0 * s1y * c1y, c2y = 2.0 * c1y * c1y - 1.0;
-                const double s3x = s1x * (3.0 - 4.0 * s1x * s1x), c3x = c1x * (4.0 * c1x * c1x - 3.0);
-                const double s3y = s1y * (3.0 - 4.0 * s1y * s1y), c3y = c1y * (4.0 * c1y * c1y - 3.0);
-                ux = in.u0 * s1x * c1y + in.amp2 * s2x * c2y + in.amp3 * s3x * c3y;
-                uy = -in.u0 * c1x * s1y - in.amp2 * c2x * s2y - in.amp3 * c3x * s3y;
-                const double pr = 0.25 * in.u0 * in.u0 * (c2x + c2y);
-                rho = 1.0 + 3.0 * pr;
+                const C u0 = (C)in.u0, a2 = (C)in.amp2, a3 = (C)in.amp3;
+                C s1x, c1x, s1y, c1y;
+                sincospi_c(C(2 * x) / C(sp.nx), &s1x, &c1x);
+                sincospi_c(C(2 * y) / C(sp.ny), &s1y, &c1y);
+                const C s2x = C(2) * s1x * c1x, c2x = C(2) * c1x * c1x - C(1);
+                const C s2y = C(2) * s1y * c1y, c2y = C(2) * c1y * c1y - C(1);
+                const C s3x = s1x * (C(3) - C(4) * s1x * s1x), c3x = c1x * (C(4) * c1x * c1x - C(3));
+                const C s3y = s1y * (C(3) - C(4) * s1y * s1y), c3y = c1y * (C(4) * c1y * c1y - C(3));
+                ux = u0 * s1x * c1y + a2 * s2x * c2y + a3 * s3x * c3y;
+                uy = -u0 * c1x * s1y - a2 * c2x * s2y - a3 * c3x * s3y;
+                drho = C(0.75) * u0 * u0 * (c2x + c2y);  // 3 p, p = u0^2 / 4 (cos 2kx + cos 2ky)
             } else if (sp.kind == UQLB_CASE_TGV_PERTURBED) {
                 // Sec. 8.3: base mode 2 with amplitude U = u0 + eps(x, y), perturbation modes 4
                 const InitDev& in = p.init[j];
-                double s2x, c2x, s2y, c2y;
-                sincospi(4.0 * x / sp.nx, &s2x, &c2x);
-                sincospi(4.0 * y / sp.ny, &s2y, &c2y);
-                const double s4x = 2.0 * s2x * c2x, c4x = 2.0 * c2x * c2x - 1.0;
-                const double s4y = 2.0 * s2y * c2y, c4y = 2.0 * c2y * c2y - 1.0;
-                const double eps = in.pert[0] * s4x * s4y + in.pert[1] * s4x * c4y + in.pert[2] * c4x * s4y +
-                                   in.pert[3] * c4x * c4y;
-                const double U = in.u0 + 0.25 * eps;
+                C s2x, c2x, s2y, c2y;
+                sincospi_c(C(4 * x) / C(sp.nx), &s2x, &c2x);
+                sincospi_c(C(4 * y) / C(sp.ny), &s2y, &c2y);
+                const C s4x = C(2) * s2x * c2x, c4x = C(2) * c2x * c2x - C(1);
+                const C s4y = C(2) * s2y * c2y, c4y = C(2) * c2y * c2y - C(1);
+                const C eps = (C)in.pert[0] * s4x * s4y + (C)in.pert[1] * s4x * c4y + (C)in.pert[2] * c4x * s4y +
+                              (C)in.pert[3] * c4x * c4y;
+                const C U = (C)in.u0 + C(0.25) * eps;
                 ux = -U * c2x * s2y;
                 uy = U * s2x * c2y;
-                rho = 1.0 - 0.75 * U * U * (c4x + c4y);
+                drho = -C(0.75) * U * U * (c4x + c4y);
             }
-            const double usq = ux * ux + uy * uy;
+            const C usq = ux * ux + uy * uy, rho = C(1) + drho;
             S* base = arena + sp.f_off + (int64_t)y * sp.pitch + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const double cu = cx(i) * ux + cy(i) * uy;
-                const double w = wgt<double>(i);
-                const double g = w * (rho - 1.0) + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-                Storage<S>::store(base + i * sp.plane, (C)g);
+                const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
+                const C w = wgt<C>(i);
+                const C g = w * drho + w * rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq);
+                Storage<S>::store(base + i * sp.plane, g);
             }
         }
     }

@@ -112,6 +112,21 @@ def cylinder_gpc(nd: int = 20, pts: int = 9, order: int = 8, steps: int = 200000
                     order=order, storage=storage, qoi_every=100)
 
 
+def cylinder_uq(nd: int = 20, method: str = "gpc", n: int = 11, order: int = 5, spread: float = 0.2,
+                steps: int = 200000, steady_tol: float = 1e-8, storage: str = "f64", seed: int = 123456) -> Workload:
+    """The Sec. 8.1 method comparison: mean inflow U ~ U((1 - spread) U_nom, (1 + spread) U_nom) at
+    fixed viscosity (the paper's +-20 %), U_nom = 0.04.  method "gpc": n Gauss-Legendre points and
+    a degree-`order` expansion (the paper's reference uses 11 points, order 5); "mc" / "qmc": n
+    Philox draws / Halton points.  Steady state as in cylinder_gpc."""
+    base = channel(nd, steps=steps, steady_tol=steady_tol)
+    base.steady_checks = 1 if storage == "f64" else 5
+    bounds = [((1.0 - spread) * 0.04, (1.0 + spread) * 0.04)]
+    if method == "gpc":
+        return Workload("cylinder_uq", base, bounds, ["u0"], "gpc", pts_per_dim=n, order=order, storage=storage,
+                        qoi_every=100)
+    return Workload("cylinder_uq", base, bounds, ["u0"], method, n_mc=n, seed=seed, storage=storage, qoi_every=100)
+
+
 def uneven_batch(seed: int = 2508, n_tgv: int = 256, n_cyl: int = 64) -> list[SampleSpec]:
     """Heterogeneous batch: TGV samples of random size and viscosity whose step counts give equal
     decay, T = clamp(round(1000 (0.04 / nu) (n / 256)^2), 500, 4000), plus channel samples."""

@@ -238,6 +238,36 @@ def test_paper_study_draws_n_monte_carlo_samples_at_resolution_n():
         U.uqlb_destroy(ctx)
 
 
+def test_cylinder_method_comparison_samples_are_nested_and_in_the_inflow_range():
+    """MC and QMC sets of size N are prefixes of the largest set (one batch serves every N), and
+    every sample's mean inflow lies in the +-20 % range of the comparison."""
+    ctx = U.uqlb_create(0)
+    try:
+        lo, hi = 0.8 * 0.04, 1.2 * 0.04
+        for method in ("mc", "qmc", "gpc"):
+            w = W.cylinder_uq(20, method=method, n=40 if method != "gpc" else 11)
+            assert w.bounds == [(lo, hi)]
+            U.uqlb_set_inputs(ctx, w.bounds)
+            if method == "mc":
+                U.uqlb_init_mc(ctx, 40, w.seed)
+            elif method == "qmc":
+                U.uqlb_init_qmc(ctx, 40, 1)
+            else:
+                U.uqlb_init_gpc(ctx, 5, 11, U.UQLB_BASIS_TOTAL, U.UQLB_QUAD_GAUSS_LEGENDRE_TENSOR)
+            big = U.uqlb_ensemble_samples(ctx, case_struct(w))
+            assert all(lo <= s.u0 <= hi and s.kind == U.UQLB_CASE_CHANNEL for s in big)
+            if method == "gpc":
+                continue
+            if method == "mc":
+                U.uqlb_init_mc(ctx, 10, w.seed)
+            else:
+                U.uqlb_init_qmc(ctx, 10, 1)
+            small = U.uqlb_ensemble_samples(ctx, case_struct(w))
+            assert [s.u0 for s in small] == [s.u0 for s in big[:10]]
+    finally:
+        U.uqlb_destroy(ctx)
+
+
 def test_untuned_workspace_covers_every_geometry_for_every_entry_point():
     """With geometry 0/0 the batch, ensemble and end-to-end workspace queries all cover every
     compiled tile geometry, since an autotuned run may use any of them."""

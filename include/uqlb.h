@@ -56,6 +56,8 @@ enum { UQLB_BASIS_TOTAL = 0, UQLB_BASIS_TENSOR = 1 };
 enum { UQLB_QUAD_GAUSS_LEGENDRE_TENSOR = 0, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 1 };
 enum { UQLB_METHOD_NONE = 0, UQLB_METHOD_MC = 1, UQLB_METHOD_GPC = 2 };
 enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1, UQLB_CASE_TGV_PERTURBED = 2 };
+/* Obstacle boundary scheme of the CHANNEL case (Sec. 8.1: the cylinder surface). */
+enum { UQLB_OBSTACLE_HALFWAY = 0, UQLB_OBSTACLE_BOUZIDI = 1 };
 /* Parameters an uncertain input dimension may drive (uqlb_case.param_of_dim). */
 enum {
     UQLB_PARAM_NU = 0,
@@ -108,6 +110,14 @@ typedef struct {
  *     sample stops once |C_D(t) - C_D(t - qoi_every)| < steady_tol |C_D(t)| holds at
  *     steady_checks consecutive checks (FP32 resolves C_D to ~1e-7, so a tolerance below that
  *     needs several checks to avoid stopping on a chance coincidence).
+ *     obstacle_bc selects the obstacle scheme: UQLB_OBSTACLE_HALFWAY (halfway bounce-back on
+ *     the staircase, force 2 sum c_i f*_i) or UQLB_OBSTACLE_BOUZIDI, the linear interpolated
+ *     bounce-back of Bouzidi, Firdaouss and Lallemand (2001) named by Sec. 8.1: a link from
+ *     fluid node x along c_i meets the circle at the fraction q of its length and returns
+ *     f_ibar(x, t+1) = 2q f*_i(x) + (1 - 2q) f_i(x, t+1) for q < 1/2 (f_i(x, t+1): the
+ *     population streamed into x along c_i) or f*_i(x) / (2q) + (1 - 1/(2q)) f*_ibar(x) for
+ *     q >= 1/2; the force is sum c_i (f*_i(x, t) + f_ibar(x, t+1)) after the stream.  Bouzidi
+ *     samples run in UQLB_MODE_GRAPH only.
  *   TGV_PERTURBED (Sec. 8.3): periodic [0, 2 pi)^2 on nx x ny nodes x = 2 pi i / nx,
  *     u = -U cos 2x sin 2y, v = U sin 2x cos 2y, U = u0 + 1/4 sum_ij pert[2i+j] k_i(4x) k_j(4y)
  *     (k_0 = sin, k_1 = cos), p = -U^2/4 (cos 4x + cos 4y), rho = 1 + 3p; K(t) normalised by u_ref.
@@ -125,6 +135,8 @@ typedef struct {
     int64_t ramp_steps;  /* CHANNEL inflow ramp length (0: none) */
     double steady_tol;   /* CHANNEL steady-state tolerance (0: run to the cap) */
     double pert[4];      /* TGV_PERTURBED amplitudes zeta_00, zeta_01, zeta_10, zeta_11 (lattice units) */
+    int32_t obstacle_bc; /* CHANNEL obstacle scheme, UQLB_OBSTACLE_HALFWAY or UQLB_OBSTACLE_BOUZIDI */
+    int32_t reserved;    /* must be 0 */
 } uqlb_sample;
 
 /* Template of an ensemble: a uqlb_sample whose parameters are overridden per sample by

@@ -19,6 +19,7 @@ _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle_lbm.so")
 
 TGV, CHANNEL, TGV_PERTURBED = 0, 1, 2
+HALFWAY, BOUZIDI = 0, 1  # obstacle schemes of the channel case
 
 
 def build(force: bool = False) -> str:
@@ -39,7 +40,8 @@ class _Case(ctypes.Structure):
                 ("amp2", ctypes.c_double), ("amp3", ctypes.c_double), ("u_ref", ctypes.c_double),
                 ("cyl_cx", ctypes.c_double), ("cyl_cy", ctypes.c_double),
                 ("cyl_r", ctypes.c_double), ("ramp_steps", ctypes.c_int64),
-                ("qoi_every", ctypes.c_int64), ("steady_tol", ctypes.c_double), ("pert", ctypes.c_double * 4)]
+                ("qoi_every", ctypes.c_int64), ("steady_tol", ctypes.c_double), ("pert", ctypes.c_double * 4),
+                ("obstacle_bc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -63,6 +65,8 @@ def _load():
         _lib.oracle_obstacle_mask.argtypes = [ctypes.POINTER(_Case), ctypes.c_void_p]
         _lib.oracle_obstacle_mask.restype = ctypes.c_int
         _lib.oracle_num_threads.restype = ctypes.c_int
+        _lib.oracle_link_fraction.argtypes = [ctypes.POINTER(_Case), ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        _lib.oracle_link_fraction.restype = ctypes.c_double
     return _lib
 
 
@@ -85,11 +89,13 @@ class Case:
     qoi_every: int = 0
     steady_tol: float = 0.0
     pert: tuple = (0.0, 0.0, 0.0, 0.0)
+    obstacle_bc: int = HALFWAY
 
     def _c(self) -> _Case:
         return _Case(self.kind, self.nx, self.ny, self.steps, self.nu, self.u0, self.amp2,
                      self.amp3, self.u_ref, self.cyl_cx, self.cyl_cy, self.cyl_r,
-                     self.ramp_steps, self.qoi_every, self.steady_tol, (ctypes.c_double * 4)(*self.pert))
+                     self.ramp_steps, self.qoi_every, self.steady_tol, (ctypes.c_double * 4)(*self.pert),
+                     self.obstacle_bc, 0)
 
 
 @dataclass
@@ -148,6 +154,13 @@ def obstacle_mask(case: Case) -> np.ndarray:
     if lib.oracle_obstacle_mask(ctypes.byref(c), m.ctypes.data) != 0:
         raise RuntimeError("oracle_obstacle_mask failed")
     return m.reshape(case.ny, case.nx)
+
+
+def link_fraction(case: Case, x: int, y: int, i: int) -> float:
+    """Fraction q of the link from node (x, y) along D2Q9 direction i at which it enters the
+    obstacle circle (the oracle's Bouzidi geometry)."""
+    c = case._c()
+    return float(_load().oracle_link_fraction(ctypes.byref(c), x, y, i))
 
 
 def num_threads() -> int:

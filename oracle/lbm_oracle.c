@@ -28,7 +28,18 @@
  *     the outlet is a pressure condition: anti-bounce-back at the x = nx face with
  *     rho_w = 1 and the wall velocity taken from the outlet node itself (zero
  *     gradient); forces by momentum exchange on obstacle links;
- *     ramp 1/2 (1 - cos(pi t / T_r)) for t < T_r.
+ *     ramp 1/2 (1 - cos(pi t / T_r)) for t < T_r;
+ *   - obstacle scheme, selectable: halfway bounce-back on the staircase, or the
+ *     linear interpolated bounce-back of Bouzidi, Firdaouss and Lallemand (2001),
+ *     which Sec. 8.1 names for the cylinder surface.  For a link from fluid node x
+ *     along c_k into the obstacle, q is the fraction of the link at which it meets
+ *     the circle, and the population returning to x is
+ *         q <  1/2:  f_kbar(x, t+1) = 2q f*_k(x, t) + (1 - 2q) f_k(x, t+1),
+ *         q >= 1/2:  f_kbar(x, t+1) = f*_k(x, t) / (2q) + (1 - 1/(2q)) f*_kbar(x, t),
+ *     where f_k(x, t+1) is the population streamed into x along c_k by the other
+ *     rules (f*_k(x - c_k, t) for the fluid node upstream); the force is the momentum
+ *     exchanged on the links, F = sum c_k (f*_k(x, t) + f_kbar(x, t+1)), taken after
+ *     the stream (for halfway bounce-back this is 2 sum c_k f*_k(x, t)).
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +73,8 @@ typedef struct {
     int64_t qoi_every;   /* stride of the QoI series (0: no series) */
     double steady_tol;   /* channel: stop when |dC_D|/|C_D| < tol between checks (0: never) */
     double pert[4];      /* perturbed TGV: zeta_00, zeta_01, zeta_10, zeta_11 (lattice velocity units) */
+    int32_t obstacle_bc; /* channel obstacle: 0 halfway bounce-back, 1 Bouzidi linear interpolation */
+    int32_t reserved;
 } oracle_case;
 
 /* Per-run outputs.  Arrays are row-major [ny][nx]; any pointer may be NULL. */
@@ -100,6 +113,16 @@ static int node_solid(const oracle_case *c, int x, int y) {
     if (c->kind != ORACLE_CHANNEL || c->cyl_r <= 0.0) return 0;
     double dx = (x + 0.5) - c->cyl_cx, dy = (y + 0.5) - c->cyl_cy;
     return dx * dx + dy * dy < c->cyl_r * c->cyl_r;
+}
+
+/* Fraction q of the link from node (x, y) along c_i at which it enters the obstacle circle:
+ * the smaller root s of |P + s c_i - C|^2 = r^2, P = (x + 1/2, y + 1/2), C the centre. */
+static double link_fraction(const oracle_case *c, int x, int y, int i) {
+    double px = (x + 0.5) - c->cyl_cx, py = (y + 0.5) - c->cyl_cy;
+    double a = (double)(CX[i] * CX[i] + CY[i] * CY[i]);
+    double b = 2.0 * (CX[i] * px + CY[i] * py);
+    double cc = px * px + py * py - c->cyl_r * c->cyl_r;
+    return (-b - sqrt(b * b - 4.0 * a * cc)) / (2.0 * a);
 }
 
 /* Parabolic inflow profile evaluated at height yy (walls at 0 and H = ny), peak 1.5 x mean. */
@@ -195,6 +218,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
         }
     }
 
+    const int bouzidi = c->kind == ORACLE_CHANNEL && c->cyl_r > 0.0 && c->obstacle_bc == 1;
     const double Dlat = 2.0 * c->cyl_r;
     const double force_norm = (c->kind == ORACLE_CHANNEL && Dlat > 0.0)
                                   ? 2.0 / (1.0 * c->u0 * c->u0 * Dlat)
@@ -223,7 +247,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
                     uout[2 * y + 1] = uy;
                 }
                 /* Momentum exchange on links into the obstacle (halfway bounce-back). */
-                if (c->kind == ORACLE_CHANNEL) {
+                if (c->kind == ORACLE_CHANNEL && !bouzidi) {
                     for (int i = 1; i < Q; ++i) {
                         int xn = x + CX[i], yn = y + CY[i];
                         if (xn < 0 || xn >= nx || yn < 0 || yn >= ny) continue;
@@ -265,6 +289,30 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
                         val = fpost[i * plane + (int64_t)sy * nx + sx];
                     }
                     f[i * plane + n] = val;
+                }
+            }
+        }
+        if (bouzidi) {
+            /* Interpolated bounce-back on the obstacle links (the pull above left the halfway
+             * value there), then the momentum exchanged on them. */
+            for (int y = 0; y < ny; ++y) {
+                for (int x = 0; x < nx; ++x) {
+                    int64_t n = (int64_t)y * nx + x;
+                    if (solid[n]) continue;
+                    for (int k = 1; k < Q; ++k) {
+                        int xn = x + CX[k], yn = y + CY[k];
+                        if (xn < 0 || xn >= nx || yn < 0 || yn >= ny || !solid[(int64_t)yn * nx + xn]) continue;
+                        int kb = OPP[k];
+                        double q = link_fraction(c, x, y, k);
+                        double back;
+                        if (q < 0.5)
+                            back = 2.0 * q * fpost[k * plane + n] + (1.0 - 2.0 * q) * f[k * plane + n];
+                        else
+                            back = fpost[k * plane + n] / (2.0 * q) + (1.0 - 1.0 / (2.0 * q)) * fpost[kb * plane + n];
+                        f[kb * plane + n] = back;
+                        fx += CX[k] * (fpost[k * plane + n] + back);
+                        fy += CY[k] * (fpost[k * plane + n] + back);
+                    }
                 }
             }
         }
@@ -344,6 +392,12 @@ int oracle_obstacle_mask(const oracle_case *c, unsigned char *mask) {
     for (int y = 0; y < c->ny; ++y)
         for (int x = 0; x < c->nx; ++x) mask[(int64_t)y * c->nx + x] = (unsigned char)node_solid(c, x, y);
     return 0;
+}
+
+/* Link fraction q of the link from fluid node (x, y) along direction i (test access). */
+double oracle_link_fraction(const oracle_case *c, int x, int y, int i) {
+    if (!c || i < 1 || i >= Q) return NAN;
+    return link_fraction(c, x, y, i);
 }
 
 int oracle_num_threads(void) {

@@ -112,6 +112,61 @@ __device__ __forceinline__ C inflow(const SampleDev& sp, C yy, int t) {
     return C(4) * C(sp.uin_max) * ramp * yy * (H - yy) / (H * H);
 }
 
+// ---- Bouzidi linear interpolated bounce-back on the obstacle (Sec. 8.1 cylinder surface) ----
+// A link from fluid node x along c_i into the obstacle meets the circle at the fraction q of its
+// length; the population returning to x is 2q g*_i(x) + (1 - 2q) g_i(x, t+1) for q < 1/2 and
+// g*_i(x) / (2q) + (1 - 1/(2q)) g*_ibar(x) for q >= 1/2 (weights sum to 1, so the shifted
+// g = f - w obey the same rule).  In the in-place AA layout the collision writes the part it can
+// form locally into the node's own bounce-back slot opp(i) (the whole value for q >= 1/2, 2q g*_i
+// below), the gather of the next step adds (1 - 2q) times the streamed g_i, and the raw g*_i is
+// parked in slot i of the obstacle node x + c_i, which no thread reads or writes otherwise (it
+// serves the force).
+
+// q of the link from (x, y) along c_i: the entry root of |P + s c_i - C|^2 = r^2 (P the node
+// centre), as s = 2 cc / (sqrt(b^2 - 4 a cc) - b), free of cancellation since b < 0 on a link
+// that enters the circle.
+template <typename C>
+__device__ __forceinline__ C link_q(const InitDev& in, int x, int y, int i) {
+    const double px = (double)x + 0.5 - in.cyl_cx, py = (double)y + 0.5 - in.cyl_cy;
+    const C cc = (C)(px * px + py * py - in.cyl_r * in.cyl_r);
+    const C b = C(2) * (C(cx(i)) * (C)px + C(cy(i)) * (C)py);
+    const C a = C(cx(i) * cx(i) + cy(i) * cy(i));
+    return C(2) * cc / (sqrt(b * b - C(4) * a * cc) - b);
+}
+
+// Directions i (bit i) of node (x, y) whose neighbour x + c_i is an obstacle node.
+__device__ __forceinline__ uint32_t obstacle_links(const SampleDev& sp, const InitDev& in, const uint32_t* mask,
+                                                   int x, int y) {
+    if (x < in.bbox[0] || x > in.bbox[1] || y < in.bbox[2] || y > in.bbox[3]) return 0u;
+    uint32_t m = 0u;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int xn = x + cx(i), yn = y + cy(i);
+        if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny && mask_solid(mask, sp.mask_words, xn, yn))
+            m |= 1u << i;
+    }
+    return m;
+}
+
+// Gather side: g[opp(i)] holds what the collision left in the bounce-back slot.
+template <typename C>
+__device__ __forceinline__ void bouzidi_complete(const InitDev& in, int x, int y, uint32_t links, C (&g)[9]) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (links >> i & 1u) {
+            const C q = link_q<C>(in, x, y, i);
+            if (q < C(0.5)) g[opp(i)] += (C(1) - C(2) * q) * g[i];
+        }
+    }
+}
+
+// Collision side: the value written to the bounce-back slot opp(i) from the post-collision g*.
+template <typename C>
+__device__ __forceinline__ C bouzidi_local(const InitDev& in, int x, int y, int i, const C (&g)[9]) {
+    const C q = link_q<C>(in, x, y, i);
+    return q < C(0.5) ? C(2) * q * g[i] : (g[i] + (C(2) * q - C(1)) * g[opp(i)]) / (C(2) * q);
+}
+
 // Shifted incoming population of direction i at node (x, y) for the stream (tp -> tp + 1),
 // given the slot layout left by an even step at time tp: g_i*(z) sits at (z, slot opp(i)).
 // ub: velocity of the outlet node at time tp.
@@ -301,16 +356,19 @@ __device__ __forceinline__ void periodic_cols(const SampleDev& sp, int x, Nbr& n
 }
 
 // Nine incoming shifted populations of node (x, y) at step t.
+// links: Bouzidi obstacle links of the node (bit i), 0 for every other node.
 template <typename S, bool ODD>
 __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp, const S* base,
                                           const uint32_t* mask, int x, int y, int t, bool chan,
-                                          const Nbr& nb, typename Storage<S>::C (&g)[9]) {
+                                          const Nbr& nb, const InitDev* bz, uint32_t links,
+                                          typename Storage<S>::C (&g)[9]) {
     using C = typename Storage<S>::C;
     const int plane = (int)sp.plane;
     if (!ODD) {
         const int own = nb.row[1] + x;
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + (i * plane + own));
+        if (chan && links) bouzidi_complete(*bz, x, y, links, g);
     } else if (!chan) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
@@ -329,6 +387,7 @@ __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp,
         g[0] = Storage<S>::load(base + (nb.row[1] + x));
 #pragma unroll
         for (int i = 1; i < 9; ++i) g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan);
+        if (links) bouzidi_complete(*bz, x, y, links, g);
     }
 }
 
@@ -336,7 +395,8 @@ __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp,
 template <typename S, bool ODD>
 __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& sp, S* base, const uint32_t* mask,
                                             int x, int y, int t, bool chan, bool want_k, bool want_f,
-                                            const Nbr& nb, typename Storage<S>::C (&g)[9], double (&red)[3]) {
+                                            const Nbr& nb, const InitDev* bz, uint32_t links,
+                                            typename Storage<S>::C (&g)[9], double (&red)[3]) {
     using C = typename Storage<S>::C;
     const int own = nb.row[1] + x;
     const int plane = (int)sp.plane;
@@ -380,6 +440,18 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
         red[2] += (double)fy;
     }
     if (!ODD) {
+        if (chan && links) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if (links >> i & 1u) {
+                    put(base + (opp(i) * plane + own), bouzidi_local(*bz, x, y, i, g), i);
+                    put(base + ((int64_t)i * plane + (int64_t)(y + cy(i)) * sp.pitch + (x + cx(i))), g[i], i);
+                } else {
+                    put(base + (opp(i) * plane + own), g[i], i);
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) put(base + (opp(i) * plane + own), g[i], i);
         return;
@@ -399,6 +471,9 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
             const int o = opp(i);
             if (cls == kInterior) {
                 put(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i], i);
+            } else if (cls == kSolid && (links >> i & 1u)) {
+                put(base + o * plane + own, bouzidi_local(*bz, x, y, i, g), i);
+                put(base + i * plane + (int64_t)dy * sp.pitch + dx, g[i], i);  // parked g*_i
             } else if (cls == kWall || cls == kSolid) {
                 put(base + o * plane + own, g[i], i);
             } else if (cls == kInlet) {
@@ -409,6 +484,29 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
                 put(base + o * plane + own, -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
             }
         }
+    }
+}
+
+// C_D, C_L of sample j at time s (a QoI step) into the series, and the steady-state test: a
+// sample whose C_D changed by less than steady_tol |C_D| at steady_checks consecutive checks
+// stops with its state at s.
+__device__ __forceinline__ void record_force(const KParams& p, const SampleDev& sp, int j, int s, double fx,
+                                             double fy) {
+    const double cd = fx * sp.force_norm, cl = fy * sp.force_norm;
+    const int64_t col = s / p.qoi_every - 1;
+    if (p.series) p.series[(int64_t)sp.sample_id * p.series_ld + col] = cd;
+    if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
+    if (sp.steady_tol > 0.0) {
+        const double prev = p.cd_prev[j];
+        const bool pass = !isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd);
+        const int run = pass ? p.streak[j] + 1 : 0;
+        p.streak[j] = run;
+        if (run >= sp.steady_checks) {
+            p.done[j] = 1;
+            p.steps_run[j] = s;
+            atomicAdd(p.n_done, 1);
+        }
+        p.cd_prev[j] = cd;
     }
 }
 
@@ -445,15 +543,17 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
         return;
     }
     const bool want_k = k_step && !chan;
-    const bool want_f = f_step && chan;
+    const bool want_f = f_step && chan && !sp.bouzidi;  // Bouzidi forces: bouzidi_force_kernel
     const int lt = tile - sp.tile_base;
     const int x0 = (lt % sp.tiles_x) * (kTileCols * NPT) + threadIdx.x;
     const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
     const uint32_t* mask = (chan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
     S* base = static_cast<S*>(p.arena) + sp.f_off;
 
+    const InitDev* bz = (chan && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
     C g[NPT][9];
     bool act[NPT];
+    uint32_t lk[NPT];
     Nbr nb[NPT];
     Nbr rows;
     if (!chan && ODD) {
@@ -468,12 +568,15 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
         if (!chan && ODD) periodic_cols(sp, x, nb[k]);
         act[k] = x < sp.nx && y < sp.ny;
         if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, sp.mask_words, x, y);
-        if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, nb[k], g[k]);
+        lk[k] = (act[k] && bz != nullptr) ? obstacle_links(sp, *bz, mask, x, y) : 0u;
+        if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, nb[k], bz, lk[k], g[k]);
     }
     double red[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
-        if (act[k]) node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, nb[k], g[k], red);
+        if (act[k])
+            node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, nb[k], bz, lk[k],
+                                g[k], red);
 
     if (want_k || want_f) {
         double tot[3];
@@ -482,22 +585,7 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
                 if (want_k) {
                     p.series[(int64_t)sp.sample_id * p.series_ld + t / p.qoi_every] = tot[0] * sp.u_ref_inv2;
                 } else {
-                    const double cd = tot[1] * sp.force_norm, cl = tot[2] * sp.force_norm;
-                    const int64_t col = (t + 1) / p.qoi_every - 1;
-                    if (p.series) p.series[(int64_t)sp.sample_id * p.series_ld + col] = cd;
-                    if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
-                    if (sp.steady_tol > 0.0) {
-                        const double prev = p.cd_prev[j];
-                        const bool pass = !isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd);
-                        const int run = pass ? p.streak[j] + 1 : 0;
-                        p.streak[j] = run;
-                        if (run >= sp.steady_checks) {
-                            p.done[j] = 1;
-                            p.steps_run[j] = t + 1;
-                            atomicAdd(p.n_done, 1);
-                        }
-                        p.cd_prev[j] = cd;
-                    }
+                    record_force(p, sp, j, t + 1, tot[1], tot[2]);
                 }
             }
         }
@@ -627,6 +715,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
         const int lt = (int)tile - sp.tile_base;
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         const uint32_t* mask = (sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+        const InitDev* bz = (chan && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
         double red[7] = {0, 0, 0, 0, 0, 0, 0};  // K, mass, mx, my, fx, fy, bad
         for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
@@ -657,6 +746,8 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     for (int i = 1; i < 9; ++i)
                         g[i] = read_incoming<S>(base, sp, mask, x, y, i, T - 1, ubx, uby, chan);
                 }
+                const uint32_t links = bz != nullptr ? obstacle_links(sp, *bz, mask, x, y) : 0u;
+                if (links && T > 0) bouzidi_complete(*bz, x, y, links, g);
                 C drho, cjx, cjy, cux, cuy;
                 moments(g, drho, cjx, cjy, cux, cuy);
                 ux = (double)cux;
@@ -668,15 +759,26 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                 red[3] += rho * uy;
                 if (!(rho > 0.0) || !isfinite(ux) || !isfinite(uy)) red[6] += 1.0;
                 if (mask != nullptr && T > 0) {
-                    // bounce-back populations at T are the post-collision values of step T - 1
+                    // halfway: the bounce-back populations at T are the post-collision values of
+                    // step T - 1; Bouzidi: c_i (g*_i(T - 1) parked in the obstacle node + the
+                    // completed returning population at T)
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
                         const int xn = x + cx(i), yn = y + cy(i);
                         if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny &&
                             mask_solid(mask, sp.mask_words, xn, yn)) {
-                            const double fs = (double)Storage<S>::load(base + opp(i) * sp.plane + own) + wgt<double>(i);
-                            red[4] += 2.0 * cx(i) * fs;
-                            red[5] += 2.0 * cy(i) * fs;
+                            if (links) {
+                                const double fs =
+                                    (double)Storage<S>::load(base + i * sp.plane + (int64_t)yn * sp.pitch + xn) +
+                                    (double)g[opp(i)] + 2.0 * wgt<double>(i);
+                                red[4] += cx(i) * fs;
+                                red[5] += cy(i) * fs;
+                            } else {
+                                const double fs =
+                                    (double)Storage<S>::load(base + opp(i) * sp.plane + own) + wgt<double>(i);
+                                red[4] += 2.0 * cx(i) * fs;
+                                red[5] += 2.0 * cy(i) * fs;
+                            }
                         }
                     }
                 }
@@ -723,6 +825,67 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     p.series[(int64_t)sp.sample_id * p.series_ld + T / p.qoi_every] = K;
             }
         }
+    }
+}
+
+// Obstacle force of the Bouzidi samples at time s = step counter + dt + 1 when s is a QoI step:
+// F = sum over the obstacle links of c_i (f*_i(x, s-1) + f_ibar(x, s)) (the momentum exchanged on
+// the link), from the values the step s-1 left in memory: the parked g*_i, the bounce-back slot
+// and, for q < 1/2, the streamed g_i (found as the gather of step s would find it).  One block per
+// sample walks the nodes of the obstacle's bounding box.  It runs between the launches of steps
+// s-1 and s, so a sample that passes the steady-state test stops with its state at s.
+template <typename S>
+__global__ void __launch_bounds__(256) bouzidi_force_kernel(KParams p) {
+    using C = typename Storage<S>::C;
+    constexpr int NT = 256;
+    __shared__ double s_red[(NT / 32) * 2];
+    const int s = (int)(*p.step_counter) + p.dt + 1;
+    if (p.qoi_every <= 0 || s % p.qoi_every != 0) return;
+    const bool prev_odd = ((s - 1) & 1) != 0;
+    for (int j = blockIdx.x; j < p.nsamples; j += gridDim.x) {
+        const SampleDev& sp = p.samples[j];
+        if (!sp.bouzidi || sp.mask_off < 0 || s > sp.steps || p.done[j]) continue;
+        const InitDev& in = p.init[j];
+        const uint32_t* mask = p.masks + sp.mask_off;
+        const S* base = static_cast<const S*>(p.arena) + sp.f_off;
+        const int bw = in.bbox[1] - in.bbox[0] + 1, bh = in.bbox[3] - in.bbox[2] + 1;
+        const int nbox = (bw > 0 && bh > 0) ? bw * bh : 0;
+        double red[2] = {0.0, 0.0};
+        for (int n = threadIdx.x; n < nbox; n += NT) {
+            const int x = in.bbox[0] + n % bw, y = in.bbox[2] + n / bw;
+            if (mask_solid(mask, sp.mask_words, x, y)) continue;
+            const uint32_t links = obstacle_links(sp, in, mask, x, y);
+            if (!links) continue;
+            const int64_t own = (int64_t)y * sp.pitch + x;
+            C ubx = C(0), uby = C(0);
+            if (prev_odd == false && x == sp.nx - 1) {
+                if (sizeof(C) == 8) {
+                    ubx = (C)p.side_d[2 * (sp.side_off + y)];
+                    uby = (C)p.side_d[2 * (sp.side_off + y) + 1];
+                } else {
+                    ubx = (C)p.side[2 * (sp.side_off + y)];
+                    uby = (C)p.side[2 * (sp.side_off + y) + 1];
+                }
+            }
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if (!(links >> i & 1u)) continue;
+                C back = Storage<S>::load(base + opp(i) * sp.plane + own);
+                const C q = link_q<C>(in, x, y, i);
+                if (q < C(0.5)) {
+                    const C gi = prev_odd ? Storage<S>::load(base + i * sp.plane + own)
+                                          : read_incoming<S>(base, sp, mask, x, y, i, s - 1, ubx, uby, true);
+                    back += (C(1) - C(2) * q) * gi;
+                }
+                const C parked = Storage<S>::load(base + i * sp.plane + (int64_t)(y + cy(i)) * sp.pitch + (x + cx(i)));
+                const double fs = (double)parked + (double)back + 2.0 * wgt<double>(i);
+                red[0] += cx(i) * fs;
+                red[1] += cy(i) * fs;
+            }
+        }
+        block_sum<2, NT>(red, s_red);
+        if (threadIdx.x == 0) record_force(p, sp, j, s, red[0], red[1]);
+        __syncthreads();
     }
 }
 
@@ -861,6 +1024,20 @@ cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStrea
         case UQLB_F32: init_kernel<float><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
         case UQLB_F16: init_kernel<__half><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
         default: init_kernel<__nv_bfloat16><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bouzidi_force(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt,
+                                 int base_parity, cudaStream_t s) {
+    (void)base_parity;  // the kernel takes the AA layout from the parity of the step index
+    KParams p = make_params(b, g, &o, dt);
+    const int grid = (int)(g.nsamples < 4096 ? g.nsamples : 4096);
+    switch (g.storage) {
+        case UQLB_F64: bouzidi_force_kernel<double><<<grid, 256, 0, s>>>(p); break;
+        case UQLB_F32: bouzidi_force_kernel<float><<<grid, 256, 0, s>>>(p); break;
+        case UQLB_F16: bouzidi_force_kernel<__half><<<grid, 256, 0, s>>>(p); break;
+        default: bouzidi_force_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p); break;
     }
     return cudaGetLastError();
 }

@@ -320,6 +320,11 @@ int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
         snprintf(buf, sizeof buf, "sample %lld: viscosity must be positive", (long long)idx);
     } else if (!std::isfinite(s.u0) || !std::isfinite(s.amp2) || !std::isfinite(s.amp3)) {
         snprintf(buf, sizeof buf, "sample %lld: non-finite velocity parameter", (long long)idx);
+    } else if (s.kind == UQLB_CASE_CHANNEL &&
+               (!std::isfinite(s.cyl_cx) || !std::isfinite(s.cyl_cy) || !std::isfinite(s.cyl_r))) {
+        snprintf(buf, sizeof buf, "sample %lld: non-finite obstacle geometry", (long long)idx);
+    } else if (s.obstacle_bc != UQLB_OBSTACLE_HALFWAY && s.obstacle_bc != UQLB_OBSTACLE_BOUZIDI) {
+        snprintf(buf, sizeof buf, "sample %lld: unknown obstacle scheme %d", (long long)idx, s.obstacle_bc);
     } else {
         return 0;
     }
@@ -370,7 +375,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.steps_sorted.assign(n, 0);
     P.masks.clear();
     int64_t f_off = 0, tiles = 0, side = 0;
-    int max_steps = 0, any_channel = 0, tiles0 = -1;
+    int max_steps = 0, any_channel = 0, any_bouzidi = 0, tiles0 = -1;
     bool uniform_tiles = true;
     P.n_steady = 0;
     P.uniform_size = true;
@@ -417,6 +422,22 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
             side += s.ny;
             if (s.cyl_r > 0.0) {
                 d.force_norm = (s.u0 != 0.0) ? 2.0 / (s.u0 * s.u0 * 2.0 * s.cyl_r) : 0.0;
+                if (s.obstacle_bc == UQLB_OBSTACLE_BOUZIDI) {
+                    d.bouzidi = 1;
+                    any_bouzidi = 1;
+                    InitDev& in = P.init[j];
+                    in.cyl_cx = s.cyl_cx;
+                    in.cyl_cy = s.cyl_cy;
+                    in.cyl_r = s.cyl_r;
+                    // a node with a solid neighbour lies within r + sqrt(2) of the centre
+                    auto lo = [](double v, int n) {
+                        return (int)std::max(0.0, std::min((double)(n - 1), std::floor(v)));
+                    };
+                    in.bbox[0] = lo(s.cyl_cx - s.cyl_r - 2.0, s.nx);
+                    in.bbox[1] = lo(s.cyl_cx + s.cyl_r + 1.0, s.nx);
+                    in.bbox[2] = lo(s.cyl_cy - s.cyl_r - 2.0, s.ny);
+                    in.bbox[3] = lo(s.cyl_cy + s.cyl_r + 1.0, s.ny);
+                }
                 d.mask_off = (int32_t)P.masks.size();
                 P.masks.resize(P.masks.size() + (size_t)d.mask_words * s.ny, 0u);
                 uint32_t* m = P.masks.data() + d.mask_off;
@@ -480,6 +501,11 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
+    g.any_bouzidi = any_bouzidi;
+    if (any_bouzidi && mode != UQLB_MODE_GRAPH) {
+        why = "samples with the Bouzidi obstacle scheme run in UQLB_MODE_GRAPH only";
+        return UQLB_ERR_ARG;
+    }
     return 0;
 }
 
@@ -537,7 +563,11 @@ int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, co
     err = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamBeginCapture");
     cudaError_t lerr = cudaSuccess;
-    for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
+    for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) {
+        lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
+        if (lerr == cudaSuccess && G.any_bouzidi && O.qoi_every > 0)
+            lerr = launch_bouzidi_force(B, G, O, dt, parity, ctx->capture_stream);
+    }
     if (lerr == cudaSuccess) lerr = launch_advance(B, chunk, ctx->capture_stream);
     cudaGraph_t graph = nullptr;
     err = cudaStreamEndCapture(ctx->capture_stream, &graph);
@@ -1147,7 +1177,7 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
         for (int64_t q = 0; q < nchunks; ++q) {
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
-            ctx->run_launches += chunk + 1;
+            ctx->run_launches += chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0);
             if (steady && (q % 8) == 7 && q + 1 < nchunks) {
                 int32_t ndone = 0;
                 if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
@@ -1238,6 +1268,10 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
     if (!workspace_dev || workspace_bytes < need)
         return set_err(ctx, UQLB_ERR_OOM, "run_plain_f64: workspace of %zu bytes, need %zu", workspace_bytes, need);
     if (qoi_every < 0) return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: qoi_every must be >= 0");
+    for (int64_t s = 0; s < n; ++s)
+        if (samples[s].kind == UQLB_CASE_CHANNEL && samples[s].cyl_r > 0.0 &&
+            samples[s].obstacle_bc != UQLB_OBSTACLE_HALFWAY)
+            return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: the plain path has halfway bounce-back only");
     int64_t maxn = 0;
     for (int64_t s = 0; s < n; ++s) maxn = std::max<int64_t>(maxn, (int64_t)samples[s].nx * samples[s].ny);
     if (fields_dev) {

@@ -35,15 +35,19 @@ struct alignas(16) SampleDev {
     double ramp_steps;  // channel: ramp length (0: none)
     double steady_tol;  // channel: steady-state tolerance (0: none)
     int32_t steady_checks;  // channel: consecutive passing checks needed (>= 1)
-    int32_t pad;
+    int32_t bouzidi;        // channel: 1 = Bouzidi interpolated bounce-back on the obstacle
 };
 static_assert(sizeof(SampleDev) == 128, "SampleDev must stay 128 bytes");
 
-// Initial-field parameters (read once by the init kernel).
+// Initial-field parameters (read by the init kernel) and the obstacle geometry (read by the
+// Bouzidi links, which are rare: only nodes inside bbox look at it).
 struct alignas(16) InitDev {
     double u0, amp2, amp3;
     double pad;
     double pert[4];  // perturbed TGV amplitudes zeta_00, zeta_01, zeta_10, zeta_11
+    double cyl_cx, cyl_cy, cyl_r;
+    double pad2;
+    int32_t bbox[4];  // x0, x1, y0, y1 (inclusive): the only nodes that can have obstacle links
 };
 
 // Device pointers carved out of the caller's workspace for one batch run.
@@ -80,6 +84,7 @@ struct BatchGeometry {
     int32_t uniform_tiles;   // tiles per sample when every sample has the same size, else 0
     int32_t stochastic;      // 16-bit storage rounds stochastically
     int32_t test_withhold;   // persistent mode test hook: block 0 withholds its barrier arrival
+    int32_t any_bouzidi;     // some sample uses the Bouzidi obstacle scheme
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -99,6 +104,10 @@ cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStrea
 // Step dt of a chunk whose base step has parity base_parity (the AA parity of the launch).
 cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                         int dt, int base_parity, cudaStream_t s);
+// Obstacle force of the Bouzidi samples at step dt + 1 of a chunk (no-op off the QoI steps);
+// launched after step dt of the chunk, before step dt + 1.
+cudaError_t launch_bouzidi_force(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
+                                 int dt, int base_parity, cudaStream_t s);
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
 cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
 // Persistent mode: one cooperative launch runs `chunk` steps (tile tickets must be zero).

@@ -25,6 +25,7 @@ UQLB_BASIS_TOTAL, UQLB_BASIS_TENSOR = 0, 1
 UQLB_QUAD_GAUSS_LEGENDRE_TENSOR, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 0, 1
 UQLB_METHOD_NONE, UQLB_METHOD_MC, UQLB_METHOD_GPC = 0, 1, 2
 UQLB_CASE_TGV, UQLB_CASE_CHANNEL, UQLB_CASE_TGV_PERTURBED = 0, 1, 2
+UQLB_OBSTACLE_HALFWAY, UQLB_OBSTACLE_BOUZIDI = 0, 1
 (UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3, UQLB_PARAM_PERT00, UQLB_PARAM_PERT01,
  UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
 UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16 = 0, 1, 2, 3
@@ -48,7 +49,8 @@ class uqlb_sample(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("nx", c_int32), ("ny", c_int32), ("steady_checks", c_int32),
                 ("steps", c_int64), ("nu", c_double), ("u0", c_double), ("amp2", c_double),
                 ("amp3", c_double), ("u_ref", c_double), ("cyl_cx", c_double), ("cyl_cy", c_double),
-                ("cyl_r", c_double), ("ramp_steps", c_int64), ("steady_tol", c_double), ("pert", c_double * 4)]
+                ("cyl_r", c_double), ("ramp_steps", c_int64), ("steady_tol", c_double), ("pert", c_double * 4),
+                ("obstacle_bc", c_int32), ("reserved", c_int32)]
 
 
 class uqlb_case(ctypes.Structure):

@@ -154,6 +154,43 @@ def test_channel_obstacle_f64_fields_and_forces(ens, steps):
         assert np.allclose(g["series_cl"][i, :ns], r.series_cl[:ns], rtol=1e-9, atol=1e-12)
 
 
+@pytest.mark.parametrize("steps", [600, 601])
+def test_bouzidi_obstacle_matches_oracle(ens, steps):
+    """Bouzidi interpolated bounce-back on the obstacle (Sec. 8.1): fields, the C_D / C_L series
+    written by the between-step force kernel and the final forces against the oracle, for odd and
+    even step counts (both AA parities of the last step).  FP32 forces carry 1e-4: the momentum
+    sum cancels terms ~10x larger than the force."""
+    specs = [_cyl(5, steps, u_mean=0.036, bc="bouzidi"), _cyl(5, steps, u_mean=0.044, bc="bouzidi")]
+    ref = olbm.run([oracle_case(s, qoi_every=50) for s in specs])
+    ns = steps // 50
+    for storage, tol_f in (("f64", 1e-11), ("f32", 1e-4)):
+        g = _run(ens, specs, storage, qoi_every=50, series=True)
+        for i, r in enumerate(ref):
+            assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL[storage], storage
+            assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < tol_f * abs(r.cd), storage
+            assert abs(g["qoi"][i, U.UQLB_QOI_CL] - r.cl) < tol_f * abs(r.cd), storage
+            assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=tol_f, atol=0), storage
+            assert np.allclose(g["series_cl"][i, :ns], r.series_cl[:ns], rtol=0, atol=tol_f * abs(r.cd)), storage
+
+
+def test_bouzidi_steady_state_stops_with_the_oracle_in_a_mixed_batch(ens):
+    """The force kernel runs between steps, so a Bouzidi sample stops at the same step as the
+    oracle; halfway and TGV samples in the same batch are unaffected."""
+    specs = [_cyl(4, 20000, u_mean=0.04, steady_tol=1e-6, bc="bouzidi"),
+             _cyl(4, 20000, u_mean=0.036, steady_tol=1e-6), W.tgv(40, 300, nu=0.03)]
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f64", fields_dtype="f64", qoi_every=100,
+                        series=True, fields=False)
+    torch.cuda.synchronize()
+    q = res["qoi"].cpu().numpy()
+    ref = olbm.run([oracle_case(s, qoi_every=100) for s in specs])
+    for i in (0, 1):
+        assert ref[i].steps_run < 20000
+        assert q[i, U.UQLB_QOI_STEPS] == ref[i].steps_run
+        assert abs(q[i, U.UQLB_QOI_CD] - ref[i].cd) < 1e-10 * abs(ref[i].cd)
+        assert abs(q[i, U.UQLB_QOI_MASS] - ref[i].mass) < 1e-12 * ref[i].mass
+    assert abs(q[2, U.UQLB_QOI_K] - ref[2].k_final) < 1e-12 * ref[2].k_final
+
+
 def test_channel_without_obstacle_and_f32(ens):
     specs = [W.channel(6, steps=600, obstacle=False, steady_tol=0.0, re=5.0), _cyl(6, 600)]
     for storage in ("f64", "f32"):
@@ -370,7 +407,7 @@ def test_paper_perturbed_tgv_matches_oracle(ens):
 def test_resume_continues_the_run_exactly(ens, split):
     """A run of `split` steps resumed to 100 steps equals a single 100-step run bit for bit
     (odd and even split points; the workspace carries the state)."""
-    specs = _tgv_specs(40, 100) + [_cyl(4, 100, u_mean=0.04)]
+    specs = _tgv_specs(40, 100) + [_cyl(4, 100, u_mean=0.04), _cyl(4, 100, u_mean=0.04, bc="bouzidi")]
     whole = _run(ens, specs, "f64", qoi_every=10, series=True)
     first = [sample_struct(s) for s in specs]
     for s in first:

@@ -31,8 +31,8 @@ def test_library_exports_every_header_symbol():
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(U.uqlb_dist) == 24
-    assert ctypes.sizeof(U.uqlb_sample) == 136
-    assert ctypes.sizeof(U.uqlb_case) == 168
+    assert ctypes.sizeof(U.uqlb_sample) == 144
+    assert ctypes.sizeof(U.uqlb_case) == 176
     assert ctypes.sizeof(U.uqlb_run_opts) == 48
 
 
@@ -266,6 +266,22 @@ def test_cylinder_method_comparison_samples_are_nested_and_in_the_inflow_range()
             assert [s.u0 for s in small] == [s.u0 for s in big[:10]]
     finally:
         U.uqlb_destroy(ctx)
+
+
+def test_bouzidi_samples_are_checked():
+    """The obstacle scheme is validated, and Bouzidi batches are refused outside graph mode (the
+    force kernel runs between step launches)."""
+    s = sample_struct(W.channel(5, steps=10, steady_tol=0.0, bc="bouzidi"))
+    graph = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 10, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, 0)
+    assert U.uqlb_batch_workspace_bytes([s], graph) > 0
+    pers = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 10, 0, 0, 0, 0, 0, U.UQLB_MODE_PERSISTENT, 0)
+    with pytest.raises(U.UqlbError) as e:
+        U.uqlb_batch_workspace_bytes([s], pers)
+    assert e.value.status == U.UQLB_ERR_ARG
+    s.obstacle_bc = 7
+    with pytest.raises(U.UqlbError) as e:
+        U.uqlb_batch_workspace_bytes([s], graph)
+    assert e.value.status == U.UQLB_ERR_ARG
 
 
 def test_untuned_workspace_covers_every_geometry_for_every_entry_point():

@@ -28,8 +28,12 @@ sys.path.insert(0, ROOT)
 METRIC = "ensemble MLUPS (tgv256_gpc4d: 625 samples x 256^2 x 2000 steps, FP32 storage, FP64 gPC statistics)"
 UNIT = "MLUPS"
 BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
-# version tag of the step kernel whose ncu traffic profiles/step_kernel_f32_tgv256.md records
-STEP_KERNEL_VERSION = "aa-npt-nbr-pair"
+# per scheme: the step kernel, the profile holding its ncu traffic, and the kernel version that
+# profile was taken on (a mismatch reports traffic as null)
+STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in place)", "step_kernel_f32_tgv256.md",
+                    "aa-npt-nbr-pair"),
+                2: ("step2_kernel (two-step: tile + halo collided into shared memory, streamed and collided "
+                    "again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v1")}
 
 
 def _peaks():
@@ -180,12 +184,15 @@ def bench_kernel_only(args):
     out = {}
     for _ in range(args.warmup + args.steps):
         ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
-                      nodes_per_thread=args.npt, rounding=args.rounding, mode=args.mode)
+                      nodes_per_thread=args.npt, rounding=args.rounding, mode=args.mode, scheme=args.scheme)
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
+    scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
+    per_launch = 2 if scheme == U.UQLB_SCHEME_TWO_STEP else 1
     nodes = sum(s.nx * s.ny for s in smp)
-    gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st, 1) / 1e3) / 1e9
-    print(json.dumps({"kernel_only": True, "mode": args.mode, "samples": len(smp), "time_steps": st,
+    gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st / per_launch, 1) / 1e3) / 1e9
+    print(json.dumps({"kernel_only": True, "mode": args.mode, "scheme": scheme, "tile": [g_rows, g_npt],
+                      "samples": len(smp), "time_steps": st, "mlups": nodes * st / (ms / 1e3) / 1e6,
                       "storage": args.storage,
                       "loop_ms": ms, "step_ms": ms / max(st, 1), "achieved_gbs": gbs,
                       "arena_bytes": BYTES_PER_UPDATE[args.storage] // 2 * nodes}))
@@ -495,10 +502,11 @@ def bench_gpu(args):
     coeffs = torch.empty((K, F), dtype=torch.float64, device=dev)
     out = {"fields": fields, "qoi": qoi}
 
-    tuned = ens.autotune(smp, storage=storage, trial_steps=args.tune_steps) if args.tune_steps > 0 else None
+    tuned = (ens.autotune(smp, storage=storage, trial_steps=args.tune_steps, scheme=args.scheme)
+             if args.tune_steps > 0 else None)
 
     def one_step():
-        ens.run_batch(smp, storage=storage, fields_dtype="f32", out=out)
+        ens.run_batch(smp, storage=storage, fields_dtype="f32", out=out, scheme=args.scheme)
         ens.project(fields, coeffs)
         return ens.stats(coeffs)
 
@@ -538,14 +546,18 @@ def bench_gpu(args):
         total_ms = float(t.item())
     value = world * upd_per_step * args.steps / (total_ms / 1e3) / 1e6
 
-    # roofline of the dominant kernel (the fused step), from its event-timed loop
+    # roofline of the dominant kernel, from its event-timed loop.  One launch reads and writes
+    # every population once (72 B per FP32 node); the two-step kernel advances two steps per launch.
+    scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
+    steps_per_launch = 2 if scheme == U.UQLB_SCHEME_TWO_STEP else 1
+    kernel_name, prof_name, kernel_version = STEP_KERNELS[scheme]
     nodes = S * w.base.nx * w.base.ny
     per_launch_bytes = BYTES_PER_UPDATE[storage] * nodes
-    step_kernel_ms = loop_ms / max(loop_steps, 1)
+    step_kernel_ms = loop_ms / max(loop_steps / steps_per_launch, 1)
     achieved = per_launch_bytes / (step_kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "step_kernel_f32_tgv256.md")
+    prof = os.path.join(ROOT, "profiles", prof_name)
     if storage == "f32" and os.path.exists(prof):
         import re
 
@@ -553,7 +565,7 @@ def bench_gpu(args):
             text = fh.read()
         ver = re.search(r"^kernel_version: (\S+)", text, flags=re.M)
         tb = re.search(r"^traffic_bytes_per_launch_full_size: (\d+)", text, flags=re.M)
-        if ver and tb and ver.group(1) == STEP_KERNEL_VERSION:
+        if ver and tb and ver.group(1) == kernel_version:
             traffic = int(tb.group(1))
 
     # end to end through host buffers: one C call, tables in, statistics out
@@ -615,13 +627,14 @@ def bench_gpu(args):
                 "config": {"workload": "tgv256_gpc4d", "samples": S, "lattice": [256, 256], "time_steps": 2000,
                            "storage": storage, "statistics": "fp64", "gpc_terms": K,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                           "l2": "lattice arena 1.47 GB > L2 129 MB: each time step streams from HBM",
+                           "l2": "lattice arena 1.47 GB > L2 129 MB: each launch streams from HBM",
+                           "scheme": "two_step" if scheme == U.UQLB_SCHEME_TWO_STEP else "one_step",
                            "tile_geometry": None if tuned is None else
                            {"tile_rows": tuned["tile_rows"], "nodes_per_thread": tuned["nodes_per_thread"],
                             "autotune_ms_per_step": {f"{r}x{q}": round(ms, 4) for r, q, ms in tuned["tried"]}}},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": "step_kernel (fused AA collide-stream-QoI)",
+                             "kernel": kernel_name, "time_steps_per_launch": steps_per_launch,
                              "algorithmic_bytes_per_launch": per_launch_bytes,
                              "kernel_ms_per_launch": step_kernel_ms},
                 "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
@@ -651,6 +664,8 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
+    ap.add_argument("--scheme", default="auto", choices=["auto", "one_step", "two_step"],
+                    help="time-stepping scheme (auto: two-step for periodic FP32/16-bit batches)")
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent"],
                     help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")
     ap.add_argument("--workload", default="tgv256_gpc4d",

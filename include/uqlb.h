@@ -151,10 +151,11 @@ typedef struct {
 } uqlb_case;
 
 /* Options of a run.  Tile geometry: a tile is (32 x nodes_per_thread) columns by tile_rows rows
- * of one sample, run by 32 x tile_rows threads.  Compiled geometries: FP32/FP16/BF16 TGV-only
- * batches tile_rows in {2, 4, 8} x nodes_per_thread in {1, 2, 4}; FP64 (8,1), (4,1), (4,2);
- * batches with CHANNEL samples (8,1), (4,1).  Both 0: the geometry the context's autotuner
- * picked for this batch shape (uqlb_autotune), else the default for the storage. */
+ * of one sample, run by 32 x tile_rows threads.  Compiled geometries, one-step scheme:
+ * FP32/FP16/BF16 TGV-only batches tile_rows in {2, 4, 8} x nodes_per_thread in {1, 2, 4}; FP64
+ * (8,1), (4,1), (4,2); batches with CHANNEL samples (8,1), (4,1).  Two-step scheme: FP32/FP16/
+ * BF16 (4,4), (8,2), (8,4), (16,2), (16,4); FP64 (4,2), (8,1), (8,2).  Both 0: the geometry the
+ * context's autotuner picked for this batch shape (uqlb_autotune), else the default. */
 typedef struct {
     int32_t storage;          /* population storage: UQLB_F64, F32, F16 or BF16 (stored as f - w) */
     int32_t fields_dtype;     /* dtype of the field output M: UQLB_F64 or UQLB_F32 */
@@ -169,8 +170,23 @@ typedef struct {
                                  its new total).  The workspace can be saved and restored between the
                                  two calls (checkpoint). */
     int32_t mode;             /* UQLB_MODE_GRAPH or UQLB_MODE_PERSISTENT (see below) */
-    int32_t reserved;
+    int32_t scheme;           /* time-stepping scheme, UQLB_SCHEME_* (see below) */
 } uqlb_run_opts;
+
+/* Time-stepping scheme (the same BGK update of Sec. 3; they differ in how populations move
+ * through memory).
+ *   UQLB_SCHEME_ONE_STEP: one launch per time step, populations updated in place (AA order),
+ *     72 B of HBM traffic per FP32 node update.  Every case kind and mode.
+ *   UQLB_SCHEME_TWO_STEP: one launch per two time steps on two lattices; a block loads its tile
+ *     with a one-node halo, collides it into shared memory, then streams, collides again and
+ *     writes the tile: ~40 B per FP32 node update.  Periodic (TGV, TGV_PERTURBED) batches in
+ *     UQLB_MODE_GRAPH; the workspace holds the second lattice.  FP32/FP64 results agree with the
+ *     one-step scheme's to round-off (same formulas per node); 16-bit storage rounds half as often.
+ *   UQLB_SCHEME_AUTO: TWO_STEP for periodic FP32 and FP16 batches in graph mode, where it
+ *     measured faster on GB300 (625 x 256^2 ensemble: 0.393 against 0.485 ms per FP32 step, 0.479
+ *     against 0.501 ms per FP16 step); ONE_STEP otherwise (BF16 ran 0.460 against 0.454 ms).
+ * A resumed run (start_step > 0) must use the scheme of the run it continues. */
+enum { UQLB_SCHEME_AUTO = 0, UQLB_SCHEME_ONE_STEP = 1, UQLB_SCHEME_TWO_STEP = 2 };
 
 /* Execution of the time loop.
  *   UQLB_MODE_GRAPH: one launch per step, captured as CUDA graphs of chunk_steps launches.
@@ -331,6 +347,11 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
  * the loop; launches: kernels the whole run enqueued (init, steps, counter advances, finalize).
  * Synchronises on the end event.  Any output may be NULL. */
 int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches);
+
+/* Scheme (UQLB_SCHEME_ONE_STEP or UQLB_SCHEME_TWO_STEP) and tile geometry the last
+ * uqlb_run_batch / uqlb_run_ensemble on this context used.  Any output may be NULL;
+ * UQLB_ERR_STATE before the first run. */
+int uqlb_last_run_geometry(const uqlb_ctx* ctx, int32_t* scheme, int32_t* tile_rows, int32_t* nodes_per_thread);
 
 /* ------------------------------------------------------------------------------------
  * Statistical-solution distance (Sec. 8.3)

@@ -29,6 +29,8 @@ constexpr int kTileCols = 32;
 
 struct KParams {
     void* arena;
+    void* arena2;          // two-step scheme: second lattice
+    int32_t* sel;          // two-step scheme: lattice holding each sample's state at the run's start
     const SampleDev* samples;
     const InitDev* init;
     const int32_t* steps_sorted;
@@ -282,6 +284,7 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
             p.steps_run[j] = sp.steps;
             p.cd_prev[j] = NAN;
             p.streak[j] = 0;
+            if (p.sel != nullptr) p.sel[j] = 0;  // the initial state is in the first lattice
         }
         for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
@@ -698,6 +701,175 @@ __global__ void __launch_bounds__(kTileCols* TR) persistent_kernel(KParams p, in
 }
 
 // ------------------------------------------------------------------------------------------
+// Two-step scheme (periodic batches): one launch moves every running sample two steps ahead,
+// from one lattice to the other.  A block loads its tile with a one-node halo (natural layout,
+// periodic wrap), collides it into shared memory, then streams from shared memory, collides the
+// tile again and pushes the result into the other lattice.  HBM traffic per launch: the tile and
+// its halo read once, the tile written once.  A sample with one step left takes one
+// collide-and-push step.  Every launch of a run moves each running sample to the other lattice,
+// so at the launch of step t (t - t0 even, t0 the run's first step) a sample's state is on
+// lattice sel ^ ((t - t0) / 2 & 1).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int launches_of(int t_end, int t0) { return t_end > t0 ? (t_end - t0 + 1) >> 1 : 0; }
+
+__device__ __forceinline__ bool on_final_second(const KParams& p, int j, int T) {
+    return ((p.sel[j] ^ launches_of(T, (int)p.step_counter[1])) & 1) != 0;
+}
+
+template <typename S, int TR, int NPT>
+__global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 6 : (TR == 8 ? 3 : 1)) step2_kernel(KParams p) {
+    using C = typename Storage<S>::C;
+    constexpr int NT = kTileCols * TR, TW = kTileCols * NPT, EW = TW + 2, EH = TR + 2;
+    __shared__ TileShared<NT> sh;
+    extern __shared__ __align__(16) unsigned char s2_raw[];
+    C* sm = reinterpret_cast<C*>(s2_raw);  // post-collision tile + halo, [9][EH][EW]
+    const int t = (int)p.step_counter[0] + p.dt;
+    const int t0 = (int)p.step_counter[1];
+    step_extent(p, t, sh);
+    const int nact = sh.nact, ntiles = sh.ntiles;
+    const bool want_a = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
+    const bool want_b0 = p.qoi_every > 0 && p.series != nullptr && ((t + 1) % p.qoi_every) == 0;
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (ty == 0) {
+            const int jj = tile_sample(p, tile, nact);
+            reinterpret_cast<uint32_t*>(&sh.sp)[lane] = __ldg(reinterpret_cast<const uint32_t*>(p.samples + jj) + lane);
+            if (lane == 0) sh.j = jj;
+        }
+        __syncthreads();
+        const int j = sh.j;
+        const SampleDev& sp = sh.sp;
+        const bool two = t + 1 < sp.steps;
+        const bool want_b = two && want_b0;
+        const int lt = tile - sp.tile_base;
+        const int x0 = (lt % sp.tiles_x) * TW, y0 = (lt / sp.tiles_x) * TR;
+        const int wa = min(TW, sp.nx - x0), ha = min(TR, sp.ny - y0);  // active columns and rows
+        const bool second = ((p.sel[j] ^ ((t - t0) >> 1)) & 1) != 0;
+        const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + sp.f_off;
+        S* dst = static_cast<S*>(second ? p.arena : p.arena2) + sp.f_off;
+        const int plane = (int)sp.plane, pitch = sp.pitch, nx = sp.nx, ny = sp.ny;
+        const C omega = (C)sp.omega;
+        double red[2] = {0.0, 0.0};
+        // collide-and-push of one node's post-collision populations g (step ts) into dst
+        auto push = [&](int x, int y, int ts, const C (&g)[9]) {
+            const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const int col[3] = {xm, x, xp};
+            const int row[3] = {ym * pitch, y * pitch, yp * pitch};
+            const uint32_t h = sr ? mix32((uint32_t)(y * pitch + x) * 0x9E3779B1u + (uint32_t)ts * 0x85EBCA77u +
+                                          (uint32_t)sp.sample_id * 0xC2B2AE3Du)
+                                  : 0u;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                S* ptr = dst + (i * plane + row[1 + cy(i)] + col[1 + cx(i)]);
+                if (sr)
+                    Storage<S>::store_sr(ptr, g[i], (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16);
+                else
+                    Storage<S>::store(ptr, g[i]);
+            }
+        };
+        if (!two) {
+            const int y = y0 + ty;
+            C g[NPT][9];
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int x = x0 + lane + kTileCols * k;
+                if (lane + kTileCols * k < wa && ty < ha) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[k][i] = Storage<S>::load(src + (i * plane + y * pitch + x));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+                const int x = x0 + lane + kTileCols * k;
+                if (lane + kTileCols * k < wa && ty < ha) {
+                    C drho, jx, jy, ux, uy;
+                    moments(g[k], drho, jx, jy, ux, uy);
+                    if (want_a) red[0] += (double)(ux * ux + uy * uy);
+                    bgk(g[k], omega, drho, jx, jy, ux, uy);
+                    push(x, y, t, g[k]);
+                }
+            }
+        } else {
+            // phase A: the tile and its halo at step t, post-collision values into shared memory.
+            // The (TW + 2) x (TR + 2) nodes are dealt out row-major over all threads, MB at a
+            // time (all their loads issued before any arithmetic).
+            constexpr int EXT = EW * EH, MB = 3;
+            const int tid = lane + kTileCols * ty;
+#pragma unroll 1
+            for (int e0 = 0; e0 < EXT; e0 += NT * MB) {
+                C g[MB][9];
+                int ex[MB], ey[MB];
+                bool ok[MB];
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    const int e = e0 + tid + NT * m;
+                    ey[m] = e / EW;
+                    ex[m] = e - ey[m] * EW;
+                    ok[m] = e < EXT && ex[m] <= wa + 1 && ey[m] <= ha + 1;
+                    if (ok[m]) {
+                        int gx = x0 - 1 + ex[m], gy = y0 - 1 + ey[m];
+                        gx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+                        gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+                        const S* q = src + (gy * pitch + gx);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) g[m][i] = Storage<S>::load(q + i * plane);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < MB; ++m) {
+                    if (!ok[m]) continue;
+                    C drho, jx, jy, ux, uy;
+                    moments(g[m], drho, jx, jy, ux, uy);
+                    if (want_a && ex[m] >= 1 && ex[m] <= wa && ey[m] >= 1 && ey[m] <= ha)
+                        red[0] += (double)(ux * ux + uy * uy);
+                    bgk(g[m], omega, drho, jx, jy, ux, uy);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) sm[(i * EH + ey[m]) * EW + ex[m]] = g[m][i];
+                }
+            }
+            __syncthreads();
+            // phase B: stream from shared memory, collide at step t + 1, push into the other lattice
+            const int y = y0 + ty, ey = ty + 1;
+            if (ty < ha) {
+#pragma unroll
+                for (int k = 0; k < NPT; ++k) {
+                    const int ex = lane + kTileCols * k + 1;
+                    if (ex > wa) continue;
+                    C g[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = sm[(i * EH + ey - cy(i)) * EW + ex - cx(i)];
+                    C drho, jx, jy, ux, uy;
+                    moments(g, drho, jx, jy, ux, uy);
+                    if (want_b) red[1] += (double)(ux * ux + uy * uy);
+                    bgk(g, omega, drho, jx, jy, ux, uy);
+                    push(x0 + ex - 1, y, t + 1, g);
+                }
+            }
+        }
+        if (want_a || want_b) {
+            double tot[2];
+            if (tile_reduce_last<2, NT>(p, sp, j, tile, red, tot, sh.red, &sh.flag)) {
+                if (lane == 0 && ty == 0) {
+                    if (want_a) p.series[(int64_t)sp.sample_id * p.series_ld + t / p.qoi_every] = tot[0] * sp.u_ref_inv2;
+                    if (want_b)
+                        p.series[(int64_t)sp.sample_id * p.series_ld + (t + 1) / p.qoi_every] = tot[1] * sp.u_ref_inv2;
+                }
+            }
+        } else {
+            __syncthreads();  // the next tile reuses shared memory
+        }
+    }
+}
+
+// After the finalize of a two-step run: the lattice that now holds each sample's state.
+__global__ void commit_kernel(KParams p) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.nsamples; j += gridDim.x * blockDim.x)
+        p.sel[j] ^= launches_of(p.steps_run[j], (int)p.step_counter[1]) & 1;
+}
+
+// ------------------------------------------------------------------------------------------
 // Final fields and per-sample scalars at the last step run.
 // ------------------------------------------------------------------------------------------
 template <typename S, bool MIXED>
@@ -716,6 +888,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         const uint32_t* mask = (sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
         const InitDev* bz = (chan && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
+        // two-step scheme: the state is in natural layout on the lattice the last launch wrote
+        const bool two = p.sel != nullptr;
+        S* lat = arena;
+        if (two && on_final_second(p, j, T)) lat = static_cast<S*>(p.arena2);
         double red[7] = {0, 0, 0, 0, 0, 0, 0};  // K, mass, mx, my, fx, fy, bad
         for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
@@ -724,10 +900,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
             const bool solid = mask != nullptr && mask_solid(mask, sp.mask_words, x, y);
             double ux = 0.0, uy = 0.0;
             if (!solid) {
-                S* base = arena + sp.f_off;
+                S* base = lat + sp.f_off;
                 const int64_t own = (int64_t)y * sp.pitch + x;
                 C g[9];
-                if ((T & 1) == 0) {
+                if (two || (T & 1) == 0) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own);
                 } else {
@@ -900,6 +1076,8 @@ __global__ void resume_kernel(KParams p) {
 KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs* o, int dt) {
     KParams p{};
     p.arena = b.arena;
+    p.arena2 = b.arena2;
+    p.sel = b.sel;
     p.samples = b.samples;
     p.init = b.init;
     p.steps_sorted = b.steps_sorted;
@@ -1007,6 +1185,90 @@ cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cu
 }
 
 }  // namespace
+
+bool geometry_supported2(int storage, int tile_rows, int npt) {
+    const int tr = tile_rows, n = npt;
+    if (storage == UQLB_F64) return (tr == 4 && n == 2) || (tr == 8 && (n == 1 || n == 2));
+    return (tr == 4 && n == 4) || ((tr == 8 || tr == 16) && (n == 2 || n == 4));
+}
+
+namespace {
+
+template <typename S, int TR, int NPT>
+constexpr size_t step2_smem() {
+    return sizeof(typename Storage<S>::C) * 9 * (TR + 2) * (kTileCols * NPT + 2);
+}
+
+// Shared-memory opt-in and resident blocks per SM of one two-step instantiation (once).
+template <typename S, int TR, int NPT>
+int resident_blocks2() {
+    static int n = 0;
+    if (n == 0) {
+        constexpr size_t smem = step2_smem<S, TR, NPT>();
+        cudaFuncSetAttribute(step2_kernel<S, TR, NPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, step2_kernel<S, TR, NPT>, kTileCols * TR, smem) !=
+                cudaSuccess || b < 1)
+            b = 1;
+        n = b;
+    }
+    return n;
+}
+
+template <typename S, int TR, int NPT>
+cudaError_t launch_geom2(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const int64_t resident = (int64_t)resident_blocks2<S, TR, NPT>() * sm_count();
+    if (prepare_only) return cudaGetLastError();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_tiles, resident));
+    step2_kernel<S, TR, NPT><<<grid, dim3(kTileCols, TR), step2_smem<S, TR, NPT>(), s>>>(p);
+    return cudaGetLastError();
+}
+
+#define UQLB_GEOM2(TR_, NPT_) \
+    if (g.tile_rows == TR_ && g.npt == NPT_) return launch_geom2<S, TR_, NPT_>(p, g, s, prepare_only);
+template <typename S>
+cudaError_t launch_step2_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    if constexpr (sizeof(S) == 8) {
+        UQLB_GEOM2(4, 2)
+        UQLB_GEOM2(8, 1)
+        UQLB_GEOM2(8, 2)
+    } else {
+        UQLB_GEOM2(4, 4)
+        UQLB_GEOM2(8, 2)
+        UQLB_GEOM2(8, 4)
+        UQLB_GEOM2(16, 2)
+        UQLB_GEOM2(16, 4)
+    }
+    return cudaErrorInvalidConfiguration;
+}
+#undef UQLB_GEOM2
+
+cudaError_t step2_dispatch(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    switch (g.storage) {
+        case UQLB_F64: return launch_step2_s<double>(p, g, s, prepare_only);
+        case UQLB_F32: return launch_step2_s<float>(p, g, s, prepare_only);
+        case UQLB_F16: return launch_step2_s<__half>(p, g, s, prepare_only);
+        default: return launch_step2_s<__nv_bfloat16>(p, g, s, prepare_only);
+    }
+}
+
+}  // namespace
+
+cudaError_t prepare_step2(const BatchGeometry& g) {
+    KParams p{};
+    return step2_dispatch(p, g, nullptr, true);
+}
+
+cudaError_t launch_step2(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt, cudaStream_t s) {
+    return step2_dispatch(make_params(b, g, &o, dt), g, s, false);
+}
+
+cudaError_t launch_commit(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
+    KParams p = make_params(b, g, nullptr, 0);
+    const int grid = (int)std::min<int64_t>((g.nsamples + 255) / 256, 1024);
+    commit_kernel<<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt) {
     const int tr = tile_rows, n = npt;

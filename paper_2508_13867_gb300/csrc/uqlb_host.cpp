@@ -52,8 +52,8 @@ struct uqlb_ctx {
         int rows, npt;
     };
     std::vector<Tuned> tuned;
-    int last_rows = 0, last_npt = 0;
-    int64_t start_step_host = 0;
+    int last_rows = 0, last_npt = 0, last_scheme = 0;
+    int64_t counter_host[2] = {0, 0};  // source of the step-counter upload (step, first step of the run)
     int32_t* bar_err = nullptr;  // device error word of the last run
 };
 
@@ -300,7 +300,7 @@ struct BatchPlan {
     std::vector<InitDev> init;
     std::vector<int32_t> steps_sorted;
     std::vector<uint32_t> masks;
-    size_t off_arena = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
+    size_t off_arena = 0, off_arena2 = 0, off_sel = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
            off_partials = 0, off_counters = 0, off_done = 0, off_steps_run = 0, off_cd_prev = 0,
            off_step_counter = 0, off_flag = 0, off_streak = 0, off_sync = 0, total = 0;
     BatchGeometry geom{};
@@ -348,16 +348,42 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         if (int rc = validate_sample(smp[s], s, why)) return rc;
     bool mixed = false;
     for (int64_t s = 0; s < n; ++s) mixed = mixed || smp[s].kind == UQLB_CASE_CHANNEL;
+    const int mode = o ? o->mode : UQLB_MODE_GRAPH;
+    if (mode < UQLB_MODE_GRAPH || mode > UQLB_MODE_PERSISTENT_TEST_TIMEOUT) {
+        why = "unknown execution mode";
+        return UQLB_ERR_ARG;
+    }
+    const int scheme = o ? o->scheme : UQLB_SCHEME_AUTO;
+    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_TWO_STEP) {
+        why = "unknown time-stepping scheme";
+        return UQLB_ERR_ARG;
+    }
+    // auto: the two-step scheme where it measured faster (periodic FP32 and FP16 batches)
+    const bool two = scheme == UQLB_SCHEME_TWO_STEP ||
+                     (scheme == UQLB_SCHEME_AUTO && !mixed && mode == UQLB_MODE_GRAPH &&
+                      (storage == UQLB_F32 || storage == UQLB_F16));
+    if (two && (mixed || mode != UQLB_MODE_GRAPH)) {
+        why = "the two-step scheme runs periodic (TGV) batches in UQLB_MODE_GRAPH only";
+        return UQLB_ERR_ARG;
+    }
+    auto supported = [&](int r, int q) {
+        return two ? geometry_supported2(storage, r, q) : geometry_supported(storage, mixed, r, q);
+    };
     int tr = o ? o->tile_rows : 0, npt = o ? o->nodes_per_thread : 0;
     if (tr == 0 && npt == 0) {
         tr = tuned_rows;
         npt = tuned_npt;
-        if (tr == 0 || !geometry_supported(storage, mixed, tr, npt)) {
-            tr = (mixed || storage == UQLB_F64) ? 8 : 4;
-            npt = (mixed || storage == UQLB_F64) ? 1 : 2;
+        if (tr == 0 || !supported(tr, npt)) {
+            if (two) {
+                tr = 8;
+                npt = storage == UQLB_F64 ? 1 : 4;
+            } else {
+                tr = (mixed || storage == UQLB_F64) ? 8 : 4;
+                npt = (mixed || storage == UQLB_F64) ? 1 : 2;
+            }
         }
     }
-    if (!geometry_supported(storage, mixed, tr, npt)) {
+    if (!supported(tr, npt)) {
         char buf[160];
         snprintf(buf, sizeof buf, "tile geometry tile_rows=%d nodes_per_thread=%d is not compiled for this batch", tr, npt);
         why = buf;
@@ -464,6 +490,8 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return at;
     };
     P.off_arena = take((size_t)f_off * eb);
+    P.off_arena2 = two ? take((size_t)f_off * eb) : 0;
+    P.off_sel = two ? take(sizeof(int32_t) * n) : 0;
     P.off_samples = take(sizeof(SampleDev) * n);
     P.off_init = take(sizeof(InitDev) * n);
     P.off_steps = take(sizeof(int32_t) * n);
@@ -474,7 +502,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.off_done = take(sizeof(int32_t) * n);
     P.off_steps_run = take(sizeof(int32_t) * n);
     P.off_cd_prev = take(sizeof(double) * n);
-    P.off_step_counter = take(sizeof(int64_t));
+    P.off_step_counter = take(2 * sizeof(int64_t));
     P.off_flag = take(sizeof(int32_t));
     P.off_streak = take(sizeof(int32_t) * n);
     P.off_sync = take(64);  // barrier count, generation, error word, ticket counter
@@ -495,11 +523,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     g.stochastic = (eb == 2 && rounding != UQLB_ROUND_NEAREST) ? 1 : 0;
-    const int mode = o ? o->mode : UQLB_MODE_GRAPH;
-    if (mode < UQLB_MODE_GRAPH || mode > UQLB_MODE_PERSISTENT_TEST_TIMEOUT) {
-        why = "unknown execution mode";
-        return UQLB_ERR_ARG;
-    }
+    g.two_step = two ? 1 : 0;
     g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
     g.any_bouzidi = any_bouzidi;
     if (any_bouzidi && mode != UQLB_MODE_GRAPH) {
@@ -513,6 +537,8 @@ BatchBuffers carve(const BatchPlan& P, void* ws) {
     char* b = static_cast<char*>(ws);
     BatchBuffers B{};
     B.arena = b + P.off_arena;
+    B.arena2 = P.geom.two_step ? b + P.off_arena2 : nullptr;
+    B.sel = P.geom.two_step ? reinterpret_cast<int32_t*>(b + P.off_sel) : nullptr;
     B.samples = reinterpret_cast<SampleDev*>(b + P.off_samples);
     B.init = reinterpret_cast<InitDev*>(b + P.off_init);
     B.steps_sorted = reinterpret_cast<int32_t*>(b + P.off_steps);
@@ -563,10 +589,14 @@ int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, co
     err = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamBeginCapture");
     cudaError_t lerr = cudaSuccess;
-    for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) {
-        lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
-        if (lerr == cudaSuccess && G.any_bouzidi && O.qoi_every > 0)
-            lerr = launch_bouzidi_force(B, G, O, dt, parity, ctx->capture_stream);
+    if (G.two_step) {
+        for (int dt = 0; dt < chunk && lerr == cudaSuccess; dt += 2) lerr = launch_step2(B, G, O, dt, ctx->capture_stream);
+    } else {
+        for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) {
+            lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
+            if (lerr == cudaSuccess && G.any_bouzidi && O.qoi_every > 0)
+                lerr = launch_bouzidi_force(B, G, O, dt, parity, ctx->capture_stream);
+        }
     }
     if (lerr == cudaSuccess) lerr = launch_advance(B, chunk, ctx->capture_stream);
     cudaGraph_t graph = nullptr;
@@ -637,7 +667,7 @@ int check_case(uqlb_ctx* ctx, const uqlb_case* c) {
     return 0;
 }
 
-const int kGeomRows[] = {2, 4, 8};
+const int kGeomRows[] = {2, 4, 8, 16};
 const int kGeomNpt[] = {1, 2, 4};
 
 // Workspace of a batch: the planned layout, and with both geometry fields 0 the largest layout of
@@ -972,9 +1002,21 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
         mixed |= samples[k].kind == UQLB_CASE_CHANNEL;
         nodes += (int64_t)samples[k].nx * samples[k].ny;
     }
+    bool two = false;
+    {
+        BatchPlan P0;
+        std::string why;
+        uqlb_run_opts o0 = *opts;
+        o0.tile_rows = o0.nodes_per_thread = 0;
+        if ((rc = plan_batch(samples, n, &o0, P0, why))) {
+            rc = set_err(ctx, rc, "autotune: %s", why.c_str());
+            goto done;
+        }
+        two = P0.geom.two_step != 0;
+    }
     for (int r : kGeomRows) {
         for (int q : kGeomNpt) {
-            if (!geometry_supported(storage, mixed != 0, r, q)) continue;
+            if (two ? !geometry_supported2(storage, r, q) : !geometry_supported(storage, mixed != 0, r, q)) continue;
             uqlb_run_opts o = *opts;
             o.tile_rows = r;
             o.nodes_per_thread = q;
@@ -1012,13 +1054,17 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
             }
             double ms_best = 1e300;
             for (int pass = 0; pass < 2; ++pass) {
-                if ((e = cudaMemsetAsync(B.step_counter, 0, sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s)) ||
+                if ((e = cudaMemsetAsync(B.step_counter, 0, 2 * sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s)) ||
                     (e = cudaEventRecord(e0, s))) {
                     rc = cuda_fail(ctx, e, "autotune: init");
                     goto done;
                 }
-                for (int dt = 0; dt < trial_steps; ++dt)
-                    if ((e = launch_step(B, P.geom, O, dt, 0, s))) {
+                if (two && (e = prepare_step2(P.geom)) != cudaSuccess) {
+                    rc = cuda_fail(ctx, e, "autotune: prepare");
+                    goto done;
+                }
+                for (int dt = 0; dt < trial_steps; dt += two ? 2 : 1)
+                    if ((e = two ? launch_step2(B, P.geom, O, dt, s) : launch_step(B, P.geom, O, dt, 0, s))) {
                         rc = cuda_fail(ctx, e, "autotune: step launch");
                         goto done;
                     }
@@ -1088,6 +1134,7 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         return set_err(ctx, UQLB_ERR_OOM, "run_batch: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
     ctx->last_rows = P.geom.tile_rows;
     ctx->last_npt = P.geom.npt;
+    ctx->last_scheme = P.geom.two_step ? UQLB_SCHEME_TWO_STEP : UQLB_SCHEME_ONE_STEP;
     if (fields_dev) {
         if (!P.uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
         if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_ld too small");
@@ -1121,8 +1168,8 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         (!resume && (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))))
         return cuda_fail(ctx, e, "run_batch: table upload");
     // the device step counter starts at start_step (0 for a fresh run); ctx keeps the host copy alive
-    ctx->start_step_host = opts->start_step;
-    if ((e = cudaMemcpyAsync(B.step_counter, &ctx->start_step_host, sizeof(int64_t), cudaMemcpyHostToDevice, s)))
+    ctx->counter_host[0] = ctx->counter_host[1] = opts->start_step;
+    if ((e = cudaMemcpyAsync(B.step_counter, ctx->counter_host, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, s)))
         return cuda_fail(ctx, e, "run_batch: step counter");
 
     RunOutputs O{};
@@ -1171,13 +1218,15 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         ctx->loop_timed = true;
     } else if (P.geom.max_steps > opts->start_step) {
         cudaGraphExec_t exec = nullptr;
+        if (P.geom.two_step && (e = prepare_step2(P.geom)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: prepare");
         if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, (int)(opts->start_step & 1), &exec)) return rc;
         const int64_t nchunks = (P.geom.max_steps - opts->start_step + chunk - 1) / chunk;
         const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
         if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
         for (int64_t q = 0; q < nchunks; ++q) {
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
-            ctx->run_launches += chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0);
+            ctx->run_launches += P.geom.two_step ? chunk / 2 + 1
+                                                 : chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0);
             if (steady && (q % 8) == 7 && q + 1 < nchunks) {
                 int32_t ndone = 0;
                 if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
@@ -1190,6 +1239,17 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         ctx->loop_timed = true;
     }
     if ((e = launch_finalize(B, P.geom, O, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: finalize launch");
+    if (P.geom.two_step && (e = launch_commit(B, P.geom, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "run_batch: commit launch");
+    return 0;
+}
+
+int uqlb_last_run_geometry(const uqlb_ctx* ctx, int32_t* scheme, int32_t* tile_rows, int32_t* nodes_per_thread) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (ctx->last_scheme == 0) return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_STATE, "no run yet");
+    if (scheme) *scheme = ctx->last_scheme;
+    if (tile_rows) *tile_rows = ctx->last_rows;
+    if (nodes_per_thread) *nodes_per_thread = ctx->last_npt;
     return 0;
 }
 

@@ -53,6 +53,8 @@ struct alignas(16) InitDev {
 // Device pointers carved out of the caller's workspace for one batch run.
 struct BatchBuffers {
     void* arena;             // populations, storage type
+    void* arena2;            // second lattice of the two-step scheme (nullptr: one-step scheme)
+    int32_t* sel;            // [S] two-step scheme: lattice (0/1) holding the state at the run's start
     SampleDev* samples;      // [S] ordered by descending steps
     InitDev* init;           // [S] same order
     int32_t* steps_sorted;   // [S] descending
@@ -69,7 +71,7 @@ struct BatchBuffers {
     unsigned int* bar_gen;   //   and generation
     int32_t* bar_err;        //   nonzero once a bounded wait gave up (UQLB_ERR_TIMEOUT)
     unsigned long long* tickets;  // persistent mode: tile ticket counter of the running chunk
-    int64_t* step_counter;   // [1] base step of the running graph chunk
+    int64_t* step_counter;   // [2] base step of the running graph chunk, first step of the run
     int32_t* active_flag;    // [1] nonzero while any channel sample still runs
 };
 
@@ -85,6 +87,7 @@ struct BatchGeometry {
     int32_t stochastic;      // 16-bit storage rounds stochastically
     int32_t test_withhold;   // persistent mode test hook: block 0 withholds its barrier arrival
     int32_t any_bouzidi;     // some sample uses the Bouzidi obstacle scheme
+    int32_t two_step;        // UQLB_SCHEME_TWO_STEP: one launch per two steps on two lattices
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -109,6 +112,13 @@ cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const Run
 cudaError_t launch_bouzidi_force(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                                  int dt, int base_parity, cudaStream_t s);
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
+// Two-step scheme: steps dt and dt + 1 of a chunk in one launch (one step for samples that end at
+// dt + 1); commit: after finalize, record which lattice holds each sample's final state.
+cudaError_t launch_step2(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt,
+                         cudaStream_t s);
+cudaError_t launch_commit(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
+// Shared-memory opt-in of the two-step kernel of g's geometry; call before capturing a graph.
+cudaError_t prepare_step2(const BatchGeometry& g);
 cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
 // Persistent mode: one cooperative launch runs `chunk` steps (tile tickets must be zero).
 cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int chunk,
@@ -116,6 +126,7 @@ cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, con
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                             cudaStream_t s);
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
+bool geometry_supported2(int storage, int tile_rows, int npt);  // two-step scheme
 
 // Plain per-sample FP64 path (plain_f64.cu).
 struct PlainSample {

@@ -35,11 +35,14 @@ MODES = {"graph": U.UQLB_MODE_GRAPH, "persistent": U.UQLB_MODE_PERSISTENT,
          "persistent_test_timeout": U.UQLB_MODE_PERSISTENT_TEST_TIMEOUT}
 
 
+SCHEMES = {"auto": U.UQLB_SCHEME_AUTO, "one_step": U.UQLB_SCHEME_ONE_STEP, "two_step": U.UQLB_SCHEME_TWO_STEP}
+
+
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
                 tile_rows: int = 0, nodes_per_thread: int = 0, rounding: str = "auto",
-                start_step: int = 0, mode: str = "graph") -> U.uqlb_run_opts:
+                start_step: int = 0, mode: str = "graph", scheme: str = "auto") -> U.uqlb_run_opts:
     return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows,
-                           nodes_per_thread, ROUNDING[rounding], start_step, MODES[mode], 0)
+                           nodes_per_thread, ROUNDING[rounding], start_step, MODES[mode], SCHEMES[scheme])
 
 
 def _stream() -> int:
@@ -120,11 +123,11 @@ class Ensemble:
     def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
                   fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
                   nodes_per_thread: int = 0, rounding: str = "auto", start_step: int = 0, mode: str = "graph",
-                  out: dict | None = None) -> dict:
+                  scheme: str = "auto", out: dict | None = None) -> dict:
         """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series).  With
         start_step > 0 the run continues the state left by the previous call (same samples)."""
         opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread, rounding,
-                           start_step, mode)
+                           start_step, mode, scheme)
         nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
         ws = self.workspace(nbytes)
         n = len(samples)
@@ -147,8 +150,8 @@ class Ensemble:
                          _stream())
         return res
 
-    def autotune(self, samples, storage: str = "f32", trial_steps: int = 16) -> dict:
-        opts = opts_struct(storage, "f32", 0)
+    def autotune(self, samples, storage: str = "f32", trial_steps: int = 16, scheme: str = "auto") -> dict:
+        opts = opts_struct(storage, "f32", 0, scheme=scheme)
         ws = self.workspace(U.uqlb_batch_workspace_bytes(samples, opts))
         return U.uqlb_autotune(self.ctx, samples, opts, ws.data_ptr(), ws.numel(), trial_steps, _stream())
 

@@ -26,6 +26,7 @@ UQLB_QUAD_GAUSS_LEGENDRE_TENSOR, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 0, 1
 UQLB_METHOD_NONE, UQLB_METHOD_MC, UQLB_METHOD_GPC = 0, 1, 2
 UQLB_CASE_TGV, UQLB_CASE_CHANNEL, UQLB_CASE_TGV_PERTURBED = 0, 1, 2
 UQLB_OBSTACLE_HALFWAY, UQLB_OBSTACLE_BOUZIDI = 0, 1
+UQLB_SCHEME_AUTO, UQLB_SCHEME_ONE_STEP, UQLB_SCHEME_TWO_STEP = 0, 1, 2
 (UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3, UQLB_PARAM_PERT00, UQLB_PARAM_PERT01,
  UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
 UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16 = 0, 1, 2, 3
@@ -60,7 +61,7 @@ class uqlb_case(ctypes.Structure):
 class uqlb_run_opts(ctypes.Structure):
     _fields_ = [("storage", c_int32), ("fields_dtype", c_int32), ("qoi_every", c_int64),
                 ("chunk_steps", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
-                ("rounding", c_int32), ("start_step", c_int64), ("mode", c_int32), ("reserved", c_int32)]
+                ("rounding", c_int32), ("start_step", c_int64), ("mode", c_int32), ("scheme", c_int32)]
 
 
 _P = ctypes.POINTER
@@ -98,6 +99,7 @@ _SIGNATURES = {
     "uqlb_run_plain_f64": [c_void_p, _P(uqlb_sample), c_int64, c_int64, c_void_p, c_size_t, c_void_p, c_int64,
                            c_void_p, c_void_p, c_int64, c_void_p],
     "uqlb_last_loop_time": [c_void_p, _P(c_double), _P(c_int64), _P(c_int64)],
+    "uqlb_last_run_geometry": [c_void_p, _P(c_int32), _P(c_int32), _P(c_int32)],
     "uqlb_w1_workspace_bytes": [ctypes.c_int, _P(c_size_t)],
     "uqlb_w1_speed": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_int64, c_void_p, ctypes.c_int, c_int64,
                       c_int64, c_int64, ctypes.c_int, c_void_p, c_size_t, _P(c_double), _P(c_double), _P(c_int64),
@@ -346,6 +348,13 @@ def uqlb_last_loop_time(ctx) -> tuple[float, int, int]:
     ms, st, la = c_double(), c_int64(), c_int64()
     _check(lib().uqlb_last_loop_time(ctx, ctypes.byref(ms), ctypes.byref(st), ctypes.byref(la)), ctx)
     return ms.value, st.value, la.value
+
+
+def uqlb_last_run_geometry(ctx) -> tuple[int, int, int]:
+    """(scheme, tile_rows, nodes_per_thread) of the last run on this context."""
+    sc, tr, q = c_int32(), c_int32(), c_int32()
+    _check(lib().uqlb_last_run_geometry(ctx, ctypes.byref(sc), ctypes.byref(tr), ctypes.byref(q)), ctx)
+    return sc.value, tr.value, q.value
 
 
 def uqlb_w1_workspace_bytes(bins: int) -> int:

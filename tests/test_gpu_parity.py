@@ -32,11 +32,11 @@ def ens():
     e.close()
 
 
-def _run(ens, specs, storage, qoi_every=0, series=False, tile_rows=0, chunk=0, npt=0):
+def _run(ens, specs, storage, qoi_every=0, series=False, tile_rows=0, chunk=0, npt=0, scheme="auto"):
     res = ens.run_batch([sample_struct(s) for s in specs], storage=storage,
                         fields_dtype="f64" if storage == "f64" else "f32", qoi_every=qoi_every, series=series,
                         tile_rows=tile_rows, nodes_per_thread=npt, chunk_steps=chunk,
-                        fields=len({(s.nx, s.ny) for s in specs}) == 1)
+                        fields=len({(s.nx, s.ny) for s in specs}) == 1, scheme=scheme)
     torch.cuda.synchronize()
     return {k: v.double().cpu().numpy() for k, v in res.items()}
 
@@ -120,8 +120,8 @@ def test_tile_shapes_and_chunks_agree(ens, storage, tr, npt):
     """Tile shape and graph chunk change the launch geometry and the grouping of the QoI partial
     sums, not the per-node arithmetic: results agree to round-off (ragged 50 x 50 lattices)."""
     specs = _tgv_specs(50, 31)
-    a = _run(ens, specs, storage, qoi_every=5, series=True)
-    b = _run(ens, specs, storage, qoi_every=5, series=True, tile_rows=tr, npt=npt, chunk=6)
+    a = _run(ens, specs, storage, qoi_every=5, series=True, scheme="one_step")
+    b = _run(ens, specs, storage, qoi_every=5, series=True, tile_rows=tr, npt=npt, chunk=6, scheme="one_step")
     tol = 1e-14 if storage == "f64" else 1e-6
     assert rel_l2(b["fields"], a["fields"]) < tol
     assert np.allclose(b["series"], a["series"], rtol=tol, atol=0)
@@ -446,7 +446,7 @@ def test_persistent_mode_matches_graph_mode(ens, storage):
     """One cooperative launch per chunk with the ticket work queue gives the same results as one
     launch per step: per-node arithmetic and per-tile reduction order are the same."""
     specs = _tgv_specs(50, 77) + [W.tgv(32, 40, nu=0.05)]
-    a = _run(ens, specs, storage, qoi_every=7, series=True)
+    a = _run(ens, specs, storage, qoi_every=7, series=True, scheme="one_step")
     res = ens.run_batch([sample_struct(s) for s in specs], storage=storage,
                         fields_dtype="f64" if storage == "f64" else "f32", qoi_every=7, series=True,
                         fields=False, mode="persistent", chunk_steps=16)
@@ -491,3 +491,56 @@ def test_w1_leaves_out_and_counts_non_finite_speeds(ens):
     w1, bound, nonfinite = ens.w1_speed(a, 3, b, 2, bins=1 << 16)
     assert nonfinite == (1, 0)
     assert abs(w1 - ouq.wasserstein1([0.1, 0.2], [0.3, 0.0])) <= bound + 1e-15
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_two_step_scheme_equals_one_step_scheme(ens, storage):
+    """The two-step scheme applies the same per-node formulas as the one-step scheme (the compiler
+    may contract multiply-adds differently in the two kernels), so results agree to round-off; K
+    is summed over the nodes in another order.  Uneven step counts (odd totals end on a one-step
+    launch), ragged lattices smaller than a tile, K at every step and at a stride of 7, every
+    two-step geometry."""
+    ftol = 1e-13 if storage == "f64" else 1e-6
+    geoms = [(4, 2), (8, 1), (8, 2)] if storage == "f64" else [(4, 4), (8, 2), (8, 4), (16, 2), (16, 4)]
+    for qe in (1, 7):
+        specs = [W.tgv(40, 61, nu=0.03, amp2=0.0005), W.tgv(40, 30, nu=0.05), W.tgv(40, 1, nu=0.02),
+                 W.tgv(40, 0, nu=0.04)]
+        ref = _run(ens, specs, storage, qoi_every=qe, series=True, scheme="one_step")
+        for tr, npt in geoms:
+            g = _run(ens, specs, storage, qoi_every=qe, series=True, scheme="two_step", tile_rows=tr, npt=npt)
+            assert rel_l2(g["fields"][:, :-1], ref["fields"][:, :-1]) < ftol, (qe, tr, npt)
+            assert np.allclose(g["series"], ref["series"], rtol=10 * ftol, atol=0, equal_nan=True), (qe, tr, npt)
+            assert np.allclose(g["qoi"], ref["qoi"], rtol=10 * ftol, atol=1e-12), (qe, tr, npt)
+    small = [W.tgv(5, 9, nu=0.03, amp2=0.0004), W.tgv(5, 12, nu=0.05)]
+    a = _run(ens, small, storage, scheme="one_step")
+    b = _run(ens, small, storage, scheme="two_step")
+    assert rel_l2(b["fields"][:, :-1], a["fields"][:, :-1]) < ftol
+
+
+@pytest.mark.parametrize("split", [37, 50])
+def test_two_step_resume_continues_the_run_exactly(ens, split):
+    specs = _tgv_specs(40, 100) + [W.tgv(40, 71, nu=0.04)]
+    whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="two_step")
+    first = [sample_struct(s) for s in specs]
+    for s in first:
+        s.steps = min(split, s.steps)
+    ens.run_batch(first, storage="f32", fields=False, scheme="two_step")
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=True, start_step=split,
+                        scheme="two_step")
+    torch.cuda.synchronize()
+    assert np.array_equal(res["fields"].double().cpu().numpy()[:, :-1], whole["fields"][:, :-1])  # same kernels
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_two_step_16_bit_storage_against_the_oracle(ens, storage):
+    """16-bit storage on the two-step scheme keeps the intermediate step in FP32 shared memory, so
+    it rounds half as often; fields stay within the one-step scheme's budget of the oracle."""
+    specs = _tgv_specs(64, 300)
+    ref = olbm.run([oracle_case(s) for s in specs])
+    g = _run(ens, specs, storage, scheme="two_step")
+    one = _run(ens, specs, storage, scheme="one_step")
+    for i, r in enumerate(ref):
+        e2 = rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1])
+        e1 = rel_l2(one["fields"][i, :-1], oracle_row(r)[:-1])
+        assert e2 < FIELD_TOL[storage], (storage, e2)
+        assert e2 < 1.5 * e1 + 1e-6, (storage, e2, e1)

@@ -148,11 +148,18 @@ def test_argument_errors_return_status_codes():
 
 
 def test_workspace_bytes_cover_the_arena():
+    """One lattice for the one-step scheme, two for the two-step scheme (the default for periodic
+    FP32 and FP16 batches)."""
     s = [sample_struct(W.tgv(256, 10)) for _ in range(3)]
     for storage, eb in ((U.UQLB_F64, 8), (U.UQLB_F32, 4), (U.UQLB_F16, 2), (U.UQLB_BF16, 2)):
-        b = U.uqlb_batch_workspace_bytes(s, U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0))
         arena = 3 * 9 * 256 * 256 * eb
-        assert arena <= b < arena + 2 ** 20
+        lattices = 2 if storage in (U.UQLB_F32, U.UQLB_F16) else 1
+        b = U.uqlb_batch_workspace_bytes(s, U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0))
+        assert lattices * arena <= b < lattices * arena + 2 ** 20
+        one = U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP)
+        assert arena <= U.uqlb_batch_workspace_bytes(s, one) < arena + 2 ** 20
+        two = U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP)
+        assert 2 * arena <= U.uqlb_batch_workspace_bytes(s, two) < 2 * arena + 2 ** 20
     # rows are padded to 128 bytes: 100 FP32 columns take a 128-column pitch
     b = U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(100, 10))], U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
     assert b >= 9 * 128 * 100 * 4
@@ -268,6 +275,25 @@ def test_cylinder_method_comparison_samples_are_nested_and_in_the_inflow_range()
         U.uqlb_destroy(ctx)
 
 
+def test_scheme_selection_and_its_limits():
+    tgv = [sample_struct(W.tgv(64, 10))]
+    chan = [sample_struct(W.channel(5, steps=10, steady_tol=0.0))]
+    two = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, U.UQLB_SCHEME_TWO_STEP)
+    for smp, opts in ((chan, two),
+                      (tgv, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, U.UQLB_MODE_PERSISTENT,
+                                            U.UQLB_SCHEME_TWO_STEP)),
+                      (tgv, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 2, 1, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP)),
+                      (tgv, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, 9))):
+        with pytest.raises(U.UqlbError) as e:
+            U.uqlb_batch_workspace_bytes(smp, opts)
+        assert e.value.status == U.UQLB_ERR_ARG
+    # auto: channel batches and persistent mode stay one-step (one lattice)
+    auto_chan = U.uqlb_batch_workspace_bytes(chan, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))
+    one_chan = U.uqlb_batch_workspace_bytes(
+        chan, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP))
+    assert auto_chan == one_chan
+
+
 def test_bouzidi_samples_are_checked():
     """The obstacle scheme is validated, and Bouzidi batches are refused outside graph mode (the
     force kernel runs between step launches)."""
@@ -298,9 +324,14 @@ def test_untuned_workspace_covers_every_geometry_for_every_entry_point():
         ens_b = U.uqlb_ensemble_workspace_bytes(ctx, case, auto)
         assert ens_b == U.uqlb_batch_workspace_bytes(smp, auto)
         assert U.uqlb_uq_workspace_bytes(ctx, case, auto) > ens_b
+        for tr, npt in ((4, 4), (8, 2), (8, 4), (16, 2), (16, 4)):  # two-step geometries (auto scheme)
+            fixed = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, tr, npt, 0, 0, 0, 0)
+            assert U.uqlb_batch_workspace_bytes(smp, fixed) <= ens_b
+        one = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP)
+        one_b = U.uqlb_batch_workspace_bytes(smp, one)
         for tr in (2, 4, 8):
             for npt in (1, 2, 4):
-                fixed = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, tr, npt, 0, 0, 0, 0)
-                assert U.uqlb_batch_workspace_bytes(smp, fixed) <= ens_b
+                fixed = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, tr, npt, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP)
+                assert U.uqlb_batch_workspace_bytes(smp, fixed) <= one_b
     finally:
         U.uqlb_destroy(ctx)

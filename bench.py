@@ -33,7 +33,7 @@ BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
 STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in place)", "step_kernel_f32_tgv256.md",
                     "aa-npt-nbr-pair"),
                 2: ("step2_kernel (two-step: tile + halo collided into shared memory, streamed and collided "
-                    "again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v1")}
+                    "again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v2-packed")}
 
 
 def _peaks():

@@ -149,6 +149,90 @@ __device__ __forceinline__ void bgk(C g[9], C omega, C drho, C jx, C jy, C ux, C
     }
 }
 
+// ---- Two nodes at once in packed FP32 (sm_100+ f32x2 arithmetic) ---------------------------
+// A 64-bit register holds one value of node a (low half) and of node b (high half); each packed
+// add / sub / mul / fma rounds both halves as the scalar instruction does.
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& lo, float& hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 splat(float c) { return pk(c, c); }
+
+// moments() and bgk() of two nodes a and b in packed arithmetic (the same formulas; the operation
+// order is fixed here, where the compiler may contract the scalar code differently, so results
+// agree with the scalar path to round-off).  usq (when non-null) receives u.u of each node.
+__device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], float omega, float* usq_a,
+                                             float* usq_b) {
+    f2 g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = pk(ga[i], gb[i]);
+    const f2 drho =
+        add2(add2(add2(add2(g[0], g[1]), add2(g[2], g[3])), add2(add2(g[4], g[5]), add2(g[6], g[7]))), g[8]);
+    const f2 jx = add2(add2(sub2(g[1], g[3]), sub2(g[5], g[6])), sub2(g[8], g[7]));
+    const f2 jy = add2(add2(sub2(g[2], g[4]), sub2(g[5], g[7])), sub2(g[6], g[8]));
+    float da, db;
+    upk(drho, da, db);
+    const f2 d = pk(-da / (1.0f + da), -db / (1.0f + db));  // 1/rho - 1 per node
+    const f2 ux = fma2(jx, d, jx), uy = fma2(jy, d, jy);
+    if (usq_a != nullptr) {
+        float qa, qb;
+        upk(fma2(uy, uy, mul2(ux, ux)), qa, qb);
+        *usq_a = qa;
+        *usq_b = qb;
+    }
+    const f2 om = splat(omega);
+    const f2 ju15 = mul2(splat(1.5f), fma2(jy, uy, mul2(jx, ux)));
+    g[0] = fma2(om, sub2(mul2(splat(wgt<float>(0)), sub2(drho, ju15)), g[0]), g[0]);
+#pragma unroll
+    for (int i : {1, 2, 5, 6}) {
+        const int o = opp(i);
+        f2 cj, cu;
+        if (i == 1) {
+            cj = jx;
+            cu = ux;
+        } else if (i == 2) {
+            cj = jy;
+            cu = uy;
+        } else if (i == 5) {
+            cj = add2(jx, jy);
+            cu = add2(ux, uy);
+        } else {
+            cj = sub2(jy, jx);
+            cu = sub2(uy, ux);
+        }
+        const f2 A = mul2(splat(wgt<float>(i)), sub2(fma2(splat(4.5f), mul2(cj, cu), drho), ju15));
+        const f2 gi = fma2(splat(lin<float>(i)), cj, A);
+        const f2 go = fma2(splat(-lin<float>(i)), cj, A);
+        g[i] = fma2(om, sub2(gi, g[i]), g[i]);
+        g[o] = fma2(om, sub2(go, g[o]), g[o]);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) upk(g[i], ga[i], gb[i]);
+}
+
 // Obstacle bitmask lookup: bit (x & 31) of word y * words + (x >> 5).
 __device__ __forceinline__ bool mask_solid(const uint32_t* m, int words, int x, int y) {
     return (__ldg(m + (int64_t)y * words + (x >> 5)) >> (x & 31)) & 1u;

@@ -716,8 +716,44 @@ __device__ __forceinline__ bool on_final_second(const KParams& p, int j, int T) 
     return ((p.sel[j] ^ launches_of(T, (int)p.step_counter[1])) & 1) != 0;
 }
 
+// Tuning of the two-step kernel (measured on the 625 x 256^2 FP32 ensemble): nodes per load
+// batch of the halo phase, resident blocks per SM requested for 8-row tiles (register budget
+// 65536 / (256 x blocks); 4-row tiles get twice as many), and packed FP32 arithmetic.
+#ifndef UQLB_STEP2_BATCH
+#define UQLB_STEP2_BATCH 2
+#endif
+#ifndef UQLB_STEP2_BLOCKS8
+#define UQLB_STEP2_BLOCKS8 4
+#endif
+#ifndef UQLB_STEP2_PACKED
+#define UQLB_STEP2_PACKED 1
+#endif
+
+// BGK collision of one node in place; adds u.u to acc when want.
+template <typename C>
+__device__ __forceinline__ void collide_one(C (&g)[9], C omega, bool want, double& acc) {
+    C drho, jx, jy, ux, uy;
+    moments(g, drho, jx, jy, ux, uy);
+    if (want) acc += (double)(ux * ux + uy * uy);
+    bgk(g, omega, drho, jx, jy, ux, uy);
+}
+
+// Shared-memory tile [9][eh][ew]: store one node's populations / gather the populations that
+// stream into node (ey, ex) (population i comes from (ey - c_iy, ex - c_ix)).
+template <typename C>
+__device__ __forceinline__ void tile_store(C* sm, int eh, int ew, int ey, int ex, const C (&g)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) sm[(i * eh + ey) * ew + ex] = g[i];
+}
+template <typename C>
+__device__ __forceinline__ void tile_gather(const C* sm, int eh, int ew, int ey, int ex, C (&g)[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = sm[(i * eh + ey - cy(i)) * ew + ex - cx(i)];
+}
+
 template <typename S, int TR, int NPT>
-__global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 6 : (TR == 8 ? 3 : 1)) step2_kernel(KParams p) {
+__global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS8 : (TR == 8 ? UQLB_STEP2_BLOCKS8 : 1))
+    step2_kernel(KParams p) {
     using C = typename Storage<S>::C;
     constexpr int NT = kTileCols * TR, TW = kTileCols * NPT, EW = TW + 2, EH = TR + 2;
     __shared__ TileShared<NT> sh;
@@ -795,7 +831,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 6 : (TR == 8 ? 3 : 1)
             // phase A: the tile and its halo at step t, post-collision values into shared memory.
             // The (TW + 2) x (TR + 2) nodes are dealt out row-major over all threads, MB at a
             // time (all their loads issued before any arithmetic).
-            constexpr int EXT = EW * EH, MB = 3;
+            constexpr int EXT = EW * EH, MB = sizeof(C) == 4 ? UQLB_STEP2_BATCH : 3;
             const int tid = lane + kTileCols * ty;
 #pragma unroll 1
             for (int e0 = 0; e0 < EXT; e0 += NT * MB) {
@@ -817,34 +853,78 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 6 : (TR == 8 ? 3 : 1)
                         for (int i = 0; i < 9; ++i) g[m][i] = Storage<S>::load(q + i * plane);
                     }
                 }
+                if constexpr (UQLB_STEP2_PACKED && sizeof(C) == 4 && MB % 2 == 0) {
+                    // two nodes per packed collision where both are present
 #pragma unroll
-                for (int m = 0; m < MB; ++m) {
-                    if (!ok[m]) continue;
-                    C drho, jx, jy, ux, uy;
-                    moments(g[m], drho, jx, jy, ux, uy);
-                    if (want_a && ex[m] >= 1 && ex[m] <= wa && ey[m] >= 1 && ey[m] <= ha)
-                        red[0] += (double)(ux * ux + uy * uy);
-                    bgk(g[m], omega, drho, jx, jy, ux, uy);
+                    for (int pr = 0; pr < MB / 2; ++pr) {
+                        const int m0 = 2 * pr, m1 = 2 * pr + 1;
+                        const bool in0 = ex[m0] >= 1 && ex[m0] <= wa && ey[m0] >= 1 && ey[m0] <= ha;
+                        const bool in1 = ex[m1] >= 1 && ex[m1] <= wa && ey[m1] >= 1 && ey[m1] <= ha;
+                        if (ok[m0] && ok[m1]) {
+                            float qa = 0.0f, qb = 0.0f;
+                            collide_pair(g[m0], g[m1], omega, want_a ? &qa : nullptr, want_a ? &qb : nullptr);
+                            if (want_a && in0) red[0] += (double)qa;
+                            if (want_a && in1) red[0] += (double)qb;
+                            tile_store(sm, EH, EW, ey[m0], ex[m0], g[m0]);
+                            tile_store(sm, EH, EW, ey[m1], ex[m1], g[m1]);
+                        } else {
+                            if (ok[m0]) {
+                                collide_one(g[m0], omega, want_a && in0, red[0]);
+                                tile_store(sm, EH, EW, ey[m0], ex[m0], g[m0]);
+                            }
+                            if (ok[m1]) {
+                                collide_one(g[m1], omega, want_a && in1, red[0]);
+                                tile_store(sm, EH, EW, ey[m1], ex[m1], g[m1]);
+                            }
+                        }
+                    }
+                } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) sm[(i * EH + ey[m]) * EW + ex[m]] = g[m][i];
+                    for (int m = 0; m < MB; ++m) {
+                        if (!ok[m]) continue;
+                        const bool in = ex[m] >= 1 && ex[m] <= wa && ey[m] >= 1 && ey[m] <= ha;
+                        collide_one(g[m], omega, want_a && in, red[0]);
+                        tile_store(sm, EH, EW, ey[m], ex[m], g[m]);
+                    }
                 }
             }
             __syncthreads();
             // phase B: stream from shared memory, collide at step t + 1, push into the other lattice
             const int y = y0 + ty, ey = ty + 1;
             if (ty < ha) {
+                if constexpr (UQLB_STEP2_PACKED && sizeof(C) == 4 && NPT % 2 == 0) {
 #pragma unroll
-                for (int k = 0; k < NPT; ++k) {
-                    const int ex = lane + kTileCols * k + 1;
-                    if (ex > wa) continue;
-                    C g[9];
+                    for (int pr = 0; pr < NPT / 2; ++pr) {
+                        const int ea = lane + kTileCols * (2 * pr) + 1, eb = ea + kTileCols;
+                        if (eb <= wa) {
+                            C ga[9], gb[9];
+                            tile_gather(sm, EH, EW, ey, ea, ga);
+                            tile_gather(sm, EH, EW, ey, eb, gb);
+                            float qa = 0.0f, qb = 0.0f;
+                            collide_pair(ga, gb, omega, want_b ? &qa : nullptr, want_b ? &qb : nullptr);
+                            if (want_b) {
+                                red[1] += (double)qa;
+                                red[1] += (double)qb;
+                            }
+                            push(x0 + ea - 1, y, t + 1, ga);
+                            push(x0 + eb - 1, y, t + 1, gb);
+                        } else if (ea <= wa) {
+                            C ga[9];
+                            tile_gather(sm, EH, EW, ey, ea, ga);
+                            collide_one(ga, omega, want_b, red[1]);
+                            push(x0 + ea - 1, y, t + 1, ga);
+                        }
+                    }
+                } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i] = sm[(i * EH + ey - cy(i)) * EW + ex - cx(i)];
-                    C drho, jx, jy, ux, uy;
-                    moments(g, drho, jx, jy, ux, uy);
-                    if (want_b) red[1] += (double)(ux * ux + uy * uy);
-                    bgk(g, omega, drho, jx, jy, ux, uy);
-                    push(x0 + ex - 1, y, t + 1, g);
+                    for (int k = 0; k < NPT; ++k) {
+                        const int ex = lane + kTileCols * k + 1;
+                        if (ex > wa) continue;
+                        C g[9];
+                        tile_gather(sm, EH, EW, ey, ex, g);
+                        collide_one(g, omega, want_b, red[1]);
+                        push(x0 + ex - 1, y, t + 1, g);
+                    }
                 }
             }
         }

@@ -363,13 +363,14 @@ def test_smolyak_and_qmc_ensembles_match_oracle(ens):
 def test_stochastic_rounding_is_reproducible_and_unbiased(ens):
     """Stochastic 16-bit rounding is seeded by (sample, node, step): two runs agree bit for bit.
     On a fine lattice over many steps (where nearest rounding stagnates) it stays closer to the
-    oracle than nearest-even rounding."""
+    oracle than nearest-even rounding, with a rounding at every step (one-step scheme; the
+    two-step scheme rounds every other step)."""
     specs = [W.tgv(128, 600, nu=0.03, u0=0.01)]
     ref = olbm.run([oracle_case(s) for s in specs])[0]
     for st in ("f16", "bf16"):
-        a = ens.run_batch([sample_struct(s) for s in specs], storage=st, rounding="stochastic")
-        b = ens.run_batch([sample_struct(s) for s in specs], storage=st, rounding="stochastic")
-        n = ens.run_batch([sample_struct(s) for s in specs], storage=st, rounding="nearest")
+        def run(r):
+            return ens.run_batch([sample_struct(s) for s in specs], storage=st, rounding=r, scheme="one_step")
+        a, b, n = run("stochastic"), run("stochastic"), run("nearest")
         torch.cuda.synchronize()
         fa, fb, fn = (x["fields"][0].double().cpu().numpy() for x in (a, b, n))
         assert np.array_equal(fa, fb), st
@@ -495,12 +496,14 @@ def test_w1_leaves_out_and_counts_non_finite_speeds(ens):
 
 @pytest.mark.parametrize("storage", ["f32", "f64"])
 def test_two_step_scheme_equals_one_step_scheme(ens, storage):
-    """The two-step scheme applies the same per-node formulas as the one-step scheme (the compiler
-    may contract multiply-adds differently in the two kernels), so results agree to round-off; K
-    is summed over the nodes in another order.  Uneven step counts (odd totals end on a one-step
-    launch), ragged lattices smaller than a tile, K at every step and at a stride of 7, every
-    two-step geometry."""
+    """The two-step scheme applies the same per-node formulas as the one-step scheme (in FP32 it
+    collides pairs of nodes with packed instructions in a fixed operation order), so results
+    agree to round-off; K is summed over the nodes in another order.  The total momentum of the
+    Taylor-Green field is zero, so its round-off (~1e-7 on a mass of 1600 in FP32) is compared in
+    absolute terms.  Uneven step counts (odd totals end on a one-step launch), ragged lattices
+    smaller than a tile, K at every step and at a stride of 7, every two-step geometry."""
     ftol = 1e-13 if storage == "f64" else 1e-6
+    qatol = 1e-12 if storage == "f64" else 1e-6
     geoms = [(4, 2), (8, 1), (8, 2)] if storage == "f64" else [(4, 4), (8, 2), (8, 4), (16, 2), (16, 4)]
     for qe in (1, 7):
         specs = [W.tgv(40, 61, nu=0.03, amp2=0.0005), W.tgv(40, 30, nu=0.05), W.tgv(40, 1, nu=0.02),
@@ -510,7 +513,7 @@ def test_two_step_scheme_equals_one_step_scheme(ens, storage):
             g = _run(ens, specs, storage, qoi_every=qe, series=True, scheme="two_step", tile_rows=tr, npt=npt)
             assert rel_l2(g["fields"][:, :-1], ref["fields"][:, :-1]) < ftol, (qe, tr, npt)
             assert np.allclose(g["series"], ref["series"], rtol=10 * ftol, atol=0, equal_nan=True), (qe, tr, npt)
-            assert np.allclose(g["qoi"], ref["qoi"], rtol=10 * ftol, atol=1e-12), (qe, tr, npt)
+            assert np.allclose(g["qoi"], ref["qoi"], rtol=10 * ftol, atol=qatol), (qe, tr, npt)
     small = [W.tgv(5, 9, nu=0.03, amp2=0.0004), W.tgv(5, 12, nu=0.05)]
     a = _run(ens, small, storage, scheme="one_step")
     b = _run(ens, small, storage, scheme="two_step")
@@ -518,7 +521,10 @@ def test_two_step_scheme_equals_one_step_scheme(ens, storage):
 
 
 @pytest.mark.parametrize("split", [37, 50])
-def test_two_step_resume_continues_the_run_exactly(ens, split):
+def test_two_step_resume_continues_the_run(ens, split):
+    """A two-step run stopped after `split` steps and resumed equals the uninterrupted run: bit
+    for bit at an even split, to FP32 round-off at an odd one (the step before the split then
+    runs on the single-step path, whose scalar operation order differs from the packed pairs)."""
     specs = _tgv_specs(40, 100) + [W.tgv(40, 71, nu=0.04)]
     whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="two_step")
     first = [sample_struct(s) for s in specs]
@@ -528,7 +534,11 @@ def test_two_step_resume_continues_the_run_exactly(ens, split):
     res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=True, start_step=split,
                         scheme="two_step")
     torch.cuda.synchronize()
-    assert np.array_equal(res["fields"].double().cpu().numpy()[:, :-1], whole["fields"][:, :-1])  # same kernels
+    got = res["fields"].double().cpu().numpy()[:, :-1]
+    if split % 2 == 0:
+        assert np.array_equal(got, whole["fields"][:, :-1])
+    else:
+        assert rel_l2(got, whole["fields"][:, :-1]) < 1e-6
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])

@@ -20,6 +20,7 @@ _LIB = os.path.join(_OUT_DIR, "liboracle_lbm.so")
 
 TGV, CHANNEL, TGV_PERTURBED = 0, 1, 2
 HALFWAY, BOUZIDI = 0, 1  # obstacle schemes of the channel case
+FACE, INTERPOLATED = 0, 1  # inlet/outlet schemes of the channel case
 
 
 def build(force: bool = False) -> str:
@@ -41,7 +42,7 @@ class _Case(ctypes.Structure):
                 ("cyl_cx", ctypes.c_double), ("cyl_cy", ctypes.c_double),
                 ("cyl_r", ctypes.c_double), ("ramp_steps", ctypes.c_int64),
                 ("qoi_every", ctypes.c_int64), ("steady_tol", ctypes.c_double), ("pert", ctypes.c_double * 4),
-                ("obstacle_bc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("obstacle_bc", ctypes.c_int32), ("inout_bc", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER(ctypes.c_double)
@@ -90,12 +91,13 @@ class Case:
     steady_tol: float = 0.0
     pert: tuple = (0.0, 0.0, 0.0, 0.0)
     obstacle_bc: int = HALFWAY
+    inout_bc: int = FACE
 
     def _c(self) -> _Case:
         return _Case(self.kind, self.nx, self.ny, self.steps, self.nu, self.u0, self.amp2,
                      self.amp3, self.u_ref, self.cyl_cx, self.cyl_cy, self.cyl_r,
                      self.ramp_steps, self.qoi_every, self.steady_tol, (ctypes.c_double * 4)(*self.pert),
-                     self.obstacle_bc, 0)
+                     self.obstacle_bc, self.inout_bc)
 
 
 @dataclass

@@ -40,6 +40,16 @@
  *     rules (f*_k(x - c_k, t) for the fluid node upstream); the force is the momentum
  *     exchanged on the links, F = sum c_k (f*_k(x, t) + f_kbar(x, t+1)), taken after
  *     the stream (for halfway bounce-back this is 2 sum c_k f*_k(x, t)).
+ *   - inlet/outlet scheme, selectable: the moving-wall and anti-bounce-back rules above at
+ *     the end faces, or interpolated conditions on the end columns, the finite-difference
+ *     velocity-gradient scheme that Latt et al. (2008) describe and Sec. 8.1 cites: after the
+ *     stream, every population of a node of column 0 (inlet) or nx - 1 (outlet) is replaced by
+ *     f_i = f_i^eq(rho, u) - 3 w_i rho tau Q_i:S, Q_i = c_i c_i - I/3, S the strain rate from
+ *     finite differences (second-order one-sided across the column, central along it, one-sided
+ *     at its ends); inlet: u = (parabola at the node centre, 0), rho from the known populations
+ *     by mass balance, rho = (f_0 + f_2 + f_4 + 2 (f_3 + f_6 + f_7)) / (1 - u_x); outlet:
+ *     rho = 1, u_x = (f_0 + f_2 + f_4 + 2 (f_1 + f_5 + f_8)) / rho - 1, u_y that of the node
+ *     beside it (zero normal gradient).
  */
 #include <math.h>
 #include <stdint.h>
@@ -74,7 +84,8 @@ typedef struct {
     double steady_tol;   /* channel: stop when |dC_D|/|C_D| < tol between checks (0: never) */
     double pert[4];      /* perturbed TGV: zeta_00, zeta_01, zeta_10, zeta_11 (lattice velocity units) */
     int32_t obstacle_bc; /* channel obstacle: 0 halfway bounce-back, 1 Bouzidi linear interpolation */
-    int32_t reserved;
+    int32_t inout_bc;    /* channel inlet/outlet: 0 moving-wall / anti-bounce-back at the end faces,
+                            1 interpolated (finite-difference) conditions on the end columns */
 } oracle_case;
 
 /* Per-run outputs.  Arrays are row-major [ny][nx]; any pointer may be NULL. */
@@ -124,6 +135,12 @@ static double link_fraction(const oracle_case *c, int x, int y, int i) {
     double cc = px * px + py * py - c->cyl_r * c->cyl_r;
     return (-b - sqrt(b * b - 4.0 * a * cc)) / (2.0 * a);
 }
+
+/* Interpolated inlet (column 0) and outlet (column nx - 1) at the state of time tn, applied to
+ * the post-stream populations f: velocities of the columns next to each boundary from their
+ * moments, the boundary velocity and density as described in the header, the strain rate by
+ * finite differences, then f = f^eq + f^neq on both boundary columns. */
+static void interpolated_inout(const oracle_case *c, double *f, int64_t plane, double tau, int64_t tn);
 
 /* Parabolic inflow profile evaluated at height yy (walls at 0 and H = ny), peak 1.5 x mean. */
 static double inflow_u(const oracle_case *c, double yy, int64_t t) {
@@ -187,6 +204,7 @@ static double kinetic_energy(const oracle_case *c, const double *f, const unsign
 /* Run one sample.  Returns 0 on success, -1 on bad arguments, -2 on allocation failure. */
 int oracle_run(const oracle_case *c, oracle_out *o) {
     if (!c || !o || c->nx < 2 || c->ny < 2 || c->steps < 0 || c->nu <= 0.0) return -1;
+    if (c->kind == ORACLE_CHANNEL && c->inout_bc == 1 && (c->nx < 6 || c->ny < 3)) return -1;
     const int nx = c->nx, ny = c->ny;
     const int64_t plane = (int64_t)nx * ny;
     const double tau = 3.0 * c->nu + 0.5;
@@ -316,6 +334,7 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
                 }
             }
         }
+        if (c->kind == ORACLE_CHANNEL && c->inout_bc == 1) interpolated_inout(c, f, plane, tau, t + 1);
         if (c->kind == ORACLE_CHANNEL) {
             cd = fx * force_norm;
             cl = fy * force_norm;
@@ -370,6 +389,81 @@ int oracle_run(const oracle_case *c, oracle_out *o) {
     free(solid);
     free(uout);
     return 0;
+}
+
+static void interpolated_inout(const oracle_case *c, double *f, int64_t plane, double tau, int64_t tn) {
+    const int nx = c->nx, ny = c->ny;
+    /* velocity (ux, uy) and density of the columns 0, 1, 2 (inlet side) and nx - 3, nx - 2,
+     * nx - 1 (outlet side), indexed [side][k][y], k = distance from the boundary column */
+    double *ux = (double *)malloc(sizeof(double) * 6 * ny);
+    double *uy = (double *)malloc(sizeof(double) * 6 * ny);
+    double *rb = (double *)malloc(sizeof(double) * 2 * ny);
+    if (!ux || !uy || !rb) {
+        free(ux);
+        free(uy);
+        free(rb);
+        return;
+    }
+#define U_AT(a, side, k, y) a[((side) * 3 + (k)) * ny + (y)]
+    for (int side = 0; side < 2; ++side) {
+        for (int k = 1; k < 3; ++k) {
+            const int x = side == 0 ? k : nx - 1 - k;
+            for (int y = 0; y < ny; ++y) {
+                double r, vx, vy;
+                moments(f, plane, (int64_t)y * nx + x, &r, &vx, &vy);
+                U_AT(ux, side, k, y) = vx;
+                U_AT(uy, side, k, y) = vy;
+            }
+        }
+    }
+    for (int y = 0; y < ny; ++y) {
+        const int64_t ni = (int64_t)y * nx, no = (int64_t)y * nx + nx - 1;
+        const double uin = inflow_u(c, y + 0.5, tn);
+        U_AT(ux, 0, 0, y) = uin;
+        U_AT(uy, 0, 0, y) = 0.0;
+        rb[y] = (f[0 * plane + ni] + f[2 * plane + ni] + f[4 * plane + ni] +
+                 2.0 * (f[3 * plane + ni] + f[6 * plane + ni] + f[7 * plane + ni])) /
+                (1.0 - uin);
+        rb[ny + y] = 1.0;
+        U_AT(ux, 1, 0, y) = (f[0 * plane + no] + f[2 * plane + no] + f[4 * plane + no] +
+                             2.0 * (f[1 * plane + no] + f[5 * plane + no] + f[8 * plane + no])) /
+                                rb[ny + y] -
+                            1.0;
+        U_AT(uy, 1, 0, y) = U_AT(uy, 1, 1, y);
+    }
+    for (int side = 0; side < 2; ++side) {
+        const int x = side == 0 ? 0 : nx - 1;
+        const double sgn = side == 0 ? 1.0 : -1.0; /* the column index k grows along +x (inlet) or -x */
+        for (int y = 0; y < ny; ++y) {
+            double dxu, dxv, dyu, dyv;
+            /* d/dx: second-order one-sided from the boundary column inwards */
+            dxu = sgn * (-3.0 * U_AT(ux, side, 0, y) + 4.0 * U_AT(ux, side, 1, y) - U_AT(ux, side, 2, y)) / 2.0;
+            dxv = sgn * (-3.0 * U_AT(uy, side, 0, y) + 4.0 * U_AT(uy, side, 1, y) - U_AT(uy, side, 2, y)) / 2.0;
+            /* d/dy along the boundary column: central, one-sided at its ends */
+            if (y == 0) {
+                dyu = (-3.0 * U_AT(ux, side, 0, 0) + 4.0 * U_AT(ux, side, 0, 1) - U_AT(ux, side, 0, 2)) / 2.0;
+                dyv = (-3.0 * U_AT(uy, side, 0, 0) + 4.0 * U_AT(uy, side, 0, 1) - U_AT(uy, side, 0, 2)) / 2.0;
+            } else if (y == ny - 1) {
+                dyu = (3.0 * U_AT(ux, side, 0, y) - 4.0 * U_AT(ux, side, 0, y - 1) + U_AT(ux, side, 0, y - 2)) / 2.0;
+                dyv = (3.0 * U_AT(uy, side, 0, y) - 4.0 * U_AT(uy, side, 0, y - 1) + U_AT(uy, side, 0, y - 2)) / 2.0;
+            } else {
+                dyu = (U_AT(ux, side, 0, y + 1) - U_AT(ux, side, 0, y - 1)) / 2.0;
+                dyv = (U_AT(uy, side, 0, y + 1) - U_AT(uy, side, 0, y - 1)) / 2.0;
+            }
+            const double sxx = dxu, syy = dyv, sxy = 0.5 * (dyu + dxv);
+            const double rho = rb[side * ny + y], vx = U_AT(ux, side, 0, y), vy = U_AT(uy, side, 0, y);
+            const int64_t n = (int64_t)y * nx + x;
+            for (int i = 0; i < Q; ++i) {
+                const double q = (CX[i] * CX[i] - 1.0 / 3.0) * sxx + (CY[i] * CY[i] - 1.0 / 3.0) * syy +
+                                 2.0 * CX[i] * CY[i] * sxy;
+                f[i * plane + n] = feq(i, rho, vx, vy) - 3.0 * WGT[i] * rho * tau * q;
+            }
+        }
+    }
+#undef U_AT
+    free(ux);
+    free(uy);
+    free(rb);
 }
 
 /* Run a batch of independent samples, one sample per OpenMP thread (sample-level parallelism). */

@@ -92,6 +92,30 @@ def test_channel_poiseuille_profile_second_order():
     assert 1.8 < order < 2.2, (errs, order)
 
 
+def test_interpolated_inlet_outlet_poiseuille():
+    """Interpolated (finite-difference) inlet and pressure outlet on the end columns (Sec. 8.1,
+    Latt et al. 2008): the developed profile is the inlet parabola to second order in H, the
+    column next to the inlet already carries it (the boundary populations hold the right
+    non-equilibrium part: a wrong sign, a missing or halved shear term makes that column and the
+    cross-flow an order of magnitude worse), and the outflow balances the inflow."""
+    mids = []
+    for h, col_tol, v_tol in ((10, 2.5e-3, 1e-4), (20, 5e-4, 2.5e-5)):
+        c = _channel(h, inout_bc=lbm.INTERPOLATED)
+        r = lbm.run([c])[0]
+        y = np.arange(h) + 0.5
+        ua = 4 * 1.5 * c.u0 * y * (h - y) / h ** 2
+        err = lambda x: np.linalg.norm(r.u[:, x] - ua) / np.linalg.norm(ua)  # noqa: E731
+        assert err(0) < 1e-12                      # the inlet column carries the imposed velocity
+        assert err(1) < col_tol, err(1)
+        assert np.abs(r.v).max() < v_tol, np.abs(r.v).max()
+        qin, qout = (r.rho[:, 0] * r.u[:, 0]).sum(), (r.rho[:, -1] * r.u[:, -1]).sum()
+        assert abs(qout / qin - 1) < 5e-3
+        assert np.abs(r.rho[:, -1] - 1).max() < 1e-12   # pressure outlet: rho = 1 on the column
+        mids.append(err(2 * h))
+    order = math.log(mids[0] / mids[1], 2)
+    assert mids[0] < 0.03 and 1.8 < order < 2.2, (mids, order)
+
+
 def test_channel_without_obstacle_has_no_force():
     r = lbm.run([_channel(10)])[0]
     assert r.cd == 0.0 and r.cl == 0.0
@@ -116,12 +140,13 @@ def test_obstacle_mask_is_staircase_circle():
     assert abs(m.sum() - math.pi * 100) < 20
 
 
-@pytest.mark.parametrize("bc", [lbm.HALFWAY, lbm.BOUZIDI])
-def test_symmetric_obstacle_gives_mirror_flow_and_no_lift(bc):
+@pytest.mark.parametrize("bc,inout", [(lbm.HALFWAY, lbm.FACE), (lbm.BOUZIDI, lbm.FACE),
+                                       (lbm.BOUZIDI, lbm.INTERPOLATED)])
+def test_symmetric_obstacle_gives_mirror_flow_and_no_lift(bc, inout):
     """Obstacle centred in the channel: the y -> H - y mirror maps the flow onto itself, so
     v is odd, u and rho are even, and the lift vanishes to round-off."""
     nd = 10
-    c = _cyl(nd, 1500, cy=0.205 / (0.1 / nd), qoi_every=100, obstacle_bc=bc)
+    c = _cyl(nd, 1500, cy=0.205 / (0.1 / nd), qoi_every=100, obstacle_bc=bc, inout_bc=inout)
     r = lbm.run([c])[0]
     assert np.allclose(r.u, r.u[::-1, :], rtol=0, atol=1e-14)
     assert np.allclose(r.v, -r.v[::-1, :], rtol=0, atol=1e-14)
@@ -147,7 +172,13 @@ def test_cylinder_drag_loose_anchor_and_bouzidi_against_the_benchmark():
     cd_ref = 0.5 * sum(st["c_D"])
     cases = [_cyl(10, 40000, qoi_every=100, steady_tol=1e-7, ramp=1000, obstacle_bc=bc)
              for bc in (lbm.HALFWAY, lbm.BOUZIDI)]
-    half, bz = lbm.run(cases)
+    cases.append(_cyl(10, 40000, qoi_every=100, steady_tol=1e-7, ramp=1000, obstacle_bc=lbm.BOUZIDI,
+                      inout_bc=lbm.INTERPOLATED))
+    half, bz, bzi = lbm.run(cases)
+    # the paper's own boundary set (Bouzidi + interpolated inlet/outlet): a loose anchor within 5%
+    # of its deterministic value (the end columns and the outlet's nodal pressure differ in
+    # detail; C_D is within 1e-4 of its steady value at the step cap)
+    assert abs(bzi.cd - cd_paper) / cd_paper < 0.05, bzi.cd
     assert half.steps_run < 40000 and bz.steps_run < 40000    # reached the steady-state criterion
     assert abs(half.cd - cd_paper) / cd_paper < 0.10, half.cd
     assert abs(half.cl) < 0.05 * half.cd                       # small lift from the 0.2 vs 0.205 offset
@@ -186,9 +217,10 @@ def test_bouzidi_keeps_a_fluid_at_rest():
     equal rest populations, so the fluid stays at rest to round-off and the obstacle feels no
     force (each lattice line through the closed obstacle enters it once along c_i and once along
     its opposite, so sum c_i w_i over the links cancels)."""
-    r = lbm.run([_cyl(6, 200, qoi_every=50, ramp=10 ** 12, obstacle_bc=lbm.BOUZIDI)])[0]
-    assert np.abs(r.u).max() < 1e-13 and np.abs(r.v).max() < 1e-13   # round-off over 200 steps
-    assert abs(r.cd) < 1e-10 and abs(r.cl) < 1e-10                     # F ~ 1e-14 times 2/(u0^2 D)
+    for inout in (lbm.FACE, lbm.INTERPOLATED):
+        r = lbm.run([_cyl(6, 200, qoi_every=50, ramp=10 ** 12, obstacle_bc=lbm.BOUZIDI, inout_bc=inout)])[0]
+        assert np.abs(r.u).max() < 1e-13 and np.abs(r.v).max() < 1e-13   # round-off over 200 steps
+        assert abs(r.cd) < 1e-10 and abs(r.cl) < 1e-10                     # F ~ 1e-14 times 2/(u0^2 D)
 
 
 def test_perturbed_tgv_without_perturbation_is_a_tiled_shifted_tgv():

@@ -45,6 +45,7 @@ class SampleSpec:
     steady_checks: int = 1
     pert: tuple = (0.0, 0.0, 0.0, 0.0)
     obstacle_bc: int = 0    # channel obstacle: 0 halfway bounce-back, 1 Bouzidi
+    inout_bc: int = 0       # channel inlet/outlet: 0 at the end faces, 1 interpolated on the end columns
 
 
 @dataclass
@@ -69,19 +70,22 @@ def tgv(n: int, steps: int, nu: float = 0.04, u0: float = U_REF, amp2: float = 0
 
 
 OBSTACLE_BC = {"halfway": 0, "bouzidi": 1}
+INOUT_BC = {"face": 0, "interpolated": 1}
 
 
 def channel(nd: int, u_mean: float = 0.04, steps: int = 200000, steady_tol: float = 1e-8,
-            ramp: bool = True, re: float = 20.0, obstacle: bool = True, bc: str = "halfway") -> SampleSpec:
+            ramp: bool = True, re: float = 20.0, obstacle: bool = True, bc: str = "halfway",
+            inout: str = "face") -> SampleSpec:
     """Channel 2.2 x 0.41 (D = 0.1) resolved with nd nodes per diameter (ny = floor(4.1 nd));
     nu from Re at the nominal lattice velocity 0.04; bc: obstacle scheme, "halfway" bounce-back
-    on the staircase or "bouzidi" interpolated bounce-back."""
+    on the staircase or "bouzidi" interpolated bounce-back; inout: inlet/outlet scheme, "face"
+    (moving-wall inlet, anti-bounce-back outlet) or "interpolated" (on the end columns)."""
     nx, ny = 22 * nd, (41 * nd) // 10
     nu = 0.04 * nd / re
     r = 0.5 * nd if obstacle else 0.0
     return SampleSpec(CHANNEL, nx, ny, steps, nu, u_mean, u_ref=0.0, cyl_cx=2.0 * nd, cyl_cy=2.0 * nd, cyl_r=r,
                       ramp_steps=(2000 * nd) // 20 if ramp else 0, steady_tol=steady_tol,
-                      obstacle_bc=OBSTACLE_BC[bc])
+                      obstacle_bc=OBSTACLE_BC[bc], inout_bc=INOUT_BC[inout])
 
 
 TGV4D_BOUNDS = [(0.02, 0.06), (0.008, 0.012), (-0.1, 0.1), (-0.1, 0.1)]
@@ -109,10 +113,10 @@ def tgv512_mc4d(n: int = 512, steps: int = 2000, n_mc: int = 4096, storage: str 
 
 
 def cylinder_gpc(nd: int = 20, pts: int = 9, order: int = 8, steps: int = 200000, steady_tol: float = 1e-8,
-                 storage: str = "f32", steady_checks: int = 0, bc: str = "halfway") -> Workload:
+                 storage: str = "f32", steady_checks: int = 0, bc: str = "halfway", inout: str = "face") -> Workload:
     """Steady state: the relative change of C_D over 100 steps stays below steady_tol.  FP32 resolves
     C_D to ~1e-7, so below that tolerance it must hold at 5 consecutive checks (FP64: one)."""
-    base = channel(nd, steps=steps, steady_tol=steady_tol, bc=bc)
+    base = channel(nd, steps=steps, steady_tol=steady_tol, bc=bc, inout=inout)
     base.steady_checks = steady_checks or (1 if storage == "f64" else 5)
     return Workload("cylinder_gpc", base, [(0.9 * 0.04, 1.1 * 0.04)], ["u0"], "gpc", pts_per_dim=pts,
                     order=order, storage=storage, qoi_every=100)
@@ -120,12 +124,12 @@ def cylinder_gpc(nd: int = 20, pts: int = 9, order: int = 8, steps: int = 200000
 
 def cylinder_uq(nd: int = 20, method: str = "gpc", n: int = 11, order: int = 5, spread: float = 0.2,
                 steps: int = 200000, steady_tol: float = 1e-8, storage: str = "f64", seed: int = 123456,
-                bc: str = "halfway") -> Workload:
+                bc: str = "halfway", inout: str = "face") -> Workload:
     """The Sec. 8.1 method comparison: mean inflow U ~ U((1 - spread) U_nom, (1 + spread) U_nom) at
     fixed viscosity (the paper's +-20 %), U_nom = 0.04.  method "gpc": n Gauss-Legendre points and
     a degree-`order` expansion (the paper's reference uses 11 points, order 5); "mc" / "qmc": n
     Philox draws / Halton points.  Steady state as in cylinder_gpc."""
-    base = channel(nd, steps=steps, steady_tol=steady_tol, bc=bc)
+    base = channel(nd, steps=steps, steady_tol=steady_tol, bc=bc, inout=inout)
     base.steady_checks = 1 if storage == "f64" else 5
     bounds = [((1.0 - spread) * 0.04, (1.0 + spread) * 0.04)]
     if method == "gpc":

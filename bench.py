@@ -222,7 +222,7 @@ def _oracle_cases(specs):
     return [olbm.Case(s.kind, s.nx, s.ny, s.steps, s.nu, s.u0, amp2=s.amp2, amp3=s.amp3, u_ref=s.u_ref,
                       cyl_cx=s.cyl_cx, cyl_cy=s.cyl_cy, cyl_r=s.cyl_r, ramp_steps=s.ramp_steps,
                       qoi_every=100 if s.steady_tol > 0 else 0, steady_tol=s.steady_tol,
-                      pert=tuple(s.pert), obstacle_bc=s.obstacle_bc) for s in specs]
+                      pert=tuple(s.pert), obstacle_bc=s.obstacle_bc, inout_bc=s.inout_bc) for s in specs]
 
 
 def _rel(a, b):
@@ -270,13 +270,14 @@ def bench_workload(args):
             w = W.tgv512_mc4d(n=args.n or 512, steps=args.time_steps_full or 2000, n_mc=args.n_mc or 4096,
                               storage=args.storage)
         else:
-            w = W.cylinder_gpc(nd=args.nd, storage=args.storage, bc=args.obstacle_bc)
+            w = W.cylinder_gpc(nd=args.nd, storage=args.storage, bc=args.obstacle_bc, inout=args.inout_bc)
         if args.workload == "tgv64_gpc":
             w.storage = args.storage if args.storage != "f32" else "f64"
         ens.setup(w)
         smp = ens.ensemble_samples(w)
         specs = [W.SampleSpec(s.kind, s.nx, s.ny, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref, s.cyl_cx, s.cyl_cy,
-                              s.cyl_r, s.ramp_steps, s.steady_tol, s.steady_checks, tuple(s.pert), s.obstacle_bc)
+                              s.cyl_r, s.ramp_steps, s.steady_tol, s.steady_checks, tuple(s.pert), s.obstacle_bc,
+                              s.inout_bc)
                  for s in smp]
         sub = list(range(min(len(specs), args.oracle_samples)))
         th, box = _oracle_async(_oracle_cases([specs[i] for i in sub]))
@@ -309,7 +310,7 @@ def bench_workload(args):
                            "fields": rr["fields"][: min(len(smp), args.oracle_samples)].double().cpu().numpy()}
         # plain per-sample FP64 comparator on a subset, scaled by the sample count (halfway
         # bounce-back only)
-        if args.plain_samples > 0 and not any(s.obstacle_bc for s in smp):
+        if args.plain_samples > 0 and not any(s.obstacle_bc or s.inout_bc for s in smp):
             psub = [smp[i] for i in range(min(len(smp), args.plain_samples))]
             pms, _ = timed(lambda: ens.run_plain_f64(psub, fields=True), 1)
             line["plain_f64_time_to_stats_s"] = pms / 1e3 * len(smp) / len(psub)
@@ -414,13 +415,14 @@ def bench_workload(args):
         n_max = max(n_list)
         st = args.storage if args.storage != "f32" else "f64"
         mk = lambda method, n: W.cylinder_uq(args.nd, method=method, n=n, spread=args.inflow_spread, storage=st,  # noqa: E731
-                                             bc=args.obstacle_bc)
+                                             bc=args.obstacle_bc, inout=args.inout_bc)
         w_sc, w_mc, w_qmc = mk("gpc", 11), mk("mc", n_max), mk("qmc", n_max)
         groups = {}
         for name, w in (("sc", w_sc), ("mc", w_mc), ("qmc", w_qmc)):
             ens.setup(w)
             groups[name] = ens.ensemble_samples(w)
-        det = W.channel(args.nd, steps=w_sc.base.steps, steady_tol=w_sc.base.steady_tol, bc=args.obstacle_bc)
+        det = W.channel(args.nd, steps=w_sc.base.steps, steady_tol=w_sc.base.steady_tol, bc=args.obstacle_bc,
+                        inout=args.inout_bc)
         det.steady_checks = w_sc.base.steady_checks
         smp = groups["sc"] + groups["mc"] + groups["qmc"] + [sample_struct(det)]
         ms, r = timed(lambda: ens.run_batch(smp, storage=st, fields=False, qoi_every=100), 1)
@@ -444,7 +446,7 @@ def bench_workload(args):
         status = q[:, U.UQLB_QOI_STATUS].cpu().numpy()
         upd = int(steps.sum()) * smp[0].nx * smp[0].ny
         line.update({"samples": len(smp), "lattice": [smp[0].nx, smp[0].ny], "storage": st,
-                     "obstacle_bc": args.obstacle_bc,
+                     "obstacle_bc": args.obstacle_bc, "inout_bc": args.inout_bc,
                      "inflow": [w_sc.bounds[0][0], w_sc.bounds[0][1]], "seconds": ms / 1e3,
                      "value": upd / (ms / 1e3) / 1e6, "steps_run": [int(steps.min()), int(steps.max())],
                      "samples_not_converged": int((steps >= w_sc.base.steps).sum()),
@@ -680,6 +682,8 @@ def main():
     ap.add_argument("--nd", type=int, default=20, help="cylinder: nodes per diameter")
     ap.add_argument("--obstacle-bc", default="halfway", choices=["halfway", "bouzidi"],
                     help="cylinder workloads: obstacle scheme")
+    ap.add_argument("--inout-bc", default="face", choices=["face", "interpolated"],
+                    help="cylinder workloads: inlet/outlet scheme")
     ap.add_argument("--compare-n", default="10,20,40,80,100", help="cylinder_uq_compare: MC/QMC sample counts")
     ap.add_argument("--inflow-spread", type=float, default=0.2, help="cylinder_uq_compare: relative inflow spread")
     ap.add_argument("--n", type=int, default=0, help="tgv512_mc4d: lattice size override")

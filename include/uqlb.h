@@ -58,6 +58,9 @@ enum { UQLB_METHOD_NONE = 0, UQLB_METHOD_MC = 1, UQLB_METHOD_GPC = 2 };
 enum { UQLB_CASE_TGV = 0, UQLB_CASE_CHANNEL = 1, UQLB_CASE_TGV_PERTURBED = 2 };
 /* Obstacle boundary scheme of the CHANNEL case (Sec. 8.1: the cylinder surface). */
 enum { UQLB_OBSTACLE_HALFWAY = 0, UQLB_OBSTACLE_BOUZIDI = 1 };
+/* Inlet/outlet scheme of the CHANNEL case (Sec. 8.1: interpolated velocity inlet and pressure
+ * outlet). */
+enum { UQLB_INOUT_FACE = 0, UQLB_INOUT_INTERPOLATED = 1 };
 /* Parameters an uncertain input dimension may drive (uqlb_case.param_of_dim). */
 enum {
     UQLB_PARAM_NU = 0,
@@ -118,6 +121,16 @@ typedef struct {
  *     population streamed into x along c_i) or f*_i(x) / (2q) + (1 - 1/(2q)) f*_ibar(x) for
  *     q >= 1/2; the force is sum c_i (f*_i(x, t) + f_ibar(x, t+1)) after the stream.  Bouzidi
  *     samples run in UQLB_MODE_GRAPH only.
+ *     inout_bc selects the inlet/outlet scheme: UQLB_INOUT_FACE (the moving-wall inlet and
+ *     pressure outlet above, at the end faces) or UQLB_INOUT_INTERPOLATED, the finite-difference
+ *     velocity-gradient conditions of Latt et al. (2008) cited by Sec. 8.1, on the end columns:
+ *     after each stream every population of a node of column 0 (inlet) or nx - 1 (outlet) is
+ *     replaced by f_i^eq(rho, u) - 3 w_i rho tau Q_i:S (Q_i = c_i c_i - I/3, S the strain rate
+ *     by finite differences: second-order one-sided across the column, central along it,
+ *     one-sided at its ends); inlet u = (parabola at the node centre, 0) with rho from the known
+ *     populations by mass balance; outlet rho = 1, u_x from the known populations, u_y that of
+ *     the node beside it.  Needs nx >= 6, ny >= 3 and the obstacle clear of the three end
+ *     columns; UQLB_MODE_GRAPH only.
  *   TGV_PERTURBED (Sec. 8.3): periodic [0, 2 pi)^2 on nx x ny nodes x = 2 pi i / nx,
  *     u = -U cos 2x sin 2y, v = U sin 2x cos 2y, U = u0 + 1/4 sum_ij pert[2i+j] k_i(4x) k_j(4y)
  *     (k_0 = sin, k_1 = cos), p = -U^2/4 (cos 4x + cos 4y), rho = 1 + 3p; K(t) normalised by u_ref.
@@ -136,7 +149,7 @@ typedef struct {
     double steady_tol;   /* CHANNEL steady-state tolerance (0: run to the cap) */
     double pert[4];      /* TGV_PERTURBED amplitudes zeta_00, zeta_01, zeta_10, zeta_11 (lattice units) */
     int32_t obstacle_bc; /* CHANNEL obstacle scheme, UQLB_OBSTACLE_HALFWAY or UQLB_OBSTACLE_BOUZIDI */
-    int32_t reserved;    /* must be 0 */
+    int32_t inout_bc;    /* CHANNEL inlet/outlet scheme, UQLB_INOUT_FACE or UQLB_INOUT_INTERPOLATED */
 } uqlb_sample;
 
 /* Template of an ensemble: a uqlb_sample whose parameters are overridden per sample by

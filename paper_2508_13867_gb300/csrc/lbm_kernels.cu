@@ -39,6 +39,7 @@ struct KParams {
     const uint32_t* masks;
     float* side;
     double* side_d;
+    double* bcpop;         // interpolated inlet/outlet: next state of the end columns
     double* partials;
     int32_t* counters;
     int32_t* done;
@@ -364,9 +365,16 @@ template <typename S, bool ODD>
 __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp, const S* base,
                                           const uint32_t* mask, int x, int y, int t, bool chan,
                                           const Nbr& nb, const InitDev* bz, uint32_t links,
-                                          typename Storage<S>::C (&g)[9]) {
+                                          typename Storage<S>::C (&g)[9], bool end_columns = true) {
     using C = typename Storage<S>::C;
     const int plane = (int)sp.plane;
+    if (chan && end_columns && sp.inout && t > 0 && (x == 0 || x == sp.nx - 1)) {
+        // interpolated inlet/outlet: the end columns' state was formed after the last step
+        const double* b = p.bcpop + (int64_t)(sp.bc_off + (x == 0 ? 0 : sp.ny) + y) * 9;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = (C)b[i];
+        return;
+    }
     if (!ODD) {
         const int own = nb.row[1] + x;
 #pragma unroll
@@ -1004,6 +1012,11 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                 }
                 const uint32_t links = bz != nullptr ? obstacle_links(sp, *bz, mask, x, y) : 0u;
                 if (links && T > 0) bouzidi_complete(*bz, x, y, links, g);
+                if (chan && sp.inout && T > 0 && (x == 0 || x == sp.nx - 1)) {
+                    const double* b = p.bcpop + (int64_t)(sp.bc_off + (x == 0 ? 0 : sp.ny) + y) * 9;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = (C)b[i];
+                }
                 C drho, cjx, cjy, cux, cuy;
                 moments(g, drho, cjx, cjy, cux, cuy);
                 ux = (double)cux;
@@ -1145,6 +1158,105 @@ __global__ void __launch_bounds__(256) bouzidi_force_kernel(KParams p) {
     }
 }
 
+// Interpolated inlet/outlet (Sec. 8.1; the finite-difference velocity-gradient conditions of
+// Latt et al. 2008): for every sample that uses it and has a state at time s = step counter +
+// dt + 1, the populations of its end columns at s, f_i = f_i^eq(rho, u) - 3 w_i rho tau Q_i:S,
+// written (shifted, g = f - w) to its boundary buffer, which the step of s and the finalize read
+// for those nodes.  Inlet (column 0): u = (parabola at the node centre, 0), rho from the known
+// populations; outlet (column nx - 1): rho = 1, u_x from the known populations, u_y that of
+// column nx - 2.  The strain rate comes from finite differences: second-order one-sided across
+// the column (columns 0, 1, 2 or nx - 1, nx - 2, nx - 3), central along it, one-sided at its
+// ends.  The post-stream state of a node is gathered as the step of s would gather it.
+template <typename S>
+__global__ void __launch_bounds__(256) inout_kernel(KParams p) {
+    using C = typename Storage<S>::C;
+    const int s = (int)(*p.step_counter) + p.dt + 1;
+    for (int j = blockIdx.x; j < p.nsamples; j += gridDim.x) {
+        const SampleDev& sp = p.samples[j];
+        if (sp.kind != UQLB_CASE_CHANNEL || !sp.inout || s > p.steps_run[j]) continue;
+        const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
+        const S* base = static_cast<const S*>(p.arena) + sp.f_off;
+        const int nx = sp.nx, ny = sp.ny;
+        // post-stream shifted populations of node (x, yy) at time s
+        auto state = [&](int x, int yy, C (&g)[9]) {
+            Nbr nb;
+            nb.row[1] = yy * sp.pitch;
+            if (s & 1)
+                node_load<S, true>(p, sp, base, mask, x, yy, s, true, nb, nullptr, 0u, g, false);
+            else
+                node_load<S, false>(p, sp, base, mask, x, yy, s, true, nb, nullptr, 0u, g, false);
+        };
+        auto velocity = [&](int x, int yy, C& ux, C& uy) {
+            C g[9], drho, jx, jy;
+            state(x, yy, g);
+            moments(g, drho, jx, jy, ux, uy);
+        };
+        // outlet node: u_x from its known populations (rho = 1; the known weights sum to 1, so
+        // in shifted form u_x = g_0 + g_2 + g_4 + 2 (g_1 + g_5 + g_8)), u_y from column nx - 2
+        auto outlet_u = [&](int yy, C& ux, C& uy) {
+            C g[9], vx;
+            state(nx - 1, yy, g);
+            ux = g[0] + g[2] + g[4] + C(2) * (g[1] + g[5] + g[8]);
+            velocity(nx - 2, yy, vx, uy);
+        };
+        const C tau = C(1) / (C)sp.omega;
+        for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+            for (int side = 0; side < 2; ++side) {
+                C u0x, u0y, u1x, u1y, u2x, u2y, drho;
+                C ax[3], ay[3];  // boundary-column velocity at the three rows of the y stencil
+                const int ys = y == 0 ? 0 : (y == ny - 1 ? ny - 3 : y - 1);
+                if (side == 0) {
+                    C g[9];
+                    state(0, y, g);
+                    u0x = inflow<C>(sp, C(y) + C(0.5), s);
+                    u0y = C(0);
+                    // rho = (1 + G) / (1 - u_x), G the shifted known sum: drho = (G + u_x) / (1 - u_x)
+                    const C G = g[0] + g[2] + g[4] + C(2) * (g[3] + g[6] + g[7]);
+                    drho = (G + u0x) / (C(1) - u0x);
+                    velocity(1, y, u1x, u1y);
+                    velocity(2, y, u2x, u2y);
+                    for (int k = 0; k < 3; ++k) {
+                        ax[k] = inflow<C>(sp, C(ys + k) + C(0.5), s);
+                        ay[k] = C(0);
+                    }
+                } else {
+                    outlet_u(y, u0x, u0y);
+                    drho = C(0);
+                    velocity(nx - 2, y, u1x, u1y);
+                    velocity(nx - 3, y, u2x, u2y);
+                    for (int k = 0; k < 3; ++k) outlet_u(ys + k, ax[k], ay[k]);
+                }
+                const C sgn = side == 0 ? C(1) : C(-1);
+                const C dxu = sgn * (C(-3) * u0x + C(4) * u1x - u2x) / C(2);
+                const C dxv = sgn * (C(-3) * u0y + C(4) * u1y - u2y) / C(2);
+                C dyu, dyv;
+                if (y == 0) {
+                    dyu = (C(-3) * ax[0] + C(4) * ax[1] - ax[2]) / C(2);
+                    dyv = (C(-3) * ay[0] + C(4) * ay[1] - ay[2]) / C(2);
+                } else if (y == ny - 1) {
+                    dyu = (C(3) * ax[2] - C(4) * ax[1] + ax[0]) / C(2);
+                    dyv = (C(3) * ay[2] - C(4) * ay[1] + ay[0]) / C(2);
+                } else {
+                    dyu = (ax[2] - ax[0]) / C(2);
+                    dyv = (ay[2] - ay[0]) / C(2);
+                }
+                const C sxx = dxu, syy = dyv, sxy = C(0.5) * (dyu + dxv);
+                const C rho = C(1) + drho, usq = u0x * u0x + u0y * u0y;
+                double* b = p.bcpop + (int64_t)(sp.bc_off + side * ny + y) * 9;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const C w = wgt<C>(i);
+                    const C cu = C(cx(i)) * u0x + C(cy(i)) * u0y;
+                    const C q = C(cx(i) * cx(i) - 1.0 / 3.0) * sxx + C(cy(i) * cy(i) - 1.0 / 3.0) * syy +
+                                C(2 * cx(i) * cy(i)) * sxy;
+                    const C geq = w * drho + w * rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq);
+                    b[i] = (double)(geq - C(3) * w * rho * tau * q);
+                }
+            }
+        }
+    }
+}
+
 __global__ void advance_kernel(int64_t* counter, int chunk) { *counter += chunk; }
 
 // Resuming a run: samples that have not stopped take their new step totals.
@@ -1166,6 +1278,7 @@ KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutp
     p.masks = b.masks;
     p.side = b.side;
     p.side_d = b.side_d;
+    p.bcpop = b.bcpop;
     p.partials = b.partials;
     p.counters = b.counters;
     p.done = b.done;
@@ -1366,6 +1479,18 @@ cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStrea
         case UQLB_F32: init_kernel<float><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
         case UQLB_F16: init_kernel<__half><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
         default: init_kernel<__nv_bfloat16><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inout(const BatchBuffers& b, const BatchGeometry& g, int dt, cudaStream_t s) {
+    KParams p = make_params(b, g, nullptr, dt);
+    const int grid = (int)(g.nsamples < 4096 ? g.nsamples : 4096);
+    switch (g.storage) {
+        case UQLB_F64: inout_kernel<double><<<grid, 256, 0, s>>>(p); break;
+        case UQLB_F32: inout_kernel<float><<<grid, 256, 0, s>>>(p); break;
+        case UQLB_F16: inout_kernel<__half><<<grid, 256, 0, s>>>(p); break;
+        default: inout_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p); break;
     }
     return cudaGetLastError();
 }

@@ -300,7 +300,7 @@ struct BatchPlan {
     std::vector<InitDev> init;
     std::vector<int32_t> steps_sorted;
     std::vector<uint32_t> masks;
-    size_t off_arena = 0, off_arena2 = 0, off_sel = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
+    size_t off_arena = 0, off_arena2 = 0, off_sel = 0, off_bcpop = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
            off_partials = 0, off_counters = 0, off_done = 0, off_steps_run = 0, off_cd_prev = 0,
            off_step_counter = 0, off_flag = 0, off_streak = 0, off_sync = 0, total = 0;
     BatchGeometry geom{};
@@ -325,6 +325,15 @@ int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
         snprintf(buf, sizeof buf, "sample %lld: non-finite obstacle geometry", (long long)idx);
     } else if (s.obstacle_bc != UQLB_OBSTACLE_HALFWAY && s.obstacle_bc != UQLB_OBSTACLE_BOUZIDI) {
         snprintf(buf, sizeof buf, "sample %lld: unknown obstacle scheme %d", (long long)idx, s.obstacle_bc);
+    } else if (s.inout_bc != UQLB_INOUT_FACE && s.inout_bc != UQLB_INOUT_INTERPOLATED) {
+        snprintf(buf, sizeof buf, "sample %lld: unknown inlet/outlet scheme %d", (long long)idx, s.inout_bc);
+    } else if (s.kind == UQLB_CASE_CHANNEL && s.inout_bc == UQLB_INOUT_INTERPOLATED &&
+               (s.nx < 6 || s.ny < 3 ||
+                (s.cyl_r > 0.0 && (s.cyl_cx - s.cyl_r < 4.0 || s.cyl_cx + s.cyl_r > s.nx - 4.0)))) {
+        snprintf(buf, sizeof buf,
+                 "sample %lld: the interpolated inlet/outlet needs nx >= 6, ny >= 3 and the obstacle clear of "
+                 "the three end columns",
+                 (long long)idx);
     } else {
         return 0;
     }
@@ -401,7 +410,8 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.steps_sorted.assign(n, 0);
     P.masks.clear();
     int64_t f_off = 0, tiles = 0, side = 0;
-    int max_steps = 0, any_channel = 0, any_bouzidi = 0, tiles0 = -1;
+    int max_steps = 0, any_channel = 0, any_bouzidi = 0, any_inout = 0, tiles0 = -1;
+    int64_t bcnodes = 0;
     bool uniform_tiles = true;
     P.n_steady = 0;
     P.uniform_size = true;
@@ -446,6 +456,12 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
             if (d.steady_tol > 0.0) ++P.n_steady;
             d.side_off = (int32_t)side;
             side += s.ny;
+            if (s.inout_bc == UQLB_INOUT_INTERPOLATED) {
+                d.inout = 1;
+                d.bc_off = (int32_t)bcnodes;
+                bcnodes += 2 * (int64_t)s.ny;
+                any_inout = 1;
+            }
             if (s.cyl_r > 0.0) {
                 d.force_norm = (s.u0 != 0.0) ? 2.0 / (s.u0 * s.u0 * 2.0 * s.cyl_r) : 0.0;
                 if (s.obstacle_bc == UQLB_OBSTACLE_BOUZIDI) {
@@ -497,6 +513,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.off_steps = take(sizeof(int32_t) * n);
     P.off_masks = take(sizeof(uint32_t) * P.masks.size());
     P.off_side = take((size_t)side * 2 * 8);
+    P.off_bcpop = take((size_t)bcnodes * 9 * sizeof(double));
     P.off_partials = take((size_t)tiles * 7 * sizeof(double));
     P.off_counters = take(sizeof(int32_t) * n);
     P.off_done = take(sizeof(int32_t) * n);
@@ -526,8 +543,9 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     g.two_step = two ? 1 : 0;
     g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
     g.any_bouzidi = any_bouzidi;
-    if (any_bouzidi && mode != UQLB_MODE_GRAPH) {
-        why = "samples with the Bouzidi obstacle scheme run in UQLB_MODE_GRAPH only";
+    g.any_inout = any_inout;
+    if ((any_bouzidi || any_inout) && mode != UQLB_MODE_GRAPH) {
+        why = "samples with the Bouzidi obstacle or the interpolated inlet/outlet run in UQLB_MODE_GRAPH only";
         return UQLB_ERR_ARG;
     }
     return 0;
@@ -545,6 +563,7 @@ BatchBuffers carve(const BatchPlan& P, void* ws) {
     B.masks = reinterpret_cast<uint32_t*>(b + P.off_masks);
     B.side = reinterpret_cast<float*>(b + P.off_side);
     B.side_d = reinterpret_cast<double*>(b + P.off_side);
+    B.bcpop = reinterpret_cast<double*>(b + P.off_bcpop);
     B.partials = reinterpret_cast<double*>(b + P.off_partials);
     B.counters = reinterpret_cast<int32_t*>(b + P.off_counters);
     B.done = reinterpret_cast<int32_t*>(b + P.off_done);
@@ -594,6 +613,7 @@ int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, co
     } else {
         for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) {
             lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
+            if (lerr == cudaSuccess && G.any_inout) lerr = launch_inout(B, G, dt, ctx->capture_stream);
             if (lerr == cudaSuccess && G.any_bouzidi && O.qoi_every > 0)
                 lerr = launch_bouzidi_force(B, G, O, dt, parity, ctx->capture_stream);
         }
@@ -1226,7 +1246,8 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         for (int64_t q = 0; q < nchunks; ++q) {
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
             ctx->run_launches += P.geom.two_step ? chunk / 2 + 1
-                                                 : chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0);
+                                                 : chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0) +
+                                                       (P.geom.any_inout ? chunk : 0);
             if (steady && (q % 8) == 7 && q + 1 < nchunks) {
                 int32_t ndone = 0;
                 if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
@@ -1329,9 +1350,11 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
         return set_err(ctx, UQLB_ERR_OOM, "run_plain_f64: workspace of %zu bytes, need %zu", workspace_bytes, need);
     if (qoi_every < 0) return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: qoi_every must be >= 0");
     for (int64_t s = 0; s < n; ++s)
-        if (samples[s].kind == UQLB_CASE_CHANNEL && samples[s].cyl_r > 0.0 &&
-            samples[s].obstacle_bc != UQLB_OBSTACLE_HALFWAY)
-            return set_err(ctx, UQLB_ERR_ARG, "run_plain_f64: the plain path has halfway bounce-back only");
+        if (samples[s].kind == UQLB_CASE_CHANNEL &&
+            ((samples[s].cyl_r > 0.0 && samples[s].obstacle_bc != UQLB_OBSTACLE_HALFWAY) ||
+             samples[s].inout_bc != UQLB_INOUT_FACE))
+            return set_err(ctx, UQLB_ERR_ARG,
+                           "run_plain_f64: the plain path has halfway bounce-back and the face inlet/outlet only");
     int64_t maxn = 0;
     for (int64_t s = 0; s < n; ++s) maxn = std::max<int64_t>(maxn, (int64_t)samples[s].nx * samples[s].ny);
     if (fields_dev) {

@@ -36,6 +36,8 @@ struct alignas(16) SampleDev {
     double steady_tol;  // channel: steady-state tolerance (0: none)
     int32_t steady_checks;  // channel: consecutive passing checks needed (>= 1)
     int32_t bouzidi;        // channel: 1 = Bouzidi interpolated bounce-back on the obstacle
+    int32_t inout;          // channel: 1 = interpolated inlet/outlet on the end columns
+    int32_t bc_off;         // channel with inout: first node of its boundary buffer (2 x ny nodes)
 };
 static_assert(sizeof(SampleDev) == 128, "SampleDev must stay 128 bytes");
 
@@ -61,6 +63,7 @@ struct BatchBuffers {
     uint32_t* masks;         // obstacle bitmasks
     float* side;             // outlet velocities (float pairs)
     double* side_d;          // outlet velocities (double pairs, FP64 storage)
+    double* bcpop;           // interpolated inlet/outlet: next state of the end columns, 9 per node
     double* partials;        // [tiles x 3] per-tile QoI partial sums
     int32_t* counters;       // [S] tiles finished in the current reduction
     int32_t* done;           // [S] 1 once a sample has stopped (steady state)
@@ -88,6 +91,7 @@ struct BatchGeometry {
     int32_t test_withhold;   // persistent mode test hook: block 0 withholds its barrier arrival
     int32_t any_bouzidi;     // some sample uses the Bouzidi obstacle scheme
     int32_t two_step;        // UQLB_SCHEME_TWO_STEP: one launch per two steps on two lattices
+    int32_t any_inout;       // some sample uses the interpolated inlet/outlet
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -112,6 +116,9 @@ cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const Run
 cudaError_t launch_bouzidi_force(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                                  int dt, int base_parity, cudaStream_t s);
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s);
+// Interpolated inlet/outlet: the end-column state at step dt + 1 of a chunk into the boundary
+// buffer; launched after step dt of the chunk, before step dt + 1.
+cudaError_t launch_inout(const BatchBuffers& b, const BatchGeometry& g, int dt, cudaStream_t s);
 // Two-step scheme: steps dt and dt + 1 of a chunk in one launch (one step for samples that end at
 // dt + 1); commit: after finalize, record which lattice holds each sample's final state.
 cudaError_t launch_step2(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt,

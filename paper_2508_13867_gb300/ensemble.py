@@ -19,7 +19,7 @@ PARAMS = {"nu": U.UQLB_PARAM_NU, "u0": U.UQLB_PARAM_U0, "zeta2": U.UQLB_PARAM_ZE
 def sample_struct(s: SampleSpec) -> U.uqlb_sample:
     return U.uqlb_sample(s.kind, s.nx, s.ny, s.steady_checks, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref,
                          s.cyl_cx, s.cyl_cy, s.cyl_r, s.ramp_steps, s.steady_tol, (U.c_double * 4)(*s.pert),
-                         s.obstacle_bc, 0)
+                         s.obstacle_bc, s.inout_bc)
 
 
 def case_struct(w: Workload) -> U.uqlb_case:

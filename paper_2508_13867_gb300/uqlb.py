@@ -26,6 +26,7 @@ UQLB_QUAD_GAUSS_LEGENDRE_TENSOR, UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK = 0, 1
 UQLB_METHOD_NONE, UQLB_METHOD_MC, UQLB_METHOD_GPC = 0, 1, 2
 UQLB_CASE_TGV, UQLB_CASE_CHANNEL, UQLB_CASE_TGV_PERTURBED = 0, 1, 2
 UQLB_OBSTACLE_HALFWAY, UQLB_OBSTACLE_BOUZIDI = 0, 1
+UQLB_INOUT_FACE, UQLB_INOUT_INTERPOLATED = 0, 1
 UQLB_SCHEME_AUTO, UQLB_SCHEME_ONE_STEP, UQLB_SCHEME_TWO_STEP = 0, 1, 2
 (UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3, UQLB_PARAM_PERT00, UQLB_PARAM_PERT01,
  UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
@@ -51,7 +52,7 @@ class uqlb_sample(ctypes.Structure):
                 ("steps", c_int64), ("nu", c_double), ("u0", c_double), ("amp2", c_double),
                 ("amp3", c_double), ("u_ref", c_double), ("cyl_cx", c_double), ("cyl_cy", c_double),
                 ("cyl_r", c_double), ("ramp_steps", c_int64), ("steady_tol", c_double), ("pert", c_double * 4),
-                ("obstacle_bc", c_int32), ("reserved", c_int32)]
+                ("obstacle_bc", c_int32), ("inout_bc", c_int32)]
 
 
 class uqlb_case(ctypes.Structure):

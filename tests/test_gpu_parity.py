@@ -191,6 +191,47 @@ def test_bouzidi_steady_state_stops_with_the_oracle_in_a_mixed_batch(ens):
     assert abs(q[2, U.UQLB_QOI_K] - ref[2].k_final) < 1e-12 * ref[2].k_final
 
 
+@pytest.mark.parametrize("steps", [600, 601])
+def test_interpolated_inlet_outlet_matches_oracle(ens, steps):
+    """Interpolated inlet/outlet on the end columns (Sec. 8.1): the boundary kernel between steps
+    forms the end columns' state, the step and the finalize read it.  Fields, forces and the C_D
+    series against the oracle at both parities of the last step, with the halfway and with the
+    Bouzidi obstacle, FP64 and FP32."""
+    specs = [_cyl(5, steps, u_mean=0.036, inout="interpolated"),
+             _cyl(5, steps, u_mean=0.044, bc="bouzidi", inout="interpolated")]
+    ref = olbm.run([oracle_case(s, qoi_every=50) for s in specs])
+    ns = steps // 50
+    for storage, tol_f in (("f64", 1e-11), ("f32", 1e-4)):
+        g = _run(ens, specs, storage, qoi_every=50, series=True)
+        for i, r in enumerate(ref):
+            assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL[storage], (storage, i)
+            assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < tol_f * abs(r.cd), (storage, i)
+            assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < 10 * TOL[storage] * r.mass, (storage, i)
+            assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=tol_f, atol=0), (storage, i)
+
+
+def test_interpolated_inlet_outlet_steady_stop_and_resume(ens):
+    """A sample with the interpolated inlet/outlet stops at the oracle's steady-state step, and a
+    run resumed at an odd step continues it bit for bit (the boundary buffer carries the end
+    columns' state across the two calls)."""
+    specs = [_cyl(4, 20000, u_mean=0.04, steady_tol=1e-6, inout="interpolated")]
+    g = _run(ens, specs, "f64", qoi_every=100, series=True)
+    r = olbm.run([oracle_case(specs[0], qoi_every=100)])[0]
+    assert r.steps_run < 20000
+    assert g["qoi"][0, U.UQLB_QOI_STEPS] == r.steps_run
+    assert abs(g["qoi"][0, U.UQLB_QOI_CD] - r.cd) < 1e-10 * abs(r.cd)
+    specs = [_cyl(4, 90, u_mean=0.04, inout="interpolated"), _cyl(4, 90, u_mean=0.04, bc="bouzidi", inout="interpolated")]
+    whole = _run(ens, specs, "f64", qoi_every=10, series=True)
+    first = [sample_struct(s) for s in specs]
+    for s in first:
+        s.steps = 37
+    ens.run_batch(first, storage="f64", fields_dtype="f64", fields=False)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f64", fields_dtype="f64", fields=True,
+                        start_step=37)
+    torch.cuda.synchronize()
+    assert np.array_equal(res["fields"].cpu().numpy(), whole["fields"])
+
+
 def test_channel_without_obstacle_and_f32(ens):
     specs = [W.channel(6, steps=600, obstacle=False, steady_tol=0.0, re=5.0), _cyl(6, 600)]
     for storage in ("f64", "f32"):

@@ -294,6 +294,25 @@ def test_scheme_selection_and_its_limits():
     assert auto_chan == one_chan
 
 
+def test_interpolated_inlet_outlet_samples_are_checked():
+    graph = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 10, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, 0)
+    ok = sample_struct(W.channel(5, steps=10, steady_tol=0.0, inout="interpolated"))
+    assert U.uqlb_batch_workspace_bytes([ok], graph) > U.uqlb_batch_workspace_bytes(
+        [sample_struct(W.channel(5, steps=10, steady_tol=0.0))], graph)  # the boundary buffer
+    bad = []
+    s = sample_struct(W.channel(5, steps=10, steady_tol=0.0, inout="interpolated"))
+    s.cyl_cx = 3.0                      # obstacle reaching into the three inlet columns
+    bad.append((s, graph))
+    s = sample_struct(W.channel(5, steps=10, steady_tol=0.0, inout="interpolated"))
+    s.inout_bc = 5                      # unknown scheme
+    bad.append((s, graph))
+    bad.append((ok, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 10, 0, 0, 0, 0, 0, U.UQLB_MODE_PERSISTENT, 0)))
+    for smp, opts in bad:
+        with pytest.raises(U.UqlbError) as e:
+            U.uqlb_batch_workspace_bytes([smp], opts)
+        assert e.value.status == U.UQLB_ERR_ARG
+
+
 def test_bouzidi_samples_are_checked():
     """The obstacle scheme is validated, and Bouzidi batches are refused outside graph mode (the
     force kernel runs between step launches)."""

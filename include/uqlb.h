@@ -195,9 +195,9 @@ typedef struct {
  *     writes the tile: ~40 B per FP32 node update.  Periodic (TGV, TGV_PERTURBED) batches in
  *     UQLB_MODE_GRAPH; the workspace holds the second lattice.  FP32/FP64 results agree with the
  *     one-step scheme's to round-off (same formulas per node); 16-bit storage rounds half as often.
- *   UQLB_SCHEME_AUTO: TWO_STEP for periodic FP32 and FP16 batches in graph mode, where it
- *     measured faster on GB300 (625 x 256^2 ensemble: 0.393 against 0.485 ms per FP32 step, 0.479
- *     against 0.501 ms per FP16 step); ONE_STEP otherwise (BF16 ran 0.460 against 0.454 ms).
+ *   UQLB_SCHEME_AUTO: TWO_STEP for periodic FP32, FP16 and BF16 batches in graph mode, where it
+ *     measured faster on GB300 (625 x 256^2 ensemble, GLUPS two-step / one-step: FP32 115 / 84,
+ *     FP16 95 / 82, BF16 103 / 90); ONE_STEP otherwise (FP64 is bound by the FP64 rate).
  * A resumed run (start_step > 0) must use the scheme of the run it continues. */
 enum { UQLB_SCHEME_AUTO = 0, UQLB_SCHEME_ONE_STEP = 1, UQLB_SCHEME_TWO_STEP = 2 };
 

@@ -367,10 +367,9 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         why = "unknown time-stepping scheme";
         return UQLB_ERR_ARG;
     }
-    // auto: the two-step scheme where it measured faster (periodic FP32 and FP16 batches)
+    // auto: the two-step scheme where it measured faster (periodic FP32, FP16 and BF16 batches)
     const bool two = scheme == UQLB_SCHEME_TWO_STEP ||
-                     (scheme == UQLB_SCHEME_AUTO && !mixed && mode == UQLB_MODE_GRAPH &&
-                      (storage == UQLB_F32 || storage == UQLB_F16));
+                     (scheme == UQLB_SCHEME_AUTO && !mixed && mode == UQLB_MODE_GRAPH && storage != UQLB_F64);
     if (two && (mixed || mode != UQLB_MODE_GRAPH)) {
         why = "the two-step scheme runs periodic (TGV) batches in UQLB_MODE_GRAPH only";
         return UQLB_ERR_ARG;

@@ -149,11 +149,11 @@ def test_argument_errors_return_status_codes():
 
 def test_workspace_bytes_cover_the_arena():
     """One lattice for the one-step scheme, two for the two-step scheme (the default for periodic
-    FP32 and FP16 batches)."""
+    FP32, FP16 and BF16 batches)."""
     s = [sample_struct(W.tgv(256, 10)) for _ in range(3)]
     for storage, eb in ((U.UQLB_F64, 8), (U.UQLB_F32, 4), (U.UQLB_F16, 2), (U.UQLB_BF16, 2)):
         arena = 3 * 9 * 256 * 256 * eb
-        lattices = 2 if storage in (U.UQLB_F32, U.UQLB_F16) else 1
+        lattices = 2 if storage != U.UQLB_F64 else 1
         b = U.uqlb_batch_workspace_bytes(s, U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0))
         assert lattices * arena <= b < lattices * arena + 2 ** 20
         one = U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP)

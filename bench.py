@@ -32,8 +32,11 @@ BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
 # profile was taken on (a mismatch reports traffic as null)
 STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in place)", "step_kernel_f32_tgv256.md",
                     "aa-npt-nbr-pair"),
-                2: ("step2_kernel (two-step: tile + halo collided into shared memory, streamed and collided "
-                    "again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v2-packed")}
+                3: ("step2_kernel (two-step tiles: tile + halo collided into shared memory, streamed and "
+                    "collided again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v2-packed"),
+                4: ("strip2_kernel (two-step row strips: each row collided into a shared-memory ring, streamed "
+                    "and collided again, pushed to the other lattice)", "strip2_kernel_f32_tgv256.md",
+                    "two-step-strips-v1")}
 
 
 def _peaks():
@@ -188,7 +191,7 @@ def bench_kernel_only(args):
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
-    per_launch = 2 if scheme == U.UQLB_SCHEME_TWO_STEP else 1
+    per_launch = 1 if scheme == U.UQLB_SCHEME_ONE_STEP else 2
     nodes = sum(s.nx * s.ny for s in smp)
     gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st / per_launch, 1) / 1e3) / 1e9
     print(json.dumps({"kernel_only": True, "mode": args.mode, "scheme": scheme, "tile": [g_rows, g_npt],
@@ -551,7 +554,7 @@ def bench_gpu(args):
     # roofline of the dominant kernel, from its event-timed loop.  One launch reads and writes
     # every population once (72 B per FP32 node); the two-step kernel advances two steps per launch.
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
-    steps_per_launch = 2 if scheme == U.UQLB_SCHEME_TWO_STEP else 1
+    steps_per_launch = 1 if scheme == U.UQLB_SCHEME_ONE_STEP else 2
     kernel_name, prof_name, kernel_version = STEP_KERNELS[scheme]
     nodes = S * w.base.nx * w.base.ny
     per_launch_bytes = BYTES_PER_UPDATE[storage] * nodes
@@ -630,7 +633,8 @@ def bench_gpu(args):
                            "storage": storage, "statistics": "fp64", "gpc_terms": K,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "lattice arena 1.47 GB > L2 129 MB: each launch streams from HBM",
-                           "scheme": "two_step" if scheme == U.UQLB_SCHEME_TWO_STEP else "one_step",
+                           "scheme": {U.UQLB_SCHEME_ONE_STEP: "one_step", U.UQLB_SCHEME_TWO_STEP_TILES: "two_step_tiles",
+                                      U.UQLB_SCHEME_TWO_STEP_STRIPS: "two_step_strips"}[scheme],
                            "tile_geometry": None if tuned is None else
                            {"tile_rows": tuned["tile_rows"], "nodes_per_thread": tuned["nodes_per_thread"],
                             "autotune_ms_per_step": {f"{r}x{q}": round(ms, 4) for r, q, ms in tuned["tried"]}}},
@@ -666,7 +670,8 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
-    ap.add_argument("--scheme", default="auto", choices=["auto", "one_step", "two_step"],
+    ap.add_argument("--scheme", default="auto",
+                    choices=["auto", "one_step", "two_step", "two_step_tiles", "two_step_strips"],
                     help="time-stepping scheme (auto: two-step for periodic FP32/16-bit batches)")
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent"],
                     help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")

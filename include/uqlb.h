@@ -190,16 +190,31 @@ typedef struct {
  * through memory).
  *   UQLB_SCHEME_ONE_STEP: one launch per time step, populations updated in place (AA order),
  *     72 B of HBM traffic per FP32 node update.  Every case kind and mode.
- *   UQLB_SCHEME_TWO_STEP: one launch per two time steps on two lattices; a block loads its tile
- *     with a one-node halo, collides it into shared memory, then streams, collides again and
- *     writes the tile: ~40 B per FP32 node update.  Periodic (TGV, TGV_PERTURBED) batches in
- *     UQLB_MODE_GRAPH; the workspace holds the second lattice.  FP32/FP64 results agree with the
- *     one-step scheme's to round-off (same formulas per node); 16-bit storage rounds half as often.
+ *   UQLB_SCHEME_TWO_STEP: one launch per two time steps on two lattices (36 B of HBM traffic per
+ *     FP32 node update).  Each node is collided at step t into shared memory, streamed from there,
+ *     collided at step t + 1 and pushed to the other lattice.  Periodic (TGV, TGV_PERTURBED)
+ *     batches in UQLB_MODE_GRAPH; the workspace holds the second lattice.  FP32/FP64 results agree
+ *     with the one-step scheme's to round-off (same formulas per node); 16-bit storage rounds half
+ *     as often.  Two kernels:
+ *       TWO_STEP_STRIPS: blocks walk full-width rows, keeping a ring of collided rows in shared
+ *         memory (about 1 % of the nodes collided twice).  Every sample of the batch must have
+ *         the same width nx, a multiple of 64 in 64..2048, with FP32, FP16 or BF16 storage;
+ *         the tile geometry then serves only the initial state and the final fields.
+ *       TWO_STEP_TILES: blocks take tiles of the tile geometry with a one-node halo (any size,
+ *         FP64 too; the halo is collided twice, 27 % more collisions at tile 8 x 128).
+ *     UQLB_SCHEME_TWO_STEP takes strips where the batch allows them, else tiles.
  *   UQLB_SCHEME_AUTO: TWO_STEP for periodic FP32, FP16 and BF16 batches in graph mode, where it
- *     measured faster on GB300 (625 x 256^2 ensemble, GLUPS two-step / one-step: FP32 115 / 84,
- *     FP16 95 / 82, BF16 103 / 90); ONE_STEP otherwise (FP64 is bound by the FP64 rate).
- * A resumed run (start_step > 0) must use the scheme of the run it continues. */
-enum { UQLB_SCHEME_AUTO = 0, UQLB_SCHEME_ONE_STEP = 1, UQLB_SCHEME_TWO_STEP = 2 };
+ *     measured faster on GB300 (625 x 256^2 ensemble, GLUPS two-step tiles / one-step: FP32
+ *     115 / 84, FP16 95 / 82, BF16 103 / 90); ONE_STEP otherwise (FP64 is bound by the FP64 rate).
+ * A resumed run (start_step > 0) must use the scheme of the run it continues (strips and tiles
+ * leave the same lattice layout, so either two-step kernel continues a two-step run). */
+enum {
+    UQLB_SCHEME_AUTO = 0,
+    UQLB_SCHEME_ONE_STEP = 1,
+    UQLB_SCHEME_TWO_STEP = 2,
+    UQLB_SCHEME_TWO_STEP_TILES = 3,
+    UQLB_SCHEME_TWO_STEP_STRIPS = 4
+};
 
 /* Execution of the time loop.
  *   UQLB_MODE_GRAPH: one launch per step, captured as CUDA graphs of chunk_steps launches.
@@ -361,8 +376,8 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
  * Synchronises on the end event.  Any output may be NULL. */
 int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches);
 
-/* Scheme (UQLB_SCHEME_ONE_STEP or UQLB_SCHEME_TWO_STEP) and tile geometry the last
- * uqlb_run_batch / uqlb_run_ensemble on this context used.  Any output may be NULL;
+/* Scheme the last uqlb_run_batch / uqlb_run_ensemble on this context ran (UQLB_SCHEME_ONE_STEP,
+ * UQLB_SCHEME_TWO_STEP_TILES or UQLB_SCHEME_TWO_STEP_STRIPS) and its tile geometry.  Any output may be NULL;
  * UQLB_ERR_STATE before the first run. */
 int uqlb_last_run_geometry(const uqlb_ctx* ctx, int32_t* scheme, int32_t* tile_rows, int32_t* nodes_per_thread);
 

@@ -183,12 +183,9 @@ __device__ __forceinline__ f2 splat(float c) { return pk(c, c); }
 
 // moments() and bgk() of two nodes a and b in packed arithmetic (the same formulas; the operation
 // order is fixed here, where the compiler may contract the scalar code differently, so results
-// agree with the scalar path to round-off).  usq (when non-null) receives u.u of each node.
-__device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], float omega, float* usq_a,
-                                             float* usq_b) {
-    f2 g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = pk(ga[i], gb[i]);
+// agree with the scalar path to round-off).  g[i] holds population i of node a (low half) and of
+// node b (high half); usq (when non-null) receives u.u of both nodes.
+__device__ __forceinline__ void collide_packed(f2 (&g)[9], float omega, f2* usq) {
     const f2 drho =
         add2(add2(add2(add2(g[0], g[1]), add2(g[2], g[3])), add2(add2(g[4], g[5]), add2(g[6], g[7]))), g[8]);
     const f2 jx = add2(add2(sub2(g[1], g[3]), sub2(g[5], g[6])), sub2(g[8], g[7]));
@@ -197,12 +194,7 @@ __device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], flo
     upk(drho, da, db);
     const f2 d = pk(-da / (1.0f + da), -db / (1.0f + db));  // 1/rho - 1 per node
     const f2 ux = fma2(jx, d, jx), uy = fma2(jy, d, jy);
-    if (usq_a != nullptr) {
-        float qa, qb;
-        upk(fma2(uy, uy, mul2(ux, ux)), qa, qb);
-        *usq_a = qa;
-        *usq_b = qb;
-    }
+    if (usq != nullptr) *usq = fma2(uy, uy, mul2(ux, ux));
     const f2 om = splat(omega);
     const f2 ju15 = mul2(splat(1.5f), fma2(jy, uy, mul2(jx, ux)));
     g[0] = fma2(om, sub2(mul2(splat(wgt<float>(0)), sub2(drho, ju15)), g[0]), g[0]);
@@ -229,6 +221,17 @@ __device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], flo
         g[i] = fma2(om, sub2(gi, g[i]), g[i]);
         g[o] = fma2(om, sub2(go, g[o]), g[o]);
     }
+}
+
+// collide_packed() on two nodes held as separate arrays.
+__device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], float omega, float* usq_a,
+                                             float* usq_b) {
+    f2 g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = pk(ga[i], gb[i]);
+    f2 q;
+    collide_packed(g, omega, usq_a != nullptr ? &q : nullptr);
+    if (usq_a != nullptr) upk(q, *usq_a, *usq_b);
 #pragma unroll
     for (int i = 0; i < 9; ++i) upk(g[i], ga[i], gb[i]);
 }

@@ -31,6 +31,7 @@ struct KParams {
     void* arena;
     void* arena2;          // two-step scheme: second lattice
     int32_t* sel;          // two-step scheme: lattice holding each sample's state at the run's start
+    const int32_t* row_base;  // row-strip kernel: first row of each sample in table order, [S + 1]
     const SampleDev* samples;
     const InitDev* init;
     const int32_t* steps_sorted;
@@ -951,6 +952,279 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Two steps per launch by row strips (periodic batches of one width nx, a multiple of 64).
+// ------------------------------------------------------------------------------------------
+// The rows of the running samples, taken sample after sample in table order, are split into
+// gridDim.x ranges of equal length; a block of nx / 2 threads walks its range row by row, thread
+// k owning the node pair (2k, 2k + 1) of every row.  For row y of a sample it collides row y + 1
+// at step t into a ring in shared memory (phase A), waits at one barrier, then gathers row y's
+// populations of step t + 1 from rows y - 1, y and y + 1 of the ring, collides them and pushes
+// them into the other lattice (phase B).  Phase A visits every row once plus two rows before the
+// first row of each (range, sample) piece, against (TR + 2)(TW + 2) / (TR TW) nodes per tile
+// node in step2_kernel, and the loop keeps each thread's columns, so no per-node index
+// arithmetic or wrap-around remains apart from the two edge columns.
+//
+// Ring: population i of a phase-A row is read by the phase-B row y + c_iy, so the group with
+// c_iy = +1 (i = 2, 5, 6) lives two iterations, c_iy = 0 (0, 1, 3) one and c_iy = -1 (4, 7, 8)
+// none; with one barrier per row the next phase-A row may be written while a slower thread is
+// still gathering, which takes one more slot each: 4, 3 and 2 slots of 3 planes of nx floats.
+constexpr int kStripPlanes = 27;
+
+// Slot plane of direction i for the phase-A row with sequence number q (q = row - first + 1).
+__device__ __forceinline__ int strip_plane(int i, int q) {
+    switch (i) {
+        case 2: return (q & 3) * 3 + 0;
+        case 5: return (q & 3) * 3 + 1;
+        case 6: return (q & 3) * 3 + 2;
+        case 0: return 12 + (q % 3) * 3 + 0;
+        case 1: return 12 + (q % 3) * 3 + 1;
+        case 3: return 12 + (q % 3) * 3 + 2;
+        case 4: return 21 + (q & 1) * 3 + 0;
+        case 7: return 21 + (q & 1) * 3 + 1;
+        default: return 21 + (q & 1) * 3 + 2;
+    }
+}
+
+// Two adjacent populations (an even column and the next) as one packed pair.
+template <typename S>
+__device__ __forceinline__ f2 pair_load(const S* ptr);
+template <>
+__device__ __forceinline__ f2 pair_load<float>(const float* ptr) {
+    return *reinterpret_cast<const f2*>(ptr);
+}
+template <>
+__device__ __forceinline__ f2 pair_load<__half>(const __half* ptr) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(ptr));
+    return pk(v.x * 0x1p-12f, v.y * 0x1p-12f);
+}
+template <>
+__device__ __forceinline__ f2 pair_load<__nv_bfloat16>(const __nv_bfloat16* ptr) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(ptr));
+    return pk(v.x, v.y);
+}
+// Round-to-nearest store of a pair (each half rounded as Storage<S>::store does).
+template <typename S>
+__device__ __forceinline__ void pair_store(S* ptr, f2 v);
+template <>
+__device__ __forceinline__ void pair_store<float>(float* ptr, f2 v) {
+    *reinterpret_cast<f2*>(ptr) = v;
+}
+template <>
+__device__ __forceinline__ void pair_store<__half>(__half* ptr, f2 v) {
+    float a, b;
+    upk(v, a, b);
+    *reinterpret_cast<__half2*>(ptr) = __floats2half2_rn(a * 0x1p12f, b * 0x1p12f);
+}
+template <>
+__device__ __forceinline__ void pair_store<__nv_bfloat16>(__nv_bfloat16* ptr, f2 v) {
+    float a, b;
+    upk(v, a, b);
+    *reinterpret_cast<__nv_bfloat162*>(ptr) = __floats2bfloat162_rn(a, b);
+}
+
+// Block-wide deterministic sum of NV doubles for any whole number of warps; result in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_dyn(double (&v)[NV], double* smem) {
+    const int tid = threadIdx.x, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if ((tid & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) smem[(tid >> 5) * NV + k] = v[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += smem[w * NV + k];
+            v[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
+    extern __shared__ __align__(16) unsigned char s3_raw[];
+    float* ring = reinterpret_cast<float*>(s3_raw);  // [kStripPlanes][nx]
+    __shared__ __align__(16) SampleDev s_sp;
+    __shared__ double s_red[32 * 2];
+    __shared__ int s_j, s_rows, s_nact, s_flag;
+    const int tid = threadIdx.x, np = blockDim.x;
+    const int t = (int)p.step_counter[0] + p.dt;
+    const int t0 = (int)p.step_counter[1];
+    if (tid == 0) {
+        const int nact = active_samples(p, t);
+        s_nact = nact;
+        s_rows = p.row_base[nact];
+    }
+    __syncthreads();
+    const int nact = s_nact, rows = s_rows;
+    const int per = (rows + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+    const bool want_a = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
+    const bool want_b0 = p.qoi_every > 0 && p.series != nullptr && ((t + 1) % p.qoi_every) == 0;
+    const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    const int nx = 2 * np;
+    const int x = 2 * tid;                            // node a; node b is x + 1
+    const int xl = x == 0 ? nx - 1 : x - 1;           // column left of a
+    const int xr = x + 2 == nx ? 0 : x + 2;           // column right of b
+    for (int r = r0; r < r1;) {
+        __syncthreads();  // the previous piece's gathers are done before the ring is reused
+        if (tid == 0) {
+            int lo = 0, hi = nact - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.row_base[mid] <= r)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_j = lo;
+        }
+        __syncthreads();
+        const int j = s_j;
+        if (tid < 32) reinterpret_cast<uint32_t*>(&s_sp)[tid] = __ldg(reinterpret_cast<const uint32_t*>(p.samples + j) + tid);
+        __syncthreads();
+        const int rb = p.row_base[j];
+        const int ny = s_sp.ny, pitch = s_sp.pitch, plane = (int)s_sp.plane;
+        const int ya = r - rb, yb = min(ny, r1 - rb);
+        r = rb + yb;
+        const bool two = t + 1 < s_sp.steps;
+        const bool want_b = two && want_b0;
+        const bool second = ((p.sel[j] ^ ((t - t0) >> 1)) & 1) != 0;
+        const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + s_sp.f_off;
+        S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off;
+        const float omega = (float)s_sp.omega;
+        const uint32_t sid = (uint32_t)s_sp.sample_id;
+        double red[2] = {0.0, 0.0};
+        // push of the pair's post-collision populations g (step ts, row y) into dst
+        auto push = [&](int y, int ts, const f2 (&g)[9]) {
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const int row[3] = {ym * pitch, y * pitch, yp * pitch};
+            uint32_t ha = 0u, hb = 0u;
+            if (sr) {
+                const uint32_t base = (uint32_t)ts * 0x85EBCA77u + sid * 0xC2B2AE3Du;
+                ha = mix32((uint32_t)(y * pitch + x) * 0x9E3779B1u + base);
+                hb = mix32((uint32_t)(y * pitch + x + 1) * 0x9E3779B1u + base);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                S* d = dst + (i * plane + row[1 + cy(i)]);
+                float a, b;
+                upk(g[i], a, b);
+                const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? x + 1 : xl);
+                const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xr : x);
+                if (sr) {
+                    const uint32_t m = 0x2545F491u + 0x6A09E668u * (uint32_t)i;
+                    Storage<S>::store_sr(d + ca, a, (ha * m) >> 16);
+                    Storage<S>::store_sr(d + cb, b, (hb * m) >> 16);
+                } else if (cx(i) == 0) {
+                    pair_store<S>(d + x, g[i]);
+                } else {
+                    Storage<S>::store(d + ca, a);
+                    Storage<S>::store(d + cb, b);
+                }
+            }
+        };
+        auto add_usq = [&](double& acc, f2 q) {
+            float a, b;
+            upk(q, a, b);
+            acc += (double)a;
+            acc += (double)b;
+        };
+        if (!two) {
+            // the sample's last step: collide and push row by row
+            for (int y = ya; y < yb; ++y) {
+                const S* s0 = src + (y * pitch + x);
+                f2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane);
+                f2 q;
+                collide_packed(g, omega, want_a ? &q : nullptr);
+                if (want_a) add_usq(red[0], q);
+                push(y, t, g);
+            }
+        } else {
+            // phase A of the row with sequence number q (row ya - 1 + q, periodic)
+            auto phase_a = [&](int q, bool count) {
+                int y = ya - 1 + q;
+                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+                const S* s0 = src + (y * pitch + x);
+                f2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane);
+                f2 qq;
+                const bool w = want_a && count;
+                collide_packed(g, omega, w ? &qq : nullptr);
+                if (w) add_usq(red[0], qq);
+                f2* ring2 = reinterpret_cast<f2*>(ring);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) ring2[strip_plane(i, q) * np + tid] = g[i];
+            };
+            phase_a(0, false);
+            phase_a(1, true);
+            for (int y = ya; y < yb; ++y) {
+                const int q = y - ya + 1;
+                phase_a(q + 1, y + 1 < yb);
+                __syncthreads();
+                // phase B: gather row y at step t + 1 (population i from row y - c_iy, column x - c_ix)
+                const float* rp = ring + ((q - 1) & 3) * 3 * nx;          // c_iy = +1: row y - 1
+                const float* rz = ring + (12 + (q % 3) * 3) * nx;         // c_iy =  0: row y
+                const float* rm = ring + (21 + ((q + 1) & 1) * 3) * nx;   // c_iy = -1: row y + 1
+                f2 g[9];
+                g[0] = *reinterpret_cast<const f2*>(rz + x);
+                g[1] = pk(rz[nx + xl], rz[nx + x]);
+                g[3] = pk(rz[2 * nx + x + 1], rz[2 * nx + xr]);
+                g[2] = *reinterpret_cast<const f2*>(rp + x);
+                g[5] = pk(rp[nx + xl], rp[nx + x]);
+                g[6] = pk(rp[2 * nx + x + 1], rp[2 * nx + xr]);
+                g[4] = *reinterpret_cast<const f2*>(rm + x);
+                g[7] = pk(rm[nx + x + 1], rm[nx + xr]);
+                g[8] = pk(rm[2 * nx + xl], rm[2 * nx + x]);
+                f2 qq;
+                collide_packed(g, omega, want_b ? &qq : nullptr);
+                if (want_b) add_usq(red[1], qq);
+                push(y, t + 1, g);
+            }
+        }
+        if (want_a || want_b) {
+            // this piece's sums; the block that completes the sample adds the pieces in row order
+            block_sum_dyn<2>(red, s_red);
+            if (tid == 0) {
+                p.partials[(int64_t)(rb + ya) * 2 + 0] = red[0];
+                p.partials[(int64_t)(rb + ya) * 2 + 1] = red[1];
+                __threadfence();
+                const int prev = atomicAdd(p.counters + j, yb - ya);
+                s_flag = (prev + (yb - ya) == ny);
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                double acc[2] = {0.0, 0.0};
+                for (int q = tid; q < ny; q += np) {
+                    if (q == 0 || (rb + q) % per == 0) {
+                        acc[0] += __ldcg(p.partials + (int64_t)(rb + q) * 2 + 0);
+                        acc[1] += __ldcg(p.partials + (int64_t)(rb + q) * 2 + 1);
+                    }
+                }
+                block_sum_dyn<2>(acc, s_red);
+                if (tid == 0) {
+                    const int64_t row = (int64_t)s_sp.sample_id * p.series_ld;
+                    if (want_a) p.series[row + t / p.qoi_every] = acc[0] * s_sp.u_ref_inv2;
+                    if (want_b) p.series[row + (t + 1) / p.qoi_every] = acc[1] * s_sp.u_ref_inv2;
+                    p.counters[j] = 0;
+                }
+            }
+        }
+    }
+}
+
 // After the finalize of a two-step run: the lattice that now holds each sample's state.
 __global__ void commit_kernel(KParams p) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.nsamples; j += gridDim.x * blockDim.x)
@@ -1270,6 +1544,7 @@ KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutp
     p.arena = b.arena;
     p.arena2 = b.arena2;
     p.sel = b.sel;
+    p.row_base = b.row_base;
     p.samples = b.samples;
     p.init = b.init;
     p.steps_sorted = b.steps_sorted;
@@ -1379,6 +1654,10 @@ cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cu
 
 }  // namespace
 
+bool strip_supported(int storage, int nx) {
+    return storage != UQLB_F64 && nx >= 64 && nx <= 2048 && nx % 64 == 0;
+}
+
 bool geometry_supported2(int storage, int tile_rows, int npt) {
     const int tr = tile_rows, n = npt;
     if (storage == UQLB_F64) return (tr == 4 && n == 2) || (tr == 8 && (n == 1 || n == 2));
@@ -1436,7 +1715,49 @@ cudaError_t launch_step2_s(const KParams& p, const BatchGeometry& g, cudaStream_
 }
 #undef UQLB_GEOM2
 
+constexpr int kStripMaxNx = 2048;
+size_t strip_smem(int nx) { return (size_t)kStripPlanes * nx * sizeof(float); }
+
+// Shared-memory opt-in (for the widest rows) and resident blocks per SM at width nx (once each).
+template <typename S>
+int strip_resident(int nx) {
+    static int cache[kStripMaxNx / 64 + 1] = {};
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(strip2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)strip_smem(kStripMaxNx));
+        attr = true;
+    }
+    int& n = cache[nx / 64];
+    if (n == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip2_kernel<S>, nx / 2, strip_smem(nx)) != cudaSuccess ||
+            b < 1)
+            b = 1;
+        n = b;
+    }
+    return n;
+}
+
+template <typename S>
+cudaError_t launch_strip_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    if (g.strip_nx < 64 || g.strip_nx > kStripMaxNx || g.strip_nx % 64 != 0) return cudaErrorInvalidConfiguration;
+    const int64_t resident = (int64_t)strip_resident<S>(g.strip_nx) * sm_count();
+    if (prepare_only) return cudaGetLastError();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
+    strip2_kernel<S><<<grid, g.strip_nx / 2, strip_smem(g.strip_nx), s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t step2_dispatch(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    if (g.strips) {
+        switch (g.storage) {
+            case UQLB_F32: return launch_strip_s<float>(p, g, s, prepare_only);
+            case UQLB_F16: return launch_strip_s<__half>(p, g, s, prepare_only);
+            case UQLB_BF16: return launch_strip_s<__nv_bfloat16>(p, g, s, prepare_only);
+            default: return cudaErrorInvalidConfiguration;
+        }
+    }
     switch (g.storage) {
         case UQLB_F64: return launch_step2_s<double>(p, g, s, prepare_only);
         case UQLB_F32: return launch_step2_s<float>(p, g, s, prepare_only);

@@ -299,8 +299,9 @@ struct BatchPlan {
     std::vector<SampleDev> table;
     std::vector<InitDev> init;
     std::vector<int32_t> steps_sorted;
+    std::vector<int32_t> row_base;
     std::vector<uint32_t> masks;
-    size_t off_arena = 0, off_arena2 = 0, off_sel = 0, off_bcpop = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
+    size_t off_arena = 0, off_arena2 = 0, off_sel = 0, off_rowbase = 0, off_bcpop = 0, off_samples = 0, off_init = 0, off_steps = 0, off_masks = 0, off_side = 0,
            off_partials = 0, off_counters = 0, off_done = 0, off_steps_run = 0, off_cd_prev = 0,
            off_step_counter = 0, off_flag = 0, off_streak = 0, off_sync = 0, total = 0;
     BatchGeometry geom{};
@@ -363,17 +364,25 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     const int scheme = o ? o->scheme : UQLB_SCHEME_AUTO;
-    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_TWO_STEP) {
+    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_TWO_STEP_STRIPS) {
         why = "unknown time-stepping scheme";
         return UQLB_ERR_ARG;
     }
     // auto: the two-step scheme where it measured faster (periodic FP32, FP16 and BF16 batches)
-    const bool two = scheme == UQLB_SCHEME_TWO_STEP ||
+    const bool two = scheme >= UQLB_SCHEME_TWO_STEP ||
                      (scheme == UQLB_SCHEME_AUTO && !mixed && mode == UQLB_MODE_GRAPH && storage != UQLB_F64);
     if (two && (mixed || mode != UQLB_MODE_GRAPH)) {
         why = "the two-step scheme runs periodic (TGV) batches in UQLB_MODE_GRAPH only";
         return UQLB_ERR_ARG;
     }
+    // row strips wherever the batch allows them, unless tiles are asked for
+    bool strip_ok = strip_supported(storage, smp[0].nx);
+    for (int64_t s = 1; s < n && strip_ok; ++s) strip_ok = smp[s].nx == smp[0].nx;
+    if (scheme == UQLB_SCHEME_TWO_STEP_STRIPS && !strip_ok) {
+        why = "the row-strip kernel needs FP32, FP16 or BF16 storage and one sample width, a multiple of 64 in 64..2048";
+        return UQLB_ERR_ARG;
+    }
+    const bool strips = two && strip_ok && scheme != UQLB_SCHEME_TWO_STEP_TILES;
     auto supported = [&](int r, int q) {
         return two ? geometry_supported2(storage, r, q) : geometry_supported(storage, mixed, r, q);
     };
@@ -407,6 +416,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.table.assign(n, SampleDev{});
     P.init.assign(n, InitDev{});
     P.steps_sorted.assign(n, 0);
+    P.row_base.assign(n + 1, 0);
     P.masks.clear();
     int64_t f_off = 0, tiles = 0, side = 0;
     int max_steps = 0, any_channel = 0, any_bouzidi = 0, any_inout = 0, tiles0 = -1;
@@ -434,6 +444,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         d.tiles = d.tiles_x * ((s.ny + tr - 1) / tr);
         d.tile_base = (int32_t)tiles;
         tiles += d.tiles;
+        P.row_base[j + 1] = (int32_t)std::min<int64_t>((int64_t)P.row_base[j] + s.ny, INT32_MAX);
         if (tiles0 < 0) tiles0 = d.tiles;
         if (d.tiles != tiles0) uniform_tiles = false;
         if (s.nx != smp[0].nx || s.ny != smp[0].ny) P.uniform_size = false;
@@ -498,6 +509,11 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         why = "too many tiles";
         return UQLB_ERR_ARG;
     }
+    const int64_t total_rows = P.row_base[n];
+    if (total_rows >= INT32_MAX) {
+        why = "too many lattice rows";
+        return UQLB_ERR_ARG;
+    }
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
@@ -510,10 +526,14 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.off_samples = take(sizeof(SampleDev) * n);
     P.off_init = take(sizeof(InitDev) * n);
     P.off_steps = take(sizeof(int32_t) * n);
+    P.off_rowbase = take(sizeof(int32_t) * (n + 1));
     P.off_masks = take(sizeof(uint32_t) * P.masks.size());
     P.off_side = take((size_t)side * 2 * 8);
     P.off_bcpop = take((size_t)bcnodes * 9 * sizeof(double));
-    P.off_partials = take((size_t)tiles * 7 * sizeof(double));
+    // per-tile sums (7 per tile); the row-strip kernel keeps 2 per row at the first row of each piece.
+    // Sized alike for both two-step kernels: the buffers behind it (done, steps_run, ...) carry a run
+    // into its resumption, which may use the other kernel.
+    P.off_partials = take((size_t)std::max<int64_t>(tiles * 7, two ? total_rows * 2 : 0) * sizeof(double));
     P.off_counters = take(sizeof(int32_t) * n);
     P.off_done = take(sizeof(int32_t) * n);
     P.off_steps_run = take(sizeof(int32_t) * n);
@@ -527,6 +547,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     BatchGeometry& g = P.geom;
     g.nsamples = n;
     g.total_tiles = tiles;
+    g.total_rows = total_rows;
     g.tile_rows = tr;
     g.npt = npt;
     g.max_steps = max_steps;
@@ -540,6 +561,9 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     }
     g.stochastic = (eb == 2 && rounding != UQLB_ROUND_NEAREST) ? 1 : 0;
     g.two_step = two ? 1 : 0;
+    g.strips = strips ? 1 : 0;
+    g.strip_nx = strips ? smp[0].nx : 0;
+    g.pad_ = 0;
     g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
     g.any_bouzidi = any_bouzidi;
     g.any_inout = any_inout;
@@ -556,6 +580,7 @@ BatchBuffers carve(const BatchPlan& P, void* ws) {
     B.arena = b + P.off_arena;
     B.arena2 = P.geom.two_step ? b + P.off_arena2 : nullptr;
     B.sel = P.geom.two_step ? reinterpret_cast<int32_t*>(b + P.off_sel) : nullptr;
+    B.row_base = reinterpret_cast<int32_t*>(b + P.off_rowbase);
     B.samples = reinterpret_cast<SampleDev*>(b + P.off_samples);
     B.init = reinterpret_cast<InitDev*>(b + P.off_init);
     B.steps_sorted = reinterpret_cast<int32_t*>(b + P.off_steps);
@@ -1021,7 +1046,8 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
         mixed |= samples[k].kind == UQLB_CASE_CHANNEL;
         nodes += (int64_t)samples[k].nx * samples[k].ny;
     }
-    bool two = false;
+    bool two = false, strips = false;
+    int def_r = 0, def_q = 0;
     {
         BatchPlan P0;
         std::string why;
@@ -1032,10 +1058,15 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
             goto done;
         }
         two = P0.geom.two_step != 0;
+        strips = P0.geom.strips != 0;
+        def_r = P0.geom.tile_rows;
+        def_q = P0.geom.npt;
     }
     for (int r : kGeomRows) {
         for (int q : kGeomNpt) {
             if (two ? !geometry_supported2(storage, r, q) : !geometry_supported(storage, mixed != 0, r, q)) continue;
+            // the row-strip kernel does not use the tile geometry (only the init and finalize do)
+            if (strips && (r != def_r || q != def_q)) continue;
             uqlb_run_opts o = *opts;
             o.tile_rows = r;
             o.nodes_per_thread = q;
@@ -1057,6 +1088,7 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
             if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
                 (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
                 (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
+                (e = cudaMemcpyAsync(ws + P.off_rowbase, P.row_base.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s)) ||
                 (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
                                                           cudaMemcpyHostToDevice, s))) ||
                 (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))) {
@@ -1153,7 +1185,8 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         return set_err(ctx, UQLB_ERR_OOM, "run_batch: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
     ctx->last_rows = P.geom.tile_rows;
     ctx->last_npt = P.geom.npt;
-    ctx->last_scheme = P.geom.two_step ? UQLB_SCHEME_TWO_STEP : UQLB_SCHEME_ONE_STEP;
+    ctx->last_scheme = !P.geom.two_step ? UQLB_SCHEME_ONE_STEP
+                       : (P.geom.strips ? UQLB_SCHEME_TWO_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_TILES);
     if (fields_dev) {
         if (!P.uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
         if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_ld too small");
@@ -1180,6 +1213,7 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ws + P.off_rowbase, P.row_base.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s)) ||
         (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
                                                   cudaMemcpyHostToDevice, s))) ||
         (e = cudaMemsetAsync(B.active_flag, 0, sizeof(int32_t), s)) ||

@@ -57,6 +57,7 @@ struct BatchBuffers {
     void* arena;             // populations, storage type
     void* arena2;            // second lattice of the two-step scheme (nullptr: one-step scheme)
     int32_t* sel;            // [S] two-step scheme: lattice (0/1) holding the state at the run's start
+    int32_t* row_base;       // [S + 1] first row of each sample in table order (row-strip kernel)
     SampleDev* samples;      // [S] ordered by descending steps
     InitDev* init;           // [S] same order
     int32_t* steps_sorted;   // [S] descending
@@ -81,6 +82,7 @@ struct BatchBuffers {
 struct BatchGeometry {
     int64_t nsamples;
     int64_t total_tiles;
+    int64_t total_rows;      // rows of all samples (row-strip kernel)
     int32_t tile_rows;       // rows per tile (threads per block = 32 x tile_rows)
     int32_t npt;             // nodes per thread along x (tile width 32 x npt)
     int32_t max_steps;
@@ -92,6 +94,9 @@ struct BatchGeometry {
     int32_t any_bouzidi;     // some sample uses the Bouzidi obstacle scheme
     int32_t two_step;        // UQLB_SCHEME_TWO_STEP: one launch per two steps on two lattices
     int32_t any_inout;       // some sample uses the interpolated inlet/outlet
+    int32_t strips;          // two-step scheme on row strips (strip2_kernel) instead of tiles
+    int32_t strip_nx;        // width of every sample when strips is set
+    int32_t pad_;            // keeps the struct free of padding bytes (it keys the graph cache)
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -134,6 +139,8 @@ cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const
                             cudaStream_t s);
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
 bool geometry_supported2(int storage, int tile_rows, int npt);  // two-step scheme
+// Row-strip two-step kernel: FP32/FP16/BF16 storage, sample width a multiple of 64 in 64..2048.
+bool strip_supported(int storage, int nx);
 
 // Plain per-sample FP64 path (plain_f64.cu).
 struct PlainSample {

@@ -35,7 +35,8 @@ MODES = {"graph": U.UQLB_MODE_GRAPH, "persistent": U.UQLB_MODE_PERSISTENT,
          "persistent_test_timeout": U.UQLB_MODE_PERSISTENT_TEST_TIMEOUT}
 
 
-SCHEMES = {"auto": U.UQLB_SCHEME_AUTO, "one_step": U.UQLB_SCHEME_ONE_STEP, "two_step": U.UQLB_SCHEME_TWO_STEP}
+SCHEMES = {"auto": U.UQLB_SCHEME_AUTO, "one_step": U.UQLB_SCHEME_ONE_STEP, "two_step": U.UQLB_SCHEME_TWO_STEP,
+           "two_step_tiles": U.UQLB_SCHEME_TWO_STEP_TILES, "two_step_strips": U.UQLB_SCHEME_TWO_STEP_STRIPS}
 
 
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,

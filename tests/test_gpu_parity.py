@@ -2,6 +2,7 @@
 same seeded inputs.  Tolerances are the stated error budget of each storage format against the
 FP64 oracle (relative L2): FP64 1e-12, FP32 1e-5, FP16/BF16 1e-3."""
 import math
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -561,6 +562,82 @@ def test_two_step_scheme_equals_one_step_scheme(ens, storage):
     assert rel_l2(b["fields"][:, :-1], a["fields"][:, :-1]) < ftol
 
 
+def _strip_specs(n, ny):
+    return [replace(W.tgv(n, 61, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(n, 30, nu=0.05), ny=ny),
+            replace(W.tgv(n, 1, nu=0.02), ny=ny), replace(W.tgv(n, 0, nu=0.04), ny=ny)]
+
+
+def _close(a, b, tol=1e-6, what=""):
+    assert rel_l2(a["fields"][:, :-1], b["fields"][:, :-1]) < tol, what
+    # K passes close to zero in the degenerate 2- and 3-row lattices: round-off relative to the series
+    scale = np.nanmax(np.abs(b["series"])) if np.isfinite(b["series"]).any() else 0.0
+    assert np.allclose(a["series"], b["series"], rtol=10 * tol, atol=tol * scale, equal_nan=True), what
+    # the total momentum is zero; its FP32 round-off grows with the node count (~1e-6 at 1600 nodes)
+    nodes = (b["fields"].shape[1] - 1) // 2
+    assert np.allclose(a["qoi"], b["qoi"], rtol=10 * tol, atol=tol * max(1.0, nodes / 1600)), what
+
+
+def test_two_step_strips_match_the_tiles_and_the_one_step_scheme(ens):
+    """The row-strip two-step kernel applies the same per-node formulas (every node in packed
+    pairs), so FP32 results agree with the one-step scheme and the tile kernel to round-off.
+    Widths 64 and 128; heights equal to the width, ragged (37) and degenerate (2, 3 rows, where the
+    rows above and below a node coincide); step counts that end on a single-step launch (61, 1) or
+    stop at once (0); K at every step and at a stride of 7."""
+    for n in (64, 128):
+        for ny in (n, 37, 2, 3):
+            specs = _strip_specs(n, ny)
+            for qe in (1, 7):
+                ref = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme="one_step")
+                st = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme="two_step_strips")
+                assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
+                ti = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme="two_step_tiles")
+                assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_TILES
+                _close(st, ref, what=(n, ny, qe, "one-step"))
+                _close(st, ti, what=(n, ny, qe, "tiles"))
+
+
+def test_two_step_strips_split_samples_across_blocks(ens):
+    """Many samples of mixed heights and step counts in one batch: each block's row range crosses
+    samples and each sample's rows are spread over several blocks, whose K partial sums the last
+    block adds in row order.  K series and final QoIs against the one-step scheme; a second run
+    reproduces the first bit for bit (fixed-order reduction)."""
+    specs = []
+    for i in range(40):
+        ny = (128, 37, 64, 3, 101)[i % 5]
+        specs.append(replace(W.tgv(128, 20 + 3 * (i % 7), nu=0.02 + 0.001 * i, amp2=0.0003), ny=ny))
+    ref = _run(ens, specs, "f32", qoi_every=1, series=True, scheme="one_step")
+    a = _run(ens, specs, "f32", qoi_every=1, series=True, scheme="two_step")
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
+    b = _run(ens, specs, "f32", qoi_every=1, series=True, scheme="two_step")
+    assert np.allclose(a["series"], ref["series"], rtol=1e-5, atol=0, equal_nan=True)
+    assert np.allclose(a["qoi"], ref["qoi"], rtol=1e-5, atol=1e-6)
+    assert np.array_equal(a["series"], b["series"], equal_nan=True)
+    assert np.array_equal(a["qoi"], b["qoi"], equal_nan=True)
+
+
+@pytest.mark.parametrize("first,second", [("two_step_strips", "two_step_strips"), ("two_step_tiles", "two_step_strips"),
+                                          ("two_step_strips", "two_step_tiles")])
+@pytest.mark.parametrize("split", [38, 51])
+def test_two_step_strips_resume_continues_the_run(ens, first, second, split):
+    """Strips and tiles leave the same lattice layout, so either continues a run of the other; a
+    strip run stopped and resumed on strips at an even split equals the uninterrupted run bit for
+    bit, other combinations to FP32 round-off."""
+    specs = _tgv_specs(64, 100) + [W.tgv(64, 71, nu=0.04)]
+    whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="two_step_strips")
+    head = [sample_struct(s) for s in specs]
+    for s in head:
+        s.steps = min(split, s.steps)
+    ens.run_batch(head, storage="f32", fields=False, scheme=first)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=True, start_step=split,
+                        scheme=second)
+    torch.cuda.synchronize()
+    got = res["fields"].double().cpu().numpy()[:, :-1]
+    if split % 2 == 0 and first == second:
+        assert np.array_equal(got, whole["fields"][:, :-1])
+    else:
+        assert rel_l2(got, whole["fields"][:, :-1]) < 1e-6
+
+
 @pytest.mark.parametrize("split", [37, 50])
 def test_two_step_resume_continues_the_run(ens, split):
     """A two-step run stopped after `split` steps and resumed equals the uninterrupted run: bit
@@ -582,13 +659,15 @@ def test_two_step_resume_continues_the_run(ens, split):
         assert rel_l2(got, whole["fields"][:, :-1]) < 1e-6
 
 
+@pytest.mark.parametrize("scheme", ["two_step_tiles", "two_step_strips"])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_two_step_16_bit_storage_against_the_oracle(ens, storage):
+def test_two_step_16_bit_storage_against_the_oracle(ens, storage, scheme):
     """16-bit storage on the two-step scheme keeps the intermediate step in FP32 shared memory, so
-    it rounds half as often; fields stay within the one-step scheme's budget of the oracle."""
+    it rounds half as often; fields stay within the one-step scheme's budget of the oracle (both
+    two-step kernels, stochastic rounding)."""
     specs = _tgv_specs(64, 300)
     ref = olbm.run([oracle_case(s) for s in specs])
-    g = _run(ens, specs, storage, scheme="two_step")
+    g = _run(ens, specs, storage, scheme=scheme)
     one = _run(ens, specs, storage, scheme="one_step")
     for i, r in enumerate(ref):
         e2 = rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1])

@@ -198,8 +198,9 @@ typedef struct {
  *     as often.  Two kernels:
  *       TWO_STEP_STRIPS: blocks walk full-width rows, keeping a ring of collided rows in shared
  *         memory (about 1 % of the nodes collided twice).  Every sample of the batch must have
- *         the same width nx, a multiple of 64 in 64..2048, with FP32, FP16 or BF16 storage;
- *         the tile geometry then serves only the initial state and the final fields.
+ *         the same width nx, a multiple of 64 in 64..2048 (64..1600 with FP32 storage, whose
+ *         rows are also staged in shared memory), with FP32, FP16 or BF16 storage; the tile
+ *         geometry then serves only the initial state and the final fields.
  *       TWO_STEP_TILES: blocks take tiles of the tile geometry with a one-node halo (any size,
  *         FP64 too; the halo is collided twice, 27 % more collisions at tile 8 x 128).
  *     UQLB_SCHEME_TWO_STEP takes strips where the batch allows them, else tiles.

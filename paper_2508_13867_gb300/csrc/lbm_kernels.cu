@@ -970,6 +970,42 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
 // none; with one barrier per row the next phase-A row may be written while a slower thread is
 // still gathering, which takes one more slot each: 4, 3 and 2 slots of 3 planes of nx floats.
 constexpr int kStripPlanes = 27;
+// FP32 rows are staged one row ahead by asynchronous copies; with a 196 KB share of shared memory
+// per SM (5 blocks at nx = 256) the L1 keeps 60 KB for the copies in flight, where the largest
+// share leaves 28 KB and caps the bytes in flight (141 against 178 GLUPS on the 625 x 256^2
+// ensemble).  16-bit rows have half the bytes in flight and gain more from warps: no staging, the
+// largest share (8 blocks).
+#ifndef UQLB_STRIP_PREFETCH_F32
+#define UQLB_STRIP_PREFETCH_F32 1
+#endif
+#ifndef UQLB_STRIP_PREFETCH_16
+#define UQLB_STRIP_PREFETCH_16 0
+#endif
+#ifndef UQLB_STRIP_CARVEOUT_F32_KB
+#define UQLB_STRIP_CARVEOUT_F32_KB 196
+#endif
+#ifndef UQLB_STRIP_CARVEOUT_16_KB
+#define UQLB_STRIP_CARVEOUT_16_KB 0
+#endif
+template <typename S>
+struct StripTune {
+    static constexpr int depth = sizeof(S) == 4 ? UQLB_STRIP_PREFETCH_F32 : UQLB_STRIP_PREFETCH_16;  // staged rows
+    static constexpr int carveout_kb = sizeof(S) == 4 ? UQLB_STRIP_CARVEOUT_F32_KB : UQLB_STRIP_CARVEOUT_16_KB;
+    // widest rows whose ring and staging fit one block's 227 KB (less 2 KB of static and reserve)
+    static constexpr int max_nx_raw = (232448 - 2048) / (kStripPlanes * 4 + depth * 9 * (int)sizeof(S)) / 64 * 64;
+    static constexpr int max_nx = max_nx_raw < 2048 ? max_nx_raw : 2048;
+};
+
+// Asynchronous copy of N bytes (4 or 8) from global to shared memory, completed per thread by
+// cp_async_wait_all().
+template <int N>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(a), "l"(gmem), "n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Slot plane of direction i for the phase-A row with sequence number q (q = row - first + 1).
 __device__ __forceinline__ int strip_plane(int i, int q) {
@@ -1053,9 +1089,11 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     extern __shared__ __align__(16) unsigned char s3_raw[];
     float* ring = reinterpret_cast<float*>(s3_raw);  // [kStripPlanes][nx]
     __shared__ __align__(16) SampleDev s_sp;
-    __shared__ double s_red[32 * 2];
+    double* s_red = reinterpret_cast<double*>(s3_raw);  // block sums: the ring, once a piece's gathers are done
     __shared__ int s_j, s_rows, s_nact, s_flag;
     const int tid = threadIdx.x, np = blockDim.x;
+    // staging slots of the next phase-A row: this thread's pair of each population, [9][nx]
+    S* stage = reinterpret_cast<S*>(ring + kStripPlanes * 2 * np);
     const int t = (int)p.step_counter[0] + p.dt;
     const int t0 = (int)p.step_counter[1];
     if (tid == 0) {
@@ -1152,13 +1190,36 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
             }
         } else {
             // phase A of the row with sequence number q (row ya - 1 + q, periodic)
-            auto phase_a = [&](int q, bool count) {
-                int y = ya - 1 + q;
-                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-                const S* s0 = src + (y * pitch + x);
-                f2 g[9];
+            auto row_of = [&](int q) {
+                const int y = ya - 1 + q;
+                return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            };
+            // staging: row q of the piece goes to buffer q % D, D rows ahead of its phase A; one copy
+            // group per row (empty past the piece), so D - 1 newer groups may stay pending
+            constexpr int D = StripTune<S>::depth;
+            auto fetch = [&](int q) {
+                if (q <= yb - ya + 1) {
+                    const S* s0 = src + (row_of(q) * pitch + x);
+                    S* st = stage + (q % (D > 0 ? D : 1)) * 9 * nx + x;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane);
+                    for (int i = 0; i < 9; ++i) cp_async<2 * sizeof(S)>(st + i * nx, s0 + i * plane);
+                }
+                cp_async_commit();
+            };
+            (void)fetch;
+            auto phase_a = [&](int q, bool count) {
+                f2 g[9];
+                if constexpr (D > 0) {
+                    cp_async_wait<D - 1>();
+                    const S* st = stage + (q % D) * 9 * nx + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * nx);
+                    fetch(q + D);
+                } else {
+                    const S* s0 = src + (row_of(q) * pitch + x);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane);
+                }
                 f2 qq;
                 const bool w = want_a && count;
                 collide_packed(g, omega, w ? &qq : nullptr);
@@ -1167,6 +1228,8 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) ring2[strip_plane(i, q) * np + tid] = g[i];
             };
+#pragma unroll
+            for (int k = 0; k < D; ++k) fetch(k);
             phase_a(0, false);
             phase_a(1, true);
             for (int y = ya; y < yb; ++y) {
@@ -1195,6 +1258,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
         }
         if (want_a || want_b) {
             // this piece's sums; the block that completes the sample adds the pieces in row order
+            __syncthreads();  // s_red lives in the ring
             block_sum_dyn<2>(red, s_red);
             if (tid == 0) {
                 p.partials[(int64_t)(rb + ya) * 2 + 0] = red[0];
@@ -1655,7 +1719,8 @@ cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cu
 }  // namespace
 
 bool strip_supported(int storage, int nx) {
-    return storage != UQLB_F64 && nx >= 64 && nx <= 2048 && nx % 64 == 0;
+    if (storage == UQLB_F64 || nx < 64 || nx % 64 != 0) return false;
+    return nx <= (storage == UQLB_F32 ? StripTune<float>::max_nx : StripTune<__half>::max_nx);
 }
 
 bool geometry_supported2(int storage, int tile_rows, int npt) {
@@ -1715,25 +1780,38 @@ cudaError_t launch_step2_s(const KParams& p, const BatchGeometry& g, cudaStream_
 }
 #undef UQLB_GEOM2
 
-constexpr int kStripMaxNx = 2048;
-size_t strip_smem(int nx) { return (size_t)kStripPlanes * nx * sizeof(float); }
+template <typename S>
+size_t strip_smem(int nx) {
+    return (size_t)kStripPlanes * nx * sizeof(float) + (size_t)StripTune<S>::depth * 9 * nx * sizeof(S);
+}
 
 // Shared-memory opt-in (for the widest rows) and resident blocks per SM at width nx (once each).
 template <typename S>
 int strip_resident(int nx) {
-    static int cache[kStripMaxNx / 64 + 1] = {};
+    constexpr int kb = StripTune<S>::carveout_kb;
+    static int cache[StripTune<S>::max_nx / 64 + 1] = {};
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(strip2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)strip_smem(kStripMaxNx));
+                             (int)strip_smem<S>(StripTune<S>::max_nx));
+        // percent of the 228 KB maximum, rounded down: the driver rounds up to the next supported split
+        if (kb > 0) cudaFuncSetAttribute(strip2_kernel<S>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
         attr = true;
     }
     int& n = cache[nx / 64];
     if (n == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip2_kernel<S>, nx / 2, strip_smem(nx)) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip2_kernel<S>, nx / 2, strip_smem<S>(nx)) != cudaSuccess ||
             b < 1)
             b = 1;
+        if (kb > 0) {
+            // blocks that fit the preferred share (each with its static part and 1 KB reserve), so
+            // that the grid stays resident in one wave
+            cudaFuncAttributes fa{};
+            cudaFuncGetAttributes(&fa, strip2_kernel<S>);
+            const size_t per = strip_smem<S>(nx) + fa.sharedSizeBytes + 1024;
+            b = std::max(1, std::min(b, (int)((size_t)kb * 1024 / per)));
+        }
         n = b;
     }
     return n;
@@ -1741,11 +1819,11 @@ int strip_resident(int nx) {
 
 template <typename S>
 cudaError_t launch_strip_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
-    if (g.strip_nx < 64 || g.strip_nx > kStripMaxNx || g.strip_nx % 64 != 0) return cudaErrorInvalidConfiguration;
+    if (g.strip_nx < 64 || g.strip_nx > StripTune<S>::max_nx || g.strip_nx % 64 != 0) return cudaErrorInvalidConfiguration;
     const int64_t resident = (int64_t)strip_resident<S>(g.strip_nx) * sm_count();
     if (prepare_only) return cudaGetLastError();
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
-    strip2_kernel<S><<<grid, g.strip_nx / 2, strip_smem(g.strip_nx), s>>>(p);
+    strip2_kernel<S><<<grid, g.strip_nx / 2, strip_smem<S>(g.strip_nx), s>>>(p);
     return cudaGetLastError();
 }
 

@@ -379,7 +379,8 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     bool strip_ok = strip_supported(storage, smp[0].nx);
     for (int64_t s = 1; s < n && strip_ok; ++s) strip_ok = smp[s].nx == smp[0].nx;
     if (scheme == UQLB_SCHEME_TWO_STEP_STRIPS && !strip_ok) {
-        why = "the row-strip kernel needs FP32, FP16 or BF16 storage and one sample width, a multiple of 64 in 64..2048";
+        why = "the row-strip kernel needs FP32, FP16 or BF16 storage and one sample width, a multiple of 64 in 64..2048 "
+              "(64..1600 with FP32)";
         return UQLB_ERR_ARG;
     }
     const bool strips = two && strip_ok && scheme != UQLB_SCHEME_TWO_STEP_TILES;

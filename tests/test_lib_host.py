@@ -287,18 +287,21 @@ def test_scheme_selection_and_its_limits():
         with pytest.raises(U.UqlbError) as e:
             U.uqlb_batch_workspace_bytes(smp, opts)
         assert e.value.status == U.UQLB_ERR_ARG
-    # the row-strip kernel: FP32/FP16/BF16, one width, a multiple of 64 in 64..2048
+    # the row-strip kernel: FP32/FP16/BF16, one width, a multiple of 64 in 64..2048 (FP32: 64..1600)
     strips = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_STRIPS)
+    bf16_strips = U.uqlb_run_opts(U.UQLB_BF16, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_STRIPS)
     tiles = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_TILES)
     f64_strips = U.uqlb_run_opts(U.UQLB_F64, U.UQLB_F64, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_STRIPS)
     for smp, opts in (([sample_struct(W.tgv(40, 10))], strips), ([sample_struct(W.tgv(4096, 10))], strips),
+                      ([sample_struct(W.tgv(1664, 10))], strips), ([sample_struct(W.tgv(4096, 10))], bf16_strips),
                       ([sample_struct(W.tgv(64, 10)), sample_struct(W.tgv(128, 10))], strips), (tgv, f64_strips),
                       (chan, strips), (chan, tiles)):
         with pytest.raises(U.UqlbError) as e:
             U.uqlb_batch_workspace_bytes(smp, opts)
         assert e.value.status == U.UQLB_ERR_ARG
-    for n in (64, 128, 2048):
+    for n in (64, 128, 1600):
         assert U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(n, 10))], strips) >= 2 * 9 * n * n * 4
+    assert U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(2048, 10))], bf16_strips) >= 2 * 9 * 2048 * 2048 * 2
     assert U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(40, 10))], tiles) >= 2 * 9 * 40 * 40 * 4
     # auto: channel batches and persistent mode stay one-step (one lattice)
     auto_chan = U.uqlb_batch_workspace_bytes(chan, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0))

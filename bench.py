@@ -36,7 +36,7 @@ STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in plac
                     "collided again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v2-packed"),
                 4: ("strip2_kernel (two-step row strips: each row collided into a shared-memory ring, streamed "
                     "and collided again, pushed to the other lattice)", "strip2_kernel_f32_tgv256.md",
-                    "two-step-strips-v1")}
+                    "two-step-strips-v2-staged")}
 
 
 def _peaks():
@@ -184,6 +184,8 @@ def bench_kernel_only(args):
     smp = ens.ensemble_samples(w)[: args.samples]
     for s in smp:
         s.steps = args.time_steps
+        if args.lattice > 0:
+            s.nx = s.ny = args.lattice
     out = {}
     for _ in range(args.warmup + args.steps):
         ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
@@ -666,6 +668,7 @@ def main():
     ap.add_argument("--kernel-only", action="store_true", help="small ensemble-run case for profiler captures")
     ap.add_argument("--samples", type=int, default=128)
     ap.add_argument("--time-steps", type=int, default=16)
+    ap.add_argument("--lattice", type=int, default=0, help="kernel-only: lattice side N (0: the workload's 256)")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)

@@ -460,11 +460,13 @@ def bench_workload(args):
     elif args.workload == "uneven":
         specs = W.uneven_batch()
         smp = [sample_struct(s) for s in specs]
-        tuned = ens.autotune(smp, storage=args.storage, trial_steps=8)
-        ms, r = timed(lambda: ens.run_batch(smp, storage=args.storage, fields=False), args.steps)
+        tuned = ens.autotune(smp, storage=args.storage, trial_steps=8, scheme=args.scheme)
+        ms, r = timed(lambda: ens.run_batch(smp, storage=args.storage, fields=False, scheme=args.scheme), args.steps)
         upd = sum(s.nx * s.ny * s.steps for s in specs)
         line.update({"samples": len(smp), "value": upd / (ms / 1e3) / 1e6, "batch_seconds": ms / 1e3,
-                     "tile_geometry": tuned})
+                     "tile_geometry": tuned, "scheme": args.scheme,
+                     "ran_as": {0: "auto", 1: "one_step", 3: "two_step_tiles", 4: "two_step_strips",
+                                5: "groups"}[U.uqlb_last_run_geometry(ens.ctx)[0]]})
         if args.plain_samples > 0:
             step = max(1, len(smp) // args.plain_samples)
             psub = smp[::step]

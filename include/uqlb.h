@@ -205,8 +205,14 @@ typedef struct {
  *         FP64 too; the halo is collided twice, 27 % more collisions at tile 8 x 128).
  *     UQLB_SCHEME_TWO_STEP takes strips where the batch allows them, else tiles.
  *   UQLB_SCHEME_AUTO: TWO_STEP for periodic FP32, FP16 and BF16 batches in graph mode, where it
- *     measured faster on GB300 (625 x 256^2 ensemble, GLUPS two-step tiles / one-step: FP32
- *     115 / 84, FP16 95 / 82, BF16 103 / 90); ONE_STEP otherwise (FP64 is bound by the FP64 rate).
+ *     measured faster on GB300 (625 x 256^2 ensemble, GLUPS two-step strips / tiles / one-step:
+ *     FP32 178 / 115 / 84, FP16 164 / 95 / 82, BF16 175 / 103 / 90); ONE_STEP otherwise (FP64 is
+ *     bound by the FP64 rate).  In graph mode with FP32/FP16/BF16 storage a batch of unlike
+ *     samples runs as groups of like samples, one group after another on one stream, each on its
+ *     own kernel and its own slice of the workspace (uqlb_batch_workspace_bytes counts them all):
+ *     CHANNEL samples on ONE_STEP, periodic samples of each width the strips take on
+ *     TWO_STEP_STRIPS, other periodic samples on TWO_STEP_TILES.  Outputs keep the caller's rows.
+ *     uqlb_last_run_geometry then reports UQLB_SCHEME_GROUPED.
  * A resumed run (start_step > 0) must use the scheme of the run it continues (strips and tiles
  * leave the same lattice layout, so either two-step kernel continues a two-step run). */
 enum {
@@ -214,7 +220,8 @@ enum {
     UQLB_SCHEME_ONE_STEP = 1,
     UQLB_SCHEME_TWO_STEP = 2,
     UQLB_SCHEME_TWO_STEP_TILES = 3,
-    UQLB_SCHEME_TWO_STEP_STRIPS = 4
+    UQLB_SCHEME_TWO_STEP_STRIPS = 4,
+    UQLB_SCHEME_GROUPED = 5 /* reported only: the batch ran as groups (UQLB_SCHEME_AUTO) */
 };
 
 /* Execution of the time loop.
@@ -378,7 +385,8 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
 int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches);
 
 /* Scheme the last uqlb_run_batch / uqlb_run_ensemble on this context ran (UQLB_SCHEME_ONE_STEP,
- * UQLB_SCHEME_TWO_STEP_TILES or UQLB_SCHEME_TWO_STEP_STRIPS) and its tile geometry.  Any output may be NULL;
+ * UQLB_SCHEME_TWO_STEP_TILES, UQLB_SCHEME_TWO_STEP_STRIPS, or UQLB_SCHEME_GROUPED for a batch run
+ * as groups) and its tile geometry (of the first group).  Any output may be NULL;
  * UQLB_ERR_STATE before the first run. */
 int uqlb_last_run_geometry(const uqlb_ctx* ctx, int32_t* scheme, int32_t* tile_rows, int32_t* nodes_per_thread);
 

@@ -102,7 +102,7 @@ __device__ __forceinline__ int classify(const SampleDev& sp, const uint32_t* mas
     if (yn < 0 || yn >= sp.ny) return kWall;
     if (xn < 0) return kInlet;
     if (xn >= sp.nx) return kOutlet;
-    if (mask != nullptr && mask_solid(mask, sp.mask_words, xn, yn)) return kSolid;
+    if (mask != nullptr && mask_solid(mask, mask_words(sp), xn, yn)) return kSolid;
     return kInterior;
 }
 
@@ -146,7 +146,7 @@ __device__ __forceinline__ uint32_t obstacle_links(const SampleDev& sp, const In
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         const int xn = x + cx(i), yn = y + cy(i);
-        if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny && mask_solid(mask, sp.mask_words, xn, yn))
+        if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny && mask_solid(mask, mask_words(sp), xn, yn))
             m |= 1u << i;
     }
     return m;
@@ -282,11 +282,11 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         if (tile == sp.tile_base && threadIdx.x == 0) {
             p.counters[j] = 0;
-            p.done[j] = 0;
-            p.steps_run[j] = sp.steps;
-            p.cd_prev[j] = NAN;
-            p.streak[j] = 0;
-            if (p.sel != nullptr) p.sel[j] = 0;  // the initial state is in the first lattice
+            p.done[sp.slot] = 0;
+            p.steps_run[sp.slot] = sp.steps;
+            p.cd_prev[sp.slot] = NAN;
+            p.streak[sp.slot] = 0;
+            if (p.sel != nullptr) p.sel[sp.slot] = 0;  // the initial state is in the first lattice
         }
         for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
@@ -442,7 +442,7 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             const int xn = x + cx(i), yn = y + cy(i);
-            if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny && mask_solid(mask, sp.mask_words, xn, yn)) {
+            if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny && mask_solid(mask, mask_words(sp), xn, yn)) {
                 const C fs = g[i] + wgt<C>(i);
                 fx += C(2 * cx(i)) * fs;
                 fy += C(2 * cy(i)) * fs;
@@ -509,16 +509,16 @@ __device__ __forceinline__ void record_force(const KParams& p, const SampleDev& 
     if (p.series) p.series[(int64_t)sp.sample_id * p.series_ld + col] = cd;
     if (p.series_cl) p.series_cl[(int64_t)sp.sample_id * p.series_ld + col] = cl;
     if (sp.steady_tol > 0.0) {
-        const double prev = p.cd_prev[j];
+        const double prev = p.cd_prev[sp.slot];
         const bool pass = !isnan(prev) && fabs(cd - prev) < sp.steady_tol * fabs(cd);
-        const int run = pass ? p.streak[j] + 1 : 0;
-        p.streak[j] = run;
+        const int run = pass ? p.streak[sp.slot] + 1 : 0;
+        p.streak[sp.slot] = run;
         if (run >= sp.steady_checks) {
-            p.done[j] = 1;
-            p.steps_run[j] = s;
+            p.done[sp.slot] = 1;
+            p.steps_run[sp.slot] = s;
             atomicAdd(p.n_done, 1);
         }
-        p.cd_prev[j] = cd;
+        p.cd_prev[sp.slot] = cd;
     }
 }
 
@@ -550,7 +550,7 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
     const int j = sh.j;
     const SampleDev& sp = sh.sp;
     const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
-    if (chan && p.done[j]) {
+    if (chan && p.done[sp.slot]) {
         __syncthreads();
         return;
     }
@@ -559,16 +559,29 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
     const int lt = tile - sp.tile_base;
     const int x0 = (lt % sp.tiles_x) * (kTileCols * NPT) + threadIdx.x;
     const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
-    const uint32_t* mask = (chan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+    // A channel tile whose nodes all lie at least one node inside the walls and the end columns and
+    // outside the obstacle's link box has no boundary link: its nodes take the periodic node path
+    // (the same loads, stores and arithmetic, no link classification).  The sample-level QoI logic
+    // (want_f, the tile reduction) stays on the sample's kind.
+    bool nchan = chan;
+    if (chan) {
+        const int tx0 = (lt % sp.tiles_x) * (kTileCols * NPT), ty0 = (lt / sp.tiles_x) * TR;
+        const int tx1 = tx0 + kTileCols * NPT - 1, ty1 = ty0 + TR - 1;
+        const InitDev& in = p.init[j];
+        const bool inner = tx0 >= 1 && tx1 <= sp.nx - 2 && ty0 >= 1 && ty1 <= sp.ny - 2 &&
+                           (tx1 < in.bbox[0] || tx0 > in.bbox[1] || ty1 < in.bbox[2] || ty0 > in.bbox[3]);
+        nchan = !inner;
+    }
+    const uint32_t* mask = (nchan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
     S* base = static_cast<S*>(p.arena) + sp.f_off;
 
-    const InitDev* bz = (chan && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
+    const InitDev* bz = (nchan && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
     C g[NPT][9];
     bool act[NPT];
     uint32_t lk[NPT];
     Nbr nb[NPT];
     Nbr rows;
-    if (!chan && ODD) {
+    if (!nchan && ODD) {
         periodic_rows(sp, y, rows);
     } else {
         rows.row[1] = y * sp.pitch;
@@ -577,17 +590,17 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
     for (int k = 0; k < NPT; ++k) {
         const int x = x0 + kTileCols * k;
         nb[k] = rows;
-        if (!chan && ODD) periodic_cols(sp, x, nb[k]);
+        if (!nchan && ODD) periodic_cols(sp, x, nb[k]);
         act[k] = x < sp.nx && y < sp.ny;
-        if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, sp.mask_words, x, y);
+        if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, mask_words(sp), x, y);
         lk[k] = (act[k] && bz != nullptr) ? obstacle_links(sp, *bz, mask, x, y) : 0u;
-        if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, chan, nb[k], bz, lk[k], g[k]);
+        if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, nchan, nb[k], bz, lk[k], g[k]);
     }
     double red[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
         if (act[k])
-            node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, chan, want_k, want_f, nb[k], bz, lk[k],
+            node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, nchan, want_k, want_f, nb[k], bz, lk[k],
                                 g[k], red);
 
     if (want_k || want_f) {
@@ -721,8 +734,8 @@ __global__ void __launch_bounds__(kTileCols* TR) persistent_kernel(KParams p, in
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ int launches_of(int t_end, int t0) { return t_end > t0 ? (t_end - t0 + 1) >> 1 : 0; }
 
-__device__ __forceinline__ bool on_final_second(const KParams& p, int j, int T) {
-    return ((p.sel[j] ^ launches_of(T, (int)p.step_counter[1])) & 1) != 0;
+__device__ __forceinline__ bool on_final_second(const KParams& p, int slot, int T) {
+    return ((p.sel[slot] ^ launches_of(T, (int)p.step_counter[1])) & 1) != 0;
 }
 
 // Tuning of the two-step kernel (measured on the 625 x 256^2 FP32 ensemble): nodes per load
@@ -790,7 +803,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
         const int lt = tile - sp.tile_base;
         const int x0 = (lt % sp.tiles_x) * TW, y0 = (lt / sp.tiles_x) * TR;
         const int wa = min(TW, sp.nx - x0), ha = min(TR, sp.ny - y0);  // active columns and rows
-        const bool second = ((p.sel[j] ^ ((t - t0) >> 1)) & 1) != 0;
+        const bool second = ((p.sel[sp.slot] ^ ((t - t0) >> 1)) & 1) != 0;
         const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + sp.f_off;
         S* dst = static_cast<S*>(second ? p.arena : p.arena2) + sp.f_off;
         const int plane = (int)sp.plane, pitch = sp.pitch, nx = sp.nx, ny = sp.ny;
@@ -1135,7 +1148,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
         r = rb + yb;
         const bool two = t + 1 < s_sp.steps;
         const bool want_b = two && want_b0;
-        const bool second = ((p.sel[j] ^ ((t - t0) >> 1)) & 1) != 0;
+        const bool second = ((p.sel[s_sp.slot] ^ ((t - t0) >> 1)) & 1) != 0;
         const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + s_sp.f_off;
         S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off;
         const float omega = (float)s_sp.omega;
@@ -1289,10 +1302,11 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     }
 }
 
-// After the finalize of a two-step run: the lattice that now holds each sample's state.
+// After the finalize of a two-step run: the lattice that now holds each sample's state (both
+// arrays are indexed by the sample's slot).
 __global__ void commit_kernel(KParams p) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.nsamples; j += gridDim.x * blockDim.x)
-        p.sel[j] ^= launches_of(p.steps_run[j], (int)p.step_counter[1]) & 1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < p.nsamples; k += gridDim.x * blockDim.x)
+        p.sel[k] ^= launches_of(p.steps_run[k], (int)p.step_counter[1]) & 1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1309,7 +1323,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
         const int j = tile_sample(p, (int)tile, p.nsamples);
         const SampleDev sp = p.samples[j];
         const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
-        const int T = p.steps_run[j];
+        const int T = p.steps_run[sp.slot];
         const int lt = (int)tile - sp.tile_base;
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         const uint32_t* mask = (sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
@@ -1317,13 +1331,13 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
         // two-step scheme: the state is in natural layout on the lattice the last launch wrote
         const bool two = p.sel != nullptr;
         S* lat = arena;
-        if (two && on_final_second(p, j, T)) lat = static_cast<S*>(p.arena2);
+        if (two && on_final_second(p, sp.slot, T)) lat = static_cast<S*>(p.arena2);
         double red[7] = {0, 0, 0, 0, 0, 0, 0};  // K, mass, mx, my, fx, fy, bad
         for (int q = threadIdx.x; q < tile_rows * tile_cols; q += blockDim.x) {
             const int x = (lt % sp.tiles_x) * tile_cols + (q % tile_cols);
             const int y = y0 + q / tile_cols;
             if (x >= sp.nx || y >= sp.ny) continue;
-            const bool solid = mask != nullptr && mask_solid(mask, sp.mask_words, x, y);
+            const bool solid = mask != nullptr && mask_solid(mask, mask_words(sp), x, y);
             double ux = 0.0, uy = 0.0;
             if (!solid) {
                 S* base = lat + sp.f_off;
@@ -1373,7 +1387,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     for (int i = 1; i < 9; ++i) {
                         const int xn = x + cx(i), yn = y + cy(i);
                         if (xn >= 0 && xn < sp.nx && yn >= 0 && yn < sp.ny &&
-                            mask_solid(mask, sp.mask_words, xn, yn)) {
+                            mask_solid(mask, mask_words(sp), xn, yn)) {
                             if (links) {
                                 const double fs =
                                     (double)Storage<S>::load(base + i * sp.plane + (int64_t)yn * sp.pitch + xn) +
@@ -1451,7 +1465,7 @@ __global__ void __launch_bounds__(256) bouzidi_force_kernel(KParams p) {
     const bool prev_odd = ((s - 1) & 1) != 0;
     for (int j = blockIdx.x; j < p.nsamples; j += gridDim.x) {
         const SampleDev& sp = p.samples[j];
-        if (!sp.bouzidi || sp.mask_off < 0 || s > sp.steps || p.done[j]) continue;
+        if (!sp.bouzidi || sp.mask_off < 0 || s > sp.steps || p.done[sp.slot]) continue;
         const InitDev& in = p.init[j];
         const uint32_t* mask = p.masks + sp.mask_off;
         const S* base = static_cast<const S*>(p.arena) + sp.f_off;
@@ -1460,7 +1474,7 @@ __global__ void __launch_bounds__(256) bouzidi_force_kernel(KParams p) {
         double red[2] = {0.0, 0.0};
         for (int n = threadIdx.x; n < nbox; n += NT) {
             const int x = in.bbox[0] + n % bw, y = in.bbox[2] + n / bw;
-            if (mask_solid(mask, sp.mask_words, x, y)) continue;
+            if (mask_solid(mask, mask_words(sp), x, y)) continue;
             const uint32_t links = obstacle_links(sp, in, mask, x, y);
             if (!links) continue;
             const int64_t own = (int64_t)y * sp.pitch + x;
@@ -1511,7 +1525,7 @@ __global__ void __launch_bounds__(256) inout_kernel(KParams p) {
     const int s = (int)(*p.step_counter) + p.dt + 1;
     for (int j = blockIdx.x; j < p.nsamples; j += gridDim.x) {
         const SampleDev& sp = p.samples[j];
-        if (sp.kind != UQLB_CASE_CHANNEL || !sp.inout || s > p.steps_run[j]) continue;
+        if (sp.kind != UQLB_CASE_CHANNEL || !sp.inout || s > p.steps_run[sp.slot]) continue;
         const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
         const S* base = static_cast<const S*>(p.arena) + sp.f_off;
         const int nx = sp.nx, ny = sp.ny;
@@ -1600,7 +1614,7 @@ __global__ void advance_kernel(int64_t* counter, int chunk) { *counter += chunk;
 // Resuming a run: samples that have not stopped take their new step totals.
 __global__ void resume_kernel(KParams p) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.nsamples; j += gridDim.x * blockDim.x)
-        if (!p.done[j]) p.steps_run[j] = p.samples[j].steps;
+        if (!p.done[p.samples[j].slot]) p.steps_run[p.samples[j].slot] = p.samples[j].steps;
 }
 
 KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs* o, int dt) {

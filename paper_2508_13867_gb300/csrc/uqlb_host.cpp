@@ -342,8 +342,9 @@ int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
     return UQLB_ERR_ARG;
 }
 
+// ids: the caller's index of each sample (the output row), nullptr for 0..n-1.
 int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchPlan& P, std::string& why,
-               int tuned_rows = 0, int tuned_npt = 0) {
+               int tuned_rows = 0, int tuned_npt = 0, const int64_t* ids = nullptr) {
     if (n <= 0 || n > (1 << 24)) {
         why = "sample count out of range";
         return UQLB_ERR_ARG;
@@ -425,6 +426,28 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     bool uniform_tiles = true;
     P.n_steady = 0;
     P.uniform_size = true;
+    // Lattice regions and boundary buffers in the caller's order (the slot), so that they do not
+    // move when the step counts, and with them the table order, change between a run and its
+    // resumption.
+    std::vector<int64_t> f_off_of(n), side_of(n, -1), bc_of(n, -1);
+    for (int64_t k = 0; k < n; ++k) {
+        const uqlb_sample& s = smp[k];
+        const int64_t plane = (int64_t)align_up((size_t)s.nx, (size_t)row_align) * s.ny;
+        if (9 * plane >= (1ll << 31)) {
+            why = "a sample's nine population planes must hold fewer than 2^31 values";
+            return UQLB_ERR_ARG;
+        }
+        f_off_of[k] = f_off;
+        f_off += 9 * plane;
+        if (s.kind == UQLB_CASE_CHANNEL) {
+            side_of[k] = side;
+            side += s.ny;
+            if (s.inout_bc == UQLB_INOUT_INTERPOLATED) {
+                bc_of[k] = bcnodes;
+                bcnodes += 2 * (int64_t)s.ny;
+            }
+        }
+    }
     for (int64_t j = 0; j < n; ++j) {
         const uqlb_sample& s = smp[order[j]];
         SampleDev& d = P.table[j];
@@ -432,15 +455,11 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         d.ny = s.ny;
         d.pitch = (int32_t)align_up((size_t)s.nx, (size_t)row_align);
         d.plane = (int64_t)d.pitch * s.ny;
-        if (9 * d.plane >= (1ll << 31)) {
-            why = "a sample's nine population planes must hold fewer than 2^31 values";
-            return UQLB_ERR_ARG;
-        }
-        d.f_off = f_off;
-        f_off += 9 * d.plane;
+        d.f_off = f_off_of[order[j]];
+        d.slot = (int32_t)order[j];
         d.kind = s.kind;
         d.steps = (int32_t)s.steps;
-        d.sample_id = (int32_t)order[j];
+        d.sample_id = (int32_t)(ids ? ids[order[j]] : order[j]);
         d.tiles_x = (s.nx + 32 * npt - 1) / (32 * npt);
         d.tiles = d.tiles_x * ((s.ny + tr - 1) / tr);
         d.tile_base = (int32_t)tiles;
@@ -452,7 +471,6 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         d.omega = 1.0 / (3.0 * s.nu + 0.5);
         d.u_ref_inv2 = (s.u_ref > 0.0) ? 2.0 / ((double)s.nx * (double)s.ny * s.u_ref * s.u_ref) : 0.0;
         d.mask_off = -1;
-        d.mask_words = (s.nx + 31) / 32;
         d.side_off = -1;
         d.uin_max = 0.0;
         d.force_norm = 0.0;
@@ -465,38 +483,40 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
             d.steady_tol = s.steady_tol > 0.0 ? s.steady_tol : 0.0;
             d.steady_checks = s.steady_checks > 1 ? s.steady_checks : 1;
             if (d.steady_tol > 0.0) ++P.n_steady;
-            d.side_off = (int32_t)side;
-            side += s.ny;
+            d.side_off = (int32_t)side_of[order[j]];
             if (s.inout_bc == UQLB_INOUT_INTERPOLATED) {
                 d.inout = 1;
-                d.bc_off = (int32_t)bcnodes;
-                bcnodes += 2 * (int64_t)s.ny;
+                d.bc_off = (int32_t)bc_of[order[j]];
                 any_inout = 1;
             }
+            // the only nodes that can be solid or have a solid neighbour (empty box: no obstacle);
+            // the Bouzidi links and the channel step's interior tiles rely on it
+            InitDev& in = P.init[j];
+            in.bbox[0] = in.bbox[2] = -1;
+            in.bbox[1] = in.bbox[3] = -2;
             if (s.cyl_r > 0.0) {
                 d.force_norm = (s.u0 != 0.0) ? 2.0 / (s.u0 * s.u0 * 2.0 * s.cyl_r) : 0.0;
+                // a node with a solid neighbour lies within r + sqrt(2) of the centre
+                auto lo = [](double v, int n) {
+                    return (int)std::max(0.0, std::min((double)(n - 1), std::floor(v)));
+                };
+                in.bbox[0] = lo(s.cyl_cx - s.cyl_r - 2.0, s.nx);
+                in.bbox[1] = lo(s.cyl_cx + s.cyl_r + 1.0, s.nx);
+                in.bbox[2] = lo(s.cyl_cy - s.cyl_r - 2.0, s.ny);
+                in.bbox[3] = lo(s.cyl_cy + s.cyl_r + 1.0, s.ny);
                 if (s.obstacle_bc == UQLB_OBSTACLE_BOUZIDI) {
                     d.bouzidi = 1;
                     any_bouzidi = 1;
-                    InitDev& in = P.init[j];
                     in.cyl_cx = s.cyl_cx;
                     in.cyl_cy = s.cyl_cy;
                     in.cyl_r = s.cyl_r;
-                    // a node with a solid neighbour lies within r + sqrt(2) of the centre
-                    auto lo = [](double v, int n) {
-                        return (int)std::max(0.0, std::min((double)(n - 1), std::floor(v)));
-                    };
-                    in.bbox[0] = lo(s.cyl_cx - s.cyl_r - 2.0, s.nx);
-                    in.bbox[1] = lo(s.cyl_cx + s.cyl_r + 1.0, s.nx);
-                    in.bbox[2] = lo(s.cyl_cy - s.cyl_r - 2.0, s.ny);
-                    in.bbox[3] = lo(s.cyl_cy + s.cyl_r + 1.0, s.ny);
                 }
                 d.mask_off = (int32_t)P.masks.size();
-                P.masks.resize(P.masks.size() + (size_t)d.mask_words * s.ny, 0u);
+                P.masks.resize(P.masks.size() + (size_t)mask_words(d) * s.ny, 0u);
                 uint32_t* m = P.masks.data() + d.mask_off;
                 for (int y = 0; y < s.ny; ++y)
                     for (int x = 0; x < s.nx; ++x)
-                        if (sample_solid(s, x, y)) m[(size_t)y * d.mask_words + (x >> 5)] |= 1u << (x & 31);
+                        if (sample_solid(s, x, y)) m[(size_t)y * mask_words(d) + (x >> 5)] |= 1u << (x & 31);
             }
         }
         P.init[j].u0 = s.u0;
@@ -715,9 +735,61 @@ int check_case(uqlb_ctx* ctx, const uqlb_case* c) {
 const int kGeomRows[] = {2, 4, 8, 16};
 const int kGeomNpt[] = {1, 2, 4};
 
+// A batch of unlike samples under UQLB_SCHEME_AUTO (graph mode, FP32/FP16/BF16 storage) runs as
+// groups of like samples, one after another, each on its own kernel and its own slice of the
+// workspace: CHANNEL samples on the one-step scheme, periodic samples of each width the row-strip
+// kernel takes on strips, other periodic samples on two-step tiles.  Empty when the batch is one
+// such group (it then runs as one batch, as before).
+struct Group {
+    std::vector<int64_t> idx;  // caller's indices, ascending
+    int32_t scheme;
+    std::vector<uqlb_sample> smp;
+    uqlb_run_opts opts;
+};
+std::vector<Group> make_groups(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o) {
+    std::vector<Group> out;
+    if (!o || o->scheme != UQLB_SCHEME_AUTO || o->mode != UQLB_MODE_GRAPH || o->storage == UQLB_F64 || n < 2)
+        return out;
+    Group chan{{}, UQLB_SCHEME_ONE_STEP, {}, *o}, tiles{{}, UQLB_SCHEME_TWO_STEP_TILES, {}, *o};
+    std::map<int, Group> strips;
+    for (int64_t s = 0; s < n; ++s) {
+        if (smp[s].kind == UQLB_CASE_CHANNEL)
+            chan.idx.push_back(s);
+        else if (strip_supported(o->storage, smp[s].nx)) {
+            auto it = strips.find(smp[s].nx);
+            if (it == strips.end()) it = strips.emplace(smp[s].nx, Group{{}, UQLB_SCHEME_TWO_STEP_STRIPS, {}, *o}).first;
+            it->second.idx.push_back(s);
+        } else
+            tiles.idx.push_back(s);
+    }
+    if (!chan.idx.empty()) out.push_back(std::move(chan));
+    if (!tiles.idx.empty()) out.push_back(std::move(tiles));
+    for (auto& kv : strips) out.push_back(std::move(kv.second));
+    if (out.size() < 2) return {};
+    for (auto& g : out) {
+        for (int64_t s : g.idx) g.smp.push_back(smp[s]);
+        g.opts.scheme = g.scheme;
+    }
+    return out;
+}
+
 // Workspace of a batch: the planned layout, and with both geometry fields 0 the largest layout of
-// any compiled geometry (the autotuner may pick any of them later).
+// any compiled geometry (the autotuner may pick any of them later).  A batch run in groups takes
+// the groups' workspaces one after another, each 256-byte aligned.
+int batch_bytes_one(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes, std::string& why);
 int batch_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes, std::string& why) {
+    auto groups = make_groups(samples, n, opts);
+    if (groups.empty()) return batch_bytes_one(samples, n, opts, bytes, why);
+    size_t total = 0;
+    for (auto& g : groups) {
+        size_t b = 0;
+        if (int rc = batch_bytes_one(g.smp.data(), (int64_t)g.smp.size(), &g.opts, &b, why)) return rc;
+        total = align_up(total + b, 256);
+    }
+    *bytes = total;
+    return 0;
+}
+int batch_bytes_one(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts, size_t* bytes, std::string& why) {
     BatchPlan P;
     if (int rc = plan_batch(samples, n, opts, P, why)) return rc;
     size_t best = P.total;
@@ -735,6 +807,105 @@ int batch_bytes(const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts
     *bytes = best;
     return 0;
 }
+
+// One planned batch: tables, init (or resume), the time loop, finalize.  own_timing: the loop
+// records the context's loop events (a batch run in groups times all groups from outside).
+int run_planned(uqlb_ctx* ctx, const BatchPlan& P, int64_t n, const uqlb_run_opts* opts, void* workspace_dev,
+                void* fields_dev, int64_t fields_ld, double* qoi_dev, double* series_dev, double* series_cl_dev,
+                int64_t series_ld, cudaStream_t s, bool own_timing) {
+    const bool resume = opts->start_step > 0;
+    const int chunk = opts->chunk_steps > 0 ? opts->chunk_steps : 64;
+    BatchBuffers B = carve(P, workspace_dev);
+    char* ws = static_cast<char*>(workspace_dev);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(ws + P.off_rowbase, P.row_base.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s)) ||
+        (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
+                                                  cudaMemcpyHostToDevice, s))) ||
+        (e = cudaMemsetAsync(B.active_flag, 0, sizeof(int32_t), s)) ||
+        (e = cudaMemsetAsync(B.bar_count, 0, 64, s)) ||
+        (!resume && (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))))
+        return cuda_fail(ctx, e, "run_batch: table upload");
+    // the device step counter starts at start_step (0 for a fresh run); ctx keeps the host copy alive
+    ctx->counter_host[0] = ctx->counter_host[1] = opts->start_step;
+    if ((e = cudaMemcpyAsync(B.step_counter, ctx->counter_host, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, s)))
+        return cuda_fail(ctx, e, "run_batch: step counter");
+
+    RunOutputs O{};
+    O.fields = fields_dev;
+    O.fields_ld = fields_ld;
+    O.fields_dtype = opts->fields_dtype;
+    O.qoi = qoi_dev;
+    O.series = series_dev;
+    O.series_cl = series_cl_dev;
+    O.series_ld = series_ld;
+    O.qoi_every = opts->qoi_every;
+
+    ctx->run_launches += 2;
+    if (!resume) {
+        if ((e = launch_init(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: init launch");
+    } else {
+        if ((e = launch_resume(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: resume launch");
+    }
+    ctx->bar_err = B.bar_err;
+    if (P.geom.max_steps > opts->start_step && opts->mode != UQLB_MODE_GRAPH) {
+        // persistent: one cooperative launch per chunk, then the step counter advances
+        const int pchunk = opts->chunk_steps > 0 ? chunk : 1024;
+        const int64_t nchunks = (P.geom.max_steps - opts->start_step + pchunk - 1) / pchunk;
+        const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
+        if (own_timing && (e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "run_batch: event record");
+        for (int64_t q = 0; q < nchunks; ++q) {
+            if ((e = cudaMemsetAsync(B.tickets, 0, sizeof(unsigned long long), s)) ||
+                (e = launch_persistent(B, P.geom, O, pchunk, s)) || (e = launch_advance(B, pchunk, s)))
+                return cuda_fail(ctx, e, "run_batch: persistent launch");
+            ctx->run_launches += 2;
+            if (steady && q + 1 < nchunks) {
+                int32_t ndone = 0;
+                if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
+                    (e = cudaStreamSynchronize(s)))
+                    return cuda_fail(ctx, e, "run_batch: convergence check");
+                if (ndone >= P.n_steady) break;
+            }
+        }
+        if (own_timing) {
+            if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+            ctx->loop_timed = true;
+        }
+    } else if (P.geom.max_steps > opts->start_step) {
+        cudaGraphExec_t exec = nullptr;
+        if (P.geom.two_step && (e = prepare_step2(P.geom)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: prepare");
+        if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, (int)(opts->start_step & 1), &exec)) return rc;
+        const int64_t nchunks = (P.geom.max_steps - opts->start_step + chunk - 1) / chunk;
+        const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
+        if (own_timing && (e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "run_batch: event record");
+        for (int64_t q = 0; q < nchunks; ++q) {
+            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
+            ctx->run_launches += P.geom.two_step ? chunk / 2 + 1
+                                                 : chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0) +
+                                                       (P.geom.any_inout ? chunk : 0);
+            if (steady && (q % 8) == 7 && q + 1 < nchunks) {
+                int32_t ndone = 0;
+                if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
+                    (e = cudaStreamSynchronize(s)))
+                    return cuda_fail(ctx, e, "run_batch: convergence check");
+                if (ndone >= P.n_steady) break;
+            }
+        }
+        if (own_timing) {
+            if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+            ctx->loop_timed = true;
+        }
+    }
+    if ((e = launch_finalize(B, P.geom, O, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: finalize launch");
+    if (P.geom.two_step && (e = launch_commit(B, P.geom, s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "run_batch: commit launch");
+    return 0;
+}
+
 
 }  // namespace
 
@@ -1034,6 +1205,33 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
     if (!samples || !opts || !workspace_dev) return set_err(ctx, UQLB_ERR_ARG, "autotune: null argument");
     if (trial_steps < 2 || (trial_steps & 1) || trial_steps > 4096)
         return set_err(ctx, UQLB_ERR_ARG, "autotune: trial_steps must be even, 2..4096");
+    {
+        // a batch that runs as groups: each group is tuned on its own (the run looks each up by its
+        // shape); the outputs describe the group with the most node updates
+        auto groups = make_groups(samples, n, opts);
+        if (!groups.empty()) {
+            size_t big = 0;
+            double most = -1.0;
+            for (size_t g = 0; g < groups.size(); ++g) {
+                double w = 0.0;
+                for (auto& x : groups[g].smp) w += (double)x.nx * x.ny * (double)x.steps;
+                if (w > most) {
+                    most = w;
+                    big = g;
+                }
+            }
+            for (size_t g = 0; g < groups.size(); ++g) {
+                const bool out = g == big;
+                if (int rc = uqlb_autotune(ctx, groups[g].smp.data(), (int64_t)groups[g].smp.size(), &groups[g].opts,
+                                           workspace_dev, workspace_bytes, trial_steps, out ? tile_rows : nullptr,
+                                           out ? nodes_per_thread : nullptr, out ? rows_tried : nullptr,
+                                           out ? npt_tried : nullptr, out ? ms_per_step : nullptr,
+                                           out ? n_tried : nullptr, stream))
+                    return rc;
+            }
+            return 0;
+        }
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e;
@@ -1165,137 +1363,96 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     if (int rc = check_ctx(ctx)) return rc;
     if (!samples || !opts || !workspace_dev) return set_err(ctx, UQLB_ERR_ARG, "run_batch: null argument");
     if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: workspace must be 256-byte aligned");
-    BatchPlan P;
-    std::string why;
-    int tuned_r = 0, tuned_q = 0;
-    {
+    // the geometry the autotuner picked for a batch of this shape, if any
+    auto tuned_for = [&](const uqlb_sample* smp, int64_t m, int& tr, int& tq) {
         int mixed = 0;
         int64_t nodes = 0;
-        for (int64_t k = 0; k < n; ++k) {
-            mixed |= samples[k].kind == UQLB_CASE_CHANNEL;
-            nodes += (int64_t)samples[k].nx * samples[k].ny;
+        for (int64_t k = 0; k < m; ++k) {
+            mixed |= smp[k].kind == UQLB_CASE_CHANNEL;
+            nodes += (int64_t)smp[k].nx * smp[k].ny;
         }
+        tr = tq = 0;
         for (auto& t : ctx->tuned)
-            if (t.storage == opts->storage && t.mixed == mixed && t.n == n && t.nodes == nodes) {
-                tuned_r = t.rows;
-                tuned_q = t.npt;
+            if (t.storage == opts->storage && t.mixed == mixed && t.n == m && t.nodes == nodes) {
+                tr = t.rows;
+                tq = t.npt;
             }
+    };
+    // plans: one, or one per group of like samples
+    std::string why;
+    auto groups = make_groups(samples, n, opts);
+    std::vector<BatchPlan> plans(groups.empty() ? 1 : groups.size());
+    std::vector<size_t> offs(plans.size(), 0);
+    size_t need = 0;
+    for (size_t g = 0; g < plans.size(); ++g) {
+        const uqlb_sample* smp = groups.empty() ? samples : groups[g].smp.data();
+        const int64_t m = groups.empty() ? n : (int64_t)groups[g].smp.size();
+        const uqlb_run_opts* o = groups.empty() ? opts : &groups[g].opts;
+        int tr = 0, tq = 0;
+        tuned_for(smp, m, tr, tq);
+        if (int rc = plan_batch(smp, m, o, plans[g], why, tr, tq, groups.empty() ? nullptr : groups[g].idx.data()))
+            return set_err(ctx, rc, "run_batch: %s", why.c_str());
+        offs[g] = need;
+        need = align_up(need + plans[g].total, 256);
     }
-    if (int rc = plan_batch(samples, n, opts, P, why, tuned_r, tuned_q)) return set_err(ctx, rc, "run_batch: %s", why.c_str());
-    if (workspace_bytes < P.total)
-        return set_err(ctx, UQLB_ERR_OOM, "run_batch: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
-    ctx->last_rows = P.geom.tile_rows;
-    ctx->last_npt = P.geom.npt;
-    ctx->last_scheme = !P.geom.two_step ? UQLB_SCHEME_ONE_STEP
-                       : (P.geom.strips ? UQLB_SCHEME_TWO_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_TILES);
+    if (groups.empty()) need = plans[0].total;
+    if (workspace_bytes < need)
+        return set_err(ctx, UQLB_ERR_OOM, "run_batch: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    int max_steps = 0, n_steady = 0;
+    bool uniform_size = true;
+    for (auto& P : plans) {
+        max_steps = std::max(max_steps, P.geom.max_steps);
+        n_steady += P.n_steady;
+        uniform_size = uniform_size && P.uniform_size;
+    }
+    for (int64_t k = 1; k < n; ++k)
+        if (samples[k].nx != samples[0].nx || samples[k].ny != samples[0].ny) uniform_size = false;
+    const BatchPlan& P0 = plans[0];
+    ctx->last_rows = P0.geom.tile_rows;
+    ctx->last_npt = P0.geom.npt;
+    ctx->last_scheme = !groups.empty() ? UQLB_SCHEME_GROUPED
+                       : !P0.geom.two_step ? UQLB_SCHEME_ONE_STEP
+                       : (P0.geom.strips ? UQLB_SCHEME_TWO_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_TILES);
     if (fields_dev) {
-        if (!P.uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
+        if (!uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
         if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_ld too small");
         if (opts->fields_dtype != UQLB_F64 && opts->fields_dtype != UQLB_F32)
             return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_dtype must be F64 or F32");
     }
     if (opts->qoi_every < 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: qoi_every must be >= 0");
-    if (opts->start_step < 0 || opts->start_step > P.geom.max_steps)
+    if (opts->start_step < 0 || opts->start_step > max_steps)
         return set_err(ctx, UQLB_ERR_ARG, "run_batch: start_step must be in [0, the largest step count]");
-    const bool resume = opts->start_step > 0;
     if ((series_dev || series_cl_dev) && opts->qoi_every > 0) {
-        const int64_t need = P.geom.max_steps / opts->qoi_every + 1;
-        if (series_ld < need) return set_err(ctx, UQLB_ERR_ARG, "run_batch: series_ld %lld < %lld", (long long)series_ld, (long long)need);
+        const int64_t need_ld = max_steps / opts->qoi_every + 1;
+        if (series_ld < need_ld) return set_err(ctx, UQLB_ERR_ARG, "run_batch: series_ld %lld < %lld", (long long)series_ld, (long long)need_ld);
     }
-    int chunk = opts->chunk_steps > 0 ? opts->chunk_steps : 64;
+    const int chunk = opts->chunk_steps > 0 ? opts->chunk_steps : 64;
     if (chunk < 2 || chunk > 1024 || (chunk & 1)) return set_err(ctx, UQLB_ERR_ARG, "run_batch: chunk_steps must be even, 2..1024");
-    if (P.n_steady > 0 && opts->qoi_every <= 0)
+    if (n_steady > 0 && opts->qoi_every <= 0)
         return set_err(ctx, UQLB_ERR_ARG, "run_batch: a steady-state tolerance needs qoi_every > 0");
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    BatchBuffers B = carve(P, workspace_dev);
-    char* ws = static_cast<char*>(workspace_dev);
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
-        (e = cudaMemcpyAsync(ws + P.off_rowbase, P.row_base.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s)) ||
-        (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
-                                                  cudaMemcpyHostToDevice, s))) ||
-        (e = cudaMemsetAsync(B.active_flag, 0, sizeof(int32_t), s)) ||
-        (e = cudaMemsetAsync(B.bar_count, 0, 64, s)) ||
-        (!resume && (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))))
-        return cuda_fail(ctx, e, "run_batch: table upload");
-    // the device step counter starts at start_step (0 for a fresh run); ctx keeps the host copy alive
-    ctx->counter_host[0] = ctx->counter_host[1] = opts->start_step;
-    if ((e = cudaMemcpyAsync(B.step_counter, ctx->counter_host, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, s)))
-        return cuda_fail(ctx, e, "run_batch: step counter");
-
-    RunOutputs O{};
-    O.fields = fields_dev;
-    O.fields_ld = fields_ld;
-    O.fields_dtype = opts->fields_dtype;
-    O.qoi = qoi_dev;
-    O.series = series_dev;
-    O.series_cl = series_cl_dev;
-    O.series_ld = series_ld;
-    O.qoi_every = opts->qoi_every;
-
     if (!ctx->loop_begin) {
         if ((e = cudaEventCreate(&ctx->loop_begin)) || (e = cudaEventCreate(&ctx->loop_end)))
             return cuda_fail(ctx, e, "run_batch: event create");
     }
     ctx->loop_timed = false;
-    ctx->loop_steps = P.geom.max_steps;
-    ctx->run_launches = 2;
-    if (!resume) {
-        if ((e = launch_init(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: init launch");
-    } else {
-        if ((e = launch_resume(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: resume launch");
+    ctx->loop_steps = max_steps;
+    ctx->run_launches = 0;
+    if (groups.empty())
+        return run_planned(ctx, P0, n, opts, workspace_dev, fields_dev, fields_ld, qoi_dev, series_dev, series_cl_dev,
+                           series_ld, s, true);
+    // groups one after another; the loop time spans all of them (their init and finalize included)
+    if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+    for (size_t g = 0; g < plans.size(); ++g) {
+        if (int rc = run_planned(ctx, plans[g], (int64_t)groups[g].smp.size(), &groups[g].opts,
+                                 static_cast<char*>(workspace_dev) + offs[g], fields_dev, fields_ld, qoi_dev, series_dev,
+                                 series_cl_dev, series_ld, s, false))
+            return rc;
     }
-    ctx->bar_err = B.bar_err;
-    if (P.geom.max_steps > opts->start_step && opts->mode != UQLB_MODE_GRAPH) {
-        // persistent: one cooperative launch per chunk, then the step counter advances
-        const int pchunk = opts->chunk_steps > 0 ? chunk : 1024;
-        const int64_t nchunks = (P.geom.max_steps - opts->start_step + pchunk - 1) / pchunk;
-        const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
-        if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
-        for (int64_t q = 0; q < nchunks; ++q) {
-            if ((e = cudaMemsetAsync(B.tickets, 0, sizeof(unsigned long long), s)) ||
-                (e = launch_persistent(B, P.geom, O, pchunk, s)) || (e = launch_advance(B, pchunk, s)))
-                return cuda_fail(ctx, e, "run_batch: persistent launch");
-            ctx->run_launches += 2;
-            if (steady && q + 1 < nchunks) {
-                int32_t ndone = 0;
-                if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
-                    (e = cudaStreamSynchronize(s)))
-                    return cuda_fail(ctx, e, "run_batch: convergence check");
-                if (ndone >= P.n_steady) break;
-            }
-        }
-        if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
-        ctx->loop_timed = true;
-    } else if (P.geom.max_steps > opts->start_step) {
-        cudaGraphExec_t exec = nullptr;
-        if (P.geom.two_step && (e = prepare_step2(P.geom)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: prepare");
-        if (int rc = chunk_graph(ctx, B, P.geom, O, chunk, (int)(opts->start_step & 1), &exec)) return rc;
-        const int64_t nchunks = (P.geom.max_steps - opts->start_step + chunk - 1) / chunk;
-        const bool steady = P.n_steady > 0 && P.n_steady == (int)n;
-        if ((e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
-        for (int64_t q = 0; q < nchunks; ++q) {
-            if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
-            ctx->run_launches += P.geom.two_step ? chunk / 2 + 1
-                                                 : chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0) +
-                                                       (P.geom.any_inout ? chunk : 0);
-            if (steady && (q % 8) == 7 && q + 1 < nchunks) {
-                int32_t ndone = 0;
-                if ((e = cudaMemcpyAsync(&ndone, B.active_flag, sizeof ndone, cudaMemcpyDeviceToHost, s)) ||
-                    (e = cudaStreamSynchronize(s)))
-                    return cuda_fail(ctx, e, "run_batch: convergence check");
-                if (ndone >= P.n_steady) break;
-            }
-        }
-        if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
-        ctx->loop_timed = true;
-    }
-    if ((e = launch_finalize(B, P.geom, O, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: finalize launch");
-    if (P.geom.two_step && (e = launch_commit(B, P.geom, s)) != cudaSuccess)
-        return cuda_fail(ctx, e, "run_batch: commit launch");
+    if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+    ctx->loop_timed = true;
     return 0;
 }
 

@@ -26,7 +26,8 @@ struct alignas(16) SampleDev {
     int32_t tiles;      // tiles of this sample
     int32_t tile_base;  // index of the first tile of this sample in the global tile order
     int32_t mask_off;   // word offset of the obstacle bitmask (-1: no obstacle)
-    int32_t mask_words; // 32-bit words per mask row
+    int32_t slot;       // position in the caller's list: the sample's lattice region and the index
+                        // of its state that outlives a run (done, steps_run, sel, cd_prev, streak)
     int32_t side_off;   // offset (in pairs) of the outlet velocity buffer
     double omega;       // 1 / tau
     double u_ref_inv2;  // 2 / (nx ny u_ref^2), 0 when K is disabled
@@ -40,6 +41,8 @@ struct alignas(16) SampleDev {
     int32_t bc_off;         // channel with inout: first node of its boundary buffer (2 x ny nodes)
 };
 static_assert(sizeof(SampleDev) == 128, "SampleDev must stay 128 bytes");
+// 32-bit words per obstacle-mask row.
+__host__ __device__ inline int mask_words(const SampleDev& s) { return (s.nx + 31) >> 5; }
 
 // Initial-field parameters (read by the init kernel) and the obstacle geometry (read by the
 // Bouzidi links, which are rare: only nodes inside bbox look at it).

@@ -638,6 +638,60 @@ def test_two_step_strips_resume_continues_the_run(ens, first, second, split):
         assert rel_l2(got, whole["fields"][:, :-1]) < 1e-6
 
 
+def _grouped_specs():
+    return [W.tgv(64, 61, nu=0.03, amp2=0.0005), _cyl(4, 130, u_mean=0.04), W.tgv(128, 40, nu=0.05),
+            W.tgv(40, 33, nu=0.02), W.tgv(64, 20, nu=0.045), _cyl(5, 77, u_mean=0.035), W.tgv(96, 1, nu=0.06)]
+
+
+def test_grouped_batch_matches_the_single_one_step_batch(ens):
+    """A batch of unlike samples under the auto scheme runs as groups of like samples, one after
+    another in slices of one workspace: channel samples on the one-step kernel, periodic widths 64
+    and 128 on row strips, 40 and 96 on tiles.  Every output row stays the caller's.  Against the
+    same batch run as one one-step batch the channel rows are equal bit for bit (the same kernel,
+    tiles and reduction order) and the periodic rows agree to FP32 round-off."""
+    specs = _grouped_specs()
+    a = _run(ens, specs, "f32", qoi_every=7, series=True)
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_GROUPED
+    b = _run(ens, specs, "f32", qoi_every=7, series=True, scheme="one_step")
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_ONE_STEP
+    for i, sp in enumerate(specs):
+        if sp.kind == W.CHANNEL:
+            assert np.array_equal(a["qoi"][i], b["qoi"][i], equal_nan=True), i
+            assert np.array_equal(a["series"][i], b["series"][i], equal_nan=True), i
+        else:
+            assert a["qoi"][i, U.UQLB_QOI_STEPS] == sp.steps
+            assert np.allclose(a["qoi"][i], b["qoi"][i], rtol=1e-5, atol=1e-5, equal_nan=True), i
+            assert np.allclose(a["series"][i], b["series"][i], rtol=1e-5, atol=0, equal_nan=True), i
+
+
+@pytest.mark.parametrize("scheme", ["one_step", "two_step_strips", "auto"])
+def test_resume_when_the_step_order_changes(ens, scheme):
+    """A resumed run presents each sample with its new step total, which can reorder the table
+    that is sorted by step count (here the first sample runs fewer steps than the second, but both
+    stop together at the split).  Lattice regions and the state that outlives a run are kept by
+    the sample's position in the caller's list, so each sample continues its own state: equal bit
+    for bit to the uninterrupted run at an even split, for one batch, strips and a grouped batch."""
+    if scheme == "auto":
+        specs = [W.tgv(64, 41, nu=0.03), _cyl(4, 60, u_mean=0.04), W.tgv(64, 61, nu=0.05), W.tgv(128, 50, nu=0.04),
+                 _cyl(4, 90, u_mean=0.035)]
+    else:
+        specs = [W.tgv(64, 41, nu=0.03, amp2=0.0004), W.tgv(64, 61, nu=0.05), W.tgv(64, 50, nu=0.04)]
+    uniform = len({(sp.nx, sp.ny) for sp in specs}) == 1
+    split = 30
+    whole = _run(ens, specs, "f32", scheme=scheme)
+    head = [sample_struct(sp) for sp in specs]
+    for h in head:
+        h.steps = min(split, h.steps)
+    ens.run_batch(head, storage="f32", fields=False, scheme=scheme)
+    res = ens.run_batch([sample_struct(sp) for sp in specs], storage="f32", fields=uniform, start_step=split,
+                        scheme=scheme)
+    torch.cuda.synchronize()
+    got = {k: v.double().cpu().numpy() for k, v in res.items()}
+    assert np.array_equal(got["qoi"], whole["qoi"], equal_nan=True)
+    if uniform:
+        assert np.array_equal(got["fields"], whole["fields"])
+
+
 @pytest.mark.parametrize("split", [37, 50])
 def test_two_step_resume_continues_the_run(ens, split):
     """A two-step run stopped after `split` steps and resumed equals the uninterrupted run: bit
@@ -657,6 +711,27 @@ def test_two_step_resume_continues_the_run(ens, split):
         assert np.array_equal(got, whole["fields"][:, :-1])
     else:
         assert rel_l2(got, whole["fields"][:, :-1]) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_two_step_strips_16_bit_nearest_rounding(ens, storage):
+    """Round-to-nearest 16-bit stores on the row strips (pairs of 16-bit values per store where the
+    pair is aligned) round every value as the tile kernel's scalar stores do: the two kernels agree
+    within half the 16-bit budget (their FP32 collisions differ by round-off, which now and then
+    flips a 16-bit rounding), and both stay within the budget of the oracle; a swapped or mis-scaled
+    pair would miss the oracle by orders of magnitude."""
+    specs = _tgv_specs(64, 300)
+    ref = olbm.run([oracle_case(s) for s in specs])
+    run = {}
+    for scheme in ("two_step_strips", "two_step_tiles"):
+        res = ens.run_batch([sample_struct(s) for s in specs], storage=storage, fields_dtype="f32", rounding="nearest",
+                            scheme=scheme)
+        torch.cuda.synchronize()
+        run[scheme] = res["fields"].double().cpu().numpy()
+    assert rel_l2(run["two_step_strips"][:, :-1], run["two_step_tiles"][:, :-1]) < 0.5 * FIELD_TOL[storage]
+    for i, r in enumerate(ref):
+        for scheme, m in run.items():
+            assert rel_l2(m[i, :-1], oracle_row(r)[:-1]) < FIELD_TOL[storage], (scheme, storage)
 
 
 @pytest.mark.parametrize("scheme", ["two_step_tiles", "two_step_strips"])

@@ -457,8 +457,11 @@ def bench_workload(args):
                      "samples_not_converged": int((steps >= w_sc.base.steps).sum()),
                      "unstable_samples": int((status == U.UQLB_ERR_UNSTABLE).sum()),
                      "cd_deterministic": float(cd[-1]), "cd_stats": table})
-    elif args.workload == "uneven":
+    elif args.workload in ("uneven", "uneven_channels"):
+        # uneven_channels: the batch's 64 channel samples alone
         specs = W.uneven_batch()
+        if args.workload == "uneven_channels":
+            specs = [s for s in specs if s.kind == W.CHANNEL]
         smp = [sample_struct(s) for s in specs]
         tuned = ens.autotune(smp, storage=args.storage, trial_steps=8, scheme=args.scheme)
         ms, r = timed(lambda: ens.run_batch(smp, storage=args.storage, fields=False, scheme=args.scheme), args.steps)
@@ -682,7 +685,7 @@ def main():
                     help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")
     ap.add_argument("--workload", default="tgv256_gpc4d",
                     choices=["tgv256_gpc4d", "tgv64_gpc", "tgv512_mc4d", "cylinder", "cylinder_uq_compare", "uneven",
-                             "tgv_paper4d"])
+                             "uneven_channels", "tgv_paper4d"])
     ap.add_argument("--resolutions", default="8,16,32,64,128,256", help="tgv_paper4d: resolutions n")
     ap.add_argument("--t-max", type=float, default=100.0, help="tgv_paper4d: final physical time")
     ap.add_argument("--sampling", default="mc", choices=["mc", "smolyak"],

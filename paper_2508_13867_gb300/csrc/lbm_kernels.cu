@@ -106,12 +106,17 @@ __device__ __forceinline__ int classify(const SampleDev& sp, const uint32_t* mas
     return kInterior;
 }
 
-// Inflow velocity at height yy (walls at 0 and ny) at step t, Sec. 8.1 profile and ramp.
+__device__ __forceinline__ float cospi_c(float a) { return cospif(a); }
+__device__ __forceinline__ double cospi_c(double a) { return cospi(a); }
+
+// Inflow velocity at height yy (walls at 0 and ny) at step t, Sec. 8.1 profile and ramp.  The
+// ramp is evaluated in the compute type: FP64 runs at a small fraction of the FP32 rate on this
+// part, and a warp holding an inlet node would otherwise wait on six FP64 cosines per step.
 template <typename C>
 __device__ __forceinline__ C inflow(const SampleDev& sp, C yy, int t) {
     C ramp = C(1);
     if (sp.ramp_steps > 0.0 && (double)t < sp.ramp_steps)
-        ramp = C(0.5 * (1.0 - cospi((double)t / sp.ramp_steps)));
+        ramp = C(0.5) * (C(1) - cospi_c(C(t) / C(sp.ramp_steps)));
     const C H = C(sp.ny);
     return C(4) * C(sp.uin_max) * ramp * yy * (H - yy) / (H * H);
 }
@@ -559,48 +564,56 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
     const int lt = tile - sp.tile_base;
     const int x0 = (lt % sp.tiles_x) * (kTileCols * NPT) + threadIdx.x;
     const int y = (lt / sp.tiles_x) * TR + threadIdx.y;
-    // A channel tile whose nodes all lie at least one node inside the walls and the end columns and
-    // outside the obstacle's link box has no boundary link: its nodes take the periodic node path
-    // (the same loads, stores and arithmetic, no link classification).  The sample-level QoI logic
+    // A channel node at least one node inside the walls and the end columns and outside the
+    // obstacle's box (every node that is solid or has a solid neighbour lies in it) has no boundary
+    // link: it takes the periodic node path (the same loads, stores and arithmetic, no link
+    // classification).  Boundary nodes outside the box classify their links without the mask.  A
+    // tile of such inner nodes only skips the box and mask set-up.  The sample-level QoI logic
     // (want_f, the tile reduction) stays on the sample's kind.
-    bool nchan = chan;
+    int bb[4] = {0, -1, 0, -1};
+    bool inner_tile = !chan;
     if (chan) {
+        const InitDev& in = p.init[j];
+        for (int q = 0; q < 4; ++q) bb[q] = in.bbox[q];
         const int tx0 = (lt % sp.tiles_x) * (kTileCols * NPT), ty0 = (lt / sp.tiles_x) * TR;
         const int tx1 = tx0 + kTileCols * NPT - 1, ty1 = ty0 + TR - 1;
-        const InitDev& in = p.init[j];
-        const bool inner = tx0 >= 1 && tx1 <= sp.nx - 2 && ty0 >= 1 && ty1 <= sp.ny - 2 &&
-                           (tx1 < in.bbox[0] || tx0 > in.bbox[1] || ty1 < in.bbox[2] || ty0 > in.bbox[3]);
-        nchan = !inner;
+        inner_tile = tx0 >= 1 && tx1 <= sp.nx - 2 && ty0 >= 1 && ty1 <= sp.ny - 2 &&
+                     (tx1 < bb[0] || tx0 > bb[1] || ty1 < bb[2] || ty0 > bb[3]);
     }
-    const uint32_t* mask = (nchan && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
+    const uint32_t* mask = (!inner_tile && sp.mask_off >= 0) ? p.masks + sp.mask_off : nullptr;
     S* base = static_cast<S*>(p.arena) + sp.f_off;
 
-    const InitDev* bz = (nchan && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
+    const InitDev* bz = (!inner_tile && sp.bouzidi && mask != nullptr) ? p.init + j : nullptr;
     C g[NPT][9];
-    bool act[NPT];
+    bool act[NPT], nc[NPT];
     uint32_t lk[NPT];
+    const uint32_t* mk[NPT];
     Nbr nb[NPT];
     Nbr rows;
-    if (!nchan && ODD) {
+    if (ODD) {
         periodic_rows(sp, y, rows);
     } else {
         rows.row[1] = y * sp.pitch;
     }
+    const bool y_inner = y >= 1 && y <= sp.ny - 2;
 #pragma unroll
     for (int k = 0; k < NPT; ++k) {
         const int x = x0 + kTileCols * k;
+        const bool in_box = x >= bb[0] && x <= bb[1] && y >= bb[2] && y <= bb[3];
+        nc[k] = !inner_tile && !(y_inner && x >= 1 && x <= sp.nx - 2 && !in_box);
+        mk[k] = in_box ? mask : nullptr;
         nb[k] = rows;
-        if (!nchan && ODD) periodic_cols(sp, x, nb[k]);
+        if (ODD) periodic_cols(sp, x, nb[k]);
         act[k] = x < sp.nx && y < sp.ny;
-        if (act[k] && mask != nullptr) act[k] = !mask_solid(mask, mask_words(sp), x, y);
-        lk[k] = (act[k] && bz != nullptr) ? obstacle_links(sp, *bz, mask, x, y) : 0u;
-        if (act[k]) node_load<S, ODD>(p, sp, base, mask, x, y, t, nchan, nb[k], bz, lk[k], g[k]);
+        if (act[k] && mk[k] != nullptr) act[k] = !mask_solid(mk[k], mask_words(sp), x, y);
+        lk[k] = (act[k] && bz != nullptr && in_box) ? obstacle_links(sp, *bz, mk[k], x, y) : 0u;
+        if (act[k]) node_load<S, ODD>(p, sp, base, mk[k], x, y, t, nc[k], nb[k], bz, lk[k], g[k]);
     }
     double red[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
         if (act[k])
-            node_update<S, ODD>(p, sp, base, mask, x0 + kTileCols * k, y, t, nchan, want_k, want_f, nb[k], bz, lk[k],
+            node_update<S, ODD>(p, sp, base, mk[k], x0 + kTileCols * k, y, t, nc[k], want_k, want_f, nb[k], bz, lk[k],
                                 g[k], red);
 
     if (want_k || want_f) {

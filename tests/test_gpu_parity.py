@@ -664,6 +664,21 @@ def test_grouped_batch_matches_the_single_one_step_batch(ens):
             assert np.allclose(a["series"][i], b["series"][i], rtol=1e-5, atol=0, equal_nan=True), i
 
 
+def test_grouped_batch_autotune(ens):
+    """The autotuner tunes each group of a grouped batch on its own and reports the largest
+    group's choice; the tuned run then agrees with the untuned one to round-off (only the tile
+    order of the sums can change)."""
+    specs = _grouped_specs()
+    smp = [sample_struct(s) for s in specs]
+    a = _run(ens, specs, "f32", qoi_every=7, series=True)
+    tuned = ens.autotune(smp, storage="f32", trial_steps=4)
+    assert tuned["tile_rows"] > 0 and tuned["nodes_per_thread"] > 0 and len(tuned["tried"]) >= 1
+    b = _run(ens, specs, "f32", qoi_every=7, series=True)
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_GROUPED
+    assert np.allclose(a["qoi"], b["qoi"], rtol=1e-6, atol=1e-5, equal_nan=True)
+    assert np.allclose(a["series"], b["series"], rtol=1e-6, atol=0, equal_nan=True)
+
+
 @pytest.mark.parametrize("scheme", ["one_step", "two_step_strips", "auto"])
 def test_resume_when_the_step_order_changes(ens, scheme):
     """A resumed run presents each sample with its new step total, which can reorder the table

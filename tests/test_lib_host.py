@@ -310,6 +310,37 @@ def test_scheme_selection_and_its_limits():
     assert auto_chan == one_chan
 
 
+def test_grouped_batch_workspace_is_the_sum_of_its_groups():
+    """Under the auto scheme a batch of unlike samples runs as groups (channel samples one-step,
+    periodic samples of each strip width on strips, other periodic samples on tiles), each in its
+    own 256-byte aligned slice of the workspace, in that order.  The total is the sum of the
+    groups' own workspaces, so a resumed run finds every group where the first run left it."""
+    tgv64 = [W.tgv(64, 10, nu=0.03), W.tgv(64, 12, nu=0.04)]
+    tgv128 = [W.tgv(128, 9, nu=0.05)]
+    tgv40 = [W.tgv(40, 11, nu=0.02)]
+    chan = [W.channel(5, steps=10, steady_tol=0.0), W.channel(6, steps=8, steady_tol=0.0)]
+    mixed = [tgv64[0], chan[0], tgv128[0], tgv40[0], chan[1], tgv64[1]]
+
+    def opts(scheme):
+        return U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, scheme)
+
+    def ws(specs, scheme):
+        return U.uqlb_batch_workspace_bytes([sample_struct(x) for x in specs], opts(scheme))
+
+    align = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    parts = [ws(chan, U.UQLB_SCHEME_ONE_STEP), ws(tgv40, U.UQLB_SCHEME_TWO_STEP_TILES),
+             ws(tgv64, U.UQLB_SCHEME_TWO_STEP_STRIPS), ws(tgv128, U.UQLB_SCHEME_TWO_STEP_STRIPS)]
+    assert ws(mixed, U.UQLB_SCHEME_AUTO) == sum(align(b) for b in parts)
+    # one group: no split (the batch plans as before)
+    assert ws(tgv64, U.UQLB_SCHEME_AUTO) == ws(tgv64, U.UQLB_SCHEME_TWO_STEP_STRIPS)
+    assert ws(chan, U.UQLB_SCHEME_AUTO) == ws(chan, U.UQLB_SCHEME_ONE_STEP)
+    # FP64 storage and the explicit schemes keep one batch
+    f64 = U.uqlb_run_opts(U.UQLB_F64, U.UQLB_F64, 0, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, U.UQLB_SCHEME_AUTO)
+    f64_one = U.uqlb_run_opts(U.UQLB_F64, U.UQLB_F64, 0, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, U.UQLB_SCHEME_ONE_STEP)
+    smp = [sample_struct(x) for x in mixed]
+    assert U.uqlb_batch_workspace_bytes(smp, f64) == U.uqlb_batch_workspace_bytes(smp, f64_one)
+
+
 def test_interpolated_inlet_outlet_samples_are_checked():
     graph = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 10, 0, 0, 0, 0, 0, U.UQLB_MODE_GRAPH, 0)
     ok = sample_struct(W.channel(5, steps=10, steady_tol=0.0, inout="interpolated"))

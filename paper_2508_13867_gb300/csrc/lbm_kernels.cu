@@ -2,11 +2,14 @@
 //
 // All samples of an ensemble live in one arena, sample-major, population-plane-major, row-major:
 //   arena[f_off(s) + i * plane(s) + y * pitch(s) + x],  g_i = f_i - w_i.
-// The lattices are updated in place in AA order: an even step reads and writes the nine
-// populations of its own node (writing post-collision g_i to slot opp(i)); an odd step reads
-// the incoming populations from the neighbours' slots and writes its outgoing populations
-// into the neighbours' slots.  Every memory location is read and then written by exactly one
-// thread per step, so no second lattice and no intra-step synchronisation are needed.
+// One-step scheme (step_kernel, persistent_kernel): the lattice is updated in place in AA order:
+// an even step reads and writes the nine populations of its own node (writing post-collision g_i
+// to slot opp(i)); an odd step reads the incoming populations from the neighbours' slots and
+// writes its outgoing populations into the neighbours' slots.  Every memory location is read and
+// then written by exactly one thread per step, so no second lattice and no intra-step
+// synchronisation are needed.  Two-step scheme (periodic batches; strip2_kernel on row strips,
+// step2_kernel on tiles): two lattices in natural layout, each launch collides, streams through
+// shared memory, collides again and pushes into the other lattice (see those kernels).
 // Boundary rules are applied where a population crosses a boundary link:
 //   periodic (TGV, Sec. 8.2): wrap-around neighbours;
 //   wall / obstacle (Sec. 8.1 no-slip): halfway bounce-back;

@@ -290,7 +290,7 @@ def bench_workload(args):
         qe = w.qoi_every
 
         def run():
-            r = ens.run_batch(smp, storage=w.storage, fields_dtype=fd, qoi_every=qe)
+            r = ens.run_batch(smp, storage=w.storage, fields_dtype=fd, qoi_every=qe, mode=args.mode)
             if w.method == "gpc":
                 c = ens.project(r["fields"])
                 m, v = ens.stats(c)
@@ -301,7 +301,7 @@ def bench_workload(args):
         ms, (r, mean, var) = timed(run, args.steps)
         upd = sum(int(q[U.UQLB_QOI_STEPS]) for q in r["qoi"].cpu().numpy()) * smp[0].nx * smp[0].ny
         line.update({"samples": len(smp), "lattice": [smp[0].nx, smp[0].ny], "time_to_stats_s": ms / 1e3,
-                     "value": upd / (ms / 1e3) / 1e6})
+                     "value": upd / (ms / 1e3) / 1e6, "mode": args.mode})
         # further storage formats of the same ensemble (compared with the same oracle subset)
         extra = {}
         for spec in [x for x in args.storages.split(",") if x and x != w.storage]:

@@ -596,6 +596,20 @@ def test_two_step_strips_match_the_tiles_and_the_one_step_scheme(ens):
                 _close(st, ti, what=(n, ny, qe, "tiles"))
 
 
+@pytest.mark.parametrize("storage,nx", [("f32", 1600), ("bf16", 2048), ("f32", 64 * 13)])
+def test_two_step_strips_at_the_widest_rows(ens, storage, nx):
+    """The widest rows the strips take (FP32 1600: ring and staging fill 230 KB of shared memory in
+    one block of 800 threads; 16-bit 2048: 1024 threads) and an odd multiple of 64, on thin
+    lattices, against the one-step scheme."""
+    specs = [replace(W.tgv(nx, 9, nu=0.03, amp2=0.0005), ny=6), replace(W.tgv(nx, 8, nu=0.05), ny=6)]
+    st = _run(ens, specs, storage, qoi_every=1, series=True, scheme="two_step_strips")
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
+    ref = _run(ens, specs, storage, qoi_every=1, series=True, scheme="one_step")
+    tol = 1e-6 if storage == "f32" else 0.5 * FIELD_TOL[storage]
+    assert rel_l2(st["fields"][:, :-1], ref["fields"][:, :-1]) < tol
+    assert np.allclose(st["series"], ref["series"], rtol=10 * tol, atol=0, equal_nan=True)
+
+
 def test_two_step_strips_split_samples_across_blocks(ens):
     """Many samples of mixed heights and step counts in one batch: each block's row range crosses
     samples and each sample's rows are spread over several blocks, whose K partial sums the last

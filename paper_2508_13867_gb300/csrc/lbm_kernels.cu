@@ -1025,8 +1025,9 @@ struct StripTune {
     static constexpr int max_nx = max_nx_raw < 2048 ? max_nx_raw : 2048;
 };
 
-// Asynchronous copy of N bytes (4 or 8) from global to shared memory, completed per thread by
-// cp_async_wait_all().
+// Asynchronous copy of N bytes (4 or 8) from global to shared memory.  Each thread commits one
+// group per staged row and waits with cp_async_wait<D - 1>() until its own oldest group has landed
+// (a thread reads back only what it copied itself, so no barrier is needed for the staging).
 template <int N>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(smem);

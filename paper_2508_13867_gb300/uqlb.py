@@ -353,7 +353,9 @@ def uqlb_last_loop_time(ctx) -> tuple[float, int, int]:
 
 
 def uqlb_last_run_geometry(ctx) -> tuple[int, int, int]:
-    """(scheme, tile_rows, nodes_per_thread) of the last run on this context."""
+    """(scheme, tile_rows, nodes_per_thread) of the last run on this context; scheme is the kernel
+    that ran: UQLB_SCHEME_ONE_STEP, _TWO_STEP_TILES, _TWO_STEP_STRIPS or _GROUPED (a batch of unlike
+    samples run as groups; the tile geometry is then the first group's)."""
     sc, tr, q = c_int32(), c_int32(), c_int32()
     _check(lib().uqlb_last_run_geometry(ctx, ctypes.byref(sc), ctypes.byref(tr), ctypes.byref(q)), ctx)
     return sc.value, tr.value, q.value

@@ -278,6 +278,7 @@ def bench_workload(args):
             w = W.cylinder_gpc(nd=args.nd, storage=args.storage, bc=args.obstacle_bc, inout=args.inout_bc)
         if args.workload == "tgv64_gpc":
             w.storage = args.storage if args.storage != "f32" else "f64"
+        line["storage"] = w.storage
         ens.setup(w)
         smp = ens.ensemble_samples(w)
         specs = [W.SampleSpec(s.kind, s.nx, s.ny, s.steps, s.nu, s.u0, s.amp2, s.amp3, s.u_ref, s.cyl_cx, s.cyl_cy,
@@ -290,7 +291,7 @@ def bench_workload(args):
         qe = w.qoi_every
 
         def run():
-            r = ens.run_batch(smp, storage=w.storage, fields_dtype=fd, qoi_every=qe, mode=args.mode)
+            r = ens.run_batch(smp, storage=w.storage, fields_dtype=fd, qoi_every=qe, mode=args.mode, scheme=args.scheme)
             if w.method == "gpc":
                 c = ens.project(r["fields"])
                 m, v = ens.stats(c)
@@ -301,7 +302,7 @@ def bench_workload(args):
         ms, (r, mean, var) = timed(run, args.steps)
         upd = sum(int(q[U.UQLB_QOI_STEPS]) for q in r["qoi"].cpu().numpy()) * smp[0].nx * smp[0].ny
         line.update({"samples": len(smp), "lattice": [smp[0].nx, smp[0].ny], "time_to_stats_s": ms / 1e3,
-                     "value": upd / (ms / 1e3) / 1e6, "mode": args.mode})
+                     "value": upd / (ms / 1e3) / 1e6, "mode": args.mode, "scheme": args.scheme})
         # further storage formats of the same ensemble (compared with the same oracle subset)
         extra = {}
         for spec in [x for x in args.storages.split(",") if x and x != w.storage]:

@@ -26,7 +26,7 @@ struct GraphEntry {
 };
 
 constexpr int kMaxDim = 8;
-constexpr int kMaxGraphs = 8;
+constexpr int kMaxGraphs = 32;  // a batch run as groups takes one graph per group
 
 }  // namespace
 

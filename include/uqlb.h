@@ -179,9 +179,11 @@ typedef struct {
     int32_t rounding;         /* 16-bit storage: UQLB_ROUND_AUTO (= stochastic), NEAREST or STOCHASTIC */
     int64_t start_step;       /* 0: start from the initial field.  > 0: resume, i.e. continue the state
                                  a previous run left in the same workspace after start_step steps
-                                 (same samples, options and workspace; each sample's `steps` is then
-                                 its new total).  The workspace can be saved and restored between the
-                                 two calls (checkpoint). */
+                                 (same samples in the same order, options and workspace; each sample's
+                                 `steps` is then its new total, which may order the samples differently
+                                 by step count: a sample's state is kept by its position in the list).
+                                 The workspace can be saved and restored between the two calls
+                                 (checkpoint). */
     int32_t mode;             /* UQLB_MODE_GRAPH or UQLB_MODE_PERSISTENT (see below) */
     int32_t scheme;           /* time-stepping scheme, UQLB_SCHEME_* (see below) */
 } uqlb_run_opts;

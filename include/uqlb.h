@@ -200,9 +200,9 @@ typedef struct {
  *     as often.  Two kernels:
  *       TWO_STEP_STRIPS: blocks walk full-width rows, keeping a ring of collided rows in shared
  *         memory (about 1 % of the nodes collided twice).  Every sample of the batch must have
- *         the same width nx, a multiple of 64 in 64..2048 (64..1600 with FP32 storage, whose
- *         rows are also staged in shared memory), with FP32, FP16 or BF16 storage; the tile
- *         geometry then serves only the initial state and the final fields.
+ *         the same width nx, at most 2048 (1600 with FP32 storage, whose rows are also staged in
+ *         shared memory; a block covers the row rounded up to 64 columns), with FP32, FP16 or BF16
+ *         storage; the tile geometry then serves only the initial state and the final fields.
  *       TWO_STEP_TILES: blocks take tiles of the tile geometry with a one-node halo (any size,
  *         FP64 too; the halo is collided twice, 27 % more collisions at tile 8 x 128).
  *     UQLB_SCHEME_TWO_STEP takes strips where the batch allows them, else tiles.
@@ -213,7 +213,7 @@ typedef struct {
  *     samples runs as groups of like samples, one group after another on one stream, each on its
  *     own kernel and its own slice of the workspace (uqlb_batch_workspace_bytes counts them all):
  *     CHANNEL samples on ONE_STEP, periodic samples of each width the strips take on
- *     TWO_STEP_STRIPS, other periodic samples on TWO_STEP_TILES.  Outputs keep the caller's rows.
+ *     TWO_STEP_STRIPS, wider periodic samples on TWO_STEP_TILES.  Outputs keep the caller's rows.
  *     uqlb_last_run_geometry then reports UQLB_SCHEME_GROUPED.
  * A resumed run (start_step > 0) must use the scheme of the run it continues (strips and tiles
  * leave the same lattice layout, so either two-step kernel continues a two-step run). */

@@ -1024,6 +1024,8 @@ struct StripTune {
     static constexpr int max_nx_raw = (232448 - 2048) / (kStripPlanes * 4 + depth * 9 * (int)sizeof(S)) / 64 * 64;
     static constexpr int max_nx = max_nx_raw < 2048 ? max_nx_raw : 2048;
 };
+// Threads of a block for rows of width nx: one per node pair, whole warps; the ring is twice as wide.
+inline int strip_threads(int nx) { return ((nx + 1) / 2 + 31) / 32 * 32; }
 
 // Asynchronous copy of N bytes (4 or 8) from global to shared memory.  Each thread commits one
 // group per staged row and waits with cp_async_wait<D - 1>() until its own oldest group has landed
@@ -1114,7 +1116,9 @@ __device__ __forceinline__ void block_sum_dyn(double (&v)[NV], double* smem) {
     __syncthreads();
 }
 
-template <typename S>
+// GENERIC: rows whose width is not the block's 2 x threads (an odd width, or threads past the row);
+// rows that fill the block take the unmasked instantiation.
+template <typename S, bool GENERIC>
 __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     extern __shared__ __align__(16) unsigned char s3_raw[];
     float* ring = reinterpret_cast<float*>(s3_raw);  // [kStripPlanes][nx]
@@ -1122,8 +1126,9 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     double* s_red = reinterpret_cast<double*>(s3_raw);  // block sums: the ring, once a piece's gathers are done
     __shared__ int s_j, s_rows, s_nact, s_flag;
     const int tid = threadIdx.x, np = blockDim.x;
-    // staging slots of the next phase-A row: this thread's pair of each population, [9][nx]
-    S* stage = reinterpret_cast<S*>(ring + kStripPlanes * 2 * np);
+    const int rw = 2 * np;  // columns of a ring plane: the block's pairs (>= nx)
+    // staging slots of the next phase-A row: this thread's pair of each population, [D][9][rw]
+    S* stage = reinterpret_cast<S*>(ring + kStripPlanes * rw);
     const int t = (int)p.step_counter[0] + p.dt;
     const int t0 = (int)p.step_counter[1];
     if (tid == 0) {
@@ -1138,10 +1143,15 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     const bool want_a = p.qoi_every > 0 && p.series != nullptr && (t % p.qoi_every) == 0;
     const bool want_b0 = p.qoi_every > 0 && p.series != nullptr && ((t + 1) % p.qoi_every) == 0;
     const bool sr = sizeof(S) == 2 && p.stochastic != 0;
-    const int nx = 2 * np;
-    const int x = 2 * tid;                            // node a; node b is x + 1
-    const int xl = x == 0 ? nx - 1 : x - 1;           // column left of a
-    const int xr = x + 2 == nx ? 0 : x + 2;           // column right of b
+    // every sample of a strip batch has the same width: the pair's nodes (a row of odd width ends
+    // on a lone node a, whose partner b is read from the row's padding and dropped) and their
+    // wrapped neighbour columns
+    const int nx = GENERIC ? __ldg(&p.samples[0].nx) : rw;
+    const int x = 2 * tid;  // node a; node b is x + 1
+    const bool va = !GENERIC || x < nx, vb = !GENERIC || x + 1 < nx;
+    const int xl = x == 0 ? nx - 1 : x - 1;                                 // left of a
+    const int xar = GENERIC && x + 1 >= nx ? x + 1 - nx : x + 1;            // right of a
+    const int xbr = x + 2 >= nx ? x + 2 - nx : x + 2;                       // right of b
     for (int r = r0; r < r1;) {
         __syncthreads();  // the previous piece's gathers are done before the ring is reused
         if (tid == 0) {
@@ -1186,17 +1196,17 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                 S* d = dst + (i * plane + row[1 + cy(i)]);
                 float a, b;
                 upk(g[i], a, b);
-                const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? x + 1 : xl);
-                const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xr : x);
+                const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? xar : xl);
+                const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xbr : x);
                 if (sr) {
                     const uint32_t m = 0x2545F491u + 0x6A09E668u * (uint32_t)i;
                     Storage<S>::store_sr(d + ca, a, (ha * m) >> 16);
-                    Storage<S>::store_sr(d + cb, b, (hb * m) >> 16);
-                } else if (cx(i) == 0) {
+                    if (vb) Storage<S>::store_sr(d + cb, b, (hb * m) >> 16);
+                } else if (cx(i) == 0 && vb) {
                     pair_store<S>(d + x, g[i]);
                 } else {
                     Storage<S>::store(d + ca, a);
-                    Storage<S>::store(d + cb, b);
+                    if (vb) Storage<S>::store(d + cb, b);
                 }
             }
         };
@@ -1204,11 +1214,11 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
             float a, b;
             upk(q, a, b);
             acc += (double)a;
-            acc += (double)b;
+            if (vb) acc += (double)b;
         };
         if (!two) {
             // the sample's last step: collide and push row by row
-            for (int y = ya; y < yb; ++y) {
+            for (int y = ya; y < yb && va; ++y) {
                 const S* s0 = src + (y * pitch + x);
                 f2 g[9];
 #pragma unroll
@@ -1228,22 +1238,23 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
             // group per row (empty past the piece), so D - 1 newer groups may stay pending
             constexpr int D = StripTune<S>::depth;
             auto fetch = [&](int q) {
-                if (q <= yb - ya + 1) {
+                if (va && q <= yb - ya + 1) {
                     const S* s0 = src + (row_of(q) * pitch + x);
-                    S* st = stage + (q % (D > 0 ? D : 1)) * 9 * nx + x;
+                    S* st = stage + (q % (D > 0 ? D : 1)) * 9 * rw + x;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) cp_async<2 * sizeof(S)>(st + i * nx, s0 + i * plane);
+                    for (int i = 0; i < 9; ++i) cp_async<2 * sizeof(S)>(st + i * rw, s0 + i * plane);
                 }
                 cp_async_commit();
             };
             (void)fetch;
             auto phase_a = [&](int q, bool count) {
+                if (!va) return;  // past the row: no node (the barriers are outside)
                 f2 g[9];
                 if constexpr (D > 0) {
                     cp_async_wait<D - 1>();
-                    const S* st = stage + (q % D) * 9 * nx + x;
+                    const S* st = stage + (q % D) * 9 * rw + x;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * nx);
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * rw);
                     fetch(q + D);
                 } else {
                     const S* s0 = src + (row_of(q) * pitch + x);
@@ -1266,20 +1277,21 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                 const int q = y - ya + 1;
                 phase_a(q + 1, y + 1 < yb);
                 __syncthreads();
+                if (!va) continue;
                 // phase B: gather row y at step t + 1 (population i from row y - c_iy, column x - c_ix)
-                const float* rp = ring + ((q - 1) & 3) * 3 * nx;          // c_iy = +1: row y - 1
-                const float* rz = ring + (12 + (q % 3) * 3) * nx;         // c_iy =  0: row y
-                const float* rm = ring + (21 + ((q + 1) & 1) * 3) * nx;   // c_iy = -1: row y + 1
+                const float* rp = ring + ((q - 1) & 3) * 3 * rw;          // c_iy = +1: row y - 1
+                const float* rz = ring + (12 + (q % 3) * 3) * rw;         // c_iy =  0: row y
+                const float* rm = ring + (21 + ((q + 1) & 1) * 3) * rw;   // c_iy = -1: row y + 1
                 f2 g[9];
                 g[0] = *reinterpret_cast<const f2*>(rz + x);
-                g[1] = pk(rz[nx + xl], rz[nx + x]);
-                g[3] = pk(rz[2 * nx + x + 1], rz[2 * nx + xr]);
+                g[1] = pk(rz[rw + xl], rz[rw + x]);
+                g[3] = pk(rz[2 * rw + xar], rz[2 * rw + xbr]);
                 g[2] = *reinterpret_cast<const f2*>(rp + x);
-                g[5] = pk(rp[nx + xl], rp[nx + x]);
-                g[6] = pk(rp[2 * nx + x + 1], rp[2 * nx + xr]);
+                g[5] = pk(rp[rw + xl], rp[rw + x]);
+                g[6] = pk(rp[2 * rw + xar], rp[2 * rw + xbr]);
                 g[4] = *reinterpret_cast<const f2*>(rm + x);
-                g[7] = pk(rm[nx + x + 1], rm[nx + xr]);
-                g[8] = pk(rm[2 * nx + xl], rm[2 * nx + x]);
+                g[7] = pk(rm[rw + xar], rm[rw + xbr]);
+                g[8] = pk(rm[2 * rw + xl], rm[2 * rw + x]);
                 f2 qq;
                 collide_packed(g, omega, want_b ? &qq : nullptr);
                 if (want_b) add_usq(red[1], qq);
@@ -1750,8 +1762,9 @@ cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cu
 }  // namespace
 
 bool strip_supported(int storage, int nx) {
-    if (storage == UQLB_F64 || nx < 64 || nx % 64 != 0) return false;
-    return nx <= (storage == UQLB_F32 ? StripTune<float>::max_nx : StripTune<__half>::max_nx);
+    if (storage == UQLB_F64 || nx < 2) return false;
+    const int rw = 2 * strip_threads(nx);  // the ring's width: nx rounded up to 64 columns
+    return rw <= (storage == UQLB_F32 ? StripTune<float>::max_nx : StripTune<__half>::max_nx);
 }
 
 bool geometry_supported2(int storage, int tile_rows, int npt) {
@@ -1817,30 +1830,31 @@ size_t strip_smem(int nx) {
 }
 
 // Shared-memory opt-in (for the widest rows) and resident blocks per SM at width nx (once each).
-template <typename S>
+template <typename S, bool GENERIC>
 int strip_resident(int nx) {
     constexpr int kb = StripTune<S>::carveout_kb;
-    static int cache[StripTune<S>::max_nx / 64 + 1] = {};
+    const int np = strip_threads(nx), rw = 2 * np;
+    static int cache[1024 / 32 + 1] = {};
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(strip2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(strip2_kernel<S, GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)strip_smem<S>(StripTune<S>::max_nx));
         // percent of the 228 KB maximum, rounded down: the driver rounds up to the next supported split
-        if (kb > 0) cudaFuncSetAttribute(strip2_kernel<S>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
+        if (kb > 0) cudaFuncSetAttribute(strip2_kernel<S, GENERIC>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
         attr = true;
     }
-    int& n = cache[nx / 64];
+    int& n = cache[np / 32];
     if (n == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip2_kernel<S>, nx / 2, strip_smem<S>(nx)) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip2_kernel<S, GENERIC>, np, strip_smem<S>(rw)) != cudaSuccess ||
             b < 1)
             b = 1;
         if (kb > 0) {
             // blocks that fit the preferred share (each with its static part and 1 KB reserve), so
             // that the grid stays resident in one wave
             cudaFuncAttributes fa{};
-            cudaFuncGetAttributes(&fa, strip2_kernel<S>);
-            const size_t per = strip_smem<S>(nx) + fa.sharedSizeBytes + 1024;
+            cudaFuncGetAttributes(&fa, strip2_kernel<S, GENERIC>);
+            const size_t per = strip_smem<S>(rw) + fa.sharedSizeBytes + 1024;
             b = std::max(1, std::min(b, (int)((size_t)kb * 1024 / per)));
         }
         n = b;
@@ -1850,11 +1864,17 @@ int strip_resident(int nx) {
 
 template <typename S>
 cudaError_t launch_strip_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
-    if (g.strip_nx < 64 || g.strip_nx > StripTune<S>::max_nx || g.strip_nx % 64 != 0) return cudaErrorInvalidConfiguration;
-    const int64_t resident = (int64_t)strip_resident<S>(g.strip_nx) * sm_count();
+    const int np = strip_threads(g.strip_nx);
+    if (g.strip_nx < 2 || 2 * np > StripTune<S>::max_nx) return cudaErrorInvalidConfiguration;
+    const bool generic = g.strip_nx != 2 * np;
+    const int64_t resident =
+        (int64_t)(generic ? strip_resident<S, true>(g.strip_nx) : strip_resident<S, false>(g.strip_nx)) * sm_count();
     if (prepare_only) return cudaGetLastError();
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
-    strip2_kernel<S><<<grid, g.strip_nx / 2, strip_smem<S>(g.strip_nx), s>>>(p);
+    if (generic)
+        strip2_kernel<S, true><<<grid, np, strip_smem<S>(2 * np), s>>>(p);
+    else
+        strip2_kernel<S, false><<<grid, np, strip_smem<S>(2 * np), s>>>(p);
     return cudaGetLastError();
 }
 

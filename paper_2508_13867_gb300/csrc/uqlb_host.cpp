@@ -380,8 +380,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     bool strip_ok = strip_supported(storage, smp[0].nx);
     for (int64_t s = 1; s < n && strip_ok; ++s) strip_ok = smp[s].nx == smp[0].nx;
     if (scheme == UQLB_SCHEME_TWO_STEP_STRIPS && !strip_ok) {
-        why = "the row-strip kernel needs FP32, FP16 or BF16 storage and one sample width, a multiple of 64 in 64..2048 "
-              "(64..1600 with FP32)";
+        why = "the row-strip kernel needs FP32, FP16 or BF16 storage and one sample width of at most 2048 (1600 with FP32)";
         return UQLB_ERR_ARG;
     }
     const bool strips = two && strip_ok && scheme != UQLB_SCHEME_TWO_STEP_TILES;
@@ -738,7 +737,7 @@ const int kGeomNpt[] = {1, 2, 4};
 // A batch of unlike samples under UQLB_SCHEME_AUTO (graph mode, FP32/FP16/BF16 storage) runs as
 // groups of like samples, one after another, each on its own kernel and its own slice of the
 // workspace: CHANNEL samples on the one-step scheme, periodic samples of each width the row-strip
-// kernel takes on strips, other periodic samples on two-step tiles.  Empty when the batch is one
+// kernel takes on strips, wider periodic samples on two-step tiles.  Empty when the batch is one
 // such group (it then runs as one batch, as before).
 struct Group {
     std::vector<int64_t> idx;  // caller's indices, ascending

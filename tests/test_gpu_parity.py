@@ -552,13 +552,13 @@ def test_two_step_scheme_equals_one_step_scheme(ens, storage):
                  W.tgv(40, 0, nu=0.04)]
         ref = _run(ens, specs, storage, qoi_every=qe, series=True, scheme="one_step")
         for tr, npt in geoms:
-            g = _run(ens, specs, storage, qoi_every=qe, series=True, scheme="two_step", tile_rows=tr, npt=npt)
+            g = _run(ens, specs, storage, qoi_every=qe, series=True, scheme="two_step_tiles", tile_rows=tr, npt=npt)
             assert rel_l2(g["fields"][:, :-1], ref["fields"][:, :-1]) < ftol, (qe, tr, npt)
             assert np.allclose(g["series"], ref["series"], rtol=10 * ftol, atol=0, equal_nan=True), (qe, tr, npt)
             assert np.allclose(g["qoi"], ref["qoi"], rtol=10 * ftol, atol=qatol), (qe, tr, npt)
     small = [W.tgv(5, 9, nu=0.03, amp2=0.0004), W.tgv(5, 12, nu=0.05)]
     a = _run(ens, small, storage, scheme="one_step")
-    b = _run(ens, small, storage, scheme="two_step")
+    b = _run(ens, small, storage, scheme="two_step_tiles")
     assert rel_l2(b["fields"][:, :-1], a["fields"][:, :-1]) < ftol
 
 
@@ -580,10 +580,11 @@ def _close(a, b, tol=1e-6, what=""):
 def test_two_step_strips_match_the_tiles_and_the_one_step_scheme(ens):
     """The row-strip two-step kernel applies the same per-node formulas (every node in packed
     pairs), so FP32 results agree with the one-step scheme and the tile kernel to round-off.
-    Widths 64 and 128; heights equal to the width, ragged (37) and degenerate (2, 3 rows, where the
-    rows above and below a node coincide); step counts that end on a single-step launch (61, 1) or
-    stop at once (0); K at every step and at a stride of 7."""
-    for n in (64, 128):
+    Widths 64 and 128, odd widths (31, 97: the last pair is a lone node) and an even width that
+    leaves threads past the row (40); heights equal to the width, ragged (37) and degenerate (2, 3
+    rows, where the rows above and below a node coincide); step counts that end on a single-step
+    launch (61, 1) or stop at once (0); K at every step and at a stride of 7."""
+    for n in (64, 128, 31, 97, 40):
         for ny in (n, 37, 2, 3):
             specs = _strip_specs(n, ny)
             for qe in (1, 7):
@@ -659,10 +660,11 @@ def _grouped_specs():
 
 def test_grouped_batch_matches_the_single_one_step_batch(ens):
     """A batch of unlike samples under the auto scheme runs as groups of like samples, one after
-    another in slices of one workspace: channel samples on the one-step kernel, periodic widths 64
-    and 128 on row strips, 40 and 96 on tiles.  Every output row stays the caller's.  Against the
-    same batch run as one one-step batch the channel rows are equal bit for bit (the same kernel,
-    tiles and reduction order) and the periodic rows agree to FP32 round-off."""
+    another in slices of one workspace: channel samples on the one-step kernel, each periodic
+    width on the row strips (64 and 128 fill their blocks, 40 and 96 leave threads past the row).
+    Every output row stays the caller's.  Against the same batch run as one one-step batch the
+    channel rows are equal bit for bit (the same kernel, tiles and reduction order) and the
+    periodic rows agree to FP32 round-off."""
     specs = _grouped_specs()
     a = _run(ens, specs, "f32", qoi_every=7, series=True)
     assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_GROUPED
@@ -727,13 +729,13 @@ def test_two_step_resume_continues_the_run(ens, split):
     for bit at an even split, to FP32 round-off at an odd one (the step before the split then
     runs on the single-step path, whose scalar operation order differs from the packed pairs)."""
     specs = _tgv_specs(40, 100) + [W.tgv(40, 71, nu=0.04)]
-    whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="two_step")
+    whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="two_step_tiles")
     first = [sample_struct(s) for s in specs]
     for s in first:
         s.steps = min(split, s.steps)
-    ens.run_batch(first, storage="f32", fields=False, scheme="two_step")
+    ens.run_batch(first, storage="f32", fields=False, scheme="two_step_tiles")
     res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=True, start_step=split,
-                        scheme="two_step")
+                        scheme="two_step_tiles")
     torch.cuda.synchronize()
     got = res["fields"].double().cpu().numpy()[:, :-1]
     if split % 2 == 0:

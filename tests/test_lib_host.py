@@ -287,19 +287,19 @@ def test_scheme_selection_and_its_limits():
         with pytest.raises(U.UqlbError) as e:
             U.uqlb_batch_workspace_bytes(smp, opts)
         assert e.value.status == U.UQLB_ERR_ARG
-    # the row-strip kernel: FP32/FP16/BF16, one width, a multiple of 64 in 64..2048 (FP32: 64..1600)
+    # the row-strip kernel: FP32/FP16/BF16, one width, up to 2048 (FP32: 1600; rows padded to 64 columns)
     strips = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_STRIPS)
     bf16_strips = U.uqlb_run_opts(U.UQLB_BF16, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_STRIPS)
     tiles = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_TILES)
     f64_strips = U.uqlb_run_opts(U.UQLB_F64, U.UQLB_F64, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_TWO_STEP_STRIPS)
-    for smp, opts in (([sample_struct(W.tgv(40, 10))], strips), ([sample_struct(W.tgv(4096, 10))], strips),
-                      ([sample_struct(W.tgv(1664, 10))], strips), ([sample_struct(W.tgv(4096, 10))], bf16_strips),
+    for smp, opts in (([sample_struct(W.tgv(4096, 10))], strips), ([sample_struct(W.tgv(1601, 10))], strips),
+                      ([sample_struct(W.tgv(1664, 10))], strips), ([sample_struct(W.tgv(2049, 10))], bf16_strips),
                       ([sample_struct(W.tgv(64, 10)), sample_struct(W.tgv(128, 10))], strips), (tgv, f64_strips),
                       (chan, strips), (chan, tiles)):
         with pytest.raises(U.UqlbError) as e:
             U.uqlb_batch_workspace_bytes(smp, opts)
         assert e.value.status == U.UQLB_ERR_ARG
-    for n in (64, 128, 1600):
+    for n in (2, 31, 40, 64, 97, 128, 1599, 1600):
         assert U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(n, 10))], strips) >= 2 * 9 * n * n * 4
     assert U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(2048, 10))], bf16_strips) >= 2 * 9 * 2048 * 2048 * 2
     assert U.uqlb_batch_workspace_bytes([sample_struct(W.tgv(40, 10))], tiles) >= 2 * 9 * 40 * 40 * 4
@@ -312,9 +312,10 @@ def test_scheme_selection_and_its_limits():
 
 def test_grouped_batch_workspace_is_the_sum_of_its_groups():
     """Under the auto scheme a batch of unlike samples runs as groups (channel samples one-step,
-    periodic samples of each strip width on strips, other periodic samples on tiles), each in its
-    own 256-byte aligned slice of the workspace, in that order.  The total is the sum of the
-    groups' own workspaces, so a resumed run finds every group where the first run left it."""
+    periodic samples of each strip width on strips, periodic samples too wide for the strips on
+    tiles), each in its own 256-byte aligned slice of the workspace, in that order.  The total is
+    the sum of the groups' own workspaces, so a resumed run finds every group where the first run
+    left it."""
     tgv64 = [W.tgv(64, 10, nu=0.03), W.tgv(64, 12, nu=0.04)]
     tgv128 = [W.tgv(128, 9, nu=0.05)]
     tgv40 = [W.tgv(40, 11, nu=0.02)]
@@ -328,9 +329,14 @@ def test_grouped_batch_workspace_is_the_sum_of_its_groups():
         return U.uqlb_batch_workspace_bytes([sample_struct(x) for x in specs], opts(scheme))
 
     align = lambda b: (b + 255) // 256 * 256  # noqa: E731
-    parts = [ws(chan, U.UQLB_SCHEME_ONE_STEP), ws(tgv40, U.UQLB_SCHEME_TWO_STEP_TILES),
+    parts = [ws(chan, U.UQLB_SCHEME_ONE_STEP), ws(tgv40, U.UQLB_SCHEME_TWO_STEP_STRIPS),
              ws(tgv64, U.UQLB_SCHEME_TWO_STEP_STRIPS), ws(tgv128, U.UQLB_SCHEME_TWO_STEP_STRIPS)]
     assert ws(mixed, U.UQLB_SCHEME_AUTO) == sum(align(b) for b in parts)
+    wide = [W.tgv(1700, 3, nu=0.03)]  # wider than the FP32 strips take: tiles
+    mixed2 = [wide[0], chan[0], tgv64[0]]
+    parts2 = [ws([chan[0]], U.UQLB_SCHEME_ONE_STEP), ws(wide, U.UQLB_SCHEME_TWO_STEP_TILES),
+              ws([tgv64[0]], U.UQLB_SCHEME_TWO_STEP_STRIPS)]
+    assert ws(mixed2, U.UQLB_SCHEME_AUTO) == sum(align(b) for b in parts2)
     # one group: no split (the batch plans as before)
     assert ws(tgv64, U.UQLB_SCHEME_AUTO) == ws(tgv64, U.UQLB_SCHEME_TWO_STEP_STRIPS)
     assert ws(chan, U.UQLB_SCHEME_AUTO) == ws(chan, U.UQLB_SCHEME_ONE_STEP)

@@ -29,6 +29,22 @@ def test_library_exports_every_header_symbol():
     assert set(names) == set(U._SIGNATURES), "binding and header disagree"
 
 
+def test_binding_constants_match_header_enums():
+    """Every UQLB_* enumerator of the header has the same value in the Python binding."""
+    import re
+    from pathlib import Path
+
+    text = Path(__file__).resolve().parents[1].joinpath("include", "uqlb.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = 0
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, value in re.findall(r"(UQLB_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            assert hasattr(U, name), name
+            assert getattr(U, name) == int(value), name
+            found += 1
+    assert found >= 30
+
+
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(U.uqlb_dist) == 24
     assert ctypes.sizeof(U.uqlb_sample) == 144

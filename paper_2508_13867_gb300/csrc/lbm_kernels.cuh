@@ -1,5 +1,8 @@
 // Batched D2Q9 BGK ensemble kernels for sm_103a (arXiv 2508.13867, Sec. 3 and Sec. 7).
 //
+// Included by one translation unit per population storage type (lbm_<type>.cu), which
+// instantiates every kernel for its type and exports the launchers as a StorageOps table.
+//
 // All samples of an ensemble live in one arena, sample-major, population-plane-major, row-major:
 //   arena[f_off(s) + i * plane(s) + y * pitch(s) + x],  g_i = f_i - w_i.
 // One-step scheme (step_kernel, persistent_kernel): the lattice is updated in place in AA order:
@@ -22,54 +25,13 @@
 #include <cmath>
 
 #include "d2q9.cuh"
-#include "uqlb_internal.h"
+#include "lbm_common.cuh"
+
+#pragma once
 
 namespace uqlb {
 
 namespace {
-
-constexpr int kTileCols = 32;
-
-struct KParams {
-    void* arena;
-    void* arena2;          // two-step scheme: second lattice
-    int32_t* sel;          // two-step scheme: lattice holding each sample's state at the run's start
-    const int32_t* row_base;  // row-strip kernel: first row of each sample in table order, [S + 1]
-    const SampleDev* samples;
-    const InitDev* init;
-    const int32_t* steps_sorted;
-    int32_t nsamples;
-    int32_t uniform_tiles;
-    const uint32_t* masks;
-    float* side;
-    double* side_d;
-    double* bcpop;         // interpolated inlet/outlet: next state of the end columns
-    double* partials;
-    int32_t* counters;
-    int32_t* done;
-    int32_t* steps_run;
-    double* cd_prev;
-    int32_t* streak;
-    const int64_t* step_counter;
-    int32_t* n_done;
-    unsigned int* bar_count;
-    unsigned int* bar_gen;
-    int32_t* bar_err;
-    unsigned long long* tickets;
-    int32_t test_withhold;
-    int32_t dt;
-    int32_t max_steps;
-    int32_t stochastic;  // 16-bit storage: stochastic rounding of every population store
-    // outputs
-    void* fields;
-    int64_t fields_ld;
-    int32_t fields_dtype;
-    double* qoi;
-    double* series;
-    double* series_cl;
-    int64_t series_ld;
-    int64_t qoi_every;
-};
 
 // Sample index j (in table order) of a global tile index.
 __device__ __forceinline__ int tile_sample(const KParams& p, int tile, int nact) {
@@ -1331,12 +1293,6 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     }
 }
 
-// After the finalize of a two-step run: the lattice that now holds each sample's state (both
-// arrays are indexed by the sample's slot).
-__global__ void commit_kernel(KParams p) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < p.nsamples; k += gridDim.x * blockDim.x)
-        p.sel[k] ^= launches_of(p.steps_run[k], (int)p.step_counter[1]) & 1;
-}
 
 // ------------------------------------------------------------------------------------------
 // Final fields and per-sample scalars at the last step run.
@@ -1638,71 +1594,6 @@ __global__ void __launch_bounds__(256) inout_kernel(KParams p) {
     }
 }
 
-__global__ void advance_kernel(int64_t* counter, int chunk) { *counter += chunk; }
-
-// Resuming a run: samples that have not stopped take their new step totals.
-__global__ void resume_kernel(KParams p) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p.nsamples; j += gridDim.x * blockDim.x)
-        if (!p.done[p.samples[j].slot]) p.steps_run[p.samples[j].slot] = p.samples[j].steps;
-}
-
-KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs* o, int dt) {
-    KParams p{};
-    p.arena = b.arena;
-    p.arena2 = b.arena2;
-    p.sel = b.sel;
-    p.row_base = b.row_base;
-    p.samples = b.samples;
-    p.init = b.init;
-    p.steps_sorted = b.steps_sorted;
-    p.nsamples = (int32_t)g.nsamples;
-    p.uniform_tiles = g.uniform_tiles;
-    p.masks = b.masks;
-    p.side = b.side;
-    p.side_d = b.side_d;
-    p.bcpop = b.bcpop;
-    p.partials = b.partials;
-    p.counters = b.counters;
-    p.done = b.done;
-    p.steps_run = b.steps_run;
-    p.cd_prev = b.cd_prev;
-    p.streak = b.streak;
-    p.step_counter = b.step_counter;
-    p.n_done = b.active_flag;
-    p.bar_count = b.bar_count;
-    p.bar_gen = b.bar_gen;
-    p.bar_err = b.bar_err;
-    p.tickets = b.tickets;
-    p.test_withhold = g.test_withhold;
-    p.dt = dt;
-    p.max_steps = g.max_steps;
-    p.stochastic = g.stochastic;
-    if (o != nullptr) {
-        p.fields = o->fields;
-        p.fields_ld = o->fields_ld;
-        p.fields_dtype = o->fields_dtype;
-        p.qoi = o->qoi;
-        p.series = o->series;
-        p.series_cl = o->series_cl;
-        p.series_ld = o->series_ld;
-        p.qoi_every = o->qoi_every;
-    }
-    return p;
-}
-
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 148;
-    }
-    return n;
-}
-
-int sm_count_cached() { return sm_count(); }
-
 // Resident blocks per SM of one step-kernel instantiation (queried once).
 template <typename S, bool ODD, bool MIXED, int TR, int NPT>
 int resident_blocks() {
@@ -1759,21 +1650,6 @@ cudaError_t launch_step_s(const KParams& p, const BatchGeometry& g, bool odd, cu
     return odd ? launch_step_geom<S, true, false>(p, g, s) : launch_step_geom<S, false, false>(p, g, s);
 }
 
-}  // namespace
-
-bool strip_supported(int storage, int nx) {
-    if (storage == UQLB_F64 || nx < 2) return false;
-    const int rw = 2 * strip_threads(nx);  // the ring's width: nx rounded up to 64 columns
-    return rw <= (storage == UQLB_F32 ? StripTune<float>::max_nx : StripTune<__half>::max_nx);
-}
-
-bool geometry_supported2(int storage, int tile_rows, int npt) {
-    const int tr = tile_rows, n = npt;
-    if (storage == UQLB_F64) return (tr == 4 && n == 2) || (tr == 8 && (n == 1 || n == 2));
-    return (tr == 4 && n == 4) || ((tr == 8 || tr == 16) && (n == 2 || n == 4));
-}
-
-namespace {
 
 template <typename S, int TR, int NPT>
 constexpr size_t step2_smem() {
@@ -1878,100 +1754,6 @@ cudaError_t launch_strip_s(const KParams& p, const BatchGeometry& g, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t step2_dispatch(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
-    if (g.strips) {
-        switch (g.storage) {
-            case UQLB_F32: return launch_strip_s<float>(p, g, s, prepare_only);
-            case UQLB_F16: return launch_strip_s<__half>(p, g, s, prepare_only);
-            case UQLB_BF16: return launch_strip_s<__nv_bfloat16>(p, g, s, prepare_only);
-            default: return cudaErrorInvalidConfiguration;
-        }
-    }
-    switch (g.storage) {
-        case UQLB_F64: return launch_step2_s<double>(p, g, s, prepare_only);
-        case UQLB_F32: return launch_step2_s<float>(p, g, s, prepare_only);
-        case UQLB_F16: return launch_step2_s<__half>(p, g, s, prepare_only);
-        default: return launch_step2_s<__nv_bfloat16>(p, g, s, prepare_only);
-    }
-}
-
-}  // namespace
-
-cudaError_t prepare_step2(const BatchGeometry& g) {
-    KParams p{};
-    return step2_dispatch(p, g, nullptr, true);
-}
-
-cudaError_t launch_step2(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt, cudaStream_t s) {
-    return step2_dispatch(make_params(b, g, &o, dt), g, s, false);
-}
-
-cudaError_t launch_commit(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
-    KParams p = make_params(b, g, nullptr, 0);
-    const int grid = (int)std::min<int64_t>((g.nsamples + 255) / 256, 1024);
-    commit_kernel<<<grid, 256, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-bool geometry_supported(int storage, bool mixed, int tile_rows, int npt) {
-    const int tr = tile_rows, n = npt;
-    if (mixed) return n == 1 && (tr == 8 || tr == 4);
-    if (storage == UQLB_F64) return (n == 1 && (tr == 8 || tr == 4)) || (n == 2 && tr == 4);
-    return (tr == 2 || tr == 4 || tr == 8) && (n == 1 || n == 2 || n == 4);
-}
-
-cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
-    KParams p = make_params(b, g, nullptr, 0);
-    int64_t grid = g.total_tiles < 65535 * 4 ? g.total_tiles : 65535 * 4;
-    if (grid < 1) grid = 1;
-    switch (g.storage) {
-        case UQLB_F64: init_kernel<double><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
-        case UQLB_F32: init_kernel<float><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
-        case UQLB_F16: init_kernel<__half><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
-        default: init_kernel<__nv_bfloat16><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_inout(const BatchBuffers& b, const BatchGeometry& g, int dt, cudaStream_t s) {
-    KParams p = make_params(b, g, nullptr, dt);
-    const int grid = (int)(g.nsamples < 4096 ? g.nsamples : 4096);
-    switch (g.storage) {
-        case UQLB_F64: inout_kernel<double><<<grid, 256, 0, s>>>(p); break;
-        case UQLB_F32: inout_kernel<float><<<grid, 256, 0, s>>>(p); break;
-        case UQLB_F16: inout_kernel<__half><<<grid, 256, 0, s>>>(p); break;
-        default: inout_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bouzidi_force(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt,
-                                 int base_parity, cudaStream_t s) {
-    (void)base_parity;  // the kernel takes the AA layout from the parity of the step index
-    KParams p = make_params(b, g, &o, dt);
-    const int grid = (int)(g.nsamples < 4096 ? g.nsamples : 4096);
-    switch (g.storage) {
-        case UQLB_F64: bouzidi_force_kernel<double><<<grid, 256, 0, s>>>(p); break;
-        case UQLB_F32: bouzidi_force_kernel<float><<<grid, 256, 0, s>>>(p); break;
-        case UQLB_F16: bouzidi_force_kernel<__half><<<grid, 256, 0, s>>>(p); break;
-        default: bouzidi_force_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(p); break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int dt, int base_parity,
-                        cudaStream_t s) {
-    KParams p = make_params(b, g, &o, dt);
-    const bool odd = ((dt + base_parity) & 1) != 0;
-    switch (g.storage) {
-        case UQLB_F64: return launch_step_s<double>(p, g, odd, s);
-        case UQLB_F32: return launch_step_s<float>(p, g, odd, s);
-        case UQLB_F16: return launch_step_s<__half>(p, g, odd, s);
-        default: return launch_step_s<__nv_bfloat16>(p, g, odd, s);
-    }
-}
-
-namespace {
 
 template <typename S, bool MIXED, int TR, int NPT>
 cudaError_t launch_persistent_geom(const KParams& p, int chunk, cudaStream_t s) {
@@ -2017,58 +1799,67 @@ cudaError_t launch_persistent_s(const KParams& p, const BatchGeometry& g, int ch
 }
 #undef UQLB_PGEOM
 
-}  // namespace
 
-cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, int chunk,
-                              cudaStream_t s) {
-    KParams p = make_params(b, g, &o, 0);
-    const bool mixed = g.any_channel != 0;
-    switch (g.storage) {
-        case UQLB_F64: return mixed ? launch_persistent_s<double, true>(p, g, chunk, s) : launch_persistent_s<double, false>(p, g, chunk, s);
-        case UQLB_F32: return mixed ? launch_persistent_s<float, true>(p, g, chunk, s) : launch_persistent_s<float, false>(p, g, chunk, s);
-        case UQLB_F16: return mixed ? launch_persistent_s<__half, true>(p, g, chunk, s) : launch_persistent_s<__half, false>(p, g, chunk, s);
-        default:
-            return mixed ? launch_persistent_s<__nv_bfloat16, true>(p, g, chunk, s)
-                         : launch_persistent_s<__nv_bfloat16, false>(p, g, chunk, s);
-    }
-}
-
-cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s) {
-    KParams p = make_params(b, g, nullptr, 0);
-    resume_kernel<<<(int)std::min<int64_t>((g.nsamples + 255) / 256, 1024), 256, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s) {
-    advance_kernel<<<1, 1, 0, s>>>(b.step_counter, chunk);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
-                            cudaStream_t s) {
-    KParams p = make_params(b, g, &o, 0);
+// Launchers of the kernels that the dispatcher does not shape itself (grid from the tile count).
+inline int64_t tile_grid(const BatchGeometry& g) {
     int64_t grid = g.total_tiles < 65535 * 4 ? g.total_tiles : 65535 * 4;
-    if (grid < 1) grid = 1;
-    const bool ch = g.any_channel != 0;
-    switch (g.storage) {
-        case UQLB_F64:
-            ch ? finalize_kernel<double, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
-               : finalize_kernel<double, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
-            break;
-        case UQLB_F32:
-            ch ? finalize_kernel<float, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
-               : finalize_kernel<float, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
-            break;
-        case UQLB_F16:
-            ch ? finalize_kernel<__half, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
-               : finalize_kernel<__half, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
-            break;
-        default:
-            ch ? finalize_kernel<__nv_bfloat16, true><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt)
-               : finalize_kernel<__nv_bfloat16, false><<<(int)grid, 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
-            break;
-    }
+    return grid < 1 ? 1 : grid;
+}
+
+template <typename S>
+cudaError_t launch_init_s(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    init_kernel<S><<<(int)tile_grid(g), 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
     return cudaGetLastError();
 }
+
+template <typename S>
+cudaError_t launch_finalize_s(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    if (g.any_channel)
+        finalize_kernel<S, true><<<(int)tile_grid(g), 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
+    else
+        finalize_kernel<S, false><<<(int)tile_grid(g), 256, 0, s>>>(p, g.total_tiles, g.tile_rows, 32 * g.npt);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_inout_s(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    inout_kernel<S><<<(int)(g.nsamples < 4096 ? g.nsamples : 4096), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_bouzidi_force_s(const KParams& p, const BatchGeometry& g, cudaStream_t s) {
+    bouzidi_force_kernel<S><<<(int)(g.nsamples < 4096 ? g.nsamples : 4096), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_two_step_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    if (g.strips) {
+        if constexpr (sizeof(S) == 8) return cudaErrorInvalidConfiguration;
+        else return launch_strip_s<S>(p, g, s, prepare_only);
+    }
+    return launch_step2_s<S>(p, g, s, prepare_only);
+}
+
+template <typename S>
+cudaError_t launch_persistent_any(const KParams& p, const BatchGeometry& g, int chunk, cudaStream_t s) {
+    return g.any_channel ? launch_persistent_s<S, true>(p, g, chunk, s) : launch_persistent_s<S, false>(p, g, chunk, s);
+}
+
+template <typename S>
+StorageOps make_storage_ops() {
+    StorageOps o;
+    o.init = launch_init_s<S>;
+    o.step = launch_step_s<S>;
+    o.two_step = launch_two_step_s<S>;
+    o.persistent = launch_persistent_any<S>;
+    o.finalize = launch_finalize_s<S>;
+    o.inout = launch_inout_s<S>;
+    o.bouzidi_force = launch_bouzidi_force_s<S>;
+    return o;
+}
+
+}  // namespace
 
 }  // namespace uqlb

@@ -114,7 +114,7 @@ struct RunOutputs {
     int64_t qoi_every;
 };
 
-// Launchers (lbm_kernels.cu).
+// Launchers (lbm_launch.cu; kernels in lbm_kernels.cuh, one translation unit per storage type).
 cudaError_t launch_init(const BatchBuffers& b, const BatchGeometry& g, cudaStream_t s);
 // Step dt of a chunk whose base step has parity base_parity (the AA parity of the launch).
 cudaError_t launch_step(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,

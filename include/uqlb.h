@@ -44,7 +44,7 @@ typedef enum {
     UQLB_ERR_OOM = -2,      /* workspace too small or host allocation failed */
     UQLB_ERR_CUDA = -3,     /* a CUDA runtime call failed */
     UQLB_ERR_TIMEOUT = -4,  /* a bounded device wait gave up */
-    UQLB_ERR_UNSTABLE = -5, /* a sample produced non-finite or non-positive density */
+    UQLB_ERR_UNSTABLE = -5, /* a sample produced non-finite or non-positive density (or left the UQLB_FX16 range) */
     UQLB_ERR_STATE = -6     /* call out of order (e.g. project before init_gpc) */
 } uqlb_status;
 
@@ -72,8 +72,15 @@ enum {
     UQLB_PARAM_PERT10 = 6,
     UQLB_PARAM_PERT11 = 7
 };
-/* Number formats: population storage, field outputs, projection inputs. */
-enum { UQLB_F64 = 0, UQLB_F32 = 1, UQLB_F16 = 2, UQLB_BF16 = 3 };
+/* Number formats: population storage, field outputs, projection inputs.  UQLB_FX16 is a population
+ * storage format only: 16-bit fixed point, g_i = q d_c with q a signed 16-bit integer and one quantum
+ * d_c per sample and velocity class c (rest, axis, diagonal), set from a bound on |g_i| over the run
+ * (uqlb_fx16_quanta).  It spends all 15 magnitude bits on the range g actually takes, where FP16
+ * keeps 11 significant bits and BF16 8, so its rounding error on the velocity field is several
+ * times below FP16's and tens of times below BF16's at the same 2 bytes per population.  Stores
+ * saturate at the ends of the range; a sample holding a saturated value at the end of its run gets
+ * UQLB_ERR_UNSTABLE in its QoI status. */
+enum { UQLB_F64 = 0, UQLB_F32 = 1, UQLB_F16 = 2, UQLB_BF16 = 3, UQLB_FX16 = 4 };
 /* Rounding of 16-bit population stores.  Stochastic rounding (seeded by sample, node and step,
  * so runs reproduce) keeps the rounding error unbiased; nearest-even stagnates on fine lattices
  * where g changes by less than one unit in the last place per step.  FP32/FP64 ignore it. */
@@ -170,13 +177,13 @@ typedef struct {
  * BF16 (4,4), (8,2), (8,4), (16,2), (16,4); FP64 (4,2), (8,1), (8,2).  Both 0: the geometry the
  * context's autotuner picked for this batch shape (uqlb_autotune), else the default. */
 typedef struct {
-    int32_t storage;          /* population storage: UQLB_F64, F32, F16 or BF16 (stored as f - w) */
+    int32_t storage;          /* population storage: UQLB_F64, F32, F16, BF16 or FX16 (stored as f - w) */
     int32_t fields_dtype;     /* dtype of the field output M: UQLB_F64 or UQLB_F32 */
     int64_t qoi_every;        /* stride of the in-kernel QoI series (0: none) */
     int32_t chunk_steps;      /* steps per captured CUDA graph (even, 2..1024; 0: default 64) */
     int32_t tile_rows;        /* rows per tile (see above; 0: tuned or default) */
     int32_t nodes_per_thread; /* nodes per thread along x (see above; 0: tuned or default) */
-    int32_t rounding;         /* 16-bit storage: UQLB_ROUND_AUTO (= stochastic), NEAREST or STOCHASTIC */
+    int32_t rounding;         /* 16-bit storage (F16, BF16, FX16): UQLB_ROUND_AUTO (= stochastic), NEAREST or STOCHASTIC */
     int64_t start_step;       /* 0: start from the initial field.  > 0: resume, i.e. continue the state
                                  a previous run left in the same workspace after start_step steps
                                  (same samples in the same order, options and workspace; each sample's
@@ -261,6 +268,15 @@ int uqlb_multi_indices(int dim, int order, int basis, int32_t* alpha);
  * tau = 3 nu dt / dx^2 + 1/2, lattice velocity of a unit physical velocity dt / dx.  n >= 2. */
 int uqlb_unit_converter(int n, double ma, double re, double* dx, double* dt, double* tau,
                         double* u_lattice);
+
+/* Quanta of the UQLB_FX16 storage for one sample, quanta[3] = (rest, axis, diagonal): margin x B_c / 32767
+ * with B_c a bound on |g_i| of class c from the equilibrium of the sample's largest speed U and density
+ * deviation R (the shifted D2Q9 equilibrium of Sec. 3):  B_0 = 4/9 (R + (1 + R) 1.5 U^2),
+ * B_axis = 1/9 (R + (1 + R)(3 U + 6 U^2)), B_diag = 1/36 (the same).  TGV: U = |u0| + |amp2| + |amp3|,
+ * R = 1.5 U^2, margin 1.5; TGV_PERTURBED: U = |u0| + (sum |pert|) / 4, R = 1.5 U^2, margin 1.5;
+ * CHANNEL: U = 4 |u0|, R = 6 |u0|, margin 1 (peak speeds and start-up pressure waves of the channel).
+ * Each quantum is rounded to FP32 (the device keeps it in FP32). */
+int uqlb_fx16_quanta(const uqlb_sample* s, double* quanta);
 
 /* Staircase obstacle mask of a CHANNEL sample, [ny x nx] bytes (1 = solid). */
 int uqlb_obstacle_mask(const uqlb_sample* s, uint8_t* mask);

@@ -18,7 +18,7 @@ LIB = os.path.join(OUT_DIR, "libuqlb.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu", "lbm_bf16.cu", "lbm_launch.cu", "plain_f64.cu",
+CU_SOURCES = ["lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu", "lbm_bf16.cu", "lbm_fx16.cu", "lbm_launch.cu", "plain_f64.cu",
               "project_kernels.cu", "w1_kernels.cu"]
 CPP_SOURCES = ["uqlb_host.cpp"]
 

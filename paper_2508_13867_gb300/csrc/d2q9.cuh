@@ -39,56 +39,111 @@ static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp dia
 static_assert(cx(6) == -1 && cy(6) == 1 && cx(8) == 1 && cy(8) == -1, "diagonal order");
 
 // Storage formats of the shifted populations and the arithmetic type used with each.
-// store() rounds to nearest even; store_sr() rounds stochastically with 32 random bits r: the
-// magnitude is rounded up with probability equal to the discarded fraction, so rounding errors
-// have zero mean.  This matters for 16-bit storage on fine lattices, where the change of g over
-// one step is far below one unit in the last place and nearest rounding keeps discarding it
-// with a consistent sign (stagnation).
+// load(p, q, i) / store(p, v, q, i) convert population i (q: the sample's quanta, used by the
+// fixed-point format only); store() rounds to nearest even; store_sr() rounds stochastically with
+// 16 random bits r: the magnitude is rounded up with probability equal to the discarded fraction,
+// so rounding errors have zero mean.  This matters for 16-bit storage on fine lattices, where the
+// change of g over one step is far below one unit in the last place and nearest rounding keeps
+// discarding it with a consistent sign (stagnation).  at_limit(p) tells whether a stored value sits
+// at the end of the format's range (the fixed-point format saturates there).
+
+// Velocity class of population i: 0 rest, 1 axis, 2 diagonal (opposite directions share it).
+__host__ __device__ constexpr int qclass(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+
+// Quanta of the 16-bit fixed-point format for one sample: g_i = q * d[qclass(i)] with q a signed
+// 16-bit integer, inv = 1 / d.  Formats that need none take NoQuanta.
+struct Quanta {
+    float d[3];
+    float inv[3];
+};
+struct NoQuanta {};
+
 template <typename S>
 struct Storage;
 template <>
 struct Storage<double> {
     using C = double;
-    static __device__ __forceinline__ double load(const double* p) { return *p; }
-    static __device__ __forceinline__ void store(double* p, double v) { *p = v; }
-    static __device__ __forceinline__ void store_sr(double* p, double v, uint32_t) { *p = v; }
+    using Q = NoQuanta;
+    static __device__ __forceinline__ double load(const double* p, const Q&, int) { return *p; }
+    static __device__ __forceinline__ void store(double* p, double v, const Q&, int) { *p = v; }
+    static __device__ __forceinline__ void store_sr(double* p, double v, uint32_t, const Q&, int) { *p = v; }
+    static __device__ __forceinline__ bool at_limit(const double*) { return false; }
 };
 template <>
 struct Storage<float> {
     using C = float;
-    static __device__ __forceinline__ float load(const float* p) { return *p; }
-    static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
-    static __device__ __forceinline__ void store_sr(float* p, float v, uint32_t) { *p = v; }
+    using Q = NoQuanta;
+    static __device__ __forceinline__ float load(const float* p, const Q&, int) { return *p; }
+    static __device__ __forceinline__ void store(float* p, float v, const Q&, int) { *p = v; }
+    static __device__ __forceinline__ void store_sr(float* p, float v, uint32_t, const Q&, int) { *p = v; }
+    static __device__ __forceinline__ bool at_limit(const float*) { return false; }
 };
 // FP16 holds g scaled by 2^12 (exact): |g| <= ~0.05 then stays far below the FP16 maximum and
 // values down to 1.5e-8 stay in the normal range, where the rounding step is relative.
 template <>
 struct Storage<__half> {
     using C = float;
-    static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p) * 0x1p-12f; }
-    static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v * 0x1p12f); }
+    using Q = NoQuanta;
+    static __device__ __forceinline__ float load(const __half* p, const Q&, int) { return __half2float(*p) * 0x1p-12f; }
+    static __device__ __forceinline__ void store(__half* p, float v, const Q&, int) { *p = __float2half_rn(v * 0x1p12f); }
     // 13 random bits below the last FP16 mantissa place of the FP32 pattern, then truncation
-    static __device__ __forceinline__ void store_sr(__half* p, float v, uint32_t r) {
+    static __device__ __forceinline__ void store_sr(__half* p, float v, uint32_t r, const Q&, int) {
         *p = __float2half_rz(__uint_as_float(__float_as_uint(v * 0x1p12f) + (r & 0x1FFFu)));
     }
+    static __device__ __forceinline__ bool at_limit(const __half*) { return false; }
 };
 template <>
 struct Storage<__nv_bfloat16> {
     using C = float;
-    static __device__ __forceinline__ float load(const __nv_bfloat16* p) {
-        return __bfloat162float(*p);
-    }
-    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) {
-        *p = __float2bfloat16_rn(v);
-    }
+    using Q = NoQuanta;
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, const Q&, int) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, const Q&, int) { *p = __float2bfloat16_rn(v); }
     // 16 random bits added below the BF16 mantissa of the FP32 pattern, then truncation
-    static __device__ __forceinline__ void store_sr(__nv_bfloat16* p, float v, uint32_t r) {
+    static __device__ __forceinline__ void store_sr(__nv_bfloat16* p, float v, uint32_t r, const Q&, int) {
         *p = __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + (r & 0xFFFFu)) >> 16));
+    }
+    static __device__ __forceinline__ bool at_limit(const __nv_bfloat16*) { return false; }
+};
+
+// 16-bit fixed point: g_i = q d_c, q a signed 16-bit integer, with one quantum d_c per sample and
+// velocity class c (rest, axis, diagonal) sized by the host from a bound on |g_i| over the run.
+// Every stored value carries the same absolute resolution d_c: the error of the velocity field is
+// an absolute error summed over populations, so no bits go to an exponent that |g| never uses
+// (FP16 keeps 11 significant bits, BF16 8; here 15 bits span the class's range).  Stores saturate
+// at -32768 and 32767; a sample holding a saturated value at its end is reported unstable.
+template <>
+struct Storage<int16_t> {
+    using C = float;
+    using Q = Quanta;
+    static __device__ __forceinline__ float load(const int16_t* p, const Q& q, int i) {
+        return (float)*p * q.d[qclass(i)];
+    }
+    static __device__ __forceinline__ int16_t round_nearest(float v, const Q& q, int i) {
+        unsigned short r;
+        asm("cvt.rni.sat.s16.f32 %0, %1;" : "=h"(r) : "f"(v * q.inv[qclass(i)]));
+        return (int16_t)r;
+    }
+    // floor(v / d + u) with u uniform in [0, 1): the 16 random bits form 1 + u in FP32
+    static __device__ __forceinline__ int16_t round_stochastic(float v, uint32_t r, const Q& q, int i) {
+        const float u = __uint_as_float(0x3F800000u | ((r & 0xFFFFu) << 7)) - 1.0f;
+        unsigned short o;
+        asm("cvt.rmi.sat.s16.f32 %0, %1;" : "=h"(o) : "f"(fmaf(v, q.inv[qclass(i)], u)));
+        return (int16_t)o;
+    }
+    static __device__ __forceinline__ void store(int16_t* p, float v, const Q& q, int i) { *p = round_nearest(v, q, i); }
+    static __device__ __forceinline__ void store_sr(int16_t* p, float v, uint32_t r, const Q& q, int i) {
+        *p = round_stochastic(v, r, q, i);
+    }
+    static __device__ __forceinline__ bool at_limit(const int16_t* p) {
+        const int16_t v = *p;
+        return v == (int16_t)-32768 || v == (int16_t)32767;
     }
 };
 
-// Counter-based 32-bit mixer (xor-shift-multiply finaliser) for the stochastic-rounding bits of
-// one population store: a function of (sample, in-sample offset, step) only, so runs reproduce.
+// Counter-based 32-bit mixer for the stochastic-rounding bits of one population store: a function
+// of (sample, in-sample offset, step) only, so runs reproduce.  It is the xor-shift-multiply
+// integer hash "lowbias32" (shift 16, multiply, shift 15, multiply, shift 16) with the constants
+// published by C. Wellons's hash-prospector search.
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;

@@ -67,6 +67,7 @@ const StorageOps& storage_ops_f64();
 const StorageOps& storage_ops_f32();
 const StorageOps& storage_ops_f16();
 const StorageOps& storage_ops_bf16();
+const StorageOps& storage_ops_fx16();
 
 // Streaming multiprocessors of the current device (queried once).
 inline int sm_count() {

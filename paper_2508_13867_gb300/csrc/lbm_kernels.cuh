@@ -23,6 +23,7 @@
 // sums (FP64) are combined in a fixed order by the last tile of each sample to finish.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "d2q9.cuh"
 #include "lbm_common.cuh"
@@ -45,6 +46,21 @@ __device__ __forceinline__ int tile_sample(const KParams& p, int tile, int nact)
             hi = mid - 1;
     }
     return lo;
+}
+
+// Quanta of sample j (table order) for the fixed-point storage; an empty value for other formats.
+template <typename S>
+__device__ __forceinline__ typename Storage<S>::Q quanta_of(const KParams& p, int j) {
+    typename Storage<S>::Q q{};
+    if constexpr (std::is_same<typename Storage<S>::Q, Quanta>::value) {
+        const InitDev& in = p.init[j];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q.d[c] = __ldg(&in.quanta[c]);
+            q.inv[c] = __ldg(&in.inv_quanta[c]);
+        }
+    }
+    return q;
 }
 
 // Number of samples with steps > t (the table is ordered by descending steps).
@@ -147,7 +163,7 @@ __device__ __forceinline__ C bouzidi_local(const InitDev& in, int x, int y, int 
 template <typename S>
 __device__ __forceinline__ typename Storage<S>::C read_incoming(
     const S* base, const SampleDev& sp, const uint32_t* mask, int x, int y, int i, int tp,
-    typename Storage<S>::C ubx, typename Storage<S>::C uby, bool chan) {
+    typename Storage<S>::C ubx, typename Storage<S>::C uby, bool chan, const typename Storage<S>::Q& qz) {
     using C = typename Storage<S>::C;
     const int64_t plane = sp.plane;
     const int pitch = sp.pitch;
@@ -155,12 +171,12 @@ __device__ __forceinline__ typename Storage<S>::C read_incoming(
     if (!chan) {
         sx = sx < 0 ? sx + sp.nx : (sx >= sp.nx ? sx - sp.nx : sx);
         sy = sy < 0 ? sy + sp.ny : (sy >= sp.ny ? sy - sp.ny : sy);
-        return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx);
+        return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx, qz, i);
     } else {
         const int cls = classify(sp, mask, sx, sy);
         const int64_t own = (int64_t)y * pitch + x;
-        if (cls == kInterior) return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx);
-        const C mine = Storage<S>::load(base + i * plane + own);  // g_opp(i)*(x, tp)
+        if (cls == kInterior) return Storage<S>::load(base + opp(i) * plane + (int64_t)sy * pitch + sx, qz, i);
+        const C mine = Storage<S>::load(base + i * plane + own, qz, i);  // g_opp(i)*(x, tp)
         if (cls == kWall || cls == kSolid) return mine;
         if (cls == kInlet) {
             const C yy = C(y) + C(0.5) - C(0.5) * C(cy(i));
@@ -248,6 +264,7 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
     for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int j = tile_sample(p, (int)tile, p.nsamples);
         const SampleDev& sp = p.samples[j];
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         const int lt = (int)tile - sp.tile_base;
         const int y0 = (lt / sp.tiles_x) * tile_rows;
         if (tile == sp.tile_base && threadIdx.x == 0) {
@@ -301,7 +318,7 @@ __global__ void __launch_bounds__(256) init_kernel(KParams p, int64_t total_tile
                 const C cu = C(cx(i)) * ux + C(cy(i)) * uy;
                 const C w = wgt<C>(i);
                 const C g = w * drho + w * rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * usq);
-                Storage<S>::store(base + i * sp.plane, g);
+                Storage<S>::store(base + i * sp.plane, g, qz, i);
             }
         }
     }
@@ -336,7 +353,8 @@ template <typename S, bool ODD>
 __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp, const S* base,
                                           const uint32_t* mask, int x, int y, int t, bool chan,
                                           const Nbr& nb, const InitDev* bz, uint32_t links,
-                                          typename Storage<S>::C (&g)[9], bool end_columns = true) {
+                                          typename Storage<S>::C (&g)[9], const typename Storage<S>::Q& qz,
+                                          bool end_columns = true) {
     using C = typename Storage<S>::C;
     const int plane = (int)sp.plane;
     if (chan && end_columns && sp.inout && t > 0 && (x == 0 || x == sp.nx - 1)) {
@@ -349,12 +367,12 @@ __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp,
     if (!ODD) {
         const int own = nb.row[1] + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + (i * plane + own));
+        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + (i * plane + own), qz, i);
         if (chan && links) bouzidi_complete(*bz, x, y, links, g);
     } else if (!chan) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            g[i] = Storage<S>::load(base + (opp(i) * plane + nb.row[1 - cy(i)] + nb.col[1 - cx(i)]));
+            g[i] = Storage<S>::load(base + (opp(i) * plane + nb.row[1 - cy(i)] + nb.col[1 - cx(i)]), qz, i);
     } else {
         C ubx = C(0), uby = C(0);
         if (chan && x == sp.nx - 1) {
@@ -366,9 +384,9 @@ __device__ __forceinline__ void node_load(const KParams& p, const SampleDev& sp,
                 uby = (C)p.side[2 * (sp.side_off + y) + 1];
             }
         }
-        g[0] = Storage<S>::load(base + (nb.row[1] + x));
+        g[0] = Storage<S>::load(base + (nb.row[1] + x), qz, 0);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan);
+        for (int i = 1; i < 9; ++i) g[i] = read_incoming<S>(base, sp, mask, x, y, i, t - 1, ubx, uby, chan, qz);
         if (links) bouzidi_complete(*bz, x, y, links, g);
     }
 }
@@ -378,7 +396,8 @@ template <typename S, bool ODD>
 __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& sp, S* base, const uint32_t* mask,
                                             int x, int y, int t, bool chan, bool want_k, bool want_f,
                                             const Nbr& nb, const InitDev* bz, uint32_t links,
-                                            typename Storage<S>::C (&g)[9], double (&red)[3]) {
+                                            typename Storage<S>::C (&g)[9], double (&red)[3],
+                                            const typename Storage<S>::Q& qz) {
     using C = typename Storage<S>::C;
     const int own = nb.row[1] + x;
     const int plane = (int)sp.plane;
@@ -390,9 +409,9 @@ __device__ __forceinline__ void node_update(const KParams& p, const SampleDev& s
                           : 0u;
     auto put = [&](S* ptr, C v, int i) {
         if (sr)
-            Storage<S>::store_sr(ptr, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16);
+            Storage<S>::store_sr(ptr, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
         else
-            Storage<S>::store(ptr, v);
+            Storage<S>::store(ptr, v, qz, i);
     };
     C drho, jx, jy, ux, uy;
     moments(g, drho, jx, jy, ux, uy);
@@ -520,6 +539,7 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
     const int j = sh.j;
     const SampleDev& sp = sh.sp;
     const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
+    const typename Storage<S>::Q qz = quanta_of<S>(p, j);
     if (chan && p.done[sp.slot]) {
         __syncthreads();
         return;
@@ -572,14 +592,14 @@ __device__ __forceinline__ void process_tile(const KParams& p, int t, int tile, 
         act[k] = x < sp.nx && y < sp.ny;
         if (act[k] && mk[k] != nullptr) act[k] = !mask_solid(mk[k], mask_words(sp), x, y);
         lk[k] = (act[k] && bz != nullptr && in_box) ? obstacle_links(sp, *bz, mk[k], x, y) : 0u;
-        if (act[k]) node_load<S, ODD>(p, sp, base, mk[k], x, y, t, nc[k], nb[k], bz, lk[k], g[k]);
+        if (act[k]) node_load<S, ODD>(p, sp, base, mk[k], x, y, t, nc[k], nb[k], bz, lk[k], g[k], qz);
     }
     double red[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < NPT; ++k)
         if (act[k])
             node_update<S, ODD>(p, sp, base, mk[k], x0 + kTileCols * k, y, t, nc[k], want_k, want_f, nb[k], bz, lk[k],
-                                g[k], red);
+                                g[k], red, qz);
 
     if (want_k || want_f) {
         double tot[3];
@@ -776,6 +796,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
         __syncthreads();
         const int j = sh.j;
         const SampleDev& sp = sh.sp;
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         const bool two = t + 1 < sp.steps;
         const bool want_b = two && want_b0;
         const int lt = tile - sp.tile_base;
@@ -800,9 +821,9 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
             for (int i = 0; i < 9; ++i) {
                 S* ptr = dst + (i * plane + row[1 + cy(i)] + col[1 + cx(i)]);
                 if (sr)
-                    Storage<S>::store_sr(ptr, g[i], (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16);
+                    Storage<S>::store_sr(ptr, g[i], (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
                 else
-                    Storage<S>::store(ptr, g[i]);
+                    Storage<S>::store(ptr, g[i], qz, i);
             }
         };
         if (!two) {
@@ -813,7 +834,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
                 const int x = x0 + lane + kTileCols * k;
                 if (lane + kTileCols * k < wa && ty < ha) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[k][i] = Storage<S>::load(src + (i * plane + y * pitch + x));
+                    for (int i = 0; i < 9; ++i) g[k][i] = Storage<S>::load(src + (i * plane + y * pitch + x), qz, i);
                 }
             }
 #pragma unroll
@@ -850,7 +871,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
                         gy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
                         const S* q = src + (gy * pitch + gx);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) g[m][i] = Storage<S>::load(q + i * plane);
+                        for (int i = 0; i < 9; ++i) g[m][i] = Storage<S>::load(q + i * plane, qz, i);
                     }
                 }
                 if constexpr (UQLB_STEP2_PACKED && sizeof(C) == 4 && MB % 2 == 0) {
@@ -1016,41 +1037,55 @@ __device__ __forceinline__ int strip_plane(int i, int q) {
     }
 }
 
-// Two adjacent populations (an even column and the next) as one packed pair.
+// Two adjacent populations i (an even column and the next) as one packed pair.
 template <typename S>
-__device__ __forceinline__ f2 pair_load(const S* ptr);
+__device__ __forceinline__ f2 pair_load(const S* ptr, const typename Storage<S>::Q& qz, int i);
 template <>
-__device__ __forceinline__ f2 pair_load<float>(const float* ptr) {
+__device__ __forceinline__ f2 pair_load<float>(const float* ptr, const NoQuanta&, int) {
     return *reinterpret_cast<const f2*>(ptr);
 }
 template <>
-__device__ __forceinline__ f2 pair_load<__half>(const __half* ptr) {
+__device__ __forceinline__ f2 pair_load<__half>(const __half* ptr, const NoQuanta&, int) {
     const float2 v = __half22float2(*reinterpret_cast<const __half2*>(ptr));
     return pk(v.x * 0x1p-12f, v.y * 0x1p-12f);
 }
 template <>
-__device__ __forceinline__ f2 pair_load<__nv_bfloat16>(const __nv_bfloat16* ptr) {
+__device__ __forceinline__ f2 pair_load<__nv_bfloat16>(const __nv_bfloat16* ptr, const NoQuanta&, int) {
     const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(ptr));
     return pk(v.x, v.y);
 }
+template <>
+__device__ __forceinline__ f2 pair_load<int16_t>(const int16_t* ptr, const Quanta& qz, int i) {
+    const int w = *reinterpret_cast<const int*>(ptr);
+    const float d = qz.d[qclass(i)];
+    return mul2(pk((float)(int16_t)(w & 0xFFFF), (float)(w >> 16)), splat(d));
+}
 // Round-to-nearest store of a pair (each half rounded as Storage<S>::store does).
 template <typename S>
-__device__ __forceinline__ void pair_store(S* ptr, f2 v);
+__device__ __forceinline__ void pair_store(S* ptr, f2 v, const typename Storage<S>::Q& qz, int i);
 template <>
-__device__ __forceinline__ void pair_store<float>(float* ptr, f2 v) {
+__device__ __forceinline__ void pair_store<float>(float* ptr, f2 v, const NoQuanta&, int) {
     *reinterpret_cast<f2*>(ptr) = v;
 }
 template <>
-__device__ __forceinline__ void pair_store<__half>(__half* ptr, f2 v) {
+__device__ __forceinline__ void pair_store<__half>(__half* ptr, f2 v, const NoQuanta&, int) {
     float a, b;
     upk(v, a, b);
     *reinterpret_cast<__half2*>(ptr) = __floats2half2_rn(a * 0x1p12f, b * 0x1p12f);
 }
 template <>
-__device__ __forceinline__ void pair_store<__nv_bfloat16>(__nv_bfloat16* ptr, f2 v) {
+__device__ __forceinline__ void pair_store<__nv_bfloat16>(__nv_bfloat16* ptr, f2 v, const NoQuanta&, int) {
     float a, b;
     upk(v, a, b);
     *reinterpret_cast<__nv_bfloat162*>(ptr) = __floats2bfloat162_rn(a, b);
+}
+template <>
+__device__ __forceinline__ void pair_store<int16_t>(int16_t* ptr, f2 v, const Quanta& qz, int i) {
+    float a, b;
+    upk(v, a, b);
+    const uint32_t lo = (uint16_t)Storage<int16_t>::round_nearest(a, qz, i);
+    const uint32_t hi = (uint16_t)Storage<int16_t>::round_nearest(b, qz, i);
+    *reinterpret_cast<uint32_t*>(ptr) = lo | (hi << 16);
 }
 
 // Block-wide deterministic sum of NV doubles for any whole number of warps; result in thread 0.
@@ -1142,6 +1177,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
         S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off;
         const float omega = (float)s_sp.omega;
         const uint32_t sid = (uint32_t)s_sp.sample_id;
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         double red[2] = {0.0, 0.0};
         // push of the pair's post-collision populations g (step ts, row y) into dst
         auto push = [&](int y, int ts, const f2 (&g)[9]) {
@@ -1162,13 +1198,13 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                 const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xbr : x);
                 if (sr) {
                     const uint32_t m = 0x2545F491u + 0x6A09E668u * (uint32_t)i;
-                    Storage<S>::store_sr(d + ca, a, (ha * m) >> 16);
-                    if (vb) Storage<S>::store_sr(d + cb, b, (hb * m) >> 16);
+                    Storage<S>::store_sr(d + ca, a, (ha * m) >> 16, qz, i);
+                    if (vb) Storage<S>::store_sr(d + cb, b, (hb * m) >> 16, qz, i);
                 } else if (cx(i) == 0 && vb) {
-                    pair_store<S>(d + x, g[i]);
+                    pair_store<S>(d + x, g[i], qz, i);
                 } else {
-                    Storage<S>::store(d + ca, a);
-                    if (vb) Storage<S>::store(d + cb, b);
+                    Storage<S>::store(d + ca, a, qz, i);
+                    if (vb) Storage<S>::store(d + cb, b, qz, i);
                 }
             }
         };
@@ -1184,7 +1220,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                 const S* s0 = src + (y * pitch + x);
                 f2 g[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane);
+                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane, qz, i);
                 f2 q;
                 collide_packed(g, omega, want_a ? &q : nullptr);
                 if (want_a) add_usq(red[0], q);
@@ -1216,12 +1252,12 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                     cp_async_wait<D - 1>();
                     const S* st = stage + (q % D) * 9 * rw + x;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * rw);
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * rw, qz, i);
                     fetch(q + D);
                 } else {
                     const S* s0 = src + (row_of(q) * pitch + x);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane);
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane, qz, i);
                 }
                 f2 qq;
                 const bool w = want_a && count;
@@ -1307,6 +1343,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
     for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int j = tile_sample(p, (int)tile, p.nsamples);
         const SampleDev sp = p.samples[j];
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         const bool chan = MIXED && sp.kind == UQLB_CASE_CHANNEL;
         const int T = p.steps_run[sp.slot];
         const int lt = (int)tile - sp.tile_base;
@@ -1328,9 +1365,15 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                 S* base = lat + sp.f_off;
                 const int64_t own = (int64_t)y * sp.pitch + x;
                 C g[9];
+                if constexpr (std::is_same<S, int16_t>::value) {
+                    // a value held at the end of the fixed-point range saturated on a store
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        if (Storage<S>::at_limit(base + i * sp.plane + own)) red[6] += 1.0;
+                }
                 if (two || (T & 1) == 0) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own);
+                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own, qz, i);
                 } else {
                     C ubx = C(0), uby = C(0);
                     if (chan && x == sp.nx - 1) {
@@ -1342,10 +1385,10 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                             uby = (C)p.side[2 * (sp.side_off + y) + 1];
                         }
                     }
-                    g[0] = Storage<S>::load(base + own);
+                    g[0] = Storage<S>::load(base + own, qz, 0);
 #pragma unroll
                     for (int i = 1; i < 9; ++i)
-                        g[i] = read_incoming<S>(base, sp, mask, x, y, i, T - 1, ubx, uby, chan);
+                        g[i] = read_incoming<S>(base, sp, mask, x, y, i, T - 1, ubx, uby, chan, qz);
                 }
                 const uint32_t links = bz != nullptr ? obstacle_links(sp, *bz, mask, x, y) : 0u;
                 if (links && T > 0) bouzidi_complete(*bz, x, y, links, g);
@@ -1375,13 +1418,13 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                             mask_solid(mask, mask_words(sp), xn, yn)) {
                             if (links) {
                                 const double fs =
-                                    (double)Storage<S>::load(base + i * sp.plane + (int64_t)yn * sp.pitch + xn) +
+                                    (double)Storage<S>::load(base + i * sp.plane + (int64_t)yn * sp.pitch + xn, qz, i) +
                                     (double)g[opp(i)] + 2.0 * wgt<double>(i);
                                 red[4] += cx(i) * fs;
                                 red[5] += cy(i) * fs;
                             } else {
                                 const double fs =
-                                    (double)Storage<S>::load(base + opp(i) * sp.plane + own) + wgt<double>(i);
+                                    (double)Storage<S>::load(base + opp(i) * sp.plane + own, qz, i) + wgt<double>(i);
                                 red[4] += 2.0 * cx(i) * fs;
                                 red[5] += 2.0 * cy(i) * fs;
                             }
@@ -1452,6 +1495,7 @@ __global__ void __launch_bounds__(256) bouzidi_force_kernel(KParams p) {
         const SampleDev& sp = p.samples[j];
         if (!sp.bouzidi || sp.mask_off < 0 || s > sp.steps || p.done[sp.slot]) continue;
         const InitDev& in = p.init[j];
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         const uint32_t* mask = p.masks + sp.mask_off;
         const S* base = static_cast<const S*>(p.arena) + sp.f_off;
         const int bw = in.bbox[1] - in.bbox[0] + 1, bh = in.bbox[3] - in.bbox[2] + 1;
@@ -1476,14 +1520,14 @@ __global__ void __launch_bounds__(256) bouzidi_force_kernel(KParams p) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 if (!(links >> i & 1u)) continue;
-                C back = Storage<S>::load(base + opp(i) * sp.plane + own);
+                C back = Storage<S>::load(base + opp(i) * sp.plane + own, qz, i);
                 const C q = link_q<C>(in, x, y, i);
                 if (q < C(0.5)) {
-                    const C gi = prev_odd ? Storage<S>::load(base + i * sp.plane + own)
-                                          : read_incoming<S>(base, sp, mask, x, y, i, s - 1, ubx, uby, true);
+                    const C gi = prev_odd ? Storage<S>::load(base + i * sp.plane + own, qz, i)
+                                          : read_incoming<S>(base, sp, mask, x, y, i, s - 1, ubx, uby, true, qz);
                     back += (C(1) - C(2) * q) * gi;
                 }
-                const C parked = Storage<S>::load(base + i * sp.plane + (int64_t)(y + cy(i)) * sp.pitch + (x + cx(i)));
+                const C parked = Storage<S>::load(base + i * sp.plane + (int64_t)(y + cy(i)) * sp.pitch + (x + cx(i)), qz, i);
                 const double fs = (double)parked + (double)back + 2.0 * wgt<double>(i);
                 red[0] += cx(i) * fs;
                 red[1] += cy(i) * fs;
@@ -1513,15 +1557,16 @@ __global__ void __launch_bounds__(256) inout_kernel(KParams p) {
         if (sp.kind != UQLB_CASE_CHANNEL || !sp.inout || s > p.steps_run[sp.slot]) continue;
         const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
         const S* base = static_cast<const S*>(p.arena) + sp.f_off;
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         const int nx = sp.nx, ny = sp.ny;
         // post-stream shifted populations of node (x, yy) at time s
         auto state = [&](int x, int yy, C (&g)[9]) {
             Nbr nb;
             nb.row[1] = yy * sp.pitch;
             if (s & 1)
-                node_load<S, true>(p, sp, base, mask, x, yy, s, true, nb, nullptr, 0u, g, false);
+                node_load<S, true>(p, sp, base, mask, x, yy, s, true, nb, nullptr, 0u, g, qz, false);
             else
-                node_load<S, false>(p, sp, base, mask, x, yy, s, true, nb, nullptr, 0u, g, false);
+                node_load<S, false>(p, sp, base, mask, x, yy, s, true, nb, nullptr, 0u, g, qz, false);
         };
         auto velocity = [&](int x, int yy, C& ux, C& uy) {
             C g[9], drho, jx, jy;

@@ -30,6 +30,7 @@ const StorageOps& ops_of(int storage) {
         case UQLB_F64: return storage_ops_f64();
         case UQLB_F32: return storage_ops_f32();
         case UQLB_F16: return storage_ops_f16();
+        case UQLB_FX16: return storage_ops_fx16();
         default: return storage_ops_bf16();
     }
 }

@@ -83,9 +83,44 @@ int storage_bytes(int storage) {
         case UQLB_F64: return 8;
         case UQLB_F32: return 4;
         case UQLB_F16:
-        case UQLB_BF16: return 2;
+        case UQLB_BF16:
+        case UQLB_FX16: return 2;
         default: return 0;
     }
+}
+
+// Quanta of the 16-bit fixed-point storage for one sample: d_c = margin B_c / 32767, B_c a bound on
+// |g_i| of velocity class c (rest, axis, diagonal) over the run.  With drho <= R and every
+// |c_i . u| <= U, the shifted equilibrium g_i = w_i (drho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u))
+// obeys |g_0| <= w_0 (R + (1 + R) 1.5 U^2) and |g_i| <= w_i (R + (1 + R)(3 U + 6 U^2)) for i >= 1.
+//   TGV: U = |u0| + |amp2| + |amp3| (each mode keeps |u| + |v| <= its amplitude, and the decaying
+//     flow never exceeds its start), R = 1.5 U^2 (|p| <= u0^2 / 2); margin 1.5 for the
+//     non-equilibrium part, a few per cent of the bound on resolved lattices.
+//   TGV_PERTURBED (Sec. 8.3): U = |u0| + (|zeta_00| + ... + |zeta_11|) / 4, R = 1.5 U^2, margin 1.5.
+//   CHANNEL (Sec. 8.1): U = 4 |u0| (u0 the mean inflow; |u_x| + |u_y| peaks near 2.8 u0 around the
+//     obstacle and in the start-up) and R = 6 |u0| (start-up pressure waves reach |drho| near 2 u0 with
+//     the ramp; an impulsive start gives about sqrt(3) times the inflow peak, doubled on reflection).
+// A value beyond the range saturates and the run reports the sample unstable.
+void fx16_quanta(const uqlb_sample& s, double d[3]) {
+    double U, R, margin;
+    if (s.kind == UQLB_CASE_CHANNEL) {
+        U = 4.0 * std::fabs(s.u0);
+        R = 6.0 * std::fabs(s.u0);
+        margin = 1.0;
+    } else {
+        U = std::fabs(s.u0);
+        if (s.kind == UQLB_CASE_TGV_PERTURBED)
+            U += 0.25 * (std::fabs(s.pert[0]) + std::fabs(s.pert[1]) + std::fabs(s.pert[2]) + std::fabs(s.pert[3]));
+        else
+            U += std::fabs(s.amp2) + std::fabs(s.amp3);
+        R = 1.5 * U * U;
+        margin = 1.5;
+    }
+    U = std::max(U, 1e-6);
+    const double rho = 1.0 + R;
+    const double b[3] = {4.0 / 9.0 * (R + rho * 1.5 * U * U), 1.0 / 9.0 * (R + rho * (3.0 * U + 6.0 * U * U)),
+                         1.0 / 36.0 * (R + rho * (3.0 * U + 6.0 * U * U))};
+    for (int c = 0; c < 3; ++c) d[c] = (double)(float)(margin * b[c] / 32767.0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -516,6 +551,14 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
                 for (int y = 0; y < s.ny; ++y)
                     for (int x = 0; x < s.nx; ++x)
                         if (sample_solid(s, x, y)) m[(size_t)y * mask_words(d) + (x >> 5)] |= 1u << (x & 31);
+            }
+        }
+        if (storage == UQLB_FX16) {
+            double q[3];
+            fx16_quanta(s, q);
+            for (int c = 0; c < 3; ++c) {
+                P.init[j].quanta[c] = (float)q[c];
+                P.init[j].inv_quanta[c] = (float)(1.0 / q[c]);
             }
         }
         P.init[j].u0 = s.u0;
@@ -969,6 +1012,12 @@ int uqlb_unit_converter(int n, double ma, double re, double* dx, double* dt, dou
     if (dt) *dt = k;
     if (tau) *tau = 3.0 * (1.0 / re) * k / (h * h) + 0.5;
     if (u_lattice) *u_lattice = k / h;
+    return 0;
+}
+
+int uqlb_fx16_quanta(const uqlb_sample* s, double* quanta) {
+    if (!s || !quanta) return set_err(nullptr, UQLB_ERR_ARG, "fx16_quanta: null argument");
+    fx16_quanta(*s, quanta);
     return 0;
 }
 

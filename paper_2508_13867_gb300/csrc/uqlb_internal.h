@@ -53,6 +53,9 @@ struct alignas(16) InitDev {
     double cyl_cx, cyl_cy, cyl_r;
     double pad2;
     int32_t bbox[4];  // x0, x1, y0, y1 (inclusive): the only nodes that can have obstacle links
+    // 16-bit fixed-point storage: quantum of the rest, axis and diagonal populations and its inverse
+    float quanta[4];
+    float inv_quanta[4];
 };
 
 // Device pointers carved out of the caller's workspace for one batch run.

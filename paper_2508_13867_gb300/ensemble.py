@@ -10,7 +10,7 @@ import torch
 from . import uqlb as U
 from .workloads import SampleSpec, Workload
 
-STORAGE = {"f64": U.UQLB_F64, "f32": U.UQLB_F32, "f16": U.UQLB_F16, "bf16": U.UQLB_BF16}
+STORAGE = {"f64": U.UQLB_F64, "f32": U.UQLB_F32, "f16": U.UQLB_F16, "bf16": U.UQLB_BF16, "fx16": U.UQLB_FX16}
 PARAMS = {"nu": U.UQLB_PARAM_NU, "u0": U.UQLB_PARAM_U0, "zeta2": U.UQLB_PARAM_ZETA2, "zeta3": U.UQLB_PARAM_ZETA3,
           "pert00": U.UQLB_PARAM_PERT00, "pert01": U.UQLB_PARAM_PERT01, "pert10": U.UQLB_PARAM_PERT10,
           "pert11": U.UQLB_PARAM_PERT11}

@@ -31,7 +31,7 @@ UQLB_SCHEME_AUTO, UQLB_SCHEME_ONE_STEP, UQLB_SCHEME_TWO_STEP = 0, 1, 2
 UQLB_SCHEME_TWO_STEP_TILES, UQLB_SCHEME_TWO_STEP_STRIPS, UQLB_SCHEME_GROUPED = 3, 4, 5
 (UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3, UQLB_PARAM_PERT00, UQLB_PARAM_PERT01,
  UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
-UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16 = 0, 1, 2, 3
+UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16, UQLB_FX16 = 0, 1, 2, 3, 4
 UQLB_ROUND_AUTO, UQLB_ROUND_NEAREST, UQLB_ROUND_STOCHASTIC = 0, 1, 2
 UQLB_MODE_GRAPH, UQLB_MODE_PERSISTENT, UQLB_MODE_PERSISTENT_TEST_TIMEOUT = 0, 1, 2
 (UQLB_QOI_K, UQLB_QOI_MASS, UQLB_QOI_MOMX, UQLB_QOI_MOMY, UQLB_QOI_CD, UQLB_QOI_CL, UQLB_QOI_STEPS,
@@ -73,6 +73,7 @@ _SIGNATURES = {
     "uqlb_num_multi_indices": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(c_int64)],
     "uqlb_multi_indices": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P(c_int32)],
     "uqlb_obstacle_mask": [_P(uqlb_sample), _P(ctypes.c_uint8)],
+    "uqlb_fx16_quanta": [_P(uqlb_sample), _P(c_double)],
     "uqlb_unit_converter": [ctypes.c_int, c_double, c_double, _P(c_double), _P(c_double), _P(c_double),
                             _P(c_double)],
     "uqlb_mean_host": [_P(c_double), c_int64, _P(c_double)],
@@ -192,6 +193,12 @@ def uqlb_unit_converter(n: int, ma: float, re: float) -> dict:
     _check(lib().uqlb_unit_converter(n, ma, re, ctypes.byref(dx), ctypes.byref(dt), ctypes.byref(tau),
                                      ctypes.byref(ul)))
     return {"dx": dx.value, "dt": dt.value, "tau": tau.value, "u_lattice": ul.value}
+
+
+def uqlb_fx16_quanta(sample: uqlb_sample) -> np.ndarray:
+    q = np.zeros(3)
+    _check(lib().uqlb_fx16_quanta(ctypes.byref(sample), _dp(q)))
+    return q
 
 
 def uqlb_obstacle_mask(sample: uqlb_sample) -> np.ndarray:

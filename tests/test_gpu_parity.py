@@ -18,7 +18,19 @@ from tests.helpers import oracle_case, oracle_row, rel_l2  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-3, "bf16": 1e-3}
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 1e-3, "bf16": 1e-3, "fx16": 1e-3}
+
+# IEEE BF16 keeps 8 significant bits: every store rounds g by up to 2^-8 of itself (stochastic
+# rounding) and the velocity is a sum of six such populations, so a single rounding of the
+# initial state already costs ~8e-4 of the field; after a few hundred steps the per-sample field
+# error is ~3e-3 to 1e-2 (measured), above the 1e-3 budget.  These cases stay asserted at the
+# budget and are expected to fail until a BF16 run meets it; the fixed-point format FX16 is the
+# 16-bit storage that does.
+BF16_MISS = pytest.mark.xfail(strict=True, reason="IEEE BF16 storage misses the 1e-3 budget (8 significant bits)")
+
+
+def _storages(*names):
+    return [pytest.param(n, marks=BF16_MISS) if n == "bf16" else n for n in names]
 
 
 @pytest.fixture(scope="module")
@@ -67,32 +79,35 @@ def test_tgv_f64_fields_energy_and_invariants(ens, n, steps):
         assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=1e-12, atol=0)
 
 
-# BF16 keeps 8 significant bits: every store rounds g by up to 2^-9 of itself, which is ~1e-3
-# of the velocity a population carries, at every step.  Its per-sample field error therefore
-# sits near 1e-2 and does not meet the 1e-3 budget; the bound below guards that level.
-FIELD_TOL = {"f32": 1e-5, "f16": 1e-3, "bf16": 2e-2}
-
-
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-def test_tgv_reduced_precision_storage(ens, storage):
+@pytest.mark.parametrize("scheme", ["auto", "one_step", "two_step_tiles"])
+@pytest.mark.parametrize("storage", _storages("f32", "f16", "bf16", "fx16"))
+def test_tgv_reduced_precision_storage(ens, storage, scheme):
+    """Per-sample velocity fields and K(T) against the oracle within the storage's budget (96 x 96,
+    300 steps, three samples), on the row strips (auto), the one-step and the two-step tile kernels."""
     specs = _tgv_specs(96, 300)
-    g = _run(ens, specs, storage)
+    g = _run(ens, specs, storage, scheme=scheme)
     ref = olbm.run([oracle_case(s) for s in specs])
     for i, r in enumerate(ref):
-        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < FIELD_TOL[storage], storage
-        # K is a sum of squares: the BF16 rounding noise adds a positive bias (measured 2.1%)
-        k_tol = 5e-2 if storage == "bf16" else FIELD_TOL[storage]
-        assert abs(g["qoi"][i, U.UQLB_QOI_K] - r.k_final) < k_tol * r.k_final
+        err = rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1])
+        print(f"storage {storage} {scheme} sample {i}: fields {err:.3e}")
+        assert err < TOL[storage], (storage, scheme, err)
+        assert abs(g["qoi"][i, U.UQLB_QOI_K] - r.k_final) < TOL[storage] * r.k_final, (storage, scheme)
+        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0
 
 
-@pytest.mark.parametrize("storage,rounding", [("f32", "auto"), ("f16", "auto"), ("bf16", "auto"),
-                                              ("f16", "nearest"), ("bf16", "nearest")])
+@pytest.mark.parametrize("storage,rounding", [("f32", "auto"), ("f16", "auto"), ("f16", "nearest"),
+                                              pytest.param("bf16", "auto", marks=BF16_MISS),
+                                              pytest.param("bf16", "nearest", marks=BF16_MISS),
+                                              ("fx16", "auto"), ("fx16", "nearest")])
 def test_reduced_precision_ensemble_statistics(ens, storage, rounding):
-    """Mean and standard deviation of the velocity fields over 16 seeded MC samples of the 4-D
-    Taylor-Green set-up (64 x 64, 300 steps) against the same statistics of the oracle.  16-bit
-    storage rounds stochastically by default ("auto") or to nearest even."""
+    """Mean and standard deviation of the velocity fields over 64 seeded MC samples of the 4-D
+    Taylor-Green set-up (64 x 64, 300 steps) against the same statistics of the oracle, within the
+    storage's budget.  16-bit storage rounds stochastically by default ("auto") or to nearest even.
+    The storage noise e of one sample moves the N-sample std by about e / (sigma sqrt N) (sigma the
+    spread of the samples, ~0.12 of the field here); 64 samples is the oracle subset of the 512 x 512
+    Monte Carlo workload."""
     e = Ensemble(0)
-    w = W.tgv512_mc4d(n=64, steps=300, n_mc=16)
+    w = W.tgv512_mc4d(n=64, steps=300, n_mc=64)
     e.setup(w)
     smp = e.ensemble_samples(w)
     res = e.run_batch(smp, storage=storage, fields_dtype="f32", rounding=rounding)
@@ -103,12 +118,11 @@ def test_reduced_precision_ensemble_statistics(ens, storage, rounding):
     mu_r, var_r = ouq.mc_mean_var(mref, ddof=1)
     m_err = rel_l2(mean.cpu().numpy()[:-1], mu_r[:-1])
     s_err = rel_l2(np.sqrt(var.cpu().numpy()[:-1]), np.sqrt(var_r[:-1]))
-    # FP16 meets the 1e-3 budget on the mean; its storage noise inflates the sample variance, so
-    # the std field sits at ~1e-3 (measured 1.03e-3); BF16 misses both (noise of 2^-9 per store).
-    bound = {("f32", "auto"): (1e-5, 1e-5), ("f16", "auto"): (1e-3, 2e-3), ("f16", "nearest"): (1e-3, 2e-3),
-             ("bf16", "auto"): (5e-3, 3e-2), ("bf16", "nearest"): (2e-2, 4e-2)}[(storage, rounding)]
-    print(f"precision {storage}/{rounding}: mean {m_err:.3e} std {s_err:.3e}")
-    assert m_err < bound[0] and s_err < bound[1], (storage, rounding, m_err, s_err)
+    f = res["fields"].double().cpu().numpy()
+    worst = max(rel_l2(f[i, :-1], mref[i, :-1]) for i in range(len(smp)))
+    print(f"precision {storage}/{rounding}: mean {m_err:.3e} std {s_err:.3e} worst sample {worst:.3e}")
+    tol = TOL[storage]
+    assert m_err < tol and s_err < tol and worst < tol, (storage, rounding, m_err, s_err, worst)
     e.close()
 
 
@@ -409,7 +423,7 @@ def test_stochastic_rounding_is_reproducible_and_unbiased(ens):
     two-step scheme rounds every other step)."""
     specs = [W.tgv(128, 600, nu=0.03, u0=0.01)]
     ref = olbm.run([oracle_case(s) for s in specs])[0]
-    for st in ("f16", "bf16"):
+    for st in ("f16", "bf16", "fx16"):
         def run(r):
             return ens.run_batch([sample_struct(s) for s in specs], storage=st, rounding=r, scheme="one_step")
         a, b, n = run("stochastic"), run("stochastic"), run("nearest")
@@ -419,7 +433,11 @@ def test_stochastic_rounding_is_reproducible_and_unbiased(ens):
         e_sr = rel_l2(fa[:-1], oracle_row(ref)[:-1])
         e_rn = rel_l2(fn[:-1], oracle_row(ref)[:-1])
         print(f"{st}: stochastic {e_sr:.3e} nearest {e_rn:.3e}")
-        assert e_sr < e_rn, (st, e_sr, e_rn)
+        if st == "fx16":
+            # 15 bits over the class's range: both roundings stay well inside the budget here
+            assert e_sr < 0.5 * TOL[st] and e_rn < 0.5 * TOL[st], (st, e_sr, e_rn)
+        else:
+            assert e_sr < e_rn, (st, e_sr, e_rn)
 
 
 def _paper4d_specs(n, steps, pert_sets):
@@ -597,18 +615,21 @@ def test_two_step_strips_match_the_tiles_and_the_one_step_scheme(ens):
                 _close(st, ti, what=(n, ny, qe, "tiles"))
 
 
-@pytest.mark.parametrize("storage,nx", [("f32", 1600), ("bf16", 2048), ("f32", 64 * 13)])
+@pytest.mark.parametrize("storage,nx", [("f32", 1600), ("fx16", 2048), pytest.param("bf16", 2048, marks=BF16_MISS),
+                                        ("f32", 64 * 13)])
 def test_two_step_strips_at_the_widest_rows(ens, storage, nx):
     """The widest rows the strips take (FP32 1600: ring and staging fill 230 KB of shared memory in
     one block of 800 threads; 16-bit 2048: 1024 threads) and an odd multiple of 64, on thin
-    lattices, against the one-step scheme."""
+    lattices: fields and the K series against the oracle within the storage's budget."""
     specs = [replace(W.tgv(nx, 9, nu=0.03, amp2=0.0005), ny=6), replace(W.tgv(nx, 8, nu=0.05), ny=6)]
     st = _run(ens, specs, storage, qoi_every=1, series=True, scheme="two_step_strips")
     assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
-    ref = _run(ens, specs, storage, qoi_every=1, series=True, scheme="one_step")
-    tol = 1e-6 if storage == "f32" else 0.5 * FIELD_TOL[storage]
-    assert rel_l2(st["fields"][:, :-1], ref["fields"][:, :-1]) < tol
-    assert np.allclose(st["series"], ref["series"], rtol=10 * tol, atol=0, equal_nan=True)
+    ref = olbm.run([oracle_case(s, qoi_every=1) for s in specs])
+    tol = TOL[storage]
+    for i, r in enumerate(ref):
+        assert rel_l2(st["fields"][i, :-1], oracle_row(r)[:-1]) < tol, (storage, nx, i)
+        ns = specs[i].steps + 1
+        assert np.allclose(st["series"][i, :ns], r.series[:ns], rtol=tol, atol=0), (storage, nx, i)
 
 
 def test_two_step_strips_split_samples_across_blocks(ens):
@@ -744,7 +765,7 @@ def test_two_step_resume_continues_the_run(ens, split):
         assert rel_l2(got, whole["fields"][:, :-1]) < 1e-6
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", _storages("f16", "bf16", "fx16"))
 def test_two_step_strips_16_bit_nearest_rounding(ens, storage):
     """Round-to-nearest 16-bit stores on the row strips (pairs of 16-bit values per store where the
     pair is aligned) round every value as the tile kernel's scalar stores do: the two kernels agree
@@ -759,14 +780,14 @@ def test_two_step_strips_16_bit_nearest_rounding(ens, storage):
                             scheme=scheme)
         torch.cuda.synchronize()
         run[scheme] = res["fields"].double().cpu().numpy()
-    assert rel_l2(run["two_step_strips"][:, :-1], run["two_step_tiles"][:, :-1]) < 0.5 * FIELD_TOL[storage]
+    assert rel_l2(run["two_step_strips"][:, :-1], run["two_step_tiles"][:, :-1]) < 0.5 * TOL[storage]
     for i, r in enumerate(ref):
         for scheme, m in run.items():
-            assert rel_l2(m[i, :-1], oracle_row(r)[:-1]) < FIELD_TOL[storage], (scheme, storage)
+            assert rel_l2(m[i, :-1], oracle_row(r)[:-1]) < TOL[storage], (scheme, storage)
 
 
 @pytest.mark.parametrize("scheme", ["two_step_tiles", "two_step_strips"])
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", _storages("f16", "bf16", "fx16"))
 def test_two_step_16_bit_storage_against_the_oracle(ens, storage, scheme):
     """16-bit storage on the two-step scheme keeps the intermediate step in FP32 shared memory, so
     it rounds half as often; fields stay within the one-step scheme's budget of the oracle (both
@@ -778,5 +799,83 @@ def test_two_step_16_bit_storage_against_the_oracle(ens, storage, scheme):
     for i, r in enumerate(ref):
         e2 = rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1])
         e1 = rel_l2(one["fields"][i, :-1], oracle_row(r)[:-1])
-        assert e2 < FIELD_TOL[storage], (storage, e2)
+        assert e2 < TOL[storage], (storage, e2)
         assert e2 < 1.5 * e1 + 1e-6, (storage, e2, e1)
+
+
+@pytest.mark.parametrize("n", [31, 97, 40, 64, 832])
+def test_strip_kernel_edge_geometries_against_the_oracle(ens, n):
+    """The row strips (FP32) against the oracle directly, at the geometries whose index arithmetic
+    differs: odd widths (31, 97: the last pair is a lone node whose partner is dropped), a width that
+    leaves threads past the row (40), a full block (64) and an odd multiple of 64 (832); heights equal
+    to the width, ragged (37) and degenerate (3, 2: the rows above and below a node coincide); step
+    counts that end on a single-step launch (61, 1), stop at once (0) or end on a two-step launch
+    (60); K at every step and at a stride of 7."""
+    heights = (37, 3, 2) if n > 128 else (n, 37, 3, 2)
+    for ny in heights:
+        specs = [replace(W.tgv(n, 61, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(n, 60, nu=0.05, amp3=-0.0004), ny=ny),
+                 replace(W.tgv(n, 1, nu=0.02), ny=ny), replace(W.tgv(n, 0, nu=0.04), ny=ny)]
+        for qe in (1, 7):
+            g = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme="two_step_strips")
+            assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
+            ref = olbm.run([oracle_case(s, qoi_every=qe) for s in specs])
+            for i, r in enumerate(ref):
+                what = (n, ny, qe, specs[i].steps)
+                assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f32"], what
+                ns = specs[i].steps // qe + 1
+                # K passes close to zero on the 2- and 3-row lattices: compare relative to the series
+                scale = np.abs(r.series[:ns]).max()
+                assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=TOL["f32"], atol=TOL["f32"] * scale), what
+                assert abs(g["qoi"][i, U.UQLB_QOI_K] - r.k_final) <= TOL["f32"] * max(abs(r.k_final), scale), what
+                assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < TOL["f32"] * r.mass, what
+                assert g["qoi"][i, U.UQLB_QOI_STEPS] == specs[i].steps, what
+
+
+@pytest.mark.parametrize("storage", _storages("f16", "bf16", "fx16"))
+def test_channel_16_bit_storage_against_the_oracle(ens, storage):
+    """16-bit population storage on the channel (one-step kernel): the staircase cylinder with the
+    face inlet/outlet, the empty channel, and the Bouzidi cylinder with the interpolated
+    inlet/outlet; velocity fields and C_D against the oracle within the 16-bit budget."""
+    specs = [_cyl(6, 600), W.channel(6, steps=600, obstacle=False, steady_tol=0.0, re=5.0),
+             _cyl(5, 601, u_mean=0.044, bc="bouzidi", inout="interpolated")]
+    g = _run(ens, specs, storage)
+    ref = olbm.run([oracle_case(s) for s in specs])
+    for i, r in enumerate(ref):
+        err = rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1])
+        print(f"channel {storage} sample {i}: fields {err:.3e} C_D {g['qoi'][i, U.UQLB_QOI_CD]:.6f} vs {r.cd:.6f}")
+        assert err < TOL[storage], (storage, i, err)
+        if specs[i].cyl_r > 0:
+            assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < TOL[storage] * abs(r.cd), (storage, i)
+        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0
+
+
+def test_fixed_point_storage_reports_a_blown_up_sample(ens):
+    """A sample that leaves the fixed-point range saturates instead of turning non-finite; the
+    finalize counts the saturated values and reports the sample unstable, as FP32 storage reports
+    the non-finite one.  The Sec. 8.3 set-up at n = 8 (7 x 7 lattice, tau - 1/2 = 1.2e-3) blows up
+    under BGK by t = 100 (965 steps)."""
+    pert_sets = [(0.02, -0.01, 0.015, -0.025), (-0.025, 0.0, 0.01, 0.02), (0.01, 0.01, -0.02, 0.0)]
+    specs = _paper4d_specs(8, 965, pert_sets) + [W.tgv(40, 200, nu=0.03)]
+    f32 = _run(ens, specs, "f32")
+    fx = _run(ens, specs, "fx16")
+    bad32 = f32["qoi"][:, U.UQLB_QOI_STATUS] == U.UQLB_ERR_UNSTABLE
+    badfx = fx["qoi"][:, U.UQLB_QOI_STATUS] == U.UQLB_ERR_UNSTABLE
+    assert bad32[:3].any() and not bad32[3]
+    assert np.all(badfx[bad32]) and not badfx[3], (bad32, badfx)
+
+
+@pytest.mark.parametrize("scheme,split", [("one_step", 37), ("one_step", 50), ("two_step_strips", 50),
+                                          ("two_step_tiles", 50)])
+def test_fixed_point_resume_continues_the_run_exactly(ens, scheme, split):
+    """Fixed-point storage holds the state exactly (integers and per-sample quanta), so a run
+    stopped after `split` steps and resumed equals the uninterrupted run bit for bit."""
+    specs = _tgv_specs(64, 100) + [W.tgv(64, 71, nu=0.04)]
+    whole = _run(ens, specs, "fx16", qoi_every=10, series=True, scheme=scheme)
+    head = [sample_struct(s) for s in specs]
+    for s in head:
+        s.steps = min(split, s.steps)
+    ens.run_batch(head, storage="fx16", fields=False, scheme=scheme)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="fx16", fields=True, start_step=split,
+                        scheme=scheme)
+    torch.cuda.synchronize()
+    assert np.array_equal(res["fields"].double().cpu().numpy(), whole["fields"])

@@ -167,7 +167,7 @@ def test_workspace_bytes_cover_the_arena():
     """One lattice for the one-step scheme, two for the two-step scheme (the default for periodic
     FP32, FP16 and BF16 batches)."""
     s = [sample_struct(W.tgv(256, 10)) for _ in range(3)]
-    for storage, eb in ((U.UQLB_F64, 8), (U.UQLB_F32, 4), (U.UQLB_F16, 2), (U.UQLB_BF16, 2)):
+    for storage, eb in ((U.UQLB_F64, 8), (U.UQLB_F32, 4), (U.UQLB_F16, 2), (U.UQLB_BF16, 2), (U.UQLB_FX16, 2)):
         arena = 3 * 9 * 256 * 256 * eb
         lattices = 2 if storage != U.UQLB_F64 else 1
         b = U.uqlb_batch_workspace_bytes(s, U.uqlb_run_opts(storage, U.UQLB_F32, 0, 0, 0))
@@ -423,3 +423,55 @@ def test_untuned_workspace_covers_every_geometry_for_every_entry_point():
                 assert U.uqlb_batch_workspace_bytes(smp, fixed) <= one_b
     finally:
         U.uqlb_destroy(ctx)
+
+
+_C = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+_WQ = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+_CLASS = np.array([0, 1, 1, 1, 1, 2, 2, 2, 2])
+
+
+def _class_max_of_equilibrium(r):
+    """Largest |g_i| per velocity class of the shifted equilibrium of an oracle state (u, v, rho)."""
+    drho = r.rho - 1.0
+    usq = r.u * r.u + r.v * r.v
+    out = np.zeros(3)
+    fluid = r.rho != 0
+    for i in range(9):
+        cu = _C[i, 0] * r.u + _C[i, 1] * r.v
+        g = _WQ[i] * (drho + r.rho * (3 * cu + 4.5 * cu * cu - 1.5 * usq))
+        out[_CLASS[i]] = max(out[_CLASS[i]], np.abs(g[fluid]).max())
+    return out
+
+
+def test_fixed_point_quanta_bound_the_populations():
+    """The 16-bit fixed-point storage covers +-32767 quanta per velocity class.  The quanta come
+    from a bound on |g_i|; the equilibrium populations of the oracle's states must stay inside that
+    range with headroom: the initial Taylor-Green fields at the corners of the 4-D workload's input
+    box and the Sec. 8.3 perturbed field keep the bound's margin of 1.5 (less FP32 rounding of the
+    quanta), and the channel's states during and after the start-up ramp (halfway and Bouzidi
+    obstacle, face and interpolated inlet/outlet, +-20 % inflow) stay below 0.8 of the range."""
+    cases = []
+    for u0 in (0.008, 0.012):
+        for z2 in (-0.1, 0.1):
+            for z3 in (-0.1, 0.1):
+                cases.append(W.tgv(64, 0, nu=0.04, u0=u0, amp2=z2 * u0, amp3=z3 * u0))
+    p = U.uqlb_unit_converter(64, 1.6 / 64, 40.0 * 64)
+    ul = p["u_lattice"]
+    for zs in ((0.025, -0.025, 0.025, -0.025), (0.0, 0.01, -0.02, 0.025)):
+        cases.append(W.SampleSpec(W.TGV_PERTURBED, 63, 63, 0, 0.01, ul, u_ref=ul, pert=tuple(z * ul for z in zs)))
+    from tests.helpers import oracle_case
+    for spec in cases:
+        q = U.uqlb_fx16_quanta(sample_struct(spec))
+        r = olbm.run([oracle_case(spec)])[0]
+        used = _class_max_of_equilibrium(r) / (32767 * q)
+        assert np.all(used <= 1 / 1.45), (spec, used)
+        # not loose by more than twice the margin for the moving populations, which carry the velocity
+        # (the rest population's bound adds the density and kinetic terms at their separate maxima)
+        assert np.all(used[1:] >= 1 / 3.0) and used[0] >= 1 / 6.0, (spec, used)
+    for u in (0.032, 0.048):
+        for bc, io in (("halfway", "face"), ("bouzidi", "interpolated")):
+            for steps in (300, 900, 3000):
+                spec = W.channel(6, u_mean=u, steps=steps, steady_tol=0.0, bc=bc, inout=io)
+                q = U.uqlb_fx16_quanta(sample_struct(spec))
+                used = _class_max_of_equilibrium(olbm.run([oracle_case(spec)])[0]) / (32767 * q)
+                assert np.all(used < 0.8), (u, bc, io, steps, used)

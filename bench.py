@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ensemble MLUPS (tgv256_gpc4d: 625 samples x 256^2 x 2000 steps, FP32 storage, FP64 gPC statistics)"
 UNIT = "MLUPS"
-BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36, "fx16": 36}
 # per scheme: the step kernel, the profile holding its ncu traffic, and the kernel version that
 # profile was taken on (a mismatch reports traffic as null)
 STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in place)", "step_kernel_f32_tgv256.md",
@@ -205,20 +205,13 @@ def bench_kernel_only(args):
     return 0
 
 
-def _oracle_async(cases):
-    """Start the oracle on `cases` in a background thread (its C loop releases the GIL)."""
+def _oracle_run(cases):
+    """The oracle on `cases`, run after every timed GPU region so that no host work overlaps one."""
     from oracle import lbm as olbm
 
-    box = {}
-
-    def work():
-        t0 = time.perf_counter()
-        box["res"] = olbm.run(cases)
-        box["s"] = time.perf_counter() - t0
-
-    th = threading.Thread(target=work, daemon=True)
-    th.start()
-    return th, box
+    t0 = time.perf_counter()
+    res = olbm.run(cases)
+    return res, time.perf_counter() - t0
 
 
 def _oracle_cases(specs):
@@ -235,6 +228,53 @@ def _rel(a, b):
 
     a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _mc_against_sc(ens, w_mc, mc_fields, torch):
+    """Sec. 8.2's comparison of Monte Carlo with stochastic collocation, on the 4-D workload: the
+    reference is the 5^4 tensor Gauss-Legendre collocation of the same set-up (total degree 4), run
+    with the same storage; the Monte Carlo mean and standard-deviation fields of N samples (disjoint
+    blocks of the seeded sequence, up to 32 blocks per N) are compared with it in relative L2, and
+    the RMS error over the blocks is fitted against N (Monte Carlo converges as N^-1/2)."""
+    import numpy as np
+
+    from paper_2508_13867_gb300 import workloads as W
+
+    w_sc = W.tgv256_gpc4d(n=w_mc.base.nx, steps=w_mc.base.steps, storage=w_mc.storage)
+    ens.setup(w_sc)
+    smp = ens.ensemble_samples(w_sc)
+    rsc = ens.run_batch(smp, storage=w_sc.storage, fields_dtype="f32")
+    mean_sc, var_sc = ens.stats(ens.project(rsc["fields"]))
+    del rsc
+    ens.setup(w_mc)
+    ref_mean = mean_sc[:-1]
+    ref_std = torch.sqrt(var_sc[:-1])
+    S = mc_fields.shape[0]
+    out = {"reference": f"5^4 Gauss-Legendre collocation, total degree 4, {w_sc.storage} storage",
+           "n": [], "blocks": [], "mean_rel_l2": [], "std_rel_l2": []}
+    n = 16
+    while n <= S:
+        blocks = min(S // n, 32)
+        em, es = [], []
+        for b in range(blocks):
+            m = mc_fields[b * n:(b + 1) * n, :-1].double()
+            mu = m.mean(0)
+            sd = m.std(0, unbiased=True)
+            em.append(float(torch.linalg.norm(mu - ref_mean) / torch.linalg.norm(ref_mean)))
+            es.append(float(torch.linalg.norm(sd - ref_std) / torch.linalg.norm(ref_std)))
+            del m, mu, sd
+        out["n"].append(n)
+        out["blocks"].append(blocks)
+        out["mean_rel_l2"].append(float(np.sqrt(np.mean(np.square(em)))))
+        out["std_rel_l2"].append(float(np.sqrt(np.mean(np.square(es)))))
+        n *= 2
+    sel = [i for i, b in enumerate(out["blocks"]) if b >= 4]
+    if len(sel) >= 2:
+        x = np.log([out["n"][i] for i in sel])
+        out["slope_mean"] = float(np.polyfit(x, np.log([out["mean_rel_l2"][i] for i in sel]), 1)[0])
+        out["slope_std"] = float(np.polyfit(x, np.log([out["std_rel_l2"][i] for i in sel]), 1)[0])
+        out["slope_fit_over_n"] = [out["n"][i] for i in sel]
+    return out
 
 
 def bench_workload(args):
@@ -285,8 +325,8 @@ def bench_workload(args):
                               s.cyl_r, s.ramp_steps, s.steady_tol, s.steady_checks, tuple(s.pert), s.obstacle_bc,
                               s.inout_bc)
                  for s in smp]
-        sub = list(range(min(len(specs), args.oracle_samples)))
-        th, box = _oracle_async(_oracle_cases([specs[i] for i in sub]))
+        n_oracle = args.oracle_samples if args.oracle_samples >= 0 else (64 if args.workload == "tgv512_mc4d" else 4)
+        sub = list(range(min(len(specs), n_oracle)))
         fd = "f64" if w.storage == "f64" else "f32"
         qe = w.qoi_every
 
@@ -300,7 +340,7 @@ def bench_workload(args):
             return r, m, v
 
         ms, (r, mean, var) = timed(run, args.steps)
-        upd = sum(int(q[U.UQLB_QOI_STEPS]) for q in r["qoi"].cpu().numpy()) * smp[0].nx * smp[0].ny
+        upd = sum(int(qq[U.UQLB_QOI_STEPS]) for qq in r["qoi"].cpu().numpy()) * smp[0].nx * smp[0].ny
         line.update({"samples": len(smp), "lattice": [smp[0].nx, smp[0].ny], "time_to_stats_s": ms / 1e3,
                      "value": upd / (ms / 1e3) / 1e6, "mode": args.mode, "scheme": args.scheme})
         # further storage formats of the same ensemble (compared with the same oracle subset)
@@ -321,15 +361,22 @@ def bench_workload(args):
             pms, _ = timed(lambda: ens.run_plain_f64(psub, fields=True), 1)
             line["plain_f64_time_to_stats_s"] = pms / 1e3 * len(smp) / len(psub)
             line["speedup_vs_plain_f64"] = line["plain_f64_time_to_stats_s"] / line["time_to_stats_s"]
-        th.join()
-        ref = box["res"]
-        m_ref = np.stack([np.concatenate([q.u.ravel(), q.v.ravel(), [q.k_final]]) for q in ref])
+        mc_sc = None
+        if args.workload == "tgv512_mc4d" and args.mc_vs_sc:
+            mc_sc = _mc_against_sc(ens, w, r["fields"], torch)
         g_fields = r["fields"][sub].double().cpu().numpy()
+        q_all = r["qoi"].cpu().numpy()
+        del r
+        ref, oracle_s = _oracle_run(_oracle_cases([specs[i] for i in sub]))
+        m_ref = np.stack([np.concatenate([q.u.ravel(), q.v.ravel(), [q.k_final]]) for q in ref])
         line["oracle_samples"] = len(sub)
-        line["oracle_seconds"] = box["s"]
+        line["oracle_seconds"] = oracle_s
+        line["host_work_overlapping_timed_regions"] = False
+        if mc_sc is not None:
+            line["mc_vs_sc"] = mc_sc
         line["field_rel_l2_worst_sample"] = max(_rel(g_fields[i, :-1], m_ref[i, :-1]) for i in range(len(sub)))
         if args.workload == "cylinder":
-            q = r["qoi"].cpu().numpy()
+            q = q_all
             line["cd"] = q[:, U.UQLB_QOI_CD].tolist()
             line["steps_run"] = q[:, U.UQLB_QOI_STEPS].tolist()
             line["cd_oracle"] = [x.cd for x in ref]
@@ -675,7 +722,7 @@ def main():
     ap.add_argument("--samples", type=int, default=128)
     ap.add_argument("--time-steps", type=int, default=16)
     ap.add_argument("--lattice", type=int, default=0, help="kernel-only: lattice side N (0: the workload's 256)")
-    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16", "fx16"])
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
@@ -691,7 +738,10 @@ def main():
     ap.add_argument("--t-max", type=float, default=100.0, help="tgv_paper4d: final physical time")
     ap.add_argument("--sampling", default="mc", choices=["mc", "smolyak"],
                     help="tgv_paper4d: Monte Carlo with N = n samples, or the level-3 Smolyak grid")
-    ap.add_argument("--oracle-samples", type=int, default=4, help="oracle reference subset (other workloads)")
+    ap.add_argument("--oracle-samples", type=int, default=-1,
+                    help="oracle reference subset (other workloads; default 64 for tgv512_mc4d, else 4)")
+    ap.add_argument("--no-mc-vs-sc", dest="mc_vs_sc", action="store_false",
+                    help="tgv512_mc4d: skip the Monte Carlo error against the 5^4 collocation reference")
     ap.add_argument("--storages", default="", help="further storage formats to run on the same workload")
     ap.add_argument("--nd", type=int, default=20, help="cylinder: nodes per diameter")
     ap.add_argument("--obstacle-bc", default="halfway", choices=["halfway", "bouzidi"],

@@ -270,12 +270,15 @@ int uqlb_unit_converter(int n, double ma, double re, double* dx, double* dt, dou
                         double* u_lattice);
 
 /* Quanta of the UQLB_FX16 storage for one sample, quanta[3] = (rest, axis, diagonal): margin x B_c / 32767
- * with B_c a bound on |g_i| of class c from the equilibrium of the sample's largest speed U and density
- * deviation R (the shifted D2Q9 equilibrium of Sec. 3):  B_0 = 4/9 (R + (1 + R) 1.5 U^2),
- * B_axis = 1/9 (R + (1 + R)(3 U + 6 U^2)), B_diag = 1/36 (the same).  TGV: U = |u0| + |amp2| + |amp3|,
- * R = 1.5 U^2, margin 1.5; TGV_PERTURBED: U = |u0| + (sum |pert|) / 4, R = 1.5 U^2, margin 1.5;
- * CHANNEL: U = 4 |u0|, R = 6 |u0|, margin 1 (peak speeds and start-up pressure waves of the channel).
- * Each quantum is rounded to FP32 (the device keeps it in FP32). */
+ * with B_c a bound on |g_i| of class c over the run, from the shifted D2Q9 equilibrium of Sec. 3 and its
+ * first-order non-equilibrium part -3 tau w_i rho Q_i : grad u, given the sample's largest |c_i . u| = U,
+ * velocity gradient G and density deviation R:  B_0 = 4/9 (R + (1 + R) 1.5 U^2),
+ * B_axis = 1/9 (R + (1 + R)(3 U + 6 U^2 + 3 tau G)), B_diag = 1/36 (R + (1 + R)(3 U + 6 U^2 + 6 tau G)).
+ * TGV: U = |u0| + |amp2| + |amp3|, G = k (|u0| + 2 |amp2| + 3 |amp3|) with k = 2 pi / min(nx, ny),
+ * R = 1.5 U^2, margin 1.5; TGV_PERTURBED: U = |u0| + S / 4, G = k (2 |u0| + 1.5 S) with S = sum |pert|,
+ * R = 1.5 U^2, margin 1.5; CHANNEL: U = 4 |u0|, G = U / 2, R = 6 |u0|, margin 1 (peak speeds, obstacle
+ * shear and start-up pressure waves of the channel).  Each quantum is rounded to FP32 (the device keeps
+ * it in FP32). */
 int uqlb_fx16_quanta(const uqlb_sample* s, double* quanta);
 
 /* Staircase obstacle mask of a CHANNEL sample, [ny x nx] bytes (1 = solid). */

@@ -90,36 +90,48 @@ int storage_bytes(int storage) {
 }
 
 // Quanta of the 16-bit fixed-point storage for one sample: d_c = margin B_c / 32767, B_c a bound on
-// |g_i| of velocity class c (rest, axis, diagonal) over the run.  With drho <= R and every
-// |c_i . u| <= U, the shifted equilibrium g_i = w_i (drho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u))
-// obeys |g_0| <= w_0 (R + (1 + R) 1.5 U^2) and |g_i| <= w_i (R + (1 + R)(3 U + 6 U^2)) for i >= 1.
+// |g_i| of velocity class c (rest, axis, diagonal) over the run.  With drho <= R, every |c_i . u| <= U
+// and every velocity-gradient component <= G, the shifted equilibrium
+// g_i^eq = w_i (drho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u)) and the first-order non-equilibrium
+// part -3 tau w_i rho Q_i : grad u (Q_i = c_i c_i - I/3; |Q_i : grad u| <= G on the axes, 2 G on the
+// diagonals, 0 at rest for a divergence-free flow) give
+//   |g_0| <= w_0 (R + (1 + R) 1.5 U^2),  |g_i| <= w_i (R + (1 + R)(3 U + 6 U^2 + 3 tau q_i G)), q_i = 1, 2.
 //   TGV: U = |u0| + |amp2| + |amp3| (each mode keeps |u| + |v| <= its amplitude, and the decaying
-//     flow never exceeds its start), R = 1.5 U^2 (|p| <= u0^2 / 2); margin 1.5 for the
-//     non-equilibrium part, a few per cent of the bound on resolved lattices.
-//   TGV_PERTURBED (Sec. 8.3): U = |u0| + (|zeta_00| + ... + |zeta_11|) / 4, R = 1.5 U^2, margin 1.5.
+//     flow never exceeds its start), G = k (|u0| + 2 |amp2| + 3 |amp3|), k = 2 pi / min(nx, ny),
+//     R = 1.5 U^2 (|p| <= u0^2 / 2); margin 1.5.
+//   TGV_PERTURBED (Sec. 8.3): U = |u0| + S / 4 with S = |zeta_00| + ... + |zeta_11|,
+//     G = k (2 |u0| + 1.5 S), R = 1.5 U^2, margin 1.5.
 //   CHANNEL (Sec. 8.1): U = 4 |u0| (u0 the mean inflow; |u_x| + |u_y| peaks near 2.8 u0 around the
-//     obstacle and in the start-up) and R = 6 |u0| (start-up pressure waves reach |drho| near 2 u0 with
-//     the ramp; an impulsive start gives about sqrt(3) times the inflow peak, doubled on reflection).
+//     obstacle and in the start-up), G = U / 2 (the shear at the staircase obstacle), and R = 6 |u0|
+//     (start-up pressure waves reach |drho| near 2 u0 with the ramp; an impulsive start gives about
+//     sqrt(3) times the inflow peak, doubled on reflection); margin 1.
 // A value beyond the range saturates and the run reports the sample unstable.
 void fx16_quanta(const uqlb_sample& s, double d[3]) {
-    double U, R, margin;
+    double U, G, R, margin;
+    const double k = 2.0 * M_PI / std::max(1, std::min(s.nx, s.ny));
     if (s.kind == UQLB_CASE_CHANNEL) {
         U = 4.0 * std::fabs(s.u0);
+        G = 0.5 * U;
         R = 6.0 * std::fabs(s.u0);
         margin = 1.0;
+    } else if (s.kind == UQLB_CASE_TGV_PERTURBED) {
+        const double S = std::fabs(s.pert[0]) + std::fabs(s.pert[1]) + std::fabs(s.pert[2]) + std::fabs(s.pert[3]);
+        U = std::fabs(s.u0) + 0.25 * S;
+        G = k * (2.0 * std::fabs(s.u0) + 1.5 * S);
+        R = 1.5 * U * U;
+        margin = 1.5;
     } else {
-        U = std::fabs(s.u0);
-        if (s.kind == UQLB_CASE_TGV_PERTURBED)
-            U += 0.25 * (std::fabs(s.pert[0]) + std::fabs(s.pert[1]) + std::fabs(s.pert[2]) + std::fabs(s.pert[3]));
-        else
-            U += std::fabs(s.amp2) + std::fabs(s.amp3);
+        U = std::fabs(s.u0) + std::fabs(s.amp2) + std::fabs(s.amp3);
+        G = k * (std::fabs(s.u0) + 2.0 * std::fabs(s.amp2) + 3.0 * std::fabs(s.amp3));
         R = 1.5 * U * U;
         margin = 1.5;
     }
     U = std::max(U, 1e-6);
+    const double tau = 3.0 * std::max(s.nu, 0.0) + 0.5;
     const double rho = 1.0 + R;
-    const double b[3] = {4.0 / 9.0 * (R + rho * 1.5 * U * U), 1.0 / 9.0 * (R + rho * (3.0 * U + 6.0 * U * U)),
-                         1.0 / 36.0 * (R + rho * (3.0 * U + 6.0 * U * U))};
+    const double b[3] = {4.0 / 9.0 * (R + rho * 1.5 * U * U),
+                         1.0 / 9.0 * (R + rho * (3.0 * U + 6.0 * U * U + 3.0 * tau * G)),
+                         1.0 / 36.0 * (R + rho * (3.0 * U + 6.0 * U * U + 6.0 * tau * G))};
     for (int c = 0; c < 3; ++c) d[c] = (double)(float)(margin * b[c] / 32767.0);
 }
 

@@ -627,6 +627,7 @@ def test_two_step_strips_at_the_widest_rows(ens, storage, nx):
     ref = olbm.run([oracle_case(s, qoi_every=1) for s in specs])
     tol = TOL[storage]
     for i, r in enumerate(ref):
+        assert st["qoi"][i, U.UQLB_QOI_STATUS] == 0, (storage, nx, i)
         assert rel_l2(st["fields"][i, :-1], oracle_row(r)[:-1]) < tol, (storage, nx, i)
         ns = specs[i].steps + 1
         assert np.allclose(st["series"][i, :ns], r.series[:ns], rtol=tol, atol=0), (storage, nx, i)
@@ -810,10 +811,15 @@ def test_strip_kernel_edge_geometries_against_the_oracle(ens, n):
     leaves threads past the row (40), a full block (64) and an odd multiple of 64 (832); heights equal
     to the width, ragged (37) and degenerate (3, 2: the rows above and below a node coincide); step
     counts that end on a single-step launch (61, 1), stop at once (0) or end on a two-step launch
-    (60); K at every step and at a stride of 7."""
+    (60); K at every step and at a stride of 7.  On the 2- and 3-row lattices the Taylor-Green field
+    decays by nu k^2 >= 0.13 per step (k = 2 pi / 3), 1e-4 of its start after 61 steps, where the
+    FP32 round-off of the start no longer sits below 1e-5 of what is left; those run 9 and 8 steps
+    (the same odd and even launch patterns), a decay of at most 10x."""
     heights = (37, 3, 2) if n > 128 else (n, 37, 3, 2)
     for ny in heights:
-        specs = [replace(W.tgv(n, 61, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(n, 60, nu=0.05, amp3=-0.0004), ny=ny),
+        t_odd, t_even = (61, 60) if ny > 3 else (9, 8)
+        specs = [replace(W.tgv(n, t_odd, nu=0.03, amp2=0.0005), ny=ny),
+                 replace(W.tgv(n, t_even, nu=0.05, amp3=-0.0004), ny=ny),
                  replace(W.tgv(n, 1, nu=0.02), ny=ny), replace(W.tgv(n, 0, nu=0.04), ny=ny)]
         for qe in (1, 7):
             g = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme="two_step_strips")
@@ -836,17 +842,18 @@ def test_channel_16_bit_storage_against_the_oracle(ens, storage):
     """16-bit population storage on the channel (one-step kernel): the staircase cylinder with the
     face inlet/outlet, the empty channel, and the Bouzidi cylinder with the interpolated
     inlet/outlet; velocity fields and C_D against the oracle within the 16-bit budget."""
-    specs = [_cyl(6, 600), W.channel(6, steps=600, obstacle=False, steady_tol=0.0, re=5.0),
+    specs = [_cyl(5, 600), W.channel(5, steps=600, obstacle=False, steady_tol=0.0, re=5.0),
              _cyl(5, 601, u_mean=0.044, bc="bouzidi", inout="interpolated")]
     g = _run(ens, specs, storage)
     ref = olbm.run([oracle_case(s) for s in specs])
     for i, r in enumerate(ref):
         err = rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1])
         print(f"channel {storage} sample {i}: fields {err:.3e} C_D {g['qoi'][i, U.UQLB_QOI_CD]:.6f} vs {r.cd:.6f}")
+        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0, (storage, i)
         assert err < TOL[storage], (storage, i, err)
         if specs[i].cyl_r > 0:
             assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < TOL[storage] * abs(r.cd), (storage, i)
-        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0
+
 
 
 def test_fixed_point_storage_reports_a_blown_up_sample(ens):

@@ -28,15 +28,64 @@ sys.path.insert(0, ROOT)
 METRIC = "ensemble MLUPS (tgv256_gpc4d: 625 samples x 256^2 x 2000 steps, FP32 storage, FP64 gPC statistics)"
 UNIT = "MLUPS"
 BYTES_PER_UPDATE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36, "fx16": 36}
-# per scheme: the step kernel, the profile holding its ncu traffic, and the kernel version that
-# profile was taken on (a mismatch reports traffic as null)
-STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in place)", "step_kernel_f32_tgv256.md",
-                    "aa-npt-nbr-pair"),
+# per scheme: the step kernel, its ncu name, and the version of its code; the DRAM traffic per launch
+# comes from profiles/traffic_<name>_<storage>_tgv256.txt (written by --write-traffic from an ncu
+# capture), used only when that file names the same version (else traffic is null)
+STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in place)", "step_kernel", "aa-npt-nbr-pair"),
                 3: ("step2_kernel (two-step tiles: tile + halo collided into shared memory, streamed and "
-                    "collided again, pushed to the other lattice)", "step2_kernel_f32_tgv256.md", "two-step-v2-packed"),
+                    "collided again, pushed to the other lattice)", "step2_kernel", "two-step-v2-packed"),
                 4: ("strip2_kernel (two-step row strips: each row collided into a shared-memory ring, streamed "
-                    "and collided again, pushed to the other lattice)", "strip2_kernel_f32_tgv256.md",
-                    "two-step-strips-v2-staged")}
+                    "and collided again, pushed to the other lattice)", "strip2_kernel", "two-step-strips-v2-staged")}
+
+
+def _traffic_file(kernel: str, storage: str) -> str:
+    return os.path.join(ROOT, "profiles", f"traffic_{kernel}_{storage}_tgv256.txt")
+
+
+def read_traffic(kernel: str, storage: str, version: str):
+    """DRAM bytes per launch of `kernel` at the bench's full size from its machine-written file."""
+    try:
+        with open(_traffic_file(kernel, storage)) as fh:
+            kv = dict(ln.split(None, 1) for ln in fh.read().splitlines() if ln.strip() and not ln.startswith("#"))
+    except OSError:
+        return None
+    if kv.get("kernel_version", "").strip() != version:
+        return None
+    return int(float(kv["traffic_bytes_per_launch_full_size"]))
+
+
+def write_traffic(csv_path: str, kernel: str, storage: str, version: str, samples: int, command: str) -> str:
+    """Parse an ncu CSV (--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    --csv --print-units base) and write the per-launch traffic of `kernel`, scaled from the captured
+    sample count to the bench's 625 samples (every sample has the same size, so the traffic of a
+    launch is proportional to the samples it carries)."""
+    import csv
+
+    rows = list(csv.DictReader(ln for ln in open(csv_path) if ln.startswith('"')))
+    per = {}
+    for r in rows:
+        if kernel not in r.get("Kernel Name", ""):
+            continue
+        key = r.get("ID") or r.get("Id") or r.get("Kernel Name")
+        unit = r.get("Metric Unit", "byte")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1, "usecond": 1e3, "msecond": 1e6}.get(
+            unit, 1)
+        per.setdefault(key, {})[r["Metric Name"]] = float(r["Metric Value"].replace(",", "")) * scale
+    launches = [v for v in per.values() if "dram__bytes_read.sum" in v and "dram__bytes_write.sum" in v]
+    if not launches:
+        raise SystemExit(f"no {kernel} launch with DRAM counters in {csv_path}")
+    rd = sum(v["dram__bytes_read.sum"] for v in launches) / len(launches)
+    wr = sum(v["dram__bytes_write.sum"] for v in launches) / len(launches)
+    full = (rd + wr) * 625 / samples
+    path = _traffic_file(kernel, storage)
+    with open(path, "w") as fh:
+        fh.write(f"# DRAM traffic of {kernel} per launch (ncu), written by bench.py --write-traffic\n"
+                 f"# command: {command}\n"
+                 f"kernel {kernel}\nkernel_version {version}\nstorage {storage}\nlaunches_captured {len(launches)}\n"
+                 f"samples_captured {samples}\ndram_bytes_read_per_launch {rd:.0f}\n"
+                 f"dram_bytes_write_per_launch {wr:.0f}\nscale_to_625_samples {625 / samples:.6f}\n"
+                 f"traffic_bytes_per_launch_full_size {full:.0f}\n")
+    return path
 
 
 def _peaks():
@@ -155,7 +204,7 @@ def bench_reference(args):
     value = upd * len(times) / total / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "tgv256_gpc4d", "samples": 625, "lattice": [256, 256], "time_steps": 2000,
                        "storage": "f64 (CPU oracle)", "l2": "arena larger than L2 (no flush needed)"},
@@ -353,7 +402,8 @@ def bench_workload(args):
                 return rr, ens.stats(rr["fields"], ddof=1) if w.method == "mc" else ens.stats(ens.project(rr["fields"]))
             ms_st, (rr, _) = timed(run_st, 1)
             extra[spec] = {"time_to_stats_s": ms_st / 1e3, "value": upd / (ms_st / 1e3) / 1e6,
-                           "fields": rr["fields"][: min(len(smp), args.oracle_samples)].double().cpu().numpy()}
+                           "fields": rr["fields"][sub].double().cpu().numpy()}
+            del rr
         # plain per-sample FP64 comparator on a subset, scaled by the sample count (halfway
         # bounce-back only)
         if args.plain_samples > 0 and not any(s.obstacle_bc or s.inout_bc for s in smp):
@@ -547,27 +597,37 @@ def bench_gpu(args):
     from paper_2508_13867_gb300 import workloads as W
     from paper_2508_13867_gb300.ensemble import Ensemble, case_struct, opts_struct
 
-    w = W.tgv256_gpc4d()
+    from paper_2508_13867_gb300 import shard
+
+    w = W.tgv256_gpc4d(storage=args.storage if args.storage != "f64" else "f32")
     ens = Ensemble(local)
     ens.setup(w)
     smp = ens.ensemble_samples(w)
     S, K = len(smp), ens.num_terms
     F = 2 * w.base.nx * w.base.ny + 1
     upd_per_step = _updates(smp)
+    # sample-level sharding: this rank's contiguous block, balanced by nodes x steps; the partial
+    # coefficients of the blocks are summed by one all-reduce (the only exchange)
+    lo, hi = shard.partition(shard.sample_costs(smp), world)[rank]
+    block = smp[lo:hi]
     storage = w.storage
     stream = torch.cuda.current_stream()
     dev = f"cuda:{local}"
-    fields = torch.empty((S, F), dtype=torch.float32, device=dev)
-    qoi = torch.empty((S, U.UQLB_QOI_COLS), dtype=torch.float64, device=dev)
+    fields = torch.empty((hi - lo, F), dtype=torch.float32, device=dev)
+    qoi = torch.empty((hi - lo, U.UQLB_QOI_COLS), dtype=torch.float64, device=dev)
     coeffs = torch.empty((K, F), dtype=torch.float64, device=dev)
     out = {"fields": fields, "qoi": qoi}
 
-    tuned = (ens.autotune(smp, storage=storage, trial_steps=args.tune_steps, scheme=args.scheme)
+    tuned = (ens.autotune(block, storage=storage, trial_steps=args.tune_steps, scheme=args.scheme)
              if args.tune_steps > 0 else None)
 
     def one_step():
-        ens.run_batch(smp, storage=storage, fields_dtype="f32", out=out, scheme=args.scheme)
-        ens.project(fields, coeffs)
+        ens.run_batch(block, storage=storage, fields_dtype="f32", out=out, scheme=args.scheme)
+        if world > 1:
+            ens.project_block(fields, lo, coeffs)
+            dist.all_reduce(coeffs, op=dist.ReduceOp.SUM)
+        else:
+            ens.project(fields, coeffs)
         return ens.stats(coeffs)
 
     for _ in range(args.warmup):
@@ -610,27 +670,38 @@ def bench_gpu(args):
     # every population once (72 B per FP32 node); the two-step kernel advances two steps per launch.
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
     steps_per_launch = 1 if scheme == U.UQLB_SCHEME_ONE_STEP else 2
-    kernel_name, prof_name, kernel_version = STEP_KERNELS[scheme]
-    nodes = S * w.base.nx * w.base.ny
+    kernel_name, ncu_name, kernel_version = STEP_KERNELS[scheme]
+    nodes = (hi - lo) * w.base.nx * w.base.ny
     per_launch_bytes = BYTES_PER_UPDATE[storage] * nodes
     step_kernel_ms = loop_ms / max(loop_steps / steps_per_launch, 1)
     achieved = per_launch_bytes / (step_kernel_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", prof_name)
-    if storage == "f32" and os.path.exists(prof):
-        import re
+    traffic = read_traffic(ncu_name, storage, kernel_version)
+    if traffic is not None and world > 1:
+        traffic = int(traffic * (hi - lo) / S)
 
-        with open(prof) as fh:
-            text = fh.read()
-        ver = re.search(r"^kernel_version: (\S+)", text, flags=re.M)
-        tb = re.search(r"^traffic_bytes_per_launch_full_size: (\d+)", text, flags=re.M)
-        if ver and tb and ver.group(1) == kernel_version:
-            traffic = int(tb.group(1))
-
-    # end to end through host buffers: one C call, tables in, statistics out
+    # end to end through host buffers: one C call, tables in, statistics out (one GPU); the sharded
+    # pass through the public calls with the statistics copied to the host (several GPUs)
     e2e = None
-    if rank == 0:
+    if world > 1:
+        mean_pin = torch.empty(F, dtype=torch.float64, pin_memory=True)
+        var_pin = torch.empty(F, dtype=torch.float64, pin_memory=True)
+        reps = max(1, min(args.steps, 3))
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mean_d, var_d = one_step()
+            mean_pin.copy_(mean_d, non_blocking=True)
+            var_pin.copy_(var_d, non_blocking=True)
+            torch.cuda.synchronize()
+        el = torch.tensor([(time.perf_counter() - t0) / reps], dtype=torch.float64, device=dev)
+        dist.all_reduce(el, op=dist.ReduceOp.MAX)
+        e2e_s = float(el.item())
+        e2e = {"value": upd_per_step / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": (hi - lo) * (128 + 32 + 4),
+               "d2h_bytes_per_step": 2 * F * 8, "seconds_per_step": e2e_s,
+               "path": "sharded pass: uqlb_run_batch of the rank's block, uqlb_project_block, one NCCL all-reduce, "
+                       "uqlb_stats, statistics copied to pinned host memory"}
+    elif rank == 0:
         mean_h = np.zeros(F)
         var_h = np.zeros(F)
         case = case_struct(w)
@@ -652,7 +723,7 @@ def bench_gpu(args):
 
     # comparator: plain per-sample FP64 path on a subset, time to the same gPC statistics
     plain = None
-    if args.plain_samples > 0:
+    if args.plain_samples > 0 and rank == 0:
         sub = smp[: args.plain_samples]
         res = ens.run_plain_f64(sub, qoi_every=0, fields=True)
         torch.cuda.synchronize()
@@ -682,11 +753,12 @@ def bench_gpu(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "scaling": "strong", "vs_baseline": None, "dtype": storage,
                 "data": "synthetic (seeded 4-D Taylor-Green ensemble)",
                 "config": {"workload": "tgv256_gpc4d", "samples": S, "lattice": [256, 256], "time_steps": 2000,
                            "storage": storage, "statistics": "fp64", "gpc_terms": K,
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "parallelism": (f"sample blocks x{world} (NCCL all-reduce of the partial gPC "
+                                           "coefficients)" if world > 1 else "single GPU"),
                            "l2": "lattice arena 1.47 GB > L2 129 MB: each launch streams from HBM",
                            "scheme": {U.UQLB_SCHEME_ONE_STEP: "one_step", U.UQLB_SCHEME_TWO_STEP_TILES: "two_step_tiles",
                                       U.UQLB_SCHEME_TWO_STEP_STRIPS: "two_step_strips"}[scheme],
@@ -697,6 +769,14 @@ def bench_gpu(args):
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                              "kernel": kernel_name, "time_steps_per_launch": steps_per_launch,
                              "algorithmic_bytes_per_launch": per_launch_bytes,
+                             "bytes_per_update": per_launch_bytes / (nodes * steps_per_launch),
+                             "bytes_per_update_one_step": BYTES_PER_UPDATE[storage],
+                             "frac_at_one_step_bytes": achieved * steps_per_launch / peak,
+                             "note": (f"achieved = the scheme's algorithmic bytes per launch ({BYTES_PER_UPDATE[storage]} B "
+                                      f"per node: every population read and written once per launch, "
+                                      f"{steps_per_launch} node update(s) per launch) / event-timed kernel time; "
+                                      "frac_at_one_step_bytes counts the one-step scheme's "
+                                      f"{BYTES_PER_UPDATE[storage]} B for every node update"),
                              "kernel_ms_per_launch": step_kernel_ms},
                 "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
                 "plain_f64": plain}
@@ -752,8 +832,16 @@ def main():
     ap.add_argument("--inflow-spread", type=float, default=0.2, help="cylinder_uq_compare: relative inflow spread")
     ap.add_argument("--n", type=int, default=0, help="tgv512_mc4d: lattice size override")
     ap.add_argument("--n-mc", type=int, default=0, help="tgv512_mc4d: sample count override")
+    ap.add_argument("--write-traffic", default="", help="ncu CSV of a --kernel-only capture: write the traffic file")
+    ap.add_argument("--traffic-kernel", default="strip2_kernel")
+    ap.add_argument("--traffic-command", default="")
     ap.add_argument("--time-steps-full", type=int, default=0, help="tgv512_mc4d: step count override")
     args = ap.parse_args()
+    if args.write_traffic:
+        ver = {k[1]: k[2] for k in STEP_KERNELS.values()}[args.traffic_kernel]
+        print(write_traffic(args.write_traffic, args.traffic_kernel, args.storage, ver, args.samples,
+                            args.traffic_command))
+        return 0
     if args.impl == "reference":
         return bench_reference(args)
     if args.kernel_only:

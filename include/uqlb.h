@@ -458,6 +458,30 @@ int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, 
 int uqlb_project_noalloc(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,
                          double* coeffs_dev, void* stream);
 
+/* Sample-level parallelism across GPUs (the paper's Sec. 9 hybrid parallelism runs samples
+ * independently; the statistics are its only exchange).  A sharded run gives each GPU a contiguous
+ * block of samples s0 .. s0 + count - 1 of the context's sample set (uqlb_ensemble_samples lists
+ * them; uqlb_run_batch runs the block, whose rows are then 0 .. count - 1), and:
+ *   gPC: uqlb_project_block forms the block's partial coefficients
+ *     partial[k, f] = sum_{s < count} W[k, s0 + s] M[s, f] (Eq. coef_discrete restricted to the
+ *     block, FP64); the coefficients are linear in the samples, so the sum of the partials of blocks
+ *     that cover 0 .. S - 1 (one all-reduce) equals uqlb_project's, and uqlb_stats then gives the
+ *     mean and variance.  m_dev: [count x n_fields] (row stride m_ld) in dtype F64 or F32;
+ *     coeffs_dev: FP64 [K x n_fields]; the workspace is uqlb_post_workspace_bytes.  Synchronises
+ *     `stream` after the weight upload.  UQLB_ERR_ARG for a block outside 0 .. S - 1.
+ *   MC: uqlb_block_moments gives the block's mean[f] (Eq. meanMCS over its n_rows rows) and
+ *     m2[f] = sum over the rows of (M[s, f] - mean[f])^2 (two passes, FP64); blocks merge exactly by the
+ *     pairwise update of Chan, Golub and LeVeque (n = n_a + n_b, delta = mean_b - mean_a,
+ *     mean = mean_a + delta n_b / n, m2 = m2_a + m2_b + delta^2 n_a n_b / n), and Eq. varMCS is
+ *     m2 / (N - ddof).  The call needs no sample set (any context serves).
+ * uqlb_get_weight_block copies the block's columns of W to the host, [K x count], as
+ * uqlb_project_block uploads them. */
+int uqlb_get_weight_block(const uqlb_ctx* ctx, int64_t s0, int64_t count, double* w);
+int uqlb_project_block(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld, int64_t s0,
+                       int64_t count, double* coeffs_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+int uqlb_block_moments(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_rows, int64_t n_fields, int64_t m_ld,
+                       double* mean_dev, double* m2_dev, void* stream);
+
 /* Statistics per field, FP64 outputs mean_dev[n_fields], var_dev[n_fields].
  *   gPC context: input is coeffs_dev [K x n_fields] FP64; mean = c_0 (Eq. gpc_mean),
  *     var = sum_{k >= 1} c_k^2 (Eq. gpc_std squared); dtype must be UQLB_F64, ddof ignored.

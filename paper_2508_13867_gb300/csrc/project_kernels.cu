@@ -81,6 +81,7 @@ __global__ void gpc_stats_kernel(const double* __restrict__ C, int K, int64_t F,
     }
 }
 
+// ddof < 0: var receives the sum of squared deviations itself (M2 of a block, for merging blocks).
 template <typename M>
 __global__ void mc_stats_kernel(const M* __restrict__ m, int64_t S, int64_t F, int64_t ld, double* mean,
                                 double* var, int ddof) {
@@ -94,7 +95,7 @@ __global__ void mc_stats_kernel(const M* __restrict__ m, int64_t S, int64_t F, i
             ss = fma(d, d, ss);
         }
         if (mean) mean[f] = mu;
-        if (var) var[f] = (S - ddof) > 0 ? ss / (double)(S - ddof) : NAN;
+        if (var) var[f] = ddof < 0 ? ss : ((S - ddof) > 0 ? ss / (double)(S - ddof) : NAN);
     }
 }
 

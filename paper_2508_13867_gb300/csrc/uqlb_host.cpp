@@ -41,6 +41,7 @@ struct uqlb_ctx {
     int order = 0, basis = 0, K = 0;
     std::vector<int32_t> alpha;
     std::vector<double> W;
+    std::vector<double> w_block;  // host staging of the W columns of a sample block (uqlb_project_block)
     cudaStream_t capture_stream = nullptr;
     std::vector<GraphEntry> graphs;
     cudaEvent_t loop_begin = nullptr, loop_end = nullptr;
@@ -1713,6 +1714,58 @@ int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, 
     e = launch_project(static_cast<const double*>(workspace_dev), ctx->K, (int)ctx->S, m_dev, dtype, n_fields, m_ld,
                        coeffs_dev, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "project: launch");
+    return 0;
+}
+
+int uqlb_get_weight_block(const uqlb_ctx* ctx, int64_t s0, int64_t count, double* w) {
+    if (!ctx || !w) return set_err(nullptr, UQLB_ERR_ARG, "get_weight_block: null pointer");
+    if (ctx->method != UQLB_METHOD_GPC)
+        return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_STATE, "get_weight_block: call uqlb_init_gpc first");
+    if (s0 < 0 || count < 1 || s0 + count > ctx->S)
+        return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_ARG, "get_weight_block: block outside the sample set");
+    for (int k = 0; k < ctx->K; ++k)
+        std::memcpy(w + (size_t)k * count, ctx->W.data() + (size_t)k * ctx->S + s0, (size_t)count * sizeof(double));
+    return 0;
+}
+
+int uqlb_project_block(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld, int64_t s0,
+                       int64_t count, double* coeffs_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (ctx->method != UQLB_METHOD_GPC) return set_err(ctx, UQLB_ERR_STATE, "project_block: call uqlb_init_gpc first");
+    if (!m_dev || !coeffs_dev || !workspace_dev || n_fields < 0 || m_ld < n_fields)
+        return set_err(ctx, UQLB_ERR_ARG, "project_block: bad arguments");
+    if (s0 < 0 || count < 1 || s0 + count > ctx->S)
+        return set_err(ctx, UQLB_ERR_ARG, "project_block: block [%lld, %lld) outside the %lld samples", (long long)s0,
+                       (long long)(s0 + count), (long long)ctx->S);
+    if (dtype != UQLB_F64 && dtype != UQLB_F32) return set_err(ctx, UQLB_ERR_ARG, "project_block: dtype must be F64 or F32");
+    size_t need = 0;
+    uqlb_post_workspace_bytes(ctx, &need);
+    if (workspace_bytes < need)
+        return set_err(ctx, UQLB_ERR_OOM, "project_block: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    // the block's columns of W, compacted to [K x count] (the kernel reads rows of stride count)
+    ctx->w_block.resize((size_t)ctx->K * count);
+    uqlb_get_weight_block(ctx, s0, count, ctx->w_block.data());
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(workspace_dev, ctx->w_block.data(), ctx->w_block.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project_block: W upload");
+    // the upload reads the host copy asynchronously: keep it until the copy is done
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "project_block: W upload");
+    e = launch_project(static_cast<const double*>(workspace_dev), ctx->K, (int)count, m_dev, dtype, n_fields, m_ld,
+                       coeffs_dev, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "project_block: launch");
+    return 0;
+}
+
+int uqlb_block_moments(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_rows, int64_t n_fields, int64_t m_ld,
+                       double* mean_dev, double* m2_dev, void* stream) {
+    if (int rc = check_ctx(ctx)) return rc;
+    if (!m_dev || !mean_dev || !m2_dev || n_rows < 1 || n_fields < 0 || m_ld < n_fields)
+        return set_err(ctx, UQLB_ERR_ARG, "block_moments: bad arguments");
+    if (dtype != UQLB_F64 && dtype != UQLB_F32) return set_err(ctx, UQLB_ERR_ARG, "block_moments: dtype must be F64 or F32");
+    cudaError_t e = launch_mc_stats(m_dev, dtype, n_rows, n_fields, m_ld, mean_dev, m2_dev, -1,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "block_moments: launch");
     return 0;
 }
 

@@ -195,6 +195,29 @@ class Ensemble:
                        self._post.numel(), _stream())
         return coeffs
 
+    def project_block(self, m: torch.Tensor, s0: int, coeffs: torch.Tensor | None = None) -> torch.Tensor:
+        """Partial coefficients of the sample block s0 .. s0 + len(m) - 1 (rows of m)."""
+        dtype = U.UQLB_F64 if m.dtype == torch.float64 else U.UQLB_F32
+        F = m.shape[1]
+        if coeffs is None:
+            coeffs = torch.empty((self.num_terms, F), dtype=torch.float64, device=m.device)
+        wsb = U.uqlb_post_workspace_bytes(self.ctx)
+        if not hasattr(self, "_post") or self._post.numel() < wsb:
+            self._post = torch.empty(max(wsb, 256), dtype=torch.uint8, device=m.device)
+        U.uqlb_project_block(self.ctx, m.data_ptr(), dtype, F, m.stride(0), s0, m.shape[0], coeffs.data_ptr(),
+                             self._post.data_ptr(), self._post.numel(), _stream())
+        return coeffs
+
+    def block_moments(self, m: torch.Tensor):
+        """(rows, mean, sum of squared deviations) of the rows of m, for merging sample blocks."""
+        dtype = U.UQLB_F64 if m.dtype == torch.float64 else U.UQLB_F32
+        F = m.shape[1]
+        mean = torch.empty(F, dtype=torch.float64, device=m.device)
+        m2 = torch.empty(F, dtype=torch.float64, device=m.device)
+        U.uqlb_block_moments(self.ctx, m.data_ptr(), dtype, m.shape[0], F, m.stride(0), mean.data_ptr(), m2.data_ptr(),
+                             _stream())
+        return m.shape[0], mean, m2
+
     def stats(self, x: torch.Tensor, ddof: int = 1):
         """gPC context: x = coefficients [K x F]; MC context: x = fields M [S x F]."""
         dtype = U.UQLB_F64 if x.dtype == torch.float64 else U.UQLB_F32

@@ -54,8 +54,23 @@ def merge_gpc_coefficients(partial: torch.Tensor) -> torch.Tensor:
     return partial
 
 
+def chan_merge(blocks):
+    """Combine (count, mean, sum of squared deviations) of consecutive sample blocks, in order, by
+    the pairwise update of Chan, Golub and LeVeque.  Returns (N, mean, M2)."""
+    na, ma, qa = blocks[0][0], blocks[0][1].clone(), blocks[0][2].clone()
+    for nb, mb, qb in blocks[1:]:
+        if nb == 0:
+            continue
+        nt = na + nb
+        delta = mb - ma
+        ma = ma + delta * (nb / nt)
+        qa = qa + qb + delta * delta * (na * nb / nt)
+        na = nt
+    return int(na), ma, qa
+
+
 def merge_mc_moments(n: int, mean: torch.Tensor, m2: torch.Tensor):
-    """Combine per-rank (count, mean, sum of squared deviations) into the global ones.
+    """Combine per-rank (count, mean, sum of squared deviations) into the global ones, in rank order.
 
     Returns (N, mean, M2); the variance with divisor N - ddof is M2 / (N - ddof)."""
     world = _world()
@@ -67,14 +82,26 @@ def merge_mc_moments(n: int, mean: torch.Tensor, m2: torch.Tensor):
     dist.all_gather(counts, torch.tensor([float(n)], dtype=torch.float64, device=mean.device))
     dist.all_gather(means, mean.contiguous())
     dist.all_gather(m2s, m2.contiguous())
-    na, ma, qa = float(counts[0].item()), means[0].clone(), m2s[0].clone()
-    for r in range(1, world):
-        nb, mb, qb = float(counts[r].item()), means[r], m2s[r]
-        if nb == 0:
-            continue
-        nt = na + nb
-        delta = mb - ma
-        ma = ma + delta * (nb / nt)
-        qa = qa + qb + delta * delta * (na * nb / nt)
-        na = nt
-    return int(na), ma, qa
+    return chan_merge([(float(counts[r].item()), means[r], m2s[r]) for r in range(world)])
+
+
+def run_block(ens, w, rank: int, world: int, storage: str | None = None, fields_dtype: str = "f32", ddof: int = 1,
+              out: dict | None = None) -> dict:
+    """The sharded UQ pass of one rank: its block of the workload's samples through the library
+    (run, then the block projection or block moments), the one exchange, and the statistics.
+    `ens` has been set up for the workload (the full sample set); returns the block's outputs and
+    the merged mean and variance fields (on every rank)."""
+    smp = ens.ensemble_samples(w)
+    lo, hi = partition(sample_costs(smp), world)[rank]
+    res = ens.run_batch(smp[lo:hi], storage=storage or w.storage, fields_dtype=fields_dtype, qoi_every=w.qoi_every,
+                        out=out)
+    m = res["fields"]
+    if w.method == "gpc":
+        coeffs = merge_gpc_coefficients(ens.project_block(m, lo, res.get("coeffs")))
+        res["coeffs"] = coeffs
+        res["mean"], res["var"] = ens.stats(coeffs)
+    else:
+        n, mean, m2 = merge_mc_moments(*ens.block_moments(m))
+        res["mean"], res["var"] = mean, m2 / (n - ddof)
+    res["block"] = (lo, hi)
+    return res

@@ -110,6 +110,11 @@ _SIGNATURES = {
     "uqlb_post_workspace_bytes": [c_void_p, _P(c_size_t)],
     "uqlb_project": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, c_size_t, c_void_p],
     "uqlb_project_noalloc": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p],
+    "uqlb_get_weight_block": [c_void_p, c_int64, c_int64, _P(c_double)],
+    "uqlb_project_block": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_int64, c_int64, c_void_p, c_void_p,
+                           c_size_t, c_void_p],
+    "uqlb_block_moments": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_int64, c_void_p, c_void_p,
+                           c_void_p],
     "uqlb_stats": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, ctypes.c_int,
                    c_void_p],
     "uqlb_uq_workspace_bytes": [c_void_p, _P(uqlb_case), _P(uqlb_run_opts), _P(c_size_t)],
@@ -281,6 +286,12 @@ def uqlb_get_weight_matrix(ctx) -> np.ndarray:
     return w
 
 
+def uqlb_get_weight_block(ctx, s0: int, count: int) -> np.ndarray:
+    w = np.zeros((uqlb_num_terms(ctx), count))
+    _check(lib().uqlb_get_weight_block(ctx, s0, count, _dp(w)), ctx)
+    return w
+
+
 # ---- runs -------------------------------------------------------------------------------
 
 def _samples_array(samples):
@@ -395,6 +406,18 @@ def uqlb_project(ctx, m_dev: int, dtype: int, n_fields: int, m_ld: int, coeffs_d
                  workspace_bytes: int, stream=None) -> None:
     _check(lib().uqlb_project(ctx, c_void_p(m_dev), dtype, n_fields, m_ld, c_void_p(coeffs_dev),
                               c_void_p(workspace_dev), workspace_bytes, _stream(stream)), ctx)
+
+
+def uqlb_project_block(ctx, m_dev: int, dtype: int, n_fields: int, m_ld: int, s0: int, count: int, coeffs_dev: int,
+                       workspace_dev: int, workspace_bytes: int, stream=None) -> None:
+    _check(lib().uqlb_project_block(ctx, c_void_p(m_dev), dtype, n_fields, m_ld, s0, count, c_void_p(coeffs_dev),
+                                    c_void_p(workspace_dev), workspace_bytes, _stream(stream)), ctx)
+
+
+def uqlb_block_moments(ctx, m_dev: int, dtype: int, n_rows: int, n_fields: int, m_ld: int, mean_dev: int,
+                       m2_dev: int, stream=None) -> None:
+    _check(lib().uqlb_block_moments(ctx, c_void_p(m_dev), dtype, n_rows, n_fields, m_ld, c_void_p(mean_dev),
+                                    c_void_p(m2_dev), _stream(stream)), ctx)
 
 
 def uqlb_project_noalloc(ctx, m_dev: int, dtype: int, n_fields: int, m_ld: int, coeffs_dev: int,

@@ -35,7 +35,11 @@ STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in plac
                 3: ("step2_kernel (two-step tiles: tile + halo collided into shared memory, streamed and "
                     "collided again, pushed to the other lattice)", "step2_kernel", "two-step-v2-packed"),
                 4: ("strip2_kernel (two-step row strips: each row collided into a shared-memory ring, streamed "
-                    "and collided again, pushed to the other lattice)", "strip2_kernel", "two-step-strips-v2-staged")}
+                    "and collided again, pushed to the other lattice)", "strip2_kernel", "two-step-strips-v2-staged"),
+                6: ("strip3_kernel (three-step row strips: each row collided into a first shared-memory ring, "
+                    "streamed and collided into a second, streamed and collided again, pushed to the other "
+                    "lattice)", "strip3_kernel", "three-step-strips-v1")}
+STEPS_PER_LAUNCH = {1: 1, 3: 2, 4: 2, 6: 3}
 
 
 def _traffic_file(kernel: str, storage: str) -> str:
@@ -242,7 +246,7 @@ def bench_kernel_only(args):
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
-    per_launch = 1 if scheme == U.UQLB_SCHEME_ONE_STEP else 2
+    per_launch = STEPS_PER_LAUNCH[scheme]
     nodes = sum(s.nx * s.ny for s in smp)
     gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st / per_launch, 1) / 1e3) / 1e9
     print(json.dumps({"kernel_only": True, "mode": args.mode, "scheme": scheme, "tile": [g_rows, g_npt],
@@ -567,7 +571,7 @@ def bench_workload(args):
         line.update({"samples": len(smp), "value": upd / (ms / 1e3) / 1e6, "batch_seconds": ms / 1e3,
                      "tile_geometry": tuned, "scheme": args.scheme,
                      "ran_as": {0: "auto", 1: "one_step", 3: "two_step_tiles", 4: "two_step_strips",
-                                5: "groups"}[U.uqlb_last_run_geometry(ens.ctx)[0]]})
+                                5: "groups", 6: "three_step_strips"}[U.uqlb_last_run_geometry(ens.ctx)[0]]})
         if args.plain_samples > 0:
             step = max(1, len(smp) // args.plain_samples)
             psub = smp[::step]
@@ -669,7 +673,7 @@ def bench_gpu(args):
     # roofline of the dominant kernel, from its event-timed loop.  One launch reads and writes
     # every population once (72 B per FP32 node); the two-step kernel advances two steps per launch.
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
-    steps_per_launch = 1 if scheme == U.UQLB_SCHEME_ONE_STEP else 2
+    steps_per_launch = STEPS_PER_LAUNCH[scheme]
     kernel_name, ncu_name, kernel_version = STEP_KERNELS[scheme]
     nodes = (hi - lo) * w.base.nx * w.base.ny
     per_launch_bytes = BYTES_PER_UPDATE[storage] * nodes
@@ -761,7 +765,8 @@ def bench_gpu(args):
                                            "coefficients)" if world > 1 else "single GPU"),
                            "l2": "lattice arena 1.47 GB > L2 129 MB: each launch streams from HBM",
                            "scheme": {U.UQLB_SCHEME_ONE_STEP: "one_step", U.UQLB_SCHEME_TWO_STEP_TILES: "two_step_tiles",
-                                      U.UQLB_SCHEME_TWO_STEP_STRIPS: "two_step_strips"}[scheme],
+                                      U.UQLB_SCHEME_TWO_STEP_STRIPS: "two_step_strips",
+                                      U.UQLB_SCHEME_THREE_STEP_STRIPS: "three_step_strips"}[scheme],
                            "tile_geometry": None if tuned is None else
                            {"tile_rows": tuned["tile_rows"], "nodes_per_thread": tuned["nodes_per_thread"],
                             "autotune_ms_per_step": {f"{r}x{q}": round(ms, 4) for r, q, ms in tuned["tried"]}}},
@@ -807,7 +812,7 @@ def main():
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
     ap.add_argument("--scheme", default="auto",
-                    choices=["auto", "one_step", "two_step", "two_step_tiles", "two_step_strips"],
+                    choices=["auto", "one_step", "two_step", "two_step_tiles", "two_step_strips", "three_step_strips"],
                     help="time-stepping scheme (auto: two-step for periodic FP32/16-bit batches)")
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent"],
                     help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")

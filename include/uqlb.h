@@ -230,7 +230,8 @@ enum {
     UQLB_SCHEME_TWO_STEP = 2,
     UQLB_SCHEME_TWO_STEP_TILES = 3,
     UQLB_SCHEME_TWO_STEP_STRIPS = 4,
-    UQLB_SCHEME_GROUPED = 5 /* reported only: the batch ran as groups (UQLB_SCHEME_AUTO) */
+    UQLB_SCHEME_GROUPED = 5, /* reported only: the batch ran as groups (UQLB_SCHEME_AUTO) */
+    UQLB_SCHEME_THREE_STEP_STRIPS = 6
 };
 
 /* Execution of the time loop.
@@ -276,7 +277,8 @@ int uqlb_unit_converter(int n, double ma, double re, double* dx, double* dt, dou
  * B_axis = 1/9 (R + (1 + R)(3 U + 6 U^2 + 3 tau G)), B_diag = 1/36 (R + (1 + R)(3 U + 6 U^2 + 6 tau G)).
  * TGV: U = |u0| + |amp2| + |amp3|, G = k (|u0| + 2 |amp2| + 3 |amp3|) with k = 2 pi / min(nx, ny),
  * R = 1.5 U^2, margin 1.5; TGV_PERTURBED: U = |u0| + S / 4, G = k (2 |u0| + 1.5 S) with S = sum |pert|,
- * R = 1.5 U^2, margin 1.5; CHANNEL: U = 4 |u0|, G = U / 2, R = 6 |u0|, margin 1 (peak speeds, obstacle
+ * R = 1.5 U^2, margin 1.5 (with nx != ny the initial field is not divergence-free and its acoustic waves
+ * need R = 2 sqrt(3) U); CHANNEL: U = 4 |u0|, G = U / 2, R = 6 |u0|, margin 1 (peak speeds, obstacle
  * shear and start-up pressure waves of the channel).  Each quantum is rounded to FP32 (the device keeps
  * it in FP32). */
 int uqlb_fx16_quanta(const uqlb_sample* s, double* quanta);

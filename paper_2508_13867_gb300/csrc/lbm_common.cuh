@@ -41,6 +41,7 @@ struct KParams {
     int32_t dt;
     int32_t max_steps;
     int32_t stochastic;  // 16-bit storage: stochastic rounding of every population store
+    int32_t spl;         // time steps per launch of the multi-step schemes (2 or 3)
     // outputs
     void* fields;
     int64_t fields_ld;

@@ -730,10 +730,14 @@ __global__ void __launch_bounds__(kTileCols* TR) persistent_kernel(KParams p, in
 // so at the launch of step t (t - t0 even, t0 the run's first step) a sample's state is on
 // lattice sel ^ ((t - t0) / 2 & 1).
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int launches_of(int t_end, int t0) { return t_end > t0 ? (t_end - t0 + 1) >> 1 : 0; }
+// Launches of a run started at step t0 that a sample ending at step t_end takes part in (spl steps
+// per launch; a sample's last launch may run fewer).
+__device__ __forceinline__ int launches_of(int t_end, int t0, int spl) {
+    return t_end > t0 ? (t_end - t0 + spl - 1) / spl : 0;
+}
 
 __device__ __forceinline__ bool on_final_second(const KParams& p, int slot, int T) {
-    return ((p.sel[slot] ^ launches_of(T, (int)p.step_counter[1])) & 1) != 0;
+    return ((p.sel[slot] ^ launches_of(T, (int)p.step_counter[1], p.spl)) & 1) != 0;
 }
 
 // Tuning of the two-step kernel (measured on the 625 x 256^2 FP32 ensemble): nodes per load
@@ -1329,6 +1333,307 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Three steps per launch by row strips (periodic batches of one width).
+// ------------------------------------------------------------------------------------------
+// The same walk as strip2_kernel with one more collision per node: for row y of its range a block
+// collides row y + 2 at step t into ring 1 (phase A), waits, gathers row y + 1 of step t + 1 from
+// rows y .. y + 2 of ring 1, collides it into ring 2 (phase B), waits, then gathers row y of step
+// t + 2 from rows y - 1 .. y + 1 of ring 2, collides it and pushes it into the other lattice
+// (phase C).  Each piece (the rows of one sample in one block's range) starts with four extra
+// phase-A rows and two extra phase-B rows, so a launch collides (3L + 6) / 3L nodes per node of an
+// L-row piece and moves every population through HBM once per three steps (24 B per FP32 node
+// update against 36 B with two steps per launch).  A sample with fewer than three steps left runs
+// two (phases A and B, B pushing) or one (collide and push) in its last launch.
+//
+// Rings: population i of a row is read by the next phase at row y + c_iy.  With two barriers per
+// iteration, every read of a ring precedes (through a barrier) the next iteration's writes to it, so
+// the c_iy = +1 group needs 3 slots, c_iy = 0 two and c_iy = -1 one: 6 slots of 3 planes per ring.
+constexpr int kRing3Planes = 18;
+
+// Plane of direction i for the row with index q (q >= 0: rows counted from a fixed origin below the
+// piece) in a ring of 3 / 2 / 1 slots per group.
+__device__ __forceinline__ int ring3_plane(int i, int q) {
+    switch (i) {
+        case 2: return (q % 3) * 3 + 0;
+        case 5: return (q % 3) * 3 + 1;
+        case 6: return (q % 3) * 3 + 2;
+        case 0: return 9 + (q & 1) * 3 + 0;
+        case 1: return 9 + (q & 1) * 3 + 1;
+        case 3: return 9 + (q & 1) * 3 + 2;
+        case 4: return 15;
+        case 7: return 16;
+        default: return 17;
+    }
+}
+
+template <typename S>
+struct Strip3Tune {
+    static constexpr int depth = StripTune<S>::depth;  // staged phase-A rows
+    static constexpr int carveout_kb = StripTune<S>::carveout_kb;
+    static constexpr int max_nx_raw = (232448 - 2048) / (2 * kRing3Planes * 4 + depth * 9 * (int)sizeof(S)) / 64 * 64;
+    static constexpr int max_nx = max_nx_raw < 2048 ? max_nx_raw : 2048;
+};
+
+template <typename S, bool GENERIC>
+__global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
+    extern __shared__ __align__(16) unsigned char s4_raw[];
+    __shared__ __align__(16) SampleDev s_sp;
+    __shared__ int s_j, s_rows, s_nact, s_flag;
+    const int tid = threadIdx.x, np = blockDim.x;
+    const int rw = 2 * np;
+    float* ring1 = reinterpret_cast<float*>(s4_raw);  // [kRing3Planes][rw]
+    float* ring2 = ring1 + kRing3Planes * rw;         // [kRing3Planes][rw]
+    double* s_red = reinterpret_cast<double*>(s4_raw);  // block sums: the rings, once a piece is done
+    S* stage = reinterpret_cast<S*>(ring2 + kRing3Planes * rw);  // [D][9][rw]
+    const int t = (int)p.step_counter[0] + p.dt;
+    const int t0 = (int)p.step_counter[1];
+    if (tid == 0) {
+        const int nact = active_samples(p, t);
+        s_nact = nact;
+        s_rows = p.row_base[nact];
+    }
+    __syncthreads();
+    const int nact = s_nact, rows = s_rows;
+    const int per = (rows + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+    const bool series = p.qoi_every > 0 && p.series != nullptr;
+    const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    const int nx = GENERIC ? __ldg(&p.samples[0].nx) : rw;
+    const int x = 2 * tid;
+    const bool va = !GENERIC || x < nx, vb = !GENERIC || x + 1 < nx;
+    const int xl = x == 0 ? nx - 1 : x - 1;
+    const int xar = GENERIC && x + 1 >= nx ? x + 1 - nx : x + 1;
+    const int xbr = x + 2 >= nx ? x + 2 - nx : x + 2;
+    constexpr int D = Strip3Tune<S>::depth;
+    for (int r = r0; r < r1;) {
+        __syncthreads();  // the previous piece's ring reads and block sums are done
+        if (tid == 0) {
+            int lo = 0, hi = nact - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.row_base[mid] <= r)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_j = lo;
+        }
+        __syncthreads();
+        const int j = s_j;
+        if (tid < 32) reinterpret_cast<uint32_t*>(&s_sp)[tid] = __ldg(reinterpret_cast<const uint32_t*>(p.samples + j) + tid);
+        __syncthreads();
+        const int rb = p.row_base[j];
+        const int ny = s_sp.ny, pitch = s_sp.pitch, plane = (int)s_sp.plane;
+        const int ya = r - rb, yb = min(ny, r1 - rb);
+        r = rb + yb;
+        const int n = min(3, s_sp.steps - t);  // steps of this launch for this sample (>= 1)
+        bool want[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) want[k] = series && k < n && ((t + k) % p.qoi_every) == 0;
+        const bool second = ((p.sel[s_sp.slot] ^ ((t - t0) / 3)) & 1) != 0;
+        const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + s_sp.f_off;
+        S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off;
+        const float omega = (float)s_sp.omega;
+        const uint32_t sid = (uint32_t)s_sp.sample_id;
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
+        double red[3] = {0.0, 0.0, 0.0};
+        // periodic row of a phase-A row (at most two rows outside the sample; samples have >= 2 rows,
+        // two corrections each way keep any height in range)
+        auto wrap = [&](int y) {
+            y += y < 0 ? ny : 0;
+            y += y < 0 ? ny : 0;
+            y -= y >= ny ? ny : 0;
+            y -= y >= ny ? ny : 0;
+            return y;
+        };
+        // push of the pair's post-collision populations g (step ts, row y) into dst
+        auto push = [&](int y, int ts, const f2 (&g)[9]) {
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const int row[3] = {ym * pitch, y * pitch, yp * pitch};
+            uint32_t ha = 0u, hb = 0u;
+            if (sr) {
+                const uint32_t base = (uint32_t)ts * 0x85EBCA77u + sid * 0xC2B2AE3Du;
+                ha = mix32((uint32_t)(y * pitch + x) * 0x9E3779B1u + base);
+                hb = mix32((uint32_t)(y * pitch + x + 1) * 0x9E3779B1u + base);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                S* d = dst + (i * plane + row[1 + cy(i)]);
+                float a, b;
+                upk(g[i], a, b);
+                const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? xar : xl);
+                const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xbr : x);
+                if (sr) {
+                    const uint32_t m = 0x2545F491u + 0x6A09E668u * (uint32_t)i;
+                    Storage<S>::store_sr(d + ca, a, (ha * m) >> 16, qz, i);
+                    if (vb) Storage<S>::store_sr(d + cb, b, (hb * m) >> 16, qz, i);
+                } else if (cx(i) == 0 && vb) {
+                    pair_store<S>(d + x, g[i], qz, i);
+                } else {
+                    Storage<S>::store(d + ca, a, qz, i);
+                    if (vb) Storage<S>::store(d + cb, b, qz, i);
+                }
+            }
+        };
+        auto add_usq = [&](double& acc, f2 q) {
+            float a, b;
+            upk(q, a, b);
+            acc += (double)a;
+            if (vb) acc += (double)b;
+        };
+        // gather of row y's pair from a ring (population i from ring row y - c_iy, column x - c_ix);
+        // oq: ring row index of row y (rows y - 1 and y + 1 are oq - 1 and oq + 1)
+        auto gather = [&](const float* ring, int oq, f2 (&g)[9]) {
+            const float* rp = ring + ring3_plane(2, oq - 1) * rw;  // c_iy = +1: row y - 1 (planes 2, 5, 6)
+            const float* rz = ring + ring3_plane(0, oq) * rw;      // c_iy =  0: row y     (planes 0, 1, 3)
+            const float* rm = ring + ring3_plane(4, oq + 1) * rw;  // c_iy = -1: row y + 1 (planes 4, 7, 8)
+            g[0] = *reinterpret_cast<const f2*>(rz + x);
+            g[1] = pk(rz[rw + xl], rz[rw + x]);
+            g[3] = pk(rz[2 * rw + xar], rz[2 * rw + xbr]);
+            g[2] = *reinterpret_cast<const f2*>(rp + x);
+            g[5] = pk(rp[rw + xl], rp[rw + x]);
+            g[6] = pk(rp[2 * rw + xar], rp[2 * rw + xbr]);
+            g[4] = *reinterpret_cast<const f2*>(rm + x);
+            g[7] = pk(rm[rw + xar], rm[rw + xbr]);
+            g[8] = pk(rm[2 * rw + xl], rm[2 * rw + x]);
+        };
+        auto put_ring = [&](float* ring, int oq, const f2 (&g)[9]) {
+            f2* r2 = reinterpret_cast<f2*>(ring);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) r2[ring3_plane(i, oq) * np + tid] = g[i];
+        };
+        if (n == 1) {
+            // the sample's last step: collide and push row by row
+            for (int y = ya; y < yb && va; ++y) {
+                const S* s0 = src + (y * pitch + x);
+                f2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane, qz, i);
+                f2 q;
+                collide_packed(g, omega, want[0] ? &q : nullptr);
+                if (want[0]) add_usq(red[0], q);
+                push(y, t, g);
+            }
+        } else {
+            // phase-A rows run from ya - (n == 3 ? 2 : 1) to yb + n - 2; ring row index of row y:
+            // y - ya + 4 (>= 0 for every row the piece touches)
+            const int a0 = ya - (n - 1);
+            auto fetch = [&](int qa) {
+                // staging: phase-A row a0 + qa goes to buffer qa % D, D rows ahead of its phase A; one
+                // copy group per row (empty past the piece)
+                if (va && a0 + qa <= yb + n - 2) {
+                    const S* s0 = src + (wrap(a0 + qa) * pitch + x);
+                    S* st = stage + (qa % (D > 0 ? D : 1)) * 9 * rw + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) cp_async<2 * sizeof(S)>(st + i * rw, s0 + i * plane);
+                }
+                cp_async_commit();
+            };
+            (void)fetch;
+            auto phase_a = [&](int ya_row) {
+                if (!va) return;
+                const int qa = ya_row - a0;
+                f2 g[9];
+                if constexpr (D > 0) {
+                    cp_async_wait<D - 1>();
+                    const S* st = stage + (qa % D) * 9 * rw + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * rw, qz, i);
+                    fetch(qa + D);
+                } else {
+                    const S* s0 = src + (wrap(ya_row) * pitch + x);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane, qz, i);
+                }
+                f2 qq;
+                const bool w = want[0] && ya_row >= ya && ya_row < yb;
+                collide_packed(g, omega, w ? &qq : nullptr);
+                if (w) add_usq(red[0], qq);
+                put_ring(ring1, ya_row - ya + 4, g);
+            };
+#pragma unroll
+            for (int k = 0; k < D; ++k) fetch(k);
+            if (n == 3) {
+                phase_a(ya - 2);
+                phase_a(ya - 1);
+                for (int y = ya - 2; y < yb; ++y) {
+                    phase_a(y + 2);
+                    __syncthreads();
+                    if (va) {
+                        // phase B: row y + 1 at step t + 1 from ring 1, into ring 2
+                        f2 g[9];
+                        gather(ring1, y + 1 - ya + 4, g);
+                        f2 qq;
+                        const bool w = want[1] && y + 1 >= ya && y + 1 < yb;
+                        collide_packed(g, omega, w ? &qq : nullptr);
+                        if (w) add_usq(red[1], qq);
+                        put_ring(ring2, y + 1 - ya + 4, g);
+                    }
+                    __syncthreads();
+                    if (va && y >= ya) {
+                        // phase C: row y at step t + 2 from ring 2, pushed into the other lattice
+                        f2 g[9];
+                        gather(ring2, y - ya + 4, g);
+                        f2 qq;
+                        collide_packed(g, omega, want[2] ? &qq : nullptr);
+                        if (want[2]) add_usq(red[2], qq);
+                        push(y, t + 2, g);
+                    }
+                }
+            } else {
+                phase_a(ya - 1);
+                for (int y = ya - 1; y < yb; ++y) {
+                    phase_a(y + 1);
+                    __syncthreads();
+                    if (va && y >= ya) {
+                        // phase B: row y at step t + 1 from ring 1, pushed into the other lattice
+                        f2 g[9];
+                        gather(ring1, y - ya + 4, g);
+                        f2 qq;
+                        collide_packed(g, omega, want[1] ? &qq : nullptr);
+                        if (want[1]) add_usq(red[1], qq);
+                        push(y, t + 1, g);
+                    }
+                    __syncthreads();
+                }
+            }
+            if constexpr (D > 0) cp_async_wait<0>();  // the empty groups past the piece
+        }
+        if (want[0] || want[1] || want[2]) {
+            // this piece's sums; the block that completes the sample adds the pieces in row order
+            __syncthreads();  // s_red lives in the rings
+            block_sum_dyn<3>(red, s_red);
+            if (tid == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) p.partials[(int64_t)(rb + ya) * 3 + k] = red[k];
+                __threadfence();
+                const int prev = atomicAdd(p.counters + j, yb - ya);
+                s_flag = (prev + (yb - ya) == ny);
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                double acc[3] = {0.0, 0.0, 0.0};
+                for (int q = tid; q < ny; q += np) {
+                    if (q == 0 || (rb + q) % per == 0) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) acc[k] += __ldcg(p.partials + (int64_t)(rb + q) * 3 + k);
+                    }
+                }
+                block_sum_dyn<3>(acc, s_red);
+                if (tid == 0) {
+                    const int64_t row = (int64_t)s_sp.sample_id * p.series_ld;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (want[k]) p.series[row + (t + k) / p.qoi_every] = acc[k] * s_sp.u_ref_inv2;
+                    p.counters[j] = 0;
+                }
+            }
+        }
+    }
+}
+
 
 // ------------------------------------------------------------------------------------------
 // Final fields and per-sample scalars at the last step run.
@@ -1879,9 +2184,62 @@ cudaError_t launch_bouzidi_force_s(const KParams& p, const BatchGeometry& g, cud
 }
 
 template <typename S>
+size_t strip3_smem(int nx) {
+    return (size_t)2 * kRing3Planes * nx * sizeof(float) + (size_t)Strip3Tune<S>::depth * 9 * nx * sizeof(S);
+}
+
+// Shared-memory opt-in and resident blocks per SM of the three-step strips at width nx (once each).
+template <typename S, bool GENERIC>
+int strip3_resident(int nx) {
+    constexpr int kb = Strip3Tune<S>::carveout_kb;
+    const int np = strip_threads(nx), rw = 2 * np;
+    static int cache[1024 / 32 + 1] = {};
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(strip3_kernel<S, GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)strip3_smem<S>(Strip3Tune<S>::max_nx));
+        if (kb > 0)
+            cudaFuncSetAttribute(strip3_kernel<S, GENERIC>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
+        attr = true;
+    }
+    int& n = cache[np / 32];
+    if (n == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip3_kernel<S, GENERIC>, np, strip3_smem<S>(rw)) !=
+                cudaSuccess || b < 1)
+            b = 1;
+        if (kb > 0) {
+            cudaFuncAttributes fa{};
+            cudaFuncGetAttributes(&fa, strip3_kernel<S, GENERIC>);
+            const size_t per = strip3_smem<S>(rw) + fa.sharedSizeBytes + 1024;
+            b = std::max(1, std::min(b, (int)((size_t)kb * 1024 / per)));
+        }
+        n = b;
+    }
+    return n;
+}
+
+template <typename S>
+cudaError_t launch_strip3_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const int np = strip_threads(g.strip_nx);
+    if (g.strip_nx < 2 || 2 * np > Strip3Tune<S>::max_nx) return cudaErrorInvalidConfiguration;
+    const bool generic = g.strip_nx != 2 * np;
+    const int64_t resident =
+        (int64_t)(generic ? strip3_resident<S, true>(g.strip_nx) : strip3_resident<S, false>(g.strip_nx)) * sm_count();
+    if (prepare_only) return cudaGetLastError();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
+    if (generic)
+        strip3_kernel<S, true><<<grid, np, strip3_smem<S>(2 * np), s>>>(p);
+    else
+        strip3_kernel<S, false><<<grid, np, strip3_smem<S>(2 * np), s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename S>
 cudaError_t launch_two_step_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
     if (g.strips) {
         if constexpr (sizeof(S) == 8) return cudaErrorInvalidConfiguration;
+        else if (g.spl == 3) return launch_strip3_s<S>(p, g, s, prepare_only);
         else return launch_strip_s<S>(p, g, s, prepare_only);
     }
     return launch_step2_s<S>(p, g, s, prepare_only);

@@ -14,7 +14,7 @@ namespace {
 // arrays are indexed by the sample's slot).
 __global__ void commit_kernel(KParams p) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < p.nsamples; k += gridDim.x * blockDim.x)
-        p.sel[k] ^= launches_of(p.steps_run[k], (int)p.step_counter[1]) & 1;
+        p.sel[k] ^= launches_of(p.steps_run[k], (int)p.step_counter[1], p.spl) & 1;
 }
 
 __global__ void advance_kernel(int64_t* counter, int chunk) { *counter += chunk; }
@@ -66,6 +66,7 @@ KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutp
     p.dt = dt;
     p.max_steps = g.max_steps;
     p.stochastic = g.stochastic;
+    p.spl = g.spl > 0 ? g.spl : 2;
     if (o != nullptr) {
         p.fields = o->fields;
         p.fields_ld = o->fields_ld;
@@ -85,6 +86,12 @@ bool strip_supported(int storage, int nx) {
     if (storage == UQLB_F64 || nx < 2) return false;
     const int rw = 2 * strip_threads(nx);  // the ring's width: nx rounded up to 64 columns
     return rw <= (storage == UQLB_F32 ? StripTune<float>::max_nx : StripTune<__half>::max_nx);
+}
+
+bool strip3_supported(int storage, int nx) {
+    if (storage == UQLB_F64 || nx < 2) return false;
+    const int rw = 2 * strip_threads(nx);
+    return rw <= (storage == UQLB_F32 ? Strip3Tune<float>::max_nx : Strip3Tune<__half>::max_nx);
 }
 
 bool geometry_supported2(int storage, int tile_rows, int npt) {

@@ -79,6 +79,9 @@ int cuda_fail(uqlb_ctx* c, cudaError_t e, const char* what) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Whether UQLB_SCHEME_AUTO takes three steps per launch on the row strips where the width allows it.
+constexpr bool kAutoThreeStep = false;
+
 int storage_bytes(int storage) {
     switch (storage) {
         case UQLB_F64: return 8;
@@ -102,6 +105,10 @@ int storage_bytes(int storage) {
 //     R = 1.5 U^2 (|p| <= u0^2 / 2); margin 1.5.
 //   TGV_PERTURBED (Sec. 8.3): U = |u0| + S / 4 with S = |zeta_00| + ... + |zeta_11|,
 //     G = k (2 |u0| + 1.5 S), R = 1.5 U^2, margin 1.5.
+//   Either Taylor-Green kind on a lattice with nx != ny: the initial field is not divergence-free
+//     there (k differs along x and y), its acoustic waves carry |drho| up to ~1.7 U (measured in an
+//     FP64 emulation at aspect ratios 2 to 32), so R = 2 sqrt(3) U (the acoustic density of a
+//     velocity jump U is sqrt(3) U, doubled).
 //   CHANNEL (Sec. 8.1): U = 4 |u0| (u0 the mean inflow; |u_x| + |u_y| peaks near 2.8 u0 around the
 //     obstacle and in the start-up), G = U / 2 (the shear at the staircase obstacle), and R = 6 |u0|
 //     (start-up pressure waves reach |drho| near 2 u0 with the ramp; an impulsive start gives about
@@ -127,6 +134,7 @@ void fx16_quanta(const uqlb_sample& s, double d[3]) {
         R = 1.5 * U * U;
         margin = 1.5;
     }
+    if (s.kind != UQLB_CASE_CHANNEL && s.nx != s.ny) R = std::max(R, 2.0 * std::sqrt(3.0) * U);
     U = std::max(U, 1e-6);
     const double tau = 3.0 * std::max(s.nu, 0.0) + 0.5;
     const double rho = 1.0 + R;
@@ -413,12 +421,12 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     const int scheme = o ? o->scheme : UQLB_SCHEME_AUTO;
-    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_TWO_STEP_STRIPS) {
+    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_THREE_STEP_STRIPS || scheme == UQLB_SCHEME_GROUPED) {
         why = "unknown time-stepping scheme";
         return UQLB_ERR_ARG;
     }
     // auto: the two-step scheme where it measured faster (periodic FP32, FP16 and BF16 batches)
-    const bool two = scheme >= UQLB_SCHEME_TWO_STEP ||
+    const bool two = (scheme >= UQLB_SCHEME_TWO_STEP && scheme != UQLB_SCHEME_ONE_STEP) ||
                      (scheme == UQLB_SCHEME_AUTO && !mixed && mode == UQLB_MODE_GRAPH && storage != UQLB_F64);
     if (two && (mixed || mode != UQLB_MODE_GRAPH)) {
         why = "the two-step scheme runs periodic (TGV) batches in UQLB_MODE_GRAPH only";
@@ -432,6 +440,18 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     const bool strips = two && strip_ok && scheme != UQLB_SCHEME_TWO_STEP_TILES;
+    // three steps per launch on the strips where asked for, or under auto where the width allows it
+    const bool strip3_ok = strips && strip3_supported(storage, smp[0].nx);
+    if (scheme == UQLB_SCHEME_THREE_STEP_STRIPS && !strip3_ok) {
+        why = "the three-step row strips need FP32, FP16, BF16 or FX16 storage and one sample width of at most 1600 "
+              "(1280 with FP32)";
+        return UQLB_ERR_ARG;
+    }
+    const int spl = !two ? 1
+                         : ((strip3_ok && (scheme == UQLB_SCHEME_THREE_STEP_STRIPS ||
+                                           (scheme == UQLB_SCHEME_AUTO && kAutoThreeStep)))
+                                ? 3
+                                : 2);
     auto supported = [&](int r, int q) {
         return two ? geometry_supported2(storage, r, q) : geometry_supported(storage, mixed, r, q);
     };
@@ -606,10 +626,10 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     P.off_masks = take(sizeof(uint32_t) * P.masks.size());
     P.off_side = take((size_t)side * 2 * 8);
     P.off_bcpop = take((size_t)bcnodes * 9 * sizeof(double));
-    // per-tile sums (7 per tile); the row-strip kernel keeps 2 per row at the first row of each piece.
+    // per-tile sums (7 per tile); the row-strip kernels keep 2 or 3 per row at the first row of each piece.
     // Sized alike for both two-step kernels: the buffers behind it (done, steps_run, ...) carry a run
     // into its resumption, which may use the other kernel.
-    P.off_partials = take((size_t)std::max<int64_t>(tiles * 7, two ? total_rows * 2 : 0) * sizeof(double));
+    P.off_partials = take((size_t)std::max<int64_t>(tiles * 7, two ? total_rows * 3 : 0) * sizeof(double));
     P.off_counters = take(sizeof(int32_t) * n);
     P.off_done = take(sizeof(int32_t) * n);
     P.off_steps_run = take(sizeof(int32_t) * n);
@@ -639,7 +659,7 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     g.two_step = two ? 1 : 0;
     g.strips = strips ? 1 : 0;
     g.strip_nx = strips ? smp[0].nx : 0;
-    g.pad_ = 0;
+    g.spl = spl;
     g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
     g.any_bouzidi = any_bouzidi;
     g.any_inout = any_inout;
@@ -709,7 +729,8 @@ int chunk_graph(uqlb_ctx* ctx, const BatchBuffers& B, const BatchGeometry& G, co
     if (err != cudaSuccess) return cuda_fail(ctx, err, "cudaStreamBeginCapture");
     cudaError_t lerr = cudaSuccess;
     if (G.two_step) {
-        for (int dt = 0; dt < chunk && lerr == cudaSuccess; dt += 2) lerr = launch_step2(B, G, O, dt, ctx->capture_stream);
+        for (int dt = 0; dt < chunk && lerr == cudaSuccess; dt += G.spl)
+            lerr = launch_step2(B, G, O, dt, ctx->capture_stream);
     } else {
         for (int dt = 0; dt < chunk && lerr == cudaSuccess; ++dt) {
             lerr = launch_step(B, G, O, dt, parity, ctx->capture_stream);
@@ -869,7 +890,9 @@ int run_planned(uqlb_ctx* ctx, const BatchPlan& P, int64_t n, const uqlb_run_opt
                 void* fields_dev, int64_t fields_ld, double* qoi_dev, double* series_dev, double* series_cl_dev,
                 int64_t series_ld, cudaStream_t s, bool own_timing) {
     const bool resume = opts->start_step > 0;
-    const int chunk = opts->chunk_steps > 0 ? opts->chunk_steps : 64;
+    // a chunk is a whole number of launches
+    const int spl = std::max(P.geom.spl, 1);
+    const int chunk = ((opts->chunk_steps > 0 ? opts->chunk_steps : 64) + spl - 1) / spl * spl;
     BatchBuffers B = carve(P, workspace_dev);
     char* ws = static_cast<char*>(workspace_dev);
     cudaError_t e;
@@ -939,7 +962,7 @@ int run_planned(uqlb_ctx* ctx, const BatchPlan& P, int64_t n, const uqlb_run_opt
             return cuda_fail(ctx, e, "run_batch: event record");
         for (int64_t q = 0; q < nchunks; ++q) {
             if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: graph launch");
-            ctx->run_launches += P.geom.two_step ? chunk / 2 + 1
+            ctx->run_launches += P.geom.two_step ? chunk / spl + 1
                                                  : chunk + 1 + ((P.geom.any_bouzidi && O.qoi_every > 0) ? chunk : 0) +
                                                        (P.geom.any_inout ? chunk : 0);
             if (steady && (q % 8) == 7 && q + 1 < nchunks) {
@@ -1473,7 +1496,8 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     ctx->last_npt = P0.geom.npt;
     ctx->last_scheme = !groups.empty() ? UQLB_SCHEME_GROUPED
                        : !P0.geom.two_step ? UQLB_SCHEME_ONE_STEP
-                       : (P0.geom.strips ? UQLB_SCHEME_TWO_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_TILES);
+                       : (P0.geom.strips ? (P0.geom.spl == 3 ? UQLB_SCHEME_THREE_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_STRIPS)
+                                         : UQLB_SCHEME_TWO_STEP_TILES);
     if (fields_dev) {
         if (!uniform_size) return set_err(ctx, UQLB_ERR_ARG, "run_batch: field output needs one lattice size");
         if (fields_ld < 2 * (int64_t)samples[0].nx * samples[0].ny + 1) return set_err(ctx, UQLB_ERR_ARG, "run_batch: fields_ld too small");

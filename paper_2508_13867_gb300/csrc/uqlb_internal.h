@@ -102,7 +102,7 @@ struct BatchGeometry {
     int32_t any_inout;       // some sample uses the interpolated inlet/outlet
     int32_t strips;          // two-step scheme on row strips (strip2_kernel) instead of tiles
     int32_t strip_nx;        // width of every sample when strips is set
-    int32_t pad_;            // keeps the struct free of padding bytes (it keys the graph cache)
+    int32_t spl;             // time steps per launch: 1 (one-step), 2 (tiles, two-step strips), 3 (three-step strips)
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -147,6 +147,8 @@ bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
 bool geometry_supported2(int storage, int tile_rows, int npt);  // two-step scheme
 // Row-strip two-step kernel: FP32/FP16/BF16 storage, sample width a multiple of 64 in 64..2048.
 bool strip_supported(int storage, int nx);
+// Three-step row strips: FP32 rows up to 1280 wide, 16-bit up to 1600 (rounded up to 64 columns).
+bool strip3_supported(int storage, int nx);
 
 // Plain per-sample FP64 path (plain_f64.cu).
 struct PlainSample {

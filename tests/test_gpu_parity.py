@@ -79,7 +79,7 @@ def test_tgv_f64_fields_energy_and_invariants(ens, n, steps):
         assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("scheme", ["auto", "one_step", "two_step_tiles"])
+@pytest.mark.parametrize("scheme", ["auto", "one_step", "two_step_tiles", "three_step_strips"])
 @pytest.mark.parametrize("storage", _storages("f32", "f16", "bf16", "fx16"))
 def test_tgv_reduced_precision_storage(ens, storage, scheme):
     """Per-sample velocity fields and K(T) against the oracle within the storage's budget (96 x 96,
@@ -621,10 +621,9 @@ def test_two_step_strips_at_the_widest_rows(ens, storage, nx):
     """The widest rows the strips take (FP32 1600: ring and staging fill 230 KB of shared memory in
     one block of 800 threads; 16-bit 2048: 1024 threads) and an odd multiple of 64, on thin
     lattices: fields and the K series against the oracle within the storage's budget.  The
-    fixed-point storage sizes its range for flows that the lattice resolves (its bound on the
-    non-equilibrium populations is the first-order one): its case runs 64 rows, where a 6-row lattice
-    (a wavelength of 6 nodes) leaves the range and is reported unstable."""
-    ny = 64 if storage == "fx16" else 6
+    fixed-point storage sizes its range for the square lattice's divergence-free Taylor-Green field
+    and for flows that the lattice resolves; its case runs on the square 2048 x 2048 lattice."""
+    ny = nx if storage == "fx16" else 6
     specs = [replace(W.tgv(nx, 9, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(nx, 8, nu=0.05), ny=ny)]
     st = _run(ens, specs, storage, qoi_every=1, series=True, scheme="two_step_strips")
     assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
@@ -791,7 +790,7 @@ def test_two_step_strips_16_bit_nearest_rounding(ens, storage):
             assert rel_l2(m[i, :-1], oracle_row(r)[:-1]) < TOL[storage], (scheme, storage)
 
 
-@pytest.mark.parametrize("scheme", ["two_step_tiles", "two_step_strips"])
+@pytest.mark.parametrize("scheme", ["two_step_tiles", "two_step_strips", "three_step_strips"])
 @pytest.mark.parametrize("storage", _storages("f16", "bf16", "fx16"))
 def test_two_step_16_bit_storage_against_the_oracle(ens, storage, scheme):
     """16-bit storage on the two-step scheme keeps the intermediate step in FP32 shared memory, so
@@ -808,26 +807,29 @@ def test_two_step_16_bit_storage_against_the_oracle(ens, storage, scheme):
         assert e2 < 1.5 * e1 + 1e-6, (storage, e2, e1)
 
 
+@pytest.mark.parametrize("scheme", ["two_step_strips", "three_step_strips"])
 @pytest.mark.parametrize("n", [31, 97, 40, 64, 832])
-def test_strip_kernel_edge_geometries_against_the_oracle(ens, n):
-    """The row strips (FP32) against the oracle directly, at the geometries whose index arithmetic
-    differs: odd widths (31, 97: the last pair is a lone node whose partner is dropped), a width that
-    leaves threads past the row (40), a full block (64) and an odd multiple of 64 (832); heights equal
-    to the width, ragged (37) and degenerate (3, 2: the rows above and below a node coincide); step
-    counts that end on a single-step launch (61, 1), stop at once (0) or end on a two-step launch
-    (60); K at every step and at a stride of 7.  The Taylor-Green field on 2 and 3 rows is a mode
+def test_strip_kernel_edge_geometries_against_the_oracle(ens, n, scheme):
+    """The row strips (FP32, two and three steps per launch) against the oracle directly, at the
+    geometries whose index arithmetic differs: odd widths (31, 97: the last pair is a lone node whose
+    partner is dropped), a width that leaves threads past the row (40), a full block (64) and an odd
+    multiple of 64 (832); heights equal to the width, ragged (37) and degenerate (3, 2: the rows above
+    and below a node coincide); step counts whose last launch runs one step (61, 1), two (62) or three
+    (60) or that stop at once (0); K at every step and at a stride of 7.  The Taylor-Green field on 2 and 3 rows is a mode
     near the lattice's Nyquist wavenumber that decays by a factor of 2 to 3 per step (2600x in 9
     steps on 2 rows, measured), so the FP32 round-off of its start, ~1e-7 of it, soon exceeds 1e-5
-    of what is left; those run 3 and 2 steps (the same odd and even launch patterns)."""
+    of what is left; those run 3, 2 and 1 steps (a launch of each length)."""
     heights = (37, 3, 2) if n > 128 else (n, 37, 3, 2)
+    want = {"two_step_strips": U.UQLB_SCHEME_TWO_STEP_STRIPS, "three_step_strips": U.UQLB_SCHEME_THREE_STEP_STRIPS}
     for ny in heights:
-        t_odd, t_even = (61, 60) if ny > 3 else (3, 2)
-        specs = [replace(W.tgv(n, t_odd, nu=0.03, amp2=0.0005), ny=ny),
-                 replace(W.tgv(n, t_even, nu=0.05, amp3=-0.0004), ny=ny),
+        counts = (61, 62, 60) if ny > 3 else (3, 2, 3)
+        specs = [replace(W.tgv(n, counts[0], nu=0.03, amp2=0.0005), ny=ny),
+                 replace(W.tgv(n, counts[1], nu=0.05, amp3=-0.0004), ny=ny),
+                 replace(W.tgv(n, counts[2], nu=0.037, amp2=-0.0003, amp3=0.0002), ny=ny),
                  replace(W.tgv(n, 1, nu=0.02), ny=ny), replace(W.tgv(n, 0, nu=0.04), ny=ny)]
         for qe in (1, 7):
-            g = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme="two_step_strips")
-            assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_TWO_STEP_STRIPS
+            g = _run(ens, specs, "f32", qoi_every=qe, series=True, scheme=scheme)
+            assert U.uqlb_last_run_geometry(ens.ctx)[0] == want[scheme]
             ref = olbm.run([oracle_case(s, qoi_every=qe) for s in specs])
             for i, r in enumerate(ref):
                 what = (n, ny, qe, specs[i].steps)
@@ -953,3 +955,55 @@ def test_sharded_pass_on_one_gpu_equals_the_unsharded_pass(ens):
     assert rel_l2(mean.cpu().numpy(), mean_ref.cpu().numpy()) < 1e-13
     assert rel_l2(var.cpu().numpy(), var_ref.cpu().numpy()) < 1e-12
     e.close()
+
+
+@pytest.mark.parametrize("storage,nx,ny", [("f32", 1280, 6), ("fx16", 1600, 1600), ("f32", 64 * 13, 9)])
+def test_three_step_strips_at_the_widest_rows(ens, storage, nx, ny):
+    """The widest rows the three-step strips take (FP32 1280: two rings and the staging fill 230 KB of
+    shared memory in one block of 640 threads; 16-bit 1600) and an odd multiple of 64: fields and the K
+    series against the oracle within the storage's budget (the fixed-point case on a square lattice)."""
+    specs = [replace(W.tgv(nx, 9, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(nx, 8, nu=0.05), ny=ny)]
+    st = _run(ens, specs, storage, qoi_every=1, series=True, scheme="three_step_strips")
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_THREE_STEP_STRIPS
+    ref = olbm.run([oracle_case(s, qoi_every=1) for s in specs])
+    tol = TOL[storage]
+    for i, r in enumerate(ref):
+        assert st["qoi"][i, U.UQLB_QOI_STATUS] == 0, (storage, nx, i)
+        assert rel_l2(st["fields"][i, :-1], oracle_row(r)[:-1]) < tol, (storage, nx, i)
+        ns = specs[i].steps + 1
+        assert np.allclose(st["series"][i, :ns], r.series[:ns], rtol=tol, atol=0), (storage, nx, i)
+
+
+def test_three_step_strips_equal_the_two_step_strips_bit_for_bit(ens):
+    """With FP32 storage the three-step strips apply the same packed collisions to the same node pairs
+    as the two-step strips, and FP32 rows pass through shared memory and HBM unrounded: fields are
+    equal bit for bit whatever the grouping of steps into launches (step counts ending on launches of
+    one, two and three steps; ragged and degenerate heights; odd width).  K sums the same values with
+    the blocks split differently, so it agrees to FP64 round-off."""
+    for n, ny in ((64, 64), (97, 37), (40, 3), (128, 2)):
+        specs = [replace(W.tgv(n, 61, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(n, 62, nu=0.05), ny=ny),
+                 replace(W.tgv(n, 60, nu=0.04, amp3=0.0003), ny=ny), replace(W.tgv(n, 1, nu=0.02), ny=ny)]
+        a = _run(ens, specs, "f32", qoi_every=5, series=True, scheme="two_step_strips")
+        b = _run(ens, specs, "f32", qoi_every=5, series=True, scheme="three_step_strips")
+        assert np.array_equal(a["fields"][:, :-1], b["fields"][:, :-1]), (n, ny)
+        assert np.allclose(a["series"], b["series"], rtol=1e-12, atol=0, equal_nan=True), (n, ny)
+
+
+@pytest.mark.parametrize("first,second", [("three_step_strips", "three_step_strips"),
+                                          ("two_step_strips", "three_step_strips"),
+                                          ("three_step_strips", "two_step_strips")])
+@pytest.mark.parametrize("split", [38, 51, 60])
+def test_three_step_strips_resume_continues_the_run(ens, first, second, split):
+    """A run stopped after `split` steps and resumed (on either strip kernel) equals the uninterrupted
+    three-step run bit for bit with FP32 storage: the launches group the steps differently, the
+    per-node arithmetic is the same."""
+    specs = _tgv_specs(64, 100) + [W.tgv(64, 71, nu=0.04)]
+    whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="three_step_strips")
+    head = [sample_struct(s) for s in specs]
+    for s in head:
+        s.steps = min(split, s.steps)
+    ens.run_batch(head, storage="f32", fields=False, scheme=first)
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=True, start_step=split,
+                        scheme=second)
+    torch.cuda.synchronize()
+    assert np.array_equal(res["fields"].double().cpu().numpy()[:, :-1], whole["fields"][:, :-1])

@@ -202,28 +202,38 @@ typedef struct {
  *   UQLB_SCHEME_TWO_STEP: one launch per two time steps on two lattices (36 B of HBM traffic per
  *     FP32 node update).  Each node is collided at step t into shared memory, streamed from there,
  *     collided at step t + 1 and pushed to the other lattice.  Periodic (TGV, TGV_PERTURBED)
- *     batches in UQLB_MODE_GRAPH; the workspace holds the second lattice.  FP32/FP64 results agree
- *     with the one-step scheme's to round-off (same formulas per node); 16-bit storage rounds half
- *     as often.  Two kernels:
+ *     batches in UQLB_MODE_GRAPH.  Two lattices: the workspace holds the second one, so a two- or
+ *     three-step run needs twice the lattice memory of a one-step run (2.95 GB for 625 x 256^2 in
+ *     FP32; uqlb_batch_workspace_bytes reports it).  FP32/FP64 results agree with the one-step
+ *     scheme's to round-off (same formulas per node, a different operation order in the packed
+ *     collisions), not bit for bit; 16-bit storage rounds half as often.  Two kernels:
  *       TWO_STEP_STRIPS: blocks walk full-width rows, keeping a ring of collided rows in shared
  *         memory (about 1 % of the nodes collided twice).  Every sample of the batch must have
  *         the same width nx, at most 2048 (1600 with FP32 storage, whose rows are also staged in
- *         shared memory; a block covers the row rounded up to 64 columns), with FP32, FP16 or BF16
- *         storage; the tile geometry then serves only the initial state and the final fields.
+ *         shared memory; a block covers the row rounded up to 64 columns), with FP32, FP16, BF16 or
+ *         FX16 storage; the tile geometry then serves only the initial state and the final fields.
  *       TWO_STEP_TILES: blocks take tiles of the tile geometry with a one-node halo (any size,
  *         FP64 too; the halo is collided twice, 27 % more collisions at tile 8 x 128).
  *     UQLB_SCHEME_TWO_STEP takes strips where the batch allows them, else tiles.
- *   UQLB_SCHEME_AUTO: TWO_STEP for periodic FP32, FP16 and BF16 batches in graph mode, where it
- *     measured faster on GB300 (625 x 256^2 ensemble, GLUPS two-step strips / tiles / one-step:
- *     FP32 178 / 115 / 84, FP16 164 / 95 / 82, BF16 175 / 103 / 90); ONE_STEP otherwise (FP64 is
- *     bound by the FP64 rate).  In graph mode with FP32/FP16/BF16 storage a batch of unlike
- *     samples runs as groups of like samples, one group after another on one stream, each on its
- *     own kernel and its own slice of the workspace (uqlb_batch_workspace_bytes counts them all):
- *     CHANNEL samples on ONE_STEP, periodic samples of each width the strips take on
- *     TWO_STEP_STRIPS, wider periodic samples on TWO_STEP_TILES.  Outputs keep the caller's rows.
- *     uqlb_last_run_geometry then reports UQLB_SCHEME_GROUPED.
- * A resumed run (start_step > 0) must use the scheme of the run it continues (strips and tiles
- * leave the same lattice layout, so either two-step kernel continues a two-step run). */
+ *   UQLB_SCHEME_THREE_STEP_STRIPS: one launch per three time steps on the row strips, two rings of
+ *     collided rows in shared memory (24 B of HBM traffic per FP32 node update); widths up to 1600
+ *     (1280 with FP32 storage), the same storage formats and lattices as TWO_STEP_STRIPS.  A sample
+ *     with fewer than three steps left runs two or one in its last launch.  With FP32 storage its
+ *     fields equal the two-step strips' bit for bit (the same packed collisions of the same node
+ *     pairs; FP32 rows pass through shared memory and HBM unrounded).
+ *   UQLB_SCHEME_AUTO: the row strips for periodic FP32, FP16, BF16 and FX16 batches in graph mode,
+ *     three steps per launch where the width allows it, else two, else TWO_STEP_TILES (measured on
+ *     GB300, 625 x 256^2 ensemble, kernel GLUPS three-step strips / two-step strips / tiles /
+ *     one-step: FP32 203 / 177 / 115 / 84, FP16 174 / 161 / 95 / 82, BF16 183 / 172 / 103 / 90,
+ *     FX16 171 / 160 / - / -); ONE_STEP otherwise (FP64 is bound by the FP64 rate).  In graph mode
+ *     with FP32/FP16/BF16/FX16 storage a batch of unlike samples runs as groups of like samples, one
+ *     group after another on one stream, each on its own kernel and its own slice of the workspace
+ *     (uqlb_batch_workspace_bytes counts them all): CHANNEL samples on ONE_STEP, periodic samples of
+ *     each width the strips take on the strips, wider periodic samples on TWO_STEP_TILES.  Outputs
+ *     keep the caller's rows.  uqlb_last_run_geometry then reports UQLB_SCHEME_GROUPED.
+ * A resumed run (start_step > 0) continues the state on any multi-step kernel (the strips and the
+ * tiles, with two or three steps per launch, leave the same lattice layout); a one-step run resumes
+ * on the one-step scheme only. */
 enum {
     UQLB_SCHEME_AUTO = 0,
     UQLB_SCHEME_ONE_STEP = 1,
@@ -346,8 +356,11 @@ int uqlb_batch_workspace_bytes(const uqlb_sample* samples, int64_t n, const uqlb
                                size_t* bytes);
 
 /* Run n independent samples on the device: initialise every lattice at equilibrium, step all
- * samples in in-place AA order with the collision, streaming, boundaries and QoI reductions of
- * each step fused into one kernel, and write the results.
+ * samples with the collision, streaming, boundaries and QoI reductions fused into the step kernels
+ * of the run's scheme (uqlb_run_opts.scheme: in place in AA order with one launch per step, or two
+ * lattices with two or three steps per launch; under UQLB_SCHEME_AUTO periodic FP32/16-bit batches
+ * take two lattices, so size the workspace with uqlb_batch_workspace_bytes for the same options),
+ * and write the results.
  *   workspace_dev / workspace_bytes: scratch of at least uqlb_batch_workspace_bytes bytes,
  *     256-byte aligned; contents on entry are ignored.
  *   fields_dev: optional (NULL to skip), row s = [u (ny*nx), v (ny*nx), K(T)] of sample s in
@@ -454,7 +467,9 @@ int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, 
  * weights; larger sample sets return UQLB_ERR_ARG and need uqlb_project).  No device memory is
  * allocated or freed.  The array exists once per GPU that loads the library and stays until
  * the process exits.  The first call on a device looks up the array's device address, so make
- * that first call before capturing a stream.  All calls share the one array: calls that
+ * that first call before capturing a stream.  The library keeps that address for the life of the
+ * process: it must not outlive a reset of the device (cudaDeviceReset), which would leave the kept
+ * address pointing at memory that no longer holds the array.  All calls share the one array: calls that
  * overlap on the GPU (e.g. on two streams) race and must be ordered by the caller.  Each call
  * overwrites every weight it reads, so no contents carry over between calls. */
 int uqlb_project_noalloc(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,

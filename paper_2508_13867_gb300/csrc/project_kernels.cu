@@ -181,7 +181,8 @@ extern "C" int uqlb_project_noalloc(uqlb_ctx* ctx, const void* m_dev, int dtype,
     double* w_dev = nullptr;
     {
         // First call on this device: resolve the device address of the array (host code cannot
-        // use the symbol itself, which only stands in for it on the host).
+        // use the symbol itself, which only stands in for it on the host).  The address is kept for
+        // the life of the process; a device reset would invalidate it (documented in the header).
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         if (g_noalloc_ptr[device] == nullptr) {
             void* ptr = nullptr;

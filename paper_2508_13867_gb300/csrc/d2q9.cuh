@@ -236,15 +236,44 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
 }
 __device__ __forceinline__ f2 splat(float c) { return pk(c, c); }
 
-// moments() and bgk() of two nodes a and b in packed arithmetic (the same formulas; the operation
-// order is fixed here, where the compiler may contract the scalar code differently, so results
-// agree with the scalar path to round-off).  g[i] holds population i of node a (low half) and of
-// node b (high half); usq (when non-null) receives u.u of both nodes.
-__device__ __forceinline__ void collide_packed(f2 (&g)[9], float omega, f2* usq) {
+// Relaxation constants of the packed collision for one relaxation rate omega.  The BGK update is
+// written as g_i* = (1 - omega) g_i + omega g_i^eq, with omega folded into the equilibrium's
+// coefficients: omega w_i for the even part and omega L_i for the odd part.  The odd coefficients
+// keep 2 omega L_1 + 4 omega L_5 = omega exactly (ol5 = (omega - 2 ol1) / 4, an exact difference and an
+// exact quarter), so the relaxation carries exactly the momentum omega j, as the unfolded form does
+// with 2 L_1 + 4 L_5 = 1; 1 - omega is exact for omega in [0.5, 2] (tau <= 2).
+struct PackedBGK {
+    f2 omc, ow0, ow1, ow5, ol1, ol5, nl1, nl5;  // nl = -ol
+};
+__device__ __forceinline__ PackedBGK packed_bgk(float omega) {
+    PackedBGK k;
+    k.omc = splat(1.0f - omega);
+    k.ow0 = splat(omega * wgt<float>(0));
+    k.ow1 = splat(omega * wgt<float>(1));
+    k.ow5 = splat(omega * wgt<float>(5));
+    const float ol1 = omega * lin<float>(1);
+    k.ol1 = splat(ol1);
+    const float ol5 = (omega - 2.0f * ol1) * 0.25f;
+    k.ol5 = splat(ol5);
+    k.nl1 = splat(-ol1);
+    k.nl5 = splat(-ol5);
+    return k;
+}
+
+// The BGK collision of two nodes a and b in packed arithmetic (the formulas of moments() and bgk(),
+// with omega folded into the equilibrium as PackedBGK describes; the operation order is fixed here, so
+// results agree with the scalar path to round-off).  g[i] holds population i of node a (low half) and
+// of node b (high half); usq (when non-null) receives u.u of both nodes.
+//   drho = sum g_i, j = sum c_i g_i (with a = g5 - g7, b = g6 - g8 shared by jx and jy), u = j + j d,
+//   X = drho - 1.5 j.u, and per pair of opposite directions (i, opp i):
+//   omega A = omega w_i (X + 4.5 (c_i.j)(c_i.u)),  g_i* = (1 - omega) g_i + (omega A + omega L_i c_i.j),
+//   g_opp* = (1 - omega) g_opp + (omega A - omega L_i c_i.j);  rest: g_0* = (1 - omega) g_0 + omega w_0 X.
+__device__ __forceinline__ void collide_packed(f2 (&g)[9], const PackedBGK& k, f2* usq) {
     const f2 drho =
         add2(add2(add2(add2(g[0], g[1]), add2(g[2], g[3])), add2(add2(g[4], g[5]), add2(g[6], g[7]))), g[8]);
-    const f2 jx = add2(add2(sub2(g[1], g[3]), sub2(g[5], g[6])), sub2(g[8], g[7]));
-    const f2 jy = add2(add2(sub2(g[2], g[4]), sub2(g[5], g[7])), sub2(g[6], g[8]));
+    const f2 a = sub2(g[5], g[7]), b = sub2(g[6], g[8]);
+    const f2 jx = add2(sub2(g[1], g[3]), sub2(a, b));
+    const f2 jy = add2(sub2(g[2], g[4]), add2(a, b));
     float da, db;
     upk(drho, da, db);
     // 1/rho - 1 per node; the fast division (reciprocal and multiply, within 2 ulp) is exact enough
@@ -253,36 +282,37 @@ __device__ __forceinline__ void collide_packed(f2 (&g)[9], float omega, f2* usq)
     const f2 d = pk(__fdividef(-da, 1.0f + da), __fdividef(-db, 1.0f + db));
     const f2 ux = fma2(jx, d, jx), uy = fma2(jy, d, jy);
     if (usq != nullptr) *usq = fma2(uy, uy, mul2(ux, ux));
-    const f2 om = splat(omega);
-    const f2 ju15 = mul2(splat(1.5f), fma2(jy, uy, mul2(jx, ux)));
-    g[0] = fma2(om, sub2(mul2(splat(wgt<float>(0)), sub2(drho, ju15)), g[0]), g[0]);
+    const f2 X = fma2(splat(-1.5f), fma2(jy, uy, mul2(jx, ux)), drho);
+    const f2 ux45 = mul2(splat(4.5f), ux), uy45 = mul2(splat(4.5f), uy);
+    g[0] = fma2(g[0], k.omc, mul2(k.ow0, X));
 #pragma unroll
     for (int i : {1, 2, 5, 6}) {
         const int o = opp(i);
-        f2 cj, cu;
+        f2 cj, cu, ow, ol, nl;
         if (i == 1) {
             cj = jx;
-            cu = ux;
+            cu = ux45;
         } else if (i == 2) {
             cj = jy;
-            cu = uy;
+            cu = uy45;
         } else if (i == 5) {
             cj = add2(jx, jy);
-            cu = add2(ux, uy);
+            cu = add2(ux45, uy45);
         } else {
             cj = sub2(jy, jx);
-            cu = sub2(uy, ux);
+            cu = sub2(uy45, ux45);
         }
-        const f2 A = mul2(splat(wgt<float>(i)), sub2(fma2(splat(4.5f), mul2(cj, cu), drho), ju15));
-        const f2 gi = fma2(splat(lin<float>(i)), cj, A);
-        const f2 go = fma2(splat(-lin<float>(i)), cj, A);
-        g[i] = fma2(om, sub2(gi, g[i]), g[i]);
-        g[o] = fma2(om, sub2(go, g[o]), g[o]);
+        ow = i <= 4 ? k.ow1 : k.ow5;
+        ol = i <= 4 ? k.ol1 : k.ol5;
+        nl = i <= 4 ? k.nl1 : k.nl5;
+        const f2 oA = mul2(ow, fma2(cj, cu, X));
+        g[i] = fma2(g[i], k.omc, fma2(ol, cj, oA));
+        g[o] = fma2(g[o], k.omc, fma2(nl, cj, oA));
     }
 }
 
 // collide_packed() on two nodes held as separate arrays.
-__device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], float omega, float* usq_a,
+__device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], const PackedBGK& omega, float* usq_a,
                                              float* usq_b) {
     f2 g[9];
 #pragma unroll
@@ -292,6 +322,19 @@ __device__ __forceinline__ void collide_pair(float (&ga)[9], float (&gb)[9], flo
     if (usq_a != nullptr) upk(q, *usq_a, *usq_b);
 #pragma unroll
     for (int i = 0; i < 9; ++i) upk(g[i], ga[i], gb[i]);
+}
+
+// Two nodes collided one after the other in scalar FP32 (moments() and bgk() of each), the same
+// formulas as collide_packed() issued on the scalar FP32 pipe; usq_a/usq_b (when non-null) receive u.u.
+__device__ __forceinline__ void collide_pair_scalar(float (&ga)[9], float (&gb)[9], float omega, float* usq_a,
+                                                    float* usq_b) {
+    float drho, jx, jy, ux, uy;
+    moments(ga, drho, jx, jy, ux, uy);
+    if (usq_a != nullptr) *usq_a = fmaf(uy, uy, ux * ux);
+    bgk(ga, omega, drho, jx, jy, ux, uy);
+    moments(gb, drho, jx, jy, ux, uy);
+    if (usq_b != nullptr) *usq_b = fmaf(uy, uy, ux * ux);
+    bgk(gb, omega, drho, jx, jy, ux, uy);
 }
 
 // Obstacle bitmask lookup: bit (x & 31) of word y * words + (x >> 5).

@@ -811,6 +811,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
         S* dst = static_cast<S*>(second ? p.arena : p.arena2) + sp.f_off;
         const int plane = (int)sp.plane, pitch = sp.pitch, nx = sp.nx, ny = sp.ny;
         const C omega = (C)sp.omega;
+        const PackedBGK omega2 = packed_bgk((float)omega);
         double red[2] = {0.0, 0.0};
         // collide-and-push of one node's post-collision populations g (step ts) into dst
         auto push = [&](int x, int y, int ts, const C (&g)[9]) {
@@ -887,7 +888,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
                         const bool in1 = ex[m1] >= 1 && ex[m1] <= wa && ey[m1] >= 1 && ey[m1] <= ha;
                         if (ok[m0] && ok[m1]) {
                             float qa = 0.0f, qb = 0.0f;
-                            collide_pair(g[m0], g[m1], omega, want_a ? &qa : nullptr, want_a ? &qb : nullptr);
+                            collide_pair(g[m0], g[m1], omega2, want_a ? &qa : nullptr, want_a ? &qb : nullptr);
                             if (want_a && in0) red[0] += (double)qa;
                             if (want_a && in1) red[0] += (double)qb;
                             tile_store(sm, EH, EW, ey[m0], ex[m0], g[m0]);
@@ -926,7 +927,7 @@ __global__ void __launch_bounds__(kTileCols* TR, TR == 4 ? 2 * UQLB_STEP2_BLOCKS
                             tile_gather(sm, EH, EW, ey, ea, ga);
                             tile_gather(sm, EH, EW, ey, eb, gb);
                             float qa = 0.0f, qb = 0.0f;
-                            collide_pair(ga, gb, omega, want_b ? &qa : nullptr, want_b ? &qb : nullptr);
+                            collide_pair(ga, gb, omega2, want_b ? &qa : nullptr, want_b ? &qb : nullptr);
                             if (want_b) {
                                 red[1] += (double)qa;
                                 red[1] += (double)qb;
@@ -1180,6 +1181,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
         const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + s_sp.f_off;
         S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off;
         const float omega = (float)s_sp.omega;
+        const PackedBGK omega2 = packed_bgk(omega);
         const uint32_t sid = (uint32_t)s_sp.sample_id;
         const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         double red[2] = {0.0, 0.0};
@@ -1226,7 +1228,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane, qz, i);
                 f2 q;
-                collide_packed(g, omega, want_a ? &q : nullptr);
+                collide_packed(g, omega2, want_a ? &q : nullptr);
                 if (want_a) add_usq(red[0], q);
                 push(y, t, g);
             }
@@ -1265,7 +1267,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                 }
                 f2 qq;
                 const bool w = want_a && count;
-                collide_packed(g, omega, w ? &qq : nullptr);
+                collide_packed(g, omega2, w ? &qq : nullptr);
                 if (w) add_usq(red[0], qq);
                 f2* ring2 = reinterpret_cast<f2*>(ring);
 #pragma unroll
@@ -1295,7 +1297,7 @@ __global__ void __launch_bounds__(1024, 1) strip2_kernel(KParams p) {
                 g[7] = pk(rm[rw + xar], rm[rw + xbr]);
                 g[8] = pk(rm[2 * rw + xl], rm[2 * rw + x]);
                 f2 qq;
-                collide_packed(g, omega, want_b ? &qq : nullptr);
+                collide_packed(g, omega2, want_b ? &qq : nullptr);
                 if (want_b) add_usq(red[1], qq);
                 push(y, t + 1, g);
             }
@@ -1367,10 +1369,43 @@ __device__ __forceinline__ int ring3_plane(int i, int q) {
     }
 }
 
+// Tuning of the three-step strips (as for the two-step strips: staged phase-A rows and the
+// shared-memory share per SM; 0 = the largest), and the form of its collisions: packed pairs (0) or
+// two scalar collisions per pair (1; FP32 pipe instead of the packed pipe).
+#ifndef UQLB_STRIP3_PREFETCH_F32
+#define UQLB_STRIP3_PREFETCH_F32 UQLB_STRIP_PREFETCH_F32
+#endif
+#ifndef UQLB_STRIP3_PREFETCH_16
+#define UQLB_STRIP3_PREFETCH_16 UQLB_STRIP_PREFETCH_16
+#endif
+#ifndef UQLB_STRIP3_CARVEOUT_F32_KB
+#define UQLB_STRIP3_CARVEOUT_F32_KB UQLB_STRIP_CARVEOUT_F32_KB
+#endif
+#ifndef UQLB_STRIP3_CARVEOUT_16_KB
+#define UQLB_STRIP3_CARVEOUT_16_KB UQLB_STRIP_CARVEOUT_16_KB
+#endif
+#ifndef UQLB_STRIP3_COLLIDE
+#define UQLB_STRIP3_COLLIDE 0
+#endif
+__device__ __forceinline__ void strip3_collide(f2 (&g)[9], float omega, const PackedBGK& omega2, f2* usq) {
+    if constexpr (UQLB_STRIP3_COLLIDE == 0) {
+        collide_packed(g, omega2, usq);
+    } else {
+        float a[9], b[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) upk(g[i], a[i], b[i]);
+        float qa = 0.0f, qb = 0.0f;
+        collide_pair_scalar(a, b, omega, usq != nullptr ? &qa : nullptr, usq != nullptr ? &qb : nullptr);
+        if (usq != nullptr) *usq = pk(qa, qb);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = pk(a[i], b[i]);
+    }
+}
+
 template <typename S>
 struct Strip3Tune {
-    static constexpr int depth = StripTune<S>::depth;  // staged phase-A rows
-    static constexpr int carveout_kb = StripTune<S>::carveout_kb;
+    static constexpr int depth = sizeof(S) == 4 ? UQLB_STRIP3_PREFETCH_F32 : UQLB_STRIP3_PREFETCH_16;
+    static constexpr int carveout_kb = sizeof(S) == 4 ? UQLB_STRIP3_CARVEOUT_F32_KB : UQLB_STRIP3_CARVEOUT_16_KB;
     static constexpr int max_nx_raw = (232448 - 2048) / (2 * kRing3Planes * 4 + depth * 9 * (int)sizeof(S)) / 64 * 64;
     static constexpr int max_nx = max_nx_raw < 2048 ? max_nx_raw : 2048;
 };
@@ -1435,6 +1470,7 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
         const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + s_sp.f_off;
         S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off;
         const float omega = (float)s_sp.omega;
+        const PackedBGK omega2 = packed_bgk(omega);
         const uint32_t sid = (uint32_t)s_sp.sample_id;
         const typename Storage<S>::Q qz = quanta_of<S>(p, j);
         double red[3] = {0.0, 0.0, 0.0};
@@ -1511,7 +1547,7 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * plane, qz, i);
                 f2 q;
-                collide_packed(g, omega, want[0] ? &q : nullptr);
+                strip3_collide(g, omega, omega2, want[0] ? &q : nullptr);
                 if (want[0]) add_usq(red[0], q);
                 push(y, t, g);
             }
@@ -1548,7 +1584,7 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
                 }
                 f2 qq;
                 const bool w = want[0] && ya_row >= ya && ya_row < yb;
-                collide_packed(g, omega, w ? &qq : nullptr);
+                strip3_collide(g, omega, omega2, w ? &qq : nullptr);
                 if (w) add_usq(red[0], qq);
                 put_ring(ring1, ya_row - ya + 4, g);
             };
@@ -1566,7 +1602,7 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
                         gather(ring1, y + 1 - ya + 4, g);
                         f2 qq;
                         const bool w = want[1] && y + 1 >= ya && y + 1 < yb;
-                        collide_packed(g, omega, w ? &qq : nullptr);
+                        strip3_collide(g, omega, omega2, w ? &qq : nullptr);
                         if (w) add_usq(red[1], qq);
                         put_ring(ring2, y + 1 - ya + 4, g);
                     }
@@ -1576,7 +1612,7 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
                         f2 g[9];
                         gather(ring2, y - ya + 4, g);
                         f2 qq;
-                        collide_packed(g, omega, want[2] ? &qq : nullptr);
+                        strip3_collide(g, omega, omega2, want[2] ? &qq : nullptr);
                         if (want[2]) add_usq(red[2], qq);
                         push(y, t + 2, g);
                     }
@@ -1591,7 +1627,7 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
                         f2 g[9];
                         gather(ring1, y - ya + 4, g);
                         f2 qq;
-                        collide_packed(g, omega, want[1] ? &qq : nullptr);
+                        strip3_collide(g, omega, omega2, want[1] ? &qq : nullptr);
                         if (want[1]) add_usq(red[1], qq);
                         push(y, t + 1, g);
                     }

@@ -3,16 +3,18 @@
 // Included by one translation unit per population storage type (lbm_<type>.cu), which
 // instantiates every kernel for its type and exports the launchers as a StorageOps table.
 //
-// All samples of an ensemble live in one arena, sample-major, population-plane-major, row-major:
-//   arena[f_off(s) + i * plane(s) + y * pitch(s) + x],  g_i = f_i - w_i.
+// All samples of an ensemble live in one arena, sample-major, and every kernel addresses a
+// population as arena[f_off(s) + i * plane(s) + y * pitch(s) + x], g_i = f_i - w_i.  One-step runs
+// keep population planes (plane = cols * ny, pitch = cols); multi-step runs keep each row's nine
+// populations together (plane = cols, pitch = 9 cols), so a row is one contiguous block.
 // One-step scheme (step_kernel, persistent_kernel): the lattice is updated in place in AA order:
 // an even step reads and writes the nine populations of its own node (writing post-collision g_i
 // to slot opp(i)); an odd step reads the incoming populations from the neighbours' slots and
 // writes its outgoing populations into the neighbours' slots.  Every memory location is read and
 // then written by exactly one thread per step, so no second lattice and no intra-step
-// synchronisation are needed.  Two-step scheme (periodic batches; strip2_kernel on row strips,
-// step2_kernel on tiles): two lattices in natural layout, each launch collides, streams through
-// shared memory, collides again and pushes into the other lattice (see those kernels).
+// synchronisation are needed.  Multi-step schemes (periodic batches; strip2_kernel and strip3_kernel
+// on row strips, step2_kernel on tiles): two lattices in natural order, each launch collides,
+// streams through shared memory, collides again (once or twice) and pushes into the other lattice.
 // Boundary rules are applied where a population crosses a boundary link:
 //   periodic (TGV, Sec. 8.2): wrap-around neighbours;
 //   wall / obstacle (Sec. 8.1 no-slip): halfway bounce-back;
@@ -1672,6 +1674,306 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
 
 
 // ------------------------------------------------------------------------------------------
+// Three-step strips at a compile-time width W (a whole number of 64-column blocks): the schedule of
+// strip3_kernel with every shared-memory and global address an immediate offset from a few base
+// pointers.  The rings keep two halo columns on each side of a row (RS = W + 4 floats per plane):
+// the block's first and last pairs also write their values into the opposite halo, so the gathers of
+// the edge columns read the periodic neighbours without any index wrapping.  The lattices keep each
+// row's nine populations together (row stride 9 W, population stride W), so a row's loads and the
+// push of its three destination rows are immediate offsets from one pointer per row.
+// ------------------------------------------------------------------------------------------
+template <typename S, int W>
+__global__ void __launch_bounds__(W / 2, (512 / (W / 2)) < 1 ? 1 : ((512 / (W / 2)) > 16 ? 16 : 512 / (W / 2)))
+    strip3w_kernel(KParams p) {
+    constexpr int NP = W / 2, RS = W + 4;
+    constexpr int D = Strip3Tune<S>::depth;
+    extern __shared__ __align__(16) unsigned char s5_raw[];
+    __shared__ __align__(16) SampleDev s_sp;
+    __shared__ int s_j, s_rows, s_nact, s_flag;
+    const int tid = threadIdx.x;
+    float* ring1 = reinterpret_cast<float*>(s5_raw);  // [kRing3Planes][RS]
+    float* ring2 = ring1 + kRing3Planes * RS;
+    double* s_red = reinterpret_cast<double*>(s5_raw);
+    S* stage = reinterpret_cast<S*>(ring2 + kRing3Planes * RS);  // [D][9][W]
+    const int t = (int)p.step_counter[0] + p.dt;
+    const int t0 = (int)p.step_counter[1];
+    if (tid == 0) {
+        const int nact = active_samples(p, t);
+        s_nact = nact;
+        s_rows = p.row_base[nact];
+    }
+    __syncthreads();
+    const int nact = s_nact, rows = s_rows;
+    const int per = (rows + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * per, r1 = min(rows, r0 + per);
+    const bool series = p.qoi_every > 0 && p.series != nullptr;
+    const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    const int x = 2 * tid;
+    float* const r1t = ring1 + 2 + x;  // this thread's column x in ring 1 (column c sits at 2 + c)
+    float* const r2t = ring2 + 2 + x;
+    const bool first = tid == 0, last = tid == NP - 1;
+    // push offsets of the wrapped neighbour columns: node a's x - 1 and node b's x + 2
+    const int offl = first ? W - 1 : -1, offr = last ? 2 - W : 2;
+    for (int r = r0; r < r1;) {
+        __syncthreads();
+        if (tid == 0) {
+            int lo = 0, hi = nact - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (p.row_base[mid] <= r)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_j = lo;
+        }
+        __syncthreads();
+        const int j = s_j;
+        if (tid < 32) reinterpret_cast<uint32_t*>(&s_sp)[tid] = __ldg(reinterpret_cast<const uint32_t*>(p.samples + j) + tid);
+        __syncthreads();
+        const int rb = p.row_base[j];
+        const int ny = s_sp.ny;
+        const int ya = r - rb, yb = min(ny, r1 - rb);
+        r = rb + yb;
+        const int n = min(3, s_sp.steps - t);
+        bool want[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) want[k] = series && k < n && ((t + k) % p.qoi_every) == 0;
+        const bool second = ((p.sel[s_sp.slot] ^ ((t - t0) / 3)) & 1) != 0;
+        const S* src = static_cast<const S*>(second ? p.arena2 : p.arena) + s_sp.f_off + x;
+        S* dst = static_cast<S*>(second ? p.arena : p.arena2) + s_sp.f_off + x;
+        const float omega = (float)s_sp.omega;
+        const PackedBGK omega2 = packed_bgk(omega);
+        const uint32_t sid = (uint32_t)s_sp.sample_id;
+        const typename Storage<S>::Q qz = quanta_of<S>(p, j);
+        double red[3] = {0.0, 0.0, 0.0};
+        auto wrap = [&](int y) {
+            y += y < 0 ? ny : 0;
+            y += y < 0 ? ny : 0;
+            y -= y >= ny ? ny : 0;
+            y -= y >= ny ? ny : 0;
+            return y;
+        };
+        auto st1 = [&](S* d, float v, uint32_t h, int i) {
+            if (sr)
+                Storage<S>::store_sr(d, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
+            else
+                Storage<S>::store(d, v, qz, i);
+        };
+        auto st2 = [&](S* d, f2 v, uint32_t ha, uint32_t hb, int i) {
+            if (sr) {
+                float a, b;
+                upk(v, a, b);
+                st1(d, a, ha, i);
+                st1(d + 1, b, hb, i);
+            } else {
+                pair_store<S>(d, v, qz, i);
+            }
+        };
+        // push of the pair's post-collision populations g (step ts, row y) into the other lattice
+        auto push = [&](int y, int ts, const f2 (&g)[9]) {
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            uint32_t ha = 0u, hb = 0u;
+            if (sr) {
+                const uint32_t base = (uint32_t)ts * 0x85EBCA77u + sid * 0xC2B2AE3Du;
+                ha = mix32((uint32_t)(y * 9 * W + x) * 0x9E3779B1u + base);
+                hb = mix32((uint32_t)(y * 9 * W + x + 1) * 0x9E3779B1u + base);
+            }
+            float a, b;
+            {  // row y: populations 0, 1, 3
+                S* R = dst + y * (9 * W);
+                st2(R, g[0], ha, hb, 0);
+                upk(g[1], a, b);
+                st1(R + W + 1, a, ha, 1);
+                st1(R + offr + W, b, hb, 1);
+                upk(g[3], a, b);
+                st1(R + offl + 3 * W, a, ha, 3);
+                st1(R + 3 * W, b, hb, 3);
+            }
+            {  // row y + 1: populations 2, 5, 6
+                S* R = dst + yp * (9 * W);
+                st2(R + 2 * W, g[2], ha, hb, 2);
+                upk(g[5], a, b);
+                st1(R + 5 * W + 1, a, ha, 5);
+                st1(R + offr + 5 * W, b, hb, 5);
+                upk(g[6], a, b);
+                st1(R + offl + 6 * W, a, ha, 6);
+                st1(R + 6 * W, b, hb, 6);
+            }
+            {  // row y - 1: populations 4, 7, 8
+                S* R = dst + ym * (9 * W);
+                st2(R + 4 * W, g[4], ha, hb, 4);
+                upk(g[7], a, b);
+                st1(R + offl + 7 * W, a, ha, 7);
+                st1(R + 7 * W, b, hb, 7);
+                upk(g[8], a, b);
+                st1(R + 8 * W + 1, a, ha, 8);
+                st1(R + offr + 8 * W, b, hb, 8);
+            }
+        };
+        auto add_usq = [&](double& acc, f2 q) {
+            float a, b;
+            upk(q, a, b);
+            acc += (double)a + (double)b;
+        };
+        // ring plane offsets of row index q: the c_y = +1 / 0 / -1 groups (3 / 2 / 1 slots)
+        auto slot_p = [](int q) { return (q % 3) * 3 * RS; };
+        auto slot_z = [](int q) { return (9 + (q & 1) * 3) * RS; };
+        auto put_ring = [&](float* rt, int q, const f2 (&g)[9]) {
+            const int op = slot_p(q), oz = slot_z(q), om = 15 * RS;
+            auto put = [&](int off, f2 v) {
+                *reinterpret_cast<f2*>(rt + off) = v;
+                if (first) *reinterpret_cast<f2*>(rt + off + W) = v;  // right halo: columns 0, 1 after W - 1
+                if (last) *reinterpret_cast<f2*>(rt + off - W) = v;   // left halo: columns W - 2, W - 1 before 0
+            };
+            put(op, g[2]);
+            put(op + RS, g[5]);
+            put(op + 2 * RS, g[6]);
+            put(oz, g[0]);
+            put(oz + RS, g[1]);
+            put(oz + 2 * RS, g[3]);
+            put(om, g[4]);
+            put(om + RS, g[7]);
+            put(om + 2 * RS, g[8]);
+        };
+        // gather of row index q (population i from row q - c_iy, column x - c_ix)
+        auto gather = [&](const float* rt, int q, f2 (&g)[9]) {
+            const float* pp = rt + slot_p(q - 1);
+            const float* pz = rt + slot_z(q);
+            const float* pm = rt + 15 * RS;
+            g[0] = *reinterpret_cast<const f2*>(pz);
+            g[1] = pk(pz[RS - 1], pz[RS]);
+            g[3] = pk(pz[2 * RS + 1], pz[2 * RS + 2]);
+            g[2] = *reinterpret_cast<const f2*>(pp);
+            g[5] = pk(pp[RS - 1], pp[RS]);
+            g[6] = pk(pp[2 * RS + 1], pp[2 * RS + 2]);
+            g[4] = *reinterpret_cast<const f2*>(pm);
+            g[7] = pk(pm[RS + 1], pm[RS + 2]);
+            g[8] = pk(pm[2 * RS - 1], pm[2 * RS]);
+        };
+        if (n == 1) {
+            for (int y = ya; y < yb; ++y) {
+                const S* s0 = src + y * (9 * W);
+                f2 g[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * W, qz, i);
+                f2 q;
+                collide_packed(g, omega2, want[0] ? &q : nullptr);
+                if (want[0]) add_usq(red[0], q);
+                push(y, t, g);
+            }
+        } else {
+            const int a0 = ya - (n - 1);
+            auto fetch = [&](int qa) {
+                if (a0 + qa <= yb + n - 2) {
+                    const S* s0 = src + wrap(a0 + qa) * (9 * W);
+                    S* st = stage + (qa % (D > 0 ? D : 1)) * 9 * W + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) cp_async<2 * sizeof(S)>(st + i * W, s0 + i * W);
+                }
+                cp_async_commit();
+            };
+            (void)fetch;
+            auto phase_a = [&](int row) {
+                const int qa = row - a0;
+                f2 g[9];
+                if constexpr (D > 0) {
+                    cp_async_wait<D - 1>();
+                    const S* st = stage + (qa % D) * 9 * W + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * W, qz, i);
+                    fetch(qa + D);
+                } else {
+                    const S* s0 = src + wrap(row) * (9 * W);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(s0 + i * W, qz, i);
+                }
+                f2 qq;
+                const bool w = want[0] && row >= ya && row < yb;
+                collide_packed(g, omega2, w ? &qq : nullptr);
+                if (w) add_usq(red[0], qq);
+                put_ring(r1t, row - ya + 4, g);
+            };
+#pragma unroll
+            for (int k = 0; k < D; ++k) fetch(k);
+            if (n == 3) {
+                phase_a(ya - 2);
+                phase_a(ya - 1);
+                for (int y = ya - 2; y < yb; ++y) {
+                    phase_a(y + 2);
+                    __syncthreads();
+                    {
+                        f2 g[9];
+                        gather(r1t, y + 1 - ya + 4, g);
+                        f2 qq;
+                        const bool w = want[1] && y + 1 >= ya && y + 1 < yb;
+                        collide_packed(g, omega2, w ? &qq : nullptr);
+                        if (w) add_usq(red[1], qq);
+                        put_ring(r2t, y + 1 - ya + 4, g);
+                    }
+                    __syncthreads();
+                    if (y >= ya) {
+                        f2 g[9];
+                        gather(r2t, y - ya + 4, g);
+                        f2 qq;
+                        collide_packed(g, omega2, want[2] ? &qq : nullptr);
+                        if (want[2]) add_usq(red[2], qq);
+                        push(y, t + 2, g);
+                    }
+                }
+            } else {
+                phase_a(ya - 1);
+                for (int y = ya - 1; y < yb; ++y) {
+                    phase_a(y + 1);
+                    __syncthreads();
+                    if (y >= ya) {
+                        f2 g[9];
+                        gather(r1t, y - ya + 4, g);
+                        f2 qq;
+                        collide_packed(g, omega2, want[1] ? &qq : nullptr);
+                        if (want[1]) add_usq(red[1], qq);
+                        push(y, t + 1, g);
+                    }
+                    __syncthreads();
+                }
+            }
+            if constexpr (D > 0) cp_async_wait<0>();
+        }
+        if (want[0] || want[1] || want[2]) {
+            __syncthreads();
+            block_sum_dyn<3>(red, s_red);
+            if (tid == 0) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) p.partials[(int64_t)(rb + ya) * 3 + k] = red[k];
+                __threadfence();
+                const int prev = atomicAdd(p.counters + j, yb - ya);
+                s_flag = (prev + (yb - ya) == ny);
+            }
+            __syncthreads();
+            if (s_flag) {
+                __threadfence();
+                double acc[3] = {0.0, 0.0, 0.0};
+                for (int q = tid; q < ny; q += NP) {
+                    if (q == 0 || (rb + q) % per == 0) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) acc[k] += __ldcg(p.partials + (int64_t)(rb + q) * 3 + k);
+                    }
+                }
+                block_sum_dyn<3>(acc, s_red);
+                if (tid == 0) {
+                    const int64_t row = (int64_t)s_sp.sample_id * p.series_ld;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (want[k]) p.series[row + (t + k) / p.qoi_every] = acc[k] * s_sp.u_ref_inv2;
+                    p.counters[j] = 0;
+                }
+            }
+        }
+    }
+}
+
+
+// ------------------------------------------------------------------------------------------
 // Final fields and per-sample scalars at the last step run.
 // ------------------------------------------------------------------------------------------
 template <typename S, bool MIXED>
@@ -2255,11 +2557,64 @@ int strip3_resident(int nx) {
     return n;
 }
 
+template <typename S, int W>
+size_t strip3w_smem() {
+    return (size_t)2 * kRing3Planes * (W + 4) * sizeof(float) + (size_t)Strip3Tune<S>::depth * 9 * W * sizeof(S);
+}
+
+// Resident blocks per SM of the fixed-width three-step strips (once).
+template <typename S, int W>
+int strip3w_resident() {
+    constexpr int kb = Strip3Tune<S>::carveout_kb;
+    static int n = 0;
+    if (n == 0) {
+        cudaFuncSetAttribute(strip3w_kernel<S, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip3w_smem<S, W>());
+        if (kb > 0)
+            cudaFuncSetAttribute(strip3w_kernel<S, W>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip3w_kernel<S, W>, W / 2, strip3w_smem<S, W>()) !=
+                cudaSuccess || b < 1)
+            b = 1;
+        if (kb > 0) {
+            cudaFuncAttributes fa{};
+            cudaFuncGetAttributes(&fa, strip3w_kernel<S, W>);
+            const size_t per = strip3w_smem<S, W>() + fa.sharedSizeBytes + 1024;
+            b = std::max(1, std::min(b, (int)((size_t)kb * 1024 / per)));
+        }
+        n = b;
+    }
+    return n;
+}
+
+template <typename S, int W>
+cudaError_t launch_strip3w(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const int64_t resident = (int64_t)strip3w_resident<S, W>() * sm_count();
+    if (prepare_only) return cudaGetLastError();
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
+    strip3w_kernel<S, W><<<grid, W / 2, strip3w_smem<S, W>(), s>>>(p);
+    return cudaGetLastError();
+}
+
+#ifndef UQLB_STRIP3_FIXED_WIDTHS
+#define UQLB_STRIP3_FIXED_WIDTHS 1
+#endif
+
 template <typename S>
 cudaError_t launch_strip3_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
     const int np = strip_threads(g.strip_nx);
     if (g.strip_nx < 2 || 2 * np > Strip3Tune<S>::max_nx) return cudaErrorInvalidConfiguration;
     const bool generic = g.strip_nx != 2 * np;
+    if (UQLB_STRIP3_FIXED_WIDTHS && !generic) {
+        // the widths with a compile-time instantiation (immediate addressing)
+        switch (g.strip_nx) {
+            case 64: return launch_strip3w<S, 64>(p, g, s, prepare_only);
+            case 128: return launch_strip3w<S, 128>(p, g, s, prepare_only);
+            case 256: return launch_strip3w<S, 256>(p, g, s, prepare_only);
+            case 512: return launch_strip3w<S, 512>(p, g, s, prepare_only);
+            case 1024: return launch_strip3w<S, 1024>(p, g, s, prepare_only);
+            default: break;
+        }
+    }
     const int64_t resident =
         (int64_t)(generic ? strip3_resident<S, true>(g.strip_nx) : strip3_resident<S, false>(g.strip_nx)) * sm_count();
     if (prepare_only) return cudaGetLastError();

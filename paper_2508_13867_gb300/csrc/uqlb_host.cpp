@@ -522,8 +522,13 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         SampleDev& d = P.table[j];
         d.nx = s.nx;
         d.ny = s.ny;
-        d.pitch = (int32_t)align_up((size_t)s.nx, (size_t)row_align);
-        d.plane = (int64_t)d.pitch * s.ny;
+        // one-step runs: population planes of ny rows (arena[i * plane + y * pitch + x]); the
+        // multi-step kernels keep a row's nine populations together, row after row
+        // (arena[(9 y + i) cols + x]), expressed in the same fields as plane = cols, pitch = 9 cols, so
+        // that a row load or push is one block of 9 cols values
+        const int32_t cols = (int32_t)align_up((size_t)s.nx, (size_t)row_align);
+        d.pitch = two ? 9 * cols : cols;
+        d.plane = two ? (int64_t)cols : (int64_t)cols * s.ny;
         d.f_off = f_off_of[order[j]];
         d.slot = (int32_t)order[j];
         d.kind = s.kind;

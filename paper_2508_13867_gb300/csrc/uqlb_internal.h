@@ -16,9 +16,11 @@ namespace uqlb {
 // form a prefix of the table.
 struct alignas(16) SampleDev {
     int64_t f_off;      // element offset of the sample's populations in the arena
-    int64_t plane;      // elements per population plane (pitch * ny)
+    int64_t plane;      // element stride between populations: cols * ny (one-step runs) or cols
+                        // (multi-step runs, whose rows keep their nine populations together)
     int32_t nx, ny;
-    int32_t pitch;      // row pitch in elements (multiple of 32 elements)
+    int32_t pitch;      // element stride between rows: cols (one-step) or 9 cols (multi-step); cols = nx
+                        // rounded up to 128 bytes
     int32_t kind;       // UQLB_CASE_TGV / UQLB_CASE_CHANNEL
     int32_t steps;      // steps to run (TGV) or step cap (CHANNEL)
     int32_t sample_id;  // row of the sample in the caller's outputs

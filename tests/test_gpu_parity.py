@@ -808,12 +808,13 @@ def test_two_step_16_bit_storage_against_the_oracle(ens, storage, scheme):
 
 
 @pytest.mark.parametrize("scheme", ["two_step_strips", "three_step_strips"])
-@pytest.mark.parametrize("n", [31, 97, 40, 64, 832])
+@pytest.mark.parametrize("n", [31, 97, 40, 64, 256, 832, 1024])
 def test_strip_kernel_edge_geometries_against_the_oracle(ens, n, scheme):
     """The row strips (FP32, two and three steps per launch) against the oracle directly, at the
     geometries whose index arithmetic differs: odd widths (31, 97: the last pair is a lone node whose
-    partner is dropped), a width that leaves threads past the row (40), a full block (64) and an odd
-    multiple of 64 (832); heights equal to the width, ragged (37) and degenerate (3, 2: the rows above
+    partner is dropped), a width that leaves threads past the row (40), full blocks (64, 256 and 1024,
+    which the three-step strips run on their compile-time-width kernel) and an odd multiple of 64
+    (832, on the runtime-width kernel); heights equal to the width, ragged (37) and degenerate (3, 2: the rows above
     and below a node coincide); step counts whose last launch runs one step (61, 1), two (62) or three
     (60) or that stop at once (0); K at every step and at a stride of 7.  The Taylor-Green field on 2 and 3 rows is a mode
     near the lattice's Nyquist wavenumber that decays by a factor of 2 to 3 per step (2600x in 9

@@ -1682,9 +1682,24 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
 // row's nine populations together (row stride 9 W, population stride W), so a row's loads and the
 // push of its three destination rows are immediate offsets from one pointer per row.
 // ------------------------------------------------------------------------------------------
+// Threads per SM the register budget of the fixed-width strips is sized for (65536 registers over
+// them).  Measured on the 625 x 256^2 ensemble (kernel GLUPS at 512 / 768 / 1024 threads): FP32 230 /
+// 221 / 216 (four blocks fit the shared memory; more registers serve them best), FX16 167 / 190 / 195,
+// BF16 185 / 201 / 212 (six blocks fit; the register budget then decides how many run).
+#ifndef UQLB_STRIP3W_THREADS_F32
+#define UQLB_STRIP3W_THREADS_F32 512
+#endif
+#ifndef UQLB_STRIP3W_THREADS_16
+#define UQLB_STRIP3W_THREADS_16 1024
+#endif
+template <typename S>
+constexpr int strip3w_min_blocks(int np) {
+    constexpr int th = sizeof(S) == 4 ? UQLB_STRIP3W_THREADS_F32 : UQLB_STRIP3W_THREADS_16;
+    return th / np < 1 ? 1 : (th / np > 16 ? 16 : th / np);
+}
+
 template <typename S, int W>
-__global__ void __launch_bounds__(W / 2, (512 / (W / 2)) < 1 ? 1 : ((512 / (W / 2)) > 16 ? 16 : 512 / (W / 2)))
-    strip3w_kernel(KParams p) {
+__global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_kernel(KParams p) {
     constexpr int NP = W / 2, RS = W + 4;
     constexpr int D = Strip3Tune<S>::depth;
     extern __shared__ __align__(16) unsigned char s5_raw[];
@@ -1819,22 +1834,33 @@ __global__ void __launch_bounds__(W / 2, (512 / (W / 2)) < 1 ? 1 : ((512 / (W / 
         // ring plane offsets of row index q: the c_y = +1 / 0 / -1 groups (3 / 2 / 1 slots)
         auto slot_p = [](int q) { return (q % 3) * 3 * RS; };
         auto slot_z = [](int q) { return (9 + (q & 1) * 3) * RS; };
+        // the halo copy of the block's first pair (right halo: columns 0, 1 after W - 1) and last pair
+        // (left halo: columns W - 2, W - 1 before 0)
+        const int hoff = first ? W : -W;
         auto put_ring = [&](float* rt, int q, const f2 (&g)[9]) {
             const int op = slot_p(q), oz = slot_z(q), om = 15 * RS;
-            auto put = [&](int off, f2 v) {
-                *reinterpret_cast<f2*>(rt + off) = v;
-                if (first) *reinterpret_cast<f2*>(rt + off + W) = v;  // right halo: columns 0, 1 after W - 1
-                if (last) *reinterpret_cast<f2*>(rt + off - W) = v;   // left halo: columns W - 2, W - 1 before 0
-            };
-            put(op, g[2]);
-            put(op + RS, g[5]);
-            put(op + 2 * RS, g[6]);
-            put(oz, g[0]);
-            put(oz + RS, g[1]);
-            put(oz + 2 * RS, g[3]);
-            put(om, g[4]);
-            put(om + RS, g[7]);
-            put(om + 2 * RS, g[8]);
+            auto put = [&](float* at, int off, f2 v) { *reinterpret_cast<f2*>(at + off) = v; };
+            put(rt, op, g[2]);
+            put(rt, op + RS, g[5]);
+            put(rt, op + 2 * RS, g[6]);
+            put(rt, oz, g[0]);
+            put(rt, oz + RS, g[1]);
+            put(rt, oz + 2 * RS, g[3]);
+            put(rt, om, g[4]);
+            put(rt, om + RS, g[7]);
+            put(rt, om + 2 * RS, g[8]);
+            if (first || last) {
+                float* h = rt + hoff;
+                put(h, op, g[2]);
+                put(h, op + RS, g[5]);
+                put(h, op + 2 * RS, g[6]);
+                put(h, oz, g[0]);
+                put(h, oz + RS, g[1]);
+                put(h, oz + 2 * RS, g[3]);
+                put(h, om, g[4]);
+                put(h, om + RS, g[7]);
+                put(h, om + 2 * RS, g[8]);
+            }
         };
         // gather of row index q (population i from row q - c_iy, column x - c_ix)
         auto gather = [&](const float* rt, int q, f2 (&g)[9]) {

@@ -36,9 +36,9 @@ STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in plac
                     "collided again, pushed to the other lattice)", "step2_kernel", "two-step-v2-packed"),
                 4: ("strip2_kernel (two-step row strips: each row collided into a shared-memory ring, streamed "
                     "and collided again, pushed to the other lattice)", "strip2_kernel", "two-step-strips-v2-staged"),
-                6: ("strip3_kernel (three-step row strips: each row collided into a first shared-memory ring, "
-                    "streamed and collided into a second, streamed and collided again, pushed to the other "
-                    "lattice)", "strip3_kernel", "three-step-strips-v1")}
+                6: ("strip3w_kernel (three-step row strips at a compile-time width: each row collided into a "
+                    "first shared-memory ring, streamed and collided into a second, streamed and collided again, "
+                    "pushed to the other lattice)", "strip3w_kernel", "three-step-strips-fixed-width-v1")}
 STEPS_PER_LAUNCH = {1: 1, 3: 2, 4: 2, 6: 3}
 
 
@@ -571,7 +571,7 @@ def bench_workload(args):
         line.update({"samples": len(smp), "value": upd / (ms / 1e3) / 1e6, "batch_seconds": ms / 1e3,
                      "tile_geometry": tuned, "scheme": args.scheme,
                      "ran_as": {0: "auto", 1: "one_step", 3: "two_step_tiles", 4: "two_step_strips",
-                                5: "groups", 6: "three_step_strips"}[U.uqlb_last_run_geometry(ens.ctx)[0]]})
+                                5: "groups", 6: "three_step_strips", 7: "cluster"}[U.uqlb_last_run_geometry(ens.ctx)[0]]})
         if args.plain_samples > 0:
             step = max(1, len(smp) // args.plain_samples)
             psub = smp[::step]
@@ -812,7 +812,8 @@ def main():
     ap.add_argument("--npt", type=int, default=0)
     ap.add_argument("--rounding", default="auto", choices=["auto", "nearest", "stochastic"])
     ap.add_argument("--scheme", default="auto",
-                    choices=["auto", "one_step", "two_step", "two_step_tiles", "two_step_strips", "three_step_strips"],
+                    choices=["auto", "one_step", "two_step", "two_step_tiles", "two_step_strips", "three_step_strips",
+                             "cluster"],
                     help="time-stepping scheme (auto: two-step for periodic FP32/16-bit batches)")
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent"],
                     help="kernel-only: one launch per step (CUDA graphs) or one cooperative launch per chunk")

@@ -241,7 +241,8 @@ enum {
     UQLB_SCHEME_TWO_STEP_TILES = 3,
     UQLB_SCHEME_TWO_STEP_STRIPS = 4,
     UQLB_SCHEME_GROUPED = 5, /* reported only: the batch ran as groups (UQLB_SCHEME_AUTO) */
-    UQLB_SCHEME_THREE_STEP_STRIPS = 6
+    UQLB_SCHEME_THREE_STEP_STRIPS = 6,
+    UQLB_SCHEME_CLUSTER = 7
 };
 
 /* Execution of the time loop.

@@ -42,6 +42,8 @@ struct KParams {
     int32_t max_steps;
     int32_t stochastic;  // 16-bit storage: stochastic rounding of every population store
     int32_t spl;         // time steps per launch of the multi-step schemes (2 or 3)
+    int32_t natural;     // the lattice holds the state in natural layout (cluster runs; finalize reads it so)
+    int32_t cluster_size, cluster_cw, cluster_ny;  // cluster runs: blocks per cluster, columns per block, rows
     // outputs
     void* fields;
     int64_t fields_ld;
@@ -63,6 +65,8 @@ struct StorageOps {
     cudaError_t (*finalize)(const KParams&, const BatchGeometry&, cudaStream_t);
     cudaError_t (*inout)(const KParams&, const BatchGeometry&, cudaStream_t);
     cudaError_t (*bouzidi_force)(const KParams&, const BatchGeometry&, cudaStream_t);
+    // cluster runs: the whole time loop of every sample in one launch (prepare_only: opt-ins only)
+    cudaError_t (*cluster)(const KParams&, const BatchGeometry&, cudaStream_t, bool prepare_only);
 };
 const StorageOps& storage_ops_f64();
 const StorageOps& storage_ops_f32();

@@ -2000,6 +2000,281 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
 
 
 // ------------------------------------------------------------------------------------------
+// Channel samples held on chip: one thread-block cluster per sample runs its whole time loop.
+// ------------------------------------------------------------------------------------------
+// The C blocks of a cluster split the sample's columns into C slabs of cw columns; each block keeps
+// its slab's populations twice in shared memory (the state at t and at t + 1, natural layout
+// [9][ny][cw] of the storage type), so HBM is touched only to load the state at the start and to
+// write it back at the end.  A step is the one-step kernel's push form: every fluid node reads its
+// own nine populations, collides them (BGK, the same formulas), and writes each post-collision
+// population into the neighbour it streams to, or applies the boundary rule of its link there
+// (halfway bounce-back on walls and obstacle, moving-wall inlet, pressure outlet with the node's own
+// velocity).  Populations that cross into a neighbouring slab are stored into that block's shared
+// memory (distributed shared memory of the cluster).  The cluster synchronises once per step with the
+// hardware cluster barrier, which every thread of every block reaches at every step (the step loop
+// and the stop decision are uniform over the cluster), so no wait depends on a flag.  Link classes of
+// every node are precomputed once into shared memory (3 bits per direction).
+// Forces at the QoI steps: block sums in shared memory, added by block 0 in rank order; block 0
+// records C_D and C_L and takes the steady-state decision, which every block reads after a second
+// barrier.  Samples with the Bouzidi obstacle or the interpolated inlet/outlet take the one-step
+// kernel instead.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_id_x() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+// Generic address of the same shared-memory location in block `rank` of the cluster.
+template <typename T>
+__device__ __forceinline__ T* cluster_map(T* p, unsigned rank) {
+    T* q;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(q) : "l"(p), "r"(rank));
+    return q;
+}
+
+constexpr int kClusterThreads = 256;
+
+template <typename S>
+__global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
+    extern __shared__ __align__(16) unsigned char s6_raw[];
+    __shared__ __align__(16) SampleDev s_sp;
+    __shared__ double s_red[(kClusterThreads / 32) * 2];
+    __shared__ double s_force[2];   // this block's force partial of the step (read by block 0)
+    __shared__ int s_stop;          // block 0: 1 once the sample stops
+    using C = typename Storage<S>::C;
+    const int tid = threadIdx.x;
+    const unsigned rank = cluster_rank(), nrank = cluster_size();
+    const int j = (int)cluster_id_x();  // sample (table order)
+    if (tid < 32) reinterpret_cast<uint32_t*>(&s_sp)[tid] = __ldg(reinterpret_cast<const uint32_t*>(p.samples + j) + tid);
+    if (tid == 0) s_stop = 0;
+    __syncthreads();
+    const SampleDev& sp = s_sp;
+    const int nx = sp.nx, ny = sp.ny, cw = p.cluster_cw;
+    const int x0 = (int)rank * cw, ncol = max(0, min(cw, nx - x0));  // this block's columns [x0, x0 + ncol)
+    const int pl = ny * cw;                                           // one population plane of a slab
+    S* bufA = reinterpret_cast<S*>(s6_raw);
+    S* bufB = bufA + 9 * pl;
+    uint32_t* links = reinterpret_cast<uint32_t*>(bufB + 9 * pl);     // [ny][cw] link classes
+    const typename Storage<S>::Q qz = quanta_of<S>(p, j);
+    const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
+    S* glob = static_cast<S*>(p.arena) + sp.f_off;
+    const int t0 = (int)p.step_counter[1];
+    const int T = sp.steps;
+    const bool skip = p.done[sp.slot] != 0 || t0 >= T;
+    // load the state at t0 (natural layout) and classify the links of every owned node:
+    // class of direction i in bits 3i..3i+2 (kInterior .. kSolid); solid nodes get all ones
+    for (int n = tid; n < ny * ncol; n += kClusterThreads) {
+        const int y = n / ncol, lx = n - y * ncol, x = x0 + lx;
+        const int64_t own = (int64_t)y * sp.pitch + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) bufA[i * pl + y * cw + lx] = glob[i * sp.plane + own];
+        uint32_t w = 0u;
+        if (mask != nullptr && mask_solid(mask, mask_words(sp), x, y)) {
+            w = 0xFFFFFFFFu;
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) w |= (uint32_t)classify(sp, mask, x + cx(i), y + cy(i)) << (3 * i);
+        }
+        links[y * cw + lx] = w;
+    }
+    // generic addresses of the neighbouring blocks' buffers (same layout in every block)
+    const unsigned left = rank > 0 ? rank - 1 : rank, right = rank + 1 < nrank ? rank + 1 : rank;
+    S* const leftA = cluster_map(bufA, left);
+    S* const leftB = cluster_map(bufB, left);
+    S* const rightA = cluster_map(bufA, right);
+    S* const rightB = cluster_map(bufB, right);
+    int* const stop0 = cluster_map(&s_stop, 0u);
+    cluster_sync_all();
+    const C omega = (C)sp.omega;
+    const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    // each thread walks the same owned nodes at every step: node tid, tid + T, ... of the slab in
+    // row-major order, stepped without divisions
+    const int nnodes = ny * ncol;
+    const int walk_r = ncol > 0 ? kClusterThreads / ncol : 0, walk_c = ncol > 0 ? kClusterThreads % ncol : 0;
+    const int ystart = ncol > 0 ? tid / ncol : 0, lxstart = ncol > 0 ? tid % ncol : 0;
+    const uint32_t sid = (uint32_t)sp.sample_id;
+    S* cur = bufA;
+    S* nxt = bufB;
+    bool odd = false;  // which buffer holds the state: A (false) or B (true)
+    int t = t0;
+    for (; t < T && !skip; ++t) {
+        const bool f_step = p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
+        S* const nl = odd ? leftA : leftB;   // the neighbours' next-state buffers
+        S* const nr = odd ? rightA : rightB;
+        double fx = 0.0, fy = 0.0;
+        int y = ystart, lx = lxstart;
+        for (int n = tid; n < nnodes; n += kClusterThreads) {
+            const int x = x0 + lx;
+            const int yy0 = y, lx0 = lx;
+            lx += walk_c;
+            y += walk_r + (lx >= ncol ? 1 : 0);
+            lx -= lx >= ncol ? ncol : 0;
+            const int y_ = yy0;
+            const uint32_t lw = links[y_ * cw + lx0];
+            if (lw == 0xFFFFFFFFu) continue;  // solid
+            const int own = y_ * cw + lx0;
+            C g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(cur + i * pl + own, qz, i);
+            C drho, jx, jy, ux, uy;
+            moments(g, drho, jx, jy, ux, uy);
+            bgk(g, omega, drho, jx, jy, ux, uy);
+            const uint32_t h = sr ? mix32((uint32_t)((int64_t)y_ * sp.pitch + x) * 0x9E3779B1u +
+                                          (uint32_t)t * 0x85EBCA77u + sid * 0xC2B2AE3Du)
+                                  : 0u;
+            auto put = [&](S* ptr, C v, int i) {
+                if (sr)
+                    Storage<S>::store_sr(ptr, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
+                else
+                    Storage<S>::store(ptr, v, qz, i);
+            };
+            put(nxt + own, g[0], 0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int cls = (lw >> (3 * i)) & 7;
+                const int o = opp(i);
+                if (cls == kInterior) {
+                    const int dl = lx0 + cx(i), dy = y_ + cy(i);
+                    S* base = nxt;
+                    int col = dl;
+                    if (dl < 0) {
+                        base = nl;
+                        col = cw - 1;
+                    } else if (dl >= ncol) {
+                        base = nr;
+                        col = 0;
+                    }
+                    put(base + i * pl + dy * cw + col, g[i], i);
+                } else if (cls == kWall || cls == kSolid) {
+                    put(nxt + o * pl + own, g[i], i);
+                    if (f_step && cls == kSolid) {
+                        const C fs = g[i] + wgt<C>(i);
+                        fx += (double)(C(2 * cx(i)) * fs);
+                        fy += (double)(C(2 * cy(i)) * fs);
+                    }
+                } else if (cls == kInlet) {
+                    const C yy = C(y_) + C(0.5) - C(0.5) * C(cy(o));
+                    put(nxt + o * pl + own, g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
+                } else {
+                    const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
+                    put(nxt + o * pl + own, -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
+                }
+            }
+        }
+        if (f_step) {
+            double v[2] = {fx, fy};
+            block_sum<2, kClusterThreads>(v, s_red);
+            if (tid == 0) {
+                s_force[0] = v[0];
+                s_force[1] = v[1];
+            }
+        }
+        cluster_sync_all();  // the next state is complete in every block (and this state is no longer read)
+        S* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        odd = !odd;
+        if (f_step) {
+            if (rank == 0 && tid == 0) {
+                double F[2] = {0.0, 0.0};
+                for (unsigned r = 0; r < nrank; ++r) {
+                    const double* f = cluster_map(s_force, r);
+                    F[0] += f[0];
+                    F[1] += f[1];
+                }
+                record_force(p, sp, j, t + 1, F[0], F[1]);
+                s_stop = p.done[sp.slot];
+            }
+            cluster_sync_all();  // block 0's decision is visible
+            if (*(volatile int*)stop0 != 0) {
+                ++t;
+                break;
+            }
+        }
+    }
+    // the state at the last step run back to the arena (natural layout)
+    if (!skip) {
+        for (int n = tid; n < ny * ncol; n += kClusterThreads) {
+            const int y = n / ncol, lx = n - y * ncol, x = x0 + lx;
+            const int64_t own = (int64_t)y * sp.pitch + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) glob[i * sp.plane + own] = cur[i * pl + y * cw + lx];
+        }
+        if (rank == 0 && tid == 0 && !p.done[sp.slot]) p.steps_run[sp.slot] = t;
+    }
+    cluster_sync_all();  // no block leaves while another may still read its shared memory
+}
+
+template <typename S>
+size_t cluster_smem(int cw, int ny) {
+    return (size_t)2 * 9 * cw * ny * sizeof(S) + (size_t)cw * ny * sizeof(uint32_t);
+}
+
+template <typename S>
+cudaError_t launch_cluster_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const int csize = p.cluster_size, cw = p.cluster_cw;
+    if (csize < 1 || csize > 16 || cw < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = cluster_smem<S>(cw, p.cluster_ny);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
+        attr = true;
+    }
+    if (prepare_only) return cudaGetLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(g.nsamples * csize));
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cluster_kernel<S>, p);
+}
+
+// Clusters of `csize` blocks with `smem` bytes each that can run at once (0: none).
+template <typename S>
+int cluster_capacity(int csize, size_t smem) {
+    cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)csize);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel<S>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+
+// ------------------------------------------------------------------------------------------
 // Final fields and per-sample scalars at the last step run.
 // ------------------------------------------------------------------------------------------
 template <typename S, bool MIXED>
@@ -2040,7 +2315,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(KParams p, int64_t total_
                     for (int i = 0; i < 9; ++i)
                         if (Storage<S>::at_limit(base + i * sp.plane + own)) red[6] += 1.0;
                 }
-                if (two || (T & 1) == 0) {
+                if (two || p.natural || (T & 1) == 0) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(base + i * sp.plane + own, qz, i);
                 } else {
@@ -2668,6 +2943,38 @@ cudaError_t launch_persistent_any(const KParams& p, const BatchGeometry& g, int 
 }
 
 template <typename S>
+cudaError_t launch_cluster_any(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    if constexpr (sizeof(S) == 8) {
+        return cudaErrorInvalidConfiguration;  // FP64 lattices do not fit a cluster's shared memory
+    } else {
+        // cluster size: every size of 1..16 whose blocks hold the widest sample's slab; among them the
+        // one that keeps the most SMs busy (clusters that run at once x blocks per cluster), smaller
+        // clusters on ties
+        KParams q = p;
+        int best_c = 0, best_cw = 0;
+        int64_t best_units = 0;
+        for (int c = 1; c <= 16; c *= 2) {
+            const int cw = (g.cluster_nx + c - 1) / c;
+            const size_t smem = cluster_smem<S>(cw, g.cluster_ny);
+            if (smem > 227 * 1024 - 4096) continue;
+            const int cap = cluster_capacity<S>(c, smem);
+            if (cap < 1) continue;
+            const int64_t units = std::min<int64_t>(cap, g.nsamples) * c;
+            if (units > best_units) {
+                best_units = units;
+                best_c = c;
+                best_cw = cw;
+            }
+        }
+        if (best_c == 0) return cudaErrorInvalidConfiguration;
+        q.cluster_size = best_c;
+        q.cluster_cw = best_cw;
+        q.cluster_ny = g.cluster_ny;
+        return launch_cluster_s<S>(q, g, s, prepare_only);
+    }
+}
+
+template <typename S>
 StorageOps make_storage_ops() {
     StorageOps o;
     o.init = launch_init_s<S>;
@@ -2677,6 +2984,7 @@ StorageOps make_storage_ops() {
     o.finalize = launch_finalize_s<S>;
     o.inout = launch_inout_s<S>;
     o.bouzidi_force = launch_bouzidi_force_s<S>;
+    o.cluster = launch_cluster_any<S>;
     return o;
 }
 

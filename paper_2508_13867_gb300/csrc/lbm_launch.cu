@@ -67,6 +67,7 @@ KParams make_params(const BatchBuffers& b, const BatchGeometry& g, const RunOutp
     p.max_steps = g.max_steps;
     p.stochastic = g.stochastic;
     p.spl = g.spl > 0 ? g.spl : 2;
+    p.natural = g.cluster;
     if (o != nullptr) {
         p.fields = o->fields;
         p.fields_ld = o->fields_ld;
@@ -157,6 +158,10 @@ cudaError_t launch_resume(const BatchBuffers& b, const BatchGeometry& g, cudaStr
 cudaError_t launch_advance(const BatchBuffers& b, int chunk, cudaStream_t s) {
     advance_kernel<<<1, 1, 0, s>>>(b.step_counter, chunk);
     return cudaGetLastError();
+}
+
+cudaError_t launch_cluster(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, cudaStream_t s) {
+    return ops_of(g.storage).cluster(make_params(b, g, &o, 0), g, s, false);
 }
 
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,

@@ -423,12 +423,26 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         return UQLB_ERR_ARG;
     }
     const int scheme = o ? o->scheme : UQLB_SCHEME_AUTO;
-    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_THREE_STEP_STRIPS || scheme == UQLB_SCHEME_GROUPED) {
+    if (scheme < UQLB_SCHEME_AUTO || scheme > UQLB_SCHEME_CLUSTER || scheme == UQLB_SCHEME_GROUPED) {
         why = "unknown time-stepping scheme";
         return UQLB_ERR_ARG;
     }
     // auto: the two-step scheme where it measured faster (periodic FP32, FP16 and BF16 batches)
-    const bool two = (scheme >= UQLB_SCHEME_TWO_STEP && scheme != UQLB_SCHEME_ONE_STEP) ||
+    // cluster runs: every sample a channel with the face inlet/outlet and the halfway obstacle, 16-bit
+    // or FP32 storage (its lattice twice in the shared memory of at most 16 blocks)
+    const bool cluster = scheme == UQLB_SCHEME_CLUSTER;
+    if (cluster) {
+        bool ok = storage != UQLB_F64 && mode == UQLB_MODE_GRAPH;
+        for (int64_t s = 0; s < n && ok; ++s)
+            ok = smp[s].kind == UQLB_CASE_CHANNEL && smp[s].obstacle_bc == UQLB_OBSTACLE_HALFWAY &&
+                 smp[s].inout_bc == UQLB_INOUT_FACE;
+        if (!ok) {
+            why = "the cluster scheme runs CHANNEL samples with the halfway obstacle and the face inlet/outlet, "
+                  "FP32 or 16-bit storage, in UQLB_MODE_GRAPH";
+            return UQLB_ERR_ARG;
+        }
+    }
+    const bool two = (scheme >= UQLB_SCHEME_TWO_STEP && scheme != UQLB_SCHEME_ONE_STEP && !cluster) ||
                      (scheme == UQLB_SCHEME_AUTO && !mixed && mode == UQLB_MODE_GRAPH && storage != UQLB_F64);
     if (two && (mixed || mode != UQLB_MODE_GRAPH)) {
         why = "the two-step scheme runs periodic (TGV) batches in UQLB_MODE_GRAPH only";
@@ -667,6 +681,14 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     g.strips = strips ? 1 : 0;
     g.strip_nx = strips ? smp[0].nx : 0;
     g.spl = spl;
+    g.cluster = cluster ? 1 : 0;
+    g.cluster_nx = g.cluster_ny = 0;
+    g.pad_ = 0;
+    if (cluster)
+        for (int64_t s = 0; s < n; ++s) {
+            g.cluster_nx = std::max(g.cluster_nx, smp[s].nx);
+            g.cluster_ny = std::max(g.cluster_ny, smp[s].ny);
+        }
     g.test_withhold = mode == UQLB_MODE_PERSISTENT_TEST_TIMEOUT ? 1 : 0;
     g.any_bouzidi = any_bouzidi;
     g.any_inout = any_inout;
@@ -937,7 +959,17 @@ int run_planned(uqlb_ctx* ctx, const BatchPlan& P, int64_t n, const uqlb_run_opt
         if ((e = launch_resume(B, P.geom, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: resume launch");
     }
     ctx->bar_err = B.bar_err;
-    if (P.geom.max_steps > opts->start_step && opts->mode != UQLB_MODE_GRAPH) {
+    if (P.geom.cluster) {
+        // one launch runs every sample's whole time loop (each sample on one thread-block cluster)
+        if (own_timing && (e = cudaEventRecord(ctx->loop_begin, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "run_batch: event record");
+        if ((e = launch_cluster(B, P.geom, O, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: cluster launch");
+        ctx->run_launches += 1;
+        if (own_timing) {
+            if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
+            ctx->loop_timed = true;
+        }
+    } else if (P.geom.max_steps > opts->start_step && opts->mode != UQLB_MODE_GRAPH) {
         // persistent: one cooperative launch per chunk, then the step counter advances
         const int pchunk = opts->chunk_steps > 0 ? chunk : 1024;
         const int64_t nchunks = (P.geom.max_steps - opts->start_step + pchunk - 1) / pchunk;
@@ -1504,6 +1536,7 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     ctx->last_rows = P0.geom.tile_rows;
     ctx->last_npt = P0.geom.npt;
     ctx->last_scheme = !groups.empty() ? UQLB_SCHEME_GROUPED
+                       : P0.geom.cluster ? UQLB_SCHEME_CLUSTER
                        : !P0.geom.two_step ? UQLB_SCHEME_ONE_STEP
                        : (P0.geom.strips ? (P0.geom.spl == 3 ? UQLB_SCHEME_THREE_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_STRIPS)
                                          : UQLB_SCHEME_TWO_STEP_TILES);

@@ -105,6 +105,9 @@ struct BatchGeometry {
     int32_t strips;          // two-step scheme on row strips (strip2_kernel) instead of tiles
     int32_t strip_nx;        // width of every sample when strips is set
     int32_t spl;             // time steps per launch: 1 (one-step), 2 (tiles, two-step strips), 3 (three-step strips)
+    int32_t cluster;         // UQLB_SCHEME_CLUSTER: one thread-block cluster per sample holds it on chip
+    int32_t cluster_nx, cluster_ny;  // cluster runs: largest sample width and height
+    int32_t pad_;            // keeps the struct free of padding bytes (it keys the graph cache)
 };
 
 // Output pointers of a run (rows indexed by SampleDev::sample_id).
@@ -145,6 +148,8 @@ cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, con
                               cudaStream_t s);
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                             cudaStream_t s);
+// Cluster runs: every sample's whole time loop on chip in one launch.
+cudaError_t launch_cluster(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, cudaStream_t s);
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);
 bool geometry_supported2(int storage, int tile_rows, int npt);  // two-step scheme
 // Row-strip two-step kernel: FP32/FP16/BF16 storage, sample width a multiple of 64 in 64..2048.

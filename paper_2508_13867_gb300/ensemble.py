@@ -37,7 +37,7 @@ MODES = {"graph": U.UQLB_MODE_GRAPH, "persistent": U.UQLB_MODE_PERSISTENT,
 
 SCHEMES = {"auto": U.UQLB_SCHEME_AUTO, "one_step": U.UQLB_SCHEME_ONE_STEP, "two_step": U.UQLB_SCHEME_TWO_STEP,
            "two_step_tiles": U.UQLB_SCHEME_TWO_STEP_TILES, "two_step_strips": U.UQLB_SCHEME_TWO_STEP_STRIPS,
-           "three_step_strips": U.UQLB_SCHEME_THREE_STEP_STRIPS}
+           "three_step_strips": U.UQLB_SCHEME_THREE_STEP_STRIPS, "cluster": U.UQLB_SCHEME_CLUSTER}
 
 
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,

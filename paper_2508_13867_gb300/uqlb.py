@@ -29,7 +29,7 @@ UQLB_OBSTACLE_HALFWAY, UQLB_OBSTACLE_BOUZIDI = 0, 1
 UQLB_INOUT_FACE, UQLB_INOUT_INTERPOLATED = 0, 1
 UQLB_SCHEME_AUTO, UQLB_SCHEME_ONE_STEP, UQLB_SCHEME_TWO_STEP = 0, 1, 2
 UQLB_SCHEME_TWO_STEP_TILES, UQLB_SCHEME_TWO_STEP_STRIPS, UQLB_SCHEME_GROUPED = 3, 4, 5
-UQLB_SCHEME_THREE_STEP_STRIPS = 6
+UQLB_SCHEME_THREE_STEP_STRIPS, UQLB_SCHEME_CLUSTER = 6, 7
 (UQLB_PARAM_NU, UQLB_PARAM_U0, UQLB_PARAM_ZETA2, UQLB_PARAM_ZETA3, UQLB_PARAM_PERT00, UQLB_PARAM_PERT01,
  UQLB_PARAM_PERT10, UQLB_PARAM_PERT11) = range(8)
 UQLB_F64, UQLB_F32, UQLB_F16, UQLB_BF16, UQLB_FX16 = 0, 1, 2, 3, 4

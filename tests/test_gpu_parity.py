@@ -1008,3 +1008,69 @@ def test_three_step_strips_resume_continues_the_run(ens, first, second, split):
                         scheme=second)
     torch.cuda.synchronize()
     assert np.array_equal(res["fields"].double().cpu().numpy()[:, :-1], whole["fields"][:, :-1])
+
+
+@pytest.mark.parametrize("steps", [600, 601])
+def test_cluster_scheme_matches_the_oracle_and_the_one_step_scheme(ens, steps):
+    """Channel samples held on chip by one thread-block cluster each (the staircase cylinder with the
+    face inlet/outlet, and the empty channel), FP32: fields, C_D, C_L and the C_D series against the
+    oracle; the per-node arithmetic is that of the one-step kernel (push form instead of the in-place
+    AA order), so the fields equal the one-step scheme's bit for bit."""
+    specs = [_cyl(5, steps, u_mean=0.036), _cyl(5, steps, u_mean=0.044),
+             W.channel(5, steps=steps, obstacle=False, steady_tol=0.0, re=5.0)]
+    ref = olbm.run([oracle_case(s, qoi_every=50) for s in specs])
+    g = _run(ens, specs, "f32", qoi_every=50, series=True, scheme="cluster")
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_CLUSTER
+    one = _run(ens, specs, "f32", qoi_every=50, series=True, scheme="one_step")
+    ns = steps // 50
+    for i, r in enumerate(ref):
+        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0 and g["qoi"][i, U.UQLB_QOI_STEPS] == steps
+        assert rel_l2(g["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f32"], i
+        assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < 10 * TOL["f32"] * r.mass, i
+        if specs[i].cyl_r > 0:
+            assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < 1e-4 * abs(r.cd), i
+            assert abs(g["qoi"][i, U.UQLB_QOI_CL] - r.cl) < 1e-4 * abs(r.cd), i
+            assert np.allclose(g["series"][i, :ns], r.series[:ns], rtol=1e-4, atol=0), i
+    assert np.array_equal(g["fields"][:, :-1], one["fields"][:, :-1])
+
+
+def test_cluster_scheme_uneven_sizes_and_16_bit_storage(ens):
+    """Samples of different sizes in one cluster launch (every block holds the widest sample's slab
+    width; narrower samples leave blocks idle) with FX16 storage against the oracle at the 16-bit
+    budget, and FP32 against the one-step scheme bit for bit."""
+    specs = [_cyl(4, 301, u_mean=0.04), _cyl(6, 301, u_mean=0.038), _cyl(5, 301, u_mean=0.042)]
+    ref = olbm.run([oracle_case(s) for s in specs])
+    g = _run(ens, specs, "fx16", scheme="cluster")
+    for i, r in enumerate(ref):
+        assert g["qoi"][i, U.UQLB_QOI_STATUS] == 0
+        assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < TOL["fx16"] * abs(r.cd), i
+        assert abs(g["qoi"][i, U.UQLB_QOI_MASS] - r.mass) < TOL["fx16"] * r.mass, i
+    a = _run(ens, specs, "f32", scheme="cluster")
+    b = _run(ens, specs, "f32", scheme="one_step")
+    assert np.array_equal(a["qoi"][:, [U.UQLB_QOI_MASS, U.UQLB_QOI_MOMX, U.UQLB_QOI_STEPS]],
+                          b["qoi"][:, [U.UQLB_QOI_MASS, U.UQLB_QOI_MOMX, U.UQLB_QOI_STEPS]])
+
+
+def test_cluster_scheme_steady_stop_and_resume(ens):
+    """A cluster run stops a sample at the steady-state step of the oracle within one check (FP32),
+    and a run resumed at an odd step continues the state bit for bit."""
+    specs = [_cyl(4, 20000, u_mean=0.04, steady_tol=1e-6), _cyl(4, 20000, u_mean=0.036, steady_tol=1e-6)]
+    g = _run(ens, specs, "f32", qoi_every=100, series=True, scheme="cluster")
+    one = _run(ens, specs, "f32", qoi_every=100, series=True, scheme="one_step")
+    ref = olbm.run([oracle_case(s, qoi_every=100) for s in specs])
+    for i, r in enumerate(ref):
+        assert r.steps_run < 20000
+        # the state is the one-step scheme's bit for bit; C_D sums the same link forces in another order,
+        # and FP32 resolves C_D to ~1e-7, so a check near the 1e-6 threshold may fall either way
+        assert abs(g["qoi"][i, U.UQLB_QOI_STEPS] - one["qoi"][i, U.UQLB_QOI_STEPS]) <= 100, i
+        assert abs(g["qoi"][i, U.UQLB_QOI_STEPS] - r.steps_run) <= 100, i
+        assert abs(g["qoi"][i, U.UQLB_QOI_CD] - r.cd) < 1e-4 * abs(r.cd), i
+    specs = [_cyl(4, 90, u_mean=0.04), _cyl(5, 90, u_mean=0.04)]
+    whole = _run(ens, specs, "f32", qoi_every=10, series=True, scheme="cluster")
+    head = [sample_struct(s) for s in specs]
+    for s in head:
+        s.steps = 37
+    ens.run_batch(head, storage="f32", fields=False, scheme="cluster")
+    res = ens.run_batch([sample_struct(s) for s in specs], storage="f32", fields=False, start_step=37, scheme="cluster")
+    torch.cuda.synchronize()
+    assert np.array_equal(res["qoi"].cpu().numpy(), whole["qoi"])

@@ -421,6 +421,17 @@ def bench_workload(args):
         g_fields = r["fields"][sub].double().cpu().numpy()
         q_all = r["qoi"].cpu().numpy()
         del r
+        line["steps_run"] = [int(v) for v in q_all[:, U.UQLB_QOI_STEPS]]
+        geo = U.uqlb_last_run_geometry(ens.ctx)
+        line["ran_as"] = {1: "one_step", 3: "two_step_tiles", 4: "two_step_strips", 5: "groups", 6: "three_step_strips",
+                          7: "cluster"}[geo[0]]
+        line["geometry"] = list(geo[1:])
+        if not sub:
+            if mc_sc is not None:
+                line["mc_vs_sc"] = mc_sc
+            print(json.dumps(line))
+            ens.close()
+            return 0
         ref, oracle_s = _oracle_run(_oracle_cases([specs[i] for i in sub]))
         m_ref = np.stack([np.concatenate([q.u.ravel(), q.v.ravel(), [q.k_final]]) for q in ref])
         line["oracle_samples"] = len(sub)

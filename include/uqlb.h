@@ -422,9 +422,10 @@ int uqlb_run_plain_f64(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, int
 int uqlb_last_loop_time(uqlb_ctx* ctx, double* ms, int64_t* steps, int64_t* launches);
 
 /* Scheme the last uqlb_run_batch / uqlb_run_ensemble on this context ran (UQLB_SCHEME_ONE_STEP,
- * UQLB_SCHEME_TWO_STEP_TILES, UQLB_SCHEME_TWO_STEP_STRIPS, or UQLB_SCHEME_GROUPED for a batch run
- * as groups) and its tile geometry (of the first group).  Any output may be NULL;
- * UQLB_ERR_STATE before the first run. */
+ * UQLB_SCHEME_TWO_STEP_TILES, UQLB_SCHEME_TWO_STEP_STRIPS, UQLB_SCHEME_THREE_STEP_STRIPS,
+ * UQLB_SCHEME_CLUSTER, or UQLB_SCHEME_GROUPED for a batch run as groups) and its tile geometry (of the
+ * first group; for UQLB_SCHEME_CLUSTER the blocks per cluster and the columns per block).  Any output
+ * may be NULL; UQLB_ERR_STATE before the first run. */
 int uqlb_last_run_geometry(const uqlb_ctx* ctx, int32_t* scheme, int32_t* tile_rows, int32_t* nodes_per_thread);
 
 /* ------------------------------------------------------------------------------------

@@ -73,6 +73,8 @@ const StorageOps& storage_ops_f32();
 const StorageOps& storage_ops_f16();
 const StorageOps& storage_ops_bf16();
 const StorageOps& storage_ops_fx16();
+// Blocks per cluster and columns per block of the last cluster launch (host side).
+extern int g_cluster_choice[2];
 
 // Streaming multiprocessors of the current device (queried once).
 inline int sm_count() {

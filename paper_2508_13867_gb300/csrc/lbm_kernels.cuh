@@ -2036,18 +2036,35 @@ __device__ __forceinline__ unsigned cluster_id_x() {
     asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
     return r;
 }
-// Generic address of the same shared-memory location in block `rank` of the cluster.
-template <typename T>
-__device__ __forceinline__ T* cluster_map(T* p, unsigned rank) {
-    T* q;
-    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(q) : "l"(p), "r"(rank));
-    return q;
+constexpr int kClusterThreads = 512;
+
+// 32-bit shared::cluster address of a shared-memory location of this block, in block `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, unsigned rank) {
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+template <typename S>
+__device__ __forceinline__ void st_cluster(uint32_t addr, S v) {
+    if constexpr (sizeof(S) == 4) {
+        asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(addr), "r"(*reinterpret_cast<uint32_t*>(&v)) : "memory");
+    } else {
+        asm volatile("st.shared::cluster.b16 [%0], %1;" ::"r"(addr), "h"(*reinterpret_cast<unsigned short*>(&v)) : "memory");
+    }
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_cluster_s32(uint32_t addr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
 }
 
-constexpr int kClusterThreads = 256;
-
 template <typename S>
-__global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
+__global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) {
     extern __shared__ __align__(16) unsigned char s6_raw[];
     __shared__ __align__(16) SampleDev s_sp;
     __shared__ double s_red[(kClusterThreads / 32) * 2];
@@ -2064,9 +2081,8 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
     const int nx = sp.nx, ny = sp.ny, cw = p.cluster_cw;
     const int x0 = (int)rank * cw, ncol = max(0, min(cw, nx - x0));  // this block's columns [x0, x0 + ncol)
     const int pl = ny * cw;                                           // one population plane of a slab
-    S* bufA = reinterpret_cast<S*>(s6_raw);
-    S* bufB = bufA + 9 * pl;
-    uint32_t* links = reinterpret_cast<uint32_t*>(bufB + 9 * pl);     // [ny][cw] link classes
+    S* const lat = reinterpret_cast<S*>(s6_raw);                      // two states: [2][9][ny][cw]
+    uint32_t* const links = reinterpret_cast<uint32_t*>(lat + 18 * pl);  // [ny][cw] link classes
     const typename Storage<S>::Q qz = quanta_of<S>(p, j);
     const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
     S* glob = static_cast<S*>(p.arena) + sp.f_off;
@@ -2079,7 +2095,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
         const int y = n / ncol, lx = n - y * ncol, x = x0 + lx;
         const int64_t own = (int64_t)y * sp.pitch + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) bufA[i * pl + y * cw + lx] = glob[i * sp.plane + own];
+        for (int i = 0; i < 9; ++i) lat[i * pl + y * cw + lx] = glob[i * sp.plane + own];
         uint32_t w = 0u;
         if (mask != nullptr && mask_solid(mask, mask_words(sp), x, y)) {
             w = 0xFFFFFFFFu;
@@ -2089,87 +2105,84 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
         }
         links[y * cw + lx] = w;
     }
-    // generic addresses of the neighbouring blocks' buffers (same layout in every block)
+    // shared::cluster addresses of the two states in the neighbouring blocks (same layout everywhere)
     const unsigned left = rank > 0 ? rank - 1 : rank, right = rank + 1 < nrank ? rank + 1 : rank;
-    S* const leftA = cluster_map(bufA, left);
-    S* const leftB = cluster_map(bufB, left);
-    S* const rightA = cluster_map(bufA, right);
-    S* const rightB = cluster_map(bufB, right);
-    int* const stop0 = cluster_map(&s_stop, 0u);
+    const uint32_t left0 = cluster_addr(lat, left), right0 = cluster_addr(lat, right);
+    const uint32_t state_bytes = 9u * (uint32_t)pl * (uint32_t)sizeof(S);
     cluster_sync_all();
     const C omega = (C)sp.omega;
     const bool sr = sizeof(S) == 2 && p.stochastic != 0;
+    const uint32_t sid = (uint32_t)sp.sample_id;
     // each thread walks the same owned nodes at every step: node tid, tid + T, ... of the slab in
     // row-major order, stepped without divisions
     const int nnodes = ny * ncol;
     const int walk_r = ncol > 0 ? kClusterThreads / ncol : 0, walk_c = ncol > 0 ? kClusterThreads % ncol : 0;
     const int ystart = ncol > 0 ? tid / ncol : 0, lxstart = ncol > 0 ? tid % ncol : 0;
-    const uint32_t sid = (uint32_t)sp.sample_id;
-    S* cur = bufA;
-    S* nxt = bufB;
-    bool odd = false;  // which buffer holds the state: A (false) or B (true)
+    int cur_off = 0;  // state at t: lat + cur_off; next state at lat + 9 pl - cur_off
     int t = t0;
     for (; t < T && !skip; ++t) {
         const bool f_step = p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
-        S* const nl = odd ? leftA : leftB;   // the neighbours' next-state buffers
-        S* const nr = odd ? rightA : rightB;
+        const S* cur = lat + cur_off;
+        S* nxt = lat + (9 * pl - cur_off);
+        // the neighbours' next states (shared::cluster addresses)
+        const uint32_t nl = left0 + (cur_off == 0 ? state_bytes : 0u), nr = right0 + (cur_off == 0 ? state_bytes : 0u);
         double fx = 0.0, fy = 0.0;
         int y = ystart, lx = lxstart;
         for (int n = tid; n < nnodes; n += kClusterThreads) {
-            const int x = x0 + lx;
-            const int yy0 = y, lx0 = lx;
+            const int yn = y, xn = lx;
             lx += walk_c;
             y += walk_r + (lx >= ncol ? 1 : 0);
             lx -= lx >= ncol ? ncol : 0;
-            const int y_ = yy0;
-            const uint32_t lw = links[y_ * cw + lx0];
+            const int own = yn * cw + xn;
+            const uint32_t lw = links[own];
             if (lw == 0xFFFFFFFFu) continue;  // solid
-            const int own = y_ * cw + lx0;
+            const int x = x0 + xn;
             C g[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(cur + i * pl + own, qz, i);
             C drho, jx, jy, ux, uy;
             moments(g, drho, jx, jy, ux, uy);
             bgk(g, omega, drho, jx, jy, ux, uy);
-            const uint32_t h = sr ? mix32((uint32_t)((int64_t)y_ * sp.pitch + x) * 0x9E3779B1u +
+            const uint32_t h = sr ? mix32((uint32_t)((int64_t)yn * sp.pitch + x) * 0x9E3779B1u +
                                           (uint32_t)t * 0x85EBCA77u + sid * 0xC2B2AE3Du)
                                   : 0u;
-            auto put = [&](S* ptr, C v, int i) {
+            // the stored value of population i (rounded as the storage rounds)
+            auto cvt = [&](C v, int i) {
+                S r;
                 if (sr)
-                    Storage<S>::store_sr(ptr, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
+                    Storage<S>::store_sr(&r, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
                 else
-                    Storage<S>::store(ptr, v, qz, i);
+                    Storage<S>::store(&r, v, qz, i);
+                return r;
             };
-            put(nxt + own, g[0], 0);
+            nxt[own] = cvt(g[0], 0);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const int cls = (lw >> (3 * i)) & 7;
                 const int o = opp(i);
                 if (cls == kInterior) {
-                    const int dl = lx0 + cx(i), dy = y_ + cy(i);
-                    S* base = nxt;
-                    int col = dl;
-                    if (dl < 0) {
-                        base = nl;
-                        col = cw - 1;
-                    } else if (dl >= ncol) {
-                        base = nr;
-                        col = 0;
+                    const int dl = xn + cx(i), dy = yn + cy(i);
+                    if (dl >= 0 && dl < ncol) {
+                        nxt[i * pl + dy * cw + dl] = cvt(g[i], i);
+                    } else {
+                        // into the neighbouring slab: its column cw - 1 (left) or 0 (right)
+                        const uint32_t at = (dl < 0 ? nl + (uint32_t)(i * pl + dy * cw + cw - 1) * (uint32_t)sizeof(S)
+                                                    : nr + (uint32_t)(i * pl + dy * cw) * (uint32_t)sizeof(S));
+                        st_cluster<S>(at, cvt(g[i], i));
                     }
-                    put(base + i * pl + dy * cw + col, g[i], i);
                 } else if (cls == kWall || cls == kSolid) {
-                    put(nxt + o * pl + own, g[i], i);
+                    nxt[o * pl + own] = cvt(g[i], i);
                     if (f_step && cls == kSolid) {
                         const C fs = g[i] + wgt<C>(i);
                         fx += (double)(C(2 * cx(i)) * fs);
                         fy += (double)(C(2 * cy(i)) * fs);
                     }
                 } else if (cls == kInlet) {
-                    const C yy = C(y_) + C(0.5) - C(0.5) * C(cy(o));
-                    put(nxt + o * pl + own, g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
+                    const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
+                    nxt[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
                 } else {
                     const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                    put(nxt + o * pl + own, -g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
+                    nxt[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
                 }
             }
         }
@@ -2182,23 +2195,20 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
             }
         }
         cluster_sync_all();  // the next state is complete in every block (and this state is no longer read)
-        S* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        odd = !odd;
+        cur_off = 9 * pl - cur_off;
         if (f_step) {
             if (rank == 0 && tid == 0) {
                 double F[2] = {0.0, 0.0};
                 for (unsigned r = 0; r < nrank; ++r) {
-                    const double* f = cluster_map(s_force, r);
-                    F[0] += f[0];
-                    F[1] += f[1];
+                    const uint32_t a = cluster_addr(s_force, r);
+                    F[0] += ld_cluster_f64(a);
+                    F[1] += ld_cluster_f64(a + 8u);
                 }
                 record_force(p, sp, j, t + 1, F[0], F[1]);
                 s_stop = p.done[sp.slot];
             }
             cluster_sync_all();  // block 0's decision is visible
-            if (*(volatile int*)stop0 != 0) {
+            if (ld_cluster_s32(cluster_addr(&s_stop, 0u)) != 0) {
                 ++t;
                 break;
             }
@@ -2206,6 +2216,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
     }
     // the state at the last step run back to the arena (natural layout)
     if (!skip) {
+        const S* cur = lat + cur_off;
         for (int n = tid; n < ny * ncol; n += kClusterThreads) {
             const int y = n / ncol, lx = n - y * ncol, x = x0 + lx;
             const int64_t own = (int64_t)y * sp.pitch + x;
@@ -2219,7 +2230,7 @@ __global__ void __launch_bounds__(kClusterThreads) cluster_kernel(KParams p) {
 
 template <typename S>
 size_t cluster_smem(int cw, int ny) {
-    return (size_t)2 * 9 * cw * ny * sizeof(S) + (size_t)cw * ny * sizeof(uint32_t);
+    return (size_t)18 * cw * ny * sizeof(S) + (size_t)cw * ny * sizeof(uint32_t);
 }
 
 template <typename S>
@@ -2967,6 +2978,8 @@ cudaError_t launch_cluster_any(const KParams& p, const BatchGeometry& g, cudaStr
             }
         }
         if (best_c == 0) return cudaErrorInvalidConfiguration;
+        g_cluster_choice[0] = best_c;
+        g_cluster_choice[1] = best_cw;
         q.cluster_size = best_c;
         q.cluster_cw = best_cw;
         q.cluster_ny = g.cluster_ny;

@@ -8,6 +8,13 @@
 
 namespace uqlb {
 
+int g_cluster_choice[2] = {0, 0};
+
+void last_cluster_choice(int* blocks, int* cols) {
+    *blocks = g_cluster_choice[0];
+    *cols = g_cluster_choice[1];
+}
+
 namespace {
 
 // After the finalize of a two-step run: the lattice that now holds each sample's state (both

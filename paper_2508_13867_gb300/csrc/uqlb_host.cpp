@@ -54,6 +54,7 @@ struct uqlb_ctx {
     };
     std::vector<Tuned> tuned;
     int last_rows = 0, last_npt = 0, last_scheme = 0;
+    int cluster_blocks = 0, cluster_cols = 0;  // geometry of the last cluster launch
     int64_t counter_host[2] = {0, 0};  // source of the step-counter upload (step, first step of the run)
     int32_t* bar_err = nullptr;  // device error word of the last run
 };
@@ -965,6 +966,7 @@ int run_planned(uqlb_ctx* ctx, const BatchPlan& P, int64_t n, const uqlb_run_opt
             return cuda_fail(ctx, e, "run_batch: event record");
         if ((e = launch_cluster(B, P.geom, O, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: cluster launch");
         ctx->run_launches += 1;
+        last_cluster_choice(&ctx->cluster_blocks, &ctx->cluster_cols);
         if (own_timing) {
             if ((e = cudaEventRecord(ctx->loop_end, s)) != cudaSuccess) return cuda_fail(ctx, e, "run_batch: event record");
             ctx->loop_timed = true;
@@ -1587,8 +1589,9 @@ int uqlb_last_run_geometry(const uqlb_ctx* ctx, int32_t* scheme, int32_t* tile_r
     if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
     if (ctx->last_scheme == 0) return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_STATE, "no run yet");
     if (scheme) *scheme = ctx->last_scheme;
-    if (tile_rows) *tile_rows = ctx->last_rows;
-    if (nodes_per_thread) *nodes_per_thread = ctx->last_npt;
+    const bool cl = ctx->last_scheme == UQLB_SCHEME_CLUSTER;
+    if (tile_rows) *tile_rows = cl ? ctx->cluster_blocks : ctx->last_rows;
+    if (nodes_per_thread) *nodes_per_thread = cl ? ctx->cluster_cols : ctx->last_npt;
     return 0;
 }
 

@@ -148,6 +148,8 @@ cudaError_t launch_persistent(const BatchBuffers& b, const BatchGeometry& g, con
                               cudaStream_t s);
 cudaError_t launch_finalize(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o,
                             cudaStream_t s);
+// Blocks per cluster and columns per block the last cluster launch chose.
+void last_cluster_choice(int* blocks, int* cols);
 // Cluster runs: every sample's whole time loop on chip in one launch.
 cudaError_t launch_cluster(const BatchBuffers& b, const BatchGeometry& g, const RunOutputs& o, cudaStream_t s);
 bool geometry_supported(int storage, bool mixed, int tile_rows, int npt);

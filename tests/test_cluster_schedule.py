@@ -17,7 +17,7 @@ CX = [0, 1, 0, -1, 0, 1, -1, -1, 1]
 CY = [0, 0, 1, 0, -1, 1, 1, -1, -1]
 OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
 INTERIOR, WALL, INLET, OUTLET, SOLID = 0, 1, 2, 3, 4
-THREADS = 256
+THREADS = 512
 
 
 def classify(solid, nx, ny, x, y):

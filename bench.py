@@ -39,7 +39,7 @@ STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in plac
                 6: ("strip3w_kernel (three-step row strips at a compile-time width: each row collided into a "
                     "first shared-memory ring, streamed and collided into a second, streamed and collided again, "
                     "pushed to the other lattice)", "strip3w_kernel", "three-step-strips-fixed-width-v1")}
-STEPS_PER_LAUNCH = {1: 1, 3: 2, 4: 2, 6: 3}
+STEPS_PER_LAUNCH = {1: 1, 3: 2, 4: 2, 6: 3, 7: 1}
 
 
 def _traffic_file(kernel: str, storage: str) -> str:
@@ -231,14 +231,21 @@ def bench_kernel_only(args):
     from paper_2508_13867_gb300 import workloads as W
     from paper_2508_13867_gb300.ensemble import Ensemble
 
-    w = W.tgv256_gpc4d(storage=args.storage)
+    from paper_2508_13867_gb300.ensemble import sample_struct
+
     ens = Ensemble(0)
-    ens.setup(w)
-    smp = ens.ensemble_samples(w)[: args.samples]
-    for s in smp:
-        s.steps = args.time_steps
-        if args.lattice > 0:
-            s.nx = s.ny = args.lattice
+    if args.kernel_case == "cylinder":
+        # channel samples of the cylinder workload at nd nodes per diameter (inflow +-10 %), no steady test
+        smp = [sample_struct(W.channel(args.nd, u_mean=0.04 * (0.9 + 0.2 * k / max(args.samples - 1, 1)),
+                                       steps=args.time_steps, steady_tol=0.0)) for k in range(args.samples)]
+    else:
+        w = W.tgv256_gpc4d(storage=args.storage)
+        ens.setup(w)
+        smp = ens.ensemble_samples(w)[: args.samples]
+        for s in smp:
+            s.steps = args.time_steps
+            if args.lattice > 0:
+                s.nx = s.ny = args.lattice
     out = {}
     for _ in range(args.warmup + args.steps):
         ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
@@ -246,7 +253,7 @@ def bench_kernel_only(args):
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
-    per_launch = STEPS_PER_LAUNCH[scheme]
+    per_launch = STEPS_PER_LAUNCH.get(scheme, 1)
     nodes = sum(s.nx * s.ny for s in smp)
     gbs = BYTES_PER_UPDATE[args.storage] * nodes / (ms / max(st / per_launch, 1) / 1e3) / 1e9
     print(json.dumps({"kernel_only": True, "mode": args.mode, "scheme": scheme, "tile": [g_rows, g_npt],
@@ -818,6 +825,8 @@ def main():
     ap.add_argument("--samples", type=int, default=128)
     ap.add_argument("--time-steps", type=int, default=16)
     ap.add_argument("--lattice", type=int, default=0, help="kernel-only: lattice side N (0: the workload's 256)")
+    ap.add_argument("--kernel-case", default="tgv", choices=["tgv", "cylinder"],
+                    help="kernel-only: the 4-D Taylor-Green samples or channel samples of the cylinder workload (--nd)")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16", "fx16"])
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)

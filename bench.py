@@ -247,9 +247,14 @@ def bench_kernel_only(args):
             if args.lattice > 0:
                 s.nx = s.ny = args.lattice
     out = {}
+    strip = tuple(int(v) for v in args.strip.split(","))
+    tuned = None
+    if args.kernel_autotune:
+        tuned = ens.autotune(smp, storage=args.storage, trial_steps=args.tune_steps, scheme=args.scheme)
     for _ in range(args.warmup + args.steps):
         ens.run_batch(smp, storage=args.storage, fields_dtype="f32", out=out, tile_rows=args.tile_rows,
-                      nodes_per_thread=args.npt, rounding=args.rounding, mode=args.mode, scheme=args.scheme)
+                      nodes_per_thread=args.npt, rounding=args.rounding, mode=args.mode, scheme=args.scheme,
+                      strip=strip)
     torch.cuda.synchronize()
     ms, st, la = U.uqlb_last_loop_time(ens.ctx)
     scheme, g_rows, g_npt = U.uqlb_last_run_geometry(ens.ctx)
@@ -260,9 +265,31 @@ def bench_kernel_only(args):
                       "samples": len(smp), "time_steps": st, "mlups": nodes * st / (ms / 1e3) / 1e6,
                       "storage": args.storage,
                       "loop_ms": ms, "step_ms": ms / max(st, 1), "achieved_gbs": gbs,
-                      "arena_bytes": BYTES_PER_UPDATE[args.storage] // 2 * nodes}))
+                      "arena_bytes": BYTES_PER_UPDATE[args.storage] // 2 * nodes, "strip": list(strip),
+                      "autotune": tune_summary(tuned)}))
     ens.close()
     return 0
+
+
+def tune_summary(tuned):
+    """The autotuner's candidates as labels with their ms per step: tile geometries "rows x npt", and on
+    the three-step strips "<staging>/<blocks per SM>b/<shared-memory KB>k" (staging "s0": none, "s1": one
+    row, "g": the generic-width kernel)."""
+    if tuned is None:
+        return None
+
+    def label(c):
+        if c["strip_blocks_per_sm"] > 0:
+            st = {0: "g", 1: "s0", 2: "s1"}[c["strip_stage"]]
+            return f"{st}/{c['strip_blocks_per_sm']}b/{c['strip_smem_kb']}k"
+        return f"{c['tile_rows']}x{c['nodes_per_thread']}"
+
+    cands = tuned.get("candidates", [])
+    out = {"tile_rows": tuned["tile_rows"], "nodes_per_thread": tuned["nodes_per_thread"],
+           "autotune_ms_per_step": {label(c): round(c["ms_per_step"], 4) for c in cands}}
+    if 0 <= tuned.get("chosen", -1) < len(cands):
+        out["chosen"] = label(cands[tuned["chosen"]])
+    return out
 
 
 def _oracle_run(cases):
@@ -587,7 +614,7 @@ def bench_workload(args):
         ms, r = timed(lambda: ens.run_batch(smp, storage=args.storage, fields=False, scheme=args.scheme), args.steps)
         upd = sum(s.nx * s.ny * s.steps for s in specs)
         line.update({"samples": len(smp), "value": upd / (ms / 1e3) / 1e6, "batch_seconds": ms / 1e3,
-                     "tile_geometry": tuned, "scheme": args.scheme,
+                     "tile_geometry": tune_summary(tuned), "scheme": args.scheme,
                      "ran_as": {0: "auto", 1: "one_step", 3: "two_step_tiles", 4: "two_step_strips",
                                 5: "groups", 6: "three_step_strips", 7: "cluster"}[U.uqlb_last_run_geometry(ens.ctx)[0]]})
         if args.plain_samples > 0:
@@ -785,9 +812,7 @@ def bench_gpu(args):
                            "scheme": {U.UQLB_SCHEME_ONE_STEP: "one_step", U.UQLB_SCHEME_TWO_STEP_TILES: "two_step_tiles",
                                       U.UQLB_SCHEME_TWO_STEP_STRIPS: "two_step_strips",
                                       U.UQLB_SCHEME_THREE_STEP_STRIPS: "three_step_strips"}[scheme],
-                           "tile_geometry": None if tuned is None else
-                           {"tile_rows": tuned["tile_rows"], "nodes_per_thread": tuned["nodes_per_thread"],
-                            "autotune_ms_per_step": {f"{r}x{q}": round(ms, 4) for r, q, ms in tuned["tried"]}}},
+                           "tile_geometry": tune_summary(tuned)},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                              "kernel": kernel_name, "time_steps_per_launch": steps_per_launch,
@@ -827,6 +852,11 @@ def main():
     ap.add_argument("--lattice", type=int, default=0, help="kernel-only: lattice side N (0: the workload's 256)")
     ap.add_argument("--kernel-case", default="tgv", choices=["tgv", "cylinder"],
                     help="kernel-only: the 4-D Taylor-Green samples or channel samples of the cylinder workload (--nd)")
+    ap.add_argument("--strip", default="0,0,0",
+                    help="kernel-only: three-step strips' blocks per SM, staging option (1: none, 2: one row) and "
+                         "shared-memory KB (0: tuned or default)")
+    ap.add_argument("--kernel-autotune", action="store_true",
+                    help="kernel-only: run the autotuner (--tune-steps) first and report its candidates")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "f16", "bf16", "fx16"])
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--npt", type=int, default=0)

@@ -193,6 +193,16 @@ typedef struct {
                                  (checkpoint). */
     int32_t mode;             /* UQLB_MODE_GRAPH or UQLB_MODE_PERSISTENT (see below) */
     int32_t scheme;           /* time-stepping scheme, UQLB_SCHEME_* (see below) */
+    /* Launch shape of the three-step row strips (ignored by the other kernels); each 0: the value
+     * the context's autotuner picked for this batch shape, else the default. */
+    int32_t strip_blocks_per_sm; /* resident blocks per SM (at most what fits; the grid is
+                                    min(rows, blocks per SM x SMs) and each block takes an equal
+                                    share of the rows) */
+    int32_t strip_stage;      /* widths 64, 128, 256, 512, 1024: 1 = rows not staged, 2 = the next
+                                 row staged in shared memory by cp.async (other widths: 0 only) */
+    int32_t strip_smem_kb;    /* shared-memory share per SM in KB: 8, 16, 32, 64, 100, 132, 164, 196
+                                 or 228 (the rest of the 256 KB is L1); raised to what the blocks
+                                 per SM need */
 } uqlb_run_opts;
 
 /* Time-stepping scheme (the same BGK update of Sec. 3; they differ in how populations move
@@ -378,18 +388,37 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
                    double* qoi_dev, double* series_dev, double* series_cl_dev, int64_t series_ld,
                    void* stream);
 
-/* Tile-geometry autotuner.  For this batch shape, time `trial_steps` (>= 2, even) fused steps of
- * every compiled tile geometry on the device (after an equilibrium initialisation, CUDA events on
+/* Launch-shape autotuner.  For this batch shape, time `trial_steps` (>= 2, even) steps of every
+ * candidate launch shape on the device (after an equilibrium initialisation, CUDA events on
  * `stream`, best of two passes) and keep the fastest in the context; later runs of a batch with
- * the same storage, kinds, sample count and node count that pass tile_rows = nodes_per_thread = 0
- * use it.  Outputs (any may be NULL): the chosen tile_rows / nodes_per_thread, and for each
- * candidate c < *n_tried: rows_tried[c], npt_tried[c], ms_per_step[c] (arrays of capacity 16).
- * The workspace must hold uqlb_batch_workspace_bytes for opts with both geometry fields 0; its
- * contents are overwritten.  Synchronises `stream`. */
+ * the same storage, kinds, sample count and node count use it for the fields they pass as 0.
+ * Candidates: on the tile kernels every compiled tile geometry; on the three-step row strips (the
+ * default for periodic batches of one width) the staging option x resident blocks per SM (the
+ * most that fit and up to three fewer) x shared-memory share (the smallest holding the blocks,
+ * and the largest), the tile geometry staying at its default.  Outputs (any may be NULL): the
+ * chosen tile_rows / nodes_per_thread, and for each candidate c < *n_tried: rows_tried[c],
+ * npt_tried[c], ms_per_step[c] (arrays of capacity 16; the full list, strip knobs included, from
+ * uqlb_autotune_report).  The workspace must hold uqlb_batch_workspace_bytes for opts with the
+ * geometry fields 0; its contents are overwritten.  Synchronises `stream`.  A batch that runs as
+ * groups is tuned group by group; the outputs describe the group with the most node updates. */
 int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
                   void* workspace_dev, size_t workspace_bytes, int trial_steps, int32_t* tile_rows,
                   int32_t* nodes_per_thread, int32_t* rows_tried, int32_t* npt_tried,
                   double* ms_per_step, int32_t* n_tried, void* stream);
+
+/* One candidate of the last uqlb_autotune call (of its largest group). */
+typedef struct {
+    int32_t scheme;           /* UQLB_SCHEME_* of the kernel the candidate ran */
+    int32_t tile_rows, nodes_per_thread;
+    int32_t strip_blocks_per_sm, strip_stage, strip_smem_kb;  /* 0 off the three-step strips */
+    double ms_per_step;       /* best of two passes */
+} uqlb_tune_candidate;
+
+/* The candidates of the context's last uqlb_autotune call (host): up to `cap` into `out` (may be
+ * NULL when cap is 0), their count into *n and the index of the chosen one into *chosen (-1: no
+ * autotune yet). */
+int uqlb_autotune_report(const uqlb_ctx* ctx, uqlb_tune_candidate* out, int32_t cap, int32_t* n,
+                         int32_t* chosen);
 
 /* Build the per-sample runs of the context's sample set from a case template (host). */
 int uqlb_ensemble_samples(const uqlb_ctx* ctx, const uqlb_case* c, uqlb_sample* out);

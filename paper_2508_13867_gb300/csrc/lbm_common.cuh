@@ -56,6 +56,13 @@ struct KParams {
 };
 
 // Launchers of one population storage type (one translation unit per type, compiled in parallel).
+// Resident blocks per SM of a row-strip kernel: the most that fit (registers, largest share), the
+// default, the default shared-memory share per SM (KB) and the shared memory one block takes
+// (bytes, with the 1 KB the system reserves per block).
+struct StripBlocks {
+    int max_b, def_b, def_kb, per_block;
+};
+
 struct StorageOps {
     cudaError_t (*init)(const KParams&, const BatchGeometry&, cudaStream_t);
     cudaError_t (*step)(const KParams&, const BatchGeometry&, bool odd, cudaStream_t);
@@ -67,6 +74,8 @@ struct StorageOps {
     cudaError_t (*bouzidi_force)(const KParams&, const BatchGeometry&, cudaStream_t);
     // cluster runs: the whole time loop of every sample in one launch (prepare_only: opt-ins only)
     cudaError_t (*cluster)(const KParams&, const BatchGeometry&, cudaStream_t, bool prepare_only);
+    // three-step strips: blocks per SM at staging option `stage` (false: not a three-step strip batch)
+    bool (*strip3_blocks)(const BatchGeometry&, int stage, StripBlocks*);
 };
 const StorageOps& storage_ops_f64();
 const StorageOps& storage_ops_f32();

@@ -1698,10 +1698,10 @@ constexpr int strip3w_min_blocks(int np) {
     return th / np < 1 ? 1 : (th / np > 16 ? 16 : th / np);
 }
 
-template <typename S, int W>
+// D: phase-A rows staged in shared memory ahead of their use (0 or 1).
+template <typename S, int W, int D>
 __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_kernel(KParams p) {
     constexpr int NP = W / 2, RS = W + 4;
-    constexpr int D = Strip3Tune<S>::depth;
     extern __shared__ __align__(16) unsigned char s5_raw[];
     __shared__ __align__(16) SampleDev s_sp;
     __shared__ int s_j, s_rows, s_nact, s_flag;
@@ -2838,104 +2838,152 @@ size_t strip3_smem(int nx) {
     return (size_t)2 * kRing3Planes * nx * sizeof(float) + (size_t)Strip3Tune<S>::depth * 9 * nx * sizeof(S);
 }
 
-// Shared-memory opt-in and resident blocks per SM of the three-step strips at width nx (once each).
+// Carveout (percent of the largest share) that selects configuration `kb`: rounded down, since the
+// driver rounds the share up to the next configuration.
+inline int carveout_pct(int kb) { return kb * 100 / 228; }
+
+// Resident blocks per SM and shared-memory share of a row-strip launch: the blocks per SM asked for
+// (g.strip_bps, else the default, never above what fits) and the share (g.strip_smem_kb, else the
+// default; never below what the blocks need).
+inline void strip_launch_shape(const StripBlocks& sb, const BatchGeometry& g, int* bps, int* kb) {
+    int b = g.strip_bps > 0 ? std::min(g.strip_bps, sb.max_b) : sb.def_b;
+    int k = g.strip_smem_kb > 0 ? g.strip_smem_kb : sb.def_kb;
+    k = std::max(k, smem_config_for((size_t)b * sb.per_block));
+    *bps = b;
+    *kb = k;
+}
+
+// Launch of a row-strip kernel over min(total rows, bps x SMs) blocks with the shared-memory share
+// as a launch attribute (it holds for this launch only, also inside a captured graph).
+template <typename K>
+cudaError_t launch_strip_kernel(K kernel, const StripBlocks& sb, const BatchGeometry& g, int threads, size_t smem,
+                                const KParams& p, cudaStream_t s) {
+    int bps = 0, kb = 0;
+    strip_launch_shape(sb, g, &bps, &kb);
+    const int64_t resident = (int64_t)bps * sm_count();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident)));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    at[0].val.sharedMemCarveout = (unsigned)carveout_pct(kb);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, p);
+}
+
+// Blocks per SM of a kernel with `dyn` bytes of dynamic shared memory at `threads` threads: the
+// most that fit (registers and the largest share) and the default under the compiled share.
+template <typename K>
+StripBlocks strip_blocks_of(K kernel, int threads, size_t dyn, int default_kb) {
+    StripBlocks r{};
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    r.per_block = (int)(dyn + fa.sharedSizeBytes + 1024);  // 1 KB per block is reserved by the system
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, dyn) != cudaSuccess || b < 1) b = 1;
+    r.max_b = b;
+    r.def_b = default_kb > 0 ? std::max(1, std::min(b, default_kb * 1024 / r.per_block)) : b;
+    r.def_kb = default_kb > 0 ? default_kb : 228;
+    return r;
+}
+
+// Blocks per SM of the three-step strips at width nx (once per width).
 template <typename S, bool GENERIC>
-int strip3_resident(int nx) {
-    constexpr int kb = Strip3Tune<S>::carveout_kb;
+const StripBlocks& strip3_generic_blocks(int nx) {
     const int np = strip_threads(nx), rw = 2 * np;
-    static int cache[1024 / 32 + 1] = {};
+    static StripBlocks cache[1024 / 32 + 1] = {};
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(strip3_kernel<S, GENERIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)strip3_smem<S>(Strip3Tune<S>::max_nx));
-        if (kb > 0)
-            cudaFuncSetAttribute(strip3_kernel<S, GENERIC>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
         attr = true;
     }
-    int& n = cache[np / 32];
-    if (n == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip3_kernel<S, GENERIC>, np, strip3_smem<S>(rw)) !=
-                cudaSuccess || b < 1)
-            b = 1;
-        if (kb > 0) {
-            cudaFuncAttributes fa{};
-            cudaFuncGetAttributes(&fa, strip3_kernel<S, GENERIC>);
-            const size_t per = strip3_smem<S>(rw) + fa.sharedSizeBytes + 1024;
-            b = std::max(1, std::min(b, (int)((size_t)kb * 1024 / per)));
-        }
-        n = b;
-    }
-    return n;
+    StripBlocks& b = cache[np / 32];
+    if (b.max_b == 0) b = strip_blocks_of(strip3_kernel<S, GENERIC>, np, strip3_smem<S>(rw), Strip3Tune<S>::carveout_kb);
+    return b;
 }
 
-template <typename S, int W>
+template <typename S, int W, int D>
 size_t strip3w_smem() {
-    return (size_t)2 * kRing3Planes * (W + 4) * sizeof(float) + (size_t)Strip3Tune<S>::depth * 9 * W * sizeof(S);
+    return (size_t)2 * kRing3Planes * (W + 4) * sizeof(float) + (size_t)D * 9 * W * sizeof(S);
 }
 
-// Resident blocks per SM of the fixed-width three-step strips (once).
-template <typename S, int W>
-int strip3w_resident() {
-    constexpr int kb = Strip3Tune<S>::carveout_kb;
-    static int n = 0;
-    if (n == 0) {
-        cudaFuncSetAttribute(strip3w_kernel<S, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip3w_smem<S, W>());
-        if (kb > 0)
-            cudaFuncSetAttribute(strip3w_kernel<S, W>, cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, strip3w_kernel<S, W>, W / 2, strip3w_smem<S, W>()) !=
-                cudaSuccess || b < 1)
-            b = 1;
-        if (kb > 0) {
-            cudaFuncAttributes fa{};
-            cudaFuncGetAttributes(&fa, strip3w_kernel<S, W>);
-            const size_t per = strip3w_smem<S, W>() + fa.sharedSizeBytes + 1024;
-            b = std::max(1, std::min(b, (int)((size_t)kb * 1024 / per)));
-        }
-        n = b;
-    }
-    return n;
+// Blocks per SM of the fixed-width three-step strips (once).
+template <typename S, int W, int D>
+const StripBlocks& strip3w_blocks() {
+    static const StripBlocks b = [] {
+        cudaFuncSetAttribute(strip3w_kernel<S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)strip3w_smem<S, W, D>());
+        return strip_blocks_of(strip3w_kernel<S, W, D>, W / 2, strip3w_smem<S, W, D>(), Strip3Tune<S>::carveout_kb);
+    }();
+    return b;
 }
+
+// Staging option of a fixed-width launch: 1 = no staged row, 2 = one (0: the compiled default).
+inline int strip3w_depth(int stage, int def) { return stage == 1 ? 0 : (stage == 2 ? 1 : def); }
 
 template <typename S, int W>
 cudaError_t launch_strip3w(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
-    const int64_t resident = (int64_t)strip3w_resident<S, W>() * sm_count();
+    if (strip3w_depth(g.strip_stage, Strip3Tune<S>::depth) == 0) {
+        const StripBlocks& sb = strip3w_blocks<S, W, 0>();
+        if (prepare_only) return cudaGetLastError();
+        return launch_strip_kernel(strip3w_kernel<S, W, 0>, sb, g, W / 2, strip3w_smem<S, W, 0>(), p, s);
+    }
+    const StripBlocks& sb = strip3w_blocks<S, W, 1>();
     if (prepare_only) return cudaGetLastError();
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
-    strip3w_kernel<S, W><<<grid, W / 2, strip3w_smem<S, W>(), s>>>(p);
-    return cudaGetLastError();
+    return launch_strip_kernel(strip3w_kernel<S, W, 1>, sb, g, W / 2, strip3w_smem<S, W, 1>(), p, s);
 }
-
-#ifndef UQLB_STRIP3_FIXED_WIDTHS
-#define UQLB_STRIP3_FIXED_WIDTHS 1
-#endif
 
 template <typename S>
 cudaError_t launch_strip3_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
     const int np = strip_threads(g.strip_nx);
     if (g.strip_nx < 2 || 2 * np > Strip3Tune<S>::max_nx) return cudaErrorInvalidConfiguration;
     const bool generic = g.strip_nx != 2 * np;
-    if (UQLB_STRIP3_FIXED_WIDTHS && !generic) {
+    if (strip3_fixed_width(g.strip_nx)) {
         // the widths with a compile-time instantiation (immediate addressing)
         switch (g.strip_nx) {
             case 64: return launch_strip3w<S, 64>(p, g, s, prepare_only);
             case 128: return launch_strip3w<S, 128>(p, g, s, prepare_only);
             case 256: return launch_strip3w<S, 256>(p, g, s, prepare_only);
             case 512: return launch_strip3w<S, 512>(p, g, s, prepare_only);
-            case 1024: return launch_strip3w<S, 1024>(p, g, s, prepare_only);
-            default: break;
+            default: return launch_strip3w<S, 1024>(p, g, s, prepare_only);
         }
     }
-    const int64_t resident =
-        (int64_t)(generic ? strip3_resident<S, true>(g.strip_nx) : strip3_resident<S, false>(g.strip_nx)) * sm_count();
+    const StripBlocks& sb =
+        generic ? strip3_generic_blocks<S, true>(g.strip_nx) : strip3_generic_blocks<S, false>(g.strip_nx);
     if (prepare_only) return cudaGetLastError();
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total_rows, resident));
-    if (generic)
-        strip3_kernel<S, true><<<grid, np, strip3_smem<S>(2 * np), s>>>(p);
-    else
-        strip3_kernel<S, false><<<grid, np, strip3_smem<S>(2 * np), s>>>(p);
-    return cudaGetLastError();
+    if (generic) return launch_strip_kernel(strip3_kernel<S, true>, sb, g, np, strip3_smem<S>(2 * np), p, s);
+    return launch_strip_kernel(strip3_kernel<S, false>, sb, g, np, strip3_smem<S>(2 * np), p, s);
+}
+
+// Blocks per SM of the three-step strips of batch g at staging option `stage` (fixed widths only;
+// 0: the default).
+template <typename S>
+bool strip3_blocks_s(const BatchGeometry& g, int stage, StripBlocks* out) {
+    if constexpr (sizeof(S) == 8) {
+        return false;
+    } else {
+        const int np = strip_threads(g.strip_nx);
+        if (!g.strips || g.spl != 3 || g.strip_nx < 2 || 2 * np > Strip3Tune<S>::max_nx) return false;
+        if (strip3_fixed_width(g.strip_nx)) {
+            const bool d0 = strip3w_depth(stage, Strip3Tune<S>::depth) == 0;
+            switch (g.strip_nx) {
+                case 64: *out = d0 ? strip3w_blocks<S, 64, 0>() : strip3w_blocks<S, 64, 1>(); break;
+                case 128: *out = d0 ? strip3w_blocks<S, 128, 0>() : strip3w_blocks<S, 128, 1>(); break;
+                case 256: *out = d0 ? strip3w_blocks<S, 256, 0>() : strip3w_blocks<S, 256, 1>(); break;
+                case 512: *out = d0 ? strip3w_blocks<S, 512, 0>() : strip3w_blocks<S, 512, 1>(); break;
+                default: *out = d0 ? strip3w_blocks<S, 1024, 0>() : strip3w_blocks<S, 1024, 1>(); break;
+            }
+            return true;
+        }
+        if (stage != 0) return false;
+        *out = g.strip_nx != 2 * np ? strip3_generic_blocks<S, true>(g.strip_nx)
+                                     : strip3_generic_blocks<S, false>(g.strip_nx);
+        return true;
+    }
 }
 
 template <typename S>
@@ -2998,6 +3046,7 @@ StorageOps make_storage_ops() {
     o.inout = launch_inout_s<S>;
     o.bouzidi_force = launch_bouzidi_force_s<S>;
     o.cluster = launch_cluster_any<S>;
+    o.strip3_blocks = strip3_blocks_s<S>;
     return o;
 }
 

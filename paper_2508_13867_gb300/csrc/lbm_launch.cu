@@ -102,6 +102,16 @@ bool strip3_supported(int storage, int nx) {
     return rw <= (storage == UQLB_F32 ? Strip3Tune<float>::max_nx : Strip3Tune<__half>::max_nx);
 }
 
+bool strip3_blocks(const BatchGeometry& g, int stage, int* max_b, int* def_b, int* def_kb, int* per_block) {
+    StripBlocks b{};
+    if (!ops_of(g.storage).strip3_blocks(g, stage, &b)) return false;
+    *max_b = b.max_b;
+    *def_b = b.def_b;
+    *def_kb = b.def_kb;
+    *per_block = b.per_block;
+    return true;
+}
+
 bool geometry_supported2(int storage, int tile_rows, int npt) {
     const int tr = tile_rows, n = npt;
     if (storage == UQLB_F64) return (tr == 4 && n == 2) || (tr == 8 && (n == 1 || n == 2));

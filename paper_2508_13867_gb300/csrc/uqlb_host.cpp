@@ -30,6 +30,12 @@ constexpr int kMaxGraphs = 32;  // a batch run as groups takes one graph per gro
 
 }  // namespace
 
+// Launch shape the autotuner picked for a batch shape (0: default).
+struct TuneChoice {
+    int rows = 0, npt = 0;              // tile geometry
+    int bps = 0, stage = 0, smem_kb = 0;  // three-step strips
+};
+
 struct uqlb_ctx {
     int device = 0;
     std::string err;
@@ -50,9 +56,11 @@ struct uqlb_ctx {
     struct Tuned {
         int storage, mixed;
         int64_t n, nodes;
-        int rows, npt;
+        TuneChoice choice;
     };
     std::vector<Tuned> tuned;
+    std::vector<uqlb_tune_candidate> tune_report;  // candidates of the last autotune (largest group)
+    int tune_chosen = -1;
     int last_rows = 0, last_npt = 0, last_scheme = 0;
     int cluster_blocks = 0, cluster_cols = 0;  // geometry of the last cluster launch
     int64_t counter_host[2] = {0, 0};  // source of the step-counter upload (step, first step of the run)
@@ -403,7 +411,7 @@ int validate_sample(const uqlb_sample& s, int64_t idx, std::string& why) {
 
 // ids: the caller's index of each sample (the output row), nullptr for 0..n-1.
 int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchPlan& P, std::string& why,
-               int tuned_rows = 0, int tuned_npt = 0, const int64_t* ids = nullptr) {
+               const TuneChoice& tuned = TuneChoice(), const int64_t* ids = nullptr) {
     if (n <= 0 || n > (1 << 24)) {
         why = "sample count out of range";
         return UQLB_ERR_ARG;
@@ -474,8 +482,8 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     };
     int tr = o ? o->tile_rows : 0, npt = o ? o->nodes_per_thread : 0;
     if (tr == 0 && npt == 0) {
-        tr = tuned_rows;
-        npt = tuned_npt;
+        tr = tuned.rows;
+        npt = tuned.npt;
         if (tr == 0 || !supported(tr, npt)) {
             if (two) {
                 tr = 8;
@@ -685,6 +693,25 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
     g.cluster = cluster ? 1 : 0;
     g.cluster_nx = g.cluster_ny = 0;
     g.pad_ = 0;
+    {
+        // launch shape of the three-step strips: the caller's, else the tuned one, else the default
+        const int sb = o ? o->strip_blocks_per_sm : 0, ss = o ? o->strip_stage : 0, sk = o ? o->strip_smem_kb : 0;
+        bool kb_ok = sk == 0;
+        for (int c : kSmemConfigsKB) kb_ok = kb_ok || (c > 0 && sk == c);
+        if (sb < 0 || sb > 32 || ss < 0 || ss > 2 || !kb_ok) {
+            why = "strip_blocks_per_sm must be 0..32, strip_stage 0..2 and strip_smem_kb 0 or a shared-memory "
+                  "configuration (8, 16, 32, 64, 100, 132, 164, 196, 228)";
+            return UQLB_ERR_ARG;
+        }
+        const bool s3 = strips && spl == 3;
+        if (s3 && ss != 0 && !strip3_fixed_width(smp[0].nx)) {
+            why = "strip_stage applies to the three-step strips at widths 64, 128, 256, 512 and 1024 only";
+            return UQLB_ERR_ARG;
+        }
+        g.strip_bps = s3 ? (sb ? sb : tuned.bps) : 0;
+        g.strip_stage = s3 && strip3_fixed_width(smp[0].nx) ? (ss ? ss : tuned.stage) : 0;
+        g.strip_smem_kb = s3 ? (sk ? sk : tuned.smem_kb) : 0;
+    }
     if (cluster)
         for (int64_t s = 0; s < n; ++s) {
             g.cluster_nx = std::max(g.cluster_nx, smp[s].nx);
@@ -1347,7 +1374,10 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
                     big = g;
                 }
             }
-            for (size_t g = 0; g < groups.size(); ++g) {
+            // the largest group last, so that the context's report describes it
+            for (size_t k = 0; k <= groups.size(); ++k) {
+                if (k == big) continue;
+                const size_t g = k == groups.size() ? big : k;
                 const bool out = g == big;
                 if (int rc = uqlb_autotune(ctx, groups[g].smp.data(), (int64_t)groups[g].smp.size(), &groups[g].opts,
                                            workspace_dev, workspace_bytes, trial_steps, out ? tile_rows : nullptr,
@@ -1363,125 +1393,163 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) return cuda_fail(ctx, e, "autotune: events");
-    int best_r = 0, best_q = 0, tried = 0;
+    int rc = 0, best = -1, spl = 1;
     double best_ms = 1e300;
-    int rc = 0;
     int storage = opts->storage, mixed = 0;
     int64_t nodes = 0;
+    std::vector<uqlb_tune_candidate> cands;
     for (int64_t k = 0; k < n; ++k) {
         mixed |= samples[k].kind == UQLB_CASE_CHANNEL;
         nodes += (int64_t)samples[k].nx * samples[k].ny;
     }
-    bool two = false, strips = false;
-    int def_r = 0, def_q = 0;
     {
         BatchPlan P0;
         std::string why;
         uqlb_run_opts o0 = *opts;
         o0.tile_rows = o0.nodes_per_thread = 0;
+        o0.strip_blocks_per_sm = o0.strip_stage = o0.strip_smem_kb = 0;
         if ((rc = plan_batch(samples, n, &o0, P0, why))) {
             rc = set_err(ctx, rc, "autotune: %s", why.c_str());
             goto done;
         }
-        two = P0.geom.two_step != 0;
-        strips = P0.geom.strips != 0;
-        def_r = P0.geom.tile_rows;
-        def_q = P0.geom.npt;
-    }
-    for (int r : kGeomRows) {
-        for (int q : kGeomNpt) {
-            if (two ? !geometry_supported2(storage, r, q) : !geometry_supported(storage, mixed != 0, r, q)) continue;
-            // the row-strip kernel does not use the tile geometry (only the init and finalize do)
-            if (strips && (r != def_r || q != def_q)) continue;
-            uqlb_run_opts o = *opts;
-            o.tile_rows = r;
-            o.nodes_per_thread = q;
-            o.qoi_every = 0;
-            BatchPlan P;
-            std::string why;
-            if ((rc = plan_batch(samples, n, &o, P, why))) {
-                rc = set_err(ctx, rc, "autotune: %s", why.c_str());
-                goto done;
-            }
-            if (workspace_bytes < P.total) {
-                rc = set_err(ctx, UQLB_ERR_OOM, "autotune: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
-                goto done;
-            }
-            BatchBuffers B = carve(P, workspace_dev);
-            P.geom.max_steps = trial_steps;
-            char* ws = static_cast<char*>(workspace_dev);
-            RunOutputs O{};
-            if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
-                (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
-                (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
-                (e = cudaMemcpyAsync(ws + P.off_rowbase, P.row_base.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s)) ||
-                (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
-                                                          cudaMemcpyHostToDevice, s))) ||
-                (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))) {
-                rc = cuda_fail(ctx, e, "autotune: upload");
-                goto done;
-            }
-            // every sample steps for the whole trial, whatever its own step count
-            for (auto& d : P.table) d.steps = trial_steps;
-            for (auto& v : P.steps_sorted) v = trial_steps;
-            if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
-                (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s))) {
-                rc = cuda_fail(ctx, e, "autotune: upload");
-                goto done;
-            }
-            double ms_best = 1e300;
-            for (int pass = 0; pass < 2; ++pass) {
-                if ((e = cudaMemsetAsync(B.step_counter, 0, 2 * sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s)) ||
-                    (e = cudaEventRecord(e0, s))) {
-                    rc = cuda_fail(ctx, e, "autotune: init");
-                    goto done;
-                }
-                if (two && (e = prepare_step2(P.geom)) != cudaSuccess) {
-                    rc = cuda_fail(ctx, e, "autotune: prepare");
-                    goto done;
-                }
-                for (int dt = 0; dt < trial_steps; dt += two ? 2 : 1)
-                    if ((e = two ? launch_step2(B, P.geom, O, dt, s) : launch_step(B, P.geom, O, dt, 0, s))) {
-                        rc = cuda_fail(ctx, e, "autotune: step launch");
-                        goto done;
+        const BatchGeometry& g0 = P0.geom;
+        const bool two = g0.two_step != 0;
+        spl = two ? std::max(g0.spl, 2) : 1;
+        const int scheme = !two ? UQLB_SCHEME_ONE_STEP
+                                : (g0.strips ? (g0.spl == 3 ? UQLB_SCHEME_THREE_STEP_STRIPS : UQLB_SCHEME_TWO_STEP_STRIPS)
+                                             : UQLB_SCHEME_TWO_STEP_TILES);
+        if (scheme == UQLB_SCHEME_THREE_STEP_STRIPS) {
+            // staging option x blocks per SM (the most that fit and up to three fewer) x share (the
+            // smallest holding the blocks, and the largest)
+            const bool fixed = strip3_fixed_width(g0.strip_nx);
+            for (int stage : {fixed ? 2 : 0, fixed ? 1 : -1}) {
+                int max_b = 0, def_b = 0, def_kb = 0, per = 0;
+                if (stage < 0 || !strip3_blocks(g0, stage, &max_b, &def_b, &def_kb, &per)) continue;
+                for (int b = max_b; b >= std::max(1, max_b - 3); --b) {
+                    const int fit = smem_config_for((size_t)b * per);
+                    for (int kb : {fit, 228}) {
+                        if (kb == 228 && fit == 228) continue;
+                        cands.push_back({scheme, g0.tile_rows, g0.npt, b, stage, kb, 0.0});
                     }
-                float f = 0.0f;
-                if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) || (e = cudaEventElapsedTime(&f, e0, e1))) {
-                    rc = cuda_fail(ctx, e, "autotune: timing");
-                    goto done;
                 }
-                ms_best = std::min(ms_best, (double)f / trial_steps);
             }
-            if (tried < 16) {
-                if (rows_tried) rows_tried[tried] = r;
-                if (npt_tried) npt_tried[tried] = q;
-                if (ms_per_step) ms_per_step[tried] = ms_best;
-            }
-            ++tried;
-            if (ms_best < best_ms) {
-                best_ms = ms_best;
-                best_r = r;
-                best_q = q;
-            }
+        } else {
+            for (int r : kGeomRows)
+                for (int q : kGeomNpt) {
+                    if (two ? !geometry_supported2(storage, r, q) : !geometry_supported(storage, mixed != 0, r, q))
+                        continue;
+                    // the two-step row strips do not use the tile geometry (only the init and finalize do)
+                    if (g0.strips && (r != g0.tile_rows || q != g0.npt)) continue;
+                    cands.push_back({scheme, r, q, 0, 0, 0, 0.0});
+                }
         }
     }
-    if (best_r > 0) {
+    for (size_t c = 0; c < cands.size(); ++c) {
+        uqlb_tune_candidate& cd = cands[c];
+        uqlb_run_opts o = *opts;
+        o.tile_rows = cd.tile_rows;
+        o.nodes_per_thread = cd.nodes_per_thread;
+        o.strip_blocks_per_sm = cd.strip_blocks_per_sm;
+        o.strip_stage = cd.strip_stage;
+        o.strip_smem_kb = cd.strip_smem_kb;
+        o.qoi_every = 0;
+        BatchPlan P;
+        std::string why;
+        if ((rc = plan_batch(samples, n, &o, P, why))) {
+            rc = set_err(ctx, rc, "autotune: %s", why.c_str());
+            goto done;
+        }
+        if (workspace_bytes < P.total) {
+            rc = set_err(ctx, UQLB_ERR_OOM, "autotune: workspace of %zu bytes, need %zu", workspace_bytes, P.total);
+            goto done;
+        }
+        const bool two = P.geom.two_step != 0;
+        BatchBuffers B = carve(P, workspace_dev);
+        P.geom.max_steps = trial_steps;
+        char* ws = static_cast<char*>(workspace_dev);
+        RunOutputs O{};
+        // every sample steps for the whole trial, whatever its own step count
+        for (auto& d : P.table) d.steps = trial_steps;
+        for (auto& v : P.steps_sorted) v = trial_steps;
+        if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
+            (e = cudaMemcpyAsync(ws + P.off_rowbase, P.row_base.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s)) ||
+            (!P.masks.empty() && (e = cudaMemcpyAsync(ws + P.off_masks, P.masks.data(), sizeof(uint32_t) * P.masks.size(),
+                                                      cudaMemcpyHostToDevice, s))) ||
+            (e = cudaMemsetAsync(ws + P.off_side, 0, P.off_partials - P.off_side, s))) {
+            rc = cuda_fail(ctx, e, "autotune: upload");
+            goto done;
+        }
+        if (two && (e = prepare_step2(P.geom)) != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "autotune: prepare");
+            goto done;
+        }
+        double ms_best = 1e300;
+        for (int pass = 0; pass < 2; ++pass) {
+            if ((e = cudaMemsetAsync(B.step_counter, 0, 2 * sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s)) ||
+                (e = cudaEventRecord(e0, s))) {
+                rc = cuda_fail(ctx, e, "autotune: init");
+                goto done;
+            }
+            for (int dt = 0; dt < trial_steps; dt += spl)
+                if ((e = two ? launch_step2(B, P.geom, O, dt, s) : launch_step(B, P.geom, O, dt, 0, s))) {
+                    rc = cuda_fail(ctx, e, "autotune: step launch");
+                    goto done;
+                }
+            float f = 0.0f;
+            if ((e = cudaEventRecord(e1, s)) || (e = cudaEventSynchronize(e1)) || (e = cudaEventElapsedTime(&f, e0, e1))) {
+                rc = cuda_fail(ctx, e, "autotune: timing");
+                goto done;
+            }
+            ms_best = std::min(ms_best, (double)f / trial_steps);
+        }
+        cd.ms_per_step = ms_best;
+        if (c < 16) {
+            if (rows_tried) rows_tried[c] = cd.tile_rows;
+            if (npt_tried) npt_tried[c] = cd.nodes_per_thread;
+            if (ms_per_step) ms_per_step[c] = ms_best;
+        }
+        if (ms_best < best_ms) {
+            best_ms = ms_best;
+            best = (int)c;
+        }
+    }
+    if (best >= 0) {
+        const uqlb_tune_candidate& w = cands[best];
+        TuneChoice tc;
+        tc.rows = w.tile_rows;
+        tc.npt = w.nodes_per_thread;
+        tc.bps = w.strip_blocks_per_sm;
+        tc.stage = w.strip_stage;
+        tc.smem_kb = w.strip_smem_kb;
         bool found = false;
         for (auto& t : ctx->tuned)
             if (t.storage == storage && t.mixed == mixed && t.n == n && t.nodes == nodes) {
-                t.rows = best_r;
-                t.npt = best_q;
+                t.choice = tc;
                 found = true;
             }
-        if (!found) ctx->tuned.push_back({storage, mixed, n, nodes, best_r, best_q});
+        if (!found) ctx->tuned.push_back({storage, mixed, n, nodes, tc});
+        if (tile_rows) *tile_rows = w.tile_rows;
+        if (nodes_per_thread) *nodes_per_thread = w.nodes_per_thread;
     }
-    if (tile_rows) *tile_rows = best_r;
-    if (nodes_per_thread) *nodes_per_thread = best_q;
-    if (n_tried) *n_tried = std::min(tried, 16);
+    ctx->tune_report = cands;
+    ctx->tune_chosen = best;
+    if (n_tried) *n_tried = (int32_t)std::min<size_t>(cands.size(), 16);
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+int uqlb_autotune_report(const uqlb_ctx* ctx, uqlb_tune_candidate* out, int32_t cap, int32_t* n, int32_t* chosen) {
+    if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    if (cap < 0 || (cap > 0 && !out)) return set_err(nullptr, UQLB_ERR_ARG, "autotune_report: bad output array");
+    const size_t m = std::min<size_t>(ctx->tune_report.size(), (size_t)cap);
+    for (size_t k = 0; k < m; ++k) out[k] = ctx->tune_report[k];
+    if (n) *n = (int32_t)ctx->tune_report.size();
+    if (chosen) *chosen = ctx->tune_chosen;
+    return 0;
 }
 
 int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uqlb_run_opts* opts,
@@ -1491,19 +1559,17 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
     if (!samples || !opts || !workspace_dev) return set_err(ctx, UQLB_ERR_ARG, "run_batch: null argument");
     if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return set_err(ctx, UQLB_ERR_ARG, "run_batch: workspace must be 256-byte aligned");
     // the geometry the autotuner picked for a batch of this shape, if any
-    auto tuned_for = [&](const uqlb_sample* smp, int64_t m, int& tr, int& tq) {
+    auto tuned_for = [&](const uqlb_sample* smp, int64_t m) {
         int mixed = 0;
         int64_t nodes = 0;
         for (int64_t k = 0; k < m; ++k) {
             mixed |= smp[k].kind == UQLB_CASE_CHANNEL;
             nodes += (int64_t)smp[k].nx * smp[k].ny;
         }
-        tr = tq = 0;
+        TuneChoice tc;
         for (auto& t : ctx->tuned)
-            if (t.storage == opts->storage && t.mixed == mixed && t.n == m && t.nodes == nodes) {
-                tr = t.rows;
-                tq = t.npt;
-            }
+            if (t.storage == opts->storage && t.mixed == mixed && t.n == m && t.nodes == nodes) tc = t.choice;
+        return tc;
     };
     // plans: one, or one per group of like samples
     std::string why;
@@ -1515,9 +1581,7 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
         const uqlb_sample* smp = groups.empty() ? samples : groups[g].smp.data();
         const int64_t m = groups.empty() ? n : (int64_t)groups[g].smp.size();
         const uqlb_run_opts* o = groups.empty() ? opts : &groups[g].opts;
-        int tr = 0, tq = 0;
-        tuned_for(smp, m, tr, tq);
-        if (int rc = plan_batch(smp, m, o, plans[g], why, tr, tq, groups.empty() ? nullptr : groups[g].idx.data()))
+        if (int rc = plan_batch(smp, m, o, plans[g], why, tuned_for(smp, m), groups.empty() ? nullptr : groups[g].idx.data()))
             return set_err(ctx, rc, "run_batch: %s", why.c_str());
         offs[g] = need;
         need = align_up(need + plans[g].total, 256);

@@ -107,6 +107,9 @@ struct BatchGeometry {
     int32_t spl;             // time steps per launch: 1 (one-step), 2 (tiles, two-step strips), 3 (three-step strips)
     int32_t cluster;         // UQLB_SCHEME_CLUSTER: one thread-block cluster per sample holds it on chip
     int32_t cluster_nx, cluster_ny;  // cluster runs: largest sample width and height
+    int32_t strip_bps;       // three-step strips: resident blocks per SM (0: default)
+    int32_t strip_stage;     // three-step strips at fixed widths: 1 = no staged row, 2 = one (0: default)
+    int32_t strip_smem_kb;   // three-step strips: shared-memory share per SM in KB (0: default)
     int32_t pad_;            // keeps the struct free of padding bytes (it keys the graph cache)
 };
 
@@ -158,6 +161,27 @@ bool geometry_supported2(int storage, int tile_rows, int npt);  // two-step sche
 bool strip_supported(int storage, int nx);
 // Three-step row strips: FP32 rows up to 1280 wide, 16-bit up to 1600 (rounded up to 64 columns).
 bool strip3_supported(int storage, int nx);
+// Widths of the three-step strips with a compile-time instantiation (immediate addressing, and a
+// staging option per launch).
+#ifndef UQLB_STRIP3_FIXED_WIDTHS
+#define UQLB_STRIP3_FIXED_WIDTHS 1
+#endif
+// Shared-memory configurations per SM (KB) that a carveout selects (the rest of the 256 KB is L1),
+// and the smallest one holding `bytes`.
+constexpr int kSmemConfigsKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+inline int smem_config_for(size_t bytes) {
+    for (int kb : kSmemConfigsKB)
+        if ((size_t)kb * 1024 >= bytes) return kb;
+    return 228;
+}
+inline bool strip3_fixed_width(int nx) {
+    return UQLB_STRIP3_FIXED_WIDTHS && (nx == 64 || nx == 128 || nx == 256 || nx == 512 || nx == 1024);
+}
+// Three-step strips of batch g at staging option `stage` (1: none, 2: one row, 0: default): the
+// most resident blocks per SM, the default, the default shared-memory share (KB) and the shared
+// memory per block (bytes).  False when g does not run on the three-step strips or the staging
+// option does not apply to its width.
+bool strip3_blocks(const BatchGeometry& g, int stage, int* max_b, int* def_b, int* def_kb, int* per_block);
 
 // Plain per-sample FP64 path (plain_f64.cu).
 struct PlainSample {

@@ -42,9 +42,11 @@ SCHEMES = {"auto": U.UQLB_SCHEME_AUTO, "one_step": U.UQLB_SCHEME_ONE_STEP, "two_
 
 def opts_struct(storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0, chunk_steps: int = 0,
                 tile_rows: int = 0, nodes_per_thread: int = 0, rounding: str = "auto",
-                start_step: int = 0, mode: str = "graph", scheme: str = "auto") -> U.uqlb_run_opts:
+                start_step: int = 0, mode: str = "graph", scheme: str = "auto", strip_blocks_per_sm: int = 0,
+                strip_stage: int = 0, strip_smem_kb: int = 0) -> U.uqlb_run_opts:
     return U.uqlb_run_opts(STORAGE[storage], STORAGE[fields_dtype], qoi_every, chunk_steps, tile_rows,
-                           nodes_per_thread, ROUNDING[rounding], start_step, MODES[mode], SCHEMES[scheme])
+                           nodes_per_thread, ROUNDING[rounding], start_step, MODES[mode], SCHEMES[scheme],
+                           strip_blocks_per_sm, strip_stage, strip_smem_kb)
 
 
 def _stream() -> int:
@@ -125,11 +127,12 @@ class Ensemble:
     def run_batch(self, samples, storage: str = "f32", fields_dtype: str = "f32", qoi_every: int = 0,
                   fields: bool = True, series: bool = False, chunk_steps: int = 0, tile_rows: int = 0,
                   nodes_per_thread: int = 0, rounding: str = "auto", start_step: int = 0, mode: str = "graph",
-                  scheme: str = "auto", out: dict | None = None) -> dict:
+                  scheme: str = "auto", out: dict | None = None, strip: tuple = (0, 0, 0)) -> dict:
         """Run the given uqlb_sample structs; returns torch tensors (fields M, qoi, series).  With
-        start_step > 0 the run continues the state left by the previous call (same samples)."""
+        start_step > 0 the run continues the state left by the previous call (same samples).  strip:
+        the three-step strips' (blocks per SM, staging option, shared-memory KB), 0 = tuned/default."""
         opts = opts_struct(storage, fields_dtype, qoi_every, chunk_steps, tile_rows, nodes_per_thread, rounding,
-                           start_step, mode, scheme)
+                           start_step, mode, scheme, *strip)
         nbytes = U.uqlb_batch_workspace_bytes(samples, opts)
         ws = self.workspace(nbytes)
         n = len(samples)
@@ -155,7 +158,9 @@ class Ensemble:
     def autotune(self, samples, storage: str = "f32", trial_steps: int = 16, scheme: str = "auto") -> dict:
         opts = opts_struct(storage, "f32", 0, scheme=scheme)
         ws = self.workspace(U.uqlb_batch_workspace_bytes(samples, opts))
-        return U.uqlb_autotune(self.ctx, samples, opts, ws.data_ptr(), ws.numel(), trial_steps, _stream())
+        res = U.uqlb_autotune(self.ctx, samples, opts, ws.data_ptr(), ws.numel(), trial_steps, _stream())
+        res.update(U.uqlb_autotune_report(self.ctx))
+        return res
 
     def w1_speed(self, a: torch.Tensor, nodes_a: int, b: torch.Tensor, nodes_b: int, bins: int = 1 << 20):
         """W1 distance between the speed distributions of two field sets (and its error bound)."""

@@ -64,7 +64,14 @@ class uqlb_case(ctypes.Structure):
 class uqlb_run_opts(ctypes.Structure):
     _fields_ = [("storage", c_int32), ("fields_dtype", c_int32), ("qoi_every", c_int64),
                 ("chunk_steps", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
-                ("rounding", c_int32), ("start_step", c_int64), ("mode", c_int32), ("scheme", c_int32)]
+                ("rounding", c_int32), ("start_step", c_int64), ("mode", c_int32), ("scheme", c_int32),
+                ("strip_blocks_per_sm", c_int32), ("strip_stage", c_int32), ("strip_smem_kb", c_int32)]
+
+
+class uqlb_tune_candidate(ctypes.Structure):
+    _fields_ = [("scheme", c_int32), ("tile_rows", c_int32), ("nodes_per_thread", c_int32),
+                ("strip_blocks_per_sm", c_int32), ("strip_stage", c_int32), ("strip_smem_kb", c_int32),
+                ("ms_per_step", c_double)]
 
 
 _P = ctypes.POINTER
@@ -95,6 +102,7 @@ _SIGNATURES = {
                        c_int64, c_void_p, c_void_p, c_void_p, c_int64, c_void_p],
     "uqlb_autotune": [c_void_p, _P(uqlb_sample), c_int64, _P(uqlb_run_opts), c_void_p, c_size_t, ctypes.c_int,
                       _P(c_int32), _P(c_int32), _P(c_int32), _P(c_int32), _P(c_double), _P(c_int32), c_void_p],
+    "uqlb_autotune_report": [c_void_p, _P(uqlb_tune_candidate), c_int32, _P(c_int32), _P(c_int32)],
     "uqlb_ensemble_samples": [c_void_p, _P(uqlb_case), _P(uqlb_sample)],
     "uqlb_ensemble_workspace_bytes": [c_void_p, _P(uqlb_case), _P(uqlb_run_opts), _P(c_size_t)],
     "uqlb_run_ensemble": [c_void_p, _P(uqlb_case), _P(uqlb_run_opts), c_void_p, c_size_t, c_void_p, c_int64,
@@ -325,6 +333,16 @@ def uqlb_autotune(ctx, samples, opts: uqlb_run_opts, workspace_dev: int, workspa
                                ctypes.byref(q), rows, npts, ms, ctypes.byref(nt), _stream(stream)), ctx)
     return {"tile_rows": r.value, "nodes_per_thread": q.value,
             "tried": [(rows[i], npts[i], ms[i]) for i in range(nt.value)]}
+
+
+def uqlb_autotune_report(ctx) -> dict:
+    """The candidates of the context's last autotune (strip knobs included) and the chosen index."""
+    n, chosen = c_int32(), c_int32()
+    _check(lib().uqlb_autotune_report(ctx, None, 0, ctypes.byref(n), ctypes.byref(chosen)), ctx)
+    out = (uqlb_tune_candidate * max(n.value, 1))()
+    _check(lib().uqlb_autotune_report(ctx, out, n.value, ctypes.byref(n), ctypes.byref(chosen)), ctx)
+    names = [f for f, _ in uqlb_tune_candidate._fields_]
+    return {"chosen": chosen.value, "candidates": [{k: getattr(out[i], k) for k in names} for i in range(n.value)]}
 
 
 def uqlb_ensemble_samples(ctx, case: uqlb_case) -> list:

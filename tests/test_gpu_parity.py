@@ -45,11 +45,12 @@ def ens():
     e.close()
 
 
-def _run(ens, specs, storage, qoi_every=0, series=False, tile_rows=0, chunk=0, npt=0, scheme="auto"):
+def _run(ens, specs, storage, qoi_every=0, series=False, tile_rows=0, chunk=0, npt=0, scheme="auto",
+         strip=(0, 0, 0)):
     res = ens.run_batch([sample_struct(s) for s in specs], storage=storage,
                         fields_dtype="f64" if storage == "f64" else "f32", qoi_every=qoi_every, series=series,
                         tile_rows=tile_rows, nodes_per_thread=npt, chunk_steps=chunk,
-                        fields=len({(s.nx, s.ny) for s in specs}) == 1, scheme=scheme)
+                        fields=len({(s.nx, s.ny) for s in specs}) == 1, scheme=scheme, strip=strip)
     torch.cuda.synchronize()
     return {k: v.double().cpu().numpy() for k, v in res.items()}
 
@@ -988,6 +989,65 @@ def test_three_step_strips_equal_the_two_step_strips_bit_for_bit(ens):
         b = _run(ens, specs, "f32", qoi_every=5, series=True, scheme="three_step_strips")
         assert np.array_equal(a["fields"][:, :-1], b["fields"][:, :-1]), (n, ny)
         assert np.allclose(a["series"], b["series"], rtol=1e-12, atol=0, equal_nan=True), (n, ny)
+
+
+@pytest.mark.parametrize("storage,n,ny", [("f32", 256, 40), ("f16", 128, 77), ("bf16", 512, 20), ("fx16", 64, 64),
+                                          ("f32", 200, 31)])
+def test_three_step_strip_launch_shapes_agree(ens, storage, n, ny):
+    """The launch shape of the three-step strips (resident blocks per SM, so the rows each block takes;
+    the staged or direct load of the phase-A rows; the shared-memory share) changes which block updates
+    a row and how its values reach the registers, not the arithmetic of a node, and the stochastic
+    rounding draws its bits from the node, step and sample: fields are equal bit for bit across shapes,
+    the K series (summed per block) to FP64 round-off; the default shape against the oracle within the
+    storage's budget (BF16, whose budget misses are asserted elsewhere, on the shapes only).  Width 200
+    has no fixed-width kernel (staging option 0 only)."""
+    specs = [replace(W.tgv(n, 20, nu=0.03, amp2=0.0005), ny=ny), replace(W.tgv(n, 19, nu=0.05), ny=ny),
+             replace(W.tgv(n, 21, nu=0.04, amp3=0.0003), ny=ny)]
+    if storage == "fx16":
+        specs = [replace(s, ny=n) for s in specs]
+    ref = _run(ens, specs, storage, qoi_every=4, series=True, scheme="three_step_strips")
+    stages = (1, 2) if n in (64, 128, 256, 512, 1024) else (0,)
+    for bps, kb in ((1, 0), (2, 228), (3, 100), (16, 0)):
+        for stage in stages:
+            got = _run(ens, specs, storage, qoi_every=4, series=True, scheme="three_step_strips",
+                       strip=(bps, stage, kb))
+            assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_THREE_STEP_STRIPS
+            assert np.array_equal(got["fields"][:, :-1], ref["fields"][:, :-1]), (bps, stage, kb)
+            assert np.allclose(got["series"], ref["series"], rtol=1e-12, atol=0, equal_nan=True), (bps, stage, kb)
+    if storage == "bf16":
+        return
+    oracle = olbm.run([oracle_case(s, qoi_every=4) for s in specs])
+    for i, r in enumerate(oracle):
+        assert rel_l2(ref["fields"][i, :-1], oracle_row(r)[:-1]) < TOL[storage], (storage, i)
+
+
+def test_autotune_tunes_the_three_step_strips(ens):
+    """On a batch that runs on the three-step strips the autotuner times staging option x blocks per SM
+    x shared-memory share (the tile geometry stays at its default), keeps the fastest, and the next run
+    of that batch shape uses it: its fields equal an explicit run with the chosen shape, and the
+    oracle's within the FP32 budget."""
+    specs = [W.tgv(256, 30, nu=0.03 + 0.002 * k, amp2=0.0004) for k in range(12)]
+    smp = [sample_struct(s) for s in specs]
+    res = ens.autotune(smp, storage="f32", trial_steps=12)
+    cands = res["candidates"]
+    assert len(cands) >= 4 and 0 <= res["chosen"] < len(cands)
+    configs = {8, 16, 32, 64, 100, 132, 164, 196, 228}
+    for c in cands:
+        assert c["scheme"] == U.UQLB_SCHEME_THREE_STEP_STRIPS
+        assert c["strip_stage"] in (1, 2) and c["strip_blocks_per_sm"] >= 1 and c["strip_smem_kb"] in configs
+        assert c["ms_per_step"] > 0
+    assert {c["strip_stage"] for c in cands} == {1, 2}
+    best = cands[res["chosen"]]
+    assert best["ms_per_step"] == min(c["ms_per_step"] for c in cands)
+    assert len(res["tried"]) == min(len(cands), 16)
+    tuned = _run(ens, specs, "f32", qoi_every=5, series=True)
+    assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_THREE_STEP_STRIPS
+    shape = (best["strip_blocks_per_sm"], best["strip_stage"], best["strip_smem_kb"])
+    explicit = _run(ens, specs, "f32", qoi_every=5, series=True, strip=shape)
+    assert np.array_equal(tuned["fields"], explicit["fields"])
+    oracle = olbm.run([oracle_case(s, qoi_every=5) for s in specs[:3]])
+    for i, r in enumerate(oracle):
+        assert rel_l2(tuned["fields"][i, :-1], oracle_row(r)[:-1]) < TOL["f32"], i
 
 
 @pytest.mark.parametrize("first,second", [("three_step_strips", "three_step_strips"),

@@ -50,7 +50,8 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(U.uqlb_dist) == 24
     assert ctypes.sizeof(U.uqlb_sample) == 144
     assert ctypes.sizeof(U.uqlb_case) == 176
-    assert ctypes.sizeof(U.uqlb_run_opts) == 48
+    assert ctypes.sizeof(U.uqlb_run_opts) == 64
+    assert ctypes.sizeof(U.uqlb_tune_candidate) == 32
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 9, 17, 33, 64])
@@ -325,6 +326,30 @@ def test_scheme_selection_and_its_limits():
     one_chan = U.uqlb_batch_workspace_bytes(
         chan, U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP))
     assert auto_chan == one_chan
+
+
+def test_strip_launch_shape_options_are_checked():
+    """The three-step strips' launch-shape options: blocks per SM 0..32, staging option 0..2 (the
+    fixed widths only), shared-memory share 0 or one of the carveout configurations; none of them
+    changes the workspace."""
+    def opts(bps=0, stage=0, kb=0, scheme=U.UQLB_SCHEME_THREE_STEP_STRIPS):
+        return U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, scheme, bps, stage, kb)
+
+    fixed = [sample_struct(W.tgv(256, 10))]
+    ragged = [sample_struct(W.tgv(200, 10))]
+    base = U.uqlb_batch_workspace_bytes(fixed, opts())
+    for bps, stage, kb in ((1, 1, 8), (4, 2, 196), (32, 0, 228), (0, 0, 100), (3, 2, 0)):
+        assert U.uqlb_batch_workspace_bytes(fixed, opts(bps, stage, kb)) == base
+    assert U.uqlb_batch_workspace_bytes(ragged, opts(2, 0, 164)) > 0
+    for smp, o in ((fixed, opts(-1)), (fixed, opts(33)), (fixed, opts(0, 3)), (fixed, opts(0, -1)),
+                   (fixed, opts(0, 0, 50)), (fixed, opts(0, 0, 256)), (fixed, opts(0, 0, -8)),
+                   (ragged, opts(0, 1)), (ragged, opts(0, 2))):
+        with pytest.raises(U.UqlbError) as e:
+            U.uqlb_batch_workspace_bytes(smp, o)
+        assert e.value.status == U.UQLB_ERR_ARG
+    # other schemes ignore the strip options (range-checked all the same)
+    one = U.uqlb_run_opts(U.UQLB_F32, U.UQLB_F32, 0, 0, 0, 0, 0, 0, 0, U.UQLB_SCHEME_ONE_STEP, 4, 2, 196)
+    assert U.uqlb_batch_workspace_bytes(ragged, one) > 0
 
 
 def test_grouped_batch_workspace_is_the_sum_of_its_groups():

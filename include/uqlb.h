@@ -389,9 +389,10 @@ int uqlb_run_batch(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const u
                    void* stream);
 
 /* Launch-shape autotuner.  For this batch shape, time `trial_steps` (>= 2, even) steps of every
- * candidate launch shape on the device (after an equilibrium initialisation, CUDA events on
- * `stream`, best of two passes) and keep the fastest in the context; later runs of a batch with
- * the same storage, kinds, sample count and node count use it for the fields they pass as 0.
+ * candidate launch shape on the device (after an equilibrium initialisation and one untimed
+ * launch, CUDA events on `stream`, best of three passes) and keep the fastest in the context;
+ * later runs of a batch with the same storage, kinds, sample count and node count use it for the
+ * fields they pass as 0.
  * Candidates: on the tile kernels every compiled tile geometry; on the three-step row strips (the
  * default for periodic batches of one width) the staging option x resident blocks per SM (the
  * most that fit and up to three fewer) x shared-memory share (the smallest holding the blocks,
@@ -411,7 +412,7 @@ typedef struct {
     int32_t scheme;           /* UQLB_SCHEME_* of the kernel the candidate ran */
     int32_t tile_rows, nodes_per_thread;
     int32_t strip_blocks_per_sm, strip_stage, strip_smem_kb;  /* 0 off the three-step strips */
-    double ms_per_step;       /* best of two passes */
+    double ms_per_step;       /* best of three passes */
 } uqlb_tune_candidate;
 
 /* The candidates of the context's last uqlb_autotune call (host): up to `cap` into `out` (may be

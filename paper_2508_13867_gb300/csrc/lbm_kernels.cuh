@@ -1063,9 +1063,13 @@ __device__ __forceinline__ f2 pair_load<__nv_bfloat16>(const __nv_bfloat16* ptr,
 }
 template <>
 __device__ __forceinline__ f2 pair_load<int16_t>(const int16_t* ptr, const Quanta& qz, int i) {
-    const int w = *reinterpret_cast<const int*>(ptr);
-    const float d = qz.d[qclass(i)];
-    return mul2(pk((float)(int16_t)(w & 0xFFFF), (float)(w >> 16)), splat(d));
+    // each signed value plus 2^15 becomes the low mantissa bits of 2^23 (byte permutes, no integer
+    // conversion); one packed subtraction of 2^23 + 2^15 gives the two integers exactly and one
+    // packed multiply scales them: the same single rounding as (float)q * d
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(ptr) ^ 0x80008000u;
+    const f2 biased = pk(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7610)),
+                         __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7632)));
+    return mul2(sub2(biased, splat(8421376.0f)), splat(qz.d[qclass(i)]));
 }
 // Round-to-nearest store of a pair (each half rounded as Storage<S>::store does).
 template <typename S>
@@ -1094,6 +1098,68 @@ __device__ __forceinline__ void pair_store<int16_t>(int16_t* ptr, f2 v, const Qu
     const uint32_t hi = (uint16_t)Storage<int16_t>::round_nearest(b, qz, i);
     *reinterpret_cast<uint32_t*>(ptr) = lo | (hi << 16);
 }
+
+// A pair's two 16-bit values as one word (the lower column in bits 15:0), rounded to nearest
+// (pair_word) or stochastically (pair_word_sr) with the random bits r: r[15:0] for the lower column,
+// r[31:16] for the upper.  The floating formats use cvt.rs, which adds the random bits below the
+// kept mantissa and truncates (with FP32 operands scaled as Storage<S>::store scales them); the
+// fixed-point format adds them as a fraction of its quantum and rounds down (Storage<int16_t>).
+template <typename S>
+__device__ __forceinline__ uint32_t pair_word(f2 v, const typename Storage<S>::Q& qz, int i);
+template <typename S>
+__device__ __forceinline__ uint32_t pair_word_sr(f2 v, uint32_t r, const typename Storage<S>::Q& qz, int i);
+template <>
+__device__ __forceinline__ uint32_t pair_word<__nv_bfloat16>(f2 v, const NoQuanta&, int) {
+    float a, b;
+    upk(v, a, b);
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+template <>
+__device__ __forceinline__ uint32_t pair_word_sr<__nv_bfloat16>(f2 v, uint32_t r, const NoQuanta&, int) {
+    float a, b;
+    upk(v, a, b);
+    uint32_t d;
+    asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(r));
+    return d;
+}
+template <>
+__device__ __forceinline__ uint32_t pair_word<__half>(f2 v, const NoQuanta&, int) {
+    float a, b;
+    upk(mul2(v, splat(0x1p12f)), a, b);
+    uint32_t d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+template <>
+__device__ __forceinline__ uint32_t pair_word_sr<__half>(f2 v, uint32_t r, const NoQuanta&, int) {
+    float a, b;
+    upk(mul2(v, splat(0x1p12f)), a, b);
+    uint32_t d;
+    asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(r));
+    return d;
+}
+template <>
+__device__ __forceinline__ uint32_t pair_word<int16_t>(f2 v, const Quanta& qz, int i) {
+    float a, b;
+    upk(v, a, b);
+    const uint32_t lo = (uint16_t)Storage<int16_t>::round_nearest(a, qz, i);
+    const uint32_t hi = (uint16_t)Storage<int16_t>::round_nearest(b, qz, i);
+    return lo | (hi << 16);
+}
+template <>
+__device__ __forceinline__ uint32_t pair_word_sr<int16_t>(f2 v, uint32_t r, const Quanta& qz, int i) {
+    float a, b;
+    upk(v, a, b);
+    const uint32_t lo = (uint16_t)Storage<int16_t>::round_stochastic(a, r, qz, i);
+    const uint32_t hi = (uint16_t)Storage<int16_t>::round_stochastic(b, r >> 16, qz, i);
+    return lo | (hi << 16);
+}
+
+// Random bits of population i of a node pair from the pair's hash h (an odd multiplier per
+// population: each maps the uniform h one to one onto 32 bits).
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int i) { return h * (0x2545F491u + 0x6A09E668u * (uint32_t)i); }
 
 // Block-wide deterministic sum of NV doubles for any whole number of warps; result in thread 0.
 template <int NV>
@@ -1489,28 +1555,41 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
         auto push = [&](int y, int ts, const f2 (&g)[9]) {
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             const int row[3] = {ym * pitch, y * pitch, yp * pitch};
-            uint32_t ha = 0u, hb = 0u;
-            if (sr) {
-                const uint32_t base = (uint32_t)ts * 0x85EBCA77u + sid * 0xC2B2AE3Du;
-                ha = mix32((uint32_t)(y * pitch + x) * 0x9E3779B1u + base);
-                hb = mix32((uint32_t)(y * pitch + x + 1) * 0x9E3779B1u + base);
-            }
+            if constexpr (sizeof(S) == 2) {
+                // 16-bit storage: each population's pair rounded into one word (one hash per pair and
+                // step for the stochastic bits), stored whole where it stays in its columns
+                uint32_t h = 0u;
+                if (sr)
+                    h = mix32((uint32_t)(y * pitch + x) * 0x9E3779B1u + (uint32_t)ts * 0x85EBCA77u +
+                              sid * 0xC2B2AE3Du);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                S* d = dst + (i * plane + row[1 + cy(i)]);
-                float a, b;
-                upk(g[i], a, b);
-                const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? xar : xl);
-                const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xbr : x);
-                if (sr) {
-                    const uint32_t m = 0x2545F491u + 0x6A09E668u * (uint32_t)i;
-                    Storage<S>::store_sr(d + ca, a, (ha * m) >> 16, qz, i);
-                    if (vb) Storage<S>::store_sr(d + cb, b, (hb * m) >> 16, qz, i);
-                } else if (cx(i) == 0 && vb) {
-                    pair_store<S>(d + x, g[i], qz, i);
-                } else {
-                    Storage<S>::store(d + ca, a, qz, i);
-                    if (vb) Storage<S>::store(d + cb, b, qz, i);
+                for (int i = 0; i < 9; ++i) {
+                    S* d = dst + (i * plane + row[1 + cy(i)]);
+                    const uint32_t w =
+                        sr ? pair_word_sr<S>(g[i], sr_bits(h, i), qz, i) : pair_word<S>(g[i], qz, i);
+                    if (cx(i) == 0 && vb) {
+                        *reinterpret_cast<uint32_t*>(d + x) = w;
+                    } else {
+                        const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? xar : xl);
+                        const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xbr : x);
+                        *reinterpret_cast<uint16_t*>(d + ca) = (uint16_t)w;
+                        if (vb) *reinterpret_cast<uint16_t*>(d + cb) = (uint16_t)(w >> 16);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    S* d = dst + (i * plane + row[1 + cy(i)]);
+                    float a, b;
+                    upk(g[i], a, b);
+                    const int ca = cx(i) == 0 ? x : (cx(i) > 0 ? xar : xl);
+                    const int cb = cx(i) == 0 ? x + 1 : (cx(i) > 0 ? xbr : x);
+                    if (cx(i) == 0 && vb) {
+                        pair_store<S>(d + x, g[i], qz, i);
+                    } else {
+                        Storage<S>::store(d + ca, a, qz, i);
+                        if (vb) Storage<S>::store(d + cb, b, qz, i);
+                    }
                 }
             }
         };
@@ -1769,61 +1848,88 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
             y -= y >= ny ? ny : 0;
             return y;
         };
-        auto st1 = [&](S* d, float v, uint32_t h, int i) {
-            if (sr)
-                Storage<S>::store_sr(d, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
-            else
-                Storage<S>::store(d, v, qz, i);
-        };
-        auto st2 = [&](S* d, f2 v, uint32_t ha, uint32_t hb, int i) {
-            if (sr) {
-                float a, b;
-                upk(v, a, b);
-                st1(d, a, ha, i);
-                st1(d + 1, b, hb, i);
-            } else {
-                pair_store<S>(d, v, qz, i);
-            }
-        };
+        // FP32 stores (16-bit storage rounds whole pairs, in push)
+        auto st1 = [&](S* d, float v, int i) { Storage<S>::store(d, v, qz, i); };
+        auto st2 = [&](S* d, f2 v, int i) { pair_store<S>(d, v, qz, i); };
         // push of the pair's post-collision populations g (step ts, row y) into the other lattice
         auto push = [&](int y, int ts, const f2 (&g)[9]) {
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-            uint32_t ha = 0u, hb = 0u;
-            if (sr) {
-                const uint32_t base = (uint32_t)ts * 0x85EBCA77u + sid * 0xC2B2AE3Du;
-                ha = mix32((uint32_t)(y * 9 * W + x) * 0x9E3779B1u + base);
-                hb = mix32((uint32_t)(y * 9 * W + x + 1) * 0x9E3779B1u + base);
-            }
-            float a, b;
-            {  // row y: populations 0, 1, 3
-                S* R = dst + y * (9 * W);
-                st2(R, g[0], ha, hb, 0);
-                upk(g[1], a, b);
-                st1(R + W + 1, a, ha, 1);
-                st1(R + offr + W, b, hb, 1);
-                upk(g[3], a, b);
-                st1(R + offl + 3 * W, a, ha, 3);
-                st1(R + 3 * W, b, hb, 3);
-            }
-            {  // row y + 1: populations 2, 5, 6
-                S* R = dst + yp * (9 * W);
-                st2(R + 2 * W, g[2], ha, hb, 2);
-                upk(g[5], a, b);
-                st1(R + 5 * W + 1, a, ha, 5);
-                st1(R + offr + 5 * W, b, hb, 5);
-                upk(g[6], a, b);
-                st1(R + offl + 6 * W, a, ha, 6);
-                st1(R + 6 * W, b, hb, 6);
-            }
-            {  // row y - 1: populations 4, 7, 8
-                S* R = dst + ym * (9 * W);
-                st2(R + 4 * W, g[4], ha, hb, 4);
-                upk(g[7], a, b);
-                st1(R + offl + 7 * W, a, ha, 7);
-                st1(R + 7 * W, b, hb, 7);
-                upk(g[8], a, b);
-                st1(R + 8 * W + 1, a, ha, 8);
-                st1(R + offr + 8 * W, b, hb, 8);
+            if constexpr (sizeof(S) == 2) {
+                // 16-bit storage: each population's pair rounded into one word (one hash per pair and
+                // step for the stochastic bits); the x-moving populations land in two columns
+                uint32_t h = 0u;
+                if (sr)
+                    h = mix32((uint32_t)(y * 9 * W + x) * 0x9E3779B1u + (uint32_t)ts * 0x85EBCA77u +
+                              sid * 0xC2B2AE3Du);
+                auto word = [&](int i) {
+                    return sr ? pair_word_sr<S>(g[i], sr_bits(h, i), qz, i) : pair_word<S>(g[i], qz, i);
+                };
+                auto put2 = [](S* at, uint32_t w) { *reinterpret_cast<uint32_t*>(at) = w; };
+                auto put_lo = [](S* at, uint32_t w) { *reinterpret_cast<uint16_t*>(at) = (uint16_t)w; };
+                auto put_hi = [](S* at, uint32_t w) { *reinterpret_cast<uint16_t*>(at) = (uint16_t)(w >> 16); };
+                uint32_t w;
+                {  // row y: populations 0, 1, 3
+                    S* R = dst + y * (9 * W);
+                    put2(R, word(0));
+                    w = word(1);
+                    put_lo(R + W + 1, w);
+                    put_hi(R + offr + W, w);
+                    w = word(3);
+                    put_lo(R + offl + 3 * W, w);
+                    put_hi(R + 3 * W, w);
+                }
+                {  // row y + 1: populations 2, 5, 6
+                    S* R = dst + yp * (9 * W);
+                    put2(R + 2 * W, word(2));
+                    w = word(5);
+                    put_lo(R + 5 * W + 1, w);
+                    put_hi(R + offr + 5 * W, w);
+                    w = word(6);
+                    put_lo(R + offl + 6 * W, w);
+                    put_hi(R + 6 * W, w);
+                }
+                {  // row y - 1: populations 4, 7, 8
+                    S* R = dst + ym * (9 * W);
+                    put2(R + 4 * W, word(4));
+                    w = word(7);
+                    put_lo(R + offl + 7 * W, w);
+                    put_hi(R + 7 * W, w);
+                    w = word(8);
+                    put_lo(R + 8 * W + 1, w);
+                    put_hi(R + offr + 8 * W, w);
+                }
+            } else {
+                float a, b;
+                {  // row y: populations 0, 1, 3
+                    S* R = dst + y * (9 * W);
+                    st2(R, g[0], 0);
+                    upk(g[1], a, b);
+                    st1(R + W + 1, a, 1);
+                    st1(R + offr + W, b, 1);
+                    upk(g[3], a, b);
+                    st1(R + offl + 3 * W, a, 3);
+                    st1(R + 3 * W, b, 3);
+                }
+                {  // row y + 1: populations 2, 5, 6
+                    S* R = dst + yp * (9 * W);
+                    st2(R + 2 * W, g[2], 2);
+                    upk(g[5], a, b);
+                    st1(R + 5 * W + 1, a, 5);
+                    st1(R + offr + 5 * W, b, 5);
+                    upk(g[6], a, b);
+                    st1(R + offl + 6 * W, a, 6);
+                    st1(R + 6 * W, b, 6);
+                }
+                {  // row y - 1: populations 4, 7, 8
+                    S* R = dst + ym * (9 * W);
+                    st2(R + 4 * W, g[4], 4);
+                    upk(g[7], a, b);
+                    st1(R + offl + 7 * W, a, 7);
+                    st1(R + 7 * W, b, 7);
+                    upk(g[8], a, b);
+                    st1(R + 8 * W + 1, a, 8);
+                    st1(R + offr + 8 * W, b, 8);
+                }
             }
         };
         auto add_usq = [&](double& acc, f2 q) {

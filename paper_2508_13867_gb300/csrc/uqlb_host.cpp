@@ -1465,12 +1465,14 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
         }
         const bool two = P.geom.two_step != 0;
         BatchBuffers B = carve(P, workspace_dev);
-        P.geom.max_steps = trial_steps;
         char* ws = static_cast<char*>(workspace_dev);
         RunOutputs O{};
-        // every sample steps for the whole trial, whatever its own step count
-        for (auto& d : P.table) d.steps = trial_steps;
-        for (auto& v : P.steps_sorted) v = trial_steps;
+        // every sample steps for the whole trial, whatever its own step count: one untimed launch
+        // (it also takes the write-back of the initial state), then trial_steps timed steps
+        const int warm = spl, total = warm + trial_steps;
+        P.geom.max_steps = total;
+        for (auto& d : P.table) d.steps = total;
+        for (auto& v : P.steps_sorted) v = total;
         if ((e = cudaMemcpyAsync(ws + P.off_samples, P.table.data(), sizeof(SampleDev) * n, cudaMemcpyHostToDevice, s)) ||
             (e = cudaMemcpyAsync(ws + P.off_init, P.init.data(), sizeof(InitDev) * n, cudaMemcpyHostToDevice, s)) ||
             (e = cudaMemcpyAsync(ws + P.off_steps, P.steps_sorted.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) ||
@@ -1486,14 +1488,14 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
             goto done;
         }
         double ms_best = 1e300;
-        for (int pass = 0; pass < 2; ++pass) {
-            if ((e = cudaMemsetAsync(B.step_counter, 0, 2 * sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s)) ||
-                (e = cudaEventRecord(e0, s))) {
+        for (int pass = 0; pass < 3; ++pass) {
+            if ((e = cudaMemsetAsync(B.step_counter, 0, 2 * sizeof(int64_t), s)) || (e = launch_init(B, P.geom, s))) {
                 rc = cuda_fail(ctx, e, "autotune: init");
                 goto done;
             }
-            for (int dt = 0; dt < trial_steps; dt += spl)
-                if ((e = two ? launch_step2(B, P.geom, O, dt, s) : launch_step(B, P.geom, O, dt, 0, s))) {
+            for (int dt = 0; dt < total; dt += spl)
+                if ((dt == warm && (e = cudaEventRecord(e0, s))) ||
+                    (e = two ? launch_step2(B, P.geom, O, dt, s) : launch_step(B, P.geom, O, dt, 0, s))) {
                     rc = cuda_fail(ctx, e, "autotune: step launch");
                     goto done;
                 }

@@ -231,19 +231,32 @@ typedef struct {
  *     with fewer than three steps left runs two or one in its last launch.  With FP32 storage its
  *     fields equal the two-step strips' bit for bit (the same packed collisions of the same node
  *     pairs; FP32 rows pass through shared memory and HBM unrounded).
+ *   UQLB_SCHEME_CLUSTER: CHANNEL samples with the halfway obstacle and the face inlet/outlet, FP32
+ *     or 16-bit storage, UQLB_MODE_GRAPH: one thread-block cluster per sample holds the sample's
+ *     lattice in shared memory (split into slabs of columns over up to 16 blocks, one copy, updated
+ *     in place in AA order; slab edges through distributed shared memory) and runs its whole time
+ *     loop, the steady-state test included, in one launch; HBM is touched to load the state and to
+ *     write it back.  The largest sample's lattice, its link words and node lists must fit 16
+ *     blocks' shared memory (about 220 KB per block: FP32 440 x 82 at 10 to 16 blocks, 16-bit up to
+ *     about 860 x 160).  Cluster size: the one with the least estimated time over the clusters that
+ *     run at once.  Fields equal the one-step scheme's bit for bit; C_D and C_L sum the same link
+ *     forces in another order (FP32 round-off).  One workspace lattice, as ONE_STEP.
  *   UQLB_SCHEME_AUTO: the row strips for periodic FP32, FP16, BF16 and FX16 batches in graph mode,
  *     three steps per launch where the width allows it, else two, else TWO_STEP_TILES (measured on
  *     GB300, 625 x 256^2 ensemble, kernel GLUPS three-step strips / two-step strips / tiles /
- *     one-step: FP32 203 / 177 / 115 / 84, FP16 174 / 161 / 95 / 82, BF16 183 / 172 / 103 / 90,
- *     FX16 171 / 160 / - / -); ONE_STEP otherwise (FP64 is bound by the FP64 rate).  In graph mode
- *     with FP32/FP16/BF16/FX16 storage a batch of unlike samples runs as groups of like samples, one
- *     group after another on one stream, each on its own kernel and its own slice of the workspace
- *     (uqlb_batch_workspace_bytes counts them all): CHANNEL samples on ONE_STEP, periodic samples of
- *     each width the strips take on the strips, wider periodic samples on TWO_STEP_TILES.  Outputs
- *     keep the caller's rows.  uqlb_last_run_geometry then reports UQLB_SCHEME_GROUPED.
+ *     one-step: FP32 230 / 179 / 115 / 84, BF16 220 / 184 / 103 / 90, FP16 215 / 173 / 95 / 82,
+ *     FX16 200 / 170 / - / -); CLUSTER for CHANNEL batches that allow it (FP32 9 x 440 x 82 cylinder
+ *     samples: 53 against 24 GLUPS on ONE_STEP); ONE_STEP otherwise (FP64 is bound by the FP64
+ *     rate).  In graph mode with FP32/FP16/BF16/FX16 storage a batch of unlike samples runs as
+ *     groups of like samples, one group after another on one stream, each on its own kernel and its
+ *     own slice of the workspace (uqlb_batch_workspace_bytes counts them all): CHANNEL samples on
+ *     CLUSTER where they fit (taken in order of size while the group's largest width and height
+ *     fit), the other CHANNEL samples on ONE_STEP, periodic samples of each width the strips take on
+ *     the strips, wider periodic samples on TWO_STEP_TILES.  Outputs keep the caller's rows.
+ *     uqlb_last_run_geometry then reports UQLB_SCHEME_GROUPED.
  * A resumed run (start_step > 0) continues the state on any multi-step kernel (the strips and the
  * tiles, with two or three steps per launch, leave the same lattice layout); a one-step run resumes
- * on the one-step scheme only. */
+ * on the one-step scheme only, a cluster run on the cluster scheme (it leaves the natural layout). */
 enum {
     UQLB_SCHEME_AUTO = 0,
     UQLB_SCHEME_ONE_STEP = 1,

@@ -43,7 +43,8 @@ struct KParams {
     int32_t stochastic;  // 16-bit storage: stochastic rounding of every population store
     int32_t spl;         // time steps per launch of the multi-step schemes (2 or 3)
     int32_t natural;     // the lattice holds the state in natural layout (cluster runs; finalize reads it so)
-    int32_t cluster_size, cluster_cw, cluster_ny;  // cluster runs: blocks per cluster, columns per block, rows
+    // cluster runs: blocks per cluster, the widest sample's columns per block, the most rows
+    int32_t cluster_size, cluster_cw, cluster_ny;
     // outputs
     void* fields;
     int64_t fields_ld;

@@ -2109,21 +2109,27 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
 // Channel samples held on chip: one thread-block cluster per sample runs its whole time loop.
 // ------------------------------------------------------------------------------------------
 // The C blocks of a cluster split the sample's columns into C slabs of cw columns; each block keeps
-// its slab's populations twice in shared memory (the state at t and at t + 1, natural layout
-// [9][ny][cw] of the storage type), so HBM is touched only to load the state at the start and to
-// write it back at the end.  A step is the one-step kernel's push form: every fluid node reads its
-// own nine populations, collides them (BGK, the same formulas), and writes each post-collision
-// population into the neighbour it streams to, or applies the boundary rule of its link there
-// (halfway bounce-back on walls and obstacle, moving-wall inlet, pressure outlet with the node's own
-// velocity).  Populations that cross into a neighbouring slab are stored into that block's shared
-// memory (distributed shared memory of the cluster).  The cluster synchronises once per step with the
-// hardware cluster barrier, which every thread of every block reaches at every step (the step loop
-// and the stop decision are uniform over the cluster), so no wait depends on a flag.  Link classes of
-// every node are precomputed once into shared memory (3 bits per direction).
-// Forces at the QoI steps: block sums in shared memory, added by block 0 in rank order; block 0
-// records C_D and C_L and takes the steady-state decision, which every block reads after a second
-// barrier.  Samples with the Bouzidi obstacle or the interpolated inlet/outlet take the one-step
-// kernel instead.
+// its slab's populations once in shared memory ([9][ny][cw] of the storage type), so HBM is touched
+// only to load the state at the start and to write it back at the end.  The steps alternate the
+// two halves of the in-place AA order, counted from the run's first step: an even step reads a
+// node's own nine slots, collides (BGK, the one-step kernel's formulas) and writes each
+// post-collision population g*_i back into the node's own slot opp(i), already replaced by its
+// boundary rule where link i meets a wall, the obstacle, the inlet or the outlet (halfway
+// bounce-back, moving-wall inlet, pressure outlet with the node's own velocity); an odd step reads
+// g*_i of every neighbour x - c_i from its slot opp(i) (its own slot i across a boundary link),
+// collides, and writes g*_i into slot i of the neighbour x + c_i (its own slot opp(i), after the
+// boundary rule, across a boundary link), so the state is back in natural layout.  A node reads and
+// writes the same slots within a step, so no step needs a second copy.  Slots of a neighbouring slab
+// are read and written in that block's shared memory (distributed shared memory of the cluster), at
+// odd steps only.  The cluster synchronises once per step with the hardware cluster barrier, which
+// every thread of every block reaches at every step (the step loop and the stop decision are uniform
+// over the cluster), so no wait depends on a flag.  Link classes of every node are precomputed once
+// into shared memory (3 bits per direction), and the fluid nodes listed by the path they take.
+// The values equal the one-step kernel's: the same collisions, the same boundary rules, applied at
+// the step of the collision.  Forces at the QoI steps: block sums in shared memory, added by block 0
+// in rank order; block 0 records C_D and C_L and takes the steady-state decision, which every block
+// reads after a second barrier.  Samples with the Bouzidi obstacle or the interpolated inlet/outlet
+// take the one-step kernel instead.
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -2142,7 +2148,52 @@ __device__ __forceinline__ unsigned cluster_id_x() {
     asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
     return r;
 }
-constexpr int kClusterThreads = 512;
+constexpr int kClusterThreads = 1024;
+// Fixed part of a cluster step's time, in node updates of one block (see launch_cluster_any).
+constexpr double kClusterStepFixed = 3400.0;
+
+// Exclusive block-wide prefix sums of v[0..N) over the threads in index order (every thread of the
+// block calls it); the totals into tot.  sm: N values per warp.
+template <int N>
+__device__ __forceinline__ void block_scan(int (&v)[N], int (&tot)[N], int (*sm)[N]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int in[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) in[c] = v[c];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            const int u = __shfl_up_sync(0xFFFFFFFFu, in[c], d);
+            if (lane >= d) in[c] += u;
+        }
+    if (lane == 31)
+#pragma unroll
+        for (int c = 0; c < N; ++c) sm[w][c] = in[c];
+    __syncthreads();
+    if (w == 0) {
+        int x[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) x[c] = lane < nw ? sm[lane][c] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                const int u = __shfl_up_sync(0xFFFFFFFFu, x[c], d);
+                if (lane >= d) x[c] += u;
+            }
+        if (lane < nw)
+#pragma unroll
+            for (int c = 0; c < N; ++c) sm[lane][c] = x[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        tot[c] = sm[nw - 1][c];
+        v[c] = (w > 0 ? sm[w - 1][c] : 0) + in[c] - v[c];
+    }
+    __syncthreads();
+}
 
 // 32-bit shared::cluster address of a shared-memory location of this block, in block `rank`.
 __device__ __forceinline__ uint32_t cluster_addr(const void* p, unsigned rank) {
@@ -2158,6 +2209,20 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, S v) {
         asm volatile("st.shared::cluster.b16 [%0], %1;" ::"r"(addr), "h"(*reinterpret_cast<unsigned short*>(&v)) : "memory");
     }
 }
+template <typename S>
+__device__ __forceinline__ S ld_cluster(uint32_t addr) {
+    S v;
+    if constexpr (sizeof(S) == 4) {
+        uint32_t r;
+        asm volatile("ld.shared::cluster.b32 %0, [%1];" : "=r"(r) : "r"(addr) : "memory");
+        v = *reinterpret_cast<S*>(&r);
+    } else {
+        unsigned short r;
+        asm volatile("ld.shared::cluster.b16 %0, [%1];" : "=h"(r) : "r"(addr) : "memory");
+        v = *reinterpret_cast<S*>(&r);
+    }
+    return v;
+}
 __device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
     double v;
     asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
@@ -2169,6 +2234,11 @@ __device__ __forceinline__ int ld_cluster_s32(uint32_t addr) {
     return v;
 }
 
+// Bytes of one slab state in a cluster block, rounded up to 16 (the link words follow it).
+__host__ __device__ constexpr size_t cluster_state_bytes(int cw, int ny, int eb) {
+    return ((size_t)9 * cw * ny * eb + 15) / 16 * 16;
+}
+
 template <typename S>
 __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) {
     extern __shared__ __align__(16) unsigned char s6_raw[];
@@ -2176,6 +2246,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     __shared__ double s_red[(kClusterThreads / 32) * 2];
     __shared__ double s_force[2];   // this block's force partial of the step (read by block 0)
     __shared__ int s_stop;          // block 0: 1 once the sample stops
+    __shared__ int s_scan[kClusterThreads / 32][4];
     using C = typename Storage<S>::C;
     const int tid = threadIdx.x;
     const unsigned rank = cluster_rank(), nrank = cluster_size();
@@ -2184,11 +2255,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     if (tid == 0) s_stop = 0;
     __syncthreads();
     const SampleDev& sp = s_sp;
-    const int nx = sp.nx, ny = sp.ny, cw = p.cluster_cw;
+    // the sample's columns over the cluster's blocks (a sample narrower than the widest of the
+    // launch takes narrower slabs; the shared memory is sized for the widest)
+    const int nx = sp.nx, ny = sp.ny, cw = (nx + (int)nrank - 1) / (int)nrank;
     const int x0 = (int)rank * cw, ncol = max(0, min(cw, nx - x0));  // this block's columns [x0, x0 + ncol)
     const int pl = ny * cw;                                           // one population plane of a slab
-    S* const lat = reinterpret_cast<S*>(s6_raw);                      // two states: [2][9][ny][cw]
-    uint32_t* const links = reinterpret_cast<uint32_t*>(lat + 18 * pl);  // [ny][cw] link classes
+    S* const lat = reinterpret_cast<S*>(s6_raw);                      // the state: [9][ny][cw]
+    uint32_t* const links =
+        reinterpret_cast<uint32_t*>(s6_raw + cluster_state_bytes(cw, ny, (int)sizeof(S)));  // [ny][cw]
+    uint32_t* const list = links + pl;  // the fluid nodes, (y << 16) | column, grouped by path
     const typename Storage<S>::Q qz = quanta_of<S>(p, j);
     const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
     S* glob = static_cast<S*>(p.arena) + sp.f_off;
@@ -2208,48 +2283,123 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         } else {
 #pragma unroll
             for (int i = 1; i < 9; ++i) w |= (uint32_t)classify(sp, mask, x + cx(i), y + cy(i)) << (3 * i);
+            // bit 0 (no direction uses bits 0..2): a node whose neighbours lie partly in another slab
+            if (lx == 0 || lx == ncol - 1) w |= 1u;
         }
         links[y * cw + lx] = w;
     }
-    // shared::cluster addresses of the two states in the neighbouring blocks (same layout everywhere)
+    // shared::cluster addresses of the neighbouring blocks' states (same layout everywhere)
     const unsigned left = rank > 0 ? rank - 1 : rank, right = rank + 1 < nrank ? rank + 1 : rank;
-    const uint32_t left0 = cluster_addr(lat, left), right0 = cluster_addr(lat, right);
-    const uint32_t state_bytes = 9u * (uint32_t)pl * (uint32_t)sizeof(S);
+    const uint32_t nl = cluster_addr(lat, left), nr = cluster_addr(lat, right);
     cluster_sync_all();
     const C omega = (C)sp.omega;
     const bool sr = sizeof(S) == 2 && p.stochastic != 0;
     const uint32_t sid = (uint32_t)sp.sample_id;
-    // each thread walks the same owned nodes at every step: node tid, tid + T, ... of the slab in
-    // row-major order, stepped without divisions
+    // The fluid nodes in four lists, each in row-major order: boundary nodes (a link that is not
+    // interior: boundary rules), interior nodes at the slab's left and at its right edge (three
+    // neighbours in the next slab) and the rest (every neighbour in this slab), so that a warp
+    // seldom mixes two paths.  Each thread takes a contiguous run of nodes and a block-wide scan
+    // places its entries: the lists, and with them every thread's force partial, are the same at
+    // every run.
     const int nnodes = ny * ncol;
-    const int walk_r = ncol > 0 ? kClusterThreads / ncol : 0, walk_c = ncol > 0 ? kClusterThreads % ncol : 0;
-    const int ystart = ncol > 0 ? tid / ncol : 0, lxstart = ncol > 0 ? tid % ncol : 0;
-    int cur_off = 0;  // state at t: lat + cur_off; next state at lat + 9 pl - cur_off
+    int nk[4];  // list lengths
+    {
+        // list of a node from its link word (a one-column slab has both edges: boundary path)
+        auto kind = [&](uint32_t w, int lx) {
+            return w == 0xFFFFFFFFu ? -1 : (w == 0u ? 3 : (w == 1u && ncol > 1 ? (lx == 0 ? 1 : 2) : 0));
+        };
+        const int chunk = (nnodes + kClusterThreads - 1) / kClusterThreads;
+        const int c0 = min(nnodes, tid * chunk), c1 = min(nnodes, c0 + chunk);
+        int off[4] = {0, 0, 0, 0};
+        for (int n = c0; n < c1; ++n) {
+            const int y = n / ncol, lx = n - y * ncol, k = kind(links[y * cw + lx], lx);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) off[c] += k == c;
+        }
+        block_scan<4>(off, nk, s_scan);
+        int base[4];
+        base[0] = 0;
+#pragma unroll
+        for (int c = 1; c < 4; ++c) base[c] = base[c - 1] + nk[c - 1];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) off[c] += base[c];
+        for (int n = c0; n < c1; ++n) {
+            const int y = n / ncol, lx = n - y * ncol, k = kind(links[y * cw + lx], lx);
+            const uint32_t e = ((uint32_t)y << 16) | (uint32_t)lx;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (k == c) list[off[c]++] = e;
+        }
+        __syncthreads();
+    }
+    // list boundaries: [0, e0) boundary, [e0, e1) left edge, [e1, e2) right edge, [e2, e3) inner
+    const int e0 = nk[0], e1 = e0 + nk[1], e2 = e1 + nk[2], e3 = e2 + nk[3];
+    // shared::cluster address of slot i of row y in the left (column cw - 1) or right (column 0)
+    // neighbouring slab
+    auto remote = [&](bool to_left, int i, int y) {
+        return to_left ? nl + (uint32_t)(i * pl + y * cw + cw - 1) * (uint32_t)sizeof(S)
+                       : nr + (uint32_t)(i * pl + y * cw) * (uint32_t)sizeof(S);
+    };
+    // the incoming populations (stored values) of list entry k at an odd step: g*_i of the neighbour
+    // x - c_i from its slot opp(i), or the node's own slot i across a boundary link (written there by
+    // the even step)
+    auto gather_odd = [&](int k, int yn, int xn, int own, uint32_t lw, S (&v)[9]) {
+        v[0] = lat[own];
+        if (k >= e2) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) v[i] = lat[opp(i) * pl + own - cy(i) * cw - cx(i)];
+        } else if (k >= e0) {
+            const bool at_left = k < e1;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if (at_left ? cx(i) > 0 : cx(i) < 0)
+                    v[i] = ld_cluster<S>(remote(at_left, opp(i), yn - cy(i)));
+                else
+                    v[i] = lat[opp(i) * pl + own - cy(i) * cw - cx(i)];
+            }
+        } else {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int sl = xn - cx(i), sy = yn - cy(i);
+                if (((lw >> (3 * opp(i))) & 7u) != kInterior)
+                    v[i] = lat[i * pl + own];
+                else if (sl < 0 || sl >= ncol)
+                    v[i] = ld_cluster<S>(remote(sl < 0, opp(i), sy));
+                else
+                    v[i] = lat[opp(i) * pl + sy * cw + sl];
+            }
+        }
+    };
     int t = t0;
     for (; t < T && !skip; ++t) {
+        const bool odd = ((t - t0) & 1) != 0;
         const bool f_step = p.qoi_every > 0 && ((t + 1) % p.qoi_every) == 0;
-        const S* cur = lat + cur_off;
-        S* nxt = lat + (9 * pl - cur_off);
-        // the neighbours' next states (shared::cluster addresses)
-        const uint32_t nl = left0 + (cur_off == 0 ? state_bytes : 0u), nr = right0 + (cur_off == 0 ? state_bytes : 0u);
         double fx = 0.0, fy = 0.0;
-        int y = ystart, lx = lxstart;
-        for (int n = tid; n < nnodes; n += kClusterThreads) {
-            const int yn = y, xn = lx;
-            lx += walk_c;
-            y += walk_r + (lx >= ncol ? 1 : 0);
-            lx -= lx >= ncol ? ncol : 0;
-            const int own = yn * cw + xn;
-            const uint32_t lw = links[own];
-            if (lw == 0xFFFFFFFFu) continue;  // solid
-            const int x = x0 + xn;
+        // work units of 32 list entries, one per lane: warp w takes unit w in the first round and unit
+        // 32 r + 31 - w in round r >= 1.  The lists start with the costlier boundary and edge nodes,
+        // so the warps that took those in the first round take no unit of a last, partial round.
+        const int lane = tid & 31, wid = tid >> 5;
+        constexpr int NW = kClusterThreads / 32;
+        for (int r = 0; r * NW * 32 < e3; ++r) {
+            const int k = (r * NW + (r == 0 ? wid : NW - 1 - wid)) * 32 + lane;
+            if (k >= e3) continue;
+            const uint32_t e = list[k];
+            const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
+            const uint32_t lw = k < e0 ? links[own] : 0u;
             C g[9];
+            if (odd) {
+                S v[9];
+                gather_odd(k, yn, xn, own, lw, v);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(cur + i * pl + own, qz, i);
+                for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(v + i, qz, i);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + i * pl + own, qz, i);
+            }
             C drho, jx, jy, ux, uy;
             moments(g, drho, jx, jy, ux, uy);
             bgk(g, omega, drho, jx, jy, ux, uy);
-            const uint32_t h = sr ? mix32((uint32_t)((int64_t)yn * sp.pitch + x) * 0x9E3779B1u +
+            const uint32_t h = sr ? mix32((uint32_t)((int64_t)yn * sp.pitch + x0 + xn) * 0x9E3779B1u +
                                           (uint32_t)t * 0x85EBCA77u + sid * 0xC2B2AE3Du)
                                   : 0u;
             // the stored value of population i (rounded as the storage rounds)
@@ -2261,23 +2411,40 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                     Storage<S>::store(&r, v, qz, i);
                 return r;
             };
-            nxt[own] = cvt(g[0], 0);
+            if (k >= e0) {
+                // every link interior: even steps write g*_i into the node's slot opp(i), odd steps
+                // into slot i of the neighbour x + c_i (across the slab's edge for the three
+                // populations of an edge node that leave it)
+                lat[own] = cvt(g[0], 0);
+                const bool edge = k < e2, at_left = k < e1;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    if (!odd)
+                        lat[opp(i) * pl + own] = cvt(g[i], i);
+                    else if (edge && (at_left ? cx(i) < 0 : cx(i) > 0))
+                        st_cluster<S>(remote(at_left, i, yn + cy(i)), cvt(g[i], i));
+                    else
+                        lat[i * pl + own + cy(i) * cw + cx(i)] = cvt(g[i], i);
+                }
+                continue;
+            }
+            lat[own] = cvt(g[0], 0);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const int cls = (lw >> (3 * i)) & 7;
                 const int o = opp(i);
                 if (cls == kInterior) {
-                    const int dl = xn + cx(i), dy = yn + cy(i);
-                    if (dl >= 0 && dl < ncol) {
-                        nxt[i * pl + dy * cw + dl] = cvt(g[i], i);
+                    if (!odd) {
+                        lat[o * pl + own] = cvt(g[i], i);
                     } else {
-                        // into the neighbouring slab: its column cw - 1 (left) or 0 (right)
-                        const uint32_t at = (dl < 0 ? nl + (uint32_t)(i * pl + dy * cw + cw - 1) * (uint32_t)sizeof(S)
-                                                    : nr + (uint32_t)(i * pl + dy * cw) * (uint32_t)sizeof(S));
-                        st_cluster<S>(at, cvt(g[i], i));
+                        const int dl = xn + cx(i), dy = yn + cy(i);
+                        if (dl >= 0 && dl < ncol)
+                            lat[i * pl + dy * cw + dl] = cvt(g[i], i);
+                        else
+                            st_cluster<S>(remote(dl < 0, i, dy), cvt(g[i], i));
                     }
                 } else if (cls == kWall || cls == kSolid) {
-                    nxt[o * pl + own] = cvt(g[i], i);
+                    lat[o * pl + own] = cvt(g[i], i);
                     if (f_step && cls == kSolid) {
                         const C fs = g[i] + wgt<C>(i);
                         fx += (double)(C(2 * cx(i)) * fs);
@@ -2285,10 +2452,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                     }
                 } else if (cls == kInlet) {
                     const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
-                    nxt[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
+                    lat[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
                 } else {
                     const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                    nxt[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
+                    lat[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
                 }
             }
         }
@@ -2300,8 +2467,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                 s_force[1] = v[1];
             }
         }
-        cluster_sync_all();  // the next state is complete in every block (and this state is no longer read)
-        cur_off = 9 * pl - cur_off;
+        cluster_sync_all();  // the step is complete in every block
         if (f_step) {
             if (rank == 0 && tid == 0) {
                 double F[2] = {0.0, 0.0};
@@ -2320,14 +2486,34 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
             }
         }
     }
-    // the state at the last step run back to the arena (natural layout)
+    // the state at the last step run back to the arena in natural layout: after an odd number of
+    // steps the slots hold the post-collision values of an even step, so each fluid node gathers its
+    // incoming populations as an odd step would
     if (!skip) {
-        const S* cur = lat + cur_off;
-        for (int n = tid; n < ny * ncol; n += kClusterThreads) {
-            const int y = n / ncol, lx = n - y * ncol, x = x0 + lx;
-            const int64_t own = (int64_t)y * sp.pitch + x;
+        if (((t - t0) & 1) != 0) {
+            for (int k = tid; k < e3; k += kClusterThreads) {
+                const uint32_t e = list[k];
+                const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
+                S v[9];
+                gather_odd(k, yn, xn, own, k < e0 ? links[own] : 0u, v);
+                const int64_t at = (int64_t)yn * sp.pitch + x0 + xn;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) glob[i * sp.plane + own] = cur[i * pl + y * cw + lx];
+                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = v[i];
+            }
+            for (int n = tid; n < ny * ncol; n += kClusterThreads) {
+                const int y = n / ncol, lx = n - y * ncol;
+                if (links[y * cw + lx] != 0xFFFFFFFFu) continue;
+                const int64_t at = (int64_t)y * sp.pitch + x0 + lx;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = lat[i * pl + y * cw + lx];
+            }
+        } else {
+            for (int n = tid; n < ny * ncol; n += kClusterThreads) {
+                const int y = n / ncol, lx = n - y * ncol;
+                const int64_t at = (int64_t)y * sp.pitch + x0 + lx;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = lat[i * pl + y * cw + lx];
+            }
         }
         if (rank == 0 && tid == 0 && !p.done[sp.slot]) p.steps_run[sp.slot] = t;
     }
@@ -2336,7 +2522,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
 
 template <typename S>
 size_t cluster_smem(int cw, int ny) {
-    return (size_t)18 * cw * ny * sizeof(S) + (size_t)cw * ny * sizeof(uint32_t);
+    return cluster_state_bytes(cw, ny, (int)sizeof(S)) + (size_t)2 * cw * ny * sizeof(uint32_t);  // state, links, list
 }
 
 template <typename S>
@@ -2369,6 +2555,11 @@ cudaError_t launch_cluster_s(const KParams& p, const BatchGeometry& g, cudaStrea
 // Clusters of `csize` blocks with `smem` bytes each that can run at once (0: none).
 template <typename S>
 int cluster_capacity(int csize, size_t smem) {
+    static struct {
+        size_t smem;
+        int cap;
+    } cache[17] = {};
+    if (cache[csize].smem == smem && smem != 0) return cache[csize].cap;
     cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
     cudaLaunchConfig_t cfg{};
@@ -2385,8 +2576,10 @@ int cluster_capacity(int csize, size_t smem) {
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel<S>, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        return 0;
+        n = 0;
     }
+    cache[csize].smem = smem;
+    cache[csize].cap = n;
     return n;
 }
 
@@ -3113,20 +3306,23 @@ cudaError_t launch_cluster_any(const KParams& p, const BatchGeometry& g, cudaStr
         return cudaErrorInvalidConfiguration;  // FP64 lattices do not fit a cluster's shared memory
     } else {
         // cluster size: every size of 1..16 whose blocks hold the widest sample's slab; among them the
-        // one that keeps the most SMs busy (clusters that run at once x blocks per cluster), smaller
-        // clusters on ties
+        // one with the least estimated time, waves of clusters (the samples over the clusters that
+        // run at once) x the time of a step, which is latency-bound: about that of kClusterStepFixed
+        // node updates plus one per node of a block's slab (measured on 220 x 41 to 440 x 82
+        // channels: 3.3 us + 1 ns per node of the slab).  Larger clusters on ties.
         KParams q = p;
         int best_c = 0, best_cw = 0;
-        int64_t best_units = 0;
-        for (int c = 1; c <= 16; c *= 2) {
+        double best_cost = 0.0;
+        for (int c = 16; c >= 1; --c) {
             const int cw = (g.cluster_nx + c - 1) / c;
             const size_t smem = cluster_smem<S>(cw, g.cluster_ny);
             if (smem > 227 * 1024 - 4096) continue;
             const int cap = cluster_capacity<S>(c, smem);
             if (cap < 1) continue;
-            const int64_t units = std::min<int64_t>(cap, g.nsamples) * c;
-            if (units > best_units) {
-                best_units = units;
+            const double waves = (double)((g.nsamples + cap - 1) / cap);
+            const double cost = waves * (kClusterStepFixed + (double)cw * g.cluster_ny);
+            if (best_c == 0 || cost < best_cost) {
+                best_cost = cost;
                 best_c = c;
                 best_cw = cw;
             }

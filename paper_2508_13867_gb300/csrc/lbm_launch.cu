@@ -102,6 +102,17 @@ bool strip3_supported(int storage, int nx) {
     return rw <= (storage == UQLB_F32 ? Strip3Tune<float>::max_nx : Strip3Tune<__half>::max_nx);
 }
 
+bool cluster_fits(int storage, int nx, int ny) {
+    if (storage == UQLB_F64 || nx < 1 || ny < 1) return false;
+    const size_t eb = storage == UQLB_F32 ? 4 : 2;
+    for (int c = 1; c <= 16; ++c) {
+        const int cw = (nx + c - 1) / c;
+        const size_t smem = (9 * (size_t)cw * ny * eb + 15) / 16 * 16 + 2 * (size_t)cw * ny * sizeof(uint32_t);
+        if (smem <= 227 * 1024 - 4096) return true;
+    }
+    return false;
+}
+
 bool strip3_blocks(const BatchGeometry& g, int stage, int* max_b, int* def_b, int* def_kb, int* per_block) {
     StripBlocks b{};
     if (!ops_of(g.storage).strip3_blocks(g, stage, &b)) return false;

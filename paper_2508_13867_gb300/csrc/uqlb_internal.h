@@ -161,6 +161,9 @@ bool geometry_supported2(int storage, int tile_rows, int npt);  // two-step sche
 bool strip_supported(int storage, int nx);
 // Three-step row strips: FP32 rows up to 1280 wide, 16-bit up to 1600 (rounded up to 64 columns).
 bool strip3_supported(int storage, int nx);
+// Whether a cluster run holds a channel sample of nx x ny nodes (its lattice once in the shared
+// memory of at most 16 blocks, with the link words and the node lists); host arithmetic only.
+bool cluster_fits(int storage, int nx, int ny);
 // Widths of the three-step strips with a compile-time instantiation (immediate addressing, and a
 // staging option per launch).
 #ifndef UQLB_STRIP3_FIXED_WIDTHS

@@ -686,20 +686,26 @@ def _grouped_specs():
 
 def test_grouped_batch_matches_the_single_one_step_batch(ens):
     """A batch of unlike samples under the auto scheme runs as groups of like samples, one after
-    another in slices of one workspace: channel samples on the one-step kernel, each periodic
-    width on the row strips (64 and 128 fill their blocks, 40 and 96 leave threads past the row).
-    Every output row stays the caller's.  Against the same batch run as one one-step batch the
-    channel rows are equal bit for bit (the same kernel, tiles and reduction order) and the
-    periodic rows agree to FP32 round-off."""
+    another in slices of one workspace: channel samples on clusters, each periodic width on the row
+    strips (64 and 128 fill their blocks, 40 and 96 leave threads past the row).  Every output row
+    stays the caller's.  Against the same batch run as one one-step batch the channel rows' final
+    state is equal bit for bit (mass, momentum and steps from the same fields; C_D and C_L sum the
+    same link forces in another order, FP32 round-off) and the periodic rows agree to FP32
+    round-off."""
     specs = _grouped_specs()
     a = _run(ens, specs, "f32", qoi_every=7, series=True)
     assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_GROUPED
     b = _run(ens, specs, "f32", qoi_every=7, series=True, scheme="one_step")
     assert U.uqlb_last_run_geometry(ens.ctx)[0] == U.UQLB_SCHEME_ONE_STEP
+    exact = [U.UQLB_QOI_MASS, U.UQLB_QOI_MOMX, U.UQLB_QOI_STEPS, U.UQLB_QOI_STATUS]
     for i, sp in enumerate(specs):
         if sp.kind == W.CHANNEL:
-            assert np.array_equal(a["qoi"][i], b["qoi"][i], equal_nan=True), i
-            assert np.array_equal(a["series"][i], b["series"][i], equal_nan=True), i
+            assert np.array_equal(a["qoi"][i, exact], b["qoi"][i, exact], equal_nan=True), i
+            # C_D sums some twenty FP32 link forces of size ~0.1 scaled by 2 / (U^2 D) ~ 300 at this
+            # resolution: FP32 round-off of the sum is a few 1e-5 in C_D units, large against the C_D
+            # of the first steps
+            assert np.allclose(a["qoi"][i], b["qoi"][i], rtol=1e-5, atol=2e-4, equal_nan=True), i
+            assert np.allclose(a["series"][i], b["series"][i], rtol=1e-5, atol=2e-4, equal_nan=True), i
         else:
             assert a["qoi"][i, U.UQLB_QOI_STEPS] == sp.steps
             assert np.allclose(a["qoi"][i], b["qoi"][i], rtol=1e-5, atol=1e-5, equal_nan=True), i
@@ -1037,6 +1043,11 @@ def test_autotune_tunes_the_three_step_strips(ens):
         assert c["strip_stage"] in (1, 2) and c["strip_blocks_per_sm"] >= 1 and c["strip_smem_kb"] in configs
         assert c["ms_per_step"] > 0
     assert {c["strip_stage"] for c in cands} == {1, 2}
+    for stage in (1, 2):
+        # the most blocks per SM of each staging option is tried at the largest share too
+        most = max(c["strip_blocks_per_sm"] for c in cands if c["strip_stage"] == stage)
+        assert any(c["strip_stage"] == stage and c["strip_blocks_per_sm"] == most and c["strip_smem_kb"] == 228
+                   for c in cands), stage
     best = cands[res["chosen"]]
     assert best["ms_per_step"] == min(c["ms_per_step"] for c in cands)
     assert len(res["tried"]) == min(len(cands), 16)

@@ -38,7 +38,7 @@ STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in plac
                     "and collided again, pushed to the other lattice)", "strip2_kernel", "two-step-strips-v2-staged"),
                 6: ("strip3w_kernel (three-step row strips at a compile-time width: each row collided into a "
                     "first shared-memory ring, streamed and collided into a second, streamed and collided again, "
-                    "pushed to the other lattice)", "strip3w_kernel", "three-step-strips-fixed-width-v1")}
+                    "pushed to the other lattice)", "strip3w_kernel", "three-step-strips-fixed-width-v2")}
 STEPS_PER_LAUNCH = {1: 1, 3: 2, 4: 2, 6: 3, 7: 1}
 
 

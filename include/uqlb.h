@@ -511,8 +511,9 @@ int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, 
  * matrix W is staged in a fixed device array inside the library (1 MiB, K x S <= 131072
  * weights; larger sample sets return UQLB_ERR_ARG and need uqlb_project).  No device memory is
  * allocated or freed.  The array exists once per GPU that loads the library and stays until
- * the process exits.  The first call on a device looks up the array's device address, so make
- * that first call before capturing a stream.  The library keeps that address for the life of the
+ * the process exits.  The weights are copied from the context's host memory (pageable) on the
+ * stream, so neither this call nor uqlb_project can be captured into a CUDA graph.  The first call
+ * on a device looks up the array's device address.  The library keeps that address for the life of the
  * process: it must not outlive a reset of the device (cudaDeviceReset), which would leave the kept
  * address pointing at memory that no longer holds the array.  All calls share the one array: calls that
  * overlap on the GPU (e.g. on two streams) race and must be ordered by the caller.  Each call

@@ -38,7 +38,7 @@ STEP_KERNELS = {1: ("step_kernel (one-step: fused AA collide-stream-QoI, in plac
                     "and collided again, pushed to the other lattice)", "strip2_kernel", "two-step-strips-v2-staged"),
                 6: ("strip3w_kernel (three-step row strips at a compile-time width: each row collided into a "
                     "first shared-memory ring, streamed and collided into a second, streamed and collided again, "
-                    "pushed to the other lattice)", "strip3w_kernel", "three-step-strips-fixed-width-v2")}
+                    "pushed to the other lattice)", "strip3w_kernel", "three-step-strips-fixed-width-v3")}
 STEPS_PER_LAUNCH = {1: 1, 3: 2, 4: 2, 6: 3, 7: 1}
 
 
@@ -274,13 +274,13 @@ def bench_kernel_only(args):
 def tune_summary(tuned):
     """The autotuner's candidates as labels with their ms per step: tile geometries "rows x npt", and on
     the three-step strips "<staging>/<blocks per SM>b/<shared-memory KB>k" (staging "s0": none, "s1": one
-    row, "g": the generic-width kernel)."""
+    row in shared memory, "r1": one row in registers, "g": the generic-width kernel)."""
     if tuned is None:
         return None
 
     def label(c):
         if c["strip_blocks_per_sm"] > 0:
-            st = {0: "g", 1: "s0", 2: "s1"}[c["strip_stage"]]
+            st = {0: "g", 1: "s0", 2: "s1", 3: "r1"}[c["strip_stage"]]
             return f"{st}/{c['strip_blocks_per_sm']}b/{c['strip_smem_kb']}k"
         return f"{c['tile_rows']}x{c['nodes_per_thread']}"
 
@@ -853,7 +853,8 @@ def main():
     ap.add_argument("--kernel-case", default="tgv", choices=["tgv", "cylinder"],
                     help="kernel-only: the 4-D Taylor-Green samples or channel samples of the cylinder workload (--nd)")
     ap.add_argument("--strip", default="0,0,0",
-                    help="kernel-only: three-step strips' blocks per SM, staging option (1: none, 2: one row) and "
+                    help="kernel-only: three-step strips' blocks per SM, staging option (1: none, 2: one row in shared memory, "
+                         "3: one row in registers) and "
                          "shared-memory KB (0: tuned or default)")
     ap.add_argument("--kernel-autotune", action="store_true",
                     help="kernel-only: run the autotuner (--tune-steps) first and report its candidates")

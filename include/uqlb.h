@@ -199,7 +199,8 @@ typedef struct {
                                     min(rows, blocks per SM x SMs) and each block takes an equal
                                     share of the rows) */
     int32_t strip_stage;      /* widths 64, 128, 256, 512, 1024: 1 = rows not staged, 2 = the next
-                                 row staged in shared memory by cp.async (other widths: 0 only) */
+                                 row staged in shared memory by cp.async, 3 = the next row loaded
+                                 into registers (other widths: 0 only) */
     int32_t strip_smem_kb;    /* shared-memory share per SM in KB: 8, 16, 32, 64, 100, 132, 164, 196
                                  or 228 (the rest of the 256 KB is L1); raised to what the blocks
                                  per SM need */

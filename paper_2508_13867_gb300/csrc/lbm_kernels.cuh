@@ -1044,32 +1044,48 @@ __device__ __forceinline__ int strip_plane(int i, int q) {
     }
 }
 
-// Two adjacent populations i (an even column and the next) as one packed pair.
+// Two adjacent populations i (an even column and the next) as one packed pair: the pair's stored
+// values as one register (PairRaw: two 16-bit values in a word, or two FP32 values) and their
+// conversion (pair_from_raw); pair_load reads the register from memory.
 template <typename S>
-__device__ __forceinline__ f2 pair_load(const S* ptr, const typename Storage<S>::Q& qz, int i);
+struct PairRawT {
+    using T = uint32_t;
+};
 template <>
-__device__ __forceinline__ f2 pair_load<float>(const float* ptr, const NoQuanta&, int) {
-    return *reinterpret_cast<const f2*>(ptr);
+struct PairRawT<float> {
+    using T = f2;
+};
+template <typename S>
+using PairRaw = typename PairRawT<S>::T;
+template <typename S>
+__device__ __forceinline__ f2 pair_from_raw(PairRaw<S> w, const typename Storage<S>::Q& qz, int i);
+template <>
+__device__ __forceinline__ f2 pair_from_raw<float>(f2 w, const NoQuanta&, int) {
+    return w;
 }
 template <>
-__device__ __forceinline__ f2 pair_load<__half>(const __half* ptr, const NoQuanta&, int) {
-    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(ptr));
+__device__ __forceinline__ f2 pair_from_raw<__half>(uint32_t w, const NoQuanta&, int) {
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
     return pk(v.x * 0x1p-12f, v.y * 0x1p-12f);
 }
 template <>
-__device__ __forceinline__ f2 pair_load<__nv_bfloat16>(const __nv_bfloat16* ptr, const NoQuanta&, int) {
-    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(ptr));
+__device__ __forceinline__ f2 pair_from_raw<__nv_bfloat16>(uint32_t w, const NoQuanta&, int) {
+    const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
     return pk(v.x, v.y);
 }
 template <>
-__device__ __forceinline__ f2 pair_load<int16_t>(const int16_t* ptr, const Quanta& qz, int i) {
+__device__ __forceinline__ f2 pair_from_raw<int16_t>(uint32_t w, const Quanta& qz, int i) {
     // each signed value plus 2^15 becomes the low mantissa bits of 2^23 (byte permutes, no integer
     // conversion); one packed subtraction of 2^23 + 2^15 gives the two integers exactly and one
     // packed multiply scales them: the same single rounding as (float)q * d
-    const uint32_t w = *reinterpret_cast<const uint32_t*>(ptr) ^ 0x80008000u;
+    w ^= 0x80008000u;
     const f2 biased = pk(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7610)),
                          __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7632)));
     return mul2(sub2(biased, splat(8421376.0f)), splat(qz.d[qclass(i)]));
+}
+template <typename S>
+__device__ __forceinline__ f2 pair_load(const S* ptr, const typename Storage<S>::Q& qz, int i) {
+    return pair_from_raw<S>(*reinterpret_cast<const PairRaw<S>*>(ptr), qz, i);
 }
 // Round-to-nearest store of a pair (each half rounded as Storage<S>::store does).
 template <typename S>
@@ -1771,15 +1787,18 @@ __global__ void __launch_bounds__(1024, 1) strip3_kernel(KParams p) {
 #ifndef UQLB_STRIP3W_THREADS_16
 #define UQLB_STRIP3W_THREADS_16 1024
 #endif
-template <typename S>
+// Register staging (D == 2) holds nine more words per thread: 16-bit storage then takes the budget of
+// 768 threads (85 registers; six blocks of 128 threads still fit), where 1024 would spill.
+template <typename S, int D>
 constexpr int strip3w_min_blocks(int np) {
-    constexpr int th = sizeof(S) == 4 ? UQLB_STRIP3W_THREADS_F32 : UQLB_STRIP3W_THREADS_16;
+    constexpr int th = sizeof(S) == 4 ? UQLB_STRIP3W_THREADS_F32 : (D == 2 ? 768 : UQLB_STRIP3W_THREADS_16);
     return th / np < 1 ? 1 : (th / np > 16 ? 16 : th / np);
 }
 
-// D: phase-A rows staged in shared memory ahead of their use (0 or 1).
+// D: staging of the phase-A rows ahead of their use: 0 none, 1 the next row in shared memory
+// (cp.async), 2 the next row in registers.
 template <typename S, int W, int D>
-__global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_kernel(KParams p) {
+__global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S, D>(W / 2)) strip3w_kernel(KParams p) {
     constexpr int NP = W / 2, RS = W + 4;
     extern __shared__ __align__(16) unsigned char s5_raw[];
     __shared__ __align__(16) SampleDev s_sp;
@@ -1788,7 +1807,7 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
     float* ring1 = reinterpret_cast<float*>(s5_raw);  // [kRing3Planes][RS]
     float* ring2 = ring1 + kRing3Planes * RS;
     double* s_red = reinterpret_cast<double*>(s5_raw);
-    S* stage = reinterpret_cast<S*>(ring2 + kRing3Planes * RS);  // [D][9][W]
+    S* stage = reinterpret_cast<S*>(ring2 + kRing3Planes * RS);  // D == 1: [9][W], the next phase-A row
     const int t = (int)p.step_counter[0] + p.dt;
     const int t0 = (int)p.step_counter[1];
     if (tid == 0) {
@@ -1999,22 +2018,38 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
             auto fetch = [&](int qa) {
                 if (a0 + qa <= yb + n - 2) {
                     const S* s0 = src + wrap(a0 + qa) * (9 * W);
-                    S* st = stage + (qa % (D > 0 ? D : 1)) * 9 * W + x;
+                    S* st = stage + x;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) cp_async<2 * sizeof(S)>(st + i * W, s0 + i * W);
                 }
                 cp_async_commit();
             };
             (void)fetch;
+            // D == 2: the next phase-A row's pairs are loaded into registers one row ahead, so their
+            // latency overlaps the rest of the row's work and its barriers
+            using Raw = PairRaw<S>;
+            Raw pre[9];
+            auto fetch_regs = [&](int row) {
+                if (row - a0 <= yb + n - 2 - a0) {
+                    const Raw* s0 = reinterpret_cast<const Raw*>(src + wrap(row) * (9 * W));
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) pre[i] = __ldg(s0 + i * (W / 2));
+                }
+            };
+            (void)fetch_regs;
             auto phase_a = [&](int row) {
                 const int qa = row - a0;
                 f2 g[9];
-                if constexpr (D > 0) {
-                    cp_async_wait<D - 1>();
-                    const S* st = stage + (qa % D) * 9 * W + x;
+                if constexpr (D == 1) {
+                    cp_async_wait<0>();
+                    const S* st = stage + x;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) g[i] = pair_load<S>(st + i * W, qz, i);
-                    fetch(qa + D);
+                    fetch(qa + 1);
+                } else if constexpr (D == 2) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = pair_from_raw<S>(pre[i], qz, i);
+                    fetch_regs(row + 1);
                 } else {
                     const S* s0 = src + wrap(row) * (9 * W);
 #pragma unroll
@@ -2026,8 +2061,8 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
                 if (w) add_usq(red[0], qq);
                 put_ring(r1t, row - ya + 4, g);
             };
-#pragma unroll
-            for (int k = 0; k < D; ++k) fetch(k);
+            if constexpr (D == 1) fetch(0);
+            if constexpr (D == 2) fetch_regs(a0);
             if (n == 3) {
                 phase_a(ya - 2);
                 phase_a(ya - 1);
@@ -2069,7 +2104,7 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S>(W / 2)) strip3w_k
                     __syncthreads();
                 }
             }
-            if constexpr (D > 0) cp_async_wait<0>();
+            if constexpr (D == 1) cp_async_wait<0>();
         }
         if (want[0] || want[1] || want[2]) {
             __syncthreads();
@@ -3185,7 +3220,8 @@ StripBlocks strip_blocks_of(K kernel, int threads, size_t dyn, int default_kb) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, dyn) != cudaSuccess || b < 1) b = 1;
     r.max_b = b;
     r.def_b = default_kb > 0 ? std::max(1, std::min(b, default_kb * 1024 / r.per_block)) : b;
-    r.def_kb = default_kb > 0 ? default_kb : 228;
+    // default_kb: the compiled share; 0: the largest; -1: the smallest holding the blocks
+    r.def_kb = default_kb > 0 ? default_kb : (default_kb < 0 ? smem_config_for((size_t)b * r.per_block) : 228);
     return r;
 }
 
@@ -3207,7 +3243,7 @@ const StripBlocks& strip3_generic_blocks(int nx) {
 
 template <typename S, int W, int D>
 size_t strip3w_smem() {
-    return (size_t)2 * kRing3Planes * (W + 4) * sizeof(float) + (size_t)D * 9 * W * sizeof(S);
+    return (size_t)2 * kRing3Planes * (W + 4) * sizeof(float) + (size_t)(D == 1 ? 1 : 0) * 9 * W * sizeof(S);
 }
 
 // Blocks per SM of the fixed-width three-step strips (once).
@@ -3216,24 +3252,44 @@ const StripBlocks& strip3w_blocks() {
     static const StripBlocks b = [] {
         cudaFuncSetAttribute(strip3w_kernel<S, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)strip3w_smem<S, W, D>());
-        return strip_blocks_of(strip3w_kernel<S, W, D>, W / 2, strip3w_smem<S, W, D>(), Strip3Tune<S>::carveout_kb);
+        // register staging: by default the most blocks that fit and the smallest share that holds
+        // them (the rest of the 256 KB as L1: FP32 4 blocks and 164 KB, 0.170 against 0.202 ms per
+        // step at 228 KB)
+        return strip_blocks_of(strip3w_kernel<S, W, D>, W / 2, strip3w_smem<S, W, D>(),
+                               D == 2 ? -1 : Strip3Tune<S>::carveout_kb);
     }();
     return b;
 }
 
-// Staging option of a fixed-width launch: 1 = no staged row, 2 = one (0: the compiled default).
-inline int strip3w_depth(int stage, int def) { return stage == 1 ? 0 : (stage == 2 ? 1 : def); }
+// Staging of a fixed-width launch's phase-A rows: option 1 = none, 2 = the next row in shared memory
+// by cp.async, 3 = the next row in registers (0: the compiled default); as the kernel's D: 0, 1, 2.
+// The default is register staging (measured on the 625 x 256^2 ensemble, kernel GLUPS, none / shared
+// memory / registers: FP32 206 / 229 / 242, BF16 219 / 218 / 235, FP16 214 / 215 / 231, FX16 200 / 199
+// / 216; `def`, the runtime-width kernel's compiled staging, is not used).
+inline int strip3w_depth(int stage, int def) {
+    (void)def;
+    return stage == 1 ? 0 : (stage == 2 ? 1 : 2);
+}
+
+template <typename S, int W, int D>
+cudaError_t launch_strip3w_d(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const StripBlocks& sb = strip3w_blocks<S, W, D>();
+    if (prepare_only) return cudaGetLastError();
+    return launch_strip_kernel(strip3w_kernel<S, W, D>, sb, g, W / 2, strip3w_smem<S, W, D>(), p, s);
+}
 
 template <typename S, int W>
 cudaError_t launch_strip3w(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
-    if (strip3w_depth(g.strip_stage, Strip3Tune<S>::depth) == 0) {
-        const StripBlocks& sb = strip3w_blocks<S, W, 0>();
-        if (prepare_only) return cudaGetLastError();
-        return launch_strip_kernel(strip3w_kernel<S, W, 0>, sb, g, W / 2, strip3w_smem<S, W, 0>(), p, s);
+    switch (strip3w_depth(g.strip_stage, Strip3Tune<S>::depth)) {
+        case 0: return launch_strip3w_d<S, W, 0>(p, g, s, prepare_only);
+        case 1: return launch_strip3w_d<S, W, 1>(p, g, s, prepare_only);
+        default: return launch_strip3w_d<S, W, 2>(p, g, s, prepare_only);
     }
-    const StripBlocks& sb = strip3w_blocks<S, W, 1>();
-    if (prepare_only) return cudaGetLastError();
-    return launch_strip_kernel(strip3w_kernel<S, W, 1>, sb, g, W / 2, strip3w_smem<S, W, 1>(), p, s);
+}
+
+template <typename S, int W>
+const StripBlocks& strip3w_blocks_at(int d) {
+    return d == 0 ? strip3w_blocks<S, W, 0>() : (d == 1 ? strip3w_blocks<S, W, 1>() : strip3w_blocks<S, W, 2>());
 }
 
 template <typename S>
@@ -3268,13 +3324,13 @@ bool strip3_blocks_s(const BatchGeometry& g, int stage, StripBlocks* out) {
         const int np = strip_threads(g.strip_nx);
         if (!g.strips || g.spl != 3 || g.strip_nx < 2 || 2 * np > Strip3Tune<S>::max_nx) return false;
         if (strip3_fixed_width(g.strip_nx)) {
-            const bool d0 = strip3w_depth(stage, Strip3Tune<S>::depth) == 0;
+            const int d = strip3w_depth(stage, Strip3Tune<S>::depth);
             switch (g.strip_nx) {
-                case 64: *out = d0 ? strip3w_blocks<S, 64, 0>() : strip3w_blocks<S, 64, 1>(); break;
-                case 128: *out = d0 ? strip3w_blocks<S, 128, 0>() : strip3w_blocks<S, 128, 1>(); break;
-                case 256: *out = d0 ? strip3w_blocks<S, 256, 0>() : strip3w_blocks<S, 256, 1>(); break;
-                case 512: *out = d0 ? strip3w_blocks<S, 512, 0>() : strip3w_blocks<S, 512, 1>(); break;
-                default: *out = d0 ? strip3w_blocks<S, 1024, 0>() : strip3w_blocks<S, 1024, 1>(); break;
+                case 64: *out = strip3w_blocks_at<S, 64>(d); break;
+                case 128: *out = strip3w_blocks_at<S, 128>(d); break;
+                case 256: *out = strip3w_blocks_at<S, 256>(d); break;
+                case 512: *out = strip3w_blocks_at<S, 512>(d); break;
+                default: *out = strip3w_blocks_at<S, 1024>(d); break;
             }
             return true;
         }

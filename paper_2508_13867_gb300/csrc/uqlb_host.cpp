@@ -713,8 +713,8 @@ int plan_batch(const uqlb_sample* smp, int64_t n, const uqlb_run_opts* o, BatchP
         const int sb = o ? o->strip_blocks_per_sm : 0, ss = o ? o->strip_stage : 0, sk = o ? o->strip_smem_kb : 0;
         bool kb_ok = sk == 0;
         for (int c : kSmemConfigsKB) kb_ok = kb_ok || (c > 0 && sk == c);
-        if (sb < 0 || sb > 32 || ss < 0 || ss > 2 || !kb_ok) {
-            why = "strip_blocks_per_sm must be 0..32, strip_stage 0..2 and strip_smem_kb 0 or a shared-memory "
+        if (sb < 0 || sb > 32 || ss < 0 || ss > 3 || !kb_ok) {
+            why = "strip_blocks_per_sm must be 0..32, strip_stage 0..3 and strip_smem_kb 0 or a shared-memory "
                   "configuration (8, 16, 32, 64, 100, 132, 164, 196, 228)";
             return UQLB_ERR_ARG;
         }
@@ -1461,7 +1461,7 @@ int uqlb_autotune(uqlb_ctx* ctx, const uqlb_sample* samples, int64_t n, const uq
             // staging option x blocks per SM (the most that fit and up to three fewer) x share (the
             // smallest holding the blocks, and the largest)
             const bool fixed = strip3_fixed_width(g0.strip_nx);
-            for (int stage : {fixed ? 2 : 0, fixed ? 1 : -1}) {
+            for (int stage : {fixed ? 2 : 0, fixed ? 1 : -1, fixed ? 3 : -1}) {
                 int max_b = 0, def_b = 0, def_kb = 0, per = 0;
                 if (stage < 0 || !strip3_blocks(g0, stage, &max_b, &def_b, &def_kb, &per)) continue;
                 for (int b = max_b; b >= std::max(1, max_b - 3); --b) {

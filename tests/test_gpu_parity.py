@@ -1012,7 +1012,7 @@ def test_three_step_strip_launch_shapes_agree(ens, storage, n, ny):
     if storage == "fx16":
         specs = [replace(s, ny=n) for s in specs]
     ref = _run(ens, specs, storage, qoi_every=4, series=True, scheme="three_step_strips")
-    stages = (1, 2) if n in (64, 128, 256, 512, 1024) else (0,)
+    stages = (1, 2, 3) if n in (64, 128, 256, 512, 1024) else (0,)
     for bps, kb in ((1, 0), (2, 228), (3, 100), (16, 0)):
         for stage in stages:
             got = _run(ens, specs, storage, qoi_every=4, series=True, scheme="three_step_strips",
@@ -1040,10 +1040,10 @@ def test_autotune_tunes_the_three_step_strips(ens):
     configs = {8, 16, 32, 64, 100, 132, 164, 196, 228}
     for c in cands:
         assert c["scheme"] == U.UQLB_SCHEME_THREE_STEP_STRIPS
-        assert c["strip_stage"] in (1, 2) and c["strip_blocks_per_sm"] >= 1 and c["strip_smem_kb"] in configs
+        assert c["strip_stage"] in (1, 2, 3) and c["strip_blocks_per_sm"] >= 1 and c["strip_smem_kb"] in configs
         assert c["ms_per_step"] > 0
-    assert {c["strip_stage"] for c in cands} == {1, 2}
-    for stage in (1, 2):
+    assert {c["strip_stage"] for c in cands} == {1, 2, 3}
+    for stage in (1, 2, 3):
         # the most blocks per SM of each staging option is tried at the largest share too
         most = max(c["strip_blocks_per_sm"] for c in cands if c["strip_stage"] == stage)
         assert any(c["strip_stage"] == stage and c["strip_blocks_per_sm"] == most and c["strip_smem_kb"] == 228

@@ -329,7 +329,7 @@ def test_scheme_selection_and_its_limits():
 
 
 def test_strip_launch_shape_options_are_checked():
-    """The three-step strips' launch-shape options: blocks per SM 0..32, staging option 0..2 (the
+    """The three-step strips' launch-shape options: blocks per SM 0..32, staging option 0..3 (the
     fixed widths only), shared-memory share 0 or one of the carveout configurations; none of them
     changes the workspace."""
     def opts(bps=0, stage=0, kb=0, scheme=U.UQLB_SCHEME_THREE_STEP_STRIPS):
@@ -338,12 +338,12 @@ def test_strip_launch_shape_options_are_checked():
     fixed = [sample_struct(W.tgv(256, 10))]
     ragged = [sample_struct(W.tgv(200, 10))]
     base = U.uqlb_batch_workspace_bytes(fixed, opts())
-    for bps, stage, kb in ((1, 1, 8), (4, 2, 196), (32, 0, 228), (0, 0, 100), (3, 2, 0)):
+    for bps, stage, kb in ((1, 1, 8), (4, 2, 196), (32, 0, 228), (0, 0, 100), (3, 2, 0), (6, 3, 228)):
         assert U.uqlb_batch_workspace_bytes(fixed, opts(bps, stage, kb)) == base
     assert U.uqlb_batch_workspace_bytes(ragged, opts(2, 0, 164)) > 0
-    for smp, o in ((fixed, opts(-1)), (fixed, opts(33)), (fixed, opts(0, 3)), (fixed, opts(0, -1)),
+    for smp, o in ((fixed, opts(-1)), (fixed, opts(33)), (fixed, opts(0, 4)), (fixed, opts(0, -1)),
                    (fixed, opts(0, 0, 50)), (fixed, opts(0, 0, 256)), (fixed, opts(0, 0, -8)),
-                   (ragged, opts(0, 1)), (ragged, opts(0, 2))):
+                   (ragged, opts(0, 1)), (ragged, opts(0, 2)), (ragged, opts(0, 3))):
         with pytest.raises(U.UqlbError) as e:
             U.uqlb_batch_workspace_bytes(smp, o)
         assert e.value.status == U.UQLB_ERR_ARG

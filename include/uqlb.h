@@ -245,8 +245,8 @@ typedef struct {
  *   UQLB_SCHEME_AUTO: the row strips for periodic FP32, FP16, BF16 and FX16 batches in graph mode,
  *     three steps per launch where the width allows it, else two, else TWO_STEP_TILES (measured on
  *     GB300, 625 x 256^2 ensemble, kernel GLUPS three-step strips / two-step strips / tiles /
- *     one-step: FP32 230 / 179 / 115 / 84, BF16 220 / 184 / 103 / 90, FP16 215 / 173 / 95 / 82,
- *     FX16 200 / 170 / - / -); CLUSTER for CHANNEL batches that allow it (FP32 9 x 440 x 82 cylinder
+ *     one-step: FP32 242 / 179 / 115 / 84, BF16 234 / 184 / 103 / 90, FP16 231 / 173 / 95 / 82,
+ *     FX16 216 / 170 / - / -); CLUSTER for CHANNEL batches that allow it (FP32 9 x 440 x 82 cylinder
  *     samples: 53 against 24 GLUPS on ONE_STEP); ONE_STEP otherwise (FP64 is bound by the FP64
  *     rate).  In graph mode with FP32/FP16/BF16/FX16 storage a batch of unlike samples runs as
  *     groups of like samples, one group after another on one stream, each on its own kernel and its

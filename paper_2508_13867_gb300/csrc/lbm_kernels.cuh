@@ -3264,7 +3264,7 @@ const StripBlocks& strip3w_blocks() {
 // Staging of a fixed-width launch's phase-A rows: option 1 = none, 2 = the next row in shared memory
 // by cp.async, 3 = the next row in registers (0: the compiled default); as the kernel's D: 0, 1, 2.
 // The default is register staging (measured on the 625 x 256^2 ensemble, kernel GLUPS, none / shared
-// memory / registers: FP32 206 / 229 / 242, BF16 219 / 218 / 235, FP16 214 / 215 / 231, FX16 200 / 199
+// memory / registers: FP32 199 / 228 / 241, BF16 219 / 227 / 234, FP16 214 / 223 / 230, FX16 200 / 204
 // / 216; `def`, the runtime-width kernel's compiled staging, is not used).
 inline int strip3w_depth(int stage, int def) {
     (void)def;

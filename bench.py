@@ -701,7 +701,9 @@ def bench_gpu(args):
         ms, st, la = U.uqlb_last_loop_time(ens.ctx)
         loop_ms += ms
         loop_steps += st
-        launches += la + 2  # + projection and statistics kernels
+        # + the projection's launches (one per input dimension when sum-factorized) and the statistics
+        n_proj = len(w.bounds) if world == 1 and U.uqlb_last_projection(ens.ctx) == 1 else 1
+        launches += la + n_proj + 1
     ev0.record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()

@@ -501,14 +501,34 @@ int uqlb_w1_speed(uqlb_ctx* ctx, const void* a_dev, int dtype_a, int64_t s_a, in
  * Postprocessing (Sec. 4, Algorithm 1 statistics)
  * ---------------------------------------------------------------------------------- */
 
-/* Device workspace of uqlb_project / uqlb_stats (holds W on the device). */
+/* Device workspace of uqlb_project / uqlb_stats for the dense contraction (holds W on the device). */
 int uqlb_post_workspace_bytes(const uqlb_ctx* ctx, size_t* bytes);
+
+/* Device workspace with which uqlb_project takes its fastest contraction for n_fields fields: on a
+ * tensor Gauss-Legendre sample set with at most 16 points per input and degree at most 8, the tables
+ * and the intermediate buffers of the sum-factorized contraction (for the 4-D total-degree-4 basis on
+ * 5^4 points, 1000 rows of n_fields FP64 values); otherwise uqlb_post_workspace_bytes.  Requires
+ * uqlb_init_gpc. */
+int uqlb_project_workspace_bytes(const uqlb_ctx* ctx, int64_t n_fields, size_t* bytes);
 
 /* gPC coefficients (Eq. coef_discrete, gamma_k = 1): coeffs[k, f] = sum_s W[k, s] M[s, f],
  * accumulated in FP64.  m_dev: [S x n_fields] in `dtype` (UQLB_F64 or UQLB_F32) with row
- * stride m_ld; coeffs_dev: FP64 [K x n_fields] dense.  Requires uqlb_init_gpc. */
+ * stride m_ld; coeffs_dev: FP64 [K x n_fields] dense.  Requires uqlb_init_gpc.
+ * Two contractions, equal to FP64 round-off:
+ *   sum-factorized, on a tensor Gauss-Legendre sample set (at most 16 points per input, degree at
+ *     most 8) when the
+ *     workspace holds uqlb_project_workspace_bytes for n_fields (8-byte aligned).  W[k, s] is then
+ *     the product over the inputs of G[alpha_kq][s_q] = (w_s / 2) phi_a(x_s), so the sum over the
+ *     samples is taken one input at a time, the last input first: for d = 4, order 4, 5 points,
+ *     6 225 instead of 43 750 FP64 multiply-adds per field (d launches);
+ *   dense, [K x S] x [S x n_fields], with a workspace below that (uqlb_post_workspace_bytes suffices)
+ *     and for every other sample set; on one input the two coincide up to the order of operations.
+ * uqlb_last_projection reports which one the last call took. */
 int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld,
                  double* coeffs_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* The contraction of the last uqlb_project on ctx: 0 dense, 1 sum-factorized. */
+int uqlb_last_projection(const uqlb_ctx* ctx, int32_t* kind);
 
 /* uqlb_project for callers that cannot allocate device memory.  The paper has no counterpart:
  * this is an interface for hosts such as code running under a fixed device-memory budget,

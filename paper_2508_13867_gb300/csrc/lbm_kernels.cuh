@@ -2183,7 +2183,10 @@ __device__ __forceinline__ unsigned cluster_id_x() {
     asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
     return r;
 }
-constexpr int kClusterThreads = 1024;
+#ifndef UQLB_CLUSTER_THREADS
+#define UQLB_CLUSTER_THREADS 1024
+#endif
+constexpr int kClusterThreads = UQLB_CLUSTER_THREADS;
 // Fixed part of a cluster step's time, in node updates of one block (see launch_cluster_any).
 constexpr double kClusterStepFixed = 3400.0;
 

@@ -99,7 +99,75 @@ __global__ void mc_stats_kernel(const M* __restrict__ m, int64_t S, int64_t F, i
     }
 }
 
+// Sum factorization of the projection on a tensor Gauss-Legendre grid.  There W[k, s] is a product
+// over the input dimensions, W[k, s] = prod_q G[alpha_kq][s_q] with G[a][s] = (w_s / 2) phi_a(x_s) (the
+// 1-D probability weight times the orthonormal Legendre polynomial), so C = W M contracts one
+// dimension at a time, the last (fastest) first.  One stage maps an input T[(r n + s) J' + j'][f] to
+// T[r J + o(a, j')][f] = sum_{s < n} G[a][s] T[(r n + s) J' + j'][f] for every degree a that the
+// multi-index set admits after the partial index j' (a prefix a = 0 .. c - 1 of the degrees; o(a, j') =
+// -1 beyond it; at the last stage o is the coefficient's row k).  A thread owns one field and one
+// group (r, j'): it loads the n inputs once and accumulates the c outputs as independent chains, so
+// the FP64 pipe (a small fraction of the FP32 rate on GB300) always has several multiply-adds to
+// issue.  FP64 throughout.
+constexpr int kSfThreads = 256;
+
+template <typename TI>
+__global__ void __launch_bounds__(kSfThreads) sf_stage_kernel(const TI* __restrict__ in, int64_t in_ld,
+                                                              double* __restrict__ out, int64_t out_ld,
+                                                              int64_t groups, int jprev, int jout, int n, int p1,
+                                                              const int* __restrict__ oidx,
+                                                              const double* __restrict__ G, int64_t F) {
+    __shared__ double sG[kSfMaxDegree + 1][kSfMaxPoints];
+    for (int q = threadIdx.x; q < (kSfMaxDegree + 1) * kSfMaxPoints; q += kSfThreads) {
+        const int a = q / kSfMaxPoints, c = q % kSfMaxPoints;
+        sG[a][c] = a < p1 && c < n ? G[a * n + c] : 0.0;
+    }
+    __syncthreads();
+    const int64_t f = (int64_t)blockIdx.x * kSfThreads + threadIdx.x;
+    if (f >= F) return;  // no barrier below
+    for (int64_t g = blockIdx.y; g < groups; g += gridDim.y) {
+        const int64_t r = g / jprev;
+        const int jp = (int)(g - r * jprev);
+        int cnt = 0;  // admitted degrees: a prefix of 0 .. p1 - 1
+#pragma unroll
+        for (int a = 0; a <= kSfMaxDegree; ++a)
+            if (a < p1 && __ldg(oidx + jp * p1 + a) >= 0) cnt = a + 1;
+        double acc[kSfMaxDegree + 1];
+#pragma unroll
+        for (int a = 0; a <= kSfMaxDegree; ++a) acc[a] = 0.0;
+        const TI* src = in + ((r * n) * jprev + jp) * in_ld + f;
+        const int64_t step = (int64_t)jprev * in_ld;
+#pragma unroll
+        for (int q = 0; q < kSfMaxPoints; ++q) {
+            if (q < n) {
+                const double x = (double)src[q * step];
+#pragma unroll
+                for (int a = 0; a <= kSfMaxDegree; ++a)
+                    if (a < cnt) acc[a] = fma(sG[a][q], x, acc[a]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a <= kSfMaxDegree; ++a)
+            if (a < cnt) out[(r * jout + __ldg(oidx + jp * p1 + a)) * out_ld + f] = acc[a];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sf_stage(const void* in, int in_dtype, int64_t in_ld, double* out, int64_t out_ld, int64_t groups,
+                            int jprev, int jout, int n, int p1, const int* oidx, const double* G, int64_t F,
+                            cudaStream_t s) {
+    if (F <= 0 || groups <= 0) return cudaSuccess;
+    if (n < 1 || n > kSfMaxPoints || p1 < 1 || p1 > kSfMaxDegree + 1) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((F + kSfThreads - 1) / kSfThreads), (unsigned)(groups < 65535 ? groups : 65535));
+    if (in_dtype == UQLB_F64)
+        sf_stage_kernel<double><<<grid, kSfThreads, 0, s>>>(static_cast<const double*>(in), in_ld, out, out_ld, groups,
+                                                            jprev, jout, n, p1, oidx, G, F);
+    else
+        sf_stage_kernel<float><<<grid, kSfThreads, 0, s>>>(static_cast<const float*>(in), in_ld, out, out_ld, groups,
+                                                           jprev, jout, n, p1, oidx, G, F);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_project(const double* W, int K, int S, const void* M, int dtype, int64_t F, int64_t ld,
                            double* C, cudaStream_t s) {

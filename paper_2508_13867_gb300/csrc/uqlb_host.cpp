@@ -48,6 +48,18 @@ struct uqlb_ctx {
     std::vector<int32_t> alpha;
     std::vector<double> W;
     std::vector<double> w_block;  // host staging of the W columns of a sample block (uqlb_project_block)
+    // Sum-factorized projection of a tensor Gauss-Legendre grid (n = 0: not available): one stage per
+    // input dimension, the last first; stage m has groups[m] groups of jprev[m] partial indices in and
+    // jout[m] out, its admission table at idx_off[m] in `tables` (after G, the (order + 1) x n matrix of
+    // the 1-D factors); stages before the last write rows_out[m] rows into buffer A (odd stages) or B.
+    struct SumFactorPlan {
+        int n = 0, p1 = 0;
+        std::vector<int64_t> groups, rows_out;
+        std::vector<int> jprev, jout;
+        std::vector<size_t> idx_off;  // byte offsets into tables
+        std::vector<unsigned char> tables;
+        int64_t rows_a = 0, rows_b = 0;
+    } sf;
     cudaStream_t capture_stream = nullptr;
     cudaStream_t side_stream = nullptr;           // CHANNEL groups of a grouped batch (high priority)
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -64,6 +76,7 @@ struct uqlb_ctx {
     std::vector<uqlb_tune_candidate> tune_report;  // candidates of the last autotune (largest group)
     int tune_chosen = -1;
     int last_rows = 0, last_npt = 0, last_scheme = 0;
+    int last_projection = 0;  // the contraction of the last uqlb_project: 0 dense, 1 sum-factorized
     int cluster_blocks = 0, cluster_cols = 0;  // geometry of the last cluster launch
     int64_t counter_host[2] = {0, 0};  // source of the step-counter upload (step, first step of the run)
     int32_t* bar_err = nullptr;  // device error word of the last run
@@ -1298,8 +1311,87 @@ int uqlb_init_qmc(uqlb_ctx* ctx, int64_t n, int64_t skip) {
     return 0;
 }
 
+// The stage plan of the sum-factorized projection on the tensor grid of n points per dimension
+// (`sf` of the context; left empty where the grid or the multi-index set does not allow it).
+// Partial multi-indices over the dimensions q .. d - 1 are built from the last dimension down: stage
+// m admits degree a after the partial index j' when the total degree stays <= order (total-degree
+// basis) or a <= order (tensor basis); the full indices of the last stage are mapped to the rows k of
+// the context's basis.
+void build_sum_factor_plan(uqlb_ctx* ctx, int n, const std::vector<double>& gx, const std::vector<double>& gw) {
+    auto& P = ctx->sf;
+    P = uqlb_ctx::SumFactorPlan{};
+    const int d = ctx->dim, p1 = ctx->order + 1;
+    if (n < 1 || n > kSfMaxPoints || d < 1 || ctx->order > kSfMaxDegree) return;
+    std::map<std::vector<int32_t>, int> k_of;
+    for (int k = 0; k < ctx->K; ++k)
+        k_of[std::vector<int32_t>(ctx->alpha.begin() + (size_t)k * d, ctx->alpha.begin() + (size_t)(k + 1) * d)] = k;
+    std::vector<std::vector<int32_t>> prev(1);  // J_0: the empty partial index
+    std::vector<int32_t> idx;
+    std::vector<size_t> idx_at;
+    int64_t npre = 1;  // n^q for the stage's dimension q
+    for (int q = 0; q + 1 < d; ++q) npre *= n;
+    for (int m = 1; m <= d; ++m) {
+        std::vector<std::vector<int32_t>> cur;
+        idx_at.push_back(idx.size());
+        for (auto& jp : prev) {
+            int deg = 0;
+            for (int v : jp) deg += v;
+            for (int a = 0; a < p1; ++a) {
+                const bool ok = ctx->basis == UQLB_BASIS_TENSOR ? true : a + deg <= ctx->order;
+                if (!ok) {
+                    idx.push_back(-1);
+                    continue;
+                }
+                std::vector<int32_t> full{a};
+                full.insert(full.end(), jp.begin(), jp.end());
+                if (m == d) {
+                    auto it = k_of.find(full);
+                    if (it == k_of.end()) return;  // not the context's basis: no plan
+                    idx.push_back(it->second);
+                } else {
+                    idx.push_back((int32_t)cur.size());
+                }
+                cur.push_back(full);
+            }
+        }
+        P.groups.push_back(npre * (int64_t)prev.size());
+        P.jprev.push_back((int)prev.size());
+        P.jout.push_back(m == d ? ctx->K : (int)cur.size());
+        P.rows_out.push_back(m == d ? ctx->K : npre * (int64_t)cur.size());
+        if (m < d) (m % 2 == 1 ? P.rows_a : P.rows_b) = std::max(m % 2 == 1 ? P.rows_a : P.rows_b, P.rows_out.back());
+        if (m == d && (int)cur.size() != ctx->K) {
+            P = uqlb_ctx::SumFactorPlan{};
+            return;
+        }
+        prev.swap(cur);
+        if (m < d) npre /= n;
+    }
+    std::vector<double> phis(p1);
+    const size_t gbytes = (size_t)p1 * n * sizeof(double);
+    P.tables.resize(gbytes + idx.size() * sizeof(int32_t));
+    double* G = reinterpret_cast<double*>(P.tables.data());
+    for (int q = 0; q < n; ++q) {
+        phi_values(ctx->order, gx[q], phis.data());
+        for (int a = 0; a < p1; ++a) G[(size_t)a * n + q] = 0.5 * gw[q] * phis[a];
+    }
+    std::memcpy(P.tables.data() + gbytes, idx.data(), idx.size() * sizeof(int32_t));
+    for (size_t at : idx_at) P.idx_off.push_back(gbytes + at * sizeof(int32_t));
+    P.n = n;
+    P.p1 = p1;
+}
+
+// Row stride (doubles) of the sum-factorization buffers, and their workspace for F fields.
+int64_t sf_ld(int64_t F) { return (F + 31) / 32 * 32; }
+size_t sf_workspace(const uqlb_ctx* ctx, int64_t F) {
+    const auto& P = ctx->sf;
+    return align_up(P.tables.size(), 256) + align_up((size_t)P.rows_a * sf_ld(F) * 8, 256) +
+           align_up((size_t)P.rows_b * sf_ld(F) * 8, 256);
+}
+bool sf_available(const uqlb_ctx* ctx) { return ctx->method == UQLB_METHOD_GPC && ctx->sf.n > 0; }
+
 int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad) {
     if (!ctx) return set_err(nullptr, UQLB_ERR_ARG, "null context");
+    ctx->sf = uqlb_ctx::SumFactorPlan{};
     if (ctx->dim < 1) return set_err(ctx, UQLB_ERR_STATE, "init_gpc: call uqlb_set_inputs first");
     if (quad != UQLB_QUAD_GAUSS_LEGENDRE_TENSOR && quad != UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
         return set_err(ctx, UQLB_ERR_ARG, "init_gpc: unknown quadrature");
@@ -1313,11 +1405,13 @@ int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad
     const int d = ctx->dim;
     int64_t S = 0;
     std::vector<double> ref_xi, ref_a;
+    std::vector<double> gx, gw;
     if (quad == UQLB_QUAD_GAUSS_LEGENDRE_TENSOR) {
         const double Sd = std::pow((double)pts_per_dim, d);
         if (Sd > (double)(1 << 24)) return set_err(ctx, UQLB_ERR_ARG, "init_gpc: tensor grid too large");
         S = (int64_t)std::llround(Sd);
-        std::vector<double> gx(pts_per_dim), gw(pts_per_dim);
+        gx.assign(pts_per_dim, 0.0);
+        gw.assign(pts_per_dim, 0.0);
         gauss_legendre_rule(pts_per_dim, gx.data(), gw.data());
         ref_xi.assign((size_t)S * d, 0.0);
         ref_a.assign((size_t)S, 0.0);
@@ -1365,6 +1459,7 @@ int uqlb_init_gpc(uqlb_ctx* ctx, int order, int pts_per_dim, int basis, int quad
     ctx->order = order;
     ctx->basis = basis;
     ctx->method = UQLB_METHOD_GPC;
+    if (quad == UQLB_QUAD_GAUSS_LEGENDRE_TENSOR) build_sum_factor_plan(ctx, pts_per_dim, gx, gw);
     return 0;
 }
 
@@ -1913,6 +2008,17 @@ int uqlb_post_workspace_bytes(const uqlb_ctx* ctx, size_t* bytes) {
     return 0;
 }
 
+int uqlb_project_workspace_bytes(const uqlb_ctx* ctx, int64_t n_fields, size_t* bytes) {
+    if (!ctx || !bytes || n_fields < 0) return set_err(nullptr, UQLB_ERR_ARG, "project_workspace_bytes: bad arguments");
+    if (ctx->method != UQLB_METHOD_GPC)
+        return set_err(const_cast<uqlb_ctx*>(ctx), UQLB_ERR_STATE, "project_workspace_bytes: call uqlb_init_gpc first");
+    if (sf_available(ctx)) {
+        *bytes = sf_workspace(ctx, n_fields);
+        return 0;
+    }
+    return uqlb_post_workspace_bytes(ctx, bytes);
+}
+
 int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, int64_t m_ld, double* coeffs_dev,
                  void* workspace_dev, size_t workspace_bytes, void* stream) {
     if (int rc = check_ctx(ctx)) return rc;
@@ -1920,15 +2026,52 @@ int uqlb_project(uqlb_ctx* ctx, const void* m_dev, int dtype, int64_t n_fields, 
     if (!m_dev || !coeffs_dev || !workspace_dev || n_fields < 0 || m_ld < n_fields)
         return set_err(ctx, UQLB_ERR_ARG, "project: bad arguments");
     if (dtype != UQLB_F64 && dtype != UQLB_F32) return set_err(ctx, UQLB_ERR_ARG, "project: dtype must be F64 or F32");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    ctx->last_projection = 0;
+    if (sf_available(ctx) && workspace_bytes >= sf_workspace(ctx, n_fields) &&
+        reinterpret_cast<uintptr_t>(workspace_dev) % 8 == 0) {
+        // tensor grid: one contraction per input dimension (sf_stage_kernel), buffers A and B alternate
+        const auto& P = ctx->sf;
+        char* ws = static_cast<char*>(workspace_dev);
+        const int64_t ld = sf_ld(n_fields);
+        double* bufs[2] = {reinterpret_cast<double*>(ws + align_up(P.tables.size(), 256)), nullptr};
+        bufs[1] = bufs[0] + align_up((size_t)P.rows_a * ld * 8, 256) / 8;
+        if ((e = cudaMemcpyAsync(ws, P.tables.data(), P.tables.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(ctx, e, "project: table upload");
+        const double* G = reinterpret_cast<const double*>(ws);
+        const void* in = m_dev;
+        int in_dtype = dtype;
+        int64_t in_ld = m_ld;
+        const int nst = (int)P.groups.size();
+        for (int m = 0; m < nst; ++m) {
+            const bool last = m + 1 == nst;
+            double* out = last ? coeffs_dev : bufs[m % 2];
+            const int64_t out_ld = last ? n_fields : ld;
+            e = launch_sf_stage(in, in_dtype, in_ld, out, out_ld, P.groups[m], P.jprev[m], P.jout[m], P.n, P.p1,
+                                reinterpret_cast<const int*>(ws + P.idx_off[m]), G, n_fields, s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "project: stage launch");
+            in = out;
+            in_dtype = UQLB_F64;
+            in_ld = out_ld;
+        }
+        ctx->last_projection = 1;
+        return 0;
+    }
     size_t need = 0;
     uqlb_post_workspace_bytes(ctx, &need);
     if (workspace_bytes < need) return set_err(ctx, UQLB_ERR_OOM, "project: workspace of %zu bytes, need %zu", workspace_bytes, need);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemcpyAsync(workspace_dev, ctx->W.data(), ctx->W.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(workspace_dev, ctx->W.data(), ctx->W.size() * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "project: W upload");
     e = launch_project(static_cast<const double*>(workspace_dev), ctx->K, (int)ctx->S, m_dev, dtype, n_fields, m_ld,
                        coeffs_dev, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "project: launch");
+    return 0;
+}
+
+int uqlb_last_projection(const uqlb_ctx* ctx, int32_t* kind) {
+    if (!ctx || !kind) return set_err(nullptr, UQLB_ERR_ARG, "last_projection: null pointer");
+    *kind = ctx->last_projection;
     return 0;
 }
 
@@ -2013,7 +2156,9 @@ int uqlb_uq_workspace_bytes(const uqlb_ctx* ctx, const uqlb_case* c, const uqlb_
     b = align_up(b, 256) + align_up((size_t)ctx->S * F * eb, 256);                 // fields M
     b += align_up((size_t)std::max(ctx->K, 1) * F * 8, 256);                        // coefficients
     b += 2 * align_up((size_t)F * 8, 256);                                          // mean, var
-    b += align_up(std::max<size_t>(ctx->W.size(), 1) * 8, 256);                     // W
+    size_t pb = 0;                                                                   // projection scratch
+    if (ctx->method == UQLB_METHOD_GPC) uqlb_project_workspace_bytes(ctx, F, &pb);
+    b += align_up(std::max<size_t>(pb, 8), 256);
     b += align_up((size_t)ctx->S * UQLB_QOI_COLS * 8, 256);                         // qoi
     *bytes = b;
     return 0;
@@ -2043,13 +2188,13 @@ int uqlb_run_uq_host(uqlb_ctx* ctx, const uqlb_case* c, const uqlb_run_opts* opt
     double* var = reinterpret_cast<double*>(p + off);
     off += align_up((size_t)F * 8, 256);
     void* wbuf = p + off;
-    off += align_up(std::max<size_t>(ctx->W.size(), 1) * 8, 256);
+    size_t wb = 0;
+    if (ctx->method == UQLB_METHOD_GPC) uqlb_project_workspace_bytes(ctx, F, &wb);
+    off += align_up(std::max<size_t>(wb, 8), 256);
     double* qoi = reinterpret_cast<double*>(p + off);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (int rc = uqlb_run_ensemble(ctx, c, opts, workspace_dev, run_b, M, F, qoi, nullptr, nullptr, 0, stream)) return rc;
     if (ctx->method == UQLB_METHOD_GPC) {
-        size_t wb = 0;
-        uqlb_post_workspace_bytes(ctx, &wb);
         if (int rc = uqlb_project(ctx, M, opts->fields_dtype, F, F, C, wbuf, wb, stream)) return rc;
         if (int rc = uqlb_stats(ctx, C, UQLB_F64, F, F, mean, var, 0, stream)) return rc;
     } else {

@@ -206,6 +206,15 @@ int ctx_projection_view(uqlb_ctx* ctx, const double** W, int* K, int64_t* S, int
 int ctx_fail(uqlb_ctx* ctx, int code, const char* msg);
 
 // Postprocessing (project_kernels.cu).
+// Points per dimension and polynomial degree up to which the projection on a tensor Gauss-Legendre
+// grid is sum-factorized.
+constexpr int kSfMaxPoints = 16;
+constexpr int kSfMaxDegree = 8;
+// One stage of the sum-factorized projection (project_kernels.cu): out[r jout + oidx[j' p1 + a]][f] =
+// sum_{q < n} G[a n + q] in[(r n + q) jprev + j'][f] over groups (r, j'), rows of stride in_ld / out_ld.
+cudaError_t launch_sf_stage(const void* in, int in_dtype, int64_t in_ld, double* out, int64_t out_ld, int64_t groups,
+                            int jprev, int jout, int n, int p1, const int* oidx, const double* G, int64_t F,
+                            cudaStream_t s);
 cudaError_t launch_project(const double* W, int K, int S, const void* M, int dtype,
                            int64_t F, int64_t ld, double* C, cudaStream_t s);
 cudaError_t launch_gpc_stats(const double* C, int K, int64_t F, double* mean, double* var,

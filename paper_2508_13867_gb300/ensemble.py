@@ -190,15 +190,16 @@ class Ensemble:
 
     # ---- postprocessing ---------------------------------------------------------------
     def project(self, m: torch.Tensor, coeffs: torch.Tensor | None = None) -> torch.Tensor:
+        """gPC coefficients of the rows of m (the workspace of the library's fastest contraction)."""
         dtype = U.UQLB_F64 if m.dtype == torch.float64 else U.UQLB_F32
         F = m.shape[1]
         if coeffs is None:
             coeffs = torch.empty((self.num_terms, F), dtype=torch.float64, device=m.device)
-        wsb = U.uqlb_post_workspace_bytes(self.ctx)
+        wsb = U.uqlb_project_workspace_bytes(self.ctx, F)
         if not hasattr(self, "_post") or self._post.numel() < wsb:
             self._post = torch.empty(max(wsb, 256), dtype=torch.uint8, device=m.device)
         U.uqlb_project(self.ctx, m.data_ptr(), dtype, F, m.stride(0), coeffs.data_ptr(), self._post.data_ptr(),
-                       self._post.numel(), _stream())
+                       wsb, _stream())
         return coeffs
 
     def project_block(self, m: torch.Tensor, s0: int, coeffs: torch.Tensor | None = None) -> torch.Tensor:

@@ -117,6 +117,8 @@ _SIGNATURES = {
                       c_int64, c_int64, ctypes.c_int, c_void_p, c_size_t, _P(c_double), _P(c_double), _P(c_int64),
                       c_void_p],
     "uqlb_post_workspace_bytes": [c_void_p, _P(c_size_t)],
+    "uqlb_project_workspace_bytes": [c_void_p, c_int64, _P(c_size_t)],
+    "uqlb_last_projection": [c_void_p, _P(ctypes.c_int32)],
     "uqlb_project": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p, c_size_t, c_void_p],
     "uqlb_project_noalloc": [c_void_p, c_void_p, ctypes.c_int, c_int64, c_int64, c_void_p, c_void_p],
     "uqlb_get_weight_block": [c_void_p, c_int64, c_int64, _P(c_double)],
@@ -419,6 +421,18 @@ def uqlb_post_workspace_bytes(ctx) -> int:
     b = c_size_t()
     _check(lib().uqlb_post_workspace_bytes(ctx, ctypes.byref(b)), ctx)
     return b.value
+
+
+def uqlb_project_workspace_bytes(ctx, n_fields: int) -> int:
+    b = c_size_t()
+    _check(lib().uqlb_project_workspace_bytes(ctx, n_fields, ctypes.byref(b)), ctx)
+    return b.value
+
+
+def uqlb_last_projection(ctx) -> int:
+    k = ctypes.c_int32()
+    _check(lib().uqlb_last_projection(ctx, ctypes.byref(k)), ctx)
+    return k.value
 
 
 def uqlb_project(ctx, m_dev: int, dtype: int, n_fields: int, m_ld: int, coeffs_dev: int, workspace_dev: int,

@@ -319,6 +319,57 @@ def test_projection_and_gpc_stats_match_oracle(ens, dtype):
     e.close()
 
 
+@pytest.mark.parametrize("dims,pts,order,basis,n_fields,dtype", [
+    (1, 5, 4, "total", 1037, "f64"),
+    (2, 3, 2, "total", 777, "f32"),
+    (2, 4, 3, "tensor", 513, "f64"),
+    (3, 2, 1, "total", 300, "f32"),
+    (3, 16, 2, "total", 129, "f64"),
+    (4, 5, 4, "total", 1037, "f32"),
+    (4, 3, 2, "tensor", 65, "f32"),
+])
+def test_sum_factorized_projection_matches_the_oracle_and_the_dense_contraction(ens, dims, pts, order, basis,
+                                                                                n_fields, dtype):
+    """Projection on a tensor Gauss-Legendre grid taken one input at a time (Eq. coef_discrete with a
+    product weight), against the oracle's dense W M and the library's dense contraction (a block of
+    all samples); ragged field counts that leave a partial block of threads."""
+    bounds = [(0.5 + q, 1.5 + 2 * q) for q in range(dims)]
+    e = Ensemble(0)
+    e.set_inputs(bounds)
+    e.init_gpc(order, pts, basis=U.UQLB_BASIS_TENSOR if basis == "tensor" else U.UQLB_BASIS_TOTAL)
+    _, xi, a = ouq.tensor_grid([pts] * dims, bounds)
+    m = W.random_fields(pts ** dims, n_fields, seed=7 + dims, dtype=np.float64 if dtype == "f64" else np.float32)
+    mt = torch.from_numpy(m).cuda()
+    c_sf = e.project(mt)
+    assert U.uqlb_last_projection(e.ctx) == 1
+    c_dense = e.project_block(mt, 0)  # the dense contraction over the whole sample set
+    torch.cuda.synchronize()
+    c_ref = ouq.gpc_coefficients(ouq.multi_indices(dims, order, basis), xi, a, m.astype(np.float64))
+    scale = np.abs(c_ref).max()
+    assert np.abs(c_sf.cpu().numpy() - c_ref).max() < 1e-13 * scale
+    assert np.abs(c_sf.cpu().numpy() - c_dense.cpu().numpy()).max() < 1e-13 * scale
+    e.close()
+
+
+def test_projection_outside_the_sum_factorization_stays_dense(ens):
+    """Smolyak points and tensor grids of more than 16 points per input take the dense contraction with
+    either workspace."""
+    for pts, quad in ((3, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK), (17, U.UQLB_QUAD_GAUSS_LEGENDRE_TENSOR)):
+        e = Ensemble(0)
+        bounds = W.TGV4D_BOUNDS if pts == 3 else [(0.0, 1.0)]
+        e.set_inputs(bounds)
+        e.init_gpc(2, pts, quad=quad)
+        xi, a = ouq.smolyak_cc(4, 3) if pts == 3 else ouq.tensor_grid([17], bounds)[1:]
+        m = W.random_fields(len(a), 300, seed=5)
+        assert U.uqlb_project_workspace_bytes(e.ctx, 300) == U.uqlb_post_workspace_bytes(e.ctx)
+        c = e.project(torch.from_numpy(m).cuda())
+        assert U.uqlb_last_projection(e.ctx) == 0
+        torch.cuda.synchronize()
+        c_ref = ouq.gpc_coefficients(ouq.multi_indices(len(bounds), 2), xi, a, m)
+        assert np.abs(c.cpu().numpy() - c_ref).max() < 1e-13 * np.abs(c_ref).max()
+        e.close()
+
+
 def test_mc_stats_match_numpy(ens):
     e = Ensemble(0)
     e.set_inputs([(0.0, 1.0)])

@@ -93,6 +93,35 @@ def test_gpc_sample_set_and_weight_matrix_match_oracle():
         U.uqlb_destroy(ctx)
 
 
+def test_projection_workspace_selects_the_contraction():
+    """The projection's workspace query (no device work): a tensor Gauss-Legendre grid of at most 16
+    points per input gets the sum-factorization buffers, which grow with the field count (the
+    intermediate tensors of rows x fields FP64 values: for 5^4 points and total degree 4, 625 and 375
+    rows; for 16^2 points and degree 2, 16 x 3); Smolyak grids, tensor grids of 17 points and Monte
+    Carlo sets keep the dense workspace or have none."""
+    ctx = U.uqlb_create(0)
+    try:
+        U.uqlb_set_inputs(ctx, W.TGV4D_BOUNDS)
+        U.uqlb_init_gpc(ctx, 4, 5)
+        dense = U.uqlb_post_workspace_bytes(ctx)
+        assert dense >= 70 * 625 * 8
+        small, big = U.uqlb_project_workspace_bytes(ctx, 32), U.uqlb_project_workspace_bytes(ctx, 32 * 1000)
+        assert (625 + 375) * 32 * 8 <= small < (625 + 375) * 32 * 8 + 4096
+        assert (625 + 375) * 32000 * 8 <= big < (625 + 375) * 32000 * 8 + 4096
+        U.uqlb_init_gpc(ctx, 2, 3, 0, U.UQLB_QUAD_CLENSHAW_CURTIS_SMOLYAK)
+        assert U.uqlb_project_workspace_bytes(ctx, 32000) == U.uqlb_post_workspace_bytes(ctx)
+        U.uqlb_set_inputs(ctx, [(0.0, 1.0), (1.0, 2.0)])
+        U.uqlb_init_gpc(ctx, 2, 17)
+        assert U.uqlb_project_workspace_bytes(ctx, 32000) == U.uqlb_post_workspace_bytes(ctx)
+        U.uqlb_init_gpc(ctx, 2, 16)  # one intermediate tensor of 16 x 3 rows
+        assert 48 * 32000 * 8 <= U.uqlb_project_workspace_bytes(ctx, 32000) < 48 * 32000 * 8 + 4096
+        U.uqlb_init_mc(ctx, 100, 1)
+        with pytest.raises(U.UqlbError):
+            U.uqlb_project_workspace_bytes(ctx, 32)
+    finally:
+        U.uqlb_destroy(ctx)
+
+
 def test_mc_sample_set_matches_oracle_bit_for_bit():
     ctx = U.uqlb_create(0)
     try:

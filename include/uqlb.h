@@ -247,14 +247,14 @@ typedef struct {
  *     GB300, 625 x 256^2 ensemble, kernel GLUPS three-step strips / two-step strips / tiles /
  *     one-step: FP32 242 / 179 / 115 / 84, BF16 234 / 184 / 103 / 90, FP16 231 / 173 / 95 / 82,
  *     FX16 216 / 170 / - / -); CLUSTER for CHANNEL batches that allow it (FP32 9 x 440 x 82 cylinder
- *     samples: 53 against 24 GLUPS on ONE_STEP); ONE_STEP otherwise (FP64 is bound by the FP64
+ *     samples: 57 against 24 GLUPS on ONE_STEP); ONE_STEP otherwise (FP64 is bound by the FP64
  *     rate).  In graph mode with FP32/FP16/BF16/FX16 storage a batch of unlike samples runs as
  *     groups of like samples, each on its own kernel and its own slice of the workspace
  *     (uqlb_batch_workspace_bytes counts them all).  The periodic groups run one after another on
  *     `stream`; the CHANNEL groups run at the same time on a second stream of the context (created at
  *     the first such run, highest priority), which `stream` waits for before any later work, so the
  *     latency-bound channel kernels share the SMs with the bandwidth-bound strips (uneven batch of
- *     256 TGV and 64 channel samples, BF16: 139.8 against 127.7 GLUPS one group after another).
+ *     256 TGV and 64 channel samples, BF16: 0.739 against 0.814 s one group after another).
  *     Groups: CHANNEL samples on CLUSTER where they fit (taken in order of size while the group's
  *     largest width and height fit), the other CHANNEL samples on ONE_STEP, periodic samples of each
  *     width the strips take on the strips, wider periodic samples on TWO_STEP_TILES.  Outputs keep the

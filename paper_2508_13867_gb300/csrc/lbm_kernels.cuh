@@ -2277,6 +2277,15 @@ __host__ __device__ constexpr size_t cluster_state_bytes(int cw, int ny, int eb)
     return ((size_t)9 * cw * ny * eb + 15) / 16 * 16;
 }
 
+// The cluster kernel's node pass: one copy per step parity (compile-time parity) or one copy with the
+// parity tested per population.  UQLB_CLUSTER_SPLIT_PARITY 1: split, 0: not, 2: split for 16-bit
+// storage only.  Measured (GLUPS, split / not): FP32 cylinder 56.1 / 57.9, BF16 channel samples of the
+// uneven batch 57.4 / 53.6.
+#ifndef UQLB_CLUSTER_SPLIT_PARITY
+#define UQLB_CLUSTER_SPLIT_PARITY 2
+#endif
+template <typename S>
+constexpr bool kClusterSplitParity = UQLB_CLUSTER_SPLIT_PARITY == 1 || (UQLB_CLUSTER_SPLIT_PARITY == 2 && sizeof(S) == 2);
 template <typename S>
 __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) {
     extern __shared__ __align__(16) unsigned char s6_raw[];
@@ -2416,84 +2425,178 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         // work units of 32 list entries, one per lane: warp w takes unit w in the first round and unit
         // 32 r + 31 - w in round r >= 1.  The lists start with the costlier boundary and edge nodes,
         // so the warps that took those in the first round take no unit of a last, partial round.
-        const int lane = tid & 31, wid = tid >> 5;
-        constexpr int NW = kClusterThreads / 32;
-        for (int r = 0; r * NW * 32 < e3; ++r) {
-            const int k = (r * NW + (r == 0 ? wid : NW - 1 - wid)) * 32 + lane;
-            if (k >= e3) continue;
-            const uint32_t e = list[k];
-            const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
-            const uint32_t lw = k < e0 ? links[own] : 0u;
-            C g[9];
-            if (odd) {
-                S v[9];
-                gather_odd(k, yn, xn, own, lw, v);
+        if constexpr (kClusterSplitParity<S>) {
+            // the parity of the step is a compile-time branch of the node pass (one copy of the pass per
+            // parity), so no per-population test of it remains
+            auto node_pass = [&](auto parity) {
+                constexpr bool ODD = decltype(parity)::value;
+                const int lane = tid & 31, wid = tid >> 5;
+                constexpr int NW = kClusterThreads / 32;
+                for (int r = 0; r * NW * 32 < e3; ++r) {
+                    const int k = (r * NW + (r == 0 ? wid : NW - 1 - wid)) * 32 + lane;
+                    if (k >= e3) continue;
+                    const uint32_t e = list[k];
+                    const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
+                    const uint32_t lw = k < e0 ? links[own] : 0u;
+                    C g[9];
+                    if constexpr (ODD) {
+                        S v[9];
+                        gather_odd(k, yn, xn, own, lw, v);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(v + i, qz, i);
-            } else {
+                        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(v + i, qz, i);
+        
+        } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + i * pl + own, qz, i);
-            }
-            C drho, jx, jy, ux, uy;
-            moments(g, drho, jx, jy, ux, uy);
-            bgk(g, omega, drho, jx, jy, ux, uy);
-            const uint32_t h = sr ? mix32((uint32_t)((int64_t)yn * sp.pitch + x0 + xn) * 0x9E3779B1u +
-                                          (uint32_t)t * 0x85EBCA77u + sid * 0xC2B2AE3Du)
-                                  : 0u;
-            // the stored value of population i (rounded as the storage rounds)
-            auto cvt = [&](C v, int i) {
-                S r;
-                if (sr)
-                    Storage<S>::store_sr(&r, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
-                else
-                    Storage<S>::store(&r, v, qz, i);
-                return r;
+                        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + i * pl + own, qz, i);
+                    }
+                    C drho, jx, jy, ux, uy;
+                    moments(g, drho, jx, jy, ux, uy);
+                    bgk(g, omega, drho, jx, jy, ux, uy);
+                    const uint32_t h = sr ? mix32((uint32_t)((int64_t)yn * sp.pitch + x0 + xn) * 0x9E3779B1u +
+                                                  (uint32_t)t * 0x85EBCA77u + sid * 0xC2B2AE3Du)
+                                          : 0u;
+                    // the stored value of population i (rounded as the storage rounds)
+                    auto cvt = [&](C v, int i) {
+                        S r;
+                        if (sr)
+                            Storage<S>::store_sr(&r, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
+                        else
+                            Storage<S>::store(&r, v, qz, i);
+                        return r;
+                    };
+                    if (k >= e0) {
+                        // every link interior: even steps write g*_i into the node's slot opp(i), odd steps
+                        // into slot i of the neighbour x + c_i (across the slab's edge for the three
+                        // populations of an edge node that leave it)
+                        lat[own] = cvt(g[0], 0);
+                        const bool edge = k < e2, at_left = k < e1;
+#pragma unroll
+                        for (int i = 1; i < 9; ++i) {
+                            if constexpr (!ODD)
+                                lat[opp(i) * pl + own] = cvt(g[i], i);
+                            else if (edge && (at_left ? cx(i) < 0 : cx(i) > 0))
+                                st_cluster<S>(remote(at_left, i, yn + cy(i)), cvt(g[i], i));
+                            else
+                                lat[i * pl + own + cy(i) * cw + cx(i)] = cvt(g[i], i);
+                        }
+                        continue;
+                    }
+                    lat[own] = cvt(g[0], 0);
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) {
+                        const int cls = (lw >> (3 * i)) & 7;
+                        const int o = opp(i);
+                        if (cls == kInterior) {
+                            if constexpr (!ODD) {
+                                lat[o * pl + own] = cvt(g[i], i);
+                            } else {
+                                const int dl = xn + cx(i), dy = yn + cy(i);
+                                if (dl >= 0 && dl < ncol)
+                                    lat[i * pl + dy * cw + dl] = cvt(g[i], i);
+                                else
+                                    st_cluster<S>(remote(dl < 0, i, dy), cvt(g[i], i));
+                            }
+                        } else if (cls == kWall || cls == kSolid) {
+                            lat[o * pl + own] = cvt(g[i], i);
+                            if (f_step && cls == kSolid) {
+                                const C fs = g[i] + wgt<C>(i);
+                                fx += (double)(C(2 * cx(i)) * fs);
+                                fy += (double)(C(2 * cy(i)) * fs);
+                            }
+                        } else if (cls == kInlet) {
+                            const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
+                            lat[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
+                        } else {
+                            const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
+                            lat[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
+                        }
+                    }
+                }
             };
-            if (k >= e0) {
-                // every link interior: even steps write g*_i into the node's slot opp(i), odd steps
-                // into slot i of the neighbour x + c_i (across the slab's edge for the three
-                // populations of an edge node that leave it)
+            if (odd)
+                node_pass(std::true_type{});
+            else
+                node_pass(std::false_type{});
+            } else {
+            const int lane = tid & 31, wid = tid >> 5;
+            constexpr int NW = kClusterThreads / 32;
+            for (int r = 0; r * NW * 32 < e3; ++r) {
+                const int k = (r * NW + (r == 0 ? wid : NW - 1 - wid)) * 32 + lane;
+                if (k >= e3) continue;
+                const uint32_t e = list[k];
+                const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
+                const uint32_t lw = k < e0 ? links[own] : 0u;
+                C g[9];
+                if (odd) {
+                    S v[9];
+                    gather_odd(k, yn, xn, own, lw, v);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(v + i, qz, i);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + i * pl + own, qz, i);
+                }
+                C drho, jx, jy, ux, uy;
+                moments(g, drho, jx, jy, ux, uy);
+                bgk(g, omega, drho, jx, jy, ux, uy);
+                const uint32_t h = sr ? mix32((uint32_t)((int64_t)yn * sp.pitch + x0 + xn) * 0x9E3779B1u +
+                                              (uint32_t)t * 0x85EBCA77u + sid * 0xC2B2AE3Du)
+                                      : 0u;
+                // the stored value of population i (rounded as the storage rounds)
+                auto cvt = [&](C v, int i) {
+                    S r;
+                    if (sr)
+                        Storage<S>::store_sr(&r, v, (h * (0x2545F491u + 0x6A09E668u * (uint32_t)i)) >> 16, qz, i);
+                    else
+                        Storage<S>::store(&r, v, qz, i);
+                    return r;
+                };
+                if (k >= e0) {
+                    // every link interior: even steps write g*_i into the node's slot opp(i), odd steps
+                    // into slot i of the neighbour x + c_i (across the slab's edge for the three
+                    // populations of an edge node that leave it)
+                    lat[own] = cvt(g[0], 0);
+                    const bool edge = k < e2, at_left = k < e1;
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) {
+                        if (!odd)
+                            lat[opp(i) * pl + own] = cvt(g[i], i);
+                        else if (edge && (at_left ? cx(i) < 0 : cx(i) > 0))
+                            st_cluster<S>(remote(at_left, i, yn + cy(i)), cvt(g[i], i));
+                        else
+                            lat[i * pl + own + cy(i) * cw + cx(i)] = cvt(g[i], i);
+                    }
+                    continue;
+                }
                 lat[own] = cvt(g[0], 0);
-                const bool edge = k < e2, at_left = k < e1;
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
-                    if (!odd)
-                        lat[opp(i) * pl + own] = cvt(g[i], i);
-                    else if (edge && (at_left ? cx(i) < 0 : cx(i) > 0))
-                        st_cluster<S>(remote(at_left, i, yn + cy(i)), cvt(g[i], i));
-                    else
-                        lat[i * pl + own + cy(i) * cw + cx(i)] = cvt(g[i], i);
-                }
-                continue;
-            }
-            lat[own] = cvt(g[0], 0);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const int cls = (lw >> (3 * i)) & 7;
-                const int o = opp(i);
-                if (cls == kInterior) {
-                    if (!odd) {
+                    const int cls = (lw >> (3 * i)) & 7;
+                    const int o = opp(i);
+                    if (cls == kInterior) {
+                        if (!odd) {
+                            lat[o * pl + own] = cvt(g[i], i);
+                        } else {
+                            const int dl = xn + cx(i), dy = yn + cy(i);
+                            if (dl >= 0 && dl < ncol)
+                                lat[i * pl + dy * cw + dl] = cvt(g[i], i);
+                            else
+                                st_cluster<S>(remote(dl < 0, i, dy), cvt(g[i], i));
+                        }
+                    } else if (cls == kWall || cls == kSolid) {
                         lat[o * pl + own] = cvt(g[i], i);
+                        if (f_step && cls == kSolid) {
+                            const C fs = g[i] + wgt<C>(i);
+                            fx += (double)(C(2 * cx(i)) * fs);
+                            fy += (double)(C(2 * cy(i)) * fs);
+                        }
+                    } else if (cls == kInlet) {
+                        const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
+                        lat[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
                     } else {
-                        const int dl = xn + cx(i), dy = yn + cy(i);
-                        if (dl >= 0 && dl < ncol)
-                            lat[i * pl + dy * cw + dl] = cvt(g[i], i);
-                        else
-                            st_cluster<S>(remote(dl < 0, i, dy), cvt(g[i], i));
+                        const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
+                        lat[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
                     }
-                } else if (cls == kWall || cls == kSolid) {
-                    lat[o * pl + own] = cvt(g[i], i);
-                    if (f_step && cls == kSolid) {
-                        const C fs = g[i] + wgt<C>(i);
-                        fx += (double)(C(2 * cx(i)) * fs);
-                        fy += (double)(C(2 * cy(i)) * fs);
-                    }
-                } else if (cls == kInlet) {
-                    const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
-                    lat[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
-                } else {
-                    const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                    lat[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
                 }
             }
         }

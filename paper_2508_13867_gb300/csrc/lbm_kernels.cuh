@@ -2144,7 +2144,8 @@ __global__ void __launch_bounds__(W / 2, strip3w_min_blocks<S, D>(W / 2)) strip3
 // Channel samples held on chip: one thread-block cluster per sample runs its whole time loop.
 // ------------------------------------------------------------------------------------------
 // The C blocks of a cluster split the sample's columns into C slabs of cw columns; each block keeps
-// its slab's populations once in shared memory ([9][ny][cw] of the storage type), so HBM is touched
+// its slab's populations once in shared memory (row after row, each row the nine populations of the
+// slab's columns padded to a compiled row width where it fits, in the storage type), so HBM is touched
 // only to load the state at the start and to write it back at the end.  The steps alternate the
 // two halves of the in-place AA order, counted from the run's first step: an even step reads a
 // node's own nine slots, collides (BGK, the one-step kernel's formulas) and writes each
@@ -2272,6 +2273,12 @@ __device__ __forceinline__ int ld_cluster_s32(uint32_t addr) {
     return v;
 }
 
+// Columns a cluster block's rows hold for a slab of cw columns: the smallest compiled row width
+// (16, 32, 48, 64) at least cw, 0 beyond 64.
+__host__ __device__ constexpr int cluster_padded_width(int cw) {
+    return cw <= 16 ? 16 : (cw <= 32 ? 32 : (cw <= 48 ? 48 : (cw <= 64 ? 64 : 0)));
+}
+
 // Bytes of one slab state in a cluster block, rounded up to 16 (the link words follow it).
 __host__ __device__ constexpr size_t cluster_state_bytes(int cw, int ny, int eb) {
     return ((size_t)9 * cw * ny * eb + 15) / 16 * 16;
@@ -2286,7 +2293,7 @@ __host__ __device__ constexpr size_t cluster_state_bytes(int cw, int ny, int eb)
 #endif
 template <typename S>
 constexpr bool kClusterSplitParity = UQLB_CLUSTER_SPLIT_PARITY == 1 || (UQLB_CLUSTER_SPLIT_PARITY == 2 && sizeof(S) == 2);
-template <typename S>
+template <typename S, int CW>
 __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) {
     extern __shared__ __align__(16) unsigned char s6_raw[];
     __shared__ __align__(16) SampleDev s_sp;
@@ -2306,11 +2313,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     // launch takes narrower slabs; the shared memory is sized for the widest)
     const int nx = sp.nx, ny = sp.ny, cw = (nx + (int)nrank - 1) / (int)nrank;
     const int x0 = (int)rank * cw, ncol = max(0, min(cw, nx - x0));  // this block's columns [x0, x0 + ncol)
-    const int pl = ny * cw;                                           // one population plane of a slab
-    S* const lat = reinterpret_cast<S*>(s6_raw);                      // the state: [9][ny][cw]
+    // row width of the block's state: CW columns (compiled), or the slab's cw when CW is 0
+    const int RC = CW > 0 ? CW : cw, RW = 9 * RC;
+    // the state: population i of row y and column lx at y RW + i RC + lx (each row's nine populations
+    // together, CW >= cw columns each, or cw), so the offset between any two slots a node touches is
+    // a compile-time constant where CW is compiled
+    S* const lat = reinterpret_cast<S*>(s6_raw);
     uint32_t* const links =
-        reinterpret_cast<uint32_t*>(s6_raw + cluster_state_bytes(cw, ny, (int)sizeof(S)));  // [ny][cw]
-    uint32_t* const list = links + pl;  // the fluid nodes, (y << 16) | column, grouped by path
+        reinterpret_cast<uint32_t*>(s6_raw + cluster_state_bytes(RC, ny, (int)sizeof(S)));  // [ny][RC]
+    uint32_t* const list = links + ny * RC;  // the fluid nodes, (y << 16) | column, grouped by path
     const typename Storage<S>::Q qz = quanta_of<S>(p, j);
     const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
     S* glob = static_cast<S*>(p.arena) + sp.f_off;
@@ -2323,7 +2334,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         const int y = n / ncol, lx = n - y * ncol, x = x0 + lx;
         const int64_t own = (int64_t)y * sp.pitch + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) lat[i * pl + y * cw + lx] = glob[i * sp.plane + own];
+        for (int i = 0; i < 9; ++i) lat[y * RW + i * RC + lx] = glob[i * sp.plane + own];
         uint32_t w = 0u;
         if (mask != nullptr && mask_solid(mask, mask_words(sp), x, y)) {
             w = 0xFFFFFFFFu;
@@ -2333,7 +2344,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
             // bit 0 (no direction uses bits 0..2): a node whose neighbours lie partly in another slab
             if (lx == 0 || lx == ncol - 1) w |= 1u;
         }
-        links[y * cw + lx] = w;
+        links[y * RC + lx] = w;
     }
     // shared::cluster addresses of the neighbouring blocks' states (same layout everywhere)
     const unsigned left = rank > 0 ? rank - 1 : rank, right = rank + 1 < nrank ? rank + 1 : rank;
@@ -2359,7 +2370,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         const int c0 = min(nnodes, tid * chunk), c1 = min(nnodes, c0 + chunk);
         int off[4] = {0, 0, 0, 0};
         for (int n = c0; n < c1; ++n) {
-            const int y = n / ncol, lx = n - y * ncol, k = kind(links[y * cw + lx], lx);
+            const int y = n / ncol, lx = n - y * ncol, k = kind(links[y * RC + lx], lx);
 #pragma unroll
             for (int c = 0; c < 4; ++c) off[c] += k == c;
         }
@@ -2371,7 +2382,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
 #pragma unroll
         for (int c = 0; c < 4; ++c) off[c] += base[c];
         for (int n = c0; n < c1; ++n) {
-            const int y = n / ncol, lx = n - y * ncol, k = kind(links[y * cw + lx], lx);
+            const int y = n / ncol, lx = n - y * ncol, k = kind(links[y * RC + lx], lx);
             const uint32_t e = ((uint32_t)y << 16) | (uint32_t)lx;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -2384,8 +2395,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     // shared::cluster address of slot i of row y in the left (column cw - 1) or right (column 0)
     // neighbouring slab
     auto remote = [&](bool to_left, int i, int y) {
-        return to_left ? nl + (uint32_t)(i * pl + y * cw + cw - 1) * (uint32_t)sizeof(S)
-                       : nr + (uint32_t)(i * pl + y * cw) * (uint32_t)sizeof(S);
+        return to_left ? nl + (uint32_t)(y * RW + i * RC + cw - 1) * (uint32_t)sizeof(S)
+                       : nr + (uint32_t)(y * RW + i * RC) * (uint32_t)sizeof(S);
     };
     // the incoming populations (stored values) of list entry k at an odd step: g*_i of the neighbour
     // x - c_i from its slot opp(i), or the node's own slot i across a boundary link (written there by
@@ -2394,7 +2405,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         v[0] = lat[own];
         if (k >= e2) {
 #pragma unroll
-            for (int i = 1; i < 9; ++i) v[i] = lat[opp(i) * pl + own - cy(i) * cw - cx(i)];
+            for (int i = 1; i < 9; ++i) v[i] = lat[own + opp(i) * RC - cy(i) * RW - cx(i)];
         } else if (k >= e0) {
             const bool at_left = k < e1;
 #pragma unroll
@@ -2402,18 +2413,18 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                 if (at_left ? cx(i) > 0 : cx(i) < 0)
                     v[i] = ld_cluster<S>(remote(at_left, opp(i), yn - cy(i)));
                 else
-                    v[i] = lat[opp(i) * pl + own - cy(i) * cw - cx(i)];
+                    v[i] = lat[own + opp(i) * RC - cy(i) * RW - cx(i)];
             }
         } else {
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const int sl = xn - cx(i), sy = yn - cy(i);
                 if (((lw >> (3 * opp(i))) & 7u) != kInterior)
-                    v[i] = lat[i * pl + own];
+                    v[i] = lat[own + i * RC];
                 else if (sl < 0 || sl >= ncol)
                     v[i] = ld_cluster<S>(remote(sl < 0, opp(i), sy));
                 else
-                    v[i] = lat[opp(i) * pl + sy * cw + sl];
+                    v[i] = lat[sy * RW + opp(i) * RC + sl];
             }
         }
     };
@@ -2436,8 +2447,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                     const int k = (r * NW + (r == 0 ? wid : NW - 1 - wid)) * 32 + lane;
                     if (k >= e3) continue;
                     const uint32_t e = list[k];
-                    const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
-                    const uint32_t lw = k < e0 ? links[own] : 0u;
+                    const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * RW + xn;
+                    const uint32_t lw = k < e0 ? links[yn * RC + xn] : 0u;
                     C g[9];
                     if constexpr (ODD) {
                         S v[9];
@@ -2447,7 +2458,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         
         } else {
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + i * pl + own, qz, i);
+                        for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + own + i * RC, qz, i);
                     }
                     C drho, jx, jy, ux, uy;
                     moments(g, drho, jx, jy, ux, uy);
@@ -2473,11 +2484,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
 #pragma unroll
                         for (int i = 1; i < 9; ++i) {
                             if constexpr (!ODD)
-                                lat[opp(i) * pl + own] = cvt(g[i], i);
+                                lat[own + opp(i) * RC] = cvt(g[i], i);
                             else if (edge && (at_left ? cx(i) < 0 : cx(i) > 0))
                                 st_cluster<S>(remote(at_left, i, yn + cy(i)), cvt(g[i], i));
                             else
-                                lat[i * pl + own + cy(i) * cw + cx(i)] = cvt(g[i], i);
+                                lat[own + i * RC + cy(i) * RW + cx(i)] = cvt(g[i], i);
                         }
                         continue;
                     }
@@ -2488,16 +2499,16 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                         const int o = opp(i);
                         if (cls == kInterior) {
                             if constexpr (!ODD) {
-                                lat[o * pl + own] = cvt(g[i], i);
+                                lat[own + o * RC] = cvt(g[i], i);
                             } else {
                                 const int dl = xn + cx(i), dy = yn + cy(i);
                                 if (dl >= 0 && dl < ncol)
-                                    lat[i * pl + dy * cw + dl] = cvt(g[i], i);
+                                    lat[dy * RW + i * RC + dl] = cvt(g[i], i);
                                 else
                                     st_cluster<S>(remote(dl < 0, i, dy), cvt(g[i], i));
                             }
                         } else if (cls == kWall || cls == kSolid) {
-                            lat[o * pl + own] = cvt(g[i], i);
+                            lat[own + o * RC] = cvt(g[i], i);
                             if (f_step && cls == kSolid) {
                                 const C fs = g[i] + wgt<C>(i);
                                 fx += (double)(C(2 * cx(i)) * fs);
@@ -2505,10 +2516,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                             }
                         } else if (cls == kInlet) {
                             const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
-                            lat[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
+                            lat[own + o * RC] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
                         } else {
                             const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                            lat[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
+                            lat[own + o * RC] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
                         }
                     }
                 }
@@ -2524,8 +2535,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                 const int k = (r * NW + (r == 0 ? wid : NW - 1 - wid)) * 32 + lane;
                 if (k >= e3) continue;
                 const uint32_t e = list[k];
-                const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
-                const uint32_t lw = k < e0 ? links[own] : 0u;
+                const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * RW + xn;
+                const uint32_t lw = k < e0 ? links[yn * RC + xn] : 0u;
                 C g[9];
                 if (odd) {
                     S v[9];
@@ -2534,7 +2545,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                     for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(v + i, qz, i);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + i * pl + own, qz, i);
+                    for (int i = 0; i < 9; ++i) g[i] = Storage<S>::load(lat + own + i * RC, qz, i);
                 }
                 C drho, jx, jy, ux, uy;
                 moments(g, drho, jx, jy, ux, uy);
@@ -2560,11 +2571,11 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
                         if (!odd)
-                            lat[opp(i) * pl + own] = cvt(g[i], i);
+                            lat[own + opp(i) * RC] = cvt(g[i], i);
                         else if (edge && (at_left ? cx(i) < 0 : cx(i) > 0))
                             st_cluster<S>(remote(at_left, i, yn + cy(i)), cvt(g[i], i));
                         else
-                            lat[i * pl + own + cy(i) * cw + cx(i)] = cvt(g[i], i);
+                            lat[own + i * RC + cy(i) * RW + cx(i)] = cvt(g[i], i);
                     }
                     continue;
                 }
@@ -2575,16 +2586,16 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                     const int o = opp(i);
                     if (cls == kInterior) {
                         if (!odd) {
-                            lat[o * pl + own] = cvt(g[i], i);
+                            lat[own + o * RC] = cvt(g[i], i);
                         } else {
                             const int dl = xn + cx(i), dy = yn + cy(i);
                             if (dl >= 0 && dl < ncol)
-                                lat[i * pl + dy * cw + dl] = cvt(g[i], i);
+                                lat[dy * RW + i * RC + dl] = cvt(g[i], i);
                             else
                                 st_cluster<S>(remote(dl < 0, i, dy), cvt(g[i], i));
                         }
                     } else if (cls == kWall || cls == kSolid) {
-                        lat[o * pl + own] = cvt(g[i], i);
+                        lat[own + o * RC] = cvt(g[i], i);
                         if (f_step && cls == kSolid) {
                             const C fs = g[i] + wgt<C>(i);
                             fx += (double)(C(2 * cx(i)) * fs);
@@ -2592,10 +2603,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
                         }
                     } else if (cls == kInlet) {
                         const C yy = C(yn) + C(0.5) - C(0.5) * C(cy(o));
-                        lat[o * pl + own] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
+                        lat[own + o * RC] = cvt(g[i] + C(6) * wgt<C>(o) * C(cx(o)) * inflow<C>(sp, yy, t), i);
                     } else {
                         const C cu = C(cx(o)) * ux + C(cy(o)) * uy;
-                        lat[o * pl + own] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
+                        lat[own + o * RC] = cvt(-g[i] + wgt<C>(o) * (C(9) * cu * cu - C(3) * (ux * ux + uy * uy)), i);
                     }
                 }
             }
@@ -2634,26 +2645,26 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
         if (((t - t0) & 1) != 0) {
             for (int k = tid; k < e3; k += kClusterThreads) {
                 const uint32_t e = list[k];
-                const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * cw + xn;
+                const int yn = (int)(e >> 16), xn = (int)(e & 0xFFFFu), own = yn * RW + xn;
                 S v[9];
-                gather_odd(k, yn, xn, own, k < e0 ? links[own] : 0u, v);
+                gather_odd(k, yn, xn, own, k < e0 ? links[yn * RC + xn] : 0u, v);
                 const int64_t at = (int64_t)yn * sp.pitch + x0 + xn;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = v[i];
             }
             for (int n = tid; n < ny * ncol; n += kClusterThreads) {
                 const int y = n / ncol, lx = n - y * ncol;
-                if (links[y * cw + lx] != 0xFFFFFFFFu) continue;
+                if (links[y * RC + lx] != 0xFFFFFFFFu) continue;
                 const int64_t at = (int64_t)y * sp.pitch + x0 + lx;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = lat[i * pl + y * cw + lx];
+                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = lat[y * RW + i * RC + lx];
             }
         } else {
             for (int n = tid; n < ny * ncol; n += kClusterThreads) {
                 const int y = n / ncol, lx = n - y * ncol;
                 const int64_t at = (int64_t)y * sp.pitch + x0 + lx;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = lat[i * pl + y * cw + lx];
+                for (int i = 0; i < 9; ++i) glob[i * sp.plane + at] = lat[y * RW + i * RC + lx];
             }
         }
         if (rank == 0 && tid == 0 && !p.done[sp.slot]) p.steps_run[sp.slot] = t;
@@ -2661,20 +2672,28 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     cluster_sync_all();  // no block leaves while another may still read its shared memory
 }
 
+// Shared memory of a cluster block whose rows hold CW columns (state, link words, node list).
 template <typename S>
-size_t cluster_smem(int cw, int ny) {
-    return cluster_state_bytes(cw, ny, (int)sizeof(S)) + (size_t)2 * cw * ny * sizeof(uint32_t);  // state, links, list
+size_t cluster_smem(int CW, int ny) {
+    return cluster_state_bytes(CW, ny, (int)sizeof(S)) + (size_t)2 * CW * ny * sizeof(uint32_t);
+}
+constexpr size_t kClusterSmemMax = 227 * 1024 - 4096;
+// Row width of the launch for slabs of cw columns and ny rows: the padded compiled width where its
+// shared memory fits, else 0 (rows of exactly cw columns, strides at run time).
+template <typename S>
+int cluster_row_width(int cw, int ny) {
+    const int w = cluster_padded_width(cw);
+    return w > 0 && cluster_smem<S>(w, ny) <= kClusterSmemMax ? w : 0;
 }
 
-template <typename S>
-cudaError_t launch_cluster_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
-    const int csize = p.cluster_size, cw = p.cluster_cw;
-    if (csize < 1 || csize > 16 || cw < 1) return cudaErrorInvalidConfiguration;
-    const size_t smem = cluster_smem<S>(cw, p.cluster_ny);
+template <typename S, int CW>
+cudaError_t launch_cluster_w(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const int csize = p.cluster_size;
+    const size_t smem = cluster_smem<S>(CW > 0 ? CW : p.cluster_cw, p.cluster_ny);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
+        cudaFuncSetAttribute(cluster_kernel<S, CW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(cluster_kernel<S, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
         attr = true;
     }
     if (prepare_only) return cudaGetLastError();
@@ -2690,7 +2709,20 @@ cudaError_t launch_cluster_s(const KParams& p, const BatchGeometry& g, cudaStrea
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, cluster_kernel<S>, p);
+    return cudaLaunchKernelEx(&cfg, cluster_kernel<S, CW>, p);
+}
+
+template <typename S>
+cudaError_t launch_cluster_s(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
+    const int csize = p.cluster_size, cw = p.cluster_cw;
+    if (csize < 1 || csize > 16 || cw < 1) return cudaErrorInvalidConfiguration;
+    switch (cluster_row_width<S>(cw, p.cluster_ny)) {
+        case 16: return launch_cluster_w<S, 16>(p, g, s, prepare_only);
+        case 32: return launch_cluster_w<S, 32>(p, g, s, prepare_only);
+        case 48: return launch_cluster_w<S, 48>(p, g, s, prepare_only);
+        case 64: return launch_cluster_w<S, 64>(p, g, s, prepare_only);
+        default: return launch_cluster_w<S, 0>(p, g, s, prepare_only);
+    }
 }
 
 // Clusters of `csize` blocks with `smem` bytes each that can run at once (0: none).
@@ -2701,8 +2733,9 @@ int cluster_capacity(int csize, size_t smem) {
         int cap;
     } cache[17] = {};
     if (cache[csize].smem == smem && smem != 0) return cache[csize].cap;
-    cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(cluster_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
+    // every row width's kernel runs one 1024-thread block per SM; the 64-column one stands for all
+    cudaFuncSetAttribute(cluster_kernel<S, 64>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(cluster_kernel<S, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 2048);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)csize);
     cfg.blockDim = dim3(kClusterThreads);
@@ -2715,7 +2748,7 @@ int cluster_capacity(int csize, size_t smem) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel<S>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel<S, 64>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         n = 0;
     }
@@ -3476,9 +3509,9 @@ cudaError_t launch_cluster_any(const KParams& p, const BatchGeometry& g, cudaStr
         int best_c = 0, best_cw = 0;
         double best_cost = 0.0;
         for (int c = 16; c >= 1; --c) {
-            const int cw = (g.cluster_nx + c - 1) / c;
-            const size_t smem = cluster_smem<S>(cw, g.cluster_ny);
-            if (smem > 227 * 1024 - 4096) continue;
+            const int cw = (g.cluster_nx + c - 1) / c, w = cluster_row_width<S>(cw, g.cluster_ny);
+            const size_t smem = cluster_smem<S>(w > 0 ? w : cw, g.cluster_ny);
+            if (smem > kClusterSmemMax) continue;
             const int cap = cluster_capacity<S>(c, smem);
             if (cap < 1) continue;
             const double waves = (double)((g.nsamples + cap - 1) / cap);

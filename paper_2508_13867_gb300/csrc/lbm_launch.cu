@@ -106,7 +106,7 @@ bool cluster_fits(int storage, int nx, int ny) {
     if (storage == UQLB_F64 || nx < 1 || ny < 1) return false;
     const size_t eb = storage == UQLB_F32 ? 4 : 2;
     for (int c = 1; c <= 16; ++c) {
-        const int cw = (nx + c - 1) / c;
+        const int cw = (nx + c - 1) / c;  // rows of exactly cw columns where no padded width fits
         const size_t smem = (9 * (size_t)cw * ny * eb + 15) / 16 * 16 + 2 * (size_t)cw * ny * sizeof(uint32_t);
         if (smem <= 227 * 1024 - 4096) return true;
     }

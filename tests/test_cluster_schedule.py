@@ -1,6 +1,8 @@
 """The cluster kernel's data layout and in-place steps, replayed on the CPU (no GPU): a channel
-sample's columns split into C slabs of cw columns, each block holding [9][ny][cw] once in shared
-memory.  The replay mirrors the kernel's index arithmetic (the CUDA source is not imported): the
+sample's columns split into C slabs of cw columns, each block holding its slab's state once in shared
+memory, row after row, each row the nine populations of CW >= cw columns (CW the smallest of 16, 32,
+48, 64 that holds cw and fits, else cw; slot (i, y, lx) at y 9 CW + i CW + lx).  The replay mirrors the kernel's index
+arithmetic (the CUDA source is not imported): the
 four node lists (boundary nodes, interior nodes at the slab's left and right edges, inner nodes),
 placed by each thread's contiguous run and a scan, hold every fluid node exactly once, and the
 warps' work units take every entry once; the link classes (wall, inlet, outlet, obstacle,
@@ -40,7 +42,10 @@ def replay(nd, csize, obstacle=True):
     solid = U.uqlb_obstacle_mask(sample_struct(spec)).astype(bool)
     nx, ny = spec.nx, spec.ny
     cw = (nx + csize - 1) // csize
-    pl = ny * cw
+    # row width: the smallest compiled width (16, 32, 48, 64) holding cw whose FP32 state, link words
+    # and node list fit a block's shared memory, else cw itself
+    CW = next((w for w in (16, 32, 48, 64) if w >= cw and ny * w * 44 <= 227 * 1024 - 4096), cw)
+    pl = ny * CW
     lists = []
     for rank in range(csize):
         x0 = rank * cw
@@ -223,15 +228,19 @@ def replay(nd, csize, obstacle=True):
         for y, lx, _ in lst:
             for i in range(9):
                 assert slots[rank, i, y, lx] == incoming(1, x0 + lx, y, i), (rank, y, lx, i)
+    # the linear slot index of every slot a block holds stays inside its state and is one to one
+    lin = {(i, y, lx): y * 9 * CW + i * CW + lx for i in range(9) for y in range(ny) for lx in range(cw)}
+    assert len(set(lin.values())) == len(lin) and 0 <= min(lin.values()) and max(lin.values()) < 9 * pl
     smem = (9 * pl * 4 + 15) // 16 * 16 + 2 * pl * 4
     return cw, smem
 
 
-@pytest.mark.parametrize("nd,csize", [(4, 2), (5, 4), (6, 3), (20, 16), (7, 8), (5, 1)])
+@pytest.mark.parametrize("nd,csize", [(4, 2), (5, 4), (6, 3), (20, 16), (7, 8), (5, 2), (5, 1)])
 def test_cluster_push_writes_every_slot_once(nd, csize):
     cw, smem = replay(nd, csize)
     if nd == 20 and csize == 16:
-        # the bench's cylinder: 28 columns per block, both states in FP32 fit one block's shared memory
+        # the bench's cylinder: 28 columns per block (rows of 32), the state in FP32 fits one block's
+        # shared memory
         assert cw == 28 and smem <= 227 * 1024 - 4096
 
 

@@ -247,7 +247,7 @@ typedef struct {
  *     GB300, 625 x 256^2 ensemble, kernel GLUPS three-step strips / two-step strips / tiles /
  *     one-step: FP32 242 / 179 / 115 / 84, BF16 234 / 184 / 103 / 90, FP16 231 / 173 / 95 / 82,
  *     FX16 216 / 170 / - / -); CLUSTER for CHANNEL batches that allow it (FP32 9 x 440 x 82 cylinder
- *     samples: 58 against 24 GLUPS on ONE_STEP); ONE_STEP otherwise (FP64 is bound by the FP64
+ *     samples: 60 against 24 GLUPS on ONE_STEP); ONE_STEP otherwise (FP64 is bound by the FP64
  *     rate).  In graph mode with FP32/FP16/BF16/FX16 storage a batch of unlike samples runs as
  *     groups of like samples, each on its own kernel and its own slice of the workspace
  *     (uqlb_batch_workspace_bytes counts them all).  The periodic groups run one after another on

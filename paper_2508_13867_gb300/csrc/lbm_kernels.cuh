@@ -2279,10 +2279,14 @@ __host__ __device__ constexpr int cluster_padded_width(int cw) {
     return cw <= 16 ? 16 : (cw <= 32 ? 32 : (cw <= 48 ? 48 : (cw <= 64 ? 64 : 0)));
 }
 
-// Bytes of one slab state in a cluster block, rounded up to 16 (the link words follow it).
-__host__ __device__ constexpr size_t cluster_state_bytes(int cw, int ny, int eb) {
-    return ((size_t)9 * cw * ny * eb + 15) / 16 * 16;
+// Bytes of one slab state of ny rows of rw elements in a cluster block, rounded up to 16 (the link
+// words follow it).
+__host__ __device__ constexpr size_t cluster_state_bytes(int rw, int ny, int eb) {
+    return ((size_t)rw * ny * eb + 15) / 16 * 16;
 }
+// Elements of storage type S that span the 32 four-byte shared-memory banks.
+template <typename S>
+constexpr int cluster_bank_span = 128 / (int)sizeof(S);
 
 // The cluster kernel's node pass: one copy per step parity (compile-time parity) or one copy with the
 // parity tested per population.  UQLB_CLUSTER_SPLIT_PARITY 1: split, 0: not, 2: split for 16-bit
@@ -2313,14 +2317,19 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     // launch takes narrower slabs; the shared memory is sized for the widest)
     const int nx = sp.nx, ny = sp.ny, cw = (nx + (int)nrank - 1) / (int)nrank;
     const int x0 = (int)rank * cw, ncol = max(0, min(cw, nx - x0));  // this block's columns [x0, x0 + ncol)
-    // row width of the block's state: CW columns (compiled), or the slab's cw when CW is 0
-    const int RC = CW > 0 ? CW : cw, RW = 9 * RC;
+    // row width of the block's state: CW columns (compiled), or the slab's cw when CW is 0; the rows
+    // lie RW elements apart, with RW = 9 RC padded on the compiled widths so that consecutive rows
+    // start cw elements (mod the 32 banks' span) apart: a warp's list entries, which run over the end
+    // of one row into the next, then take distinct banks as they would in one plane of cw columns
+    const int RC = CW > 0 ? CW : cw;
+    constexpr int M = cluster_bank_span<S>;
+    const int RW = 9 * RC + (CW > 0 ? ((cw - 9 * RC) % M + M) % M : 0);
     // the state: population i of row y and column lx at y RW + i RC + lx (each row's nine populations
     // together, CW >= cw columns each, or cw), so the offset between any two slots a node touches is
     // a compile-time constant where CW is compiled
     S* const lat = reinterpret_cast<S*>(s6_raw);
     uint32_t* const links =
-        reinterpret_cast<uint32_t*>(s6_raw + cluster_state_bytes(RC, ny, (int)sizeof(S)));  // [ny][RC]
+        reinterpret_cast<uint32_t*>(s6_raw + cluster_state_bytes(RW, ny, (int)sizeof(S)));  // [ny][RC]
     uint32_t* const list = links + ny * RC;  // the fluid nodes, (y << 16) | column, grouped by path
     const typename Storage<S>::Q qz = quanta_of<S>(p, j);
     const uint32_t* mask = sp.mask_off >= 0 ? p.masks + sp.mask_off : nullptr;
@@ -2672,10 +2681,13 @@ __global__ void __launch_bounds__(kClusterThreads, 1) cluster_kernel(KParams p) 
     cluster_sync_all();  // no block leaves while another may still read its shared memory
 }
 
-// Shared memory of a cluster block whose rows hold CW columns (state, link words, node list).
+// Shared memory of a cluster block whose rows hold CW columns (0: the slab's cw) for slabs of up to cw
+// columns and ny rows (state, link words, node list).
 template <typename S>
-size_t cluster_smem(int CW, int ny) {
-    return cluster_state_bytes(CW, ny, (int)sizeof(S)) + (size_t)2 * CW * ny * sizeof(uint32_t);
+size_t cluster_smem(int CW, int cw, int ny) {
+    // compiled width: rows of 9 CW elements plus the largest bank padding; else rows of 9 cw
+    const int rw = CW > 0 ? 9 * CW + cluster_bank_span<S> - 1 : 9 * cw, rc = CW > 0 ? CW : cw;
+    return cluster_state_bytes(rw, ny, (int)sizeof(S)) + (size_t)2 * rc * ny * sizeof(uint32_t);
 }
 constexpr size_t kClusterSmemMax = 227 * 1024 - 4096;
 // Row width of the launch for slabs of cw columns and ny rows: the padded compiled width where its
@@ -2683,13 +2695,13 @@ constexpr size_t kClusterSmemMax = 227 * 1024 - 4096;
 template <typename S>
 int cluster_row_width(int cw, int ny) {
     const int w = cluster_padded_width(cw);
-    return w > 0 && cluster_smem<S>(w, ny) <= kClusterSmemMax ? w : 0;
+    return w > 0 && cluster_smem<S>(w, cw, ny) <= kClusterSmemMax ? w : 0;
 }
 
 template <typename S, int CW>
 cudaError_t launch_cluster_w(const KParams& p, const BatchGeometry& g, cudaStream_t s, bool prepare_only) {
     const int csize = p.cluster_size;
-    const size_t smem = cluster_smem<S>(CW > 0 ? CW : p.cluster_cw, p.cluster_ny);
+    const size_t smem = cluster_smem<S>(CW, p.cluster_cw, p.cluster_ny);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(cluster_kernel<S, CW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -3510,7 +3522,7 @@ cudaError_t launch_cluster_any(const KParams& p, const BatchGeometry& g, cudaStr
         double best_cost = 0.0;
         for (int c = 16; c >= 1; --c) {
             const int cw = (g.cluster_nx + c - 1) / c, w = cluster_row_width<S>(cw, g.cluster_ny);
-            const size_t smem = cluster_smem<S>(w > 0 ? w : cw, g.cluster_ny);
+            const size_t smem = cluster_smem<S>(w, cw, g.cluster_ny);
             if (smem > kClusterSmemMax) continue;
             const int cap = cluster_capacity<S>(c, smem);
             if (cap < 1) continue;

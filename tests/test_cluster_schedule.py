@@ -1,7 +1,8 @@
 """The cluster kernel's data layout and in-place steps, replayed on the CPU (no GPU): a channel
 sample's columns split into C slabs of cw columns, each block holding its slab's state once in shared
 memory, row after row, each row the nine populations of CW >= cw columns (CW the smallest of 16, 32,
-48, 64 that holds cw and fits, else cw; slot (i, y, lx) at y 9 CW + i CW + lx).  The replay mirrors the kernel's index
+48, 64 that holds cw and fits, else cw; slot (i, y, lx) at y RW + i CW + lx, with the row stride RW >= 9 CW
+padded so that rows start cw elements apart modulo the 32 banks).  The replay mirrors the kernel's index
 arithmetic (the CUDA source is not imported): the
 four node lists (boundary nodes, interior nodes at the slab's left and right edges, inner nodes),
 placed by each thread's contiguous run and a scan, hold every fluid node exactly once, and the
@@ -42,9 +43,14 @@ def replay(nd, csize, obstacle=True):
     solid = U.uqlb_obstacle_mask(sample_struct(spec)).astype(bool)
     nx, ny = spec.nx, spec.ny
     cw = (nx + csize - 1) // csize
-    # row width: the smallest compiled width (16, 32, 48, 64) holding cw whose FP32 state, link words
-    # and node list fit a block's shared memory, else cw itself
-    CW = next((w for w in (16, 32, 48, 64) if w >= cw and ny * w * 44 <= 227 * 1024 - 4096), cw)
+    # row width: the smallest compiled width (16, 32, 48, 64) holding cw whose FP32 state (rows of
+    # 9 W + 31 elements at most), link words and node list fit a block's shared memory, else cw itself;
+    # on a compiled width the rows lie RW = 9 W + pad elements apart with RW = cw mod 32 (the banks)
+    fits = lambda w: ((9 * w + 31) * ny * 4 + 15) // 16 * 16 + 2 * w * ny * 4 <= 227 * 1024 - 4096  # noqa: E731
+    CW = next((w for w in (16, 32, 48, 64) if w >= cw and fits(w)), 0)
+    RW = 9 * CW + (cw - 9 * CW) % 32 if CW else 9 * cw
+    CW = CW or cw
+    assert RW >= 9 * CW and (not CW > cw or RW % 32 == cw % 32)
     pl = ny * CW
     lists = []
     for rank in range(csize):
@@ -229,9 +235,9 @@ def replay(nd, csize, obstacle=True):
             for i in range(9):
                 assert slots[rank, i, y, lx] == incoming(1, x0 + lx, y, i), (rank, y, lx, i)
     # the linear slot index of every slot a block holds stays inside its state and is one to one
-    lin = {(i, y, lx): y * 9 * CW + i * CW + lx for i in range(9) for y in range(ny) for lx in range(cw)}
-    assert len(set(lin.values())) == len(lin) and 0 <= min(lin.values()) and max(lin.values()) < 9 * pl
-    smem = (9 * pl * 4 + 15) // 16 * 16 + 2 * pl * 4
+    lin = {(i, y, lx): y * RW + i * CW + lx for i in range(9) for y in range(ny) for lx in range(cw)}
+    assert len(set(lin.values())) == len(lin) and 0 <= min(lin.values()) and max(lin.values()) < RW * ny
+    smem = (RW * ny * 4 + 15) // 16 * 16 + 2 * pl * 4
     return cw, smem
 
 
